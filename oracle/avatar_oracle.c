@@ -1,0 +1,680 @@
+/*
+ * FP64 CPU ORACLE for the relit-avatar render path of "Interactive Rendering
+ * of Relightable and Animatable Gaussian Avatars" (arXiv 2407.10707).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file; only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark do.  It shares no code, header, table or helper with the CUDA
+ * library: every definition below is written out again from the paper.
+ *
+ * Plain and slow on purpose: one loop nest per definition, double precision,
+ * no tiling, no fusion.  Per-pixel compositing runs over ALL Gaussians.
+ *
+ * Layout: row-major AoS double arrays ([N][3] etc.), indices int32.
+ *
+ * Passages followed:
+ *   orc_fk          Sec. 3.1 (forward kinematics feeding LBS; SMPL-style tree)
+ *   orc_skin        Sec. 3.1, Eq. 1 (attribute interpolation), LBS of position,
+ *                   normal and covariance ("rotated accordingly")
+ *   orc_visibility  Sec. 3.2 (mesh rasterisation toward D directions), in its
+ *                   shadow-mapping form (depth map + per-vertex depth test,
+ *                   the variant Sec. 3.2 contrasts itself with); integer rules
+ *   orc_shade       Eq. 2 (discrete rendering equation) with the BRDF of App. A,
+ *                   back-face cull and gamma of Sec. 3.1
+ *   orc_project     Sec. 3.1 (3DGS rasteriser input): EWA projection
+ *   orc_composite   Sec. 3.1 (3DGS rasteriser): front-to-back alpha blending,
+ *                   brute force per pixel over all Gaussians
+ *   orc_bin         tile membership and (depth, index) order of the 3DGS
+ *                   rasteriser, by brute force per tile
+ *
+ * Parity: pinned by the tests in tests/test_oracle_pins.py (closed forms,
+ * invariants, brute force on tiny inputs).  Readings of silent points are the
+ * ones listed in the design notes (lat-long geometry, gamma 2.2, integer
+ * visibility rules, 3DGS conventions).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------ */
+/* small dense helpers (3x3 row-major)                                 */
+/* ------------------------------------------------------------------ */
+static void mat3_mul(const double *A, const double *B, double *C)
+{
+    double t[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += A[3 * i + k] * B[3 * k + j];
+            t[3 * i + j] = s;
+        }
+    memcpy(C, t, sizeof t);
+}
+
+static void mat3_vec(const double *A, const double *x, double *y)
+{
+    double t[3];
+    for (int i = 0; i < 3; ++i) t[i] = A[3 * i] * x[0] + A[3 * i + 1] * x[1] + A[3 * i + 2] * x[2];
+    memcpy(y, t, sizeof t);
+}
+
+/* Rotation matrix of an axis-angle vector (Rodrigues' formula). */
+static void axis_angle_to_matrix(const double *r, double *R)
+{
+    double th = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    double K[9] = {0, -r[2], r[1], r[2], 0, -r[0], -r[1], r[0], 0};
+    double a, b;
+    if (th < 1e-8) {
+        a = 1.0 - th * th / 6.0;
+        b = 0.5 - th * th / 24.0;
+    } else {
+        a = sin(th) / th;
+        b = (1.0 - cos(th)) / (th * th);
+    }
+    double K2[9];
+    mat3_mul(K, K, K2);
+    for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0 ? 1.0 : 0.0) + a * K[i] + b * K2[i];
+}
+
+/* ------------------------------------------------------------------ */
+/* Forward kinematics: bone transforms G_j = T_j * translate(-J_j)      */
+/* T_j = T_parent(j) * [R(theta_j) | J_j - J_parent(j)],  T_root = [R|J]*/
+/* bone: [J][3][4] row-major (rotation | translation)                  */
+/* ------------------------------------------------------------------ */
+void orc_fk(int J, const int *parents, const double *joints, const double *pose, double *bone)
+{
+    double *Rg = (double *)malloc(sizeof(double) * 9 * J);
+    double *tg = (double *)malloc(sizeof(double) * 3 * J);
+    for (int j = 0; j < J; ++j) {
+        double Rl[9];
+        axis_angle_to_matrix(pose + 3 * j, Rl);
+        int p = parents[j];
+        if (p < 0) {
+            memcpy(Rg + 9 * j, Rl, sizeof Rl);
+            memcpy(tg + 3 * j, joints + 3 * j, 3 * sizeof(double));
+        } else {
+            double off[3] = {joints[3 * j] - joints[3 * p], joints[3 * j + 1] - joints[3 * p + 1],
+                             joints[3 * j + 2] - joints[3 * p + 2]};
+            mat3_mul(Rg + 9 * p, Rl, Rg + 9 * j);
+            double ro[3];
+            mat3_vec(Rg + 9 * p, off, ro);
+            for (int i = 0; i < 3; ++i) tg[3 * j + i] = tg[3 * p + i] + ro[i];
+        }
+        double rj[3];
+        mat3_vec(Rg + 9 * j, joints + 3 * j, rj);
+        for (int i = 0; i < 3; ++i) {
+            for (int k = 0; k < 3; ++k) bone[12 * j + 4 * i + k] = Rg[9 * j + 3 * i + k];
+            bone[12 * j + 4 * i + 3] = tg[3 * j + i] - rj[i];
+        }
+    }
+    free(Rg);
+    free(tg);
+}
+
+/* ------------------------------------------------------------------ */
+/* Skinning (Sec. 3.1)                                                 */
+/*   u_j = 1/max(|x_g - x_j|, 1e-8), ubar_j = u_j / sum u       (Eq. 1)   */
+/*   *_g = sum_j ubar_j *_j  for a, gamma, p, n, w, dx         (Eq. 1)   */
+/*   xbar = x_g + dx_g; A_g = sum_k w_gk G_k; x_gd = A_g xbar (affine)    */
+/*   Sigma = R(q) S^2 R(q)^T, S = diag(exp(logscale)); Sigma_gd = M Sigma M^T*/
+/*   n_gd = normalize(M normalize(n_g)),  M = linear part of A_g           */
+/* Vertices: xp_v = A_v (x_v + dx_v), A_v = sum_k w_vk G_k               */
+/* cov stored as (xx, xy, xz, yy, yz, zz).                              */
+/* ------------------------------------------------------------------ */
+void orc_skin(int G, int Nv, int K, int J,
+              const double *xg, const double *logscale, const double *quat, const int *knn,
+              const double *xv, const double *dxv, const double *wv, const double *av,
+              const double *rv, const double *pv, const double *nv, const double *bone,
+              double *xp, double *xd, double *cov, double *nd, double *ag, double *rg,
+              double *pg, double *ubar, double *wg_out)
+{
+    /* vertices */
+    for (int v = 0; v < Nv; ++v) {
+        double A[12] = {0};
+        for (int k = 0; k < J; ++k)
+            for (int i = 0; i < 12; ++i) A[i] += wv[(size_t)v * J + k] * bone[12 * k + i];
+        double x[3];
+        for (int i = 0; i < 3; ++i) x[i] = xv[3 * v + i] + (dxv ? dxv[3 * v + i] : 0.0);
+        for (int i = 0; i < 3; ++i)
+            xp[3 * v + i] = A[4 * i] * x[0] + A[4 * i + 1] * x[1] + A[4 * i + 2] * x[2] + A[4 * i + 3];
+    }
+    /* Gaussians */
+    double *w = (double *)malloc(sizeof(double) * J);
+    for (int g = 0; g < G; ++g) {
+        const double *x = xg + 3 * g;
+        double u[16], usum = 0.0;
+        for (int j = 0; j < K; ++j) {
+            const double *y = xv + 3 * knn[g * K + j];
+            double d = sqrt((x[0] - y[0]) * (x[0] - y[0]) + (x[1] - y[1]) * (x[1] - y[1]) +
+                            (x[2] - y[2]) * (x[2] - y[2]));
+            u[j] = 1.0 / (d > 1e-8 ? d : 1e-8);
+            usum += u[j];
+        }
+        for (int j = 0; j < K; ++j) u[j] /= usum;
+        double a[3] = {0}, r = 0, p = 0, n[3] = {0}, dx[3] = {0};
+        for (int k = 0; k < J; ++k) w[k] = 0.0;
+        for (int j = 0; j < K; ++j) {
+            int v = knn[g * K + j];
+            for (int i = 0; i < 3; ++i) {
+                a[i] += u[j] * av[3 * v + i];
+                n[i] += u[j] * nv[3 * v + i];
+                dx[i] += u[j] * (dxv ? dxv[3 * v + i] : 0.0);
+            }
+            r += u[j] * rv[v];
+            p += u[j] * pv[v];
+            for (int k = 0; k < J; ++k) w[k] += u[j] * wv[(size_t)v * J + k];
+        }
+        double A[12] = {0};
+        for (int k = 0; k < J; ++k)
+            for (int i = 0; i < 12; ++i) A[i] += w[k] * bone[12 * k + i];
+        double M[9] = {A[0], A[1], A[2], A[4], A[5], A[6], A[8], A[9], A[10]};
+        double xb[3] = {x[0] + dx[0], x[1] + dx[1], x[2] + dx[2]};
+        double y[3];
+        mat3_vec(M, xb, y);
+        for (int i = 0; i < 3; ++i) xd[3 * g + i] = y[i] + A[4 * i + 3];
+        /* covariance */
+        const double *q = quat + 4 * g;
+        double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        double qw = q[0] / qn, qx = q[1] / qn, qy = q[2] / qn, qz = q[3] / qn;
+        double R[9] = {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy),
+                       2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx),
+                       2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)};
+        double s2[3];
+        for (int i = 0; i < 3; ++i) s2[i] = exp(2.0 * logscale[3 * g + i]);
+        double S[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double t = 0.0;
+                for (int k = 0; k < 3; ++k) t += R[3 * i + k] * s2[k] * R[3 * j + k];
+                S[3 * i + j] = t;
+            }
+        double MS[9], C[9];
+        mat3_mul(M, S, MS);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double t = 0.0;
+                for (int k = 0; k < 3; ++k) t += MS[3 * i + k] * M[3 * j + k];
+                C[3 * i + j] = t;
+            }
+        cov[6 * g + 0] = C[0];
+        cov[6 * g + 1] = C[1];
+        cov[6 * g + 2] = C[2];
+        cov[6 * g + 3] = C[4];
+        cov[6 * g + 4] = C[5];
+        cov[6 * g + 5] = C[8];
+        /* normal */
+        double nl = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        for (int i = 0; i < 3; ++i) n[i] /= nl;
+        double m[3];
+        mat3_vec(M, n, m);
+        double ml = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+        for (int i = 0; i < 3; ++i) nd[3 * g + i] = m[i] / ml;
+        for (int i = 0; i < 3; ++i) ag[3 * g + i] = a[i];
+        rg[g] = r;
+        pg[g] = p;
+        for (int j = 0; j < K; ++j) ubar[g * K + j] = u[j];
+        if (wg_out)
+            for (int k = 0; k < J; ++k) wg_out[(size_t)g * J + k] = w[k];
+    }
+    free(w);
+}
+
+/* ------------------------------------------------------------------ */
+/* Visibility by depth maps (Sec. 3.2, shadow-mapping form), integer.   */
+/*                                                                      */
+/* All rules below are exact integer arithmetic, so any correct         */
+/* implementation produces the same bits:                              */
+/*  q   = rint(x * 2^13) - rint(c * 2^13)        (|q_i| < 2^16 required) */
+/*  B   = rint(frame * 2^13), rows e1, e2, w (w points to the light)     */
+/*  s = e1.q, t = e2.q (units 2^-26), zd = floor(-(w.q) / 2^10) (2^-16)  */
+/*  H = rint(h * 2^26), M = floor(R 2^35 / H)   (16R < H <= 2^30)        */
+/*  X = floor((s + H) M / 2^32), Y likewise from t   (1/16-pixel units)  */
+/*  a vertex is in the window iff 0 <= X, Y < 16R                        */
+/*  triangle: skipped if any vertex is outside the window or its doubled */
+/*  area is 0; two-sided (orientation normalised to positive area);      */
+/*  covers pixel (i,j) (centre 16i+8, 16j+8) iff all three edge          */
+/*  functions are >= 0; depth there = floor(sum w_i zd_i / area)         */
+/*  depth map = min over covering triangles (empty = +inf)               */
+/*  bit(v,d) = 1 iff v outside the window, its pixel empty, or           */
+/*             zd_v <= depth[pixel(v)] + rint(bias * 2^16)               */
+/* bits: [Nv][D/32] uint32, bit d&31 of word d>>5.                      */
+/* Returns 0, or -1 on an argument outside the supported range.         */
+/* ------------------------------------------------------------------ */
+static int64_t floor_div(int64_t a, int64_t b) /* b > 0 */
+{
+    int64_t q = a / b;
+    if ((a % b != 0) && (a < 0)) q -= 1;
+    return q;
+}
+
+int orc_visibility(int Nv, int F, int D, int R, const double *xp, const int *faces,
+                   const double *frames, const double *center, double half_extent, double bias,
+                   uint32_t *bits, int32_t *depth_out)
+{
+    if (D <= 0 || D % 32 != 0 || R < 1 || R > 1024 || Nv < 0 || F < 0) return -1;
+    int64_t H = (int64_t)llrint(half_extent * 67108864.0);
+    if (!(H > 16 * (int64_t)R && H <= ((int64_t)1 << 30))) return -1;
+    int64_t Mmul = ((int64_t)R << 35) / H;
+    int64_t biasq = (int64_t)llrint(bias * 65536.0);
+    int64_t qc[3];
+    for (int i = 0; i < 3; ++i) qc[i] = (int64_t)llrint(center[i] * 8192.0);
+    int64_t *q = (int64_t *)malloc(sizeof(int64_t) * 3 * (size_t)(Nv > 0 ? Nv : 1));
+    for (int v = 0; v < Nv; ++v)
+        for (int i = 0; i < 3; ++i) {
+            q[3 * v + i] = (int64_t)llrint(xp[3 * v + i] * 8192.0) - qc[i];
+            if (q[3 * v + i] <= -65536 || q[3 * v + i] >= 65536) {
+                free(q);
+                return -1;
+            }
+        }
+    int DW = D / 32;
+    memset(bits, 0, sizeof(uint32_t) * (size_t)Nv * DW);
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int d = 0; d < D; ++d) {
+        int64_t B[9];
+        for (int i = 0; i < 9; ++i) B[i] = (int64_t)llrint(frames[9 * d + i] * 8192.0);
+        for (int r = 0; r < 3; ++r)
+            if (B[3 * r] * B[3 * r] + B[3 * r + 1] * B[3 * r + 1] + B[3 * r + 2] * B[3 * r + 2] >
+                (int64_t)8194 * 8194)
+                err = 1;
+        int64_t *X = (int64_t *)malloc(sizeof(int64_t) * (size_t)(Nv > 0 ? Nv : 1));
+        int64_t *Y = (int64_t *)malloc(sizeof(int64_t) * (size_t)(Nv > 0 ? Nv : 1));
+        int64_t *Z = (int64_t *)malloc(sizeof(int64_t) * (size_t)(Nv > 0 ? Nv : 1));
+        unsigned char *in = (unsigned char *)malloc((size_t)(Nv > 0 ? Nv : 1));
+        int64_t *depth = (int64_t *)malloc(sizeof(int64_t) * (size_t)R * R);
+        const int64_t EMPTY = INT64_MAX;
+        for (int p = 0; p < R * R; ++p) depth[p] = EMPTY;
+        for (int v = 0; v < Nv; ++v) {
+            const int64_t *qv = q + 3 * v;
+            int64_t s = B[0] * qv[0] + B[1] * qv[1] + B[2] * qv[2];
+            int64_t t = B[3] * qv[0] + B[4] * qv[1] + B[5] * qv[2];
+            int64_t z = B[6] * qv[0] + B[7] * qv[1] + B[8] * qv[2];
+            X[v] = floor_div((s + H) * Mmul, (int64_t)1 << 32);
+            Y[v] = floor_div((t + H) * Mmul, (int64_t)1 << 32);
+            Z[v] = floor_div(-z, 1024);
+            in[v] = (X[v] >= 0 && X[v] < 16 * (int64_t)R && Y[v] >= 0 && Y[v] < 16 * (int64_t)R);
+        }
+        for (int f = 0; f < F; ++f) {
+            int a = faces[3 * f], b = faces[3 * f + 1], c = faces[3 * f + 2];
+            if (!in[a] || !in[b] || !in[c]) continue;
+            int64_t area = (X[b] - X[a]) * (Y[c] - Y[a]) - (Y[b] - Y[a]) * (X[c] - X[a]);
+            if (area == 0) continue;
+            if (area < 0) {
+                int tmp = b;
+                b = c;
+                c = tmp;
+                area = -area;
+            }
+            int64_t xmin = X[a], xmax = X[a], ymin = Y[a], ymax = Y[a];
+            int64_t vx[2] = {X[b], X[c]}, vy[2] = {Y[b], Y[c]};
+            for (int k = 0; k < 2; ++k) {
+                if (vx[k] < xmin) xmin = vx[k];
+                if (vx[k] > xmax) xmax = vx[k];
+                if (vy[k] < ymin) ymin = vy[k];
+                if (vy[k] > ymax) ymax = vy[k];
+            }
+            /* pixels whose centre 16i+8 lies in [min, max] */
+            int64_t i0 = -floor_div(-(xmin - 8), 16), i1 = floor_div(xmax - 8, 16);
+            int64_t j0 = -floor_div(-(ymin - 8), 16), j1 = floor_div(ymax - 8, 16);
+            if (i0 < 0) i0 = 0;
+            if (j0 < 0) j0 = 0;
+            if (i1 > R - 1) i1 = R - 1;
+            if (j1 > R - 1) j1 = R - 1;
+            for (int64_t j = j0; j <= j1; ++j)
+                for (int64_t i = i0; i <= i1; ++i) {
+                    int64_t px = 16 * i + 8, py = 16 * j + 8;
+                    int64_t wa = (X[c] - X[b]) * (py - Y[b]) - (Y[c] - Y[b]) * (px - X[b]);
+                    int64_t wb = (X[a] - X[c]) * (py - Y[c]) - (Y[a] - Y[c]) * (px - X[c]);
+                    int64_t wc = (X[b] - X[a]) * (py - Y[a]) - (Y[b] - Y[a]) * (px - X[a]);
+                    if (wa < 0 || wb < 0 || wc < 0) continue;
+                    int64_t z = floor_div(wa * Z[a] + wb * Z[b] + wc * Z[c], area);
+                    if (z < depth[j * R + i]) depth[j * R + i] = z;
+                }
+        }
+        for (int v = 0; v < Nv; ++v) {
+            int vis;
+            if (!in[v]) {
+                vis = 1;
+            } else {
+                int64_t pix = (Y[v] >> 4) * R + (X[v] >> 4);
+                vis = (depth[pix] == EMPTY) || (Z[v] <= depth[pix] + biasq);
+            }
+            if (vis) {
+#pragma omp atomic
+                bits[(size_t)v * DW + (d >> 5)] |= (uint32_t)1u << (d & 31);
+            }
+        }
+        if (depth_out)
+            for (int p = 0; p < R * R; ++p)
+                depth_out[(size_t)d * R * R + p] =
+                    depth[p] == EMPTY ? INT32_MAX : (int32_t)depth[p];
+        free(X);
+        free(Y);
+        free(Z);
+        free(in);
+        free(depth);
+    }
+    free(q);
+    return err ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Shading (Eq. 2, App. A, Sec. 3.1)                                    */
+/*  cull  : decided in FP32 exactly as  s = fma(n2,d2, fma(n1,d1, n0*d0)) */
+/*          with d = C - x_gd (FP32 subtractions); culled iff !(s > 0)   */
+/*  w_o   = normalize(C - x_gd), c_o = max(n.w_o, 0)                     */
+/*  per light k with c_i = n.w_k > 0:                                   */
+/*     vis = sum_j ubar_j bit(S_j, d(k))          (Eq. 1 on visibility)  */
+/*     h = normalize(w_k + w_o), alpha = gamma^2, kk = (gamma+1)^2/8     */
+/*     D = alpha^2 / (pi ((n.h)^2 (alpha^2-1) + 1)^2)                    */
+/*     F = 0.04 + 0.96 * 2^((-5.55473 (w_o.h) - 6.98316)(w_o.h))         */
+/*     f_s = D F / (4 (c_i(1-kk)+kk) (c_o(1-kk)+kk))   (G cancelled)     */
+/*     L_o += L^k A^k vis c_i (a/pi + p f_s)                             */
+/*  colour = max(L_o, 1e-6)^(1/2.2); culled Gaussians get colour 0.      */
+/* ------------------------------------------------------------------ */
+void orc_shade(int G, int K, int NL, int D, const double *xd, const double *nd, const double *ag,
+               const double *rg, const double *pg, const double *ubar, const int *knn,
+               const uint32_t *bits, const double *light_L, const double *light_A,
+               const double *light_w, const int *dmap, const double *cam_center,
+               double *color, double *radiance, unsigned char *cull)
+{
+    int DW = D / 32;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int g = 0; g < G; ++g) {
+        const double *x = xd + 3 * g, *n = nd + 3 * g;
+        float fd0 = (float)cam_center[0] - (float)x[0];
+        float fd1 = (float)cam_center[1] - (float)x[1];
+        float fd2 = (float)cam_center[2] - (float)x[2];
+        float fs = fmaf((float)n[2], fd2, fmaf((float)n[1], fd1, (float)n[0] * fd0));
+        int culled = !(fs > 0.0f);
+        if (cull) cull[g] = (unsigned char)culled;
+        if (culled) {
+            for (int c = 0; c < 3; ++c) {
+                color[3 * g + c] = 0.0;
+                if (radiance) radiance[3 * g + c] = 0.0;
+            }
+            continue;
+        }
+        double wo[3] = {cam_center[0] - x[0], cam_center[1] - x[1], cam_center[2] - x[2]};
+        double l = sqrt(wo[0] * wo[0] + wo[1] * wo[1] + wo[2] * wo[2]);
+        for (int i = 0; i < 3; ++i) wo[i] /= l;
+        double co = n[0] * wo[0] + n[1] * wo[1] + n[2] * wo[2];
+        if (co < 0.0) co = 0.0;
+        double gam = rg[g], p = pg[g];
+        double alpha = gam * gam, a2 = alpha * alpha, kk = (gam + 1.0) * (gam + 1.0) / 8.0;
+        double Lo[3] = {0, 0, 0};
+        for (int k = 0; k < NL; ++k) {
+            const double *wi = light_w + 3 * k;
+            double ci = n[0] * wi[0] + n[1] * wi[1] + n[2] * wi[2];
+            if (!(ci > 0.0)) continue;
+            int d = dmap[k];
+            double vis = 0.0;
+            for (int j = 0; j < K; ++j) {
+                int v = knn[g * K + j];
+                uint32_t word = bits[(size_t)v * DW + (d >> 5)];
+                if ((word >> (d & 31)) & 1u) vis += ubar[g * K + j];
+            }
+            if (vis == 0.0) continue;
+            double h[3] = {wi[0] + wo[0], wi[1] + wo[1], wi[2] + wo[2]};
+            double hl = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+            double fsp = 0.0;
+            if (hl > 0.0) {
+                for (int i = 0; i < 3; ++i) h[i] /= hl;
+                double nh = n[0] * h[0] + n[1] * h[1] + n[2] * h[2];
+                double voh = wo[0] * h[0] + wo[1] * h[1] + wo[2] * h[2];
+                double den = nh * nh * (a2 - 1.0) + 1.0;
+                double Dn = a2 / (ORC_PI * den * den);
+                double Fr = 0.04 + 0.96 * pow(2.0, (-5.55473 * voh - 6.98316) * voh);
+                fsp = Dn * Fr / (4.0 * (ci * (1.0 - kk) + kk) * (co * (1.0 - kk) + kk));
+            }
+            for (int c = 0; c < 3; ++c)
+                Lo[c] += light_L[3 * k + c] * light_A[k] * vis * ci * (ag[3 * g + c] / ORC_PI + p * fsp);
+        }
+        for (int c = 0; c < 3; ++c) {
+            if (radiance) radiance[3 * g + c] = Lo[c];
+            color[3 * g + c] = pow(Lo[c] > 1e-6 ? Lo[c] : 1e-6, 1.0 / 2.2);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* EWA projection (3DGS conventions, Sec. 3.1)                          */
+/*  cam: fx fy cx cy R[9] t[3] (world->camera, x right, y down, z fwd)  */
+/*  p = R x + t; valid iff not culled, p.z > 0.2, opacity > 1/255        */
+/*  mean2d = (fx p.x/p.z + cx, fy p.y/p.z + cy)                          */
+/*  J = [[fx/z, 0, -fx x/z^2], [0, fy/z, -fy y/z^2]], T = J R            */
+/*  Sigma' = T Sigma_gd T^T + 0.3 I ; conic = inverse(Sigma') (a, b, c)  */
+/*  support: ellipse q <= 2 ln(255 o), AABB half-extents                 */
+/*  r sqrt(Sigma'_xx) + 1, r sqrt(Sigma'_yy) + 1 (1 px pad);             */
+/*  rect = pixels whose centre (i+1/2) lies in the AABB, clipped.        */
+/*  rect_amb flags a rect bound within 2e-3 px of an integer step.      */
+/* ------------------------------------------------------------------ */
+void orc_project(int G, const double *xd, const double *cov, const double *opacity,
+                 const unsigned char *cull, const double *cam, int W, int Hh, double *mean2d,
+                 double *conic, double *depth, int *rect, int *valid, unsigned char *rect_amb)
+{
+    double fx = cam[0], fy = cam[1], cx = cam[2], cy = cam[3];
+    const double *Rw = cam + 4, *tw = cam + 13;
+    for (int g = 0; g < G; ++g) {
+        double p[3];
+        mat3_vec(Rw, xd + 3 * g, p);
+        for (int i = 0; i < 3; ++i) p[i] += tw[i];
+        double o = opacity[g];
+        int ok = !(cull && cull[g]) && p[2] > 0.2 && o > 1.0 / 255.0;
+        depth[g] = p[2];
+        rect[4 * g] = 0;
+        rect[4 * g + 1] = 0;
+        rect[4 * g + 2] = -1;
+        rect[4 * g + 3] = -1;
+        if (rect_amb) rect_amb[g] = (unsigned char)(fabs(p[2] - 0.2) < 1e-6);
+        if (!ok) {
+            valid[g] = 0;
+            mean2d[2 * g] = mean2d[2 * g + 1] = 0.0;
+            conic[3 * g] = conic[3 * g + 1] = conic[3 * g + 2] = 0.0;
+            continue;
+        }
+        double z = p[2];
+        double u = fx * p[0] / z + cx, v = fy * p[1] / z + cy;
+        double Jm[6] = {fx / z, 0.0, -fx * p[0] / (z * z), 0.0, fy / z, -fy * p[1] / (z * z)};
+        double T[6];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 3; ++j)
+                T[3 * i + j] = Jm[3 * i] * Rw[j] + Jm[3 * i + 1] * Rw[3 + j] + Jm[3 * i + 2] * Rw[6 + j];
+        const double *c6 = cov + 6 * g;
+        double S[9] = {c6[0], c6[1], c6[2], c6[1], c6[3], c6[4], c6[2], c6[4], c6[5]};
+        double TS[6];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 3; ++j)
+                TS[3 * i + j] = T[3 * i] * S[j] + T[3 * i + 1] * S[3 + j] + T[3 * i + 2] * S[6 + j];
+        double s00 = TS[0] * T[0] + TS[1] * T[1] + TS[2] * T[2] + 0.3;
+        double s01 = TS[0] * T[3] + TS[1] * T[4] + TS[2] * T[5];
+        double s11 = TS[3] * T[3] + TS[4] * T[4] + TS[5] * T[5] + 0.3;
+        double det = s00 * s11 - s01 * s01;
+        if (!(det > 0.0)) {
+            valid[g] = 0;
+            mean2d[2 * g] = mean2d[2 * g + 1] = 0.0;
+            conic[3 * g] = conic[3 * g + 1] = conic[3 * g + 2] = 0.0;
+            continue;
+        }
+        valid[g] = 1;
+        mean2d[2 * g] = u;
+        mean2d[2 * g + 1] = v;
+        conic[3 * g] = s11 / det;
+        conic[3 * g + 1] = -s01 / det;
+        conic[3 * g + 2] = s00 / det;
+        double r2 = 2.0 * log(255.0 * o);
+        double ex = sqrt(r2 * s00) + 1.0, ey = sqrt(r2 * s11) + 1.0;
+        double bx0 = u - ex - 0.5, bx1 = u + ex - 0.5, by0 = v - ey - 0.5, by1 = v + ey - 0.5;
+        double x0 = ceil(bx0), x1 = floor(bx1), y0 = ceil(by0), y1 = floor(by1);
+        if (rect_amb) {
+            double b4[4] = {bx0, bx1, by0, by1};
+            for (int i = 0; i < 4; ++i)
+                if (fabs(b4[i] - nearbyint(b4[i])) < 2e-3) rect_amb[g] = 1;
+            if (fabs(det) < 1e-12) rect_amb[g] = 1;
+        }
+        if (x0 < 0) x0 = 0;
+        if (y0 < 0) y0 = 0;
+        if (x1 > W - 1) x1 = W - 1;
+        if (y1 > Hh - 1) y1 = Hh - 1;
+        if (x0 > x1 || y0 > y1) {
+            rect[4 * g] = 0;
+            rect[4 * g + 1] = 0;
+            rect[4 * g + 2] = -1;
+            rect[4 * g + 3] = -1;
+        } else {
+            rect[4 * g] = (int)x0;
+            rect[4 * g + 1] = (int)y0;
+            rect[4 * g + 2] = (int)x1;
+            rect[4 * g + 3] = (int)y1;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Brute-force compositing (3DGS blending, Sec. 3.1; background black,  */
+/* Sec. 4.2).  For a pixel centre P = (i+1/2, j+1/2):                   */
+/*   alpha_g = min(0.99, o_g exp(-1/2 d^T conic d)), d = P - mean2d      */
+/*   contributors = valid g with alpha_g >= 1/255, in (depth, index)     */
+/*   order; T = 1; for each: if T(1-alpha) < 1e-4 stop; C += c alpha T;  */
+/*   T *= 1 - alpha.  Outputs C, T_final, the contributor count and an   */
+/*   ambiguity flag (some traversed alpha within 2e-5 (relative) of      */
+/*   1/255, or the stop test within 1e-7 of 1e-4).                        */
+/* pix: list of npix pixel indices (j*W+i), or NULL for all W*H.         */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double depth;
+    int idx;
+    double alpha;
+    int near_thresh;
+} orc_contrib;
+
+static int contrib_cmp(const void *a, const void *b)
+{
+    const orc_contrib *x = (const orc_contrib *)a, *y = (const orc_contrib *)b;
+    if (x->depth < y->depth) return -1;
+    if (x->depth > y->depth) return 1;
+    return (x->idx > y->idx) - (x->idx < y->idx);
+}
+
+void orc_composite(int G, int W, int Hh, const double *mean2d, const double *conic,
+                   const double *opacity, const double *color, const double *depth,
+                   const int *valid, int npix, const int *pix, double *out_rgb, double *out_T,
+                   int *out_count, unsigned char *ambiguous)
+{
+    int n = pix ? npix : W * Hh;
+#pragma omp parallel
+    {
+        orc_contrib *list = (orc_contrib *)malloc(sizeof(orc_contrib) * (size_t)(G > 0 ? G : 1));
+#pragma omp for schedule(dynamic, 16)
+        for (int t = 0; t < n; ++t) {
+            int p = pix ? pix[t] : t;
+            double px = (p % W) + 0.5, py = (p / W) + 0.5;
+            int m = 0;
+            for (int g = 0; g < G; ++g) {
+                if (!valid[g]) continue;
+                double dx = px - mean2d[2 * g], dy = py - mean2d[2 * g + 1];
+                double q = conic[3 * g] * dx * dx + 2.0 * conic[3 * g + 1] * dx * dy +
+                           conic[3 * g + 2] * dy * dy;
+                double araw = opacity[g] * exp(-0.5 * q);
+                int near_t = fabs(araw * 255.0 - 1.0) < 2e-5;
+                double a = araw < 0.99 ? araw : 0.99;
+                if (a >= 1.0 / 255.0 || near_t) {
+                    list[m].depth = depth[g];
+                    list[m].idx = g;
+                    list[m].alpha = a;
+                    list[m].near_thresh = near_t;
+                    ++m;
+                }
+            }
+            qsort(list, (size_t)m, sizeof(orc_contrib), contrib_cmp);
+            double T = 1.0, C[3] = {0, 0, 0};
+            int count = 0, amb = 0;
+            for (int i = 0; i < m; ++i) {
+                if (list[i].near_thresh) amb = 1;
+                double a = list[i].alpha;
+                if (a < 1.0 / 255.0) continue;
+                double test = T * (1.0 - a);
+                if (fabs(test - 1e-4) < 1e-7) amb = 1;
+                if (test < 1e-4) break;
+                int g = list[i].idx;
+                for (int c = 0; c < 3; ++c) C[c] += color[3 * g + c] * a * T;
+                T = test;
+                ++count;
+            }
+            for (int c = 0; c < 3; ++c) out_rgb[3 * t + c] = C[c];
+            out_T[t] = T;
+            if (out_count) out_count[t] = count;
+            if (ambiguous) ambiguous[t] = (unsigned char)amb;
+        }
+        free(list);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Tile membership and order (3DGS binning), brute force per tile.      */
+/* Gaussian g belongs to tile (tx,ty) iff its pixel rect [x0..x1]x[y0..y1]*/
+/* (inclusive, empty if x0>x1) meets the tile: x0/TS <= tx <= x1/TS and  */
+/* likewise in y.  Each tile's list is ordered by (key, index), key the  */
+/* depth's FP32 bit pattern.  tile_start has ntiles+1 entries; list has   */
+/* capacity cap.  Returns the total number of (tile, Gaussian) pairs.     */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    uint32_t key;
+    int idx;
+} orc_pair;
+
+static int pair_cmp(const void *a, const void *b)
+{
+    const orc_pair *x = (const orc_pair *)a, *y = (const orc_pair *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return (x->idx > y->idx) - (x->idx < y->idx);
+}
+
+long orc_bin(int G, const int *rect, const uint32_t *key, int W, int Hh, int TS, int *tile_start,
+             int *list, long cap)
+{
+    int tx = (W + TS - 1) / TS, ty = (Hh + TS - 1) / TS;
+    long total = 0;
+    orc_pair *buf = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(G > 0 ? G : 1));
+    for (int t = 0; t < tx * ty; ++t) {
+        int cx = t % tx, cy = t / tx;
+        int m = 0;
+        for (int g = 0; g < G; ++g) {
+            const int *r = rect + 4 * g;
+            if (r[0] > r[2] || r[1] > r[3]) continue;
+            if (r[0] / TS <= cx && cx <= r[2] / TS && r[1] / TS <= cy && cy <= r[3] / TS) {
+                buf[m].key = key[g];
+                buf[m].idx = g;
+                ++m;
+            }
+        }
+        qsort(buf, (size_t)m, sizeof(orc_pair), pair_cmp);
+        tile_start[t] = (int)total;
+        for (int i = 0; i < m; ++i) {
+            if (total + i < cap) list[total + i] = buf[i].idx;
+        }
+        total += m;
+    }
+    tile_start[tx * ty] = (int)total;
+    free(buf);
+    return total;
+}

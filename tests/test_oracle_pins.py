@@ -1,0 +1,604 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms, invariants, special cases, constants printed in the paper
+(tests/golden/), an independent restatement, or central finite differences.
+No GPU is used.
+"""
+import copy
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import adjoint as AJ
+from oracle import oracle as O
+from oracle import pipeline as OP
+from paper_2407_10707_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def golden_constants():
+    vals = {}
+    with open(os.path.join(GOLDEN, "app_a_brdf_constants.txt")) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                k, v = line.split()[:2]
+                vals[k] = float(v)
+    return vals
+
+
+def rot(axis, ang):
+    axis = np.asarray(axis, float)
+    axis = axis / np.linalg.norm(axis)
+    K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+    return np.eye(3) + math.sin(ang) * K + (1 - math.cos(ang)) * K @ K
+
+
+@pytest.fixture(scope="module")
+def small_avatar():
+    return synth.make_avatar(642, 300, seed=5)
+
+
+# ---------------------------------------------------------------- FK / skin
+def test_fk_identity_pose_gives_identity_bones():
+    pose = np.zeros((24, 3))
+    bone = O.fk(synth.PARENTS, synth.REST_JOINTS, pose)
+    for j in range(24):
+        np.testing.assert_allclose(bone[j, :, :3], np.eye(3), atol=1e-15)
+        np.testing.assert_allclose(bone[j, :, 3], 0, atol=1e-15)
+
+
+def test_fk_root_rotation_is_rigid():
+    pose = np.zeros((24, 3))
+    pose[0] = [0.2, -0.4, 0.3]
+    Q = rot(pose[0], np.linalg.norm(pose[0]))
+    J0 = synth.REST_JOINTS[0]
+    bone = O.fk(synth.PARENTS, synth.REST_JOINTS, pose)
+    for j in range(24):
+        np.testing.assert_allclose(bone[j, :, :3], Q, atol=1e-13)
+        np.testing.assert_allclose(bone[j, :, 3], J0 - Q @ J0, atol=1e-13)
+
+
+def test_fk_chain_closed_form():
+    parents = np.array([-1, 0, 1], np.int32)
+    joints = np.array([[0.0, 0, 0], [1.0, 0, 0], [2.0, 0, 0]])
+    pose = np.array([[0, 0, math.pi / 2], [0, 0, math.pi / 2], [0, 0, 0]])
+    bone = O.fk(parents, joints, pose)
+    # joint 1 moves to R0 (J1 - J0) = (0,1,0); joint 2 to (0,1,0) + R0 R1 (1,0,0) = (-1,1,0)
+    apply = lambda j, x: bone[j, :, :3] @ x + bone[j, :, 3]
+    np.testing.assert_allclose(apply(1, joints[1]), [0, 1, 0], atol=1e-14)
+    np.testing.assert_allclose(apply(2, joints[2]), [-1, 1, 0], atol=1e-14)
+
+
+def test_skin_identity_pose(small_avatar):
+    av = copy.deepcopy(small_avatar)
+    av.pose = np.zeros((24, 3))
+    bone = O.fk(av.parents, av.joints, av.pose)
+    sk = O.skin(av, bone)
+    np.testing.assert_allclose(sk["xd"], av.xg, atol=1e-14)
+    np.testing.assert_allclose(sk["xp"], av.xv, atol=1e-14)
+    # covariance eigen-structure: eigenvalues exp(2 s), eigenvectors = rotation columns
+    for g in range(0, av.G, 37):
+        c = sk["cov"][g]
+        S = np.array([[c[0], c[1], c[2]], [c[1], c[3], c[4]], [c[2], c[4], c[5]]])
+        ev = np.sort(np.linalg.eigvalsh(S))
+        np.testing.assert_allclose(ev, np.sort(np.exp(2 * av.logscale[g])), rtol=1e-10)
+    # interpolated attributes stay inside the range of the neighbours
+    for name, vert in (("ag", av.av), ("rg", av.rv), ("pg", av.pv)):
+        nb = vert[av.knn]
+        assert np.all(sk[name] >= nb.min(axis=1) - 1e-12)
+        assert np.all(sk[name] <= nb.max(axis=1) + 1e-12)
+    np.testing.assert_allclose(np.linalg.norm(sk["nd"], axis=1), 1, atol=1e-14)
+    np.testing.assert_allclose(sk["wg"].sum(axis=1), 1, atol=1e-12)
+    np.testing.assert_allclose(sk["ubar"].sum(axis=1), 1, atol=1e-14)
+
+
+def test_skin_rigid_motion(small_avatar):
+    av = copy.deepcopy(small_avatar)
+    av.pose = np.zeros((24, 3))
+    sk0 = O.skin(av, O.fk(av.parents, av.joints, av.pose))
+    av.pose[0] = [0.3, 0.5, -0.2]
+    Q = rot(av.pose[0], np.linalg.norm(av.pose[0]))
+    J0 = av.joints[0]
+    sk = O.skin(av, O.fk(av.parents, av.joints, av.pose))
+    np.testing.assert_allclose(sk["xd"], (av.xg - J0) @ Q.T + J0, atol=1e-12)
+    np.testing.assert_allclose(sk["nd"], sk0["nd"] @ Q.T, atol=1e-12)
+    for g in range(0, av.G, 23):
+        c0 = sk0["cov"][g]
+        S0 = np.array([[c0[0], c0[1], c0[2]], [c0[1], c0[3], c0[4]], [c0[2], c0[4], c0[5]]])
+        S1 = Q @ S0 @ Q.T
+        np.testing.assert_allclose(sk["cov"][g], S1[[0, 0, 0, 1, 1, 2], [0, 1, 2, 1, 2, 2]],
+                                   rtol=1e-10, atol=1e-16)
+
+
+def test_skin_eq1_on_a_vertex_and_equidistant(small_avatar):
+    av = copy.deepcopy(small_avatar)
+    av.pose = np.zeros((24, 3))
+    # Gaussian 0 sits on its first neighbour: Eq. 1 weight 1/d dominates
+    av.xg[0] = av.xv[av.knn[0, 0]]
+    # Gaussian 1: neighbours forced equidistant by placing it at their centroid
+    # of a symmetric configuration (all K neighbours = the same vertex index)
+    av.knn[1, :] = av.knn[1, 0]
+    sk = O.skin(av, O.fk(av.parents, av.joints, av.pose))
+    v0 = av.knn[0, 0]
+    np.testing.assert_allclose(sk["ag"][0], av.av[v0], atol=1e-6)
+    np.testing.assert_allclose(sk["rg"][0], av.rv[v0], atol=1e-6)
+    v1 = av.knn[1, 0]
+    np.testing.assert_allclose(sk["ag"][1], av.av[v1], atol=1e-14)
+    np.testing.assert_allclose(sk["ubar"][1], 1.0 / av.K, atol=1e-15)
+
+
+# ---------------------------------------------------------------- visibility
+def _frames_for(dirs):
+    return synth.direction_frames(np.asarray(dirs, float)).astype(np.float32).astype(np.float64)
+
+
+def test_visibility_single_triangle_visible_from_both_sides():
+    # nothing occludes a lone triangle: with the 2-pixel depth bias every vertex
+    # is visible from every direction that is not within ~70 degrees of edge-on
+    xp = np.array([[0.0, 0, 0], [0.3, 0, 0], [0, 0.3, 0]])
+    faces = np.array([[0, 1, 2]], np.int32)
+    dirs = synth.fibonacci_directions(64)
+    R, half = 64, 1.0
+    bits = O.visibility(xp, faces, _frames_for(dirs), [0.1, 0.1, 0], half, 2 * (2 * half / R), R)
+    vb = np.unpackbits(bits.view(np.uint8), bitorder="little").reshape(3, 64)
+    facing = np.abs(dirs[:, 2]) >= 0.35
+    assert np.all(vb[:, facing] == 1)
+    # and with no triangle at all every vertex is visible from everywhere
+    bits = O.visibility(xp, np.zeros((0, 3), np.int32), _frames_for(dirs), [0.1, 0.1, 0], half,
+                        0.0, R)
+    assert np.all(bits == 0xFFFFFFFF)
+
+
+def test_visibility_parallel_quads_occlusion():
+    # near quad at z=+0.2 (spans [-0.5,0.5]^2), far quad at z=-0.2 (spans [0,1]x[-0.5,0.5])
+    def quad(x0, x1, y0, y1, z, n):
+        xs = np.linspace(x0, x1, n)
+        ys = np.linspace(y0, y1, n)
+        X, Y = np.meshgrid(xs, ys)
+        v = np.stack([X.ravel(), Y.ravel(), np.full(X.size, z)], 1)
+        f = []
+        for j in range(n - 1):
+            for i in range(n - 1):
+                a = j * n + i
+                f += [(a, a + 1, a + n), (a + 1, a + n + 1, a + n)]
+        return v, np.array(f, np.int32)
+    v1, f1 = quad(-0.5, 0.5, -0.5, 0.5, 0.2, 9)
+    v2, f2 = quad(0.0, 1.0, -0.5, 0.5, -0.2, 9)
+    xp = np.concatenate([v1, v2])
+    faces = np.concatenate([f1, f2 + len(v1)])
+    dirs = np.zeros((32, 3))
+    dirs[:, 2] = 1.0                     # direction 0..31: light straight above (+z)
+    dirs[16:, 2] = -1.0                  # 16..31: light straight below
+    bits = O.visibility(xp, faces, _frames_for(dirs), [0.25, 0, 0], 1.2, 0.02, 128)
+    b = bits[:, 0]
+    up = (b & 1) != 0
+    down = ((b >> 16) & 1) != 0
+    n1 = len(v1)
+    assert np.all(up[:n1])                                  # near quad lit from above
+    far = v2
+    inside = (far[:, 0] < 0.5 - 0.02) & (np.abs(far[:, 1]) < 0.5 - 0.02)
+    outside = far[:, 0] > 0.5 + 0.02
+    assert np.all(~up[n1:][inside])                         # shadowed by the near quad
+    assert np.all(up[n1:][outside])
+    assert np.all(down[n1:])                                # far quad lit from below
+    near_inside = (v1[:, 0] > 0.02) & (np.abs(v1[:, 1]) < 0.5 - 0.02)
+    assert np.all(~down[:n1][near_inside])
+
+
+def test_visibility_convex_sphere_hemisphere():
+    v, f, n = synth._tessellate_capsule((0, 0, 0), (0, 0, 0), 0.5, 2000)
+    dirs = synth.fibonacci_directions(128)
+    R = 256
+    half = 0.6
+    bias = 2.0 * (2 * half / R)
+    bits = O.visibility(v, f, _frames_for(dirs), [0, 0, 0], half, bias, R)
+    vb = np.unpackbits(bits.view(np.uint8), bitorder="little").reshape(len(v), -1)[:, :128]
+    cosines = n @ dirs.T
+    tau = 0.35
+    assert np.all(vb[cosines >= tau] == 1)
+    assert np.all(vb[cosines <= -tau] == 0)
+
+
+def test_visibility_depth_map_of_a_plane():
+    # one big triangle facing +z; depth at each covered pixel centre equals the
+    # plane's depth (zd = -z * 2^16) up to the integer floor and quantisation.
+    xp = np.array([[-0.5, -0.5, 0.1], [0.5, -0.5, 0.3], [-0.5, 0.5, -0.1]])
+    faces = np.array([[0, 1, 2]], np.int32)
+    dirs = np.zeros((32, 3))
+    dirs[:, 2] = 1
+    fr = _frames_for(dirs)
+    R = 64
+    half = 0.75
+    bits, depth = O.visibility(xp, faces, fr, [0, 0, 0], half, 0.0, R, want_depth=True)
+    e1, e2, w = fr[0].reshape(3, 3)
+    d0 = depth[0]
+    covered = d0 != np.iinfo(np.int32).max
+    assert covered.sum() > 0.15 * R * R      # the triangle covers 2/9 of the window
+    # plane z(x,y) through the three vertices
+    A = np.c_[xp[:, :2], np.ones(3)]
+    coef = np.linalg.solve(A, xp[:, 2])
+    jj, ii = np.nonzero(covered)
+    # pixel centre -> s, t world coordinates in the frame basis
+    s = (ii + 0.5) / R * 2 * half - half
+    t = (jj + 0.5) / R * 2 * half - half
+    P = np.outer(s, e1) + np.outer(t, e2)
+    z = coef[0] * P[:, 0] + coef[1] * P[:, 1] + coef[2]
+    expect = -z * 65536.0
+    assert np.max(np.abs(d0[jj, ii] - expect)) < 40.0   # ~0.6 mm: fixed-point steps
+
+
+def test_visibility_rejects_unsupported_arguments():
+    xp = np.zeros((3, 3))
+    faces = np.array([[0, 1, 2]], np.int32)
+    with pytest.raises(ValueError):
+        O.visibility(xp, faces, _frames_for(np.eye(3)[[2] * 30]), [0, 0, 0], 1.0, 0.0, 64)
+    with pytest.raises(ValueError):
+        O.visibility(xp, faces, _frames_for(np.eye(3)[[2] * 32]), [0, 0, 0], 1.0, 0.0, 2048)
+    with pytest.raises(ValueError):
+        O.visibility(np.full((3, 3), 9.0), faces, _frames_for(np.eye(3)[[2] * 32]), [0, 0, 0],
+                     1.0, 0.0, 64)
+
+
+# ---------------------------------------------------------------- shading
+def _one_gaussian(n, x=(0, 0, 0), a=(0.5, 0.5, 0.5), rough=0.5, spec=0.0):
+    return (np.array([x], float), np.array([n], float), np.array([a], float),
+            np.array([rough]), np.array([spec]), np.ones((1, 1)), np.zeros((1, 1), np.int32))
+
+
+def test_light_solid_angles_and_quadrature():
+    rng = np.random.default_rng(0)
+    for rows, cols in ((8, 16), (16, 32), (32, 64)):
+        lt = synth.latlong_light(rng, rows, cols)
+        assert abs(lt.A.sum() - 4 * math.pi) < 1e-12
+    lt = synth.latlong_light(rng, 32, 64)
+    for n in ([0, 1, 0], [1, 0, 0], [0.3, -0.5, 0.8]):
+        n = np.array(n) / np.linalg.norm(n)
+        Q = np.sum(lt.A * np.maximum(0, lt.w @ n))
+        assert abs(Q - math.pi) < 0.01
+
+
+def test_shade_lambertian_constant_light_all_visible():
+    """Constant L, full visibility, p = 0: colour = (a L Q(n)/pi)^(1/2.2)."""
+    rng = np.random.default_rng(1)
+    lt = synth.latlong_light(rng, 16, 32)
+    Lc = np.full_like(lt.L, 1.7)
+    dmap = np.arange(len(lt.A), dtype=np.int32) % 32
+    bits = np.full((1, 1), 0xFFFFFFFF, np.uint32)
+    for n in ([0, 0, 1], [0.6, 0.0, 0.8], [0.1, 0.9, 0.3]):
+        n = np.array(n) / np.linalg.norm(n)
+        xd, nd, a, r, p, ub, knn = _one_gaussian(n, a=(0.2, 0.5, 0.9))
+        cam = 10.0 * n
+        col, rad, cull = O.shade(xd, nd, a, r, p, ub, knn, bits, Lc, lt.A, lt.w, dmap, cam, 32)
+        Q = np.sum(lt.A * np.maximum(0, lt.w @ n))
+        np.testing.assert_allclose(rad[0], a[0] * 1.7 * Q / math.pi, rtol=1e-13)
+        np.testing.assert_allclose(col[0], (a[0] * 1.7 * Q / math.pi) ** (1 / 2.2), rtol=1e-13)
+        # albedo x L within the quadrature error of the 16x32 light
+        np.testing.assert_allclose(rad[0], a[0] * 1.7, rtol=0.02)
+        assert cull[0] == 0
+
+
+def test_shade_visibility_is_linear_in_the_bits():
+    rng = np.random.default_rng(2)
+    lt = synth.latlong_light(rng, 8, 16)
+    dmap = np.arange(128, dtype=np.int32)
+    n = np.array([0.2, 0.7, 0.3])
+    n /= np.linalg.norm(n)
+    xd, nd, a, r, p, ub, knn = _one_gaussian(n, spec=0.7, rough=0.4)
+    cam = 5.0 * np.array([0.3, 0.8, 0.4])
+    mask = rng.integers(0, 2 ** 32, size=(1, 4), dtype=np.uint64).astype(np.uint32)
+    full = np.full((1, 4), 0xFFFFFFFF, np.uint32)
+    _, r_all, _ = O.shade(xd, nd, a, r, p, ub, knn, full, lt.L, lt.A, lt.w, dmap, cam, 128)
+    _, r_m, _ = O.shade(xd, nd, a, r, p, ub, knn, mask, lt.L, lt.A, lt.w, dmap, cam, 128)
+    _, r_c, _ = O.shade(xd, nd, a, r, p, ub, knn, ~mask, lt.L, lt.A, lt.w, dmap, cam, 128)
+    np.testing.assert_allclose(r_m + r_c, r_all, rtol=1e-13)
+    # two neighbours with weights 0.25/0.75 and complementary bits: vis = 0.25 / 0.75
+    ub2 = np.array([[0.25, 0.75]])
+    knn2 = np.array([[0, 1]], np.int32)
+    bits2 = np.concatenate([mask, ~mask])
+    _, r_mix, _ = O.shade(xd, nd, a, r, p, ub2, knn2, bits2, lt.L, lt.A, lt.w, dmap, cam, 128)
+    np.testing.assert_allclose(r_mix, 0.25 * r_m + 0.75 * r_c, rtol=1e-13)
+
+
+def test_shade_normal_incidence_closed_form():
+    """Light, view and normal aligned: f_s = F(1) / (4 pi alpha^2), App. A."""
+    gc = golden_constants()
+    n = np.array([0.0, 0.0, 1.0])
+    for gamma in (0.3, 0.55, 0.9):
+        xd, nd, a, r, p, ub, knn = _one_gaussian(n, a=(0, 0, 0), rough=gamma, spec=1.0)
+        L = np.array([[1.0, 2.0, 3.0]])
+        A = np.array([0.01])
+        w = np.array([n])
+        cam = 1e7 * n
+        _, rad, _ = O.shade(xd, nd, a, r, p, ub, knn, np.full((1, 1), 1, np.uint32), L, A, w,
+                            np.zeros(1, np.int32), cam, 32)
+        alpha = gamma ** gc["alpha_power"]
+        F = gc["F0"] + (1 - gc["F0"]) * 2.0 ** ((gc["fresnel_a"] + gc["fresnel_b"]))
+        fs = F / (4 * math.pi * alpha * alpha)
+        np.testing.assert_allclose(rad[0], L[0] * A[0] * fs, rtol=1e-9)
+
+
+def test_shade_brdf_reciprocity_and_furnace_bound():
+    n = np.array([0.0, 1.0, 0.0])
+    rng = np.random.default_rng(3)
+    for _ in range(6):
+        w1 = rng.normal(size=3); w1[1] = abs(w1[1]) + 0.1; w1 /= np.linalg.norm(w1)
+        w2 = rng.normal(size=3); w2[1] = abs(w2[1]) + 0.1; w2 /= np.linalg.norm(w2)
+        gamma = rng.uniform(0.3, 0.9)
+        xd, nd, a, r, p, ub, knn = _one_gaussian(n, a=(0, 0, 0), rough=gamma, spec=1.0)
+        one = np.ones((1, 3))
+        bits = np.full((1, 1), 1, np.uint32)
+        z = np.zeros(1, np.int32)
+        _, r12, _ = O.shade(xd, nd, a, r, p, ub, knn, bits, one, np.ones(1), w1[None], z, 1e7 * w2, 32)
+        _, r21, _ = O.shade(xd, nd, a, r, p, ub, knn, bits, one, np.ones(1), w2[None], z, 1e7 * w1, 32)
+        np.testing.assert_allclose(r12 / (n @ w1), r21 / (n @ w2), rtol=1e-6)
+    # white furnace: specular directional albedo never exceeds 1
+    lt = synth.latlong_light(rng, 64, 128)
+    full = np.full((1, 256), 0xFFFFFFFF, np.uint32)
+    dmap = np.arange(len(lt.A), dtype=np.int32) % 8192
+    for gamma in (0.3, 0.6, 0.9):
+        for th in (0.0, 0.7, 1.3):
+            wo = np.array([math.sin(th), math.cos(th), 0.0])
+            xd, nd, a, r, p, ub, knn = _one_gaussian(n, a=(0, 0, 0), rough=gamma, spec=1.0)
+            _, rad, _ = O.shade(xd, nd, a, r, p, ub, knn, full, np.ones_like(lt.L), lt.A, lt.w,
+                                dmap, 1e7 * wo, 8192)
+            assert 0.0 < rad[0, 0] <= 1.0
+
+
+def test_shade_backface_cull():
+    n = np.array([0.0, 0.0, 1.0])
+    xd, nd, a, r, p, ub, knn = _one_gaussian(n)
+    lt = synth.latlong_light(np.random.default_rng(0), 8, 16)
+    dmap = np.zeros(128, np.int32)
+    bits = np.full((1, 1), 1, np.uint32)
+    col, rad, cull = O.shade(xd, nd, a, r, p, ub, knn, bits, lt.L, lt.A, lt.w, dmap,
+                             np.array([0, 0, -3.0]), 32)
+    assert cull[0] == 1 and np.all(col == 0)
+    col, rad, cull = O.shade(xd, nd, a, r, p, ub, knn, bits, lt.L, lt.A, lt.w, dmap,
+                             np.array([0, 0, 3.0]), 32)
+    assert cull[0] == 0 and np.all(col > 0)
+
+
+# ---------------------------------------------------------------- projection
+def _cam(width=64, height=64, f=100.0, R=None, t=(0, 0, 0)):
+    R = np.eye(3) if R is None else R
+    t = np.asarray(t, float)
+    return synth.Camera(fx=f, fy=f * 1.1, cx=width / 2, cy=height / 2, width=width, height=height,
+                        R=R, t=t, center=-R.T @ t)
+
+
+def test_project_isotropic_on_axis_closed_form():
+    cam = _cam()
+    sigma, z = 0.02, 2.0
+    xd = np.array([[0.0, 0.0, z]])
+    cov = np.array([[sigma ** 2, 0, 0, sigma ** 2, 0, sigma ** 2]])
+    pr = O.project(xd, cov, np.array([0.8]), None, cam)
+    sx = (cam.fx * sigma / z) ** 2 + 0.3
+    sy = (cam.fy * sigma / z) ** 2 + 0.3
+    np.testing.assert_allclose(pr["conic"][0], [1 / sx, 0, 1 / sy], rtol=1e-13, atol=1e-16)
+    np.testing.assert_allclose(pr["mean2d"][0], [cam.cx, cam.cy], atol=1e-13)
+    assert pr["valid"][0] == 1 and pr["depth"][0] == z
+
+
+def test_project_offaxis_matches_numeric_jacobian():
+    rng = np.random.default_rng(4)
+    R = rot([0.3, 1, 0.2], 0.4)
+    cam = _cam(R=R, t=(0.1, -0.2, 3.0))
+    for _ in range(5):
+        x = rng.normal(scale=0.3, size=3)
+        A = rng.normal(scale=0.03, size=(3, 3))
+        S = A @ A.T
+        cov = S[[0, 0, 0, 1, 1, 2], [0, 1, 2, 1, 2, 2]][None]
+        pr = O.project(x[None], cov, np.array([0.9]), None, cam)
+
+        def pix(y):
+            p = R @ y + cam.t
+            return np.array([cam.fx * p[0] / p[2] + cam.cx, cam.fy * p[1] / p[2] + cam.cy])
+        h = 1e-6
+        Jn = np.stack([(pix(x + h * e) - pix(x - h * e)) / (2 * h) for e in np.eye(3)], axis=1)
+        S2 = Jn @ S @ Jn.T + 0.3 * np.eye(2)
+        inv = np.linalg.inv(S2)
+        np.testing.assert_allclose(pr["conic"][0], [inv[0, 0], inv[0, 1], inv[1, 1]], rtol=1e-6)
+        np.testing.assert_allclose(pr["mean2d"][0], pix(x), rtol=1e-13)
+
+
+def test_project_validity_rules():
+    cam = _cam()
+    xd = np.array([[0, 0, 0.1], [0, 0, 1.0], [0, 0, 1.0], [0, 0, 1.0]])
+    cov = np.tile([[1e-4, 0, 0, 1e-4, 0, 1e-4]], (4, 1))
+    op = np.array([0.5, 0.5, 0.5, 1.0 / 300])
+    cull = np.array([0, 1, 0, 0], np.uint8)
+    pr = O.project(xd, cov, op, cull, cam)
+    assert list(pr["valid"]) == [0, 0, 1, 0]
+
+
+def test_project_rect_contains_the_alpha_support():
+    rng = np.random.default_rng(6)
+    cam = _cam(width=96, height=80, f=120.0)
+    G = 40
+    xd = np.c_[rng.uniform(-0.3, 0.3, G), rng.uniform(-0.3, 0.3, G), rng.uniform(1.0, 2.0, G)]
+    covs = []
+    for _ in range(G):
+        A = rng.normal(scale=0.03, size=(3, 3))
+        S = A @ A.T
+        covs.append(S[[0, 0, 0, 1, 1, 2], [0, 1, 2, 1, 2, 2]])
+    op = rng.uniform(0.3, 0.95, G)
+    pr = O.project(xd, np.array(covs), op, None, cam)
+    ys, xs = np.mgrid[0:cam.height, 0:cam.width]
+    for g in range(G):
+        dx = xs + 0.5 - pr["mean2d"][g, 0]
+        dy = ys + 0.5 - pr["mean2d"][g, 1]
+        c = pr["conic"][g]
+        a = op[g] * np.exp(-0.5 * (c[0] * dx * dx + 2 * c[1] * dx * dy + c[2] * dy * dy))
+        jj, ii = np.nonzero(a >= 1 / 255)
+        r = pr["rect"][g]
+        assert np.all((ii >= r[0]) & (ii <= r[2]) & (jj >= r[1]) & (jj <= r[3]))
+
+
+# ---------------------------------------------------------------- compositing
+def test_composite_one_and_two_gaussians_closed_form():
+    W = H = 16
+    m = np.array([[8.0, 8.0], [8.5, 7.5]])
+    conic = np.array([[0.05, 0.01, 0.04], [0.03, -0.005, 0.06]])
+    op = np.array([0.7, 0.6])
+    col = np.array([[1.0, 0.2, 0.1], [0.1, 0.3, 0.9]])
+    px = np.array([7 * W + 9])
+    x, y = 9.5, 7.5
+
+    def alpha(g):
+        dx, dy = x - m[g, 0], y - m[g, 1]
+        c = conic[g]
+        return min(0.99, op[g] * math.exp(-0.5 * (c[0] * dx * dx + 2 * c[1] * dx * dy + c[2] * dy * dy)))
+    a0, a1 = alpha(0), alpha(1)
+    rgb, T, cnt, _ = O.composite(m[:1], conic[:1], op[:1], col[:1], np.array([1.0]), [1], W, H, px)
+    np.testing.assert_allclose(rgb[0], col[0] * a0, rtol=1e-14)
+    np.testing.assert_allclose(T[0], 1 - a0, rtol=1e-14)
+    for d in ([1.0, 2.0], [2.0, 1.0]):
+        rgb, T, cnt, _ = O.composite(m, conic, op, col, np.array(d), [1, 1], W, H, px)
+        f, b = (0, 1) if d[0] < d[1] else (1, 0)
+        af, ab = (a0, a1) if f == 0 else (a1, a0)
+        np.testing.assert_allclose(rgb[0], col[f] * af + col[b] * ab * (1 - af), rtol=1e-14)
+        np.testing.assert_allclose(T[0], (1 - af) * (1 - ab), rtol=1e-14)
+        assert cnt[0] == 2
+
+
+def test_composite_weights_sum_to_at_most_one_and_stop_rule():
+    sc = synth.config_scene("c3_fd")
+    fr = OP.frame(sc)
+    pr = fr["proj"]
+    ones = np.ones_like(fr["color"])
+    rgb, T, cnt, amb = O.composite(pr["mean2d"], pr["conic"], sc.avatar.opacity, ones,
+                                   pr["depth"], pr["valid"], 64, 64)
+    np.testing.assert_allclose(rgb[:, 0], 1 - T, atol=1e-12)
+    assert np.all(T >= 1e-4 - 1e-15) and np.all(T <= 1.0)
+    # a stack of opaque Gaussians stops once T would drop below 1e-4
+    n = 12
+    m = np.tile([[8.0, 8.0]], (n, 1))
+    conic = np.tile([[1e-4, 0, 1e-4]], (n, 1))
+    op = np.full(n, 0.9)
+    rgb, T, cnt, _ = O.composite(m, conic, op, np.ones((n, 3)), np.arange(n, dtype=float),
+                                 np.ones(n), 16, 16, np.array([8 * 16 + 8]))
+    a = 0.9 * math.exp(-0.5 * 1e-4 * 0.5)
+    k = 0
+    t = 1.0
+    while t * (1 - a) >= 1e-4:
+        t *= 1 - a
+        k += 1
+    assert cnt[0] == k
+    np.testing.assert_allclose(T[0], t, rtol=1e-13)
+
+
+# ---------------------------------------------------------------- binning
+def test_bin_matches_pairwise_enumeration():
+    rng = np.random.default_rng(7)
+    G, W, H, TS = 300, 100, 70, 16
+    x0 = rng.integers(-5, W, G); y0 = rng.integers(-5, H, G)
+    x1 = x0 + rng.integers(-3, 40, G); y1 = y0 + rng.integers(-3, 30, G)
+    rect = np.c_[np.clip(x0, 0, W - 1), np.clip(y0, 0, H - 1), np.clip(x1, 0, W - 1), np.clip(y1, 0, H - 1)]
+    rect[x1 < 0] = [0, 0, -1, -1]
+    key = rng.integers(0, 50, G).astype(np.uint32)     # many equal keys: tests the index tie-break
+    start, lst = O.bin_tiles(rect, key, W, H, TS)
+    tx = (W + TS - 1) // TS
+    pairs = []
+    for g in range(G):
+        r = rect[g]
+        if r[0] > r[2] or r[1] > r[3]:
+            continue
+        for ty in range(r[1] // TS, r[3] // TS + 1):
+            for txx in range(r[0] // TS, r[2] // TS + 1):
+                pairs.append((ty * tx + txx, int(key[g]), g))
+    pairs.sort()
+    assert len(pairs) == len(lst)
+    assert [p[2] for p in pairs] == list(lst)
+    counts = np.bincount([p[0] for p in pairs], minlength=len(start) - 1)
+    np.testing.assert_array_equal(np.diff(start), counts)
+
+
+# ---------------------------------------------------------------- adjoint
+def _fd_setup():
+    sc = synth.config_scene("c3_fd")
+    fr = OP.frame(sc)
+    av = sc.avatar
+    fixed = dict(knn=av.knn, xv=AJ.t64(av.xv), dxv=AJ.t64(av.dxv), nv=AJ.t64(av.nv),
+                 bone=AJ.t64(fr["bone"]), bits=fr["bits"], dmap=sc.dmap, A=AJ.t64(sc.light.A),
+                 w=AJ.t64(sc.light.w), cam_center=AJ.t64(sc.camera.center), culled=fr["cull"],
+                 valid=fr["proj"]["valid"], cam=sc.camera)
+    params = dict(xg=av.xg, logscale=av.logscale, quat=av.quat, opacity=av.opacity, av=av.av,
+                  rv=av.rv, pv=av.pv, L=sc.light.L, wv=av.wv)
+    return sc, fr, fixed, params
+
+
+def test_adjoint_forward_agrees_with_c_oracle():
+    sc, fr, fixed, params = _fd_setup()
+    tp = {k: AJ.t64(v) for k, v in params.items()}
+    img = AJ.render(tp, fixed).numpy().reshape(-1, 3)
+    ok = fr["amb"] == 0
+    assert ok.mean() > 0.98
+    np.testing.assert_allclose(img[ok], fr["rgb"][ok], atol=1e-11)
+
+
+def _c_loss(sc, fr, params, target):
+    s2 = copy.deepcopy(sc)
+    av = s2.avatar
+    av.xg, av.logscale, av.quat, av.opacity = params["xg"], params["logscale"], params["quat"], params["opacity"]
+    av.av, av.rv, av.pv, av.wv = params["av"], params["rv"], params["pv"], params["wv"]
+    s2.light.L = params["L"]
+    out = OP.frame(s2, bits=fr["bits"])
+    return np.abs(out["rgb"] - target).mean()
+
+
+def test_adjoint_matches_central_finite_differences():
+    sc, fr, fixed, params = _fd_setup()
+    rng = np.random.default_rng(11)
+    # target: the same frame with perturbed albedo, roughness and light
+    tgt_params = dict(params)
+    tgt_params["av"] = np.clip(params["av"] * rng.uniform(0.8, 1.2, params["av"].shape), 0, 1)
+    tgt_params["rv"] = np.clip(params["rv"] + rng.normal(0, 0.05, params["rv"].shape), 0.2, 1)
+    tgt_params["L"] = params["L"] * rng.uniform(0.8, 1.2, params["L"].shape)
+    s_t = copy.deepcopy(sc)
+    s_t.avatar.av, s_t.avatar.rv, s_t.light.L = tgt_params["av"], tgt_params["rv"], tgt_params["L"]
+    target = OP.frame(s_t, bits=fr["bits"])["rgb"]
+    tp = {k: AJ.t64(v).requires_grad_(True) for k, v in params.items()}
+    img = AJ.render(tp, fixed)
+    loss = AJ.l1_loss(img, AJ.t64(target).reshape(img.shape))
+    loss.backward()
+    valid = np.nonzero(fr["proj"]["valid"])[0]
+    used_v = np.unique(sc.avatar.knn[valid])
+    picks = {
+        "xg": [(g, c) for g in rng.choice(valid, 4) for c in (rng.integers(3),)],
+        "logscale": [(g, rng.integers(3)) for g in rng.choice(valid, 4)],
+        "quat": [(g, rng.integers(4)) for g in rng.choice(valid, 4)],
+        "opacity": [(g,) for g in rng.choice(valid, 4)],
+        "av": [(v, rng.integers(3)) for v in rng.choice(used_v, 4)],
+        "rv": [(v,) for v in rng.choice(used_v, 4)],
+        "pv": [(v,) for v in rng.choice(used_v, 4)],
+        "L": [(k, rng.integers(3)) for k in rng.integers(0, len(sc.light.A), 4)],
+        "wv": [(v, rng.integers(24)) for v in rng.choice(used_v, 4)],
+    }
+    kinks = 0
+    for name, idxs in picks.items():
+        g_all = tp[name].grad.numpy()
+        for idx in idxs:
+            idx = tuple(int(i) for i in idx)
+            base = params[name]
+            h = 1e-6 * max(1.0, abs(float(base[idx])))
+            def fd(step):
+                p_plus = dict(params); p_minus = dict(params)
+                a = base.copy(); a[idx] += step; p_plus[name] = a
+                b = base.copy(); b[idx] -= step; p_minus[name] = b
+                return (_c_loss(sc, fr, p_plus, target) - _c_loss(sc, fr, p_minus, target)) / (2 * step)
+            d1 = fd(h)
+            ga = float(g_all[idx])
+            if abs(d1 - ga) <= 1e-5 * max(abs(d1), abs(ga)) + 1e-10:
+                continue
+            d2 = fd(h / 4)
+            if abs(d1 - d2) > 1e-4 * max(abs(d1), 1e-8):   # threshold crossing: not a smooth point
+                kinks += 1
+                continue
+            raise AssertionError(f"{name}{idx}: autograd {ga} vs FD {d1}")
+    assert kinks <= 2
