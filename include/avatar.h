@@ -1,0 +1,321 @@
+/*
+ * avatar.h - C ABI of the GB300 (sm_103a) relit-avatar render path.
+ *
+ * The per-frame path of "Interactive Rendering of Relightable and Animatable
+ * Gaussian Avatars" (arXiv 2407.10707): for a novel pose and environment
+ * light, (a) skin the canonical Gaussians and mesh (Sec. 3.1, Eq. 1),
+ * (b) compute per-vertex visibility toward D directions by rasterising the
+ * posed mesh into depth maps (Sec. 3.2, shadow-mapping form), (c) shade every
+ * Gaussian with the discrete rendering equation (Eq. 2, BRDF of App. A), and
+ * (d) splat the Gaussians with tile-binned, depth-sorted front-to-back alpha
+ * blending (the 3DGS rasteriser of Sec. 3.1).  Backward calls give the
+ * adjoints used by the training loop (Sec. 3.3).
+ *
+ * Conventions shared by every call
+ *  - Every pointer is a DEVICE pointer owned by the caller, except where a
+ *    field says "host".  Arrays are float32 structure-of-arrays: "[3][G]"
+ *    means three contiguous planes of G floats.  Index arrays are int32.
+ *  - Calls are asynchronous on the given stream (NULL = legacy default
+ *    stream) and never synchronise the device; they allocate no device
+ *    memory.  Scratch comes from a caller-provided workspace whose size the
+ *    matching *_workspace_size query returns; workspaces must be 256-byte
+ *    aligned.
+ *  - The return value reports argument errors found on the host and launch
+ *    failures.  Errors found on the device (index out of range, pair-buffer
+ *    overflow, a bounded wait that expired) are written to the optional
+ *    device word `status` (first error wins; the caller zeroes it), so that
+ *    calls stay capturable in CUDA graphs.
+ *  - Outputs are overwritten, never accumulated, unless a field says so.
+ *  - The library is single-GPU: the context binds one device.
+ */
+#ifndef AVATAR_H
+#define AVATAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t; declared opaquely so this header needs no CUDA include. */
+typedef struct CUstream_st *avatar_stream_t;
+
+enum avatar_status {
+    AVATAR_OK = 0,
+    AVATAR_ERR_INVALID_ARG = 1,  /* bad size, NULL pointer, out-of-range value */
+    AVATAR_ERR_WORKSPACE = 2,    /* workspace missing, misaligned or too small */
+    AVATAR_ERR_OVERFLOW = 3,     /* (tile, Gaussian) pairs exceed pair_capacity */
+    AVATAR_ERR_TIMEOUT = 4,      /* a bounded device-side wait expired */
+    AVATAR_ERR_CUDA = 5,         /* a CUDA runtime call or launch failed */
+    AVATAR_ERR_UNSUPPORTED = 6,  /* device or configuration not supported */
+    AVATAR_ERR_INDEX = 7         /* device: an index array entry is out of range */
+};
+
+/* Static English description of a status code; never NULL. */
+const char *avatar_status_string(int status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int avatar_version(void);
+
+/* ------------------------------------------------------------------ */
+/* Context: binds a device, caches its SM count and tuning choices.     */
+/* ------------------------------------------------------------------ */
+typedef struct avatar_ctx avatar_ctx;
+
+/* Create a context for CUDA device `device` (host pointer out).  Fails with
+ * AVATAR_ERR_UNSUPPORTED on devices other than compute capability 10.3. */
+int avatar_ctx_create(avatar_ctx **out, int device);
+int avatar_ctx_destroy(avatar_ctx *ctx);
+/* Number of streaming multiprocessors of the context's device. */
+int avatar_ctx_sm_count(const avatar_ctx *ctx);
+
+/* ------------------------------------------------------------------ */
+/* (a) Skinning - Sec. 3.1, Eq. 1                                       */
+/*                                                                      */
+/* Forward kinematics: bone_j = T_j * translate(-J_j) with               */
+/*   T_j = T_parent(j) * [Rodrigues(pose_j) | J_j - J_parent(j)].         */
+/* Vertices: A_v = sum_k w_vk bone_k, xp_v = A_v (x_v + dx_v).            */
+/* Gaussians (Eq. 1): u_j = 1/max(|x_g - x_j|, 1e-8) over the K nearest   */
+/*   vertices, ubar = u / sum u, *_g = sum_j ubar_j *_j for albedo,       */
+/*   roughness, specular tint, normal, LBS weights and displacement;      */
+/*   xbar = x_g + dx_g; A_g = sum_k w_gk bone_k (= sum_j ubar_j A_j);     */
+/*   x_gd = A_g xbar; Sigma_gd = M Sigma M^T with Sigma = R(q) S^2 R(q)^T,*/
+/*   S = diag(exp(logscale)); n_gd = normalize(M normalize(n_g)), M the   */
+/*   linear part of A_g.                                                  */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int G;                 /* Gaussians (>= 0) */
+    int Nv;                /* mesh vertices (>= 1) */
+    int K;                 /* neighbours per Gaussian, 1..8 (paper: 3) */
+    int J;                 /* joints, 1..64 (SMPL: 24) */
+    /* canonical Gaussians */
+    const float *xg;       /* [3][G] positions */
+    const float *logscale; /* [3][G] log of the three axis scales */
+    const float *quat;     /* [4][G] rotation quaternion (w,x,y,z), any norm > 0 */
+    const int32_t *knn;    /* [K][G] indices of the K nearest vertices (S_g) */
+    /* canonical mesh attributes */
+    const float *xv;       /* [3][Nv] positions */
+    const float *dxv;      /* [3][Nv] displacement, or NULL for zero */
+    const float *wv;       /* [Nv][J] LBS weights, vertex-major */
+    const float *av;       /* [3][Nv] albedo */
+    const float *rv;       /* [Nv] roughness */
+    const float *pv;       /* [Nv] specular tint */
+    const float *nv;       /* [3][Nv] normals */
+    /* skeleton */
+    const int32_t *parents; /* [J] parent index, parents[j] < j, root -1 */
+    const float *joints;   /* [J][3] rest joint positions */
+    const float *pose;     /* [J][3] axis-angle joint rotations */
+    /* outputs */
+    float *bone;           /* [J][12] bone transforms, row-major 3x4 */
+    float *xp;             /* [3][Nv] posed vertices */
+    float *xd;             /* [3][G] posed Gaussian positions x_gd */
+    float *cov;            /* [6][G] posed covariance (xx,xy,xz,yy,yz,zz) */
+    float *nd;             /* [3][G] posed unit normals n_gd */
+    float *ag;             /* [3][G] albedo */
+    float *rg;             /* [G] roughness */
+    float *pg;             /* [G] specular tint */
+    float *ubar;           /* [K][G] normalised Eq. 1 weights */
+    int32_t *status;       /* optional device status word */
+} avatar_skin_args;
+
+/* Workspace for avatar_skin: per-vertex packed records (Nv*112 bytes).
+ * avatar_skin_backward reads the records the forward left there, so keep
+ * the workspace intact between the two calls. */
+size_t avatar_skin_workspace_size(const avatar_skin_args *a);
+int avatar_skin(avatar_ctx *ctx, const avatar_skin_args *a, void *ws, size_t ws_bytes,
+                avatar_stream_t stream);
+
+typedef struct {
+    /* upstream gradients ([.][G]); NULL = zero.  d_xd2 is a second upstream
+     * gradient of x_gd (splatting and shading both reach x_gd); it is added
+     * to d_xd. */
+    const float *d_xd, *d_cov, *d_nd, *d_ag, *d_rg, *d_pg, *d_ubar, *d_xd2;
+    /* gradients written ([.][G] and [.][Nv]); NULL = not wanted */
+    float *d_xg;           /* [3][G] */
+    float *d_logscale;     /* [3][G] */
+    float *d_quat;         /* [4][G] */
+    float *d_wv;           /* [Nv][J] */
+    float *d_av;           /* [3][Nv] */
+    float *d_rv;           /* [Nv] */
+    float *d_pv;           /* [Nv] */
+    float *d_dxv;          /* [3][Nv] */
+} avatar_skin_grads;
+
+/* Backward workspace (per-vertex accumulators), disjoint from the forward's. */
+size_t avatar_skin_backward_workspace_size(const avatar_skin_args *a);
+int avatar_skin_backward(avatar_ctx *ctx, const avatar_skin_args *a, const avatar_skin_grads *g,
+                         const void *fwd_ws, void *ws, size_t ws_bytes, avatar_stream_t stream);
+
+/* ------------------------------------------------------------------ */
+/* (b) Visibility - Sec. 3.2, depth-map (shadow-mapping) form.          */
+/*                                                                      */
+/* Exact integer rules (any correct implementation gives the same bits):*/
+/*  q = rint(x*2^13) - rint(center*2^13), |q_i| < 2^16                    */
+/*  B = rint(frame*2^13); s = e1.q, t = e2.q; zd = floor(-(w.q)/2^10)     */
+/*  H = rint(half_extent*2^26) with 16R < H <= 2^30; M = floor(R 2^35/H)  */
+/*  X = floor((s+H) M / 2^32), Y from t: 1/16-pixel units, in the window  */
+/*  iff 0 <= X,Y < 16R.  Triangles with a vertex outside the window or    */
+/*  zero area are skipped; a triangle (either winding) covers pixel (i,j) */
+/*  iff its three edge functions at (16i+8, 16j+8) are >= 0; its depth    */
+/*  there is floor(sum w_i zd_i / area); the depth map keeps the minimum. */
+/*  bit(v,d) = 1 iff v is outside the window, its pixel is empty, or      */
+/*  zd_v <= depth[pixel(v)] + rint(bias*2^16).                            */
+/* Output bit layout: vertex-major words.  With dmap == NULL the word     */
+/* index is d>>5 over the D viewpoints ([Nv][D/32]); with a light->view   */
+/* map dmap[NL] the bits are re-ordered per light: bit k of vertex v is  */
+/* bit(v, dmap[k]) in words [Nv][ceil(NL/32)] (the form avatar_shade     */
+/* reads).                                                              */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int Nv;                /* vertices */
+    int F;                 /* triangles */
+    int D;                 /* viewpoints, multiple of 32, <= 4096 */
+    int R;                 /* depth-map resolution, 8..512 */
+    const float *xp;       /* [3][Nv] posed vertices */
+    const int32_t *faces;  /* [F][3] vertex indices */
+    const float *frames;   /* [D][9] unit rows e1, e2, w (w points toward the light) */
+    float center[3];       /* host value: window centre (world) */
+    float half_extent;     /* host value: window half width (world) */
+    float bias;            /* host value: depth bias (world units) */
+    int NL;                /* lights for the re-ordered output (0: none) */
+    const int32_t *dmap;   /* [NL] light -> viewpoint, or NULL */
+    uint32_t *bits;        /* output, layout above */
+    int32_t *status;       /* optional device status word */
+} avatar_vis_args;
+
+size_t avatar_visibility_workspace_size(const avatar_vis_args *a);
+int avatar_visibility(avatar_ctx *ctx, const avatar_vis_args *a, void *ws, size_t ws_bytes,
+                      avatar_stream_t stream);
+
+/* ------------------------------------------------------------------ */
+/* (c) Shading - Eq. 2 with the BRDF of App. A, cull and gamma (Sec 3.1)*/
+/*                                                                      */
+/* cull: with d = C - x_gd (FP32), culled iff !(fma(n2,d2,fma(n1,d1,     */
+/*   n0*d0)) > 0); culled Gaussians get colour 0 and are not splatted.   */
+/* Otherwise, w_o = normalize(C - x_gd), c_o = max(n.w_o, 0), and over   */
+/* lights k with c_i = n.w_k > 0:                                       */
+/*   vis = sum_j ubar_j bit(S_j, k)                                      */
+/*   f_s = D F / (4 (c_i(1-kk)+kk)(c_o(1-kk)+kk)),  alpha = gamma^2,      */
+/*   kk = (gamma+1)^2/8, D = alpha^2/(pi((n.h)^2(alpha^2-1)+1)^2),       */
+/*   F = 0.04 + 0.96*2^((-5.55473 w_o.h - 6.98316) w_o.h)                */
+/*   L_o += L_k A_k vis c_i (a/pi + p f_s)                               */
+/* colour = max(L_o, 1e-6)^(1/2.2).                                      */
+/* Bits are light-ordered ([Nv][ceil(NL/32)], see avatar_visibility).   */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int G, K, NL, Nv;
+    const float *xd, *nd, *ag, *rg, *pg; /* skinning outputs */
+    const float *ubar;     /* [K][G] */
+    const int32_t *knn;    /* [K][G] */
+    const uint32_t *bits;  /* [Nv][ceil(NL/32)] light-ordered visibility */
+    const float *light_L;  /* [NL][3] radiance */
+    const float *light_A;  /* [NL] solid angle */
+    const float *light_w;  /* [NL][3] unit direction toward the light */
+    float cam_center[3];   /* host value: camera centre (world) */
+    float *color;          /* [3][G] output shading colour */
+    float *radiance;       /* [3][G] output L_o before gamma (read by the backward) */
+    uint8_t *cull;         /* [G] output, 1 = back-facing */
+    int32_t *status;
+} avatar_shade_args;
+
+int avatar_shade(avatar_ctx *ctx, const avatar_shade_args *a, avatar_stream_t stream);
+
+typedef struct {
+    const float *d_color;  /* [3][G] upstream */
+    float *d_xd;           /* [3][G] written (through w_o) */
+    float *d_nd;           /* [3][G] written */
+    float *d_ag;           /* [3][G] written */
+    float *d_rg;           /* [G] written */
+    float *d_pg;           /* [G] written */
+    float *d_ubar;         /* [K][G] written (through vis) */
+    float *d_light_L;      /* [NL][3] written */
+} avatar_shade_grads;
+
+int avatar_shade_backward(avatar_ctx *ctx, const avatar_shade_args *a, const avatar_shade_grads *g,
+                          avatar_stream_t stream);
+
+/* ------------------------------------------------------------------ */
+/* (d) Splatting - the 3DGS rasteriser of Sec. 3.1, black background    */
+/*                                                                      */
+/* project: p = R x + t; valid iff not culled, p.z > 0.2, o > 1/255 and  */
+/*   det > 0; mean = (fx p.x/p.z + cx, fy p.y/p.z + cy); Sigma' = T Sigma */
+/*   T^T + 0.3 I with T = J R (EWA); conic = inverse(Sigma');            */
+/*   rect = pixels whose centre (i+1/2) lies in the AABB of the ellipse   */
+/*   q <= 2 ln(255 o) padded by 1 pixel (tile-size independent).         */
+/* bin: Gaussian g belongs to every tile its rect meets; each tile's     */
+/*   list is ordered by (depth bits, g) - a stable device radix sort.    */
+/* blend: per pixel centre, front to back: alpha = min(0.99, o e^{-q/2}),*/
+/*   skip alpha < 1/255, stop before T(1-alpha) < 1e-4, C += c alpha T.   */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    float fx, fy, cx, cy;  /* pinhole intrinsics (pixels) */
+    float R[9];            /* world->camera rotation, row-major (x right, y down, z forward) */
+    float t[3];            /* world->camera translation */
+    int width, height;     /* image size, 1..16384 */
+} avatar_camera;
+
+typedef struct {
+    int G;
+    avatar_camera cam;     /* host value */
+    int tile;              /* tile edge: 8, 16 or 32 pixels; 0 = 16 */
+    const float *xd;       /* [3][G] */
+    const float *cov;      /* [6][G] */
+    const float *opacity;  /* [G] */
+    const float *color;    /* [3][G] */
+    const uint8_t *cull;   /* [G] or NULL */
+    /* per-Gaussian projection (written by project) */
+    float *mean2d;         /* [2][G] */
+    float *conic;          /* [3][G] (a, b, c): q = a dx^2 + 2 b dx dy + c dy^2 */
+    float *depth;          /* [G] camera-space z */
+    int32_t *rect;         /* [4][G] inclusive pixel rect x0,y0,x1,y1 (x0 > x1: empty) */
+    /* binning (written by bin) */
+    int32_t *tile_range;   /* [ntiles][2] begin, end into pair_gauss */
+    int32_t *pair_gauss;   /* [pair_capacity] Gaussian index of each sorted pair */
+    int64_t pair_capacity; /* capacity of pair_gauss, >= 1 */
+    int32_t *num_pairs;    /* [1] total pairs (the required capacity on overflow) */
+    /* image (written by blend) */
+    float *image;          /* [3][H][W] */
+    float *T_final;        /* [H][W] final transmittance */
+    int32_t *n_last;       /* [H][W] list positions traversed up to the last contributor */
+    int32_t *status;
+} avatar_splat_args;
+
+/* ntiles = ceil(W/tile) * ceil(H/tile). */
+int avatar_splat_num_tiles(const avatar_splat_args *a);
+/* Workspace shared by all splat calls of one frame; keep it intact from
+ * avatar_splat to avatar_splat_backward. */
+size_t avatar_splat_workspace_size(const avatar_splat_args *a);
+/* The three steps, and all three in order. */
+int avatar_splat_project(avatar_ctx *ctx, const avatar_splat_args *a, void *ws, size_t ws_bytes,
+                         avatar_stream_t stream);
+int avatar_splat_bin(avatar_ctx *ctx, const avatar_splat_args *a, void *ws, size_t ws_bytes,
+                     avatar_stream_t stream);
+int avatar_splat_blend(avatar_ctx *ctx, const avatar_splat_args *a, void *ws, size_t ws_bytes,
+                       avatar_stream_t stream);
+int avatar_splat(avatar_ctx *ctx, const avatar_splat_args *a, void *ws, size_t ws_bytes,
+                 avatar_stream_t stream);
+
+typedef struct {
+    const float *d_image;  /* [3][H][W] upstream */
+    float *d_xd;           /* [3][G] written */
+    float *d_cov;          /* [6][G] written */
+    float *d_opacity;      /* [G] written */
+    float *d_color;        /* [3][G] written */
+} avatar_splat_grads;
+
+int avatar_splat_backward(avatar_ctx *ctx, const avatar_splat_args *a, const avatar_splat_grads *g,
+                          void *ws, size_t ws_bytes, avatar_stream_t stream);
+
+/* ------------------------------------------------------------------ */
+/* Image loss - L1 part of Eq. 5 (Sec. 3.3): loss = mean |img - target|, */
+/* d_img = sign(img - target) / n.  loss is a device float, d_img may be */
+/* NULL.                                                                */
+/* ------------------------------------------------------------------ */
+int avatar_l1_loss(avatar_ctx *ctx, int64_t n, const float *img, const float *target, float *loss,
+                   float *d_img, avatar_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AVATAR_H */

@@ -1,0 +1,129 @@
+"""ctypes mirror of include/avatar.h and the loader of libavatar.so.
+
+Argument marshalling only.  The library must exist and a GB300 must be
+present; there is no fallback of any kind: every entry point raises if the
+native library or the device is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libavatar.so")
+
+P = C.c_void_p
+I32 = C.c_int
+F32 = C.c_float
+
+STATUS = {0: "AVATAR_OK", 1: "AVATAR_ERR_INVALID_ARG", 2: "AVATAR_ERR_WORKSPACE", 3: "AVATAR_ERR_OVERFLOW",
+          4: "AVATAR_ERR_TIMEOUT", 5: "AVATAR_ERR_CUDA", 6: "AVATAR_ERR_UNSUPPORTED", 7: "AVATAR_ERR_INDEX"}
+
+
+class AvatarError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+class SkinArgs(C.Structure):
+    _fields_ = [("G", I32), ("Nv", I32), ("K", I32), ("J", I32),
+                ("xg", P), ("logscale", P), ("quat", P), ("knn", P),
+                ("xv", P), ("dxv", P), ("wv", P), ("av", P), ("rv", P), ("pv", P), ("nv", P),
+                ("parents", P), ("joints", P), ("pose", P),
+                ("bone", P), ("xp", P), ("xd", P), ("cov", P), ("nd", P), ("ag", P), ("rg", P),
+                ("pg", P), ("ubar", P), ("status", P)]
+
+
+class SkinGrads(C.Structure):
+    _fields_ = [("d_xd", P), ("d_cov", P), ("d_nd", P), ("d_ag", P), ("d_rg", P), ("d_pg", P),
+                ("d_ubar", P), ("d_xd2", P), ("d_xg", P), ("d_logscale", P), ("d_quat", P), ("d_wv", P),
+                ("d_av", P), ("d_rv", P), ("d_pv", P), ("d_dxv", P)]
+
+
+class VisArgs(C.Structure):
+    _fields_ = [("Nv", I32), ("F", I32), ("D", I32), ("R", I32),
+                ("xp", P), ("faces", P), ("frames", P),
+                ("center", F32 * 3), ("half_extent", F32), ("bias", F32),
+                ("NL", I32), ("dmap", P), ("bits", P), ("status", P)]
+
+
+class ShadeArgs(C.Structure):
+    _fields_ = [("G", I32), ("K", I32), ("NL", I32), ("Nv", I32),
+                ("xd", P), ("nd", P), ("ag", P), ("rg", P), ("pg", P), ("ubar", P), ("knn", P),
+                ("bits", P), ("light_L", P), ("light_A", P), ("light_w", P),
+                ("cam_center", F32 * 3), ("color", P), ("radiance", P), ("cull", P), ("status", P)]
+
+
+class ShadeGrads(C.Structure):
+    _fields_ = [("d_color", P), ("d_xd", P), ("d_nd", P), ("d_ag", P), ("d_rg", P), ("d_pg", P),
+                ("d_ubar", P), ("d_light_L", P)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("fx", F32), ("fy", F32), ("cx", F32), ("cy", F32), ("R", F32 * 9), ("t", F32 * 3),
+                ("width", I32), ("height", I32)]
+
+
+class SplatArgs(C.Structure):
+    _fields_ = [("G", I32), ("cam", Camera), ("tile", I32),
+                ("xd", P), ("cov", P), ("opacity", P), ("color", P), ("cull", P),
+                ("mean2d", P), ("conic", P), ("depth", P), ("rect", P),
+                ("tile_range", P), ("pair_gauss", P), ("pair_capacity", C.c_int64), ("num_pairs", P),
+                ("image", P), ("T_final", P), ("n_last", P), ("status", P)]
+
+
+class SplatGrads(C.Structure):
+    _fields_ = [("d_image", P), ("d_xd", P), ("d_cov", P), ("d_opacity", P), ("d_color", P)]
+
+
+# (name, argtypes, restype)
+_SIGNATURES = [
+    ("avatar_status_string", [I32], C.c_char_p),
+    ("avatar_version", [], I32),
+    ("avatar_ctx_create", [C.POINTER(P), I32], I32),
+    ("avatar_ctx_destroy", [P], I32),
+    ("avatar_ctx_sm_count", [P], I32),
+    ("avatar_skin_workspace_size", [C.POINTER(SkinArgs)], C.c_size_t),
+    ("avatar_skin", [P, C.POINTER(SkinArgs), P, C.c_size_t, P], I32),
+    ("avatar_skin_backward_workspace_size", [C.POINTER(SkinArgs)], C.c_size_t),
+    ("avatar_skin_backward", [P, C.POINTER(SkinArgs), C.POINTER(SkinGrads), P, P, C.c_size_t, P], I32),
+    ("avatar_visibility_workspace_size", [C.POINTER(VisArgs)], C.c_size_t),
+    ("avatar_visibility", [P, C.POINTER(VisArgs), P, C.c_size_t, P], I32),
+    ("avatar_shade", [P, C.POINTER(ShadeArgs), P], I32),
+    ("avatar_shade_backward", [P, C.POINTER(ShadeArgs), C.POINTER(ShadeGrads), P], I32),
+    ("avatar_splat_num_tiles", [C.POINTER(SplatArgs)], I32),
+    ("avatar_splat_workspace_size", [C.POINTER(SplatArgs)], C.c_size_t),
+    ("avatar_splat_project", [P, C.POINTER(SplatArgs), P, C.c_size_t, P], I32),
+    ("avatar_splat_bin", [P, C.POINTER(SplatArgs), P, C.c_size_t, P], I32),
+    ("avatar_splat_blend", [P, C.POINTER(SplatArgs), P, C.c_size_t, P], I32),
+    ("avatar_splat", [P, C.POINTER(SplatArgs), P, C.c_size_t, P], I32),
+    ("avatar_splat_backward", [P, C.POINTER(SplatArgs), C.POINTER(SplatGrads), P, C.c_size_t, P], I32),
+    ("avatar_l1_loss", [P, C.c_int64, P, P, P, P, P], I32),
+]
+
+EXPORTED = [s[0] for s in _SIGNATURES]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libavatar.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: run `python -c 'import __graft_entry__ as g; g.build()'` "
+                           "(the CUDA library is required; there is no CPU path)")
+    lib = C.CDLL(path)
+    for name, args, res in _SIGNATURES:
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def check(rc: int, where: str):
+    if rc != 0:
+        raise AvatarError(rc, where)

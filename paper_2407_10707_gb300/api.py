@@ -1,0 +1,347 @@
+"""PyTorch-facing binding of the C ABI (include/avatar.h), same names.
+
+Each function marshals torch CUDA tensors (float32 structure-of-arrays,
+int32 indices) into the argument structs and calls the native entry point
+on the current stream.  Outputs that are not passed in are allocated with
+torch (the library itself never allocates).  No arithmetic of the render
+path happens here.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _p(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _need_cuda(t, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+_CTX = {}
+
+
+def context(device=None):
+    """The avatar_ctx of a CUDA device (created once per device)."""
+    if not torch.cuda.is_available():
+        raise RuntimeError("a CUDA device (GB300, sm_103a) is required: the render path has no CPU fallback")
+    lib = L.load()
+    dev = torch.cuda.current_device() if device is None else torch.device(device).index or 0
+    if dev not in _CTX:
+        h = C.c_void_p()
+        L.check(lib.avatar_ctx_create(C.byref(h), dev), "avatar_ctx_create")
+        _CTX[dev] = h
+    return _CTX[dev]
+
+
+def workspace(nbytes, device):
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def status_word(device):
+    return torch.zeros(1, dtype=torch.int32, device=device)
+
+
+def raise_on_status(status, where="device"):
+    v = int(status.item())
+    if v != 0:
+        raise L.AvatarError(v, where)
+
+
+# ---------------------------------------------------------------- inputs
+def avatar_tensors(av, device="cuda"):
+    """Device layout of a synth.Avatar: SoA float32, int32 indices."""
+    f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=device)
+    i = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.int32, device=device)
+    return dict(xg=f(av.xg.T), logscale=f(av.logscale.T), quat=f(av.quat.T), opacity=f(av.opacity),
+                knn=i(av.knn.T), xv=f(av.xv.T), dxv=f(av.dxv.T), wv=f(av.wv), av=f(av.av.T), rv=f(av.rv),
+                pv=f(av.pv), nv=f(av.nv.T), parents=i(av.parents), joints=f(av.joints), pose=f(av.pose),
+                faces=i(av.faces))
+
+
+def camera_struct(cam):
+    c = L.Camera()
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    R = np.asarray(cam.R, np.float32).reshape(-1)
+    t = np.asarray(cam.t, np.float32).reshape(-1)
+    for k in range(9):
+        c.R[k] = float(R[k])
+    for k in range(3):
+        c.t[k] = float(t[k])
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+# ---------------------------------------------------------------- (a) skinning
+def _skin_struct(t, out, status):
+    G = t["xg"].shape[1]
+    Nv = t["xv"].shape[1]
+    K = t["knn"].shape[0]
+    J = t["parents"].shape[0]
+    a = L.SkinArgs()
+    a.G, a.Nv, a.K, a.J = G, Nv, K, J
+    for k in ("xg", "logscale", "quat", "knn", "xv", "dxv", "wv", "av", "rv", "pv", "nv", "parents", "joints",
+              "pose"):
+        setattr(a, k, _p(t.get(k)))
+    for k in ("bone", "xp", "xd", "cov", "nd", "ag", "rg", "pg", "ubar"):
+        setattr(a, k, _p(out[k]))
+    a.status = _p(status)
+    return a
+
+
+def alloc_skin_outputs(t):
+    dev = t["xg"].device
+    G, Nv, K, J = t["xg"].shape[1], t["xv"].shape[1], t["knn"].shape[0], t["parents"].shape[0]
+    e = lambda *s: torch.empty(*s, dtype=torch.float32, device=dev)
+    return dict(bone=e(J, 12), xp=e(3, Nv), xd=e(3, G), cov=e(6, G), nd=e(3, G), ag=e(3, G), rg=e(G), pg=e(G),
+                ubar=e(K, G))
+
+
+def avatar_skin(t, out=None, ws=None, status=None):
+    """(a) Skinning (Sec. 3.1, Eq. 1).  Returns the output dict; out['_ws']
+    holds the workspace the backward needs."""
+    lib = L.load()
+    ctx = context()
+    out = alloc_skin_outputs(t) if out is None else out
+    a = _skin_struct(t, out, status)
+    need = lib.avatar_skin_workspace_size(C.byref(a))
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, t["xg"].device)
+    L.check(lib.avatar_skin(ctx, C.byref(a), _p(ws), ws.numel(), _stream()), "avatar_skin")
+    out["_ws"] = ws
+    return out
+
+
+def avatar_skin_backward(t, out, up, want=("xg", "logscale", "quat", "wv", "av", "rv", "pv")):
+    """Adjoint of avatar_skin.  up: dict of upstream grads (d_xd, d_xd2,
+    d_cov, d_nd, d_ag, d_rg, d_pg, d_ubar; missing = zero)."""
+    lib = L.load()
+    ctx = context()
+    a = _skin_struct(t, out, None)
+    dev = t["xg"].device
+    g = L.SkinGrads()
+    keep = []
+    for k in ("d_xd", "d_cov", "d_nd", "d_ag", "d_rg", "d_pg", "d_ubar", "d_xd2"):
+        v = up.get(k)
+        v = v.contiguous() if v is not None else None
+        keep.append(v)
+        setattr(g, k, _p(v))
+    res = {}
+    for k in want:
+        res[k] = torch.empty_like(t[k])
+        setattr(g, "d_" + k, _p(res[k]))
+    need = lib.avatar_skin_backward_workspace_size(C.byref(a))
+    ws = workspace(need, dev)
+    L.check(lib.avatar_skin_backward(ctx, C.byref(a), C.byref(g), _p(out["_ws"]), _p(ws), ws.numel(), _stream()),
+            "avatar_skin_backward")
+    del keep
+    return res
+
+
+# ---------------------------------------------------------------- (b) visibility
+def _vis_struct(xp, faces, frames, center, half_extent, bias, R, dmap, bits, status):
+    a = L.VisArgs()
+    a.Nv = xp.shape[1]
+    a.F = faces.shape[0]
+    a.D = frames.shape[0]
+    a.R = int(R)
+    a.xp, a.faces, a.frames = _p(xp), _p(faces), _p(frames)
+    for k in range(3):
+        a.center[k] = float(center[k])
+    a.half_extent = float(half_extent)
+    a.bias = float(bias)
+    a.NL = 0 if dmap is None else dmap.shape[0]
+    a.dmap = _p(dmap)
+    a.bits = _p(bits)
+    a.status = _p(status)
+    return a
+
+
+def avatar_visibility(xp, faces, frames, center, half_extent, bias, R, dmap=None, bits=None, ws=None,
+                      status=None):
+    """(b) Depth-map visibility bits (Sec. 3.2).  xp [3,Nv] f32, faces [F,3]
+    i32, frames [D,9] f32.  Returns uint32-valued int32 words, light-ordered
+    [Nv, ceil(NL/32)] when dmap is given, else [Nv, D/32]."""
+    lib = L.load()
+    ctx = context()
+    Nv = xp.shape[1]
+    nout = dmap.shape[0] if dmap is not None else frames.shape[0]
+    if bits is None:
+        bits = torch.empty(Nv, (nout + 31) // 32, dtype=torch.int32, device=xp.device)
+    a = _vis_struct(xp, faces, frames, center, half_extent, bias, R, dmap, bits, status)
+    need = lib.avatar_visibility_workspace_size(C.byref(a))
+    if need == 0:
+        raise L.AvatarError(1, "avatar_visibility_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, xp.device)
+    L.check(lib.avatar_visibility(ctx, C.byref(a), _p(ws), ws.numel(), _stream()), "avatar_visibility")
+    return bits
+
+
+# ---------------------------------------------------------------- (c) shading
+def _shade_struct(sk, knn, bits, light, cam_center, color, radiance, cull, status):
+    a = L.ShadeArgs()
+    a.G = sk["xd"].shape[1]
+    a.K = knn.shape[0]
+    a.NL = light["L"].shape[0]
+    a.Nv = bits.shape[0]
+    a.xd, a.nd, a.ag, a.rg, a.pg, a.ubar = (_p(sk[k]) for k in ("xd", "nd", "ag", "rg", "pg", "ubar"))
+    a.knn, a.bits = _p(knn), _p(bits)
+    a.light_L, a.light_A, a.light_w = _p(light["L"]), _p(light["A"]), _p(light["w"])
+    for k in range(3):
+        a.cam_center[k] = float(cam_center[k])
+    a.color, a.radiance, a.cull, a.status = _p(color), _p(radiance), _p(cull), _p(status)
+    return a
+
+
+def avatar_shade(sk, knn, bits, light, cam_center, out=None, status=None):
+    """(c) Shading (Eq. 2, App. A).  light: dict L [NL,3], A [NL], w [NL,3]."""
+    lib = L.load()
+    ctx = context()
+    dev = sk["xd"].device
+    G = sk["xd"].shape[1]
+    if out is None:
+        out = dict(color=torch.empty(3, G, device=dev), radiance=torch.empty(3, G, device=dev),
+                   cull=torch.empty(G, dtype=torch.uint8, device=dev))
+    a = _shade_struct(sk, knn, bits, light, cam_center, out["color"], out["radiance"], out["cull"], status)
+    L.check(lib.avatar_shade(ctx, C.byref(a), _stream()), "avatar_shade")
+    return out
+
+
+def avatar_shade_backward(sk, knn, bits, light, cam_center, out, d_color):
+    lib = L.load()
+    ctx = context()
+    a = _shade_struct(sk, knn, bits, light, cam_center, out["color"], out["radiance"], out["cull"], None)
+    d_color = d_color.contiguous()
+    res = dict(xd=torch.empty_like(sk["xd"]), nd=torch.empty_like(sk["nd"]), ag=torch.empty_like(sk["ag"]),
+               rg=torch.empty_like(sk["rg"]), pg=torch.empty_like(sk["pg"]), ubar=torch.empty_like(sk["ubar"]),
+               L=torch.empty_like(light["L"]))
+    g = L.ShadeGrads()
+    g.d_color = _p(d_color)
+    g.d_xd, g.d_nd, g.d_ag, g.d_rg, g.d_pg, g.d_ubar, g.d_light_L = (
+        _p(res[k]) for k in ("xd", "nd", "ag", "rg", "pg", "ubar", "L"))
+    L.check(lib.avatar_shade_backward(ctx, C.byref(a), C.byref(g), _stream()), "avatar_shade_backward")
+    return res
+
+
+# ---------------------------------------------------------------- (d) splatting
+@dataclass
+class SplatBuffers:
+    mean2d: torch.Tensor
+    conic: torch.Tensor
+    depth: torch.Tensor
+    rect: torch.Tensor
+    tile_range: torch.Tensor
+    pair_gauss: torch.Tensor
+    num_pairs: torch.Tensor
+    image: torch.Tensor
+    T_final: torch.Tensor
+    n_last: torch.Tensor
+    ws: torch.Tensor
+    tile: int
+
+
+def num_tiles(width, height, tile):
+    return ((width + tile - 1) // tile) * ((height + tile - 1) // tile)
+
+
+def alloc_splat(G, cam, tile=16, pair_capacity=None, device="cuda"):
+    tile = tile or 16
+    W, H = int(cam.width), int(cam.height)
+    cap = int(pair_capacity or max(1 << 16, 32 * G))
+    e = lambda *s, dt=torch.float32: torch.empty(*s, dtype=dt, device=device)
+    b = SplatBuffers(mean2d=e(2, G), conic=e(3, G), depth=e(G), rect=e(4, G, dt=torch.int32),
+                     tile_range=e(num_tiles(W, H, tile), 2, dt=torch.int32), pair_gauss=e(cap, dt=torch.int32),
+                     num_pairs=e(1, dt=torch.int32), image=e(3, H, W), T_final=e(H, W),
+                     n_last=e(H, W, dt=torch.int32), ws=None, tile=tile)
+    a = _splat_struct(G, cam, None, None, None, None, None, b, None)
+    need = L.load().avatar_splat_workspace_size(C.byref(a))
+    if need == 0:
+        raise L.AvatarError(1, "avatar_splat_workspace_size")
+    b.ws = workspace(need, device)
+    return b
+
+
+def _splat_struct(G, cam, xd, cov, opacity, color, cull, b: SplatBuffers, status):
+    a = L.SplatArgs()
+    a.G = G
+    a.cam = camera_struct(cam)
+    a.tile = b.tile
+    a.xd, a.cov, a.opacity, a.color, a.cull = _p(xd), _p(cov), _p(opacity), _p(color), _p(cull)
+    a.mean2d, a.conic, a.depth, a.rect = _p(b.mean2d), _p(b.conic), _p(b.depth), _p(b.rect)
+    a.tile_range, a.pair_gauss, a.num_pairs = _p(b.tile_range), _p(b.pair_gauss), _p(b.num_pairs)
+    a.pair_capacity = b.pair_gauss.numel()
+    a.image, a.T_final, a.n_last = _p(b.image), _p(b.T_final), _p(b.n_last)
+    a.status = _p(status)
+    return a
+
+
+def _splat_call(name, xd, cov, opacity, color, cull, cam, b, status):
+    lib = L.load()
+    ctx = context()
+    G = xd.shape[1]
+    a = _splat_struct(G, cam, xd, cov, opacity, color, cull, b, status)
+    L.check(getattr(lib, name)(ctx, C.byref(a), _p(b.ws), b.ws.numel(), _stream()), name)
+    return b
+
+
+def avatar_splat_project(xd, cov, opacity, color, cull, cam, b, status=None):
+    return _splat_call("avatar_splat_project", xd, cov, opacity, color, cull, cam, b, status)
+
+
+def avatar_splat_bin(xd, cov, opacity, color, cull, cam, b, status=None):
+    return _splat_call("avatar_splat_bin", xd, cov, opacity, color, cull, cam, b, status)
+
+
+def avatar_splat_blend(xd, cov, opacity, color, cull, cam, b, status=None):
+    return _splat_call("avatar_splat_blend", xd, cov, opacity, color, cull, cam, b, status)
+
+
+def avatar_splat(xd, cov, opacity, color, cull, cam, b=None, tile=16, pair_capacity=None, status=None):
+    """(d) Splatting (3DGS rasteriser of Sec. 3.1).  Returns SplatBuffers."""
+    if b is None:
+        b = alloc_splat(xd.shape[1], cam, tile, pair_capacity, xd.device)
+    return _splat_call("avatar_splat", xd, cov, opacity, color, cull, cam, b, status)
+
+
+def avatar_splat_backward(xd, cov, opacity, color, cull, cam, b, d_image):
+    lib = L.load()
+    ctx = context()
+    G = xd.shape[1]
+    a = _splat_struct(G, cam, xd, cov, opacity, color, cull, b, None)
+    d_image = d_image.contiguous()
+    res = dict(xd=torch.empty_like(xd), cov=torch.empty_like(cov), opacity=torch.empty_like(opacity),
+               color=torch.empty_like(color))
+    g = L.SplatGrads()
+    g.d_image = _p(d_image)
+    g.d_xd, g.d_cov, g.d_opacity, g.d_color = _p(res["xd"]), _p(res["cov"]), _p(res["opacity"]), _p(res["color"])
+    L.check(lib.avatar_splat_backward(ctx, C.byref(a), C.byref(g), _p(b.ws), b.ws.numel(), _stream()),
+            "avatar_splat_backward")
+    return res
+
+
+# ---------------------------------------------------------------- loss
+def avatar_l1_loss(img, target, want_grad=True):
+    lib = L.load()
+    ctx = context()
+    img = img.contiguous()
+    target = target.contiguous()
+    loss = torch.empty(1, dtype=torch.float32, device=img.device)
+    d_img = torch.empty_like(img) if want_grad else None
+    L.check(lib.avatar_l1_loss(ctx, img.numel(), _p(img), _p(target), _p(loss), _p(d_img), _stream()),
+            "avatar_l1_loss")
+    return loss, d_img

@@ -1,0 +1,86 @@
+// Shared device helpers of the sm_103a relit-avatar library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "avatar.h"
+
+struct avatar_ctx {
+    int device;
+    int sm_count;
+    int max_smem_optin;
+    int cluster_ok;
+};
+
+#define AV_CHECK_LAUNCH()                                    \
+    do {                                                     \
+        if (cudaPeekAtLastError() != cudaSuccess) {          \
+            (void)cudaGetLastError();                        \
+            return AVATAR_ERR_CUDA;                          \
+        }                                                    \
+    } while (0)
+
+#define AV_TRY(expr)                          \
+    do {                                      \
+        int _rc = (expr);                     \
+        if (_rc != AVATAR_OK) return _rc;     \
+    } while (0)
+
+static inline size_t av_align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Carves aligned sub-buffers out of a caller workspace.
+struct WsCarver {
+    char *base;
+    size_t off;
+    size_t cap;
+    __host__ WsCarver(void *p, size_t c) : base((char *)p), off(0), cap(c) {}
+    template <class T>
+    __host__ T *take(size_t n) {
+        size_t bytes = av_align256(n * sizeof(T));
+        T *r = base ? (T *)(base + off) : nullptr;
+        off += bytes;
+        return r;
+    }
+    __host__ bool ok() const { return base != nullptr && off <= cap; }
+};
+
+__device__ __forceinline__ void av_report(int32_t *status, int code)
+{
+    if (status) atomicCAS(status, 0, code);
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int warp_sum_i(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Loads through the read-only path with an L1 no-allocate hint for streamed data.
+__device__ __forceinline__ float4 ldg_stream4(const float4 *p)
+{
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+constexpr float AV_PI = 3.14159265358979323846f;

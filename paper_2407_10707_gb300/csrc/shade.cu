@@ -1,0 +1,407 @@
+// (c) Shading of every Gaussian with the discrete rendering equation -
+// Eq. 2, BRDF of App. A, back-face cull and gamma of Sec. 3.1.
+//
+// Work split: one warp per Gaussian, lanes over the lights (light k is
+// handled by lane k % 32 in chunk k / 32).  The light table (w_k, L_k A_k)
+// is staged once per block in shared memory; the visibility words of the K
+// neighbours for a 32-light chunk are warp-uniform loads, and each lane
+// extracts its own bit.  Per-Gaussian sums are reduced with shuffles.  The
+// backward pass reuses the same split: per-light gradients accumulate in
+// shared memory and are flushed once per block.
+#include "common.cuh"
+
+namespace {
+
+constexpr int SHADE_THREADS = 256;
+constexpr float FRES_C1 = -5.55473f;
+constexpr float FRES_C0 = -6.98316f;
+constexpr float INV_GAMMA = 1.0f / 2.2f;
+
+struct GaussIn {
+    float x[3], n[3], a[3], r, p;
+    float ub[8];
+    int nb[8];
+};
+
+__device__ __forceinline__ void load_gauss(const avatar_shade_args &s, int g, GaussIn &q)
+{
+    const int G = s.G;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        q.x[i] = __ldg(s.xd + (size_t)i * G + g);
+        q.n[i] = __ldg(s.nd + (size_t)i * G + g);
+        q.a[i] = __ldg(s.ag + (size_t)i * G + g);
+    }
+    q.r = __ldg(s.rg + g);
+    q.p = __ldg(s.pg + g);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if (j < s.K) {
+            q.ub[j] = __ldg(s.ubar + (size_t)j * G + g);
+            q.nb[j] = __ldg(s.knn + (size_t)j * G + g);
+        } else {
+            q.ub[j] = 0.f;
+            q.nb[j] = -1;
+        }
+    }
+}
+
+// Exact FP32 back-face decision (identical operation order to the header).
+__device__ __forceinline__ bool is_culled(const float *x, const float *n, const float *C)
+{
+    float d0 = __fsub_rn(C[0], x[0]), d1 = __fsub_rn(C[1], x[1]), d2 = __fsub_rn(C[2], x[2]);
+    float s = __fmaf_rn(n[2], d2, __fmaf_rn(n[1], d1, __fmul_rn(n[0], d0)));
+    return !(s > 0.0f);
+}
+
+struct Frame {
+    float wo[3];
+    float co_raw, co;
+    float a2, kk, Go;
+    float inv_len;
+};
+
+__device__ __forceinline__ Frame view_frame(const GaussIn &q, const float *C)
+{
+    Frame f;
+    float v0 = C[0] - q.x[0], v1 = C[1] - q.x[1], v2 = C[2] - q.x[2];
+    float il = rsqrtf(v0 * v0 + v1 * v1 + v2 * v2);
+    f.inv_len = il;
+    f.wo[0] = v0 * il;
+    f.wo[1] = v1 * il;
+    f.wo[2] = v2 * il;
+    f.co_raw = q.n[0] * f.wo[0] + q.n[1] * f.wo[1] + q.n[2] * f.wo[2];
+    f.co = fmaxf(f.co_raw, 0.f);
+    float alpha = q.r * q.r;
+    f.a2 = alpha * alpha;
+    f.kk = (q.r + 1.f) * (q.r + 1.f) * 0.125f;
+    f.Go = f.co * (1.f - f.kk) + f.kk;
+    return f;
+}
+
+// Visibility bit of neighbour j for this lane's light in the current chunk.
+__device__ __forceinline__ float lane_vis(const unsigned *words, const GaussIn &q, int K, int lane)
+{
+    float vis = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        if (j < K && ((words[j] >> lane) & 1u)) vis += q.ub[j];
+    return vis;
+}
+
+__global__ void __launch_bounds__(SHADE_THREADS)
+shade_kernel(avatar_shade_args s)
+{
+    extern __shared__ float4 lsm[];  // [NL] (w, 0) then [NL] (L*A, 0)
+    const int NL = s.NL, G = s.G, K = s.K;
+    float4 *lw = lsm, *lb = lsm + NL;
+    for (int k = threadIdx.x; k < NL; k += blockDim.x) {
+        float A = __ldg(s.light_A + k);
+        lw[k] = make_float4(__ldg(s.light_w + 3 * k), __ldg(s.light_w + 3 * k + 1), __ldg(s.light_w + 3 * k + 2), 0.f);
+        lb[k] = make_float4(__ldg(s.light_L + 3 * k) * A, __ldg(s.light_L + 3 * k + 1) * A,
+                            __ldg(s.light_L + 3 * k + 2) * A, 0.f);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int OW = (NL + 31) / 32;
+    const int warps_total = gridDim.x * (blockDim.x >> 5);
+    const float C[3] = {s.cam_center[0], s.cam_center[1], s.cam_center[2]};
+    for (int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < G; g += warps_total) {
+        GaussIn q;
+        load_gauss(s, g, q);
+        bool bad = false;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < K && (unsigned)q.nb[j] >= (unsigned)s.Nv) bad = true;
+        if (bad && lane == 0) av_report(s.status, AVATAR_ERR_INDEX);
+        if (is_culled(q.x, q.n, C) || bad) {
+            if (lane == 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    s.color[(size_t)c * G + g] = 0.f;
+                    if (s.radiance) s.radiance[(size_t)c * G + g] = 0.f;
+                }
+                if (s.cull) s.cull[g] = 1;
+            }
+            continue;
+        }
+        Frame f = view_frame(q, C);
+        const float spec_scale = f.a2 / (4.f * AV_PI * f.Go);
+        float E0 = 0.f, E1 = 0.f, E2 = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f;
+        for (int ch = 0; ch < OW; ++ch) {
+            unsigned words[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) words[j] = (j < K) ? __ldg(s.bits + (size_t)q.nb[j] * OW + ch) : 0u;
+            const int k = ch * 32 + lane;
+            if (k >= NL) continue;
+            float4 w = lw[k];
+            float ci = q.n[0] * w.x + q.n[1] * w.y + q.n[2] * w.z;
+            if (!(ci > 0.f)) continue;
+            float vis = lane_vis(words, q, K, lane);
+            if (vis == 0.f) continue;
+            float4 B = lb[k];
+            float fw = vis * ci;
+            E0 = fmaf(B.x, fw, E0);
+            E1 = fmaf(B.y, fw, E1);
+            E2 = fmaf(B.z, fw, E2);
+            float dwo = w.x * f.wo[0] + w.y * f.wo[1] + w.z * f.wo[2];
+            float len2 = 2.f + 2.f * dwo;
+            if (len2 > 0.f) {
+                float rinv = rsqrtf(len2);
+                float nh = (ci + f.co_raw) * rinv;
+                float voh = (1.f + dwo) * rinv;
+                float den = fmaf(nh * nh, f.a2 - 1.f, 1.f);
+                float Fr = fmaf(0.96f, exp2f(fmaf(FRES_C1, voh, FRES_C0) * voh), 0.04f);
+                float Gi = fmaf(ci, 1.f - f.kk, f.kk);
+                float fs = spec_scale * Fr / (den * den * Gi);
+                float sw = fw * fs;
+                S0 = fmaf(B.x, sw, S0);
+                S1 = fmaf(B.y, sw, S1);
+                S2 = fmaf(B.z, sw, S2);
+            }
+        }
+        E0 = warp_sum(E0);
+        E1 = warp_sum(E1);
+        E2 = warp_sum(E2);
+        S0 = warp_sum(S0);
+        S1 = warp_sum(S1);
+        S2 = warp_sum(S2);
+        if (lane < 3) {
+            float E = lane == 0 ? E0 : (lane == 1 ? E1 : E2);
+            float S = lane == 0 ? S0 : (lane == 1 ? S1 : S2);
+            float Lo = q.a[lane] * (1.f / AV_PI) * E + q.p * S;
+            float col = exp2f(log2f(fmaxf(Lo, 1e-6f)) * INV_GAMMA);
+            s.color[(size_t)lane * G + g] = col;
+            if (s.radiance) s.radiance[(size_t)lane * G + g] = Lo;
+        }
+        if (lane == 0 && s.cull) s.cull[g] = 0;
+    }
+}
+
+// ---------------------------------------------------------------- backward
+__global__ void __launch_bounds__(SHADE_THREADS)
+shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr)
+{
+    extern __shared__ float4 lsm[];  // [NL] (w,A) ; [NL] (L*A) ; [NL] dB accum (3 floats)
+    const int NL = s.NL, G = s.G, K = s.K;
+    float4 *lw = lsm, *lb = lsm + NL;
+    float *dB = reinterpret_cast<float *>(lsm + 2 * NL);
+    for (int k = threadIdx.x; k < NL; k += blockDim.x) {
+        float A = __ldg(s.light_A + k);
+        lw[k] = make_float4(__ldg(s.light_w + 3 * k), __ldg(s.light_w + 3 * k + 1), __ldg(s.light_w + 3 * k + 2), A);
+        lb[k] = make_float4(__ldg(s.light_L + 3 * k) * A, __ldg(s.light_L + 3 * k + 1) * A,
+                            __ldg(s.light_L + 3 * k + 2) * A, 0.f);
+        dB[3 * k] = dB[3 * k + 1] = dB[3 * k + 2] = 0.f;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int OW = (NL + 31) / 32;
+    const int warps_total = gridDim.x * (blockDim.x >> 5);
+    const float C[3] = {s.cam_center[0], s.cam_center[1], s.cam_center[2]};
+    for (int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < G; g += warps_total) {
+        GaussIn q;
+        load_gauss(s, g, q);
+        bool bad = false;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < K && (unsigned)q.nb[j] >= (unsigned)s.Nv) bad = true;
+        float dLo[3];
+        bool culled = is_culled(q.x, q.n, C) || bad;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float Lo = __ldg(s.radiance + (size_t)c * G + g);
+            float dc = __ldg(gr.d_color + (size_t)c * G + g);
+            dLo[c] = (Lo > 1e-6f) ? dc * INV_GAMMA * exp2f(log2f(Lo) * (INV_GAMMA - 1.f)) : 0.f;
+        }
+        if (culled || (dLo[0] == 0.f && dLo[1] == 0.f && dLo[2] == 0.f)) {
+            if (lane < 3) {
+                gr.d_xd[(size_t)lane * G + g] = 0.f;
+                gr.d_nd[(size_t)lane * G + g] = 0.f;
+                gr.d_ag[(size_t)lane * G + g] = 0.f;
+            }
+            if (lane == 0) {
+                gr.d_rg[g] = 0.f;
+                gr.d_pg[g] = 0.f;
+            }
+            if (lane < K) gr.d_ubar[(size_t)lane * G + g] = 0.f;
+            continue;
+        }
+        Frame f = view_frame(q, C);
+        const float spec_scale = f.a2 / (4.f * AV_PI * f.Go);
+        const float ia0 = q.a[0] * (1.f / AV_PI), ia1 = q.a[1] * (1.f / AV_PI), ia2 = q.a[2] * (1.f / AV_PI);
+        float E0 = 0.f, E1 = 0.f, E2 = 0.f;
+        float dnv0 = 0.f, dnv1 = 0.f, dnv2 = 0.f, dwv0 = 0.f, dwv1 = 0.f, dwv2 = 0.f;
+        float dco = 0.f, da2 = 0.f, dkk = 0.f, dp = 0.f;
+        float dub[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) dub[j] = 0.f;
+        for (int ch = 0; ch < OW; ++ch) {
+            unsigned words[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) words[j] = (j < K) ? __ldg(s.bits + (size_t)q.nb[j] * OW + ch) : 0u;
+            const int k = ch * 32 + lane;
+            if (k >= NL) continue;
+            float4 w = lw[k];
+            float ci = q.n[0] * w.x + q.n[1] * w.y + q.n[2] * w.z;
+            if (!(ci > 0.f)) continue;
+            float vis = lane_vis(words, q, K, lane);
+            if (vis == 0.f) continue;
+            float4 B = lb[k];
+            float Q = dLo[0] * B.x + dLo[1] * B.y + dLo[2] * B.z;
+            float Qa = ia0 * dLo[0] * B.x + ia1 * dLo[1] * B.y + ia2 * dLo[2] * B.z;
+            float fw = vis * ci;
+            E0 = fmaf(B.x, fw, E0);
+            E1 = fmaf(B.y, fw, E1);
+            E2 = fmaf(B.z, fw, E2);
+            float fs = 0.f, dci = 0.f;
+            float dwo = w.x * f.wo[0] + w.y * f.wo[1] + w.z * f.wo[2];
+            float len2 = 2.f + 2.f * dwo;
+            if (len2 > 0.f) {
+                float rinv = rsqrtf(len2);
+                float nh = (ci + f.co_raw) * rinv;
+                float voh = (1.f + dwo) * rinv;
+                float den = fmaf(nh * nh, f.a2 - 1.f, 1.f);
+                float ex = exp2f(fmaf(FRES_C1, voh, FRES_C0) * voh);
+                float Fr = fmaf(0.96f, ex, 0.04f);
+                float Gi = fmaf(ci, 1.f - f.kk, f.kk);
+                float base = spec_scale / (den * den * Gi);  // fs / Fr
+                fs = base * Fr;
+                float dfs = fw * q.p * Q;
+                dp += fw * fs * Q;
+                // fs = a2 Fr / (4 pi den^2 Gi Go)
+                float dFr = dfs * base;
+                float dden = -2.f * dfs * fs / den;
+                float dGi = -dfs * fs / Gi;
+                float dGo = -dfs * fs / f.Go;
+                da2 += dfs * fs / f.a2 + dden * nh * nh;
+                float dnh = dden * 2.f * nh * (f.a2 - 1.f);
+                float dvoh = dFr * 0.96f * ex * 0.69314718056f * (2.f * FRES_C1 * voh + FRES_C0);
+                dci += dGi * (1.f - f.kk);
+                dkk += dGi * (1.f - ci) + dGo * (1.f - f.co);
+                if (f.co_raw > 0.f) dco += dGo * (1.f - f.kk);
+                dci += dnh * rinv;
+                dco += dnh * rinv;
+                float drinv = dnh * (ci + f.co_raw) + dvoh * (1.f + dwo);
+                float ddwo = dvoh * rinv - drinv * rinv * rinv * rinv;
+                dwv0 = fmaf(ddwo, w.x, dwv0);
+                dwv1 = fmaf(ddwo, w.y, dwv1);
+                dwv2 = fmaf(ddwo, w.z, dwv2);
+            }
+            float term = Qa + q.p * fs * Q;  // sum_c dLo_c B_c (a_c/pi + p fs)
+            dci += vis * term;
+            float dvis = ci * term;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j < K && ((words[j] >> lane) & 1u)) dub[j] += dvis;
+            dnv0 = fmaf(dci, w.x, dnv0);
+            dnv1 = fmaf(dci, w.y, dnv1);
+            dnv2 = fmaf(dci, w.z, dnv2);
+            // dL/dB_kc = dLo_c vis ci (a_c/pi + p fs)
+            atomicAdd(dB + 3 * k, dLo[0] * fw * (ia0 + q.p * fs));
+            atomicAdd(dB + 3 * k + 1, dLo[1] * fw * (ia1 + q.p * fs));
+            atomicAdd(dB + 3 * k + 2, dLo[2] * fw * (ia2 + q.p * fs));
+        }
+        E0 = warp_sum(E0);
+        E1 = warp_sum(E1);
+        E2 = warp_sum(E2);
+        dnv0 = warp_sum(dnv0);
+        dnv1 = warp_sum(dnv1);
+        dnv2 = warp_sum(dnv2);
+        dwv0 = warp_sum(dwv0);
+        dwv1 = warp_sum(dwv1);
+        dwv2 = warp_sum(dwv2);
+        dco = warp_sum(dco);
+        da2 = warp_sum(da2);
+        dkk = warp_sum(dkk);
+        dp = warp_sum(dp);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < K) dub[j] = warp_sum(dub[j]);
+        if (lane == 0) {
+            float dn[3] = {dnv0 + dco * f.wo[0], dnv1 + dco * f.wo[1], dnv2 + dco * f.wo[2]};
+            float dw[3] = {dwv0 + dco * q.n[0], dwv1 + dco * q.n[1], dwv2 + dco * q.n[2]};
+            float dd = dw[0] * f.wo[0] + dw[1] * f.wo[1] + dw[2] * f.wo[2];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                gr.d_nd[(size_t)c * G + g] = dn[c];
+                gr.d_xd[(size_t)c * G + g] = -(dw[c] - dd * f.wo[c]) * f.inv_len;
+            }
+            gr.d_ag[g] = dLo[0] * E0 * (1.f / AV_PI);
+            gr.d_ag[G + g] = dLo[1] * E1 * (1.f / AV_PI);
+            gr.d_ag[2 * G + g] = dLo[2] * E2 * (1.f / AV_PI);
+            float alpha = q.r * q.r;
+            gr.d_rg[g] = da2 * 4.f * alpha * q.r + dkk * (q.r + 1.f) * 0.25f;
+            gr.d_pg[g] = dp;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j < K) gr.d_ubar[(size_t)j * G + g] = dub[j];
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < NL; k += blockDim.x) {
+        float A = lw[k].w;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float v = dB[3 * k + c];
+            if (v != 0.f) atomicAdd(gr.d_light_L + 3 * k + c, v * A);
+        }
+    }
+}
+
+int check_shade(const avatar_shade_args *a)
+{
+    if (!a || a->G < 0 || a->K < 1 || a->K > 8 || a->NL < 1 || a->NL > 4096 || a->Nv < 1)
+        return AVATAR_ERR_INVALID_ARG;
+    if (a->G > 0 && (!a->xd || !a->nd || !a->ag || !a->rg || !a->pg || !a->ubar || !a->knn || !a->bits ||
+                     !a->color))
+        return AVATAR_ERR_INVALID_ARG;
+    if (!a->light_L || !a->light_A || !a->light_w) return AVATAR_ERR_INVALID_ARG;
+    return AVATAR_OK;
+}
+
+int shade_grid(const avatar_ctx *ctx, int G)
+{
+    long warps = G;
+    long blocks = (warps + SHADE_THREADS / 32 - 1) / (SHADE_THREADS / 32);
+    long cap = (long)ctx->sm_count * 8;
+    if (blocks > cap) blocks = cap;
+    return blocks < 1 ? 1 : (int)blocks;
+}
+
+}  // namespace
+
+extern "C" int avatar_shade(avatar_ctx *ctx, const avatar_shade_args *a, avatar_stream_t stream)
+{
+    if (!ctx) return AVATAR_ERR_INVALID_ARG;
+    AV_TRY(check_shade(a));
+    if (a->G == 0) return AVATAR_OK;
+    size_t smem = (size_t)2 * a->NL * sizeof(float4);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(shade_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return AVATAR_ERR_CUDA;
+    shade_kernel<<<shade_grid(ctx, a->G), SHADE_THREADS, smem, (cudaStream_t)stream>>>(*a);
+    AV_CHECK_LAUNCH();
+    return AVATAR_OK;
+}
+
+extern "C" int avatar_shade_backward(avatar_ctx *ctx, const avatar_shade_args *a, const avatar_shade_grads *g,
+                                     avatar_stream_t stream)
+{
+    if (!ctx || !g) return AVATAR_ERR_INVALID_ARG;
+    AV_TRY(check_shade(a));
+    if (!a->radiance || !g->d_color || !g->d_xd || !g->d_nd || !g->d_ag || !g->d_rg || !g->d_pg || !g->d_ubar ||
+        !g->d_light_L)
+        return AVATAR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(g->d_light_L, 0, (size_t)a->NL * 3 * sizeof(float), st) != cudaSuccess)
+        return AVATAR_ERR_CUDA;
+    if (a->G == 0) return AVATAR_OK;
+    size_t smem = (size_t)2 * a->NL * sizeof(float4) + (size_t)3 * a->NL * sizeof(float);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(shade_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+        return AVATAR_ERR_CUDA;
+    shade_backward_kernel<<<shade_grid(ctx, a->G), SHADE_THREADS, smem, st>>>(*a, *g);
+    AV_CHECK_LAUNCH();
+    return AVATAR_OK;
+}

@@ -1,0 +1,907 @@
+// (d) Tile-binned, depth-sorted, front-to-back Gaussian splatting - the 3DGS
+// rasteriser the paper renders with (Sec. 3.1), black background (Sec. 4.2).
+//
+// Pipeline (all on the device, no host synchronisation; the pair count is
+// data dependent and only ever read on the device):
+//   project   one thread per Gaussian: EWA projection, conic, tile-independent
+//             pixel rect, pair count, depth key, packed blend records.
+//   depth sort  stable LSD radix sort of (depth bits, index) over G keys.
+//   scan      exclusive scan of pair counts in depth order -> pair offsets.
+//   emit      each Gaussian writes (tile id, index) for its tiles at its
+//             offset; emission follows depth order.
+//   tile sort stable LSD radix sort of the pairs on the tile id only; with
+//             the depth-ordered emission this yields (tile, depth, index).
+//   ranges    begin/end of every tile's run.
+//   blend     one CTA per tile, one thread per pixel, Gaussians staged in
+//             shared memory one CTA-width batch at a time; the CTA leaves
+//             as soon as every pixel is saturated.
+// Backward: reverse traversal from the per-pixel checkpoint (T_final,
+// n_last) with warp-reduced atomics, then a per-Gaussian projection adjoint.
+#include "common.cuh"
+
+namespace {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RADIX = 256;
+constexpr float NEAR_Z = 0.2f;
+constexpr float ALPHA_MIN = 1.0f / 255.0f;
+constexpr float T_MIN = 1e-4f;
+
+struct CamDev {
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    int W, H;
+};
+
+CamDev to_dev(const avatar_camera &c)
+{
+    CamDev d;
+    d.fx = c.fx;
+    d.fy = c.fy;
+    d.cx = c.cx;
+    d.cy = c.cy;
+    for (int i = 0; i < 9; ++i) d.R[i] = c.R[i];
+    for (int i = 0; i < 3; ++i) d.t[i] = c.t[i];
+    d.W = c.width;
+    d.H = c.height;
+    return d;
+}
+
+struct SplatWs {
+    uint32_t *dkey_a, *dkey_b;   // [G] depth keys
+    int32_t *dval_a, *dval_b;    // [G] Gaussian indices
+    int32_t *npairs;             // [G]
+    int32_t *offsets;            // [G]
+    uint32_t *pkey_a, *pkey_b;   // [cap] tile keys
+    int32_t *pval_b;             // [cap] ping-pong partner of pair_gauss
+    float4 *rec0, *rec1;         // [G]
+    float *rec2;                 // [G]
+    int32_t *hist;               // [RADIX][NB]
+    int32_t *totals;             // [RADIX]
+    int32_t *block_sums;         // [NB]
+    int32_t *count_g;            // [1] = G on the device
+    float *d_mean2d;             // [2][G]
+    float *d_conic;              // [3][G]
+    int NB;
+};
+
+// Fixed radix grid: two blocks per SM of a 152-SM GB300.
+constexpr int RADIX_BLOCKS = 304;
+int radix_blocks(const avatar_ctx *) { return RADIX_BLOCKS; }
+
+size_t splat_ws_layout(const avatar_splat_args *a, int NB, void *base, size_t cap, SplatWs *out)
+{
+    WsCarver c(base, cap);
+    SplatWs w;
+    size_t G = (size_t)(a->G > 0 ? a->G : 1);
+    size_t P = (size_t)(a->pair_capacity > 0 ? a->pair_capacity : 1);
+    w.dkey_a = c.take<uint32_t>(G);
+    w.dkey_b = c.take<uint32_t>(G);
+    w.dval_a = c.take<int32_t>(G);
+    w.dval_b = c.take<int32_t>(G);
+    w.npairs = c.take<int32_t>(G);
+    w.offsets = c.take<int32_t>(G);
+    w.pkey_a = c.take<uint32_t>(P);
+    w.pkey_b = c.take<uint32_t>(P);
+    w.pval_b = c.take<int32_t>(P);
+    w.rec0 = c.take<float4>(G);
+    w.rec1 = c.take<float4>(G);
+    w.rec2 = c.take<float>(G);
+    w.hist = c.take<int32_t>((size_t)RADIX * NB);
+    w.totals = c.take<int32_t>(RADIX);
+    w.block_sums = c.take<int32_t>((size_t)NB);
+    w.count_g = c.take<int32_t>(1);
+    w.d_mean2d = c.take<float>(2 * G);
+    w.d_conic = c.take<float>(3 * G);
+    w.NB = NB;
+    if (out) *out = w;
+    return c.off;
+}
+
+// ---------------------------------------------------------------- project
+__global__ void __launch_bounds__(256)
+project_kernel(avatar_splat_args a, CamDev cam)
+{
+    const int G = a.G;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        float x = a.xd[g], y = a.xd[G + g], z = a.xd[2 * G + g];
+        float o = a.opacity[g];
+        float px = cam.R[0] * x + cam.R[1] * y + cam.R[2] * z + cam.t[0];
+        float py = cam.R[3] * x + cam.R[4] * y + cam.R[5] * z + cam.t[1];
+        float pz = cam.R[6] * x + cam.R[7] * y + cam.R[8] * z + cam.t[2];
+        bool ok = !(a.cull && a.cull[g]) && pz > NEAR_Z && o > ALPHA_MIN;
+        float u = 0.f, v = 0.f, ca = 0.f, cb = 0.f, cc = 0.f;
+        int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
+        if (ok) {
+            float iz = 1.0f / pz;
+            u = cam.fx * px * iz + cam.cx;
+            v = cam.fy * py * iz + cam.cy;
+            float j00 = cam.fx * iz, j02 = -cam.fx * px * iz * iz;
+            float j11 = cam.fy * iz, j12 = -cam.fy * py * iz * iz;
+            float T0[3], T1[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                T0[k] = j00 * cam.R[k] + j02 * cam.R[6 + k];
+                T1[k] = j11 * cam.R[3 + k] + j12 * cam.R[6 + k];
+            }
+            float c0 = a.cov[g], c1 = a.cov[G + g], c2 = a.cov[2 * G + g];
+            float c3 = a.cov[3 * G + g], c4 = a.cov[4 * G + g], c5 = a.cov[5 * G + g];
+            float S0[3] = {c0 * T0[0] + c1 * T0[1] + c2 * T0[2], c1 * T0[0] + c3 * T0[1] + c4 * T0[2],
+                           c2 * T0[0] + c4 * T0[1] + c5 * T0[2]};
+            float S1[3] = {c0 * T1[0] + c1 * T1[1] + c2 * T1[2], c1 * T1[0] + c3 * T1[1] + c4 * T1[2],
+                           c2 * T1[0] + c4 * T1[1] + c5 * T1[2]};
+            float s00 = T0[0] * S0[0] + T0[1] * S0[1] + T0[2] * S0[2] + 0.3f;
+            float s01 = T1[0] * S0[0] + T1[1] * S0[1] + T1[2] * S0[2];
+            float s11 = T1[0] * S1[0] + T1[1] * S1[1] + T1[2] * S1[2] + 0.3f;
+            float det = s00 * s11 - s01 * s01;
+            if (det > 0.f) {
+                float id = 1.0f / det;
+                ca = s11 * id;
+                cb = -s01 * id;
+                cc = s00 * id;
+                float r2 = 2.0f * logf(255.0f * o);
+                float ex = sqrtf(r2 * s00) + 1.0f, ey = sqrtf(r2 * s11) + 1.0f;
+                float fx0 = ceilf(u - ex - 0.5f), fx1 = floorf(u + ex - 0.5f);
+                float fy0 = ceilf(v - ey - 0.5f), fy1 = floorf(v + ey - 0.5f);
+                fx0 = fmaxf(fx0, 0.f);
+                fy0 = fmaxf(fy0, 0.f);
+                fx1 = fminf(fx1, (float)(cam.W - 1));
+                fy1 = fminf(fy1, (float)(cam.H - 1));
+                if (fx0 <= fx1 && fy0 <= fy1) {
+                    x0 = (int)fx0;
+                    x1 = (int)fx1;
+                    y0 = (int)fy0;
+                    y1 = (int)fy1;
+                }
+            } else {
+                ok = false;
+            }
+        }
+        if (!ok) {
+            u = v = ca = cb = cc = 0.f;
+            x0 = y0 = 0;
+            x1 = y1 = -1;
+        }
+        a.mean2d[g] = u;
+        a.mean2d[G + g] = v;
+        a.conic[g] = ca;
+        a.conic[G + g] = cb;
+        a.conic[2 * G + g] = cc;
+        a.depth[g] = pz;
+        a.rect[g] = x0;
+        a.rect[G + g] = y0;
+        a.rect[2 * G + g] = x1;
+        a.rect[3 * G + g] = y1;
+    }
+}
+
+// Per-Gaussian pair count, depth key and packed blend record, from the
+// caller-visible projection buffers (rect, depth, mean2d, conic) and the
+// opacity and colour.
+__global__ void __launch_bounds__(256)
+bin_keys_kernel(avatar_splat_args a, int TS, SplatWs w)
+{
+    const int G = a.G;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        int x0 = a.rect[g], y0 = a.rect[G + g], x1 = a.rect[2 * G + g], y1 = a.rect[3 * G + g];
+        int n = 0;
+        if (x0 <= x1 && y0 <= y1 && x0 >= 0 && y0 >= 0 && x1 < a.cam.width && y1 < a.cam.height)
+            n = (x1 / TS - x0 / TS + 1) * (y1 / TS - y0 / TS + 1);
+        w.npairs[g] = n;
+        w.dkey_a[g] = n > 0 ? __float_as_uint(a.depth[g]) : 0xffffffffu;
+        w.dval_a[g] = g;
+        w.rec0[g] = make_float4(a.mean2d[g], a.mean2d[G + g], a.conic[g], a.conic[G + g]);
+        w.rec1[g] = make_float4(a.conic[2 * G + g], a.opacity[g], a.color[g], a.color[G + g]);
+        w.rec2[g] = a.color[2 * G + g];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *w.count_g = G;
+}
+
+// ---------------------------------------------------------------- radix sort
+__device__ __forceinline__ int chunk_range(int n, int NB, int b, int &begin)
+{
+    int chunk = (n + NB - 1) / NB;
+    begin = b * chunk;
+    int end = begin + chunk;
+    if (end > n) end = n;
+    if (begin > n) begin = n;
+    return end;
+}
+
+__global__ void __launch_bounds__(RS_THREADS)
+radix_hist_kernel(const uint32_t *__restrict__ keys, const int32_t *__restrict__ n_ptr, int cap, int shift,
+                  int NB, int32_t *__restrict__ hist)
+{
+    __shared__ int cnt[RADIX];
+    for (int i = threadIdx.x; i < RADIX; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    int n = min(*n_ptr, cap);
+    int begin;
+    int end = chunk_range(n, NB, blockIdx.x, begin);
+    for (int i = begin + threadIdx.x; i < end; i += blockDim.x) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1);
+    __syncthreads();
+    for (int d = threadIdx.x; d < RADIX; d += blockDim.x) hist[d * NB + blockIdx.x] = cnt[d];
+}
+
+// Exclusive block-wide scan of one value per thread (blockDim <= 1024).
+__device__ __forceinline__ int block_exclusive_scan(int v, int &total)
+{
+    __shared__ int wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    if (warp == 0) {
+        int s = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        wsum[lane] = s;  // inclusive warp prefix
+    }
+    __syncthreads();
+    int warp_base = warp > 0 ? wsum[warp - 1] : 0;
+    total = wsum[nw - 1];
+    __syncthreads();
+    return warp_base + x - v;
+}
+
+// One block per digit: exclusive scan over the NB per-block counts.
+__global__ void __launch_bounds__(1024)
+radix_scan_kernel(int32_t *__restrict__ hist, int NB, int32_t *__restrict__ totals)
+{
+    const int d = blockIdx.x;
+    int running = 0;
+    for (int base = 0; base < NB; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        int v = i < NB ? hist[d * NB + i] : 0;
+        int tot;
+        int ex = block_exclusive_scan(v, tot);
+        if (i < NB) hist[d * NB + i] = running + ex;
+        running += tot;
+    }
+    if (threadIdx.x == 0) totals[d] = running;
+}
+
+__global__ void __launch_bounds__(RS_THREADS)
+radix_scatter_kernel(const uint32_t *__restrict__ kin, const int32_t *__restrict__ vin, uint32_t *__restrict__ kout,
+                     int32_t *__restrict__ vout, const int32_t *__restrict__ n_ptr, int cap, int shift, int NB,
+                     const int32_t *__restrict__ hist, const int32_t *__restrict__ totals)
+{
+    __shared__ int s_off[RADIX];
+    __shared__ int s_wcnt[RS_WARPS][RADIX];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    {
+        int tot;
+        int t = totals[tid];
+        int base = block_exclusive_scan(t, tot);
+        s_off[tid] = base + hist[tid * NB + blockIdx.x];
+    }
+    int n = min(*n_ptr, cap);
+    int begin;
+    int end = chunk_range(n, NB, blockIdx.x, begin);
+    __syncthreads();
+    for (int tb = begin; tb < end; tb += RS_THREADS) {
+        int i = tb + tid;
+        bool valid = i < end;
+        uint32_t key = valid ? kin[i] : 0u;
+        int32_t val = valid ? vin[i] : 0;
+        int digit = valid ? (int)((key >> shift) & 255u) : RADIX;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) s_wcnt[w][tid] = 0;
+        __syncthreads();
+        unsigned peers = __match_any_sync(0xffffffffu, digit);
+        int rank = __popc(peers & lanemask_lt());
+        if (valid && rank == 0) s_wcnt[warp][digit] = __popc(peers);
+        __syncthreads();
+        int sum = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) {
+            int c = s_wcnt[w][tid];
+            s_wcnt[w][tid] = sum;
+            sum += c;
+        }
+        __syncthreads();
+        if (valid) {
+            int dst = s_off[digit] + s_wcnt[warp][digit] + rank;
+            kout[dst] = key;
+            vout[dst] = val;
+        }
+        __syncthreads();
+        s_off[tid] += sum;
+        __syncthreads();
+    }
+}
+
+// Sorts (keys, vals) of *n_ptr (<= cap) items stably on bits [0, bits); the
+// result lands in (k_final, v_final); the other pair is scratch.
+int radix_sort(uint32_t *k0, int32_t *v0, uint32_t *k1, int32_t *v1, int bits, const int32_t *n_ptr, int cap,
+               const SplatWs &w, uint32_t *k_final, int32_t *v_final, cudaStream_t st)
+{
+    int passes = (bits + 7) / 8;
+    if (passes == 0) passes = 1;
+    // choose the start buffer so that an odd/even number of passes ends in the final pair
+    uint32_t *kin = k0, *kout = k1;
+    int32_t *vin = v0, *vout = v1;
+    for (int p = 0; p < passes; ++p) {
+        radix_hist_kernel<<<w.NB, RS_THREADS, 0, st>>>(kin, n_ptr, cap, 8 * p, w.NB, w.hist);
+        radix_scan_kernel<<<RADIX, 1024, 0, st>>>(w.hist, w.NB, w.totals);
+        radix_scatter_kernel<<<w.NB, RS_THREADS, 0, st>>>(kin, vin, kout, vout, n_ptr, cap, 8 * p, w.NB, w.hist,
+                                                         w.totals);
+        uint32_t *tk = kin;
+        kin = kout;
+        kout = tk;
+        int32_t *tv = vin;
+        vin = vout;
+        vout = tv;
+    }
+    AV_CHECK_LAUNCH();
+    (void)k_final;
+    (void)v_final;
+    return AVATAR_OK;
+}
+
+// ---------------------------------------------------------------- scan + emit
+__global__ void __launch_bounds__(1024)
+pair_scan_reduce_kernel(const int32_t *__restrict__ sorted_idx, const int32_t *__restrict__ npairs, int G, int NB,
+                        int32_t *__restrict__ block_sums)
+{
+    int begin;
+    int end = chunk_range(G, NB, blockIdx.x, begin);
+    long s = 0;
+    for (int i = begin + threadIdx.x; i < end; i += blockDim.x) s += npairs[sorted_idx[i]];
+    int v = (int)min(s, (long)0x3fffffff);
+    int tot;
+    block_exclusive_scan(v, tot);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024)
+pair_scan_down_kernel(const int32_t *__restrict__ sorted_idx, const int32_t *__restrict__ npairs, int G, int NB,
+                      const int32_t *__restrict__ block_sums, int32_t *__restrict__ offsets,
+                      int32_t *__restrict__ num_pairs, long cap, int32_t *status)
+{
+    __shared__ long s_base;
+    if (threadIdx.x == 0) {
+        long b = 0, tot = 0;
+        for (int i = 0; i < NB; ++i) {
+            if (i < (int)blockIdx.x) b += block_sums[i];
+            tot += block_sums[i];
+        }
+        s_base = b;
+        if (blockIdx.x == 0) {
+            long t = tot > 0x7fffffffL ? 0x7fffffffL : tot;
+            *num_pairs = (int32_t)t;
+            if (tot > cap) av_report(status, AVATAR_ERR_OVERFLOW);
+        }
+    }
+    __syncthreads();
+    long running = s_base;
+    int begin;
+    int end = chunk_range(G, NB, blockIdx.x, begin);
+    for (int tb = begin; tb < end; tb += blockDim.x) {
+        int i = tb + threadIdx.x;
+        int v = i < end ? npairs[sorted_idx[i]] : 0;
+        int tot;
+        int ex = block_exclusive_scan(v, tot);
+        if (i < end) offsets[i] = (int32_t)min(running + ex, (long)0x7fffffff);
+        running += tot;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+emit_pairs_kernel(const int32_t *__restrict__ sorted_idx, const int32_t *__restrict__ offsets,
+                  const int32_t *__restrict__ npairs, const int32_t *__restrict__ rect, int G, int TS, int ntx,
+                  long cap, uint32_t *__restrict__ keys, int32_t *__restrict__ vals)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G; i += gridDim.x * blockDim.x) {
+        int g = sorted_idx[i];
+        int n = npairs[g];
+        if (n == 0) continue;
+        long off = offsets[i];
+        if (off + n > cap) continue;
+        int tx0 = rect[g] / TS, ty0 = rect[G + g] / TS, tx1 = rect[2 * G + g] / TS, ty1 = rect[3 * G + g] / TS;
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) {
+                keys[off] = (uint32_t)(ty * ntx + tx);
+                vals[off] = g;
+                ++off;
+            }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+tile_ranges_kernel(const uint32_t *__restrict__ keys, const int32_t *__restrict__ num_pairs, long cap, int ntiles,
+                   int2 *__restrict__ ranges)
+{
+    // after an overflow the pair list is incomplete: leave every tile empty
+    if ((long)*num_pairs > cap) return;
+    int n = *num_pairs;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t t = keys[i];
+        if (t >= (uint32_t)ntiles) continue;
+        if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
+        if (i == n - 1 || keys[i + 1] != t) ranges[t].y = i + 1;
+    }
+}
+
+// ---------------------------------------------------------------- blend
+template <int TS>
+__global__ void __launch_bounds__(TS *TS)
+blend_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_gauss, const float4 *__restrict__ rec0,
+             const float4 *__restrict__ rec1, const float *__restrict__ rec2, int W, int H, int ntx,
+             float *__restrict__ image, float *__restrict__ T_final, int32_t *__restrict__ n_last)
+{
+    constexpr int NT = TS * TS;
+    __shared__ float4 s0[NT];
+    __shared__ float4 s1[NT];
+    __shared__ float s2[NT];
+    const int tile = blockIdx.x;
+    const int tx = tile % ntx, ty = tile / ntx;
+    const int tid = threadIdx.x;
+    const int px = tx * TS + tid % TS, py = ty * TS + tid / TS;
+    const bool inside = px < W && py < H;
+    const float fx = px + 0.5f, fy = py + 0.5f;
+    const int2 rg = ranges[tile];
+    const int n = rg.y - rg.x;
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    int last = 0;
+    bool done = !inside;
+    for (int base = 0; base < n; base += NT) {
+        if (__syncthreads_count(done) == NT) break;
+        int idx = base + tid;
+        if (idx < n) {
+            int g = pair_gauss[rg.x + idx];
+            s0[tid] = rec0[g];
+            s1[tid] = rec1[g];
+            s2[tid] = rec2[g];
+        }
+        __syncthreads();
+        if (!done) {
+            int m = min(NT, n - base);
+            for (int j = 0; j < m; ++j) {
+                float4 r0 = s0[j];
+                float4 r1 = s1[j];
+                float dx = fx - r0.x, dy = fy - r0.y;
+                float power = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
+                float alpha = fminf(0.99f, r1.y * __expf(power));
+                if (alpha < ALPHA_MIN) continue;
+                float test_T = T * (1.f - alpha);
+                if (test_T < T_MIN) {
+                    done = true;
+                    break;
+                }
+                float wgt = alpha * T;
+                C0 = fmaf(r1.z, wgt, C0);
+                C1 = fmaf(r1.w, wgt, C1);
+                C2 = fmaf(s2[j], wgt, C2);
+                T = test_T;
+                last = base + j + 1;
+            }
+        }
+    }
+    if (inside) {
+        const int pix = py * W + px;
+        image[pix] = C0;
+        image[W * H + pix] = C1;
+        image[2 * W * H + pix] = C2;
+        T_final[pix] = T;
+        n_last[pix] = last;
+    }
+}
+
+// ---------------------------------------------------------------- backward
+template <int TS>
+__global__ void __launch_bounds__(TS *TS)
+blend_backward_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_gauss,
+                      const float4 *__restrict__ rec0, const float4 *__restrict__ rec1, const float *__restrict__ rec2,
+                      int W, int H, int ntx, const float *__restrict__ T_final, const int32_t *__restrict__ n_last,
+                      const float *__restrict__ d_image, int G, float *__restrict__ d_mean2d,
+                      float *__restrict__ d_conic, float *__restrict__ d_opacity, float *__restrict__ d_color)
+{
+    constexpr int NT = TS * TS;
+    __shared__ float4 s0[NT];
+    __shared__ float4 s1[NT];
+    __shared__ float s2[NT];
+    __shared__ int sg[NT];
+    __shared__ int s_max;
+    const int tile = blockIdx.x;
+    const int tx = tile % ntx, ty = tile / ntx;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int px = tx * TS + tid % TS, py = ty * TS + tid / TS;
+    const bool inside = px < W && py < H;
+    const float fx = px + 0.5f, fy = py + 0.5f;
+    const int2 rg = ranges[tile];
+    const int pix = py * W + px;
+    int my_last = inside ? n_last[pix] : 0;
+    float T = inside ? T_final[pix] : 1.f;
+    float dC0 = 0.f, dC1 = 0.f, dC2 = 0.f;
+    if (inside) {
+        dC0 = d_image[pix];
+        dC1 = d_image[W * H + pix];
+        dC2 = d_image[2 * W * H + pix];
+    }
+    if (tid == 0) s_max = 0;
+    __syncthreads();
+    atomicMax(&s_max, my_last);
+    __syncthreads();
+    const int n = s_max;
+    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;  // colour behind the current Gaussian
+    for (int end = n; end > 0; end -= NT) {
+        const int start = max(0, end - NT);
+        __syncthreads();
+        int idx = start + tid;
+        if (idx < end) {
+            int g = pair_gauss[rg.x + idx];
+            sg[tid] = g;
+            s0[tid] = rec0[g];
+            s1[tid] = rec1[g];
+            s2[tid] = rec2[g];
+        }
+        __syncthreads();
+        for (int j = end - 1; j >= start; --j) {
+            const int sj = j - start;
+            float4 r0 = s0[sj];
+            float4 r1 = s1[sj];
+            float g_col0 = 0.f, g_col1 = 0.f, g_col2 = 0.f, g_op = 0.f, g_mx = 0.f, g_my = 0.f, g_ca = 0.f,
+                  g_cb = 0.f, g_cc = 0.f;
+            bool contrib = false;
+            if (j < my_last) {
+                float dx = fx - r0.x, dy = fy - r0.y;
+                float power = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
+                float ex = __expf(power);
+                float raw = r1.y * ex;
+                float alpha = fminf(0.99f, raw);
+                if (alpha >= ALPHA_MIN) {
+                    contrib = true;
+                    float c2 = s2[sj];
+                    T = T / (1.f - alpha);
+                    float wgt = alpha * T;
+                    g_col0 = wgt * dC0;
+                    g_col1 = wgt * dC1;
+                    g_col2 = wgt * dC2;
+                    float dalpha = T * ((r1.z - acc0) * dC0 + (r1.w - acc1) * dC1 + (c2 - acc2) * dC2);
+                    acc0 = alpha * r1.z + (1.f - alpha) * acc0;
+                    acc1 = alpha * r1.w + (1.f - alpha) * acc1;
+                    acc2 = alpha * c2 + (1.f - alpha) * acc2;
+                    if (raw < 0.99f) {
+                        g_op = dalpha * ex;
+                        float dpow = dalpha * alpha;
+                        g_mx = dpow * (r0.z * dx + r0.w * dy);
+                        g_my = dpow * (r0.w * dx + r1.x * dy);
+                        g_ca = -0.5f * dx * dx * dpow;
+                        g_cb = -dx * dy * dpow;
+                        g_cc = -0.5f * dy * dy * dpow;
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+                g_col0 = warp_sum(g_col0);
+                g_col1 = warp_sum(g_col1);
+                g_col2 = warp_sum(g_col2);
+                g_op = warp_sum(g_op);
+                g_mx = warp_sum(g_mx);
+                g_my = warp_sum(g_my);
+                g_ca = warp_sum(g_ca);
+                g_cb = warp_sum(g_cb);
+                g_cc = warp_sum(g_cc);
+                if (lane == 0) {
+                    int g = sg[sj];
+                    atomicAdd(d_color + g, g_col0);
+                    atomicAdd(d_color + G + g, g_col1);
+                    atomicAdd(d_color + 2 * G + g, g_col2);
+                    atomicAdd(d_opacity + g, g_op);
+                    atomicAdd(d_mean2d + g, g_mx);
+                    atomicAdd(d_mean2d + G + g, g_my);
+                    atomicAdd(d_conic + g, g_ca);
+                    atomicAdd(d_conic + G + g, g_cb);
+                    atomicAdd(d_conic + 2 * G + g, g_cc);
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+project_backward_kernel(avatar_splat_args a, CamDev cam, const float *__restrict__ d_mean2d,
+                        const float *__restrict__ d_conic, float *__restrict__ d_xd, float *__restrict__ d_cov)
+{
+    const int G = a.G;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        float dmx = d_mean2d[g], dmy = d_mean2d[G + g];
+        float da = d_conic[g], db = d_conic[G + g], dc = d_conic[2 * G + g];
+        bool has = a.rect[2 * G + g] >= a.rect[g];
+        if (!has || (dmx == 0.f && dmy == 0.f && da == 0.f && db == 0.f && dc == 0.f)) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) d_xd[i * G + g] = 0.f;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) d_cov[i * G + g] = 0.f;
+            continue;
+        }
+        float x = a.xd[g], y = a.xd[G + g], z = a.xd[2 * G + g];
+        float px = cam.R[0] * x + cam.R[1] * y + cam.R[2] * z + cam.t[0];
+        float py = cam.R[3] * x + cam.R[4] * y + cam.R[5] * z + cam.t[1];
+        float pz = cam.R[6] * x + cam.R[7] * y + cam.R[8] * z + cam.t[2];
+        float iz = 1.0f / pz;
+        float j00 = cam.fx * iz, j02 = -cam.fx * px * iz * iz;
+        float j11 = cam.fy * iz, j12 = -cam.fy * py * iz * iz;
+        float T0[3], T1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T0[k] = j00 * cam.R[k] + j02 * cam.R[6 + k];
+            T1[k] = j11 * cam.R[3 + k] + j12 * cam.R[6 + k];
+        }
+        float c[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) c[i] = a.cov[i * G + g];
+        float S[9] = {c[0], c[1], c[2], c[1], c[3], c[4], c[2], c[4], c[5]};
+        float S0[3], S1[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            S0[i] = S[3 * i] * T0[0] + S[3 * i + 1] * T0[1] + S[3 * i + 2] * T0[2];
+            S1[i] = S[3 * i] * T1[0] + S[3 * i + 1] * T1[1] + S[3 * i + 2] * T1[2];
+        }
+        float s00 = T0[0] * S0[0] + T0[1] * S0[1] + T0[2] * S0[2] + 0.3f;
+        float s01 = T1[0] * S0[0] + T1[1] * S0[1] + T1[2] * S0[2];
+        float s11 = T1[0] * S1[0] + T1[1] * S1[1] + T1[2] * S1[2] + 0.3f;
+        float det = s00 * s11 - s01 * s01;
+        float id = 1.0f / det;
+        float ca = s11 * id, cb = -s01 * id, cc = s00 * id;
+        // conic (a,b,c) -> Sigma' entries (s00, s01 (scalar, both positions), s11)
+        float ds00 = -ca * ca * da - ca * cb * db - cb * cb * dc;
+        float ds11 = -cb * cb * da - cb * cc * db - cc * cc * dc;
+        float ds01 = -2.f * ca * cb * da - (ca * cc + cb * cb) * db - 2.f * cb * cc * dc;
+        // symmetric 2x2 gradient
+        float g00 = ds00, g01 = 0.5f * ds01, g11 = ds11;
+        // dSigma = T^T Gm T (3x3 symmetric)
+        float dS[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                dS[3 * i + j] = T0[i] * (g00 * T0[j] + g01 * T1[j]) + T1[i] * (g01 * T0[j] + g11 * T1[j]);
+        d_cov[g] = dS[0];
+        d_cov[G + g] = dS[1] + dS[3];
+        d_cov[2 * G + g] = dS[2] + dS[6];
+        d_cov[3 * G + g] = dS[4];
+        d_cov[4 * G + g] = dS[5] + dS[7];
+        d_cov[5 * G + g] = dS[8];
+        // dT = 2 Gm T Sigma  (rows 0 and 1)
+        float dT0[3], dT1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            dT0[k] = 2.f * (g00 * S0[k] + g01 * S1[k]);
+            dT1[k] = 2.f * (g01 * S0[k] + g11 * S1[k]);
+        }
+        // T = J R -> dJ = dT R^T (only the non-zero entries of J)
+        float dj00 = dT0[0] * cam.R[0] + dT0[1] * cam.R[1] + dT0[2] * cam.R[2];
+        float dj02 = dT0[0] * cam.R[6] + dT0[1] * cam.R[7] + dT0[2] * cam.R[8];
+        float dj11 = dT1[0] * cam.R[3] + dT1[1] * cam.R[4] + dT1[2] * cam.R[5];
+        float dj12 = dT1[0] * cam.R[6] + dT1[1] * cam.R[7] + dT1[2] * cam.R[8];
+        float iz2 = iz * iz, iz3 = iz2 * iz;
+        float dpx = dmx * cam.fx * iz - dj02 * cam.fx * iz2;
+        float dpy = dmy * cam.fy * iz - dj12 * cam.fy * iz2;
+        float dpz = -dmx * cam.fx * px * iz2 - dmy * cam.fy * py * iz2 - dj00 * cam.fx * iz2 +
+                    dj02 * 2.f * cam.fx * px * iz3 - dj11 * cam.fy * iz2 + dj12 * 2.f * cam.fy * py * iz3;
+        d_xd[g] = cam.R[0] * dpx + cam.R[3] * dpy + cam.R[6] * dpz;
+        d_xd[G + g] = cam.R[1] * dpx + cam.R[4] * dpy + cam.R[7] * dpz;
+        d_xd[2 * G + g] = cam.R[2] * dpx + cam.R[5] * dpy + cam.R[8] * dpz;
+    }
+}
+
+// Sizes only (what the workspace and tile-count queries need).
+int check_splat_dims(const avatar_splat_args *a)
+{
+    if (!a || a->G < 0) return AVATAR_ERR_INVALID_ARG;
+    if (a->cam.width < 1 || a->cam.height < 1 || a->cam.width > 16384 || a->cam.height > 16384)
+        return AVATAR_ERR_INVALID_ARG;
+    int ts = a->tile == 0 ? 16 : a->tile;
+    if (ts != 8 && ts != 16 && ts != 32) return AVATAR_ERR_INVALID_ARG;
+    if (a->pair_capacity < 1 || a->pair_capacity > 0x7fffffffL) return AVATAR_ERR_INVALID_ARG;
+    return AVATAR_OK;
+}
+
+int check_splat(const avatar_splat_args *a)
+{
+    AV_TRY(check_splat_dims(a));
+    if (a->G > 0 && (!a->xd || !a->cov || !a->opacity || !a->color || !a->mean2d || !a->conic || !a->depth ||
+                     !a->rect))
+        return AVATAR_ERR_INVALID_ARG;
+    if (!a->tile_range || !a->pair_gauss || !a->num_pairs || !a->image || !a->T_final || !a->n_last)
+        return AVATAR_ERR_INVALID_ARG;
+    return AVATAR_OK;
+}
+
+int tile_of(const avatar_splat_args *a) { return a->tile == 0 ? 16 : a->tile; }
+
+int ntiles_of(const avatar_splat_args *a)
+{
+    int ts = tile_of(a);
+    return ((a->cam.width + ts - 1) / ts) * ((a->cam.height + ts - 1) / ts);
+}
+
+int prep(avatar_ctx *ctx, const avatar_splat_args *a, void *ws, size_t ws_bytes, SplatWs *w)
+{
+    if (!ctx) return AVATAR_ERR_INVALID_ARG;
+    AV_TRY(check_splat(a));
+    if (!ws || (((uintptr_t)ws) & 255)) return AVATAR_ERR_WORKSPACE;
+    if (splat_ws_layout(a, radix_blocks(ctx), ws, ws_bytes, w) > ws_bytes) return AVATAR_ERR_WORKSPACE;
+    return AVATAR_OK;
+}
+
+int grid_cap(const avatar_ctx *ctx, long n, int threads, int per_sm)
+{
+    long b = (n + threads - 1) / threads;
+    long cap = (long)ctx->sm_count * per_sm;
+    if (b > cap) b = cap;
+    return b < 1 ? 1 : (int)b;
+}
+
+int bits_for(int ntiles)
+{
+    int b = 0;
+    while ((1L << b) < ntiles) ++b;
+    return b;
+}
+
+}  // namespace
+
+extern "C" int avatar_splat_num_tiles(const avatar_splat_args *a)
+{
+    if (check_splat_dims(a) != AVATAR_OK) return 0;
+    return ntiles_of(a);
+}
+
+extern "C" size_t avatar_splat_workspace_size(const avatar_splat_args *a)
+{
+    if (check_splat_dims(a) != AVATAR_OK) return 0;
+    return splat_ws_layout(a, RADIX_BLOCKS, nullptr, 0, nullptr);
+}
+
+extern "C" int avatar_splat_project(avatar_ctx *ctx, const avatar_splat_args *a, void *ws, size_t ws_bytes,
+                                    avatar_stream_t stream)
+{
+    SplatWs w;
+    AV_TRY(prep(ctx, a, ws, ws_bytes, &w));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (a->G == 0) return AVATAR_OK;
+    project_kernel<<<grid_cap(ctx, a->G, 256, 8), 256, 0, st>>>(*a, to_dev(a->cam));
+    AV_CHECK_LAUNCH();
+    return AVATAR_OK;
+}
+
+extern "C" int avatar_splat_bin(avatar_ctx *ctx, const avatar_splat_args *a, void *ws, size_t ws_bytes,
+                                avatar_stream_t stream)
+{
+    SplatWs w;
+    AV_TRY(prep(ctx, a, ws, ws_bytes, &w));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ntiles = ntiles_of(a);
+    if (cudaMemsetAsync(a->tile_range, 0, (size_t)ntiles * 2 * sizeof(int32_t), st) != cudaSuccess)
+        return AVATAR_ERR_CUDA;
+    if (a->G == 0) {
+        if (cudaMemsetAsync(a->num_pairs, 0, sizeof(int32_t), st) != cudaSuccess) return AVATAR_ERR_CUDA;
+        return AVATAR_OK;
+    }
+    const int G = a->G;
+    const long cap = a->pair_capacity;
+    // 0. pair counts, depth keys and blend records from the projection buffers
+    bin_keys_kernel<<<grid_cap(ctx, G, 256, 8), 256, 0, st>>>(*a, tile_of(a), w);
+    AV_CHECK_LAUNCH();
+    // 1. stable depth sort of all Gaussians (4 passes -> result back in dkey_a/dval_a)
+    AV_TRY(radix_sort(w.dkey_a, w.dval_a, w.dkey_b, w.dval_b, 32, w.count_g, G, w, w.dkey_a, w.dval_a, st));
+    // 2. pair offsets in depth order
+    pair_scan_reduce_kernel<<<w.NB, 1024, 0, st>>>(w.dval_a, w.npairs, G, w.NB, w.block_sums);
+    pair_scan_down_kernel<<<w.NB, 1024, 0, st>>>(w.dval_a, w.npairs, G, w.NB, w.block_sums, w.offsets, a->num_pairs,
+                                                 cap, a->status);
+    AV_CHECK_LAUNCH();
+    // 3. emit in depth order into the buffer that makes the tile sort end in pair_gauss
+    const int ts = tile_of(a);
+    const int ntx = (a->cam.width + ts - 1) / ts;
+    int tbits = bits_for(ntiles);
+    int passes = tbits <= 8 ? 1 : (tbits + 7) / 8;
+    uint32_t *k_emit = (passes % 2 == 0) ? w.pkey_a : w.pkey_b;
+    int32_t *v_emit = (passes % 2 == 0) ? a->pair_gauss : w.pval_b;
+    uint32_t *k_other = (passes % 2 == 0) ? w.pkey_b : w.pkey_a;
+    int32_t *v_other = (passes % 2 == 0) ? w.pval_b : a->pair_gauss;
+    emit_pairs_kernel<<<grid_cap(ctx, G, 256, 8), 256, 0, st>>>(w.dval_a, w.offsets, w.npairs, a->rect, G, ts, ntx,
+                                                                 cap, k_emit, v_emit);
+    AV_CHECK_LAUNCH();
+    // 4. stable sort of the pairs on the tile id
+    AV_TRY(radix_sort(k_emit, v_emit, k_other, v_other, passes * 8, a->num_pairs, (int)cap, w, w.pkey_a,
+                      a->pair_gauss, st));
+    // 5. tile ranges (sorted keys are in pkey_a)
+    tile_ranges_kernel<<<ctx->sm_count * 8, 256, 0, st>>>(w.pkey_a, a->num_pairs, cap, ntiles,
+                                                          (int2 *)a->tile_range);
+    AV_CHECK_LAUNCH();
+    return AVATAR_OK;
+}
+
+extern "C" int avatar_splat_blend(avatar_ctx *ctx, const avatar_splat_args *a, void *ws, size_t ws_bytes,
+                                  avatar_stream_t stream)
+{
+    SplatWs w;
+    AV_TRY(prep(ctx, a, ws, ws_bytes, &w));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ts = tile_of(a);
+    const int ntx = (a->cam.width + ts - 1) / ts;
+    const int ntiles = ntiles_of(a);
+    const int W = a->cam.width, H = a->cam.height;
+    const int2 *rg = (const int2 *)a->tile_range;
+    switch (ts) {
+        case 8:
+            blend_kernel<8><<<ntiles, 64, 0, st>>>(rg, a->pair_gauss, w.rec0, w.rec1, w.rec2, W, H, ntx, a->image,
+                                                   a->T_final, a->n_last);
+            break;
+        case 32:
+            blend_kernel<32><<<ntiles, 1024, 0, st>>>(rg, a->pair_gauss, w.rec0, w.rec1, w.rec2, W, H, ntx, a->image,
+                                                      a->T_final, a->n_last);
+            break;
+        default:
+            blend_kernel<16><<<ntiles, 256, 0, st>>>(rg, a->pair_gauss, w.rec0, w.rec1, w.rec2, W, H, ntx, a->image,
+                                                     a->T_final, a->n_last);
+            break;
+    }
+    AV_CHECK_LAUNCH();
+    return AVATAR_OK;
+}
+
+extern "C" int avatar_splat(avatar_ctx *ctx, const avatar_splat_args *a, void *ws, size_t ws_bytes,
+                            avatar_stream_t stream)
+{
+    AV_TRY(avatar_splat_project(ctx, a, ws, ws_bytes, stream));
+    AV_TRY(avatar_splat_bin(ctx, a, ws, ws_bytes, stream));
+    return avatar_splat_blend(ctx, a, ws, ws_bytes, stream);
+}
+
+extern "C" int avatar_splat_backward(avatar_ctx *ctx, const avatar_splat_args *a, const avatar_splat_grads *g,
+                                     void *ws, size_t ws_bytes, avatar_stream_t stream)
+{
+    SplatWs w;
+    AV_TRY(prep(ctx, a, ws, ws_bytes, &w));
+    if (!g || !g->d_image || !g->d_xd || !g->d_cov || !g->d_opacity || !g->d_color) return AVATAR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int G = a->G;
+    if (G == 0) return AVATAR_OK;
+    if (cudaMemsetAsync(w.d_mean2d, 0, (size_t)2 * G * sizeof(float), st) != cudaSuccess ||
+        cudaMemsetAsync(w.d_conic, 0, (size_t)3 * G * sizeof(float), st) != cudaSuccess ||
+        cudaMemsetAsync(g->d_opacity, 0, (size_t)G * sizeof(float), st) != cudaSuccess ||
+        cudaMemsetAsync(g->d_color, 0, (size_t)3 * G * sizeof(float), st) != cudaSuccess)
+        return AVATAR_ERR_CUDA;
+    const int ts = tile_of(a);
+    const int ntx = (a->cam.width + ts - 1) / ts;
+    const int ntiles = ntiles_of(a);
+    const int W = a->cam.width, H = a->cam.height;
+    const int2 *rg = (const int2 *)a->tile_range;
+    switch (ts) {
+        case 8:
+            blend_backward_kernel<8><<<ntiles, 64, 0, st>>>(rg, a->pair_gauss, w.rec0, w.rec1, w.rec2, W, H, ntx,
+                                                            a->T_final, a->n_last, g->d_image, G, w.d_mean2d,
+                                                            w.d_conic, g->d_opacity, g->d_color);
+            break;
+        case 32:
+            blend_backward_kernel<32><<<ntiles, 1024, 0, st>>>(rg, a->pair_gauss, w.rec0, w.rec1, w.rec2, W, H, ntx,
+                                                               a->T_final, a->n_last, g->d_image, G, w.d_mean2d,
+                                                               w.d_conic, g->d_opacity, g->d_color);
+            break;
+        default:
+            blend_backward_kernel<16><<<ntiles, 256, 0, st>>>(rg, a->pair_gauss, w.rec0, w.rec1, w.rec2, W, H, ntx,
+                                                              a->T_final, a->n_last, g->d_image, G, w.d_mean2d,
+                                                              w.d_conic, g->d_opacity, g->d_color);
+            break;
+    }
+    AV_CHECK_LAUNCH();
+    project_backward_kernel<<<grid_cap(ctx, G, 256, 8), 256, 0, st>>>(*a, to_dev(a->cam), w.d_mean2d, w.d_conic,
+                                                                       g->d_xd, g->d_cov);
+    AV_CHECK_LAUNCH();
+    return AVATAR_OK;
+}

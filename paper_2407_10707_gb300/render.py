@@ -1,0 +1,281 @@
+"""Frame-level composition of the four native stages.
+
+Renderer   : the relit novel-pose frame (Sec. 3.1-3.2, test-time path of
+             Sec. 3.5): skin -> visibility -> shade -> splat, all buffers
+             preallocated so that a frame allocates nothing and can be
+             captured in a CUDA graph.
+TrainStep  : the differentiable step (Sec. 3.3): the frame above, the L1
+             image loss and the hand-written backward kernels in reverse
+             order (splat -> shade -> skin); also graph-capturable.
+Autograd   : torch.autograd.Function wrappers of the same entry points for
+             user training loops (visibility bits are constants, as the
+             paper precomputes visibility for training poses, Sec. 3.5).
+
+Only argument marshalling happens here; every arithmetic step is a kernel
+of libavatar.so.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import api
+
+
+def scene_tensors(scene, device="cuda"):
+    """Device copies of a synth.Scene (SoA float32 / int32)."""
+    f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=device)
+    t = api.avatar_tensors(scene.avatar, device)
+    light = dict(L=f(scene.light.L), A=f(scene.light.A), w=f(scene.light.w))
+    return dict(avatar=t, light=light, frames=f(scene.frames.reshape(-1, 9)),
+                dmap=torch.as_tensor(scene.dmap, dtype=torch.int32, device=device), camera=scene.camera,
+                depth_res=int(scene.depth_res), center=[float(c) for c in scene.window_center],
+                half=float(scene.window_half), bias=float(scene.vis_bias),
+                cam_center=[float(c) for c in scene.camera.center])
+
+
+class Renderer:
+    """Preallocated forward frame.  forward() launches exactly the library's
+    kernels on the current stream."""
+
+    def __init__(self, st, tile=16, pair_capacity=None):
+        self.st = st
+        t = st["avatar"]
+        dev = t["xg"].device
+        self.device = dev
+        self.status = api.status_word(dev)
+        self.sk = api.alloc_skin_outputs(t)
+        self.sk["_ws"] = None
+        self.skin_ws = None
+        G = t["xg"].shape[1]
+        Nv = t["xv"].shape[1]
+        NL = st["light"]["L"].shape[0]
+        self.bits = torch.empty(Nv, (NL + 31) // 32, dtype=torch.int32, device=dev)
+        self.vis_ws = None
+        self.sh = dict(color=torch.empty(3, G, device=dev), radiance=torch.empty(3, G, device=dev),
+                       cull=torch.empty(G, dtype=torch.uint8, device=dev))
+        self.sb = api.alloc_splat(G, st["camera"], tile, pair_capacity, dev)
+        self.graph = None
+        # first eager call sizes the workspaces
+        self.forward()
+        torch.cuda.synchronize()
+
+    def skin(self):
+        out = api.avatar_skin(self.st["avatar"], out=self.sk, ws=self.skin_ws, status=self.status)
+        self.skin_ws = out["_ws"]
+
+    def visibility(self):
+        st = self.st
+        if self.vis_ws is None:
+            self.vis_ws = self._vis_ws()
+        api.avatar_visibility(self.sk["xp"], st["avatar"]["faces"], st["frames"], st["center"], st["half"],
+                              st["bias"], st["depth_res"], dmap=st["dmap"], bits=self.bits, ws=self.vis_ws,
+                              status=self.status)
+
+    def _vis_ws(self):
+        import ctypes as C
+        from . import _lib as L
+        st = self.st
+        a = api._vis_struct(self.sk["xp"], st["avatar"]["faces"], st["frames"], st["center"], st["half"],
+                            st["bias"], st["depth_res"], st["dmap"], self.bits, None)
+        return api.workspace(L.load().avatar_visibility_workspace_size(C.byref(a)), self.device)
+
+    def shade(self):
+        st = self.st
+        api.avatar_shade(self.sk, st["avatar"]["knn"], self.bits, st["light"], st["cam_center"], out=self.sh,
+                         status=self.status)
+
+    def splat(self):
+        t = self.st["avatar"]
+        api.avatar_splat(self.sk["xd"], self.sk["cov"], t["opacity"], self.sh["color"], self.sh["cull"],
+                         self.st["camera"], b=self.sb, status=self.status)
+
+    def forward(self):
+        self.skin()
+        self.visibility()
+        self.shade()
+        self.splat()
+        return self.sb.image
+
+    def capture(self):
+        """Capture forward() in a CUDA graph (after one eager call)."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.forward()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.forward()
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+        return self.sb.image
+
+    def check(self):
+        api.raise_on_status(self.status, "render")
+
+
+class TrainStep(Renderer):
+    """Forward frame + L1 loss + backward through every stage."""
+
+    def __init__(self, st, target, tile=16, pair_capacity=None):
+        self.target = target
+        super().__init__(st, tile, pair_capacity)
+        t = st["avatar"]
+        self.loss = torch.empty(1, device=self.device)
+        self.d_img = torch.empty_like(self.sb.image)
+        self.g_splat = dict(xd=torch.empty_like(self.sk["xd"]), cov=torch.empty_like(self.sk["cov"]),
+                            opacity=torch.empty_like(t["opacity"]), color=torch.empty_like(self.sh["color"]))
+        self.g_shade = dict(xd=torch.empty_like(self.sk["xd"]), nd=torch.empty_like(self.sk["nd"]),
+                            ag=torch.empty_like(self.sk["ag"]), rg=torch.empty_like(self.sk["rg"]),
+                            pg=torch.empty_like(self.sk["pg"]), ubar=torch.empty_like(self.sk["ubar"]),
+                            L=torch.empty_like(st["light"]["L"]))
+        self.g_skin = {k: torch.empty_like(t[k]) for k in ("xg", "logscale", "quat", "wv", "av", "rv", "pv")}
+        self._bwd_ws = None
+        self.step()
+        torch.cuda.synchronize()
+
+    def backward(self):
+        import ctypes as C
+        from . import _lib as L
+        lib = L.load()
+        ctx = api.context()
+        st = self.st
+        t = st["avatar"]
+        s = api._stream()
+        # loss
+        L.check(lib.avatar_l1_loss(ctx, self.sb.image.numel(), api._p(self.sb.image), api._p(self.target),
+                                   api._p(self.loss), api._p(self.d_img), s), "avatar_l1_loss")
+        # splat adjoint
+        G = t["xg"].shape[1]
+        a = api._splat_struct(G, st["camera"], self.sk["xd"], self.sk["cov"], t["opacity"], self.sh["color"],
+                              self.sh["cull"], self.sb, None)
+        gs = L.SplatGrads()
+        gs.d_image = api._p(self.d_img)
+        gs.d_xd, gs.d_cov, gs.d_opacity, gs.d_color = (api._p(self.g_splat[k]) for k in
+                                                       ("xd", "cov", "opacity", "color"))
+        L.check(lib.avatar_splat_backward(ctx, C.byref(a), C.byref(gs), api._p(self.sb.ws), self.sb.ws.numel(), s),
+                "avatar_splat_backward")
+        # shade adjoint
+        sa = api._shade_struct(self.sk, t["knn"], self.bits, st["light"], st["cam_center"], self.sh["color"],
+                               self.sh["radiance"], self.sh["cull"], None)
+        gh = L.ShadeGrads()
+        gh.d_color = api._p(self.g_splat["color"])
+        gh.d_xd, gh.d_nd, gh.d_ag, gh.d_rg, gh.d_pg, gh.d_ubar, gh.d_light_L = (
+            api._p(self.g_shade[k]) for k in ("xd", "nd", "ag", "rg", "pg", "ubar", "L"))
+        L.check(lib.avatar_shade_backward(ctx, C.byref(sa), C.byref(gh), s), "avatar_shade_backward")
+        # skin adjoint
+        ka = api._skin_struct(t, self.sk, None)
+        gk = L.SkinGrads()
+        gk.d_xd, gk.d_xd2 = api._p(self.g_splat["xd"]), api._p(self.g_shade["xd"])
+        gk.d_cov, gk.d_nd = api._p(self.g_splat["cov"]), api._p(self.g_shade["nd"])
+        gk.d_ag, gk.d_rg, gk.d_pg, gk.d_ubar = (api._p(self.g_shade[k]) for k in ("ag", "rg", "pg", "ubar"))
+        for k in ("xg", "logscale", "quat", "wv", "av", "rv", "pv"):
+            setattr(gk, "d_" + k, api._p(self.g_skin[k]))
+        if self._bwd_ws is None:
+            self._bwd_ws = api.workspace(lib.avatar_skin_backward_workspace_size(C.byref(ka)), self.device)
+        L.check(lib.avatar_skin_backward(ctx, C.byref(ka), C.byref(gk), api._p(self.skin_ws), api._p(self._bwd_ws),
+                                         self._bwd_ws.numel(), s), "avatar_skin_backward")
+
+    def step(self):
+        self.forward()
+        self.backward()
+        return self.loss
+
+    def capture(self):
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.step()
+        self.graph = g
+        return g
+
+    def grads(self):
+        return dict(**self.g_skin, opacity=self.g_splat["opacity"], L=self.g_shade["L"])
+
+
+# ---------------------------------------------------------------- autograd
+class SkinFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, xg, logscale, quat, wv, av, rv, pv, const):
+        t = dict(const)
+        t.update(xg=xg.detach(), logscale=logscale.detach(), quat=quat.detach(), wv=wv.detach(), av=av.detach(),
+                 rv=rv.detach(), pv=pv.detach())
+        out = api.avatar_skin(t)
+        ctx.t = t
+        ctx.out = out
+        ctx.mark_non_differentiable(out["xp"])
+        return out["xp"], out["xd"], out["cov"], out["nd"], out["ag"], out["rg"], out["pg"], out["ubar"]
+
+    @staticmethod
+    def backward(ctx, dxp, dxd, dcov, dnd, dag, drg, dpg, dubar):
+        up = dict(d_xd=dxd, d_cov=dcov, d_nd=dnd, d_ag=dag, d_rg=drg, d_pg=dpg, d_ubar=dubar)
+        g = api.avatar_skin_backward(ctx.t, ctx.out, up)
+        return g["xg"], g["logscale"], g["quat"], g["wv"], g["av"], g["rv"], g["pv"], None
+
+
+class ShadeFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, xd, nd, ag, rg, pg, ubar, L, const):
+        sk = dict(xd=xd.detach(), nd=nd.detach(), ag=ag.detach(), rg=rg.detach(), pg=pg.detach(),
+                  ubar=ubar.detach())
+        light = dict(L=L.detach(), A=const["A"], w=const["w"])
+        out = api.avatar_shade(sk, const["knn"], const["bits"], light, const["cam_center"])
+        ctx.sk, ctx.light, ctx.const, ctx.out = sk, light, const, out
+        ctx.mark_non_differentiable(out["cull"])
+        return out["color"], out["cull"]
+
+    @staticmethod
+    def backward(ctx, dcolor, dcull):
+        c = ctx.const
+        g = api.avatar_shade_backward(ctx.sk, c["knn"], c["bits"], ctx.light, c["cam_center"], ctx.out, dcolor)
+        return g["xd"], g["nd"], g["ag"], g["rg"], g["pg"], g["ubar"], g["L"], None
+
+
+class SplatFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, xd, cov, opacity, color, cull, cam, tile=16):
+        xd, cov, opacity, color = xd.detach(), cov.detach(), opacity.detach(), color.detach()
+        b = api.avatar_splat(xd, cov, opacity, color, cull, cam, tile=tile)
+        ctx.saved = (xd, cov, opacity, color, cull, cam, b)
+        return b.image
+
+    @staticmethod
+    def backward(ctx, dimg):
+        xd, cov, opacity, color, cull, cam, b = ctx.saved
+        g = api.avatar_splat_backward(xd, cov, opacity, color, cull, cam, b, dimg)
+        return g["xd"], g["cov"], g["opacity"], g["color"], None, None, None
+
+
+class L1Fn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, img, target):
+        loss, d = api.avatar_l1_loss(img.detach(), target)
+        ctx.save_for_backward(d)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, g):
+        (d,) = ctx.saved_tensors
+        return d * g, None
+
+
+def render_differentiable(params, st, bits, tile=16):
+    """One frame through the autograd wrappers.  params: leaf tensors xg,
+    logscale, quat, opacity, wv, av, rv, pv, L (device layout)."""
+    t = st["avatar"]
+    const = {k: t[k] for k in ("knn", "xv", "dxv", "nv", "parents", "joints", "pose")}
+    xp, xd, cov, nd, ag, rg, pg, ub = SkinFn.apply(params["xg"], params["logscale"], params["quat"], params["wv"],
+                                                   params["av"], params["rv"], params["pv"], const)
+    sconst = dict(A=st["light"]["A"], w=st["light"]["w"], knn=t["knn"], bits=bits, cam_center=st["cam_center"])
+    color, cull = ShadeFn.apply(xd, nd, ag, rg, pg, ub, params["L"], sconst)
+    return SplatFn.apply(xd, cov.reshape(6, -1), params["opacity"], color, cull, st["camera"], tile)

@@ -1,0 +1,361 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Every test feeds the same seeded inputs to both sides.  Stage tests give
+each stage identical FP32 inputs (taken from the oracle's own upstream
+stage, rounded to FP32), so integer outputs must match bit for bit and
+floating outputs within the stated tolerances:
+  visibility bits, tile membership and order : bit-exact
+  pixel colours                               : 2e-4 max-abs
+  gradients                                   : 1e-3 relative (to the FP64 adjoint)
+Other FP32 outputs are compared relative to their largest magnitude with
+bounds from FP32 rounding (unit roundoff u = 2^-24): a chain of n
+operations is within ~n u, so 1e-5 for the short skinning chains, 5e-5 for
+normalised vectors, covariances and the 512-term shading sums.
+"""
+import numpy as np
+import pytest
+
+from _common import O, OP, f32, light_ordered_bits, oracle_frame, rel_err, scene, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PIX_TOL = 2e-4
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2407_10707_gb300 import api, render
+    return api, render
+
+
+def T(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def N(t):
+    return t.detach().cpu().numpy()
+
+
+# ---------------------------------------------------------------- (a) skinning
+@pytest.mark.parametrize("name", ["c1_small", "c3_fd"])
+def test_skin_matches_oracle(gpu, name):
+    api, render = gpu
+    sc = scene(name)
+    ref = oracle_frame(name)
+    st = render.scene_tensors(sc)
+    st_status = api.status_word("cuda")
+    out = api.avatar_skin(st["avatar"], status=st_status)
+    torch.cuda.synchronize()
+    api.raise_on_status(st_status)
+    sk = ref["skin"]
+    assert rel_err(N(out["bone"]).reshape(-1, 3, 4), ref["bone"]) < 1e-5
+    assert rel_err(N(out["xp"]).T, sk["xp"]) < 1e-5
+    assert rel_err(N(out["xd"]).T, sk["xd"]) < 1e-5
+    assert rel_err(N(out["cov"]).T, sk["cov"]) < 5e-5
+    assert rel_err(N(out["nd"]).T, sk["nd"]) < 5e-5
+    assert rel_err(N(out["ag"]).T, sk["ag"]) < 1e-5
+    assert rel_err(N(out["rg"]), sk["rg"]) < 1e-5
+    assert rel_err(N(out["pg"]), sk["pg"]) < 1e-5
+    assert rel_err(N(out["ubar"]).T, sk["ubar"]) < 1e-5
+
+
+def test_skin_bad_neighbour_index_sets_status(gpu):
+    api, render = gpu
+    st = render.scene_tensors(scene("c3_fd"))
+    t = dict(st["avatar"])
+    knn = t["knn"].clone()
+    knn[0, 5] = 10 ** 6
+    t["knn"] = knn
+    status = api.status_word("cuda")
+    api.avatar_skin(t, status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 7
+
+
+# ---------------------------------------------------------------- (b) visibility
+def _vis_case(sc, xp):
+    return dict(xp=T(f32(xp).T), faces=T(sc.avatar.faces, torch.int32), frames=T(f32(sc.frames.reshape(-1, 9))),
+                center=sc.window_center, half=sc.window_half, bias=sc.vis_bias, R=sc.depth_res)
+
+
+def _oracle_bits(sc, xp):
+    return O.visibility(f32(xp).astype(np.float64), sc.avatar.faces,
+                        f32(sc.frames.reshape(-1, 9)).astype(np.float64), f32(sc.window_center),
+                        float(np.float32(sc.window_half)), float(np.float32(sc.vis_bias)), sc.depth_res)
+
+
+@pytest.mark.parametrize("name,over", [
+    ("c1_small", {}),                                             # 64 dirs at 64^2, one CTA per direction
+    ("c1_small", dict(n_dirs=128, depth_res=256)),                # 4-CTA clusters
+    ("c1_small", dict(n_vertices=10_000, n_dirs=96, depth_res=512)),  # 8-CTA clusters, 1 MB depth maps
+    ("c1_small", dict(n_vertices=1_003, n_dirs=32, depth_res=128)),   # ragged vertex count
+])
+def test_visibility_bits_bit_exact(gpu, name, over):
+    api, render = gpu
+    sc = synth.config_scene(name, **over)
+    sk = O.skin(sc.avatar, O.fk(sc.avatar.parents, sc.avatar.joints, sc.avatar.pose))
+    xp = sk["xp"]
+    ref = _oracle_bits(sc, xp)
+    c = _vis_case(sc, xp)
+    status = api.status_word("cuda")
+    bits = api.avatar_visibility(c["xp"], c["faces"], c["frames"], c["center"], c["half"], c["bias"], c["R"],
+                                 status=status)
+    torch.cuda.synchronize()
+    api.raise_on_status(status)
+    got = N(bits).view(np.uint32)
+    assert got.shape == ref.shape
+    assert np.array_equal(got, ref), f"{int((got != ref).sum())} words differ"
+    # light-ordered output through d(k)
+    dmap = T(sc.dmap, torch.int32)
+    bits_l = api.avatar_visibility(c["xp"], c["faces"], c["frames"], c["center"], c["half"], c["bias"], c["R"],
+                                   dmap=dmap)
+    torch.cuda.synchronize()
+    assert np.array_equal(N(bits_l).view(np.uint32), light_ordered_bits(ref, sc.dmap))
+
+
+def test_visibility_edge_cases(gpu):
+    api, render = gpu
+    rng = np.random.default_rng(3)
+    # degenerate triangles, repeated vertices, vertices outside the window, no faces
+    xp = rng.uniform(-0.5, 0.5, size=(77, 3))
+    xp[5] = [3.0, 0.0, 0.0]                       # outside the window (visible by definition)
+    faces = rng.integers(0, 77, size=(150, 3)).astype(np.int32)
+    faces[:10, 1] = faces[:10, 0]                 # zero-area triangles
+    dirs = synth.fibonacci_directions(64)
+    fr = f32(synth.direction_frames(dirs).reshape(-1, 9))
+    for F in (150, 0):
+        ref = O.visibility(f32(xp).astype(np.float64), faces[:F], fr.astype(np.float64), [0, 0, 0], 1.0, 0.03, 64)
+        bits = api.avatar_visibility(T(f32(xp).T), T(faces[:F].reshape(-1, 3), torch.int32), T(fr), [0, 0, 0],
+                                     1.0, 0.03, 64)
+        torch.cuda.synchronize()
+        assert np.array_equal(N(bits).view(np.uint32), ref)
+    # argument errors are reported on the host
+    with pytest.raises(Exception):
+        api.avatar_visibility(T(f32(xp).T), T(faces, torch.int32), T(fr[:30]), [0, 0, 0], 1.0, 0.03, 64)
+
+
+# ---------------------------------------------------------------- (c) shading
+@pytest.mark.parametrize("name", ["c1_small", "c3_fd"])
+def test_shade_matches_oracle(gpu, name):
+    api, render = gpu
+    sc = scene(name)
+    ref = oracle_frame(name)
+    sk = ref["skin"]
+    ins = {k: f32(sk[k]) for k in ("xd", "nd", "ag", "rg", "pg", "ubar")}
+    cam_c = f32(sc.camera.center)
+    light = dict(L=f32(sc.light.L), A=f32(sc.light.A), w=f32(sc.light.w))
+    col_ref, rad_ref, cull_ref = O.shade(*(ins[k].astype(np.float64) for k in ("xd", "nd", "ag", "rg", "pg", "ubar")),
+                                         sc.avatar.knn, ref["bits"], *(light[k].astype(np.float64) for k in "LAw"),
+                                         sc.dmap, cam_c.astype(np.float64), sc.frames.shape[0])
+    bits_l = light_ordered_bits(ref["bits"], sc.dmap)
+    skt = {k: T(v.T if v.ndim == 2 else v) for k, v in ins.items()}
+    lt = {k: T(v) for k, v in light.items()}
+    status = api.status_word("cuda")
+    out = api.avatar_shade(skt, T(sc.avatar.knn.T, torch.int32), T(bits_l.view(np.int32), torch.int32), lt, cam_c,
+                           status=status)
+    torch.cuda.synchronize()
+    api.raise_on_status(status)
+    assert np.array_equal(N(out["cull"]), cull_ref)
+    keep = cull_ref == 0
+    assert np.abs(N(out["color"]).T[keep] - col_ref[keep]).max() < PIX_TOL
+    assert rel_err(N(out["radiance"]).T[keep], rad_ref[keep]) < 5e-5
+
+
+# ---------------------------------------------------------------- (d) splatting
+def _splat_inputs(name):
+    sc = scene(name)
+    ref = oracle_frame(name)
+    sk = ref["skin"]
+    return sc, ref, f32(sk["xd"]), f32(sk["cov"]), f32(sc.avatar.opacity), f32(ref["color"]), ref["cull"]
+
+
+@pytest.mark.parametrize("name", ["c1_small", "c3_fd"])
+def test_project_matches_oracle(gpu, name):
+    api, render = gpu
+    sc, ref, xd, cov, op, col, cull = _splat_inputs(name)
+    pr = O.project(xd.astype(np.float64), cov.astype(np.float64), op.astype(np.float64), cull, sc.camera)
+    b = api.alloc_splat(xd.shape[0], sc.camera)
+    api.avatar_splat_project(T(xd.T), T(cov.T), T(op), T(col.T), T(cull, torch.uint8), sc.camera, b)
+    torch.cuda.synchronize()
+    valid = pr["valid"] == 1
+    assert rel_err(N(b.mean2d).T[valid], pr["mean2d"][valid]) < 1e-6
+    assert rel_err(N(b.conic).T[valid], pr["conic"][valid]) < 1e-4
+    assert rel_err(N(b.depth)[valid], pr["depth"][valid]) < 1e-6
+    rect = N(b.rect).T
+    sure = ~pr["rect_amb"].astype(bool)
+    assert np.array_equal(rect[sure], pr["rect"][sure])
+    assert sure.mean() > 0.97   # four bounds, each within 2e-3 px of an integer with p ~ 4e-3
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_bin_tile_lists_bit_exact(gpu, tile):
+    api, render = gpu
+    sc, ref, xd, cov, op, col, cull = _splat_inputs("c1_small")
+    pr = O.project(xd.astype(np.float64), cov.astype(np.float64), op.astype(np.float64), cull, sc.camera)
+    depth32 = f32(pr["depth"])
+    key = depth32.view(np.uint32).copy()
+    start, lst = O.bin_tiles(pr["rect"], key, sc.camera.width, sc.camera.height, tile)
+    G = xd.shape[0]
+    b = api.alloc_splat(G, sc.camera, tile=tile)
+    b.rect.copy_(T(pr["rect"].T, torch.int32))
+    b.depth.copy_(T(depth32))
+    b.mean2d.copy_(T(f32(pr["mean2d"]).T))
+    b.conic.copy_(T(f32(pr["conic"]).T))
+    status = api.status_word("cuda")
+    api.avatar_splat_bin(T(xd.T), T(cov.T), T(op), T(col.T), T(cull, torch.uint8), sc.camera, b, status=status)
+    torch.cuda.synchronize()
+    api.raise_on_status(status)
+    P = int(N(b.num_pairs)[0])
+    assert P == len(lst)
+    assert np.array_equal(N(b.pair_gauss)[:P], lst)
+    rng_ = N(b.tile_range)
+    assert np.array_equal(rng_[:, 1] - rng_[:, 0], np.diff(start))
+    nonempty = np.diff(start) > 0
+    assert np.array_equal(rng_[nonempty, 0], start[:-1][nonempty])
+
+
+@pytest.mark.parametrize("name,tile", [("c1_small", 16), ("c3_fd", 8), ("c1_small", 32)])
+def test_blend_matches_bruteforce_oracle(gpu, name, tile):
+    api, render = gpu
+    sc, ref, xd, cov, op, col, cull = _splat_inputs(name)
+    pr = O.project(xd.astype(np.float64), cov.astype(np.float64), op.astype(np.float64), cull, sc.camera)
+    m32, c32, d32 = f32(pr["mean2d"]), f32(pr["conic"]), f32(pr["depth"])
+    W, H = sc.camera.width, sc.camera.height
+    rgb, Tf, cnt, amb = O.composite(m32.astype(np.float64), c32.astype(np.float64), op.astype(np.float64),
+                                    col.astype(np.float64), d32.astype(np.float64), pr["valid"], W, H)
+    G = xd.shape[0]
+    b = api.alloc_splat(G, sc.camera, tile=tile)
+    b.rect.copy_(T(pr["rect"].T, torch.int32))
+    b.depth.copy_(T(d32))
+    b.mean2d.copy_(T(m32.T))
+    b.conic.copy_(T(c32.T))
+    args = (T(xd.T), T(cov.T), T(op), T(col.T), T(cull, torch.uint8), sc.camera, b)
+    api.avatar_splat_bin(*args)
+    api.avatar_splat_blend(*args)
+    torch.cuda.synchronize()
+    img = N(b.image).reshape(3, -1).T
+    ok = amb == 0
+    assert ok.mean() > 0.99
+    err = np.abs(img[ok] - rgb[ok]).max()
+    assert err < PIX_TOL, err
+    assert np.abs(N(b.T_final).reshape(-1)[ok] - Tf[ok]).max() < PIX_TOL
+
+
+def test_image_is_tile_size_invariant_and_graph_replay_is_identical(gpu):
+    api, render = gpu
+    st = render.scene_tensors(scene("c1_small"))
+    imgs = []
+    for tile in (8, 16, 32):
+        r = render.Renderer(st, tile=tile)
+        imgs.append(N(r.forward()).copy())
+        r.check()
+    assert np.array_equal(imgs[0], imgs[1]) and np.array_equal(imgs[1], imgs[2])
+    r = render.Renderer(st)
+    eager = N(r.forward()).copy()
+    r.capture()
+    r.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(N(r.sb.image), eager)
+
+
+def test_pair_overflow_is_reported_not_faulted(gpu):
+    api, render = gpu
+    st = render.scene_tensors(scene("c3_fd"))
+    r = render.Renderer(st, pair_capacity=64)
+    torch.cuda.synchronize()
+    assert int(r.status.item()) == 3
+    assert int(N(r.sb.num_pairs)[0]) > 64
+    assert float(N(r.sb.image).max()) == 0.0
+
+
+# ---------------------------------------------------------------- whole frame
+@pytest.mark.parametrize("name", ["c1_small", "c3_fd"])
+def test_frame_end_to_end(gpu, name):
+    api, render = gpu
+    sc = scene(name)
+    ref = oracle_frame(name)
+    st = render.scene_tensors(sc)
+    r = render.Renderer(st)
+    img = N(r.forward()).reshape(3, -1).T
+    r.check()
+    bits_gpu = N(r.bits).view(np.uint32)
+    bits_ref = light_ordered_bits(ref["bits"], sc.dmap)
+    flipped = int((bits_gpu != bits_ref).sum())
+    ok = ref["amb"] == 0
+    bad = np.abs(img - ref["rgb"]).max(axis=1) > PIX_TOL
+    # FP32 skinning moves vertices by ~1 ulp, which may flip a few visibility
+    # bits and cull decisions end to end; everything else agrees to 2e-4.
+    print(f"{name}: {flipped} visibility words differ, {int((bad & ok).sum())} pixels > {PIX_TOL}")
+    assert (bad & ok).mean() < 0.01
+    assert np.abs(img - ref["rgb"]).max() < 0.05
+
+
+# ---------------------------------------------------------------- gradients
+def _fd_problem(gpu):
+    api, render = gpu
+    from oracle import adjoint as AJ
+    sc = scene("c3_fd")
+    ref = oracle_frame("c3_fd")
+    av = sc.avatar
+    rng = np.random.default_rng(5)
+    target = np.clip(ref["rgb"] * rng.uniform(0.8, 1.2, ref["rgb"].shape), 0, None)
+    fixed = dict(knn=av.knn, xv=AJ.t64(av.xv), dxv=AJ.t64(av.dxv), nv=AJ.t64(av.nv), bone=AJ.t64(ref["bone"]),
+                 bits=ref["bits"], dmap=sc.dmap, A=AJ.t64(sc.light.A), w=AJ.t64(sc.light.w),
+                 cam_center=AJ.t64(sc.camera.center), culled=ref["cull"], valid=ref["proj"]["valid"], cam=sc.camera)
+    params = dict(xg=av.xg, logscale=av.logscale, quat=av.quat, opacity=av.opacity, av=av.av, rv=av.rv, pv=av.pv,
+                  L=sc.light.L, wv=av.wv)
+    tp = {k: AJ.t64(v).requires_grad_(True) for k, v in params.items()}
+    img = AJ.render(tp, fixed)
+    loss = AJ.l1_loss(img, AJ.t64(target).reshape(img.shape))
+    loss.backward()
+    return sc, ref, target, {k: v.grad.numpy() for k, v in tp.items()}, float(loss)
+
+
+def test_train_step_gradients_match_fp64_adjoint(gpu):
+    api, render = gpu
+    sc, ref, target, g_ref, loss_ref = _fd_problem(gpu)
+    st = render.scene_tensors(sc)
+    W, H = sc.camera.width, sc.camera.height
+    tgt = T(f32(target).T.reshape(3, H, W))
+    ts = render.TrainStep(st, tgt)
+    loss = float(ts.step().item())
+    torch.cuda.synchronize()
+    ts.check()
+    assert abs(loss - loss_ref) < 1e-3 * abs(loss_ref) + 1e-6
+    g = {k: N(v) for k, v in ts.grads().items()}
+    pairs = dict(xg=(g["xg"].T, g_ref["xg"]), logscale=(g["logscale"].T, g_ref["logscale"]),
+                 quat=(g["quat"].T, g_ref["quat"]), opacity=(g["opacity"], g_ref["opacity"]),
+                 av=(g["av"].T, g_ref["av"]), rv=(g["rv"], g_ref["rv"]), pv=(g["pv"], g_ref["pv"]),
+                 L=(g["L"], g_ref["L"]), wv=(g["wv"], g_ref["wv"]))
+    for k, (got, want) in pairs.items():
+        e = rel_err(got, want)
+        assert e < 1e-3, f"{k}: relative error {e}"
+
+
+def test_autograd_wrappers_match_train_step(gpu):
+    api, render = gpu
+    sc = scene("c3_fd")
+    ref = oracle_frame("c3_fd")
+    st = render.scene_tensors(sc)
+    t = st["avatar"]
+    r = render.Renderer(st)
+    bits = r.bits.clone()
+    params = {k: t[k].clone().requires_grad_(True) for k in ("xg", "logscale", "quat", "opacity", "wv", "av", "rv",
+                                                               "pv")}
+    params["L"] = st["light"]["L"].clone().requires_grad_(True)
+    img = render.render_differentiable(params, st, bits)
+    tgt = torch.zeros_like(img)
+    loss = render.L1Fn.apply(img, tgt)
+    loss.backward()
+    ts = render.TrainStep(st, tgt)
+    ts.step()
+    torch.cuda.synchronize()
+    g = ts.grads()
+    for k in ("xg", "logscale", "quat", "opacity", "wv", "av", "rv", "pv", "L"):
+        assert rel_err(N(params[k].grad), N(g[k])) < 1e-4, k
+    np.testing.assert_allclose(float(loss), float(ts.loss.item()), rtol=1e-6)
