@@ -118,7 +118,7 @@ def run_gpu(args):
     STM = sys.modules[__name__]
 
     dev = torch.device("cuda", local)
-    sc = synth.config_scene(WORKLOAD)
+    sc = synth.config_scene(args.workload)
     st = render.scene_tensors(sc, dev)
     G, Nv, F = sc.avatar.G, sc.avatar.Nv, sc.avatar.F
     NL, D, R = len(sc.light.A), sc.frames.shape[0], sc.depth_res
@@ -205,6 +205,8 @@ def run_gpu(args):
     }
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(sc, budget_s=args.cpu_budget)
+    if args.workload != WORKLOAD:
+        line["config"]["workload"] = args.workload
     print(json.dumps(line), flush=True)
 
 
@@ -432,6 +434,7 @@ def main():
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--workload", default=WORKLOAD, help="named synthetic configuration (profiling uses smaller ones)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

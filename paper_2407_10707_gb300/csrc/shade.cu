@@ -17,13 +17,15 @@ constexpr float FRES_C1 = -5.55473f;
 constexpr float FRES_C0 = -6.98316f;
 constexpr float INV_GAMMA = 1.0f / 2.2f;
 
+template <int K>
 struct GaussIn {
     float x[3], n[3], a[3], r, p;
-    float ub[8];
-    int nb[8];
+    float ub[K];
+    int nb[K];
 };
 
-__device__ __forceinline__ void load_gauss(const avatar_shade_args &s, int g, GaussIn &q)
+template <int K>
+__device__ __forceinline__ bool load_gauss(const avatar_shade_args &s, int g, GaussIn<K> &q)
 {
     const int G = s.G;
 #pragma unroll
@@ -34,16 +36,14 @@ __device__ __forceinline__ void load_gauss(const avatar_shade_args &s, int g, Ga
     }
     q.r = __ldg(s.rg + g);
     q.p = __ldg(s.pg + g);
+    bool ok = true;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        if (j < s.K) {
-            q.ub[j] = __ldg(s.ubar + (size_t)j * G + g);
-            q.nb[j] = __ldg(s.knn + (size_t)j * G + g);
-        } else {
-            q.ub[j] = 0.f;
-            q.nb[j] = -1;
-        }
+    for (int j = 0; j < K; ++j) {
+        q.ub[j] = __ldg(s.ubar + (size_t)j * G + g);
+        q.nb[j] = __ldg(s.knn + (size_t)j * G + g);
+        if ((unsigned)q.nb[j] >= (unsigned)s.Nv) ok = false;
     }
+    return ok;
 }
 
 // Exact FP32 back-face decision (identical operation order to the header).
@@ -61,7 +61,8 @@ struct Frame {
     float inv_len;
 };
 
-__device__ __forceinline__ Frame view_frame(const GaussIn &q, const float *C)
+template <int K>
+__device__ __forceinline__ Frame view_frame(const GaussIn<K> &q, const float *C)
 {
     Frame f;
     float v0 = C[0] - q.x[0], v1 = C[1] - q.x[1], v2 = C[2] - q.x[2];
@@ -79,21 +80,47 @@ __device__ __forceinline__ Frame view_frame(const GaussIn &q, const float *C)
     return f;
 }
 
-// Visibility bit of neighbour j for this lane's light in the current chunk.
-__device__ __forceinline__ float lane_vis(const unsigned *words, const GaussIn &q, int K, int lane)
+// Neighbour visibility words of one 32-light chunk (warp-uniform loads) and
+// their AND / OR, which settle vis = 1 / vis = 0 without per-bit work.
+template <int K>
+struct ChunkBits {
+    unsigned w[K];
+    unsigned all, any;
+};
+
+template <int K>
+__device__ __forceinline__ void load_chunk(const avatar_shade_args &s, const GaussIn<K> &q, int OW, int ch,
+                                           ChunkBits<K> &cb)
 {
+    cb.all = 0xffffffffu;
+    cb.any = 0u;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        cb.w[j] = __ldg(s.bits + (size_t)q.nb[j] * OW + ch);
+        cb.all &= cb.w[j];
+        cb.any |= cb.w[j];
+    }
+}
+
+// vis = sum_j ubar_j bit_j for this lane's light (Eq. 1 applied to v).
+template <int K>
+__device__ __forceinline__ float lane_vis(const ChunkBits<K> &cb, const GaussIn<K> &q, unsigned bit)
+{
+    if (cb.all & bit) return 1.0f;  // sum of the normalised Eq. 1 weights
+    if (!(cb.any & bit)) return 0.0f;
     float vis = 0.f;
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-        if (j < K && ((words[j] >> lane) & 1u)) vis += q.ub[j];
+    for (int j = 0; j < K; ++j)
+        if (cb.w[j] & bit) vis += q.ub[j];
     return vis;
 }
 
+template <int K>
 __global__ void __launch_bounds__(SHADE_THREADS)
 shade_kernel(avatar_shade_args s)
 {
     extern __shared__ float4 lsm[];  // [NL] (w, 0) then [NL] (L*A, 0)
-    const int NL = s.NL, G = s.G, K = s.K;
+    const int NL = s.NL, G = s.G;
     float4 *lw = lsm, *lb = lsm + NL;
     for (int k = threadIdx.x; k < NL; k += blockDim.x) {
         float A = __ldg(s.light_A + k);
@@ -103,73 +130,59 @@ shade_kernel(avatar_shade_args s)
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    const unsigned bit = 1u << lane;
     const int OW = (NL + 31) / 32;
     const int warps_total = gridDim.x * (blockDim.x >> 5);
     const float C[3] = {s.cam_center[0], s.cam_center[1], s.cam_center[2]};
     for (int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < G; g += warps_total) {
-        GaussIn q;
-        load_gauss(s, g, q);
-        bool bad = false;
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (j < K && (unsigned)q.nb[j] >= (unsigned)s.Nv) bad = true;
-        if (bad && lane == 0) av_report(s.status, AVATAR_ERR_INDEX);
-        if (is_culled(q.x, q.n, C) || bad) {
-            if (lane == 0) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    s.color[(size_t)c * G + g] = 0.f;
-                    if (s.radiance) s.radiance[(size_t)c * G + g] = 0.f;
-                }
-                if (s.cull) s.cull[g] = 1;
+        GaussIn<K> q;
+        bool ok = load_gauss<K>(s, g, q);
+        if (!ok && lane == 0) av_report(s.status, AVATAR_ERR_INDEX);
+        if (is_culled(q.x, q.n, C) || !ok) {
+            if (lane < 3) {
+                s.color[(size_t)lane * G + g] = 0.f;
+                if (s.radiance) s.radiance[(size_t)lane * G + g] = 0.f;
             }
+            if (lane == 0 && s.cull) s.cull[g] = 1;
             continue;
         }
-        Frame f = view_frame(q, C);
+        Frame f = view_frame<K>(q, C);
         const float spec_scale = f.a2 / (4.f * AV_PI * f.Go);
-        float E0 = 0.f, E1 = 0.f, E2 = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f;
+        const float a2m1 = f.a2 - 1.f, omk = 1.f - f.kk;
+        const float ia0 = q.a[0] * (1.f / AV_PI), ia1 = q.a[1] * (1.f / AV_PI), ia2 = q.a[2] * (1.f / AV_PI);
+        float L0 = 0.f, L1 = 0.f, L2 = 0.f;  // this lane's share of L_o
         for (int ch = 0; ch < OW; ++ch) {
-            unsigned words[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) words[j] = (j < K) ? __ldg(s.bits + (size_t)q.nb[j] * OW + ch) : 0u;
+            ChunkBits<K> cb;
+            load_chunk<K>(s, q, OW, ch, cb);
             const int k = ch * 32 + lane;
-            if (k >= NL) continue;
+            if (k >= NL || !(cb.any & bit)) continue;
             float4 w = lw[k];
             float ci = q.n[0] * w.x + q.n[1] * w.y + q.n[2] * w.z;
             if (!(ci > 0.f)) continue;
-            float vis = lane_vis(words, q, K, lane);
-            if (vis == 0.f) continue;
+            float fw = lane_vis<K>(cb, q, bit) * ci;
             float4 B = lb[k];
-            float fw = vis * ci;
-            E0 = fmaf(B.x, fw, E0);
-            E1 = fmaf(B.y, fw, E1);
-            E2 = fmaf(B.z, fw, E2);
             float dwo = w.x * f.wo[0] + w.y * f.wo[1] + w.z * f.wo[2];
+            float fs = 0.f;
             float len2 = 2.f + 2.f * dwo;
             if (len2 > 0.f) {
                 float rinv = rsqrtf(len2);
                 float nh = (ci + f.co_raw) * rinv;
                 float voh = (1.f + dwo) * rinv;
-                float den = fmaf(nh * nh, f.a2 - 1.f, 1.f);
+                float den = fmaf(nh * nh, a2m1, 1.f);
                 float Fr = fmaf(0.96f, exp2f(fmaf(FRES_C1, voh, FRES_C0) * voh), 0.04f);
-                float Gi = fmaf(ci, 1.f - f.kk, f.kk);
-                float fs = spec_scale * Fr / (den * den * Gi);
-                float sw = fw * fs;
-                S0 = fmaf(B.x, sw, S0);
-                S1 = fmaf(B.y, sw, S1);
-                S2 = fmaf(B.z, sw, S2);
+                float Gi = fmaf(ci, omk, f.kk);
+                fs = spec_scale * __fdividef(Fr, den * den * Gi);
             }
+            float ps = q.p * fs;
+            L0 = fmaf(B.x * fw, ia0 + ps, L0);
+            L1 = fmaf(B.y * fw, ia1 + ps, L1);
+            L2 = fmaf(B.z * fw, ia2 + ps, L2);
         }
-        E0 = warp_sum(E0);
-        E1 = warp_sum(E1);
-        E2 = warp_sum(E2);
-        S0 = warp_sum(S0);
-        S1 = warp_sum(S1);
-        S2 = warp_sum(S2);
+        L0 = warp_sum(L0);
+        L1 = warp_sum(L1);
+        L2 = warp_sum(L2);
         if (lane < 3) {
-            float E = lane == 0 ? E0 : (lane == 1 ? E1 : E2);
-            float S = lane == 0 ? S0 : (lane == 1 ? S1 : S2);
-            float Lo = q.a[lane] * (1.f / AV_PI) * E + q.p * S;
+            float Lo = lane == 0 ? L0 : (lane == 1 ? L1 : L2);
             float col = exp2f(log2f(fmaxf(Lo, 1e-6f)) * INV_GAMMA);
             s.color[(size_t)lane * G + g] = col;
             if (s.radiance) s.radiance[(size_t)lane * G + g] = Lo;
@@ -179,11 +192,12 @@ shade_kernel(avatar_shade_args s)
 }
 
 // ---------------------------------------------------------------- backward
+template <int K>
 __global__ void __launch_bounds__(SHADE_THREADS)
 shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr)
 {
-    extern __shared__ float4 lsm[];  // [NL] (w,A) ; [NL] (L*A) ; [NL] dB accum (3 floats)
-    const int NL = s.NL, G = s.G, K = s.K;
+    extern __shared__ float4 lsm[];  // [NL] (w, A) ; [NL] (L*A) ; [NL][3] dL/dB accumulators
+    const int NL = s.NL, G = s.G;
     float4 *lw = lsm, *lb = lsm + NL;
     float *dB = reinterpret_cast<float *>(lsm + 2 * NL);
     for (int k = threadIdx.x; k < NL; k += blockDim.x) {
@@ -195,25 +209,21 @@ shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr)
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    const unsigned bit = 1u << lane;
     const int OW = (NL + 31) / 32;
     const int warps_total = gridDim.x * (blockDim.x >> 5);
     const float C[3] = {s.cam_center[0], s.cam_center[1], s.cam_center[2]};
     for (int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < G; g += warps_total) {
-        GaussIn q;
-        load_gauss(s, g, q);
-        bool bad = false;
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (j < K && (unsigned)q.nb[j] >= (unsigned)s.Nv) bad = true;
+        GaussIn<K> q;
+        bool ok = load_gauss<K>(s, g, q);
         float dLo[3];
-        bool culled = is_culled(q.x, q.n, C) || bad;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             float Lo = __ldg(s.radiance + (size_t)c * G + g);
             float dc = __ldg(gr.d_color + (size_t)c * G + g);
             dLo[c] = (Lo > 1e-6f) ? dc * INV_GAMMA * exp2f(log2f(Lo) * (INV_GAMMA - 1.f)) : 0.f;
         }
-        if (culled || (dLo[0] == 0.f && dLo[1] == 0.f && dLo[2] == 0.f)) {
+        if (!ok || is_culled(q.x, q.n, C) || (dLo[0] == 0.f && dLo[1] == 0.f && dLo[2] == 0.f)) {
             if (lane < 3) {
                 gr.d_xd[(size_t)lane * G + g] = 0.f;
                 gr.d_nd[(size_t)lane * G + g] = 0.f;
@@ -226,26 +236,25 @@ shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr)
             if (lane < K) gr.d_ubar[(size_t)lane * G + g] = 0.f;
             continue;
         }
-        Frame f = view_frame(q, C);
+        Frame f = view_frame<K>(q, C);
         const float spec_scale = f.a2 / (4.f * AV_PI * f.Go);
+        const float a2m1 = f.a2 - 1.f, omk = 1.f - f.kk;
         const float ia0 = q.a[0] * (1.f / AV_PI), ia1 = q.a[1] * (1.f / AV_PI), ia2 = q.a[2] * (1.f / AV_PI);
         float E0 = 0.f, E1 = 0.f, E2 = 0.f;
         float dnv0 = 0.f, dnv1 = 0.f, dnv2 = 0.f, dwv0 = 0.f, dwv1 = 0.f, dwv2 = 0.f;
         float dco = 0.f, da2 = 0.f, dkk = 0.f, dp = 0.f;
-        float dub[8];
+        float dub[K];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) dub[j] = 0.f;
+        for (int j = 0; j < K; ++j) dub[j] = 0.f;
         for (int ch = 0; ch < OW; ++ch) {
-            unsigned words[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) words[j] = (j < K) ? __ldg(s.bits + (size_t)q.nb[j] * OW + ch) : 0u;
+            ChunkBits<K> cb;
+            load_chunk<K>(s, q, OW, ch, cb);
             const int k = ch * 32 + lane;
-            if (k >= NL) continue;
+            if (k >= NL || !(cb.any & bit)) continue;
             float4 w = lw[k];
             float ci = q.n[0] * w.x + q.n[1] * w.y + q.n[2] * w.z;
             if (!(ci > 0.f)) continue;
-            float vis = lane_vis(words, q, K, lane);
-            if (vis == 0.f) continue;
+            float vis = lane_vis<K>(cb, q, bit);
             float4 B = lb[k];
             float Q = dLo[0] * B.x + dLo[1] * B.y + dLo[2] * B.z;
             float Qa = ia0 * dLo[0] * B.x + ia1 * dLo[1] * B.y + ia2 * dLo[2] * B.z;
@@ -260,25 +269,25 @@ shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr)
                 float rinv = rsqrtf(len2);
                 float nh = (ci + f.co_raw) * rinv;
                 float voh = (1.f + dwo) * rinv;
-                float den = fmaf(nh * nh, f.a2 - 1.f, 1.f);
+                float den = fmaf(nh * nh, a2m1, 1.f);
                 float ex = exp2f(fmaf(FRES_C1, voh, FRES_C0) * voh);
                 float Fr = fmaf(0.96f, ex, 0.04f);
-                float Gi = fmaf(ci, 1.f - f.kk, f.kk);
-                float base = spec_scale / (den * den * Gi);  // fs / Fr
+                float Gi = fmaf(ci, omk, f.kk);
+                float base = spec_scale * __fdividef(1.f, den * den * Gi);  // fs / Fr
                 fs = base * Fr;
                 float dfs = fw * q.p * Q;
-                dp += fw * fs * Q;
+                dp = fmaf(fw * fs, Q, dp);
                 // fs = a2 Fr / (4 pi den^2 Gi Go)
                 float dFr = dfs * base;
-                float dden = -2.f * dfs * fs / den;
-                float dGi = -dfs * fs / Gi;
-                float dGo = -dfs * fs / f.Go;
-                da2 += dfs * fs / f.a2 + dden * nh * nh;
-                float dnh = dden * 2.f * nh * (f.a2 - 1.f);
+                float dden = -2.f * dfs * fs * __fdividef(1.f, den);
+                float dGi = -dfs * fs * __fdividef(1.f, Gi);
+                float dGo = -dfs * fs * __fdividef(1.f, f.Go);
+                da2 += dfs * fs * __fdividef(1.f, f.a2) + dden * nh * nh;
+                float dnh = dden * 2.f * nh * a2m1;
                 float dvoh = dFr * 0.96f * ex * 0.69314718056f * (2.f * FRES_C1 * voh + FRES_C0);
-                dci += dGi * (1.f - f.kk);
+                dci += dGi * omk;
                 dkk += dGi * (1.f - ci) + dGo * (1.f - f.co);
-                if (f.co_raw > 0.f) dco += dGo * (1.f - f.kk);
+                if (f.co_raw > 0.f) dco += dGo * omk;
                 dci += dnh * rinv;
                 dco += dnh * rinv;
                 float drinv = dnh * (ci + f.co_raw) + dvoh * (1.f + dwo);
@@ -291,15 +300,16 @@ shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr)
             dci += vis * term;
             float dvis = ci * term;
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (j < K && ((words[j] >> lane) & 1u)) dub[j] += dvis;
+            for (int j = 0; j < K; ++j)
+                if (cb.w[j] & bit) dub[j] += dvis;
             dnv0 = fmaf(dci, w.x, dnv0);
             dnv1 = fmaf(dci, w.y, dnv1);
             dnv2 = fmaf(dci, w.z, dnv2);
             // dL/dB_kc = dLo_c vis ci (a_c/pi + p fs)
-            atomicAdd(dB + 3 * k, dLo[0] * fw * (ia0 + q.p * fs));
-            atomicAdd(dB + 3 * k + 1, dLo[1] * fw * (ia1 + q.p * fs));
-            atomicAdd(dB + 3 * k + 2, dLo[2] * fw * (ia2 + q.p * fs));
+            float ps = q.p * fs;
+            atomicAdd(dB + 3 * k, dLo[0] * fw * (ia0 + ps));
+            atomicAdd(dB + 3 * k + 1, dLo[1] * fw * (ia1 + ps));
+            atomicAdd(dB + 3 * k + 2, dLo[2] * fw * (ia2 + ps));
         }
         E0 = warp_sum(E0);
         E1 = warp_sum(E1);
@@ -315,8 +325,7 @@ shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr)
         dkk = warp_sum(dkk);
         dp = warp_sum(dp);
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (j < K) dub[j] = warp_sum(dub[j]);
+        for (int j = 0; j < K; ++j) dub[j] = warp_sum(dub[j]);
         if (lane == 0) {
             float dn[3] = {dnv0 + dco * f.wo[0], dnv1 + dco * f.wo[1], dnv2 + dco * f.wo[2]};
             float dw[3] = {dwv0 + dco * q.n[0], dwv1 + dco * q.n[1], dwv2 + dco * q.n[2]};
@@ -333,8 +342,7 @@ shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr)
             gr.d_rg[g] = da2 * 4.f * alpha * q.r + dkk * (q.r + 1.f) * 0.25f;
             gr.d_pg[g] = dp;
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (j < K) gr.d_ubar[(size_t)j * G + g] = dub[j];
+            for (int j = 0; j < K; ++j) gr.d_ubar[(size_t)j * G + g] = dub[j];
         }
     }
     __syncthreads();
@@ -346,6 +354,29 @@ shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr)
             if (v != 0.f) atomicAdd(gr.d_light_L + 3 * k + c, v * A);
         }
     }
+}
+
+template <int K>
+int launch_shade(const avatar_shade_args &a, int grid, size_t smem, cudaStream_t st)
+{
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(shade_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return AVATAR_ERR_CUDA;
+    shade_kernel<K><<<grid, SHADE_THREADS, smem, st>>>(a);
+    AV_CHECK_LAUNCH();
+    return AVATAR_OK;
+}
+
+template <int K>
+int launch_shade_bwd(const avatar_shade_args &a, const avatar_shade_grads &g, int grid, size_t smem,
+                     cudaStream_t st)
+{
+    if (smem > 48 * 1024 && cudaFuncSetAttribute(shade_backward_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem) != cudaSuccess)
+        return AVATAR_ERR_CUDA;
+    shade_backward_kernel<K><<<grid, SHADE_THREADS, smem, st>>>(a, g);
+    AV_CHECK_LAUNCH();
+    return AVATAR_OK;
 }
 
 int check_shade(const avatar_shade_args *a)
@@ -376,12 +407,18 @@ extern "C" int avatar_shade(avatar_ctx *ctx, const avatar_shade_args *a, avatar_
     AV_TRY(check_shade(a));
     if (a->G == 0) return AVATAR_OK;
     size_t smem = (size_t)2 * a->NL * sizeof(float4);
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(shade_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return AVATAR_ERR_CUDA;
-    shade_kernel<<<shade_grid(ctx, a->G), SHADE_THREADS, smem, (cudaStream_t)stream>>>(*a);
-    AV_CHECK_LAUNCH();
-    return AVATAR_OK;
+    int grid = shade_grid(ctx, a->G);
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (a->K) {
+        case 1: return launch_shade<1>(*a, grid, smem, st);
+        case 2: return launch_shade<2>(*a, grid, smem, st);
+        case 3: return launch_shade<3>(*a, grid, smem, st);
+        case 4: return launch_shade<4>(*a, grid, smem, st);
+        case 5: return launch_shade<5>(*a, grid, smem, st);
+        case 6: return launch_shade<6>(*a, grid, smem, st);
+        case 7: return launch_shade<7>(*a, grid, smem, st);
+        default: return launch_shade<8>(*a, grid, smem, st);
+    }
 }
 
 extern "C" int avatar_shade_backward(avatar_ctx *ctx, const avatar_shade_args *a, const avatar_shade_grads *g,
@@ -397,11 +434,15 @@ extern "C" int avatar_shade_backward(avatar_ctx *ctx, const avatar_shade_args *a
         return AVATAR_ERR_CUDA;
     if (a->G == 0) return AVATAR_OK;
     size_t smem = (size_t)2 * a->NL * sizeof(float4) + (size_t)3 * a->NL * sizeof(float);
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(shade_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-        return AVATAR_ERR_CUDA;
-    shade_backward_kernel<<<shade_grid(ctx, a->G), SHADE_THREADS, smem, st>>>(*a, *g);
-    AV_CHECK_LAUNCH();
-    return AVATAR_OK;
+    int grid = shade_grid(ctx, a->G);
+    switch (a->K) {
+        case 1: return launch_shade_bwd<1>(*a, *g, grid, smem, st);
+        case 2: return launch_shade_bwd<2>(*a, *g, grid, smem, st);
+        case 3: return launch_shade_bwd<3>(*a, *g, grid, smem, st);
+        case 4: return launch_shade_bwd<4>(*a, *g, grid, smem, st);
+        case 5: return launch_shade_bwd<5>(*a, *g, grid, smem, st);
+        case 6: return launch_shade_bwd<6>(*a, *g, grid, smem, st);
+        case 7: return launch_shade_bwd<7>(*a, *g, grid, smem, st);
+        default: return launch_shade_bwd<8>(*a, *g, grid, smem, st);
+    }
 }

@@ -56,8 +56,9 @@ struct SplatWs {
     int32_t *offsets;            // [G]
     uint32_t *pkey_a, *pkey_b;   // [cap] tile keys
     int32_t *pval_b;             // [cap] ping-pong partner of pair_gauss
-    float4 *rec0, *rec1;         // [G]
-    float *rec2;                 // [G]
+    float4 *rec0;                // [G] (mx, my, qa, qb): log2-domain conic, see bin_keys_kernel
+    float2 *rec1;                // [G] (qc, log2 o)
+    float4 *rec2;                // [G] (r, g, b, o)
     int32_t *hist;               // [RADIX][NB]
     int32_t *totals;             // [RADIX]
     int32_t *block_sums;         // [NB]
@@ -87,8 +88,8 @@ size_t splat_ws_layout(const avatar_splat_args *a, int NB, void *base, size_t ca
     w.pkey_b = c.take<uint32_t>(P);
     w.pval_b = c.take<int32_t>(P);
     w.rec0 = c.take<float4>(G);
-    w.rec1 = c.take<float4>(G);
-    w.rec2 = c.take<float>(G);
+    w.rec1 = c.take<float2>(G);
+    w.rec2 = c.take<float4>(G);
     w.hist = c.take<int32_t>((size_t)RADIX * NB);
     w.totals = c.take<int32_t>(RADIX);
     w.block_sums = c.take<int32_t>((size_t)NB);
@@ -179,7 +180,10 @@ project_kernel(avatar_splat_args a, CamDev cam)
 
 // Per-Gaussian pair count, depth key and packed blend record, from the
 // caller-visible projection buffers (rect, depth, mean2d, conic) and the
-// opacity and colour.
+// opacity and colour.  The record holds the conic in log2 units,
+//   log2(alpha_raw) = qa dx^2 + qb dx dy + qc dy^2 + log2 o
+// with qa = -a/2 log2(e), qb = -b log2(e), qc = -c/2 log2(e), so that a pixel
+// rejects a Gaussian (alpha < 1/255) with a few FMAs and no exponential.
 __global__ void __launch_bounds__(256)
 bin_keys_kernel(avatar_splat_args a, int TS, SplatWs w)
 {
@@ -192,9 +196,11 @@ bin_keys_kernel(avatar_splat_args a, int TS, SplatWs w)
         w.npairs[g] = n;
         w.dkey_a[g] = n > 0 ? __float_as_uint(a.depth[g]) : 0xffffffffu;
         w.dval_a[g] = g;
-        w.rec0[g] = make_float4(a.mean2d[g], a.mean2d[G + g], a.conic[g], a.conic[G + g]);
-        w.rec1[g] = make_float4(a.conic[2 * G + g], a.opacity[g], a.color[g], a.color[G + g]);
-        w.rec2[g] = a.color[2 * G + g];
+        const float L2E = 1.4426950408889634f;
+        float o = a.opacity[g];
+        w.rec0[g] = make_float4(a.mean2d[g], a.mean2d[G + g], -0.5f * L2E * a.conic[g], -L2E * a.conic[G + g]);
+        w.rec1[g] = make_float2(-0.5f * L2E * a.conic[2 * G + g], o > 0.f ? log2f(o) : -1e30f);
+        w.rec2[g] = make_float4(a.color[g], a.color[G + g], a.color[2 * G + g], o);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *w.count_g = G;
 }
@@ -435,16 +441,18 @@ tile_ranges_kernel(const uint32_t *__restrict__ keys, const int32_t *__restrict_
 }
 
 // ---------------------------------------------------------------- blend
+constexpr float LOG2_ALPHA_MIN = -7.99435343685886f;  // log2(1/255)
+
 template <int TS>
 __global__ void __launch_bounds__(TS *TS)
 blend_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_gauss, const float4 *__restrict__ rec0,
-             const float4 *__restrict__ rec1, const float *__restrict__ rec2, int W, int H, int ntx,
+             const float2 *__restrict__ rec1, const float4 *__restrict__ rec2, int W, int H, int ntx,
              float *__restrict__ image, float *__restrict__ T_final, int32_t *__restrict__ n_last)
 {
     constexpr int NT = TS * TS;
     __shared__ float4 s0[NT];
-    __shared__ float4 s1[NT];
-    __shared__ float s2[NT];
+    __shared__ float2 s1[NT];
+    __shared__ float4 s2[NT];
     const int tile = blockIdx.x;
     const int tx = tile % ntx, ty = tile / ntx;
     const int tid = threadIdx.x;
@@ -470,20 +478,21 @@ blend_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_g
             int m = min(NT, n - base);
             for (int j = 0; j < m; ++j) {
                 float4 r0 = s0[j];
-                float4 r1 = s1[j];
+                float2 r1 = s1[j];
                 float dx = fx - r0.x, dy = fy - r0.y;
-                float power = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
-                float alpha = fminf(0.99f, r1.y * __expf(power));
-                if (alpha < ALPHA_MIN) continue;
+                float l2a = fmaf(fmaf(r0.z, dx, r0.w * dy), dx, fmaf(r1.x * dy, dy, r1.y));
+                if (l2a < LOG2_ALPHA_MIN) continue;
+                float alpha = fminf(0.99f, exp2f(l2a));
                 float test_T = T * (1.f - alpha);
                 if (test_T < T_MIN) {
                     done = true;
                     break;
                 }
+                float4 c = s2[j];
                 float wgt = alpha * T;
-                C0 = fmaf(r1.z, wgt, C0);
-                C1 = fmaf(r1.w, wgt, C1);
-                C2 = fmaf(s2[j], wgt, C2);
+                C0 = fmaf(c.x, wgt, C0);
+                C1 = fmaf(c.y, wgt, C1);
+                C2 = fmaf(c.z, wgt, C2);
                 T = test_T;
                 last = base + j + 1;
             }
@@ -503,15 +512,16 @@ blend_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_g
 template <int TS>
 __global__ void __launch_bounds__(TS *TS)
 blend_backward_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_gauss,
-                      const float4 *__restrict__ rec0, const float4 *__restrict__ rec1, const float *__restrict__ rec2,
+                      const float4 *__restrict__ rec0, const float2 *__restrict__ rec1, const float4 *__restrict__ rec2,
                       int W, int H, int ntx, const float *__restrict__ T_final, const int32_t *__restrict__ n_last,
                       const float *__restrict__ d_image, int G, float *__restrict__ d_mean2d,
                       float *__restrict__ d_conic, float *__restrict__ d_opacity, float *__restrict__ d_color)
 {
     constexpr int NT = TS * TS;
+    constexpr float LN2 = 0.6931471805599453f;
     __shared__ float4 s0[NT];
-    __shared__ float4 s1[NT];
-    __shared__ float s2[NT];
+    __shared__ float2 s1[NT];
+    __shared__ float4 s2[NT];
     __shared__ int sg[NT];
     __shared__ int s_max;
     const int tile = blockIdx.x;
@@ -551,33 +561,34 @@ blend_backward_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict
         for (int j = end - 1; j >= start; --j) {
             const int sj = j - start;
             float4 r0 = s0[sj];
-            float4 r1 = s1[sj];
+            float2 r1 = s1[sj];
             float g_col0 = 0.f, g_col1 = 0.f, g_col2 = 0.f, g_op = 0.f, g_mx = 0.f, g_my = 0.f, g_ca = 0.f,
                   g_cb = 0.f, g_cc = 0.f;
             bool contrib = false;
             if (j < my_last) {
                 float dx = fx - r0.x, dy = fy - r0.y;
-                float power = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
-                float ex = __expf(power);
-                float raw = r1.y * ex;
-                float alpha = fminf(0.99f, raw);
-                if (alpha >= ALPHA_MIN) {
+                float l2a = fmaf(fmaf(r0.z, dx, r0.w * dy), dx, fmaf(r1.x * dy, dy, r1.y));
+                if (l2a >= LOG2_ALPHA_MIN) {
+                    float raw = exp2f(l2a);
+                    float alpha = fminf(0.99f, raw);
                     contrib = true;
-                    float c2 = s2[sj];
+                    float4 c = s2[sj];
                     T = T / (1.f - alpha);
                     float wgt = alpha * T;
                     g_col0 = wgt * dC0;
                     g_col1 = wgt * dC1;
                     g_col2 = wgt * dC2;
-                    float dalpha = T * ((r1.z - acc0) * dC0 + (r1.w - acc1) * dC1 + (c2 - acc2) * dC2);
-                    acc0 = alpha * r1.z + (1.f - alpha) * acc0;
-                    acc1 = alpha * r1.w + (1.f - alpha) * acc1;
-                    acc2 = alpha * c2 + (1.f - alpha) * acc2;
+                    float dalpha = T * ((c.x - acc0) * dC0 + (c.y - acc1) * dC1 + (c.z - acc2) * dC2);
+                    acc0 = alpha * c.x + (1.f - alpha) * acc0;
+                    acc1 = alpha * c.y + (1.f - alpha) * acc1;
+                    acc2 = alpha * c.z + (1.f - alpha) * acc2;
                     if (raw < 0.99f) {
-                        g_op = dalpha * ex;
-                        float dpow = dalpha * alpha;
-                        g_mx = dpow * (r0.z * dx + r0.w * dy);
-                        g_my = dpow * (r0.w * dx + r1.x * dy);
+                        g_op = dalpha * raw / c.w;  // d alpha / d o = exp(power)
+                        float dpow = dalpha * raw;  // d alpha / d power = alpha
+                        // conic (a, b, c) from the log2-domain record
+                        float ca = -2.f * LN2 * r0.z, cb = -LN2 * r0.w, cc = -2.f * LN2 * r1.x;
+                        g_mx = dpow * (ca * dx + cb * dy);
+                        g_my = dpow * (cb * dx + cc * dy);
                         g_ca = -0.5f * dx * dx * dpow;
                         g_cb = -dx * dy * dpow;
                         g_cc = -0.5f * dy * dy * dpow;

@@ -22,13 +22,14 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int VIS_THREADS = 512;
+constexpr int VIS_THREADS = 256;
 constexpr int EMPTY_DEPTH = 0x7fffffff;
 
 struct VisParams {
     int Nv, F, D, R, NW;
     int H, M, biasq;
     int rows_per_cta;
+    int inv_rows;  // ceil(2^20 / rows_per_cta): row / rows_per_cta == (row * inv_rows) >> 20 for row < 2^11
 };
 
 __global__ void vis_quantize_kernel(const float *__restrict__ xp, int Nv, int qc0, int qc1, int qc2,
@@ -71,34 +72,129 @@ __device__ __forceinline__ Proj project_vertex(int4 q, const int *B, const VisPa
 // integer remainders.
 __device__ __forceinline__ int floor_div_small(long long num, int den)
 {
-    long long q = (long long)floorf(__fdiv_rn((float)num, (float)den));
-    long long r = num - q * (long long)den;
-#pragma unroll
-    for (int it = 0; it < 2; ++it)
+    // estimate (|error| < 1.5), then the exact remainder decides the last step
+    int q = (int)floorf(__fdividef((float)num, (float)den));
+    int r = (int)(num - (long long)q * den);  // |r| < 3 den < 2^30
+    if (r < 0) {
+        --q;
+        r += den;
         if (r < 0) {
             --q;
             r += den;
         }
-#pragma unroll
-    for (int it = 0; it < 2; ++it)
-        if (r >= den) {
-            ++q;
-            r -= den;
+    } else if (r >= den) {
+        ++q;
+        r -= den;
+        if (r >= den) ++q;
+    }
+    return q;
+}
+
+// Packed projected vertex for the shared-memory cache: X | Y << 16 (0xffffffff
+// = outside the window) and Z.
+constexpr unsigned OUTSIDE = 0xffffffffu;
+constexpr int VIS_CHUNK = 1024;                 // triangles per CTA per chunk
+constexpr int VIS_TPT = VIS_CHUNK / VIS_THREADS; // triangles per thread per chunk
+constexpr int VIS_VCAP = 2048;                   // cached projected vertices per chunk
+constexpr int VIS_SLAB_BYTES = 32 * 1024;        // depth-map share of one CTA (R <= 256)
+
+__device__ __forceinline__ uint2 pack_proj(const Proj &q)
+{
+    return make_uint2(q.in ? ((unsigned)q.X | ((unsigned)q.Y << 16)) : OUTSIDE, (unsigned)q.Z);
+}
+
+template <int CL>
+__device__ __forceinline__ void raster_triangle(uint2 pa, uint2 pb, uint2 pc, int *slab, const VisParams &p,
+                                                cg::cluster_group &cluster)
+{
+    if (pa.x == OUTSIDE || pb.x == OUTSIDE || pc.x == OUTSIDE) return;
+    int ax = pa.x & 0xffff, ay = pa.x >> 16, az = (int)pa.y;
+    int bx = pb.x & 0xffff, by = pb.x >> 16, bz = (int)pb.y;
+    int cx = pc.x & 0xffff, cy = pc.x >> 16, cz = (int)pc.y;
+    int area = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
+    if (area == 0) return;
+    if (area < 0) {
+        int t;
+        t = bx; bx = cx; cx = t;
+        t = by; by = cy; cy = t;
+        t = bz; bz = cz; cz = t;
+        area = -area;
+    }
+    const int R = p.R;
+    int i0 = max(0, (min(ax, min(bx, cx)) + 7) >> 4), i1 = min(R - 1, (max(ax, max(bx, cx)) - 8) >> 4);
+    int j0 = max(0, (min(ay, min(by, cy)) + 7) >> 4), j1 = min(R - 1, (max(ay, max(by, cy)) - 8) >> 4);
+    for (int j = j0; j <= j1; ++j) {
+        const int py = 16 * j + 8;
+        int *dst;
+        if (CL == 1) {
+            dst = slab + j * R;
+        } else {
+            int owner = (j * p.inv_rows) >> 20;  // exact j / rows_per_cta for j < 2^11
+            dst = cluster.map_shared_rank(slab, owner) + (j - owner * p.rows_per_cta) * R;
         }
-    return (int)q;
+        // edge functions are affine in px: e = e0 + (px - px0) * slope
+        for (int i = i0; i <= i1; ++i) {
+            const int px = 16 * i + 8;
+            int wa = (cx - bx) * (py - by) - (cy - by) * (px - bx);
+            int wb = (ax - cx) * (py - cy) - (ay - cy) * (px - cx);
+            int wc = (bx - ax) * (py - ay) - (by - ay) * (px - ax);
+            if ((wa | wb | wc) < 0) continue;
+            long long num = (long long)wa * az + (long long)wb * bz + (long long)wc * cz;
+            atomicMin(dst + i, floor_div_small(num, area));
+        }
+    }
+}
+
+// Direction-independent per-chunk vertex range [min, max] of the indices a
+// chunk of VIS_CHUNK triangles references (x > y: a bad index, or no faces).
+__global__ void vis_chunk_ranges_kernel(const int32_t *__restrict__ faces, int F, int Nv, int2 *__restrict__ vr,
+                                        int32_t *status)
+{
+    const int c = blockIdx.x;
+    int vmin = 0x7fffffff, vmax = -1;
+    bool bad = false;
+    for (int f = c * VIS_CHUNK + threadIdx.x; f < min(F, (c + 1) * VIS_CHUNK); f += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            int v = __ldg(faces + 3 * f + k);
+            if ((unsigned)v >= (unsigned)Nv) bad = true;
+            vmin = min(vmin, v);
+            vmax = max(vmax, v);
+        }
+    __shared__ int smin, smax, sbad;
+    if (threadIdx.x == 0) {
+        smin = 0x7fffffff;
+        smax = -1;
+        sbad = 0;
+    }
+    __syncthreads();
+    atomicMin(&smin, vmin);
+    atomicMax(&smax, vmax);
+    if (bad) atomicOr(&sbad, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (sbad) {
+            av_report(status, AVATAR_ERR_INDEX);
+            vr[c] = make_int2(1, 0);
+        } else {
+            vr[c] = make_int2(smin, smax);
+        }
+    }
 }
 
 template <int CL>
 __global__ void __launch_bounds__(VIS_THREADS)
 vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *__restrict__ faces,
-                       const float *__restrict__ frames, uint32_t *__restrict__ dirbits, int32_t *status)
+                       const int2 *__restrict__ vranges, const float *__restrict__ frames,
+                       uint32_t *__restrict__ dirbits, int32_t *status)
 {
     extern __shared__ int slab[];
     cg::cluster_group cluster = cg::this_cluster();
-    const int rank = (int)cluster.block_rank();
+    const int rank = CL == 1 ? 0 : (int)cluster.block_rank();
     const int d = blockIdx.y;
     const int R = p.R;
     const int slab_elems = p.rows_per_cta * R;
+    uint2 *vcache = reinterpret_cast<uint2 *>(slab + slab_elems);
 
     for (int i = threadIdx.x; i < slab_elems; i += blockDim.x) slab[i] = EMPTY_DEPTH;
 
@@ -118,69 +214,98 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
         for (int i = 0; i < 9; ++i) B[i] = 0;
     }
 
-    int *slabs[CL];
+    // faces of this CTA's first chunk (the next chunk's are prefetched while
+    // the current one is rasterised)
+    int cur[VIS_TPT][3];
+    auto load_faces = [&](int chunk, int (&dst)[VIS_TPT][3]) {
 #pragma unroll
-    for (int c = 0; c < CL; ++c) slabs[c] = cluster.map_shared_rank(slab, c);
+        for (int t = 0; t < VIS_TPT; ++t) {
+            int f = chunk * VIS_CHUNK + t * VIS_THREADS + threadIdx.x;
+            if (f < p.F) {
+                dst[t][0] = __ldg(faces + 3 * f);
+                dst[t][1] = __ldg(faces + 3 * f + 1);
+                dst[t][2] = __ldg(faces + 3 * f + 2);
+            } else {
+                dst[t][0] = -1;
+            }
+        }
+    };
+    const int nchunks = (p.F + VIS_CHUNK - 1) / VIS_CHUNK;
+    int chunk = rank;
+    if (chunk < nchunks) load_faces(chunk, cur);
     cluster.sync();
 
-    // ---- rasterise this CTA's share of the triangles
-    const int stride = CL * blockDim.x;
-    for (int f = rank * blockDim.x + threadIdx.x; f < p.F; f += stride) {
-        int ia = __ldg(faces + 3 * f), ib = __ldg(faces + 3 * f + 1), ic = __ldg(faces + 3 * f + 2);
-        if ((unsigned)ia >= (unsigned)p.Nv || (unsigned)ib >= (unsigned)p.Nv || (unsigned)ic >= (unsigned)p.Nv) {
-            av_report(status, AVATAR_ERR_INDEX);
-            continue;
+    for (; chunk < nchunks; chunk += CL) {
+        const int2 vr = __ldg(vranges + chunk);
+        const int v0 = vr.x, nv = vr.y - vr.x + 1;
+        const bool cached = nv > 0 && nv <= VIS_VCAP;
+        if (cached) {
+#pragma unroll 4
+            for (int i = threadIdx.x; i < nv; i += VIS_THREADS)
+                vcache[i] = pack_proj(project_vertex(__ldg(qv + v0 + i), B, p));
         }
-        Proj a = project_vertex(__ldg(qv + ia), B, p);
-        Proj b = project_vertex(__ldg(qv + ib), B, p);
-        Proj c = project_vertex(__ldg(qv + ic), B, p);
-        if (!(a.in && b.in && c.in)) continue;
-        int area = (b.X - a.X) * (c.Y - a.Y) - (b.Y - a.Y) * (c.X - a.X);
-        if (area == 0) continue;
-        if (area < 0) {
-            Proj t = b;
-            b = c;
-            c = t;
-            area = -area;
-        }
-        int xmin = min(a.X, min(b.X, c.X)), xmax = max(a.X, max(b.X, c.X));
-        int ymin = min(a.Y, min(b.Y, c.Y)), ymax = max(a.Y, max(b.Y, c.Y));
-        int i0 = max(0, (xmin + 7) >> 4), i1 = min(R - 1, (xmax - 8) >> 4);
-        int j0 = max(0, (ymin + 7) >> 4), j1 = min(R - 1, (ymax - 8) >> 4);
-        for (int j = j0; j <= j1; ++j) {
-            const int py = 16 * j + 8;
-            int *dst = slabs[j / p.rows_per_cta] + (j % p.rows_per_cta) * R;
-            for (int i = i0; i <= i1; ++i) {
-                const int px = 16 * i + 8;
-                int wa = (c.X - b.X) * (py - b.Y) - (c.Y - b.Y) * (px - b.X);
-                int wb = (a.X - c.X) * (py - c.Y) - (a.Y - c.Y) * (px - c.X);
-                int wc = (b.X - a.X) * (py - a.Y) - (b.Y - a.Y) * (px - a.X);
-                if ((wa | wb | wc) < 0) continue;
-                long long num = (long long)wa * a.Z + (long long)wb * b.Z + (long long)wc * c.Z;
-                atomicMin(dst + i, floor_div_small(num, area));
+        int nxt[VIS_TPT][3];
+        if (chunk + CL < nchunks) load_faces(chunk + CL, nxt);
+        __syncthreads();
+        if (nv > 0) {
+#pragma unroll
+            for (int t = 0; t < VIS_TPT; ++t) {
+                if (cur[t][0] < 0) continue;
+                uint2 pa, pb, pc;
+                if (cached) {
+                    pa = vcache[cur[t][0] - v0];
+                    pb = vcache[cur[t][1] - v0];
+                    pc = vcache[cur[t][2] - v0];
+                } else {
+                    pa = pack_proj(project_vertex(__ldg(qv + cur[t][0]), B, p));
+                    pb = pack_proj(project_vertex(__ldg(qv + cur[t][1]), B, p));
+                    pc = pack_proj(project_vertex(__ldg(qv + cur[t][2]), B, p));
+                }
+                raster_triangle<CL>(pa, pb, pc, slab, p, cluster);
             }
+        }
+        __syncthreads();  // the next chunk overwrites the cache
+#pragma unroll
+        for (int t = 0; t < VIS_TPT; ++t) {
+            cur[t][0] = nxt[t][0];
+            cur[t][1] = nxt[t][1];
+            cur[t][2] = nxt[t][2];
         }
     }
     cluster.sync();
 
-    // ---- depth-test vertices: one warp -> one 32-bit word of this direction
+    // ---- depth-test vertices: one warp -> 32-bit words of this direction,
+    // four words in flight per iteration
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nwarps = blockDim.x >> 5;
-    for (int w = rank * nwarps + warp; w < p.NW; w += CL * nwarps) {
-        int v = w * 32 + lane;
-        bool vis = false;
-        if (v < p.Nv) {
-            Proj q = project_vertex(__ldg(qv + v), B, p);
-            if (!q.in) {
-                vis = true;
-            } else {
-                int row = q.Y >> 4, col = q.X >> 4;
-                int dep = slabs[row / p.rows_per_cta][(row % p.rows_per_cta) * R + col];
-                vis = (dep == EMPTY_DEPTH) || (q.Z <= dep + p.biasq);
+    const int nwarps = VIS_THREADS / 32;
+    const int wstride = CL * nwarps;
+    for (int w0 = rank * nwarps + warp; w0 < p.NW; w0 += 4 * wstride) {
+        int4 qq[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int v = (w0 + u * wstride) * 32 + lane;
+            qq[u] = (w0 + u * wstride < p.NW && v < p.Nv) ? __ldg(qv + v) : make_int4(0, 0, 0, 2);
+        }
+        int dep[4];
+        Proj pr[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            pr[u] = project_vertex(qq[u], B, p);
+            dep[u] = EMPTY_DEPTH;
+            if (pr[u].in) {
+                int row = pr[u].Y >> 4, col = pr[u].X >> 4;
+                int owner = CL == 1 ? 0 : (row * p.inv_rows) >> 20;
+                const int *src = CL == 1 ? slab : cluster.map_shared_rank(slab, owner);
+                dep[u] = src[(row - owner * p.rows_per_cta) * R + col];
             }
         }
-        unsigned word = __ballot_sync(0xffffffffu, vis);
-        if (lane == 0) dirbits[(size_t)d * p.NW + w] = word;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int w = w0 + u * wstride;
+            bool vis = !pr[u].in || dep[u] == EMPTY_DEPTH || pr[u].Z <= dep[u] + p.biasq;
+            unsigned word = __ballot_sync(0xffffffffu, vis && qq[u].w != 2);
+            if (lane == 0 && w < p.NW) dirbits[(size_t)d * p.NW + w] = word;
+        }
     }
     cluster.sync();  // keep every slab alive until all remote reads are done
 }
@@ -217,8 +342,8 @@ __global__ void vis_transpose_kernel(const uint32_t *__restrict__ dirbits, int N
 }
 
 template <int CL>
-int launch_raster(const VisParams &p, const int4 *qv, const int32_t *faces, const float *frames,
-                  uint32_t *dirbits, int32_t *status, size_t smem, cudaStream_t st)
+int launch_raster(const VisParams &p, const int4 *qv, const int32_t *faces, const int2 *vranges,
+                  const float *frames, uint32_t *dirbits, int32_t *status, size_t smem, cudaStream_t st)
 {
     auto kern = vis_raster_test_kernel<CL>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -235,7 +360,7 @@ int launch_raster(const VisParams &p, const int4 *qv, const int32_t *faces, cons
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, kern, p, qv, faces, frames, dirbits, status) != cudaSuccess) {
+    if (cudaLaunchKernelEx(&cfg, kern, p, qv, faces, vranges, frames, dirbits, status) != cudaSuccess) {
         (void)cudaGetLastError();
         return AVATAR_ERR_CUDA;
     }
@@ -245,7 +370,7 @@ int launch_raster(const VisParams &p, const int4 *qv, const int32_t *faces, cons
 int cluster_size_for(int R)
 {
     long bytes = (long)R * R * 4;
-    int cl = (int)((bytes + 65535) / 65536);
+    int cl = (int)((bytes + VIS_SLAB_BYTES - 1) / VIS_SLAB_BYTES);
     if (cl < 1) cl = 1;
     int p2 = 1;
     while (p2 < cl) p2 <<= 1;
@@ -264,6 +389,7 @@ int check_vis(const avatar_vis_args *a)
 struct VisWs {
     int4 *qv;
     uint32_t *dirbits;
+    int2 *vranges;
 };
 
 size_t vis_ws_layout(const avatar_vis_args *a, void *base, size_t cap, VisWs *out)
@@ -273,6 +399,7 @@ size_t vis_ws_layout(const avatar_vis_args *a, void *base, size_t cap, VisWs *ou
     VisWs w;
     w.qv = c.take<int4>((size_t)a->Nv);
     w.dirbits = c.take<uint32_t>((size_t)a->D * NW);
+    w.vranges = c.take<int2>((size_t)(a->F + VIS_CHUNK - 1) / VIS_CHUNK + 1);
     if (out) *out = w;
     return c.off;
 }
@@ -319,19 +446,25 @@ extern "C" int avatar_visibility(avatar_ctx *ctx, const avatar_vis_args *a, void
     p.biasq = (int)biasq;
     int CL = cluster_size_for(a->R);
     p.rows_per_cta = a->R / CL;
-    size_t smem = (size_t)p.rows_per_cta * a->R * sizeof(int);
+    p.inv_rows = ((1 << 20) + p.rows_per_cta - 1) / p.rows_per_cta;
+    size_t smem = (size_t)p.rows_per_cta * a->R * sizeof(int) + (size_t)VIS_VCAP * sizeof(uint2);
 
     int qgrid = (int)((a->Nv + 255) / 256);
     if (qgrid > ctx->sm_count * 8) qgrid = ctx->sm_count * 8;
     vis_quantize_kernel<<<qgrid, 256, 0, st>>>(a->xp, a->Nv, qc[0], qc[1], qc[2], w.qv, a->status);
     AV_CHECK_LAUNCH();
 
+    int nchunks = (a->F + VIS_CHUNK - 1) / VIS_CHUNK;
+    if (nchunks > 0) {
+        vis_chunk_ranges_kernel<<<nchunks, 256, 0, st>>>(a->faces, a->F, a->Nv, w.vranges, a->status);
+        AV_CHECK_LAUNCH();
+    }
     int rc;
     switch (CL) {
-        case 1: rc = launch_raster<1>(p, w.qv, a->faces, a->frames, w.dirbits, a->status, smem, st); break;
-        case 2: rc = launch_raster<2>(p, w.qv, a->faces, a->frames, w.dirbits, a->status, smem, st); break;
-        case 4: rc = launch_raster<4>(p, w.qv, a->faces, a->frames, w.dirbits, a->status, smem, st); break;
-        default: rc = launch_raster<8>(p, w.qv, a->faces, a->frames, w.dirbits, a->status, smem, st); break;
+        case 1: rc = launch_raster<1>(p, w.qv, a->faces, w.vranges, a->frames, w.dirbits, a->status, smem, st); break;
+        case 2: rc = launch_raster<2>(p, w.qv, a->faces, w.vranges, a->frames, w.dirbits, a->status, smem, st); break;
+        case 4: rc = launch_raster<4>(p, w.qv, a->faces, w.vranges, a->frames, w.dirbits, a->status, smem, st); break;
+        default: rc = launch_raster<8>(p, w.qv, a->faces, w.vranges, a->frames, w.dirbits, a->status, smem, st); break;
     }
     if (rc != AVATAR_OK) return rc;
 
