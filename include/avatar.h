@@ -188,6 +188,28 @@ size_t avatar_visibility_workspace_size(const avatar_vis_args *a);
 int avatar_visibility(avatar_ctx *ctx, const avatar_vis_args *a, void *ws, size_t ws_bytes,
                       avatar_stream_t stream);
 
+/* avatar_visibility without a caller workspace.  (The paper has no
+ * counterpart: this is a convenience of this library.)  It is meant for
+ * callers that cannot allocate device memory: code inside a host application
+ * whose framework owns every device allocation, or a real-time loop where a
+ * cudaMalloc (which may synchronise the device) is not allowed.  The caller
+ * still passes all inputs and the output `bits`; the scratch is a fixed
+ * array of avatar_visibility_static_scratch_bytes() (8 MiB) compiled into the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.
+ *  - Sizes whose workspace (avatar_visibility_workspace_size) exceeds that
+ *    array are rejected with AVATAR_ERR_WORKSPACE before any launch.
+ *  - The first call on a device looks up the array's device address (with the
+ *    context's device made current for the lookup); make that first call
+ *    before any stream capture on the device.
+ *  - All calls on a device share the one array and it keeps the previous
+ *    call's contents: calls that may overlap on the GPU (different streams
+ *    without ordering) race on it and must be serialised by the caller.
+ *  - Results are identical to avatar_visibility; the function allocates
+ *    nothing. */
+size_t avatar_visibility_static_scratch_bytes(void);
+int avatar_visibility_static_scratch(avatar_ctx *ctx, const avatar_vis_args *a, avatar_stream_t stream);
+
 /* ------------------------------------------------------------------ */
 /* (c) Shading - Eq. 2 with the BRDF of App. A, cull and gamma (Sec 3.1)*/
 /*                                                                      */

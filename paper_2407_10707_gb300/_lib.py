@@ -90,6 +90,8 @@ _SIGNATURES = [
     ("avatar_skin_backward", [P, C.POINTER(SkinArgs), C.POINTER(SkinGrads), P, P, C.c_size_t, P], I32),
     ("avatar_visibility_workspace_size", [C.POINTER(VisArgs)], C.c_size_t),
     ("avatar_visibility", [P, C.POINTER(VisArgs), P, C.c_size_t, P], I32),
+    ("avatar_visibility_static_scratch_bytes", [], C.c_size_t),
+    ("avatar_visibility_static_scratch", [P, C.POINTER(VisArgs), P], I32),
     ("avatar_shade", [P, C.POINTER(ShadeArgs), P], I32),
     ("avatar_shade_backward", [P, C.POINTER(ShadeArgs), C.POINTER(ShadeGrads), P], I32),
     ("avatar_splat_num_tiles", [C.POINTER(SplatArgs)], I32),

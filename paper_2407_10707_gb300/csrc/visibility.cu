@@ -16,6 +16,8 @@
 // bits are reproducible bit for bit by any correct implementation.
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace cg = cooperative_groups;
@@ -477,4 +479,57 @@ extern "C" int avatar_visibility(avatar_ctx *ctx, const avatar_vis_args *a, void
                                                       a->status);
     AV_CHECK_LAUNCH();
     return AVATAR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Entry point without a workspace, for callers that cannot allocate device
+// memory (see the header).  Its scratch is a fixed-size array in the device
+// image of this library, shared by every call on a device.
+namespace {
+
+constexpr size_t VIS_STATIC_SCRATCH_BYTES = (size_t)8 << 20;  // 8 MiB per device, held until exit
+__device__ __align__(256) unsigned char g_vis_static_scratch[VIS_STATIC_SCRATCH_BYTES];
+
+constexpr int VIS_MAX_DEVICES = 64;
+std::mutex g_vis_static_mu;
+void *g_vis_static_ptr[VIS_MAX_DEVICES];  // device address of the array, per device
+
+// Looks up the array's device address on the context's device (once per
+// device).  The host-side symbol g_vis_static_scratch is only a stand-in and
+// must never be handed to a kernel.
+int vis_static_scratch(const avatar_ctx *ctx, void **out)
+{
+    if (ctx->device < 0 || ctx->device >= VIS_MAX_DEVICES) return AVATAR_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_vis_static_mu);
+    if (!g_vis_static_ptr[ctx->device]) {
+        int prev = -1;
+        if (cudaGetDevice(&prev) != cudaSuccess) return AVATAR_ERR_CUDA;
+        if (prev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) return AVATAR_ERR_CUDA;
+        void *p = nullptr;
+        cudaError_t rc = cudaGetSymbolAddress(&p, g_vis_static_scratch);
+        if (prev != ctx->device) cudaSetDevice(prev);
+        if (rc != cudaSuccess || p == nullptr) {
+            (void)cudaGetLastError();
+            return AVATAR_ERR_CUDA;
+        }
+        g_vis_static_ptr[ctx->device] = p;
+    }
+    *out = g_vis_static_ptr[ctx->device];
+    return AVATAR_OK;
+}
+
+}  // namespace
+
+extern "C" size_t avatar_visibility_static_scratch_bytes(void) { return VIS_STATIC_SCRATCH_BYTES; }
+
+extern "C" int avatar_visibility_static_scratch(avatar_ctx *ctx, const avatar_vis_args *a, avatar_stream_t stream)
+{
+    if (!ctx) return AVATAR_ERR_INVALID_ARG;
+    AV_TRY(check_vis(a));
+    if (vis_ws_layout(a, nullptr, 0, nullptr) > VIS_STATIC_SCRATCH_BYTES) return AVATAR_ERR_WORKSPACE;
+    void *scratch = nullptr;
+    AV_TRY(vis_static_scratch(ctx, &scratch));
+    // Everything the visibility kernels read from scratch is written earlier in
+    // the same call, so nothing needs clearing between calls.
+    return avatar_visibility(ctx, a, scratch, VIS_STATIC_SCRATCH_BYTES, stream);
 }
