@@ -70,6 +70,18 @@ int avatar_ctx_destroy(avatar_ctx *ctx);
 /* Number of streaming multiprocessors of the context's device. */
 int avatar_ctx_sm_count(const avatar_ctx *ctx);
 
+/* Tuning knobs of a context (work split only: results do not depend on
+ * them).  The library's autotuner (paper_2407_10707_gb300.autotune) times
+ * the choices on the actual workload and sets the fastest. */
+enum avatar_tune_key {
+    AVATAR_TUNE_BLEND_PPT = 0,     /* pixels per thread in the blend: 1, 2 or 4 (default 1) */
+    AVATAR_TUNE_BLEND_BWD_PPT = 1, /* pixels per thread in the blend backward: 1, 2 or 4 (default 2) */
+    AVATAR_TUNE_COUNT = 4
+};
+int avatar_ctx_set_tuning(avatar_ctx *ctx, int key, int value);
+/* Current value of a knob, or -1 for an invalid key. */
+int avatar_ctx_get_tuning(const avatar_ctx *ctx, int key);
+
 /* ------------------------------------------------------------------ */
 /* (a) Skinning - Sec. 3.1, Eq. 1                                       */
 /*                                                                      */

@@ -20,6 +20,10 @@ STATUS = {0: "AVATAR_OK", 1: "AVATAR_ERR_INVALID_ARG", 2: "AVATAR_ERR_WORKSPACE"
           4: "AVATAR_ERR_TIMEOUT", 5: "AVATAR_ERR_CUDA", 6: "AVATAR_ERR_UNSUPPORTED", 7: "AVATAR_ERR_INDEX"}
 
 
+TUNE_BLEND_PPT = 0
+TUNE_BLEND_BWD_PPT = 1
+
+
 class AvatarError(RuntimeError):
     def __init__(self, code, where):
         super().__init__(f"{where}: {STATUS.get(code, code)}")
@@ -84,6 +88,8 @@ _SIGNATURES = [
     ("avatar_ctx_create", [C.POINTER(P), I32], I32),
     ("avatar_ctx_destroy", [P], I32),
     ("avatar_ctx_sm_count", [P], I32),
+    ("avatar_ctx_set_tuning", [P, I32, I32], I32),
+    ("avatar_ctx_get_tuning", [P, I32], I32),
     ("avatar_skin_workspace_size", [C.POINTER(SkinArgs)], C.c_size_t),
     ("avatar_skin", [P, C.POINTER(SkinArgs), P, C.c_size_t, P], I32),
     ("avatar_skin_backward_workspace_size", [C.POINTER(SkinArgs)], C.c_size_t),

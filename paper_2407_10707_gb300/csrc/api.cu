@@ -66,6 +66,9 @@ extern "C" int avatar_ctx_create(avatar_ctx **out, int device)
     c->sm_count = sms;
     c->max_smem_optin = smem;
     c->cluster_ok = cluster;
+    for (int i = 0; i < AVATAR_TUNE_COUNT; ++i) c->tune[i] = 0;
+    c->tune[AVATAR_TUNE_BLEND_PPT] = 1;
+    c->tune[AVATAR_TUNE_BLEND_BWD_PPT] = 2;
     *out = c;
     return AVATAR_OK;
 }
@@ -89,4 +92,24 @@ extern "C" int avatar_l1_loss(avatar_ctx *ctx, int64_t n, const float *img, cons
     l1_loss_kernel<<<(int)blocks, 256, 0, st>>>(n, img, target, loss, d_img, (float)(1.0 / (double)n));
     AV_CHECK_LAUNCH();
     return AVATAR_OK;
+}
+
+extern "C" int avatar_ctx_set_tuning(avatar_ctx *ctx, int key, int value)
+{
+    if (!ctx || key < 0 || key >= AVATAR_TUNE_COUNT) return AVATAR_ERR_INVALID_ARG;
+    switch (key) {
+        case AVATAR_TUNE_BLEND_PPT:
+        case AVATAR_TUNE_BLEND_BWD_PPT:
+            if (value != 1 && value != 2 && value != 4) return AVATAR_ERR_INVALID_ARG;
+            break;
+        default: break;
+    }
+    ctx->tune[key] = value;
+    return AVATAR_OK;
+}
+
+extern "C" int avatar_ctx_get_tuning(const avatar_ctx *ctx, int key)
+{
+    if (!ctx || key < 0 || key >= AVATAR_TUNE_COUNT) return -1;
+    return ctx->tune[key];
 }

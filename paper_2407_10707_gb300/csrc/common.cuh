@@ -11,6 +11,7 @@ struct avatar_ctx {
     int sm_count;
     int max_smem_optin;
     int cluster_ok;
+    int tune[AVATAR_TUNE_COUNT];
 };
 
 #define AV_CHECK_LAUNCH()                                    \

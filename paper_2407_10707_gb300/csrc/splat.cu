@@ -21,8 +21,6 @@
 
 namespace {
 
-constexpr int RS_THREADS = 256;
-constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RADIX = 256;
 constexpr float NEAR_Z = 0.2f;
 constexpr float ALPHA_MIN = 1.0f / 255.0f;
@@ -59,8 +57,8 @@ struct SplatWs {
     float4 *rec0;                // [G] (mx, my, qa, qb): log2-domain conic, see bin_keys_kernel
     float2 *rec1;                // [G] (qc, log2 o)
     float4 *rec2;                // [G] (r, g, b, o)
-    int32_t *hist;               // [RADIX][NB]
-    int32_t *totals;             // [RADIX]
+    int32_t *sort_hist;          // [OS_MAX_PASSES][RADIX] digit histograms + [OS_MAX_PASSES] tile tickets
+    unsigned *sort_desc;         // [OS_MAX_PASSES][tiles][RADIX] look-back descriptors
     int32_t *block_sums;         // [NB]
     int32_t *count_g;            // [1] = G on the device
     float *d_mean2d;             // [2][G]
@@ -90,8 +88,11 @@ size_t splat_ws_layout(const avatar_splat_args *a, int NB, void *base, size_t ca
     w.rec0 = c.take<float4>(G);
     w.rec1 = c.take<float2>(G);
     w.rec2 = c.take<float4>(G);
-    w.hist = c.take<int32_t>((size_t)RADIX * NB);
-    w.totals = c.take<int32_t>(RADIX);
+    w.sort_hist = c.take<int32_t>((size_t)(4 * RADIX + 4));
+    {
+        size_t t = (size_t)((P > G ? P : G) + 2047) / 2048;
+        w.sort_desc = c.take<unsigned>(4 * t * RADIX);
+    }
     w.block_sums = c.take<int32_t>((size_t)NB);
     w.count_g = c.take<int32_t>(1);
     w.d_mean2d = c.take<float>(2 * G);
@@ -205,7 +206,7 @@ bin_keys_kernel(avatar_splat_args a, int TS, SplatWs w)
     if (blockIdx.x == 0 && threadIdx.x == 0) *w.count_g = G;
 }
 
-// ---------------------------------------------------------------- radix sort
+// ---------------------------------------------------------------- scans
 __device__ __forceinline__ int chunk_range(int n, int NB, int b, int &begin)
 {
     int chunk = (n + NB - 1) / NB;
@@ -214,21 +215,6 @@ __device__ __forceinline__ int chunk_range(int n, int NB, int b, int &begin)
     if (end > n) end = n;
     if (begin > n) begin = n;
     return end;
-}
-
-__global__ void __launch_bounds__(RS_THREADS)
-radix_hist_kernel(const uint32_t *__restrict__ keys, const int32_t *__restrict__ n_ptr, int cap, int shift,
-                  int NB, int32_t *__restrict__ hist)
-{
-    __shared__ int cnt[RADIX];
-    for (int i = threadIdx.x; i < RADIX; i += blockDim.x) cnt[i] = 0;
-    __syncthreads();
-    int n = min(*n_ptr, cap);
-    int begin;
-    int end = chunk_range(n, NB, blockIdx.x, begin);
-    for (int i = begin + threadIdx.x; i < end; i += blockDim.x) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1);
-    __syncthreads();
-    for (int d = threadIdx.x; d < RADIX; d += blockDim.x) hist[d * NB + blockIdx.x] = cnt[d];
 }
 
 // Exclusive block-wide scan of one value per thread (blockDim <= 1024).
@@ -261,88 +247,174 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int &total)
     return warp_base + x - v;
 }
 
-// One block per digit: exclusive scan over the NB per-block counts.
-__global__ void __launch_bounds__(1024)
-radix_scan_kernel(int32_t *__restrict__ hist, int NB, int32_t *__restrict__ totals)
+// ---------------------------------------------------------------- radix sort
+// Stable LSD radix sort, 8-bit digits, one kernel per digit pass:
+//   sort_hist_kernel   global digit histograms of every pass in one read
+//   onesweep_kernel    each block takes the next 2048-key tile (ticket order),
+//                      ranks its keys stably in shared memory, publishes its
+//                      digit counts and finds its global offsets by
+//                      decoupled look-back over earlier tiles, then scatters.
+// Look-back spins are bounded: a wait that expires reports
+// AVATAR_ERR_TIMEOUT and the block carries on (never hangs).
+constexpr int OS_THREADS = 256;
+constexpr int OS_WARPS = OS_THREADS / 32;
+constexpr int OS_ITEMS = 8;
+constexpr int OS_TILE = OS_THREADS * OS_ITEMS;  // 2048 keys per tile
+constexpr int OS_MAX_PASSES = 4;
+constexpr unsigned FLAG_AGG = 1u << 30, FLAG_INC = 2u << 30, FLAG_MASK = 3u << 30;
+constexpr int SPIN_LIMIT = 1 << 22;
+constexpr int OS_LOOKBACK = 16;
+
+__device__ __forceinline__ unsigned ld_volatile(const unsigned *p)
 {
-    const int d = blockIdx.x;
-    int running = 0;
-    for (int base = 0; base < NB; base += blockDim.x) {
-        int i = base + threadIdx.x;
-        int v = i < NB ? hist[d * NB + i] : 0;
-        int tot;
-        int ex = block_exclusive_scan(v, tot);
-        if (i < NB) hist[d * NB + i] = running + ex;
-        running += tot;
-    }
-    if (threadIdx.x == 0) totals[d] = running;
+    unsigned v;
+    asm volatile("ld.volatile.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
 }
 
-__global__ void __launch_bounds__(RS_THREADS)
-radix_scatter_kernel(const uint32_t *__restrict__ kin, const int32_t *__restrict__ vin, uint32_t *__restrict__ kout,
-                     int32_t *__restrict__ vout, const int32_t *__restrict__ n_ptr, int cap, int shift, int NB,
-                     const int32_t *__restrict__ hist, const int32_t *__restrict__ totals)
+__device__ __forceinline__ void st_volatile(unsigned *p, unsigned v)
 {
-    __shared__ int s_off[RADIX];
-    __shared__ int s_wcnt[RS_WARPS][RADIX];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    {
-        int tot;
-        int t = totals[tid];
-        int base = block_exclusive_scan(t, tot);
-        s_off[tid] = base + hist[tid * NB + blockIdx.x];
-    }
-    int n = min(*n_ptr, cap);
-    int begin;
-    int end = chunk_range(n, NB, blockIdx.x, begin);
+    asm volatile("st.volatile.global.u32 [%0], %1;" ::"l"(p), "r"(v));
+}
+
+__global__ void __launch_bounds__(OS_THREADS)
+sort_hist_kernel(const uint32_t *__restrict__ keys, const int32_t *__restrict__ n_ptr, int cap, int passes,
+                 int32_t *__restrict__ hist)
+{
+    __shared__ int cnt[OS_MAX_PASSES][RADIX];
+    for (int i = threadIdx.x; i < OS_MAX_PASSES * RADIX; i += blockDim.x) (&cnt[0][0])[i] = 0;
     __syncthreads();
-    for (int tb = begin; tb < end; tb += RS_THREADS) {
-        int i = tb + tid;
-        bool valid = i < end;
-        uint32_t key = valid ? kin[i] : 0u;
-        int32_t val = valid ? vin[i] : 0;
-        int digit = valid ? (int)((key >> shift) & 255u) : RADIX;
+    const int n = min(*n_ptr, cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&cnt[p][(k >> (8 * p)) & 255u], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) {
+        int v = (&cnt[0][0])[i];
+        if (v) atomicAdd(hist + i, v);
+    }
+}
+
+__global__ void __launch_bounds__(OS_THREADS)
+onesweep_kernel(const uint32_t *__restrict__ kin, const int32_t *__restrict__ vin, uint32_t *__restrict__ kout,
+                int32_t *__restrict__ vout, const int32_t *__restrict__ n_ptr, int cap, int shift,
+                const int32_t *__restrict__ hist, unsigned *__restrict__ desc, int32_t *__restrict__ ticket,
+                int32_t *status)
+{
+    __shared__ int s_tile;
+    __shared__ int s_wcnt[OS_WARPS][RADIX];  // running, then exclusive-over-warps digit counts
+    __shared__ int s_gbase[RADIX];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(ticket, 1);
+    for (int i = tid; i < OS_WARPS * RADIX; i += OS_THREADS) (&s_wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const int tile = s_tile;
+    const int n = min(*n_ptr, cap);
+    const int base = tile * OS_TILE;
+    if (base >= n) return;  // tickets are taken in order: no later tile waits on this one
+    // warp w owns the contiguous segment [base + 256 w, base + 256 (w + 1))
+    uint32_t key[OS_ITEMS];
+    int32_t val[OS_ITEMS];
+    int rank[OS_ITEMS];
+    int dig[OS_ITEMS];
 #pragma unroll
-        for (int w = 0; w < RS_WARPS; ++w) s_wcnt[w][tid] = 0;
-        __syncthreads();
-        unsigned peers = __match_any_sync(0xffffffffu, digit);
-        int rank = __popc(peers & lanemask_lt());
-        if (valid && rank == 0) s_wcnt[warp][digit] = __popc(peers);
-        __syncthreads();
+    for (int i = 0; i < OS_ITEMS; ++i) {
+        int idx = base + warp * (32 * OS_ITEMS) + i * 32 + lane;
+        bool ok = idx < n;
+        key[i] = ok ? kin[idx] : 0u;
+        val[i] = ok ? vin[idx] : 0;
+        dig[i] = ok ? (int)((key[i] >> shift) & 255u) : RADIX;
+    }
+#pragma unroll
+    for (int i = 0; i < OS_ITEMS; ++i) {
+        unsigned peers = __match_any_sync(0xffffffffu, dig[i]);
+        int before = dig[i] < RADIX ? s_wcnt[warp][dig[i]] : 0;
+        rank[i] = before + __popc(peers & lanemask_lt());
+        __syncwarp();
+        if (dig[i] < RADIX && (peers & lanemask_lt()) == 0) s_wcnt[warp][dig[i]] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // thread d: exclusive scan of digit d over warps, publish, look back
+    {
+        const int d = tid;
         int sum = 0;
 #pragma unroll
-        for (int w = 0; w < RS_WARPS; ++w) {
-            int c = s_wcnt[w][tid];
-            s_wcnt[w][tid] = sum;
+        for (int w = 0; w < OS_WARPS; ++w) {
+            int c = s_wcnt[w][d];
+            s_wcnt[w][d] = sum;
             sum += c;
         }
-        __syncthreads();
-        if (valid) {
-            int dst = s_off[digit] + s_wcnt[warp][digit] + rank;
-            kout[dst] = key;
-            vout[dst] = val;
+        unsigned *my = desc + (size_t)tile * RADIX + d;
+        st_volatile(my, (tile == 0 ? FLAG_INC : FLAG_AGG) | (unsigned)sum);
+        // decoupled look-back, OS_LOOKBACK predecessors per round trip
+        int prefix = 0;
+        bool found = tile == 0;
+        for (int p = tile - 1; p >= 0 && !found; p -= OS_LOOKBACK) {
+            unsigned v[OS_LOOKBACK];
+#pragma unroll
+            for (int i = 0; i < OS_LOOKBACK; ++i)
+                v[i] = (p - i >= 0) ? ld_volatile(desc + (size_t)(p - i) * RADIX + d) : FLAG_INC;
+#pragma unroll
+            for (int i = 0; i < OS_LOOKBACK; ++i) {
+                if (found) break;
+                unsigned x = v[i];
+                if (p - i >= 0) {
+                    int spins = 0;
+                    while ((x & FLAG_MASK) == 0) {
+                        if (++spins > SPIN_LIMIT) {
+                            av_report(status, AVATAR_ERR_TIMEOUT);
+                            x = FLAG_INC;
+                            break;
+                        }
+                        __nanosleep(32);
+                        x = ld_volatile(desc + (size_t)(p - i) * RADIX + d);
+                    }
+                }
+                prefix += (int)(x & ~FLAG_MASK);
+                if ((x & FLAG_MASK) == FLAG_INC) found = true;
+            }
         }
-        __syncthreads();
-        s_off[tid] += sum;
-        __syncthreads();
+        if (tile > 0) st_volatile(my, FLAG_INC | (unsigned)(prefix + sum));
+        // global base of digit d: exclusive scan of this pass's histogram
+        int tot;
+        int gex = block_exclusive_scan(hist[d], tot);
+        s_gbase[d] = gex + prefix;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < OS_ITEMS; ++i) {
+        if (dig[i] >= RADIX) continue;
+        int dst = s_gbase[dig[i]] + s_wcnt[warp][dig[i]] + rank[i];
+        kout[dst] = key[i];
+        vout[dst] = val[i];
     }
 }
 
-// Sorts (keys, vals) of *n_ptr (<= cap) items stably on bits [0, bits); the
-// result lands in (k_final, v_final); the other pair is scratch.
+// Sorts (k0, v0) of *n_ptr (<= cap) items stably on bits [0, bits) in 8-bit
+// passes, ping-ponging with (k1, v1): an even number of passes ends in
+// (k0, v0), an odd number in (k1, v1).
 int radix_sort(uint32_t *k0, int32_t *v0, uint32_t *k1, int32_t *v1, int bits, const int32_t *n_ptr, int cap,
-               const SplatWs &w, uint32_t *k_final, int32_t *v_final, cudaStream_t st)
+               const SplatWs &w, int32_t *status, cudaStream_t st)
 {
     int passes = (bits + 7) / 8;
-    if (passes == 0) passes = 1;
-    // choose the start buffer so that an odd/even number of passes ends in the final pair
+    if (passes < 1) passes = 1;
+    if (passes > OS_MAX_PASSES) return AVATAR_ERR_INVALID_ARG;
+    const int ntiles = (cap + OS_TILE - 1) / OS_TILE;
+    if (cudaMemsetAsync(w.sort_hist, 0, sizeof(int32_t) * (OS_MAX_PASSES * RADIX + OS_MAX_PASSES), st) != cudaSuccess ||
+        cudaMemsetAsync(w.sort_desc, 0, sizeof(unsigned) * (size_t)passes * ntiles * RADIX, st) != cudaSuccess)
+        return AVATAR_ERR_CUDA;
+    int hgrid = (cap + OS_THREADS * 8 - 1) / (OS_THREADS * 8);
+    if (hgrid > 304) hgrid = 304;
+    if (hgrid < 1) hgrid = 1;
+    sort_hist_kernel<<<hgrid, OS_THREADS, 0, st>>>(k0, n_ptr, cap, passes, w.sort_hist);
     uint32_t *kin = k0, *kout = k1;
     int32_t *vin = v0, *vout = v1;
+    int32_t *tickets = w.sort_hist + OS_MAX_PASSES * RADIX;
     for (int p = 0; p < passes; ++p) {
-        radix_hist_kernel<<<w.NB, RS_THREADS, 0, st>>>(kin, n_ptr, cap, 8 * p, w.NB, w.hist);
-        radix_scan_kernel<<<RADIX, 1024, 0, st>>>(w.hist, w.NB, w.totals);
-        radix_scatter_kernel<<<w.NB, RS_THREADS, 0, st>>>(kin, vin, kout, vout, n_ptr, cap, 8 * p, w.NB, w.hist,
-                                                         w.totals);
+        onesweep_kernel<<<ntiles, OS_THREADS, 0, st>>>(kin, vin, kout, vout, n_ptr, cap, 8 * p, w.sort_hist + p * RADIX,
+                                                       w.sort_desc + (size_t)p * ntiles * RADIX, tickets + p, status);
         uint32_t *tk = kin;
         kin = kout;
         kout = tk;
@@ -351,8 +423,6 @@ int radix_sort(uint32_t *k0, int32_t *v0, uint32_t *k1, int32_t *v1, int bits, c
         vout = tv;
     }
     AV_CHECK_LAUNCH();
-    (void)k_final;
-    (void)v_final;
     return AVATAR_OK;
 }
 
@@ -443,29 +513,41 @@ tile_ranges_kernel(const uint32_t *__restrict__ keys, const int32_t *__restrict_
 // ---------------------------------------------------------------- blend
 constexpr float LOG2_ALPHA_MIN = -7.99435343685886f;  // log2(1/255)
 
-template <int TS>
-__global__ void __launch_bounds__(TS *TS)
+// One CTA per TS x TS tile, PPT pixels per thread (pixel k of thread t is
+// tile pixel k * NTH + t), Gaussians staged NTH at a time in shared memory.
+template <int TS, int PPT>
+__global__ void __launch_bounds__(TS *TS / PPT)
 blend_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_gauss, const float4 *__restrict__ rec0,
              const float2 *__restrict__ rec1, const float4 *__restrict__ rec2, int W, int H, int ntx,
              float *__restrict__ image, float *__restrict__ T_final, int32_t *__restrict__ n_last)
 {
-    constexpr int NT = TS * TS;
-    __shared__ float4 s0[NT];
-    __shared__ float2 s1[NT];
-    __shared__ float4 s2[NT];
+    constexpr int NTH = TS * TS / PPT;
+    __shared__ float4 s0[NTH];
+    __shared__ float2 s1[NTH];
+    __shared__ float4 s2[NTH];
     const int tile = blockIdx.x;
     const int tx = tile % ntx, ty = tile / ntx;
     const int tid = threadIdx.x;
-    const int px = tx * TS + tid % TS, py = ty * TS + tid / TS;
-    const bool inside = px < W && py < H;
-    const float fx = px + 0.5f, fy = py + 0.5f;
+    float fx[PPT], fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
+    int last[PPT];
+    bool live[PPT];
+    bool done = true;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int lp = k * NTH + tid;
+        const int px = tx * TS + lp % TS, py = ty * TS + lp / TS;
+        fx[k] = px + 0.5f;
+        fy[k] = py + 0.5f;
+        T[k] = 1.f;
+        C0[k] = C1[k] = C2[k] = 0.f;
+        last[k] = 0;
+        live[k] = px < W && py < H;
+        done = done && !live[k];
+    }
     const int2 rg = ranges[tile];
     const int n = rg.y - rg.x;
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    int last = 0;
-    bool done = !inside;
-    for (int base = 0; base < n; base += NT) {
-        if (__syncthreads_count(done) == NT) break;
+    for (int base = 0; base < n; base += NTH) {
+        if (__syncthreads_count(done) == NTH) break;
         int idx = base + tid;
         if (idx < n) {
             int g = pair_gauss[rg.x + idx];
@@ -475,79 +557,101 @@ blend_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_g
         }
         __syncthreads();
         if (!done) {
-            int m = min(NT, n - base);
+            int m = min(NTH, n - base);
             for (int j = 0; j < m; ++j) {
                 float4 r0 = s0[j];
                 float2 r1 = s1[j];
-                float dx = fx - r0.x, dy = fy - r0.y;
-                float l2a = fmaf(fmaf(r0.z, dx, r0.w * dy), dx, fmaf(r1.x * dy, dy, r1.y));
-                if (l2a < LOG2_ALPHA_MIN) continue;
-                float alpha = fminf(0.99f, exp2f(l2a));
-                float test_T = T * (1.f - alpha);
-                if (test_T < T_MIN) {
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    if (!live[k]) continue;
+                    float dx = fx[k] - r0.x, dy = fy[k] - r0.y;
+                    float l2a = fmaf(fmaf(r0.z, dx, r0.w * dy), dx, fmaf(r1.x * dy, dy, r1.y));
+                    if (l2a < LOG2_ALPHA_MIN) continue;
+                    float alpha = fminf(0.99f, exp2f(l2a));
+                    float test_T = T[k] * (1.f - alpha);
+                    if (test_T < T_MIN) {
+                        live[k] = false;
+                        continue;
+                    }
+                    float4 c = s2[j];
+                    float wgt = alpha * T[k];
+                    C0[k] = fmaf(c.x, wgt, C0[k]);
+                    C1[k] = fmaf(c.y, wgt, C1[k]);
+                    C2[k] = fmaf(c.z, wgt, C2[k]);
+                    T[k] = test_T;
+                    last[k] = base + j + 1;
+                }
+                bool any = false;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) any = any || live[k];
+                if (!any) {
                     done = true;
                     break;
                 }
-                float4 c = s2[j];
-                float wgt = alpha * T;
-                C0 = fmaf(c.x, wgt, C0);
-                C1 = fmaf(c.y, wgt, C1);
-                C2 = fmaf(c.z, wgt, C2);
-                T = test_T;
-                last = base + j + 1;
             }
         }
     }
-    if (inside) {
-        const int pix = py * W + px;
-        image[pix] = C0;
-        image[W * H + pix] = C1;
-        image[2 * W * H + pix] = C2;
-        T_final[pix] = T;
-        n_last[pix] = last;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int lp = k * NTH + tid;
+        const int px = tx * TS + lp % TS, py = ty * TS + lp / TS;
+        if (px < W && py < H) {
+            const int pix = py * W + px;
+            image[pix] = C0[k];
+            image[W * H + pix] = C1[k];
+            image[2 * W * H + pix] = C2[k];
+            T_final[pix] = T[k];
+            n_last[pix] = last[k];
+        }
     }
 }
 
 // ---------------------------------------------------------------- backward
-template <int TS>
-__global__ void __launch_bounds__(TS *TS)
+template <int TS, int PPT>
+__global__ void __launch_bounds__(TS *TS / PPT)
 blend_backward_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_gauss,
                       const float4 *__restrict__ rec0, const float2 *__restrict__ rec1, const float4 *__restrict__ rec2,
                       int W, int H, int ntx, const float *__restrict__ T_final, const int32_t *__restrict__ n_last,
                       const float *__restrict__ d_image, int G, float *__restrict__ d_mean2d,
                       float *__restrict__ d_conic, float *__restrict__ d_opacity, float *__restrict__ d_color)
 {
-    constexpr int NT = TS * TS;
+    constexpr int NTH = TS * TS / PPT;
     constexpr float LN2 = 0.6931471805599453f;
-    __shared__ float4 s0[NT];
-    __shared__ float2 s1[NT];
-    __shared__ float4 s2[NT];
-    __shared__ int sg[NT];
+    __shared__ float4 s0[NTH];
+    __shared__ float2 s1[NTH];
+    __shared__ float4 s2[NTH];
+    __shared__ int sg[NTH];
     __shared__ int s_max;
     const int tile = blockIdx.x;
     const int tx = tile % ntx, ty = tile / ntx;
     const int tid = threadIdx.x, lane = tid & 31;
-    const int px = tx * TS + tid % TS, py = ty * TS + tid / TS;
-    const bool inside = px < W && py < H;
-    const float fx = px + 0.5f, fy = py + 0.5f;
-    const int2 rg = ranges[tile];
-    const int pix = py * W + px;
-    int my_last = inside ? n_last[pix] : 0;
-    float T = inside ? T_final[pix] : 1.f;
-    float dC0 = 0.f, dC1 = 0.f, dC2 = 0.f;
-    if (inside) {
-        dC0 = d_image[pix];
-        dC1 = d_image[W * H + pix];
-        dC2 = d_image[2 * W * H + pix];
+    float fx[PPT], fy[PPT], T[PPT], dC0[PPT], dC1[PPT], dC2[PPT], acc0[PPT], acc1[PPT], acc2[PPT];
+    int my_last[PPT];
+    int mx_last = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int lp = k * NTH + tid;
+        const int px = tx * TS + lp % TS, py = ty * TS + lp / TS;
+        const bool inside = px < W && py < H;
+        const int pix = py * W + px;
+        fx[k] = px + 0.5f;
+        fy[k] = py + 0.5f;
+        my_last[k] = inside ? n_last[pix] : 0;
+        T[k] = inside ? T_final[pix] : 1.f;
+        dC0[k] = inside ? d_image[pix] : 0.f;
+        dC1[k] = inside ? d_image[W * H + pix] : 0.f;
+        dC2[k] = inside ? d_image[2 * W * H + pix] : 0.f;
+        acc0[k] = acc1[k] = acc2[k] = 0.f;
+        mx_last = max(mx_last, my_last[k]);
     }
     if (tid == 0) s_max = 0;
     __syncthreads();
-    atomicMax(&s_max, my_last);
+    atomicMax(&s_max, mx_last);
     __syncthreads();
+    const int2 rg = ranges[tile];
     const int n = s_max;
-    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;  // colour behind the current Gaussian
-    for (int end = n; end > 0; end -= NT) {
-        const int start = max(0, end - NT);
+    for (int end = n; end > 0; end -= NTH) {
+        const int start = max(0, end - NTH);
         __syncthreads();
         int idx = start + tid;
         if (idx < end) {
@@ -560,39 +664,40 @@ blend_backward_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict
         __syncthreads();
         for (int j = end - 1; j >= start; --j) {
             const int sj = j - start;
-            float4 r0 = s0[sj];
-            float2 r1 = s1[sj];
+            const float4 r0 = s0[sj];
+            const float2 r1 = s1[sj];
+            const float4 c = s2[sj];
+            // per-thread sums over this thread's pixels
             float g_col0 = 0.f, g_col1 = 0.f, g_col2 = 0.f, g_op = 0.f, g_mx = 0.f, g_my = 0.f, g_ca = 0.f,
                   g_cb = 0.f, g_cc = 0.f;
             bool contrib = false;
-            if (j < my_last) {
-                float dx = fx - r0.x, dy = fy - r0.y;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (j >= my_last[k]) continue;
+                float dx = fx[k] - r0.x, dy = fy[k] - r0.y;
                 float l2a = fmaf(fmaf(r0.z, dx, r0.w * dy), dx, fmaf(r1.x * dy, dy, r1.y));
-                if (l2a >= LOG2_ALPHA_MIN) {
-                    float raw = exp2f(l2a);
-                    float alpha = fminf(0.99f, raw);
-                    contrib = true;
-                    float4 c = s2[sj];
-                    T = T / (1.f - alpha);
-                    float wgt = alpha * T;
-                    g_col0 = wgt * dC0;
-                    g_col1 = wgt * dC1;
-                    g_col2 = wgt * dC2;
-                    float dalpha = T * ((c.x - acc0) * dC0 + (c.y - acc1) * dC1 + (c.z - acc2) * dC2);
-                    acc0 = alpha * c.x + (1.f - alpha) * acc0;
-                    acc1 = alpha * c.y + (1.f - alpha) * acc1;
-                    acc2 = alpha * c.z + (1.f - alpha) * acc2;
-                    if (raw < 0.99f) {
-                        g_op = dalpha * raw / c.w;  // d alpha / d o = exp(power)
-                        float dpow = dalpha * raw;  // d alpha / d power = alpha
-                        // conic (a, b, c) from the log2-domain record
-                        float ca = -2.f * LN2 * r0.z, cb = -LN2 * r0.w, cc = -2.f * LN2 * r1.x;
-                        g_mx = dpow * (ca * dx + cb * dy);
-                        g_my = dpow * (cb * dx + cc * dy);
-                        g_ca = -0.5f * dx * dx * dpow;
-                        g_cb = -dx * dy * dpow;
-                        g_cc = -0.5f * dy * dy * dpow;
-                    }
+                if (l2a < LOG2_ALPHA_MIN) continue;
+                float raw = exp2f(l2a);
+                float alpha = fminf(0.99f, raw);
+                contrib = true;
+                T[k] = T[k] / (1.f - alpha);
+                float wgt = alpha * T[k];
+                g_col0 = fmaf(wgt, dC0[k], g_col0);
+                g_col1 = fmaf(wgt, dC1[k], g_col1);
+                g_col2 = fmaf(wgt, dC2[k], g_col2);
+                float dalpha = T[k] * ((c.x - acc0[k]) * dC0[k] + (c.y - acc1[k]) * dC1[k] + (c.z - acc2[k]) * dC2[k]);
+                acc0[k] = alpha * c.x + (1.f - alpha) * acc0[k];
+                acc1[k] = alpha * c.y + (1.f - alpha) * acc1[k];
+                acc2[k] = alpha * c.z + (1.f - alpha) * acc2[k];
+                if (raw < 0.99f) {
+                    float dpow = dalpha * raw;  // d alpha / d power = alpha
+                    g_op += dpow;               // d alpha / d o = alpha / o (divided once below)
+                    float ca = -2.f * LN2 * r0.z, cb = -LN2 * r0.w, cc = -2.f * LN2 * r1.x;
+                    g_mx = fmaf(dpow, ca * dx + cb * dy, g_mx);
+                    g_my = fmaf(dpow, cb * dx + cc * dy, g_my);
+                    g_ca = fmaf(-0.5f * dpow, dx * dx, g_ca);
+                    g_cb = fmaf(-dpow, dx * dy, g_cb);
+                    g_cc = fmaf(-0.5f * dpow, dy * dy, g_cc);
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
@@ -610,7 +715,7 @@ blend_backward_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict
                     atomicAdd(d_color + g, g_col0);
                     atomicAdd(d_color + G + g, g_col1);
                     atomicAdd(d_color + 2 * G + g, g_col2);
-                    atomicAdd(d_opacity + g, g_op);
+                    atomicAdd(d_opacity + g, g_op / c.w);
                     atomicAdd(d_mean2d + g, g_mx);
                     atomicAdd(d_mean2d + G + g, g_my);
                     atomicAdd(d_conic + g, g_ca);
@@ -809,7 +914,7 @@ extern "C" int avatar_splat_bin(avatar_ctx *ctx, const avatar_splat_args *a, voi
     bin_keys_kernel<<<grid_cap(ctx, G, 256, 8), 256, 0, st>>>(*a, tile_of(a), w);
     AV_CHECK_LAUNCH();
     // 1. stable depth sort of all Gaussians (4 passes -> result back in dkey_a/dval_a)
-    AV_TRY(radix_sort(w.dkey_a, w.dval_a, w.dkey_b, w.dval_b, 32, w.count_g, G, w, w.dkey_a, w.dval_a, st));
+    AV_TRY(radix_sort(w.dkey_a, w.dval_a, w.dkey_b, w.dval_b, 32, w.count_g, G, w, a->status, st));
     // 2. pair offsets in depth order
     pair_scan_reduce_kernel<<<w.NB, 1024, 0, st>>>(w.dval_a, w.npairs, G, w.NB, w.block_sums);
     pair_scan_down_kernel<<<w.NB, 1024, 0, st>>>(w.dval_a, w.npairs, G, w.NB, w.block_sums, w.offsets, a->num_pairs,
@@ -828,13 +933,28 @@ extern "C" int avatar_splat_bin(avatar_ctx *ctx, const avatar_splat_args *a, voi
                                                                  cap, k_emit, v_emit);
     AV_CHECK_LAUNCH();
     // 4. stable sort of the pairs on the tile id
-    AV_TRY(radix_sort(k_emit, v_emit, k_other, v_other, passes * 8, a->num_pairs, (int)cap, w, w.pkey_a,
-                      a->pair_gauss, st));
+    AV_TRY(radix_sort(k_emit, v_emit, k_other, v_other, passes * 8, a->num_pairs, (int)cap, w, a->status, st));
     // 5. tile ranges (sorted keys are in pkey_a)
     tile_ranges_kernel<<<ctx->sm_count * 8, 256, 0, st>>>(w.pkey_a, a->num_pairs, cap, ntiles,
                                                           (int2 *)a->tile_range);
     AV_CHECK_LAUNCH();
     return AVATAR_OK;
+}
+
+template <int TS, int PPT>
+void launch_blend(const avatar_splat_args *a, const SplatWs &w, int ntiles, int ntx, cudaStream_t st)
+{
+    blend_kernel<TS, PPT><<<ntiles, TS * TS / PPT, 0, st>>>((const int2 *)a->tile_range, a->pair_gauss, w.rec0,
+                                                            w.rec1, w.rec2, a->cam.width, a->cam.height, ntx,
+                                                            a->image, a->T_final, a->n_last);
+}
+
+template <int TS>
+void launch_blend_ppt(int ppt, const avatar_splat_args *a, const SplatWs &w, int ntiles, int ntx, cudaStream_t st)
+{
+    if (ppt == 4) launch_blend<TS, 4>(a, w, ntiles, ntx, st);
+    else if (ppt == 2) launch_blend<TS, 2>(a, w, ntiles, ntx, st);
+    else launch_blend<TS, 1>(a, w, ntiles, ntx, st);
 }
 
 extern "C" int avatar_splat_blend(avatar_ctx *ctx, const avatar_splat_args *a, void *ws, size_t ws_bytes,
@@ -846,21 +966,11 @@ extern "C" int avatar_splat_blend(avatar_ctx *ctx, const avatar_splat_args *a, v
     const int ts = tile_of(a);
     const int ntx = (a->cam.width + ts - 1) / ts;
     const int ntiles = ntiles_of(a);
-    const int W = a->cam.width, H = a->cam.height;
-    const int2 *rg = (const int2 *)a->tile_range;
+    const int ppt = ctx->tune[AVATAR_TUNE_BLEND_PPT];
     switch (ts) {
-        case 8:
-            blend_kernel<8><<<ntiles, 64, 0, st>>>(rg, a->pair_gauss, w.rec0, w.rec1, w.rec2, W, H, ntx, a->image,
-                                                   a->T_final, a->n_last);
-            break;
-        case 32:
-            blend_kernel<32><<<ntiles, 1024, 0, st>>>(rg, a->pair_gauss, w.rec0, w.rec1, w.rec2, W, H, ntx, a->image,
-                                                      a->T_final, a->n_last);
-            break;
-        default:
-            blend_kernel<16><<<ntiles, 256, 0, st>>>(rg, a->pair_gauss, w.rec0, w.rec1, w.rec2, W, H, ntx, a->image,
-                                                     a->T_final, a->n_last);
-            break;
+        case 8: launch_blend_ppt<8>(ppt > 2 ? 2 : ppt, a, w, ntiles, ntx, st); break;
+        case 32: launch_blend_ppt<32>(ppt, a, w, ntiles, ntx, st); break;
+        default: launch_blend_ppt<16>(ppt, a, w, ntiles, ntx, st); break;
     }
     AV_CHECK_LAUNCH();
     return AVATAR_OK;
@@ -872,6 +982,24 @@ extern "C" int avatar_splat(avatar_ctx *ctx, const avatar_splat_args *a, void *w
     AV_TRY(avatar_splat_project(ctx, a, ws, ws_bytes, stream));
     AV_TRY(avatar_splat_bin(ctx, a, ws, ws_bytes, stream));
     return avatar_splat_blend(ctx, a, ws, ws_bytes, stream);
+}
+
+template <int TS, int PPT>
+void launch_blend_bwd(const avatar_splat_args *a, const avatar_splat_grads *g, const SplatWs &w, int ntiles, int ntx,
+                      int G, cudaStream_t st)
+{
+    blend_backward_kernel<TS, PPT><<<ntiles, TS * TS / PPT, 0, st>>>(
+        (const int2 *)a->tile_range, a->pair_gauss, w.rec0, w.rec1, w.rec2, a->cam.width, a->cam.height, ntx,
+        a->T_final, a->n_last, g->d_image, G, w.d_mean2d, w.d_conic, g->d_opacity, g->d_color);
+}
+
+template <int TS>
+void launch_blend_bwd_ppt(int ppt, const avatar_splat_args *a, const avatar_splat_grads *g, const SplatWs &w,
+                          int ntiles, int ntx, int G, cudaStream_t st)
+{
+    if (ppt == 4) launch_blend_bwd<TS, 4>(a, g, w, ntiles, ntx, G, st);
+    else if (ppt == 2) launch_blend_bwd<TS, 2>(a, g, w, ntiles, ntx, G, st);
+    else launch_blend_bwd<TS, 1>(a, g, w, ntiles, ntx, G, st);
 }
 
 extern "C" int avatar_splat_backward(avatar_ctx *ctx, const avatar_splat_args *a, const avatar_splat_grads *g,
@@ -891,24 +1019,11 @@ extern "C" int avatar_splat_backward(avatar_ctx *ctx, const avatar_splat_args *a
     const int ts = tile_of(a);
     const int ntx = (a->cam.width + ts - 1) / ts;
     const int ntiles = ntiles_of(a);
-    const int W = a->cam.width, H = a->cam.height;
-    const int2 *rg = (const int2 *)a->tile_range;
+    const int bppt = ctx->tune[AVATAR_TUNE_BLEND_BWD_PPT];
     switch (ts) {
-        case 8:
-            blend_backward_kernel<8><<<ntiles, 64, 0, st>>>(rg, a->pair_gauss, w.rec0, w.rec1, w.rec2, W, H, ntx,
-                                                            a->T_final, a->n_last, g->d_image, G, w.d_mean2d,
-                                                            w.d_conic, g->d_opacity, g->d_color);
-            break;
-        case 32:
-            blend_backward_kernel<32><<<ntiles, 1024, 0, st>>>(rg, a->pair_gauss, w.rec0, w.rec1, w.rec2, W, H, ntx,
-                                                               a->T_final, a->n_last, g->d_image, G, w.d_mean2d,
-                                                               w.d_conic, g->d_opacity, g->d_color);
-            break;
-        default:
-            blend_backward_kernel<16><<<ntiles, 256, 0, st>>>(rg, a->pair_gauss, w.rec0, w.rec1, w.rec2, W, H, ntx,
-                                                              a->T_final, a->n_last, g->d_image, G, w.d_mean2d,
-                                                              w.d_conic, g->d_opacity, g->d_color);
-            break;
+        case 8: launch_blend_bwd_ppt<8>(bppt > 2 ? 2 : bppt, a, g, w, ntiles, ntx, G, st); break;
+        case 32: launch_blend_bwd_ppt<32>(bppt, a, g, w, ntiles, ntx, G, st); break;
+        default: launch_blend_bwd_ppt<16>(bppt, a, g, w, ntiles, ntx, G, st); break;
     }
     AV_CHECK_LAUNCH();
     project_backward_kernel<<<grid_cap(ctx, G, 256, 8), 256, 0, st>>>(*a, to_dev(a->cam), w.d_mean2d, w.d_conic,
