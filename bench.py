@@ -302,6 +302,19 @@ def roofline(stages, stats, sc, peaks, peak_kind, clocks):
         v["frac"] = round(v["achieved"] / v["peak"], 4)
         v["achieved"] = round(v["achieved"], 3)
         v["peak"] = round(v["peak"], 1)
+    # DRAM traffic per launch from the committed ncu summary, only while the
+    # kernel source is unchanged since the capture
+    try:
+        import hashlib
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic_c2.json")) as f:
+            tr = json.load(f)["kernels"]
+        for stage, rec in tr.items():
+            with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() == rec["source_sha256"] and stage in out:
+                    out[stage]["traffic"] = rec["dram_bytes_per_launch"]
+                    out[stage]["traffic_kernel"] = rec["kernel"]
+    except (OSError, KeyError, ValueError):
+        pass
     dom = max(stages, key=lambda k: stages[k])
     res = dict(out[dom])
     res["stage"] = dom
