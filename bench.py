@@ -193,7 +193,8 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD_DESC, "gaussians": G, "mesh_vertices": Nv, "faces": F, "lights": NL,
                    "vis_dirs": D, "vis_res": R, "image": [W, H], "tile": args.tile,
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "flushed (256 MB write) between timed steps", "graph": "CUDA graph replay"},
+                   "l2": "flushed (256 MB write) between timed steps", "graph": "CUDA graph replay",
+                   "visibility": "one-sided raster of the closed capsule body (same bits as two-sided)"},
         "train": {"value": round(world * 1000.0 / train_ms, 3), "unit": "train steps/s", "ms_per_step":
                   round(train_ms, 5)},
         "stages_us": {k: round(v * 1000.0, 2) for k, v in stages.items()},

@@ -173,6 +173,7 @@ int avatar_skin_backward(avatar_ctx *ctx, const avatar_skin_args *a, const avata
 /*  there is floor(sum w_i zd_i / area); the depth map keeps the minimum. */
 /*  bit(v,d) = 1 iff v is outside the window, its pixel is empty, or      */
 /*  zd_v <= depth[pixel(v)] + rint(bias*2^16).                            */
+/* (cull_back = 1 keeps only triangles of positive area, see the field.) */
 /* Output bit layout: vertex-major words.  With dmap == NULL the word     */
 /* index is d>>5 over the D viewpoints ([Nv][D/32]); with a light->view   */
 /* map dmap[NL] the bits are re-ordered per light: bit k of vertex v is  */
@@ -194,6 +195,11 @@ typedef struct {
     const int32_t *dmap;   /* [NL] light -> viewpoint, or NULL */
     uint32_t *bits;        /* output, layout above */
     int32_t *status;       /* optional device status word */
+    int cull_back;         /* host value: 0 = two-sided (the rules above); 1 = rasterise only
+                            * triangles whose integer area (a->b->c) is positive, i.e. that face
+                            * the light for outward winding.  For closed, consistently outward-
+                            * wound meshes both give identical bits (the nearest surface along
+                            * any ray toward the light faces it); 1 does about half the work. */
 } avatar_vis_args;
 
 size_t avatar_visibility_workspace_size(const avatar_vis_args *a);

@@ -255,6 +255,8 @@ void orc_skin(int G, int Nv, int K, int J,
 /*  depth map = min over covering triangles (empty = +inf)               */
 /*  bit(v,d) = 1 iff v outside the window, its pixel empty, or           */
 /*             zd_v <= depth[pixel(v)] + rint(bias * 2^16)               */
+/*  cull_back != 0: only triangles with positive area (a->b->c) are      */
+/*  rasterised (light-facing for outward winding).                       */
 /* bits: [Nv][D/32] uint32, bit d&31 of word d>>5.                      */
 /* Returns 0, or -1 on an argument outside the supported range.         */
 /* ------------------------------------------------------------------ */
@@ -267,7 +269,7 @@ static int64_t floor_div(int64_t a, int64_t b) /* b > 0 */
 
 int orc_visibility(int Nv, int F, int D, int R, const double *xp, const int *faces,
                    const double *frames, const double *center, double half_extent, double bias,
-                   uint32_t *bits, int32_t *depth_out)
+                   int cull_back, uint32_t *bits, int32_t *depth_out)
 {
     if (D <= 0 || D % 32 != 0 || R < 1 || R > 1024 || Nv < 0 || F < 0) return -1;
     int64_t H = (int64_t)llrint(half_extent * 67108864.0);
@@ -318,6 +320,7 @@ int orc_visibility(int Nv, int F, int D, int R, const double *xp, const int *fac
             if (!in[a] || !in[b] || !in[c]) continue;
             int64_t area = (X[b] - X[a]) * (Y[c] - Y[a]) - (Y[b] - Y[a]) * (X[c] - X[a]);
             if (area == 0) continue;
+            if (area < 0 && cull_back) continue; /* one-sided: faces away from the light */
             if (area < 0) {
                 int tmp = b;
                 b = c;

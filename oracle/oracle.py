@@ -81,7 +81,7 @@ def skin(av, bone):
     return out
 
 
-def visibility(xp, faces, frames, center, half_extent, bias, depth_res, want_depth=False):
+def visibility(xp, faces, frames, center, half_extent, bias, depth_res, want_depth=False, cull_back=False):
     """Exact integer visibility bits [Nv, D/32] (uint32); raises on bad args."""
     xp, faces, frames = _d(xp), _i(faces), _d(np.asarray(frames).reshape(-1, 9))
     center = _d(center)
@@ -90,8 +90,8 @@ def visibility(xp, faces, frames, center, half_extent, bias, depth_res, want_dep
     depth = np.zeros((D, depth_res, depth_res), dtype=np.int32) if want_depth else None
     rc = lib().orc_visibility(ctypes.c_int(Nv), ctypes.c_int(F), ctypes.c_int(D),
                               ctypes.c_int(depth_res), _p(xp), _p(faces), _p(frames), _p(center),
-                              ctypes.c_double(half_extent), ctypes.c_double(bias), _p(bits),
-                              _p(depth))
+                              ctypes.c_double(half_extent), ctypes.c_double(bias),
+                              ctypes.c_int(1 if cull_back else 0), _p(bits), _p(depth))
     if rc != 0:
         raise ValueError("oracle visibility: argument outside the supported range")
     return (bits, depth) if want_depth else bits

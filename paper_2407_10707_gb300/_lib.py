@@ -49,7 +49,7 @@ class VisArgs(C.Structure):
     _fields_ = [("Nv", I32), ("F", I32), ("D", I32), ("R", I32),
                 ("xp", P), ("faces", P), ("frames", P),
                 ("center", F32 * 3), ("half_extent", F32), ("bias", F32),
-                ("NL", I32), ("dmap", P), ("bits", P), ("status", P)]
+                ("NL", I32), ("dmap", P), ("bits", P), ("status", P), ("cull_back", I32)]
 
 
 class ShadeArgs(C.Structure):

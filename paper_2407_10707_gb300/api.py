@@ -153,7 +153,7 @@ def avatar_skin_backward(t, out, up, want=("xg", "logscale", "quat", "wv", "av",
 
 
 # ---------------------------------------------------------------- (b) visibility
-def _vis_struct(xp, faces, frames, center, half_extent, bias, R, dmap, bits, status):
+def _vis_struct(xp, faces, frames, center, half_extent, bias, R, dmap, bits, status, cull_back=False):
     a = L.VisArgs()
     a.Nv = xp.shape[1]
     a.F = faces.shape[0]
@@ -168,11 +168,12 @@ def _vis_struct(xp, faces, frames, center, half_extent, bias, R, dmap, bits, sta
     a.dmap = _p(dmap)
     a.bits = _p(bits)
     a.status = _p(status)
+    a.cull_back = 1 if cull_back else 0
     return a
 
 
 def avatar_visibility(xp, faces, frames, center, half_extent, bias, R, dmap=None, bits=None, ws=None,
-                      status=None):
+                      status=None, cull_back=False):
     """(b) Depth-map visibility bits (Sec. 3.2).  xp [3,Nv] f32, faces [F,3]
     i32, frames [D,9] f32.  Returns uint32-valued int32 words, light-ordered
     [Nv, ceil(NL/32)] when dmap is given, else [Nv, D/32]."""
@@ -182,7 +183,7 @@ def avatar_visibility(xp, faces, frames, center, half_extent, bias, R, dmap=None
     nout = dmap.shape[0] if dmap is not None else frames.shape[0]
     if bits is None:
         bits = torch.empty(Nv, (nout + 31) // 32, dtype=torch.int32, device=xp.device)
-    a = _vis_struct(xp, faces, frames, center, half_extent, bias, R, dmap, bits, status)
+    a = _vis_struct(xp, faces, frames, center, half_extent, bias, R, dmap, bits, status, cull_back)
     need = lib.avatar_visibility_workspace_size(C.byref(a))
     if need == 0:
         raise L.AvatarError(1, "avatar_visibility_workspace_size")

@@ -55,7 +55,7 @@ struct SplatWs {
     uint32_t *pkey_a, *pkey_b;   // [cap] tile keys
     int32_t *pval_b;             // [cap] ping-pong partner of pair_gauss
     float4 *rec0;                // [G] (mx, my, qa, qb): log2-domain conic, see bin_keys_kernel
-    float2 *rec1;                // [G] (qc, log2 o)
+    float4 *rec1;                // [G] (qc, log2 o, x0 | y0 << 16, x1 | y1 << 16) rect bits
     float4 *rec2;                // [G] (r, g, b, o)
     int32_t *sort_hist;          // [OS_MAX_PASSES][RADIX] digit histograms + [OS_MAX_PASSES] tile tickets
     unsigned *sort_desc;         // [OS_MAX_PASSES][tiles][RADIX] look-back descriptors
@@ -86,7 +86,7 @@ size_t splat_ws_layout(const avatar_splat_args *a, int NB, void *base, size_t ca
     w.pkey_b = c.take<uint32_t>(P);
     w.pval_b = c.take<int32_t>(P);
     w.rec0 = c.take<float4>(G);
-    w.rec1 = c.take<float2>(G);
+    w.rec1 = c.take<float4>(G);
     w.rec2 = c.take<float4>(G);
     w.sort_hist = c.take<int32_t>((size_t)(4 * RADIX + 4));
     {
@@ -200,7 +200,8 @@ bin_keys_kernel(avatar_splat_args a, int TS, SplatWs w)
         const float L2E = 1.4426950408889634f;
         float o = a.opacity[g];
         w.rec0[g] = make_float4(a.mean2d[g], a.mean2d[G + g], -0.5f * L2E * a.conic[g], -L2E * a.conic[G + g]);
-        w.rec1[g] = make_float2(-0.5f * L2E * a.conic[2 * G + g], o > 0.f ? log2f(o) : -1e30f);
+        w.rec1[g] = make_float4(-0.5f * L2E * a.conic[2 * G + g], o > 0.f ? log2f(o) : -1e30f,
+                                __int_as_float((x0 & 0xffff) | (y0 << 16)), __int_as_float((x1 & 0xffff) | (y1 << 16)));
         w.rec2[g] = make_float4(a.color[g], a.color[G + g], a.color[2 * G + g], o);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *w.count_g = G;
@@ -513,29 +514,63 @@ tile_ranges_kernel(const uint32_t *__restrict__ keys, const int32_t *__restrict_
 // ---------------------------------------------------------------- blend
 constexpr float LOG2_ALPHA_MIN = -7.99435343685886f;  // log2(1/255)
 
-// One CTA per TS x TS tile, PPT pixels per thread (pixel k of thread t is
-// tile pixel k * NTH + t), Gaussians staged NTH at a time in shared memory.
+// One CTA per TS x TS tile.  Warp w owns an 8 x (4 PPT) pixel box of the
+// tile (lane l, pixel k at (l % 8, l / 8 + 4 k) inside it); Gaussians are
+// staged NTH at a time in shared memory, and a warp skips every Gaussian
+// whose pixel rect misses its box (no pixel there can reach alpha = 1/255).
+template <int TS, int PPT>
+struct BoxMap {
+    static constexpr int BW = 8, BH = 4 * PPT, BPR = TS / BW;
+    int x0, y0;  // box origin (pixels)
+    __device__ BoxMap(int tx, int ty, int warp)
+    {
+        x0 = tx * TS + (warp % BPR) * BW;
+        y0 = ty * TS + (warp / BPR) * BH;
+    }
+    __device__ int px(int lane) const { return x0 + (lane & 7); }
+    __device__ int py(int lane, int k) const { return y0 + (lane >> 3) + 4 * k; }
+    // bit w set iff the packed rect (x0|y0<<16, x1|y1<<16) meets warp w's box
+    static __device__ unsigned mask(int tx, int ty, float lo, float hi)
+    {
+        constexpr int NB = TS * TS / (BW * BH);
+        int a = __float_as_int(lo), b = __float_as_int(hi);
+        int rx0 = (a & 0xffff) - tx * TS, ry0 = ((unsigned)a >> 16) - ty * TS;
+        int rx1 = (b & 0xffff) - tx * TS, ry1 = ((unsigned)b >> 16) - ty * TS;
+        // box columns [c0, c1] and rows [r0, r1] the rect overlaps (tile-local)
+        int c0 = max(rx0, 0) / BW, c1 = min(rx1, TS - 1) / BW;
+        int r0 = max(ry0, 0) / BH, r1 = min(ry1, TS - 1) / BH;
+        unsigned m = 0;
+#pragma unroll
+        for (int w = 0; w < NB; ++w) {
+            int c = w % BPR, r = w / BPR;
+            if (c >= c0 && c <= c1 && r >= r0 && r <= r1) m |= 1u << w;
+        }
+        return (rx1 < 0 || ry1 < 0 || rx0 >= TS || ry0 >= TS) ? 0u : m;
+    }
+};
 template <int TS, int PPT>
 __global__ void __launch_bounds__(TS *TS / PPT)
 blend_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_gauss, const float4 *__restrict__ rec0,
-             const float2 *__restrict__ rec1, const float4 *__restrict__ rec2, int W, int H, int ntx,
+             const float4 *__restrict__ rec1, const float4 *__restrict__ rec2, int W, int H, int ntx,
              float *__restrict__ image, float *__restrict__ T_final, int32_t *__restrict__ n_last)
 {
     constexpr int NTH = TS * TS / PPT;
     __shared__ float4 s0[NTH];
-    __shared__ float2 s1[NTH];
+    __shared__ float4 s1[NTH];
     __shared__ float4 s2[NTH];
+    __shared__ unsigned smask[NTH];
     const int tile = blockIdx.x;
     const int tx = tile % ntx, ty = tile / ntx;
     const int tid = threadIdx.x;
+    const unsigned wbit = 1u << (tid >> 5);
+    const BoxMap<TS, PPT> box(tx, ty, tid >> 5);
     float fx[PPT], fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
     int last[PPT];
     bool live[PPT];
     bool done = true;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        const int lp = k * NTH + tid;
-        const int px = tx * TS + lp % TS, py = ty * TS + lp / TS;
+        const int px = box.px(tid & 31), py = box.py(tid & 31, k);
         fx[k] = px + 0.5f;
         fy[k] = py + 0.5f;
         T[k] = 1.f;
@@ -552,15 +587,18 @@ blend_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_g
         if (idx < n) {
             int g = pair_gauss[rg.x + idx];
             s0[tid] = rec0[g];
-            s1[tid] = rec1[g];
+            float4 r1 = rec1[g];
+            s1[tid] = r1;
             s2[tid] = rec2[g];
+            smask[tid] = BoxMap<TS, PPT>::mask(tx, ty, r1.z, r1.w);
         }
         __syncthreads();
         if (!done) {
             int m = min(NTH, n - base);
             for (int j = 0; j < m; ++j) {
+                if (!(smask[j] & wbit)) continue;  // warp-uniform: rect misses this warp's box
+                float4 r1 = s1[j];
                 float4 r0 = s0[j];
-                float2 r1 = s1[j];
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
                     if (!live[k]) continue;
@@ -593,8 +631,7 @@ blend_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_g
     }
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        const int lp = k * NTH + tid;
-        const int px = tx * TS + lp % TS, py = ty * TS + lp / TS;
+        const int px = box.px(tid & 31), py = box.py(tid & 31, k);
         if (px < W && py < H) {
             const int pix = py * W + px;
             image[pix] = C0[k];
@@ -610,7 +647,7 @@ blend_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_g
 template <int TS, int PPT>
 __global__ void __launch_bounds__(TS *TS / PPT)
 blend_backward_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_gauss,
-                      const float4 *__restrict__ rec0, const float2 *__restrict__ rec1, const float4 *__restrict__ rec2,
+                      const float4 *__restrict__ rec0, const float4 *__restrict__ rec1, const float4 *__restrict__ rec2,
                       int W, int H, int ntx, const float *__restrict__ T_final, const int32_t *__restrict__ n_last,
                       const float *__restrict__ d_image, int G, float *__restrict__ d_mean2d,
                       float *__restrict__ d_conic, float *__restrict__ d_opacity, float *__restrict__ d_color)
@@ -618,20 +655,22 @@ blend_backward_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict
     constexpr int NTH = TS * TS / PPT;
     constexpr float LN2 = 0.6931471805599453f;
     __shared__ float4 s0[NTH];
-    __shared__ float2 s1[NTH];
+    __shared__ float4 s1[NTH];
     __shared__ float4 s2[NTH];
     __shared__ int sg[NTH];
+    __shared__ unsigned smask[NTH];
     __shared__ int s_max;
     const int tile = blockIdx.x;
     const int tx = tile % ntx, ty = tile / ntx;
     const int tid = threadIdx.x, lane = tid & 31;
+    const unsigned wbit = 1u << (tid >> 5);
+    const BoxMap<TS, PPT> box(tx, ty, tid >> 5);
     float fx[PPT], fy[PPT], T[PPT], dC0[PPT], dC1[PPT], dC2[PPT], acc0[PPT], acc1[PPT], acc2[PPT];
     int my_last[PPT];
     int mx_last = 0;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        const int lp = k * NTH + tid;
-        const int px = tx * TS + lp % TS, py = ty * TS + lp / TS;
+        const int px = box.px(lane), py = box.py(lane, k);
         const bool inside = px < W && py < H;
         const int pix = py * W + px;
         fx[k] = px + 0.5f;
@@ -658,14 +697,17 @@ blend_backward_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict
             int g = pair_gauss[rg.x + idx];
             sg[tid] = g;
             s0[tid] = rec0[g];
-            s1[tid] = rec1[g];
+            float4 r1 = rec1[g];
+            s1[tid] = r1;
             s2[tid] = rec2[g];
+            smask[tid] = BoxMap<TS, PPT>::mask(tx, ty, r1.z, r1.w);
         }
         __syncthreads();
         for (int j = end - 1; j >= start; --j) {
             const int sj = j - start;
+            if (!(smask[sj] & wbit)) continue;  // warp-uniform: rect misses this warp's box
+            const float4 r1 = s1[sj];
             const float4 r0 = s0[sj];
-            const float2 r1 = s1[sj];
             const float4 c = s2[sj];
             // per-thread sums over this thread's pixels
             float g_col0 = 0.f, g_col1 = 0.f, g_col2 = 0.f, g_op = 0.f, g_mx = 0.f, g_my = 0.f, g_ca = 0.f,

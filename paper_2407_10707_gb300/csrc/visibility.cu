@@ -105,7 +105,25 @@ __device__ __forceinline__ uint2 pack_proj(const Proj &q)
     return make_uint2(q.in ? ((unsigned)q.X | ((unsigned)q.Y << 16)) : OUTSIDE, (unsigned)q.Z);
 }
 
-template <int CL>
+// floor(num / den) for 0 < den < 2^20 and a quotient below 2^10 in magnitude
+// (|num| < 2^31): float estimate plus exact 32-bit remainder corrections.
+__device__ __forceinline__ int floor_div_i32(int num, int den)
+{
+    int q = (int)floorf(__fdividef((float)num, (float)den));
+    int r = num - q * den;
+    if (r < 0) {
+        --q;
+        r += den;
+        if (r < 0) --q;
+    } else if (r >= den) {
+        ++q;
+        r -= den;
+        if (r >= den) ++q;
+    }
+    return q;
+}
+
+template <int CL, bool CULL_BACK>
 __device__ __forceinline__ void raster_triangle(uint2 pa, uint2 pb, uint2 pc, int *slab, const VisParams &p,
                                                 cg::cluster_group &cluster)
 {
@@ -113,18 +131,28 @@ __device__ __forceinline__ void raster_triangle(uint2 pa, uint2 pb, uint2 pc, in
     int ax = pa.x & 0xffff, ay = pa.x >> 16, az = (int)pa.y;
     int bx = pb.x & 0xffff, by = pb.x >> 16, bz = (int)pb.y;
     int cx = pc.x & 0xffff, cy = pc.x >> 16, cz = (int)pc.y;
-    int area = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
-    if (area == 0) return;
-    if (area < 0) {
-        int t;
-        t = bx; bx = cx; cx = t;
-        t = by; by = cy; cy = t;
-        t = bz; bz = cz; cz = t;
-        area = -area;
-    }
     const int R = p.R;
+    // pixel centres 16i+8 inside the bounding box; most triangles have none
     int i0 = max(0, (min(ax, min(bx, cx)) + 7) >> 4), i1 = min(R - 1, (max(ax, max(bx, cx)) - 8) >> 4);
     int j0 = max(0, (min(ay, min(by, cy)) + 7) >> 4), j1 = min(R - 1, (max(ay, max(by, cy)) - 8) >> 4);
+    if (i0 > i1 || j0 > j1) return;
+    int area = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
+    if (CULL_BACK) {
+        if (area <= 0) return;  // faces away from the light (outward winding)
+    } else {
+        if (area == 0) return;
+        if (area < 0) {
+            int t;
+            t = bx; bx = cx; cx = t;
+            t = by; by = cy; cy = t;
+            t = bz; bz = cz; cz = t;
+            area = -area;
+        }
+    }
+    // depth = az + floor((wb (bz - az) + wc (cz - az)) / area) since wa + wb + wc = area;
+    // 32-bit arithmetic when the products provably fit, else 64-bit
+    const int dzb = bz - az, dzc = cz - az;
+    const bool small = area < (1 << 20) && abs(dzb) < (1 << 10) && abs(dzc) < (1 << 10);
     for (int j = j0; j <= j1; ++j) {
         const int py = 16 * j + 8;
         int *dst;
@@ -134,15 +162,20 @@ __device__ __forceinline__ void raster_triangle(uint2 pa, uint2 pb, uint2 pc, in
             int owner = (j * p.inv_rows) >> 20;  // exact j / rows_per_cta for j < 2^11
             dst = cluster.map_shared_rank(slab, owner) + (j - owner * p.rows_per_cta) * R;
         }
-        // edge functions are affine in px: e = e0 + (px - px0) * slope
         for (int i = i0; i <= i1; ++i) {
             const int px = 16 * i + 8;
             int wa = (cx - bx) * (py - by) - (cy - by) * (px - bx);
             int wb = (ax - cx) * (py - cy) - (ay - cy) * (px - cx);
             int wc = (bx - ax) * (py - ay) - (by - ay) * (px - ax);
             if ((wa | wb | wc) < 0) continue;
-            long long num = (long long)wa * az + (long long)wb * bz + (long long)wc * cz;
-            atomicMin(dst + i, floor_div_small(num, area));
+            int dep;
+            if (small) {
+                dep = az + floor_div_i32(wb * dzb + wc * dzc, area);
+            } else {
+                long long num = (long long)wa * az + (long long)wb * bz + (long long)wc * cz;
+                dep = floor_div_small(num, area);
+            }
+            atomicMin(dst + i, dep);
         }
     }
 }
@@ -184,7 +217,7 @@ __global__ void vis_chunk_ranges_kernel(const int32_t *__restrict__ faces, int F
     }
 }
 
-template <int CL>
+template <int CL, bool CULL_BACK>
 __global__ void __launch_bounds__(VIS_THREADS)
 vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *__restrict__ faces,
                        const int2 *__restrict__ vranges, const float *__restrict__ frames,
@@ -263,7 +296,7 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
                     pb = pack_proj(project_vertex(__ldg(qv + cur[t][1]), B, p));
                     pc = pack_proj(project_vertex(__ldg(qv + cur[t][2]), B, p));
                 }
-                raster_triangle<CL>(pa, pb, pc, slab, p, cluster);
+                raster_triangle<CL, CULL_BACK>(pa, pb, pc, slab, p, cluster);
             }
         }
         __syncthreads();  // the next chunk overwrites the cache
@@ -343,11 +376,11 @@ __global__ void vis_transpose_kernel(const uint32_t *__restrict__ dirbits, int N
     }
 }
 
-template <int CL>
+template <int CL, bool CULL_BACK>
 int launch_raster(const VisParams &p, const int4 *qv, const int32_t *faces, const int2 *vranges,
                   const float *frames, uint32_t *dirbits, int32_t *status, size_t smem, cudaStream_t st)
 {
-    auto kern = vis_raster_test_kernel<CL>;
+    auto kern = vis_raster_test_kernel<CL, CULL_BACK>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return AVATAR_ERR_CUDA;
     cudaLaunchConfig_t cfg = {};
@@ -462,12 +495,17 @@ extern "C" int avatar_visibility(avatar_ctx *ctx, const avatar_vis_args *a, void
         AV_CHECK_LAUNCH();
     }
     int rc;
+    const bool cb = a->cull_back != 0;
+#define AV_RASTER(CLV)                                                                                          \
+    (cb ? launch_raster<CLV, true>(p, w.qv, a->faces, w.vranges, a->frames, w.dirbits, a->status, smem, st)     \
+        : launch_raster<CLV, false>(p, w.qv, a->faces, w.vranges, a->frames, w.dirbits, a->status, smem, st))
     switch (CL) {
-        case 1: rc = launch_raster<1>(p, w.qv, a->faces, w.vranges, a->frames, w.dirbits, a->status, smem, st); break;
-        case 2: rc = launch_raster<2>(p, w.qv, a->faces, w.vranges, a->frames, w.dirbits, a->status, smem, st); break;
-        case 4: rc = launch_raster<4>(p, w.qv, a->faces, w.vranges, a->frames, w.dirbits, a->status, smem, st); break;
-        default: rc = launch_raster<8>(p, w.qv, a->faces, w.vranges, a->frames, w.dirbits, a->status, smem, st); break;
+        case 1: rc = AV_RASTER(1); break;
+        case 2: rc = AV_RASTER(2); break;
+        case 4: rc = AV_RASTER(4); break;
+        default: rc = AV_RASTER(8); break;
     }
+#undef AV_RASTER
     if (rc != AVATAR_OK) return rc;
 
     int nout = a->dmap ? a->NL : a->D;

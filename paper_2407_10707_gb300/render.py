@@ -36,10 +36,14 @@ def scene_tensors(scene, device="cuda"):
 
 class Renderer:
     """Preallocated forward frame.  forward() launches exactly the library's
-    kernels on the current stream."""
+    kernels on the current stream.  vis_cull_back rasterises only light-facing
+    triangles for visibility; it gives the same bits as the two-sided rule for
+    closed, outward-wound meshes such as the capsule body (set it to False
+    for open or inconsistently wound meshes)."""
 
-    def __init__(self, st, tile=16, pair_capacity=None):
+    def __init__(self, st, tile=16, pair_capacity=None, vis_cull_back=True):
         self.st = st
+        self.vis_cull_back = vis_cull_back
         t = st["avatar"]
         dev = t["xg"].device
         self.device = dev
@@ -70,7 +74,7 @@ class Renderer:
             self.vis_ws = self._vis_ws()
         api.avatar_visibility(self.sk["xp"], st["avatar"]["faces"], st["frames"], st["center"], st["half"],
                               st["bias"], st["depth_res"], dmap=st["dmap"], bits=self.bits, ws=self.vis_ws,
-                              status=self.status)
+                              status=self.status, cull_back=self.vis_cull_back)
 
     def _vis_ws(self):
         import ctypes as C
@@ -122,9 +126,9 @@ class Renderer:
 class TrainStep(Renderer):
     """Forward frame + L1 loss + backward through every stage."""
 
-    def __init__(self, st, target, tile=16, pair_capacity=None):
+    def __init__(self, st, target, tile=16, pair_capacity=None, vis_cull_back=True):
         self.target = target
-        super().__init__(st, tile, pair_capacity)
+        super().__init__(st, tile, pair_capacity, vis_cull_back)
         t = st["avatar"]
         self.loss = torch.empty(1, device=self.device)
         self.d_img = torch.empty_like(self.sb.image)

@@ -110,6 +110,16 @@ def test_visibility_bits_bit_exact(gpu, name, over):
     got = N(bits).view(np.uint32)
     assert got.shape == ref.shape
     assert np.array_equal(got, ref), f"{int((got != ref).sum())} words differ"
+    # one-sided rasterisation: same bits on this closed mesh, and bit-exact
+    # against the oracle's one-sided rule
+    ref1 = O.visibility(f32(xp).astype(np.float64), sc.avatar.faces, f32(sc.frames.reshape(-1, 9)).astype(np.float64),
+                        f32(sc.window_center), float(np.float32(sc.window_half)), float(np.float32(sc.vis_bias)),
+                        sc.depth_res, cull_back=True)
+    bits1 = api.avatar_visibility(c["xp"], c["faces"], c["frames"], c["center"], c["half"], c["bias"], c["R"],
+                                  cull_back=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(N(bits1).view(np.uint32), ref1)
+    assert np.array_equal(ref1, ref)
     # light-ordered output through d(k)
     dmap = T(sc.dmap, torch.int32)
     bits_l = api.avatar_visibility(c["xp"], c["faces"], c["frames"], c["center"], c["half"], c["bias"], c["R"],

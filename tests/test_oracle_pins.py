@@ -205,6 +205,29 @@ def test_visibility_convex_sphere_hemisphere():
     assert np.all(vb[cosines <= -tau] == 0)
 
 
+def test_visibility_one_sided_equals_two_sided_on_a_closed_mesh():
+    # the capsule body is a union of watertight, outward-wound meshes: the
+    # nearest surface along any ray toward a light faces that light, so
+    # rasterising only light-facing triangles gives the same depth maps
+    sc = synth.config_scene("c1_small", n_dirs=64, depth_res=128)
+    av = sc.avatar
+    sk = O.skin(av, O.fk(av.parents, av.joints, av.pose))
+    xp = np.asarray(sk["xp"], np.float32).astype(np.float64)
+    fr = np.asarray(sc.frames.reshape(-1, 9), np.float32).astype(np.float64)
+    args = (xp, av.faces, fr, sc.window_center, sc.window_half, sc.vis_bias, sc.depth_res)
+    b2, d2 = O.visibility(*args, want_depth=True)
+    b1, d1 = O.visibility(*args, want_depth=True, cull_back=True)
+    assert np.array_equal(d1, d2)
+    assert np.array_equal(b1, b2)
+    # but not on an open surface seen from behind: a lone triangle casts no
+    # shadow from its back side when culled
+    tri = np.array([[0.0, 0, 0], [0.3, 0, 0], [0, 0.3, 0]])
+    dirs = np.array([[0, 0, -1.0]] * 32)
+    _, dd = O.visibility(tri, np.array([[0, 1, 2]], np.int32), _frames_for(dirs), [0.1, 0.1, 0], 1.0, 0.0,
+                         64, want_depth=True, cull_back=True)
+    assert np.all(dd == np.iinfo(np.int32).max)
+
+
 def test_visibility_depth_map_of_a_plane():
     # one big triangle facing +z; depth at each covered pixel centre equals the
     # plane's depth (zd = -z * 2^16) up to the integer floor and quantisation.
