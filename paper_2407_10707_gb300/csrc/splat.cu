@@ -594,39 +594,57 @@ blend_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_g
         }
         __syncthreads();
         if (!done) {
-            int m = min(NTH, n - base);
-            for (int j = 0; j < m; ++j) {
-                if (!(smask[j] & wbit)) continue;  // warp-uniform: rect misses this warp's box
-                float4 r1 = s1[j];
-                float4 r0 = s0[j];
+            const int m = min(NTH, n - base);
+            // one Gaussian's contribution to pixel k (the front-to-back step)
+            auto step = [&](int j, int k, float l2a) {
+                if (l2a < LOG2_ALPHA_MIN) return;
+                float alpha = fminf(0.99f, exp2f(l2a));
+                float test_T = T[k] * (1.f - alpha);
+                if (test_T < T_MIN) {
+                    live[k] = false;
+                    return;
+                }
+                float4 c = s2[j];
+                float wgt = alpha * T[k];
+                C0[k] = fmaf(c.x, wgt, C0[k]);
+                C1[k] = fmaf(c.y, wgt, C1[k]);
+                C2[k] = fmaf(c.z, wgt, C2[k]);
+                T[k] = test_T;
+                last[k] = base + j + 1;
+            };
+            auto l2alpha = [&](int j, int k) {
+                const float4 r0 = s0[j];
+                const float4 r1 = s1[j];
+                float dx = fx[k] - r0.x, dy = fy[k] - r0.y;
+                return fmaf(fmaf(r0.z, dx, r0.w * dy), dx, fmaf(r1.x * dy, dy, r1.y));
+            };
+            int j = 0;
+            // two Gaussians per iteration: both exponents are independent of T
+            for (; j + 1 < m; j += 2) {
+                const bool m0 = smask[j] & wbit, m1 = smask[j + 1] & wbit;  // warp-uniform
+                if (!(m0 || m1)) continue;
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
                     if (!live[k]) continue;
-                    float dx = fx[k] - r0.x, dy = fy[k] - r0.y;
-                    float l2a = fmaf(fmaf(r0.z, dx, r0.w * dy), dx, fmaf(r1.x * dy, dy, r1.y));
-                    if (l2a < LOG2_ALPHA_MIN) continue;
-                    float alpha = fminf(0.99f, exp2f(l2a));
-                    float test_T = T[k] * (1.f - alpha);
-                    if (test_T < T_MIN) {
-                        live[k] = false;
-                        continue;
-                    }
-                    float4 c = s2[j];
-                    float wgt = alpha * T[k];
-                    C0[k] = fmaf(c.x, wgt, C0[k]);
-                    C1[k] = fmaf(c.y, wgt, C1[k]);
-                    C2[k] = fmaf(c.z, wgt, C2[k]);
-                    T[k] = test_T;
-                    last[k] = base + j + 1;
+                    float a0 = m0 ? l2alpha(j, k) : -1e30f;
+                    float a1 = m1 ? l2alpha(j + 1, k) : -1e30f;
+                    step(j, k, a0);
+                    if (live[k]) step(j + 1, k, a1);
                 }
                 bool any = false;
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) any = any || live[k];
-                if (!any) {
-                    done = true;
-                    break;
-                }
+                if (!any) break;
             }
+            if (j < m && (smask[j] & wbit)) {
+#pragma unroll
+                for (int k = 0; k < PPT; ++k)
+                    if (live[k]) step(j, k, l2alpha(j, k));
+            }
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) any = any || live[k];
+            if (!any) done = true;
         }
     }
 #pragma unroll

@@ -61,8 +61,11 @@ __device__ __forceinline__ Proj project_vertex(int4 q, const int *B, const VisPa
     int t = B[3] * q.x + B[4] * q.y + B[5] * q.z;
     int z = B[6] * q.x + B[7] * q.y + B[8] * q.z;
     Proj r;
-    r.X = (int)((((long long)s + p.H) * (long long)p.M) >> 32);
-    r.Y = (int)((((long long)t + p.H) * (long long)p.M) >> 32);
+    // X = floor((s + H) M / 2^32): one high-half multiply when s + H >= 0
+    // (s + H < 2^31 by the bounds); s + H < 0 lies left of the window
+    const int sh = s + p.H, th = t + p.H;
+    r.X = sh >= 0 ? (int)__umulhi((unsigned)sh, (unsigned)p.M) : -1;
+    r.Y = th >= 0 ? (int)__umulhi((unsigned)th, (unsigned)p.M) : -1;
     r.Z = (-z) >> 10;
     const int lim = 16 * p.R;
     r.in = (q.w == 0) && ((unsigned)r.X < (unsigned)lim) && ((unsigned)r.Y < (unsigned)lim);
