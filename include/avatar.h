@@ -261,6 +261,33 @@ typedef struct {
 
 int avatar_shade(avatar_ctx *ctx, const avatar_shade_args *a, avatar_stream_t stream);
 
+/* Relighting under many environment lights at once (the relighting use of
+ * Sec. 3.5 applied to Eq. 2): every light l shares the texel geometry of
+ * `base` (light_w, light_A) and has its own radiance env_L[l].  Because the
+ * sums of Eq. 2 are linear in the radiance,
+ *   L_o[g,(l,c)] = a_gc/pi (D B)[g,(l,c)] + p_g (S B)[g,(l,c)],
+ *   D = vis * max(0, n.w_k), S = D * f_s, B[k,(l,c)] = L^(l)_kc A_k,
+ * which this call evaluates on the tensor cores (tcgen05, BF16 operands,
+ * FP32 accumulation in TMEM); D and S are rounded to BF16 (relative error
+ * 2^-9 per term).  Colours follow avatar_shade (gamma 2.2, culled -> 0);
+ * `base.light_L` and `base.radiance` are not used, `base.cull` is written.
+ * A first pass writes the culled colours and lists the live Gaussians in
+ * the workspace, so the tensor-core tiles hold live rows only.
+ * Requires NL a multiple of 64 and at most 512, 1 <= n_env <= 32;
+ * otherwise AVATAR_ERR_UNSUPPORTED / AVATAR_ERR_INVALID_ARG. */
+typedef struct {
+    avatar_shade_args base;
+    int n_env;             /* number of environment lights */
+    const float *env_L;    /* [n_env][NL][3] radiance of each light */
+    float *env_color;      /* [n_env][3][G] output colours */
+    void *workspace;       /* device scratch, avatar_shade_multi_workspace_size bytes */
+    size_t workspace_bytes;
+} avatar_shade_multi_args;
+
+/* Workspace bytes for avatar_shade_multi (depends on base.G only). */
+size_t avatar_shade_multi_workspace_size(const avatar_shade_multi_args *a);
+int avatar_shade_multi(avatar_ctx *ctx, const avatar_shade_multi_args *a, avatar_stream_t stream);
+
 typedef struct {
     const float *d_color;  /* [3][G] upstream */
     float *d_xd;           /* [3][G] written (through w_o) */

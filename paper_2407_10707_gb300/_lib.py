@@ -59,6 +59,11 @@ class ShadeArgs(C.Structure):
                 ("cam_center", F32 * 3), ("color", P), ("radiance", P), ("cull", P), ("status", P)]
 
 
+class ShadeMultiArgs(C.Structure):
+    _fields_ = [("base", ShadeArgs), ("n_env", I32), ("env_L", P), ("env_color", P), ("workspace", P),
+                ("workspace_bytes", C.c_size_t)]
+
+
 class ShadeGrads(C.Structure):
     _fields_ = [("d_color", P), ("d_xd", P), ("d_nd", P), ("d_ag", P), ("d_rg", P), ("d_pg", P),
                 ("d_ubar", P), ("d_light_L", P)]
@@ -100,6 +105,8 @@ _SIGNATURES = [
     ("avatar_visibility_static_scratch", [P, C.POINTER(VisArgs), P], I32),
     ("avatar_shade", [P, C.POINTER(ShadeArgs), P], I32),
     ("avatar_shade_backward", [P, C.POINTER(ShadeArgs), C.POINTER(ShadeGrads), P], I32),
+    ("avatar_shade_multi_workspace_size", [C.POINTER(ShadeMultiArgs)], C.c_size_t),
+    ("avatar_shade_multi", [P, C.POINTER(ShadeMultiArgs), P], I32),
     ("avatar_splat_num_tiles", [C.POINTER(SplatArgs)], I32),
     ("avatar_splat_workspace_size", [C.POINTER(SplatArgs)], C.c_size_t),
     ("avatar_splat_project", [P, C.POINTER(SplatArgs), P, C.c_size_t, P], I32),

@@ -223,6 +223,32 @@ def avatar_shade(sk, knn, bits, light, cam_center, out=None, status=None):
     return out
 
 
+def avatar_shade_multi(sk, knn, bits, light, cam_center, env_L, out=None, cull=None, status=None, ws=None):
+    """Colours under n_env environment lights sharing light['A'], light['w']
+    (tensor-core path).  env_L: [n_env, NL, 3].  Returns [n_env, 3, G]."""
+    lib = L.load()
+    ctx = context()
+    dev = sk["xd"].device
+    G = sk["xd"].shape[1]
+    n_env = env_L.shape[0]
+    env_L = env_L.contiguous()
+    if out is None:
+        out = torch.empty(n_env, 3, G, device=dev)
+    if cull is None:
+        cull = torch.empty(G, dtype=torch.uint8, device=dev)
+    m = L.ShadeMultiArgs()
+    m.base = _shade_struct(sk, knn, bits, dict(light, L=light.get("L", env_L[0])), cam_center, None, None, cull, status)
+    m.n_env = n_env
+    m.env_L = _p(env_L)
+    m.env_color = _p(out)
+    need = lib.avatar_shade_multi_workspace_size(C.byref(m))
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    m.workspace, m.workspace_bytes = _p(ws), ws.numel()
+    L.check(lib.avatar_shade_multi(ctx, C.byref(m), _stream()), "avatar_shade_multi")
+    return out
+
+
 def avatar_shade_backward(sk, knn, bits, light, cam_center, out, d_color):
     lib = L.load()
     ctx = context()
