@@ -52,6 +52,16 @@ enum avatar_status {
     AVATAR_ERR_INDEX = 7         /* device: an index array entry is out of range */
 };
 
+/* Storage type of the learnable per-Gaussian / per-vertex attributes that a
+ * struct marks "(attr_dtype)": albedo, roughness, specular tint, opacity,
+ * log-scale and rotation.  Positions, displacements, LBS weights and the
+ * light stay FP32 (a BF16 position step is ~4 mm at 1 m, a BF16 weight sum
+ * is off by up to 2^-9).  All arithmetic is FP32 either way. */
+enum avatar_dtype {
+    AVATAR_DTYPE_F32 = 0,
+    AVATAR_DTYPE_BF16 = 1        /* bfloat16, round-to-nearest-even from FP32 */
+};
+
 /* Static English description of a status code; never NULL. */
 const char *avatar_status_string(int status);
 
@@ -103,16 +113,16 @@ typedef struct {
     int J;                 /* joints, 1..64 (SMPL: 24) */
     /* canonical Gaussians */
     const float *xg;       /* [3][G] positions */
-    const float *logscale; /* [3][G] log of the three axis scales */
-    const float *quat;     /* [4][G] rotation quaternion (w,x,y,z), any norm > 0 */
+    const void *logscale;  /* [3][G] log of the three axis scales (attr_dtype) */
+    const void *quat;      /* [4][G] rotation quaternion (w,x,y,z), any norm > 0 (attr_dtype) */
     const int32_t *knn;    /* [K][G] indices of the K nearest vertices (S_g) */
     /* canonical mesh attributes */
     const float *xv;       /* [3][Nv] positions */
     const float *dxv;      /* [3][Nv] displacement, or NULL for zero */
     const float *wv;       /* [Nv][J] LBS weights, vertex-major */
-    const float *av;       /* [3][Nv] albedo */
-    const float *rv;       /* [Nv] roughness */
-    const float *pv;       /* [Nv] specular tint */
+    const void *av;        /* [3][Nv] albedo (attr_dtype) */
+    const void *rv;        /* [Nv] roughness (attr_dtype) */
+    const void *pv;        /* [Nv] specular tint (attr_dtype) */
     const float *nv;       /* [3][Nv] normals */
     /* skeleton */
     const int32_t *parents; /* [J] parent index, parents[j] < j, root -1 */
@@ -129,6 +139,7 @@ typedef struct {
     float *pg;             /* [G] specular tint */
     float *ubar;           /* [K][G] normalised Eq. 1 weights */
     int32_t *status;       /* optional device status word */
+    int attr_dtype;        /* storage of the (attr_dtype) inputs: AVATAR_DTYPE_F32 or _BF16 */
 } avatar_skin_args;
 
 /* Workspace for avatar_skin: per-vertex packed records (Nv*112 bytes).
@@ -270,10 +281,14 @@ int avatar_shade(avatar_ctx *ctx, const avatar_shade_args *a, avatar_stream_t st
  * which this call evaluates on the tensor cores (tcgen05, BF16 operands,
  * FP32 accumulation in TMEM); D and S are rounded to BF16 (relative error
  * 2^-9 per term).  Colours follow avatar_shade (gamma 2.2, culled -> 0);
- * `base.light_L` and `base.radiance` are not used, `base.cull` is written.
+ * `base.light_L` and `base.color` are not used, `base.cull` is written, and
+ * with n_env == 1 a non-null `base.radiance` receives L_o before gamma (so
+ * avatar_shade_backward can follow this call in a training step).
  * A first pass writes the culled colours and lists the live Gaussians in
  * the workspace, so the tensor-core tiles hold live rows only.
- * Requires NL a multiple of 64 and at most 512, 1 <= n_env <= 32;
+ * Requires NL a multiple of 64 and at most 2048, 1 <= n_env <= 32, and the
+ * resident light matrix (3 n_env rounded up to 16, times NL, BF16) plus 64 KB
+ * of tiles and 16 B per light within the shared memory of one SM;
  * otherwise AVATAR_ERR_UNSUPPORTED / AVATAR_ERR_INVALID_ARG. */
 typedef struct {
     avatar_shade_args base;
@@ -328,7 +343,7 @@ typedef struct {
     int tile;              /* tile edge: 8, 16 or 32 pixels; 0 = 16 */
     const float *xd;       /* [3][G] */
     const float *cov;      /* [6][G] */
-    const float *opacity;  /* [G] */
+    const void *opacity;   /* [G] (attr_dtype) */
     const float *color;    /* [3][G] */
     const uint8_t *cull;   /* [G] or NULL */
     /* per-Gaussian projection (written by project) */
@@ -346,6 +361,7 @@ typedef struct {
     float *T_final;        /* [H][W] final transmittance */
     int32_t *n_last;       /* [H][W] list positions traversed up to the last contributor */
     int32_t *status;
+    int attr_dtype;        /* storage of opacity: AVATAR_DTYPE_F32 or _BF16 */
 } avatar_splat_args;
 
 /* ntiles = ceil(W/tile) * ceil(H/tile). */

@@ -20,6 +20,8 @@ STATUS = {0: "AVATAR_OK", 1: "AVATAR_ERR_INVALID_ARG", 2: "AVATAR_ERR_WORKSPACE"
           4: "AVATAR_ERR_TIMEOUT", 5: "AVATAR_ERR_CUDA", 6: "AVATAR_ERR_UNSUPPORTED", 7: "AVATAR_ERR_INDEX"}
 
 
+DTYPE_F32 = 0   # avatar_dtype
+DTYPE_BF16 = 1
 TUNE_BLEND_PPT = 0
 TUNE_BLEND_BWD_PPT = 1
 
@@ -36,7 +38,7 @@ class SkinArgs(C.Structure):
                 ("xv", P), ("dxv", P), ("wv", P), ("av", P), ("rv", P), ("pv", P), ("nv", P),
                 ("parents", P), ("joints", P), ("pose", P),
                 ("bone", P), ("xp", P), ("xd", P), ("cov", P), ("nd", P), ("ag", P), ("rg", P),
-                ("pg", P), ("ubar", P), ("status", P)]
+                ("pg", P), ("ubar", P), ("status", P), ("attr_dtype", I32)]
 
 
 class SkinGrads(C.Structure):
@@ -79,7 +81,7 @@ class SplatArgs(C.Structure):
                 ("xd", P), ("cov", P), ("opacity", P), ("color", P), ("cull", P),
                 ("mean2d", P), ("conic", P), ("depth", P), ("rect", P),
                 ("tile_range", P), ("pair_gauss", P), ("pair_capacity", C.c_int64), ("num_pairs", P),
-                ("image", P), ("T_final", P), ("n_last", P), ("status", P)]
+                ("image", P), ("T_final", P), ("n_last", P), ("status", P), ("attr_dtype", I32)]
 
 
 class SplatGrads(C.Structure):

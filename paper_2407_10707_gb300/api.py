@@ -63,14 +63,35 @@ def raise_on_status(status, where="device"):
 
 
 # ---------------------------------------------------------------- inputs
-def avatar_tensors(av, device="cuda"):
-    """Device layout of a synth.Avatar: SoA float32, int32 indices."""
+# Learnable attributes that may be stored in BF16 (AVATAR_DTYPE_BF16).
+ATTR_KEYS = ("logscale", "quat", "opacity", "av", "rv", "pv")
+
+
+def avatar_tensors(av, device="cuda", attr_dtype="f32"):
+    """Device layout of a synth.Avatar: SoA float32, int32 indices; with
+    attr_dtype='bf16' the ATTR_KEYS tensors are stored as bfloat16."""
     f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=device)
     i = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.int32, device=device)
-    return dict(xg=f(av.xg.T), logscale=f(av.logscale.T), quat=f(av.quat.T), opacity=f(av.opacity),
-                knn=i(av.knn.T), xv=f(av.xv.T), dxv=f(av.dxv.T), wv=f(av.wv), av=f(av.av.T), rv=f(av.rv),
-                pv=f(av.pv), nv=f(av.nv.T), parents=i(av.parents), joints=f(av.joints), pose=f(av.pose),
-                faces=i(av.faces))
+    t = dict(xg=f(av.xg.T), logscale=f(av.logscale.T), quat=f(av.quat.T), opacity=f(av.opacity),
+             knn=i(av.knn.T), xv=f(av.xv.T), dxv=f(av.dxv.T), wv=f(av.wv), av=f(av.av.T), rv=f(av.rv),
+             pv=f(av.pv), nv=f(av.nv.T), parents=i(av.parents), joints=f(av.joints), pose=f(av.pose),
+             faces=i(av.faces))
+    if attr_dtype == "bf16":
+        for k in ATTR_KEYS:
+            t[k] = t[k].to(torch.bfloat16)
+    elif attr_dtype != "f32":
+        raise ValueError(f"attr_dtype must be 'f32' or 'bf16', not {attr_dtype!r}")
+    return t
+
+
+def _dtype_code(*tensors):
+    """AVATAR_DTYPE_* of the attribute tensors given (all must agree)."""
+    kinds = {x.dtype for x in tensors if x is not None}
+    if not kinds:
+        return L.DTYPE_F32
+    if len(kinds) > 1 or not kinds <= {torch.float32, torch.bfloat16}:
+        raise ValueError(f"attribute tensors must all be float32 or all bfloat16, got {sorted(map(str, kinds))}")
+    return L.DTYPE_BF16 if kinds == {torch.bfloat16} else L.DTYPE_F32
 
 
 def camera_struct(cam):
@@ -100,6 +121,7 @@ def _skin_struct(t, out, status):
     for k in ("bone", "xp", "xd", "cov", "nd", "ag", "rg", "pg", "ubar"):
         setattr(a, k, _p(out[k]))
     a.status = _p(status)
+    a.attr_dtype = _dtype_code(*(t.get(k) for k in ("logscale", "quat", "av", "rv", "pv")))
     return a
 
 
@@ -141,8 +163,8 @@ def avatar_skin_backward(t, out, up, want=("xg", "logscale", "quat", "wv", "av",
         keep.append(v)
         setattr(g, k, _p(v))
     res = {}
-    for k in want:
-        res[k] = torch.empty_like(t[k])
+    for k in want:   # gradients are FP32 whatever the storage type
+        res[k] = torch.empty_like(t[k], dtype=torch.float32)
         setattr(g, "d_" + k, _p(res[k]))
     need = lib.avatar_skin_backward_workspace_size(C.byref(a))
     ws = workspace(need, dev)
@@ -223,9 +245,11 @@ def avatar_shade(sk, knn, bits, light, cam_center, out=None, status=None):
     return out
 
 
-def avatar_shade_multi(sk, knn, bits, light, cam_center, env_L, out=None, cull=None, status=None, ws=None):
+def avatar_shade_multi(sk, knn, bits, light, cam_center, env_L, out=None, cull=None, status=None, ws=None,
+                       radiance=None):
     """Colours under n_env environment lights sharing light['A'], light['w']
-    (tensor-core path).  env_L: [n_env, NL, 3].  Returns [n_env, 3, G]."""
+    (tensor-core path).  env_L: [n_env, NL, 3].  Returns [n_env, 3, G];
+    with n_env == 1, `radiance` ([3, G]) receives L_o before gamma."""
     lib = L.load()
     ctx = context()
     dev = sk["xd"].device
@@ -237,7 +261,8 @@ def avatar_shade_multi(sk, knn, bits, light, cam_center, env_L, out=None, cull=N
     if cull is None:
         cull = torch.empty(G, dtype=torch.uint8, device=dev)
     m = L.ShadeMultiArgs()
-    m.base = _shade_struct(sk, knn, bits, dict(light, L=light.get("L", env_L[0])), cam_center, None, None, cull, status)
+    m.base = _shade_struct(sk, knn, bits, dict(light, L=light.get("L", env_L[0])), cam_center, None, radiance, cull,
+                           status)
     m.n_env = n_env
     m.env_L = _p(env_L)
     m.env_color = _p(out)
@@ -314,6 +339,7 @@ def _splat_struct(G, cam, xd, cov, opacity, color, cull, b: SplatBuffers, status
     a.pair_capacity = b.pair_gauss.numel()
     a.image, a.T_final, a.n_last = _p(b.image), _p(b.T_final), _p(b.n_last)
     a.status = _p(status)
+    a.attr_dtype = _dtype_code(opacity)
     return a
 
 
@@ -351,8 +377,8 @@ def avatar_splat_backward(xd, cov, opacity, color, cull, cam, b, d_image):
     G = xd.shape[1]
     a = _splat_struct(G, cam, xd, cov, opacity, color, cull, b, None)
     d_image = d_image.contiguous()
-    res = dict(xd=torch.empty_like(xd), cov=torch.empty_like(cov), opacity=torch.empty_like(opacity),
-               color=torch.empty_like(color))
+    res = dict(xd=torch.empty_like(xd), cov=torch.empty_like(cov),
+               opacity=torch.empty_like(opacity, dtype=torch.float32), color=torch.empty_like(color))
     g = L.SplatGrads()
     g.d_image = _p(d_image)
     g.d_xd, g.d_cov, g.d_opacity, g.d_color = _p(res["xd"]), _p(res["cov"]), _p(res["opacity"]), _p(res["color"])

@@ -1,6 +1,7 @@
 // Shared device helpers of the sm_103a relit-avatar library.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -82,6 +83,13 @@ __device__ __forceinline__ float4 ldg_stream4(const float4 *p)
                  : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                  : "l"(p));
     return v;
+}
+
+// Element i of an attribute array stored as FP32 or BF16 (attr_dtype).
+__device__ __forceinline__ float ld_attr(const void *p, size_t i, int dtype)
+{
+    return dtype == AVATAR_DTYPE_BF16 ? __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16 *>(p) + i))
+                                      : __ldg(reinterpret_cast<const float *>(p) + i);
 }
 
 constexpr float AV_PI = 3.14159265358979323846f;

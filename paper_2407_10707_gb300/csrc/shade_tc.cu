@@ -23,7 +23,7 @@ constexpr int TC_M = 128;        // Gaussians per tile (tensor-core M)
 constexpr int TC_THREADS = 512;  // four threads per Gaussian row (16 lights each per chunk)
 constexpr int TC_KC = 64;        // lights per chunk
 constexpr int TC_MAX_ENV = 32;   // N = 3 * n_env <= 96
-constexpr int TC_MAX_K = 512;    // resident stacked-light matrix
+constexpr int TC_MAX_K = 2048;   // resident stacked-light matrix (shared-memory size permitting)
 constexpr int TC_TMEM_COLS = 256;
 constexpr int TC_WAIT_LIMIT = 1 << 22;
 constexpr float FRES_C1 = -5.55473f;
@@ -139,8 +139,11 @@ tc_compact_kernel(avatar_shade_args s, int n_env, float *env_color, int32_t *liv
         if (!ok) av_report(s.status, AVATAR_ERR_INDEX);
         live = ok && !culled_fp32(x, n, s.cam_center);
         if (s.cull) s.cull[g] = (uint8_t)(live ? 0 : 1);
-        if (!live)
+        if (!live) {
             for (int c = 0; c < 3 * n_env; ++c) env_color[(size_t)c * s.G + g] = 0.f;
+            if (s.radiance && n_env == 1)
+                for (int c = 0; c < 3; ++c) s.radiance[(size_t)c * s.G + g] = 0.f;
+        }
     }
     const unsigned bal = __ballot_sync(0xffffffffu, live);
     if (lane == 0) s_warp[warp] = __popc(bal);
@@ -328,6 +331,7 @@ shade_multi_tc_kernel(TcParams P)
             const int col0 = ((warp >> 2) & 1) * (N / 2);
             const bool epi = warp < 8;  // warps 0-7 read the accumulators
             const int gr = s_g[wl * 32 + lane];
+            const bool want_rad = s.radiance != nullptr && P.n_env == 1;
             const bool ok = gr >= 0;
             float ar[3] = {0, 0, 0}, pr = 0.f;
             if (ok) {
@@ -347,6 +351,7 @@ shade_multi_tc_kernel(TcParams P)
                     if (!ok || nn >= 3 * P.n_env) continue;
                     const float Lo = ar[nn % 3] * dv[i] + pr * sv[i];
                     P.env_color[(size_t)nn * G + gr] = exp2f(log2f(fmaxf(Lo, 1e-6f)) * INV_GAMMA);
+                    if (want_rad) s.radiance[(size_t)nn * G + gr] = Lo;
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -158,8 +158,9 @@ skin_vertices_kernel(avatar_skin_args a, VertexRec *__restrict__ rec)
         r.a0 = make_float4(A[0], A[1], A[2], A[3]);
         r.a1 = make_float4(A[4], A[5], A[6], A[7]);
         r.a2 = make_float4(A[8], A[9], A[10], A[11]);
-        r.xr = make_float4(x, y, z, a.rv[v]);
-        r.ap = make_float4(a.av[v], a.av[Nv + v], a.av[2 * Nv + v], a.pv[v]);
+        r.xr = make_float4(x, y, z, ld_attr(a.rv, v, a.attr_dtype));
+        r.ap = make_float4(ld_attr(a.av, v, a.attr_dtype), ld_attr(a.av, (size_t)Nv + v, a.attr_dtype),
+                           ld_attr(a.av, (size_t)2 * Nv + v, a.attr_dtype), ld_attr(a.pv, v, a.attr_dtype));
         r.nd0 = make_float4(a.nv[v], a.nv[Nv + v], a.nv[2 * Nv + v], dx);
         r.d12 = make_float4(dy, dz, 0.f, 0.f);
         rec[v] = r;
@@ -274,13 +275,15 @@ skin_gaussians_kernel(avatar_skin_args a, const VertexRec *__restrict__ rec)
         for (int i = 0; i < 3; ++i)
             a.xd[i * G + g] = fmaf(A[4 * i], xb0, fmaf(A[4 * i + 1], xb1, fmaf(A[4 * i + 2], xb2, A[4 * i + 3])));
         // covariance
-        float qw = a.quat[g], qx = a.quat[G + g], qy = a.quat[2 * G + g], qz = a.quat[3 * G + g];
+        const int dt = a.attr_dtype;
+        float qw = ld_attr(a.quat, g, dt), qx = ld_attr(a.quat, (size_t)G + g, dt),
+              qy = ld_attr(a.quat, (size_t)2 * G + g, dt), qz = ld_attr(a.quat, (size_t)3 * G + g, dt);
         float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
         float R[9];
         quat_to_rot(qw * qn, qx * qn, qy * qn, qz * qn, R);
         float s2[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) s2[i] = expf(2.f * a.logscale[i * G + g]);
+        for (int i = 0; i < 3; ++i) s2[i] = expf(2.f * ld_attr(a.logscale, (size_t)i * G + g, dt));
         // MR = M * R * diag(s):  cov = (MR)(MR)^T
         float MR[9];
 #pragma unroll
@@ -352,14 +355,16 @@ skin_gaussians_backward_kernel(avatar_skin_args a, avatar_skin_grads gr, const V
             }
         }
         // ---- covariance: cov = M Sigma M^T, Sigma = R diag(s2) R^T
-        float qw0 = a.quat[g], qx0 = a.quat[G + g], qy0 = a.quat[2 * G + g], qz0 = a.quat[3 * G + g];
+        const int adt = a.attr_dtype;
+        float qw0 = ld_attr(a.quat, g, adt), qx0 = ld_attr(a.quat, (size_t)G + g, adt),
+              qy0 = ld_attr(a.quat, (size_t)2 * G + g, adt), qz0 = ld_attr(a.quat, (size_t)3 * G + g, adt);
         float qinv = rsqrtf(qw0 * qw0 + qx0 * qx0 + qy0 * qy0 + qz0 * qz0);
         float qw = qw0 * qinv, qx = qx0 * qinv, qy = qy0 * qinv, qz = qz0 * qinv;
         float R[9];
         quat_to_rot(qw, qx, qy, qz, R);
         float s2[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) s2[i] = expf(2.f * a.logscale[i * G + g]);
+        for (int i = 0; i < 3; ++i) s2[i] = expf(2.f * ld_attr(a.logscale, (size_t)i * G + g, adt));
         float dls[3] = {0, 0, 0}, dq[4] = {0, 0, 0, 0};
         if (gr.d_cov) {
             float dc[6];
@@ -567,6 +572,7 @@ int check_skin_args(const avatar_skin_args *a)
                      !a->ag || !a->rg || !a->pg || !a->ubar))
         return AVATAR_ERR_INVALID_ARG;
     if ((a->J & 3) == 0 && (((uintptr_t)a->wv) & 15)) return AVATAR_ERR_INVALID_ARG;
+    if (a->attr_dtype != AVATAR_DTYPE_F32 && a->attr_dtype != AVATAR_DTYPE_BF16) return AVATAR_ERR_INVALID_ARG;
     return AVATAR_OK;
 }
 

@@ -109,7 +109,7 @@ project_kernel(avatar_splat_args a, CamDev cam)
     const int G = a.G;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
         float x = a.xd[g], y = a.xd[G + g], z = a.xd[2 * G + g];
-        float o = a.opacity[g];
+        float o = ld_attr(a.opacity, g, a.attr_dtype);
         float px = cam.R[0] * x + cam.R[1] * y + cam.R[2] * z + cam.t[0];
         float py = cam.R[3] * x + cam.R[4] * y + cam.R[5] * z + cam.t[1];
         float pz = cam.R[6] * x + cam.R[7] * y + cam.R[8] * z + cam.t[2];
@@ -198,7 +198,7 @@ bin_keys_kernel(avatar_splat_args a, int TS, SplatWs w)
         w.dkey_a[g] = n > 0 ? __float_as_uint(a.depth[g]) : 0xffffffffu;
         w.dval_a[g] = g;
         const float L2E = 1.4426950408889634f;
-        float o = a.opacity[g];
+        float o = ld_attr(a.opacity, g, a.attr_dtype);
         w.rec0[g] = make_float4(a.mean2d[g], a.mean2d[G + g], -0.5f * L2E * a.conic[g], -L2E * a.conic[G + g]);
         w.rec1[g] = make_float4(-0.5f * L2E * a.conic[2 * G + g], o > 0.f ? log2f(o) : -1e30f,
                                 __int_as_float((x0 & 0xffff) | (y0 << 16)), __int_as_float((x1 & 0xffff) | (y1 << 16)));
@@ -894,6 +894,7 @@ int check_splat(const avatar_splat_args *a)
         return AVATAR_ERR_INVALID_ARG;
     if (!a->tile_range || !a->pair_gauss || !a->num_pairs || !a->image || !a->T_final || !a->n_last)
         return AVATAR_ERR_INVALID_ARG;
+    if (a->attr_dtype != AVATAR_DTYPE_F32 && a->attr_dtype != AVATAR_DTYPE_BF16) return AVATAR_ERR_INVALID_ARG;
     return AVATAR_OK;
 }
 

@@ -22,10 +22,11 @@ import torch
 from . import api
 
 
-def scene_tensors(scene, device="cuda"):
-    """Device copies of a synth.Scene (SoA float32 / int32)."""
+def scene_tensors(scene, device="cuda", attr_dtype="f32"):
+    """Device copies of a synth.Scene (SoA float32 / int32; the learnable
+    attributes in BF16 with attr_dtype='bf16')."""
     f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=device)
-    t = api.avatar_tensors(scene.avatar, device)
+    t = api.avatar_tensors(scene.avatar, device, attr_dtype)
     light = dict(L=f(scene.light.L), A=f(scene.light.A), w=f(scene.light.w))
     return dict(avatar=t, light=light, frames=f(scene.frames.reshape(-1, 9)),
                 dmap=torch.as_tensor(scene.dmap, dtype=torch.int32, device=device), camera=scene.camera,
@@ -39,11 +40,15 @@ class Renderer:
     kernels on the current stream.  vis_cull_back rasterises only light-facing
     triangles for visibility; it gives the same bits as the two-sided rule for
     closed, outward-wound meshes such as the capsule body (set it to False
-    for open or inconsistently wound meshes)."""
+    for open or inconsistently wound meshes).  shade_tc evaluates the shading
+    sums on the tensor cores (BF16 weights, FP32 accumulation; needs a light
+    count that is a multiple of 64)."""
 
-    def __init__(self, st, tile=16, pair_capacity=None, vis_cull_back=True):
+    def __init__(self, st, tile=16, pair_capacity=None, vis_cull_back=True, shade_tc=False):
         self.st = st
         self.vis_cull_back = vis_cull_back
+        self.shade_tc = shade_tc
+        self.tc_ws = None
         t = st["avatar"]
         dev = t["xg"].device
         self.device = dev
@@ -86,8 +91,23 @@ class Renderer:
 
     def shade(self):
         st = self.st
+        if self.shade_tc:
+            if self.tc_ws is None:
+                self.tc_ws = self._tc_ws()
+            L1 = st["light"]["L"].unsqueeze(0)
+            api.avatar_shade_multi(self.sk, st["avatar"]["knn"], self.bits, st["light"], st["cam_center"], L1,
+                                   out=self.sh["color"].unsqueeze(0), cull=self.sh["cull"], status=self.status,
+                                   ws=self.tc_ws, radiance=self.sh["radiance"])
+            return
         api.avatar_shade(self.sk, st["avatar"]["knn"], self.bits, st["light"], st["cam_center"], out=self.sh,
                          status=self.status)
+
+    def _tc_ws(self):
+        import ctypes as C
+        from . import _lib as L
+        m = L.ShadeMultiArgs()
+        m.base.G = self.sk["xd"].shape[1]
+        return api.workspace(L.load().avatar_shade_multi_workspace_size(C.byref(m)), self.device)
 
     def splat(self):
         t = self.st["avatar"]
@@ -126,19 +146,21 @@ class Renderer:
 class TrainStep(Renderer):
     """Forward frame + L1 loss + backward through every stage."""
 
-    def __init__(self, st, target, tile=16, pair_capacity=None, vis_cull_back=True):
+    def __init__(self, st, target, tile=16, pair_capacity=None, vis_cull_back=True, shade_tc=False):
         self.target = target
-        super().__init__(st, tile, pair_capacity, vis_cull_back)
+        super().__init__(st, tile, pair_capacity, vis_cull_back, shade_tc)
         t = st["avatar"]
         self.loss = torch.empty(1, device=self.device)
         self.d_img = torch.empty_like(self.sb.image)
         self.g_splat = dict(xd=torch.empty_like(self.sk["xd"]), cov=torch.empty_like(self.sk["cov"]),
-                            opacity=torch.empty_like(t["opacity"]), color=torch.empty_like(self.sh["color"]))
+                            opacity=torch.empty_like(t["opacity"], dtype=torch.float32),
+                            color=torch.empty_like(self.sh["color"]))
         self.g_shade = dict(xd=torch.empty_like(self.sk["xd"]), nd=torch.empty_like(self.sk["nd"]),
                             ag=torch.empty_like(self.sk["ag"]), rg=torch.empty_like(self.sk["rg"]),
                             pg=torch.empty_like(self.sk["pg"]), ubar=torch.empty_like(self.sk["ubar"]),
                             L=torch.empty_like(st["light"]["L"]))
-        self.g_skin = {k: torch.empty_like(t[k]) for k in ("xg", "logscale", "quat", "wv", "av", "rv", "pv")}
+        self.g_skin = {k: torch.empty_like(t[k], dtype=torch.float32)
+                       for k in ("xg", "logscale", "quat", "wv", "av", "rv", "pv")}
         self._bwd_ws = None
         self.step()
         torch.cuda.synchronize()

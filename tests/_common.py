@@ -36,6 +36,24 @@ def light_ordered_bits(bits_view, dmap):
     return np.packbits(out, bitorder="little").view(np.uint32).reshape(Nv, -1)
 
 
+def bf16_round(a):
+    """FP32 -> bfloat16 (round to nearest, ties to even) -> FP32, by bit
+    arithmetic on finite values: the value a BF16-stored attribute holds."""
+    x = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((x + 0x7FFF + ((x >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).reshape(np.shape(a))
+
+
+BF16_ATTRS = ("logscale", "quat", "opacity", "av", "rv", "pv")
+
+
+def bf16_scene(sc):
+    """The scene whose learnable attributes hold their BF16-rounded values."""
+    import dataclasses
+    av = dataclasses.replace(sc.avatar, **{k: bf16_round(getattr(sc.avatar, k)) for k in BF16_ATTRS})
+    return dataclasses.replace(sc, avatar=av)
+
+
 def rel_err(got, ref):
     got = np.asarray(got, np.float64)
     ref = np.asarray(ref, np.float64)
@@ -43,4 +61,5 @@ def rel_err(got, ref):
     return float(np.abs(got - ref).max()) / scale
 
 
-__all__ = ["O", "OP", "synth", "f32", "scene", "oracle_frame", "light_ordered_bits", "rel_err"]
+__all__ = ["O", "OP", "synth", "f32", "scene", "oracle_frame", "light_ordered_bits", "rel_err", "bf16_round",
+           "bf16_scene", "BF16_ATTRS"]

@@ -625,3 +625,15 @@ def test_adjoint_matches_central_finite_differences():
                 continue
             raise AssertionError(f"{name}{idx}: autograd {ga} vs FD {d1}")
     assert kinks <= 2
+
+
+def test_bf16_rounding_helper_matches_torch():
+    """The tests' BF16 rounding of oracle inputs equals torch's FP32->BF16
+    conversion (round to nearest even), including ties and subnormals."""
+    torch = pytest.importorskip("torch")
+    from _common import bf16_round
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.normal(0, 3, 10000), rng.uniform(-1, 1, 1000) * 1e-39,
+                        [1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -(1.0 + 2.0 ** -8), 0.0, -0.0]]).astype(np.float32)
+    want = torch.from_numpy(x).to(torch.bfloat16).float().numpy()
+    assert np.array_equal(bf16_round(x).view(np.uint32), want.view(np.uint32))
