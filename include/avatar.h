@@ -86,6 +86,7 @@ int avatar_ctx_sm_count(const avatar_ctx *ctx);
 enum avatar_tune_key {
     AVATAR_TUNE_BLEND_PPT = 0,     /* pixels per thread in the blend: 1, 2 or 4 (default 1) */
     AVATAR_TUNE_BLEND_BWD_PPT = 1, /* pixels per thread in the blend backward: 1, 2 or 4 (default 2) */
+    AVATAR_TUNE_BATCH_TILE = 2,    /* tile edge of the batched render when its desc says 0 (default 16) */
     AVATAR_TUNE_COUNT = 4
 };
 int avatar_ctx_set_tuning(avatar_ctx *ctx, int key, int value);
@@ -389,6 +390,95 @@ typedef struct {
 
 int avatar_splat_backward(avatar_ctx *ctx, const avatar_splat_args *a, const avatar_splat_grads *g,
                           void *ws, size_t ws_bytes, avatar_stream_t stream);
+
+/* ------------------------------------------------------------------ */
+/* Batching: many poses, cameras and lights in one launch per step      */
+/*                                                                      */
+/* B poses of one avatar, each with its own environment light (Sec. 3.5 */
+/* relighting under novel poses), seen by V cameras of any resolution.  */
+/* Every stage runs once over the whole batch: skinning and visibility  */
+/* over the poses, shading and projection over the views, one depth     */
+/* sort and one tile sort over all views' Gaussians and pairs, and one  */
+/* persistent blend whose CTAs take tiles of every view from a shared   */
+/* counter (uneven resolutions and Gaussian-per-tile loads balance on   */
+/* the device).  The calls are asynchronous and capturable in a CUDA    */
+/* graph; each view's image equals what the per-frame calls produce.    */
+/* ------------------------------------------------------------------ */
+#define AVATAR_BATCH_MAX_VIEWS 4096
+
+typedef struct {
+    avatar_camera cam;     /* host value */
+    int pose;              /* pose shown, 0..B-1 */
+    float center[3];       /* host value: camera centre (world), the w_o origin of Eq. 2 */
+} avatar_view;
+
+typedef struct {
+    /* the canonical avatar: G, Nv, K, J, the canonical arrays and
+     * attr_dtype as in avatar_skin_args (its pose, outputs and status are
+     * not used) */
+    avatar_skin_args avatar;
+    const void *opacity;   /* [G] (avatar.attr_dtype) */
+    /* mesh and visibility geometry, as in avatar_vis_args */
+    int F;
+    const int32_t *faces;  /* [F][3] */
+    int D, R;              /* viewpoints (multiple of 32), depth-map resolution */
+    const float *frames;   /* [D][9] */
+    float center[3];       /* host value */
+    float half_extent;     /* host value */
+    float bias;            /* host value */
+    int cull_back;         /* host value, as in avatar_vis_args */
+    /* light texels shared by every pose (Eq. 2) */
+    int NL;
+    const float *light_A;  /* [NL] */
+    const float *light_w;  /* [NL][3] */
+    const int32_t *dmap;   /* [NL] light -> viewpoint */
+    /* the batch */
+    int B;                 /* poses, 1..65535 */
+    const float *poses;    /* [B][J][3] axis-angle */
+    const float *light_L;  /* [B][NL][3] each pose's environment light */
+    int V;                 /* views, 1..AVATAR_BATCH_MAX_VIEWS */
+    const avatar_view *views; /* host array [V] */
+    int tile;              /* 8, 16, 32, or 0 = the context's tuned tile (16 until tuned) */
+    int64_t pair_capacity; /* (tile, Gaussian) pairs over all views, 1..2^31-1 */
+    float *images;         /* output: the views' [3][H][W] images back to back in view order */
+    int32_t *num_pairs;    /* [1] output: pairs over all views (required capacity on overflow) */
+    int32_t *status;       /* optional device status word */
+} avatar_batch_desc;
+
+/* Workspace of the batched forward and backward (one buffer serves both;
+ * keep it between the two calls).  0 on invalid sizes. */
+size_t avatar_render_batch_workspace_size(const avatar_batch_desc *d);
+int avatar_render_batch(avatar_ctx *ctx, const avatar_batch_desc *d, void *ws, size_t ws_bytes,
+                        avatar_stream_t stream);
+
+typedef struct {
+    const float *d_images; /* upstream, laid out like images */
+    /* outputs, FP32 whatever the storage type, summed over the batch */
+    float *d_xg;           /* [3][G] */
+    float *d_logscale;     /* [3][G] */
+    float *d_quat;         /* [4][G] */
+    float *d_opacity;      /* [G] */
+    float *d_wv;           /* [Nv][J] */
+    float *d_av;           /* [3][Nv] */
+    float *d_rv;           /* [Nv] */
+    float *d_pv;           /* [Nv] */
+    float *d_light_L;      /* [B][NL][3] */
+} avatar_batch_grads;
+
+/* Adjoint of the last avatar_render_batch on the same workspace. */
+int avatar_render_batch_backward(avatar_ctx *ctx, const avatar_batch_desc *d, const avatar_batch_grads *g,
+                                 void *ws, size_t ws_bytes, avatar_stream_t stream);
+
+/* Autotuner: times the batch on this GPU for each tile edge (8, 16, 32)
+ * and each blend work split (pixels per thread, forward and backward, with
+ * g non-NULL), keeps the fastest in the context (used when d->tile == 0
+ * and by the per-frame blend) and writes the choices to tuned[3] =
+ * {tile, blend pixels per thread, backward pixels per thread} if non-NULL.
+ * Synchronous: it waits for the stream, so it must not run during graph
+ * capture (AVATAR_ERR_INVALID_ARG).  Candidates whose pairs overflow
+ * pair_capacity are skipped. */
+int avatar_render_batch_autotune(avatar_ctx *ctx, const avatar_batch_desc *d, const avatar_batch_grads *g,
+                                 void *ws, size_t ws_bytes, avatar_stream_t stream, int *tuned);
 
 /* ------------------------------------------------------------------ */
 /* Image loss - L1 part of Eq. 5 (Sec. 3.3): loss = mean |img - target|, */

@@ -24,6 +24,7 @@ DTYPE_F32 = 0   # avatar_dtype
 DTYPE_BF16 = 1
 TUNE_BLEND_PPT = 0
 TUNE_BLEND_BWD_PPT = 1
+TUNE_BATCH_TILE = 2
 
 
 class AvatarError(RuntimeError):
@@ -84,6 +85,24 @@ class SplatArgs(C.Structure):
                 ("image", P), ("T_final", P), ("n_last", P), ("status", P), ("attr_dtype", I32)]
 
 
+class View(C.Structure):
+    _fields_ = [("cam", Camera), ("pose", I32), ("center", F32 * 3)]
+
+
+class BatchDesc(C.Structure):
+    _fields_ = [("avatar", SkinArgs), ("opacity", P),
+                ("F", I32), ("faces", P), ("D", I32), ("R", I32), ("frames", P), ("center", F32 * 3),
+                ("half_extent", F32), ("bias", F32), ("cull_back", I32),
+                ("NL", I32), ("light_A", P), ("light_w", P), ("dmap", P),
+                ("B", I32), ("poses", P), ("light_L", P), ("V", I32), ("views", P), ("tile", I32),
+                ("pair_capacity", C.c_int64), ("images", P), ("num_pairs", P), ("status", P)]
+
+
+class BatchGrads(C.Structure):
+    _fields_ = [("d_images", P), ("d_xg", P), ("d_logscale", P), ("d_quat", P), ("d_opacity", P), ("d_wv", P),
+                ("d_av", P), ("d_rv", P), ("d_pv", P), ("d_light_L", P)]
+
+
 class SplatGrads(C.Structure):
     _fields_ = [("d_image", P), ("d_xd", P), ("d_cov", P), ("d_opacity", P), ("d_color", P)]
 
@@ -116,6 +135,11 @@ _SIGNATURES = [
     ("avatar_splat_blend", [P, C.POINTER(SplatArgs), P, C.c_size_t, P], I32),
     ("avatar_splat", [P, C.POINTER(SplatArgs), P, C.c_size_t, P], I32),
     ("avatar_splat_backward", [P, C.POINTER(SplatArgs), C.POINTER(SplatGrads), P, C.c_size_t, P], I32),
+    ("avatar_render_batch_workspace_size", [C.POINTER(BatchDesc)], C.c_size_t),
+    ("avatar_render_batch", [P, C.POINTER(BatchDesc), P, C.c_size_t, P], I32),
+    ("avatar_render_batch_backward", [P, C.POINTER(BatchDesc), C.POINTER(BatchGrads), P, C.c_size_t, P], I32),
+    ("avatar_render_batch_autotune", [P, C.POINTER(BatchDesc), C.POINTER(BatchGrads), P, C.c_size_t, P,
+                                      C.POINTER(C.c_int)], I32),
     ("avatar_l1_loss", [P, C.c_int64, P, P, P, P, P], I32),
 ]
 

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libavatar.so")
-SOURCES = ["api.cu", "skin.cu", "visibility.cu", "shade.cu", "shade_tc.cu", "splat.cu"]
+SOURCES = ["api.cu", "skin.cu", "visibility.cu", "shade.cu", "shade_tc.cu", "splat.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -33,7 +33,8 @@ def nvcc() -> str:
 def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(CSRC, "common.cuh"), os.path.join(INCLUDE, "avatar.h")]
+    deps = [src, os.path.join(INCLUDE, "avatar.h")] + [os.path.join(CSRC, h) for h in os.listdir(CSRC)
+                                                       if h.endswith((".cuh", ".h"))]
     t = os.path.getmtime(obj)
     return any(os.path.getmtime(d) > t for d in deps)
 

@@ -69,6 +69,7 @@ extern "C" int avatar_ctx_create(avatar_ctx **out, int device)
     for (int i = 0; i < AVATAR_TUNE_COUNT; ++i) c->tune[i] = 0;
     c->tune[AVATAR_TUNE_BLEND_PPT] = 1;
     c->tune[AVATAR_TUNE_BLEND_BWD_PPT] = 2;
+    c->tune[AVATAR_TUNE_BATCH_TILE] = 16;
     *out = c;
     return AVATAR_OK;
 }
@@ -101,6 +102,9 @@ extern "C" int avatar_ctx_set_tuning(avatar_ctx *ctx, int key, int value)
         case AVATAR_TUNE_BLEND_PPT:
         case AVATAR_TUNE_BLEND_BWD_PPT:
             if (value != 1 && value != 2 && value != 4) return AVATAR_ERR_INVALID_ARG;
+            break;
+        case AVATAR_TUNE_BATCH_TILE:
+            if (value != 8 && value != 16 && value != 32) return AVATAR_ERR_INVALID_ARG;
             break;
         default: break;
     }

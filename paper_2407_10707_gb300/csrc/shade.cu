@@ -8,6 +8,7 @@
 // extracts its own bit.  Per-Gaussian sums are reduced with shuffles.  The
 // backward pass reuses the same split: per-light gradients accumulate in
 // shared memory and are flushed once per block.
+#include "batch_internal.h"
 #include "common.cuh"
 
 namespace {
@@ -24,14 +25,48 @@ struct GaussIn {
     int nb[K];
 };
 
+// Batched launches (blockIdx.y = view): the views' poses, camera centres and
+// the two strides.  Per-pose arrays (xd, nd, bits, light_L) hold B poses
+// with channel stride B G; per-view arrays (color, radiance, cull and the
+// gradients) hold V views with channel stride V G.  A single frame is
+// B = V = 1 with null tables.
+struct ShadeBatch {
+    int B, V;
+    const int32_t *view_pose;  // [V] or NULL
+    const float *view_cc;      // [V][3] or NULL (then args.cam_center)
+};
+
+struct ShadeSlot {
+    int p, y;       // pose, view
+    size_t SG, VG;  // channel strides of per-pose and per-view arrays
+    size_t op, oy;  // element offsets p G and y G
+    float C[3];     // camera centre
+};
+
+__device__ __forceinline__ ShadeSlot shade_slot(const avatar_shade_args &s, const ShadeBatch &sb)
+{
+    ShadeSlot t;
+    t.y = blockIdx.y;
+    t.p = sb.view_pose ? __ldg(sb.view_pose + t.y) : 0;
+    t.SG = (size_t)sb.B * s.G;
+    t.VG = (size_t)sb.V * s.G;
+    t.op = (size_t)t.p * s.G;
+    t.oy = (size_t)t.y * s.G;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t.C[i] = sb.view_cc ? __ldg(sb.view_cc + 3 * t.y + i) : s.cam_center[i];
+    return t;
+}
+
 template <int K>
-__device__ __forceinline__ bool load_gauss(const avatar_shade_args &s, int g, GaussIn<K> &q)
+__device__ __forceinline__ bool load_gauss(const avatar_shade_args &s, int g, GaussIn<K> &q, size_t SG = 0,
+                                           size_t op = 0)
 {
     const int G = s.G;
+    if (SG == 0) SG = (size_t)G;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        q.x[i] = __ldg(s.xd + (size_t)i * G + g);
-        q.n[i] = __ldg(s.nd + (size_t)i * G + g);
+        q.x[i] = __ldg(s.xd + (size_t)i * SG + op + g);
+        q.n[i] = __ldg(s.nd + (size_t)i * SG + op + g);
         q.a[i] = __ldg(s.ag + (size_t)i * G + g);
     }
     q.r = __ldg(s.rg + g);
@@ -89,14 +124,14 @@ struct ChunkBits {
 };
 
 template <int K>
-__device__ __forceinline__ void load_chunk(const avatar_shade_args &s, const GaussIn<K> &q, int OW, int ch,
+__device__ __forceinline__ void load_chunk(const uint32_t *__restrict__ bits, const GaussIn<K> &q, int OW, int ch,
                                            ChunkBits<K> &cb)
 {
     cb.all = 0xffffffffu;
     cb.any = 0u;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-        cb.w[j] = __ldg(s.bits + (size_t)q.nb[j] * OW + ch);
+        cb.w[j] = __ldg(bits + (size_t)q.nb[j] * OW + ch);
         cb.all &= cb.w[j];
         cb.any |= cb.w[j];
     }
@@ -117,33 +152,39 @@ __device__ __forceinline__ float lane_vis(const ChunkBits<K> &cb, const GaussIn<
 
 template <int K>
 __global__ void __launch_bounds__(SHADE_THREADS)
-shade_kernel(avatar_shade_args s)
+shade_kernel(avatar_shade_args s, ShadeBatch sb)
 {
     extern __shared__ float4 lsm[];  // [NL] (w, 0) then [NL] (L*A, 0)
     const int NL = s.NL, G = s.G;
+    const ShadeSlot t = shade_slot(s, sb);
+    const int OW = (NL + 31) / 32;
+    const float *light_L = s.light_L + (size_t)t.p * NL * 3;
+    const uint32_t *bits = s.bits + (size_t)t.p * s.Nv * OW;
+    float *color = s.color + t.oy;
+    float *radiance = s.radiance ? s.radiance + t.oy : nullptr;
+    uint8_t *cull = s.cull ? s.cull + t.oy : nullptr;
     float4 *lw = lsm, *lb = lsm + NL;
     for (int k = threadIdx.x; k < NL; k += blockDim.x) {
         float A = __ldg(s.light_A + k);
         lw[k] = make_float4(__ldg(s.light_w + 3 * k), __ldg(s.light_w + 3 * k + 1), __ldg(s.light_w + 3 * k + 2), 0.f);
-        lb[k] = make_float4(__ldg(s.light_L + 3 * k) * A, __ldg(s.light_L + 3 * k + 1) * A,
-                            __ldg(s.light_L + 3 * k + 2) * A, 0.f);
+        lb[k] = make_float4(__ldg(light_L + 3 * k) * A, __ldg(light_L + 3 * k + 1) * A, __ldg(light_L + 3 * k + 2) * A,
+                            0.f);
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const unsigned bit = 1u << lane;
-    const int OW = (NL + 31) / 32;
     const int warps_total = gridDim.x * (blockDim.x >> 5);
-    const float C[3] = {s.cam_center[0], s.cam_center[1], s.cam_center[2]};
+    const float *C = t.C;
     for (int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < G; g += warps_total) {
         GaussIn<K> q;
-        bool ok = load_gauss<K>(s, g, q);
+        bool ok = load_gauss<K>(s, g, q, t.SG, t.op);
         if (!ok && lane == 0) av_report(s.status, AVATAR_ERR_INDEX);
         if (is_culled(q.x, q.n, C) || !ok) {
             if (lane < 3) {
-                s.color[(size_t)lane * G + g] = 0.f;
-                if (s.radiance) s.radiance[(size_t)lane * G + g] = 0.f;
+                color[(size_t)lane * t.VG + g] = 0.f;
+                if (radiance) radiance[(size_t)lane * t.VG + g] = 0.f;
             }
-            if (lane == 0 && s.cull) s.cull[g] = 1;
+            if (lane == 0 && cull) cull[g] = 1;
             continue;
         }
         Frame f = view_frame<K>(q, C);
@@ -153,7 +194,7 @@ shade_kernel(avatar_shade_args s)
         float L0 = 0.f, L1 = 0.f, L2 = 0.f;  // this lane's share of L_o
         for (int ch = 0; ch < OW; ++ch) {
             ChunkBits<K> cb;
-            load_chunk<K>(s, q, OW, ch, cb);
+            load_chunk<K>(bits, q, OW, ch, cb);
             const int k = ch * 32 + lane;
             if (k >= NL || !(cb.any & bit)) continue;
             float4 w = lw[k];
@@ -184,56 +225,70 @@ shade_kernel(avatar_shade_args s)
         if (lane < 3) {
             float Lo = lane == 0 ? L0 : (lane == 1 ? L1 : L2);
             float col = exp2f(log2f(fmaxf(Lo, 1e-6f)) * INV_GAMMA);
-            s.color[(size_t)lane * G + g] = col;
-            if (s.radiance) s.radiance[(size_t)lane * G + g] = Lo;
+            color[(size_t)lane * t.VG + g] = col;
+            if (radiance) radiance[(size_t)lane * t.VG + g] = Lo;
         }
-        if (lane == 0 && s.cull) s.cull[g] = 0;
+        if (lane == 0 && cull) cull[g] = 0;
     }
 }
 
 // ---------------------------------------------------------------- backward
 template <int K>
 __global__ void __launch_bounds__(SHADE_THREADS)
-shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr)
+shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr, ShadeBatch sb)
 {
     extern __shared__ float4 lsm[];  // [NL] (w, A) ; [NL] (L*A) ; [NL][3] dL/dB accumulators
     const int NL = s.NL, G = s.G;
+    const ShadeSlot t = shade_slot(s, sb);
+    const int OW = (NL + 31) / 32;
+    const size_t VG = t.VG;
+    const float *light_L = s.light_L + (size_t)t.p * NL * 3;
+    const uint32_t *bits = s.bits + (size_t)t.p * s.Nv * OW;
+    const float *radiance = s.radiance + t.oy;
+    // per-view gradient slices; dL/dL^k of the view's pose
+    gr.d_color += t.oy;
+    gr.d_xd += t.oy;
+    gr.d_nd += t.oy;
+    gr.d_ag += t.oy;
+    gr.d_rg += t.oy;
+    gr.d_pg += t.oy;
+    gr.d_ubar += t.oy;
+    gr.d_light_L += (size_t)t.p * NL * 3;
     float4 *lw = lsm, *lb = lsm + NL;
     float *dB = reinterpret_cast<float *>(lsm + 2 * NL);
     for (int k = threadIdx.x; k < NL; k += blockDim.x) {
         float A = __ldg(s.light_A + k);
         lw[k] = make_float4(__ldg(s.light_w + 3 * k), __ldg(s.light_w + 3 * k + 1), __ldg(s.light_w + 3 * k + 2), A);
-        lb[k] = make_float4(__ldg(s.light_L + 3 * k) * A, __ldg(s.light_L + 3 * k + 1) * A,
-                            __ldg(s.light_L + 3 * k + 2) * A, 0.f);
+        lb[k] = make_float4(__ldg(light_L + 3 * k) * A, __ldg(light_L + 3 * k + 1) * A, __ldg(light_L + 3 * k + 2) * A,
+                            0.f);
         dB[3 * k] = dB[3 * k + 1] = dB[3 * k + 2] = 0.f;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const unsigned bit = 1u << lane;
-    const int OW = (NL + 31) / 32;
     const int warps_total = gridDim.x * (blockDim.x >> 5);
-    const float C[3] = {s.cam_center[0], s.cam_center[1], s.cam_center[2]};
+    const float *C = t.C;
     for (int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < G; g += warps_total) {
         GaussIn<K> q;
-        bool ok = load_gauss<K>(s, g, q);
+        bool ok = load_gauss<K>(s, g, q, t.SG, t.op);
         float dLo[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            float Lo = __ldg(s.radiance + (size_t)c * G + g);
-            float dc = __ldg(gr.d_color + (size_t)c * G + g);
+            float Lo = __ldg(radiance + (size_t)c * VG + g);
+            float dc = __ldg(gr.d_color + (size_t)c * VG + g);
             dLo[c] = (Lo > 1e-6f) ? dc * INV_GAMMA * exp2f(log2f(Lo) * (INV_GAMMA - 1.f)) : 0.f;
         }
         if (!ok || is_culled(q.x, q.n, C) || (dLo[0] == 0.f && dLo[1] == 0.f && dLo[2] == 0.f)) {
             if (lane < 3) {
-                gr.d_xd[(size_t)lane * G + g] = 0.f;
-                gr.d_nd[(size_t)lane * G + g] = 0.f;
-                gr.d_ag[(size_t)lane * G + g] = 0.f;
+                gr.d_xd[(size_t)lane * VG + g] = 0.f;
+                gr.d_nd[(size_t)lane * VG + g] = 0.f;
+                gr.d_ag[(size_t)lane * VG + g] = 0.f;
             }
             if (lane == 0) {
                 gr.d_rg[g] = 0.f;
                 gr.d_pg[g] = 0.f;
             }
-            if (lane < K) gr.d_ubar[(size_t)lane * G + g] = 0.f;
+            if (lane < K) gr.d_ubar[(size_t)lane * VG + g] = 0.f;
             continue;
         }
         Frame f = view_frame<K>(q, C);
@@ -248,7 +303,7 @@ shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr)
         for (int j = 0; j < K; ++j) dub[j] = 0.f;
         for (int ch = 0; ch < OW; ++ch) {
             ChunkBits<K> cb;
-            load_chunk<K>(s, q, OW, ch, cb);
+            load_chunk<K>(bits, q, OW, ch, cb);
             const int k = ch * 32 + lane;
             if (k >= NL || !(cb.any & bit)) continue;
             float4 w = lw[k];
@@ -332,17 +387,17 @@ shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr)
             float dd = dw[0] * f.wo[0] + dw[1] * f.wo[1] + dw[2] * f.wo[2];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                gr.d_nd[(size_t)c * G + g] = dn[c];
-                gr.d_xd[(size_t)c * G + g] = -(dw[c] - dd * f.wo[c]) * f.inv_len;
+                gr.d_nd[(size_t)c * VG + g] = dn[c];
+                gr.d_xd[(size_t)c * VG + g] = -(dw[c] - dd * f.wo[c]) * f.inv_len;
             }
             gr.d_ag[g] = dLo[0] * E0 * (1.f / AV_PI);
-            gr.d_ag[G + g] = dLo[1] * E1 * (1.f / AV_PI);
-            gr.d_ag[2 * G + g] = dLo[2] * E2 * (1.f / AV_PI);
+            gr.d_ag[VG + g] = dLo[1] * E1 * (1.f / AV_PI);
+            gr.d_ag[2 * VG + g] = dLo[2] * E2 * (1.f / AV_PI);
             float alpha = q.r * q.r;
             gr.d_rg[g] = da2 * 4.f * alpha * q.r + dkk * (q.r + 1.f) * 0.25f;
             gr.d_pg[g] = dp;
 #pragma unroll
-            for (int j = 0; j < K; ++j) gr.d_ubar[(size_t)j * G + g] = dub[j];
+            for (int j = 0; j < K; ++j) gr.d_ubar[(size_t)j * VG + g] = dub[j];
         }
     }
     __syncthreads();
@@ -357,24 +412,24 @@ shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr)
 }
 
 template <int K>
-int launch_shade(const avatar_shade_args &a, int grid, size_t smem, cudaStream_t st)
+int launch_shade(const avatar_shade_args &a, const ShadeBatch &sb, int grid, size_t smem, cudaStream_t st)
 {
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(shade_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return AVATAR_ERR_CUDA;
-    shade_kernel<K><<<grid, SHADE_THREADS, smem, st>>>(a);
+    shade_kernel<K><<<dim3(grid, sb.V), SHADE_THREADS, smem, st>>>(a, sb);
     AV_CHECK_LAUNCH();
     return AVATAR_OK;
 }
 
 template <int K>
-int launch_shade_bwd(const avatar_shade_args &a, const avatar_shade_grads &g, int grid, size_t smem,
-                     cudaStream_t st)
+int launch_shade_bwd(const avatar_shade_args &a, const avatar_shade_grads &g, const ShadeBatch &sb, int grid,
+                     size_t smem, cudaStream_t st)
 {
     if (smem > 48 * 1024 && cudaFuncSetAttribute(shade_backward_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem) != cudaSuccess)
         return AVATAR_ERR_CUDA;
-    shade_backward_kernel<K><<<grid, SHADE_THREADS, smem, st>>>(a, g);
+    shade_backward_kernel<K><<<dim3(grid, sb.V), SHADE_THREADS, smem, st>>>(a, g, sb);
     AV_CHECK_LAUNCH();
     return AVATAR_OK;
 }
@@ -409,15 +464,16 @@ extern "C" int avatar_shade(avatar_ctx *ctx, const avatar_shade_args *a, avatar_
     size_t smem = (size_t)2 * a->NL * sizeof(float4);
     int grid = shade_grid(ctx, a->G);
     cudaStream_t st = (cudaStream_t)stream;
+    const ShadeBatch sb{1, 1, nullptr, nullptr};
     switch (a->K) {
-        case 1: return launch_shade<1>(*a, grid, smem, st);
-        case 2: return launch_shade<2>(*a, grid, smem, st);
-        case 3: return launch_shade<3>(*a, grid, smem, st);
-        case 4: return launch_shade<4>(*a, grid, smem, st);
-        case 5: return launch_shade<5>(*a, grid, smem, st);
-        case 6: return launch_shade<6>(*a, grid, smem, st);
-        case 7: return launch_shade<7>(*a, grid, smem, st);
-        default: return launch_shade<8>(*a, grid, smem, st);
+        case 1: return launch_shade<1>(*a, sb, grid, smem, st);
+        case 2: return launch_shade<2>(*a, sb, grid, smem, st);
+        case 3: return launch_shade<3>(*a, sb, grid, smem, st);
+        case 4: return launch_shade<4>(*a, sb, grid, smem, st);
+        case 5: return launch_shade<5>(*a, sb, grid, smem, st);
+        case 6: return launch_shade<6>(*a, sb, grid, smem, st);
+        case 7: return launch_shade<7>(*a, sb, grid, smem, st);
+        default: return launch_shade<8>(*a, sb, grid, smem, st);
     }
 }
 
@@ -435,14 +491,62 @@ extern "C" int avatar_shade_backward(avatar_ctx *ctx, const avatar_shade_args *a
     if (a->G == 0) return AVATAR_OK;
     size_t smem = (size_t)2 * a->NL * sizeof(float4) + (size_t)3 * a->NL * sizeof(float);
     int grid = shade_grid(ctx, a->G);
+    const ShadeBatch sb{1, 1, nullptr, nullptr};
     switch (a->K) {
-        case 1: return launch_shade_bwd<1>(*a, *g, grid, smem, st);
-        case 2: return launch_shade_bwd<2>(*a, *g, grid, smem, st);
-        case 3: return launch_shade_bwd<3>(*a, *g, grid, smem, st);
-        case 4: return launch_shade_bwd<4>(*a, *g, grid, smem, st);
-        case 5: return launch_shade_bwd<5>(*a, *g, grid, smem, st);
-        case 6: return launch_shade_bwd<6>(*a, *g, grid, smem, st);
-        case 7: return launch_shade_bwd<7>(*a, *g, grid, smem, st);
-        default: return launch_shade_bwd<8>(*a, *g, grid, smem, st);
+        case 1: return launch_shade_bwd<1>(*a, *g, sb, grid, smem, st);
+        case 2: return launch_shade_bwd<2>(*a, *g, sb, grid, smem, st);
+        case 3: return launch_shade_bwd<3>(*a, *g, sb, grid, smem, st);
+        case 4: return launch_shade_bwd<4>(*a, *g, sb, grid, smem, st);
+        case 5: return launch_shade_bwd<5>(*a, *g, sb, grid, smem, st);
+        case 6: return launch_shade_bwd<6>(*a, *g, sb, grid, smem, st);
+        case 7: return launch_shade_bwd<7>(*a, *g, sb, grid, smem, st);
+        default: return launch_shade_bwd<8>(*a, *g, sb, grid, smem, st);
+    }
+}
+
+int av_shade_batch(avatar_ctx *ctx, const avatar_shade_args *a, int B, int V, const int32_t *view_pose,
+                   const float *view_cc, cudaStream_t st)
+{
+    if (!ctx || B < 1 || V < 1 || V > 65535 || !view_pose || !view_cc) return AVATAR_ERR_INVALID_ARG;
+    AV_TRY(check_shade(a));
+    if (a->G == 0) return AVATAR_OK;
+    size_t smem = (size_t)2 * a->NL * sizeof(float4);
+    int grid = shade_grid(ctx, a->G);
+    const ShadeBatch sb{B, V, view_pose, view_cc};
+    switch (a->K) {
+        case 1: return launch_shade<1>(*a, sb, grid, smem, st);
+        case 2: return launch_shade<2>(*a, sb, grid, smem, st);
+        case 3: return launch_shade<3>(*a, sb, grid, smem, st);
+        case 4: return launch_shade<4>(*a, sb, grid, smem, st);
+        case 5: return launch_shade<5>(*a, sb, grid, smem, st);
+        case 6: return launch_shade<6>(*a, sb, grid, smem, st);
+        case 7: return launch_shade<7>(*a, sb, grid, smem, st);
+        default: return launch_shade<8>(*a, sb, grid, smem, st);
+    }
+}
+
+int av_shade_batch_backward(avatar_ctx *ctx, const avatar_shade_args *a, const avatar_shade_grads *g, int B, int V,
+                            const int32_t *view_pose, const float *view_cc, cudaStream_t st)
+{
+    if (!ctx || !g || B < 1 || V < 1 || V > 65535 || !view_pose || !view_cc) return AVATAR_ERR_INVALID_ARG;
+    AV_TRY(check_shade(a));
+    if (!a->radiance || !g->d_color || !g->d_xd || !g->d_nd || !g->d_ag || !g->d_rg || !g->d_pg || !g->d_ubar ||
+        !g->d_light_L)
+        return AVATAR_ERR_INVALID_ARG;
+    if (cudaMemsetAsync(g->d_light_L, 0, (size_t)B * a->NL * 3 * sizeof(float), st) != cudaSuccess)
+        return AVATAR_ERR_CUDA;
+    if (a->G == 0) return AVATAR_OK;
+    size_t smem = (size_t)2 * a->NL * sizeof(float4) + (size_t)3 * a->NL * sizeof(float);
+    int grid = shade_grid(ctx, a->G);
+    const ShadeBatch sb{B, V, view_pose, view_cc};
+    switch (a->K) {
+        case 1: return launch_shade_bwd<1>(*a, *g, sb, grid, smem, st);
+        case 2: return launch_shade_bwd<2>(*a, *g, sb, grid, smem, st);
+        case 3: return launch_shade_bwd<3>(*a, *g, sb, grid, smem, st);
+        case 4: return launch_shade_bwd<4>(*a, *g, sb, grid, smem, st);
+        case 5: return launch_shade_bwd<5>(*a, *g, sb, grid, smem, st);
+        case 6: return launch_shade_bwd<6>(*a, *g, sb, grid, smem, st);
+        case 7: return launch_shade_bwd<7>(*a, *g, sb, grid, smem, st);
+        default: return launch_shade_bwd<8>(*a, *g, sb, grid, smem, st);
     }
 }

@@ -12,6 +12,7 @@
 //                    and normal.
 // Backward: per-Gaussian adjoint with atomic scatter into per-vertex
 // accumulators, then a per-vertex pass turning dA_v into dw_v.
+#include "batch_internal.h"
 #include "common.cuh"
 
 namespace {
@@ -114,10 +115,18 @@ __device__ void fk_shared(int J, const int32_t *parents, const float *joints, co
     __syncthreads();
 }
 
+// blockIdx.y = pose of a batch of gridDim.y poses (pose [B][J][3], bone
+// [B][J][12], xp [3][B Nv], records [B Nv]).
 __global__ void __launch_bounds__(SKIN_THREADS)
 skin_vertices_kernel(avatar_skin_args a, VertexRec *__restrict__ rec)
 {
     __shared__ float bone_s[MAX_J * 12];
+    const int pb = blockIdx.y;
+    const size_t SN = (size_t)gridDim.y * a.Nv;  // channel stride of xp
+    a.pose += (size_t)pb * 3 * a.J;
+    a.bone += (size_t)pb * 12 * a.J;
+    a.xp += (size_t)pb * a.Nv;
+    rec += (size_t)pb * a.Nv;
     fk_shared(a.J, a.parents, a.joints, a.pose, bone_s, a.status);
     if (blockIdx.x == 0)
         for (int i = threadIdx.x; i < 12 * a.J; i += blockDim.x) a.bone[i] = bone_s[i];
@@ -153,7 +162,7 @@ skin_vertices_kernel(avatar_skin_args a, VertexRec *__restrict__ rec)
         float px = x + dx, py = y + dy, pz = z + dz;
 #pragma unroll
         for (int i = 0; i < 3; ++i)
-            a.xp[i * Nv + v] = fmaf(A[4 * i], px, fmaf(A[4 * i + 1], py, fmaf(A[4 * i + 2], pz, A[4 * i + 3])));
+            a.xp[i * SN + v] = fmaf(A[4 * i], px, fmaf(A[4 * i + 1], py, fmaf(A[4 * i + 2], pz, A[4 * i + 3])));
         VertexRec r;
         r.a0 = make_float4(A[0], A[1], A[2], A[3]);
         r.a1 = make_float4(A[4], A[5], A[6], A[7]);
@@ -265,7 +274,16 @@ template <int K>
 __global__ void __launch_bounds__(SKIN_THREADS)
 skin_gaussians_kernel(avatar_skin_args a, const VertexRec *__restrict__ rec)
 {
+    // blockIdx.y = pose of a batch: xd, nd [3][B G], cov [6][B G], records
+    // [B Nv]; the pose-independent ag, rg, pg, ubar are written by pose 0.
     const int G = a.G;
+    const int pb = blockIdx.y;
+    const size_t SG = (size_t)gridDim.y * G;
+    a.xd += (size_t)pb * G;
+    a.cov += (size_t)pb * G;
+    a.nd += (size_t)pb * G;
+    rec += (size_t)pb * a.Nv;
+    const bool shared_out = pb == 0;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
         GaussState<K> s;
         if (!gauss_gather<K>(a, rec, g, s)) av_report(a.status, AVATAR_ERR_INDEX);
@@ -273,7 +291,7 @@ skin_gaussians_kernel(avatar_skin_args a, const VertexRec *__restrict__ rec)
         float xb0 = s.x[0] + s.dx[0], xb1 = s.x[1] + s.dx[1], xb2 = s.x[2] + s.dx[2];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
-            a.xd[i * G + g] = fmaf(A[4 * i], xb0, fmaf(A[4 * i + 1], xb1, fmaf(A[4 * i + 2], xb2, A[4 * i + 3])));
+            a.xd[i * SG + g] = fmaf(A[4 * i], xb0, fmaf(A[4 * i + 1], xb1, fmaf(A[4 * i + 2], xb2, A[4 * i + 3])));
         // covariance
         const int dt = a.attr_dtype;
         float qw = ld_attr(a.quat, g, dt), qx = ld_attr(a.quat, (size_t)G + g, dt),
@@ -300,7 +318,7 @@ skin_gaussians_kernel(avatar_skin_args a, const VertexRec *__restrict__ rec)
                    MR[3 * i + 2] * MR[3 * j + 2] * s2[2];
         }
 #pragma unroll
-        for (int e = 0; e < 6; ++e) a.cov[e * G + g] = c[e];
+        for (int e = 0; e < 6; ++e) a.cov[e * SG + g] = c[e];
         // normal
         float nl = rsqrtf(s.n[0] * s.n[0] + s.n[1] * s.n[1] + s.n[2] * s.n[2]);
         float n0 = s.n[0] * nl, n1 = s.n[1] * nl, n2 = s.n[2] * nl;
@@ -309,8 +327,9 @@ skin_gaussians_kernel(avatar_skin_args a, const VertexRec *__restrict__ rec)
         float m2 = A[8] * n0 + A[9] * n1 + A[10] * n2;
         float ml = rsqrtf(m0 * m0 + m1 * m1 + m2 * m2);
         a.nd[g] = m0 * ml;
-        a.nd[G + g] = m1 * ml;
-        a.nd[2 * G + g] = m2 * ml;
+        a.nd[SG + g] = m1 * ml;
+        a.nd[2 * SG + g] = m2 * ml;
+        if (!shared_out) continue;
         a.ag[g] = s.a[0];
         a.ag[G + g] = s.a[1];
         a.ag[2 * G + g] = s.a[2];
@@ -331,19 +350,29 @@ __device__ __forceinline__ float ld_or0(const float *p, size_t i) { return p ? _
 template <int K>
 __global__ void __launch_bounds__(SKIN_THREADS)
 skin_gaussians_backward_kernel(avatar_skin_args a, avatar_skin_grads gr, const VertexRec *__restrict__ rec,
-                               float *__restrict__ dAv)
+                               float *__restrict__ dAv, int B)
 {
+    // B poses: upstream d_xd, d_xd2, d_nd [3][B G] and d_cov [6][B G] per pose,
+    // d_ag, d_rg, d_pg, d_ubar once; records and dA_v accumulators per pose
+    // ([B Nv]); the canonical gradients are summed over the poses here.
     const int G = a.G, Nv = a.Nv;
+    const size_t SG = (size_t)B * G;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        float dxg_s[3] = {0.f, 0.f, 0.f}, dls_s[3] = {0.f, 0.f, 0.f}, dq_s[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int pb = 0; pb < B; ++pb) {
+        const VertexRec *recp = rec + (size_t)pb * Nv;
+        float *dAvp = dAv + (size_t)pb * Nv * 12;
+        const size_t gi = (size_t)pb * G + g;  // element of the per-pose arrays (stride SG)
+        const bool shared_in = pb == 0;        // pose-independent upstream enters once
         GaussState<K> s;
-        gauss_gather<K>(a, rec, g, s);
+        gauss_gather<K>(a, recp, g, s);
         const float *A = s.A;
         float dM[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         float dt[3];
         float xb[3] = {s.x[0] + s.dx[0], s.x[1] + s.dx[1], s.x[2] + s.dx[2]};
         // ---- position: xd = M xb + t
-        float dxd[3] = {ld_or0(gr.d_xd, g) + ld_or0(gr.d_xd2, g), ld_or0(gr.d_xd, G + g) + ld_or0(gr.d_xd2, G + g),
-                        ld_or0(gr.d_xd, 2 * G + g) + ld_or0(gr.d_xd2, 2 * G + g)};
+        float dxd[3] = {ld_or0(gr.d_xd, gi) + ld_or0(gr.d_xd2, gi), ld_or0(gr.d_xd, SG + gi) + ld_or0(gr.d_xd2, SG + gi),
+                        ld_or0(gr.d_xd, 2 * SG + gi) + ld_or0(gr.d_xd2, 2 * SG + gi)};
         float dxb[3] = {0, 0, 0};
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
@@ -369,7 +398,7 @@ skin_gaussians_backward_kernel(avatar_skin_args a, avatar_skin_grads gr, const V
         if (gr.d_cov) {
             float dc[6];
 #pragma unroll
-            for (int e = 0; e < 6; ++e) dc[e] = __ldg(gr.d_cov + (size_t)e * G + g);
+            for (int e = 0; e < 6; ++e) dc[e] = __ldg(gr.d_cov + (size_t)e * SG + gi);
             float Gc[9] = {dc[0], 0.5f * dc[1], 0.5f * dc[2], 0.5f * dc[1], dc[3], 0.5f * dc[4],
                            0.5f * dc[2], 0.5f * dc[4], dc[5]};
             float Sg[9];
@@ -433,7 +462,7 @@ skin_gaussians_backward_kernel(avatar_skin_args a, avatar_skin_grads gr, const V
         // ---- normal: nd = normalize(M nhat), nhat = normalize(n_g)
         float dn_g[3] = {0, 0, 0};
         if (gr.d_nd) {
-            float dnd[3] = {__ldg(gr.d_nd + g), __ldg(gr.d_nd + G + g), __ldg(gr.d_nd + 2 * G + g)};
+            float dnd[3] = {__ldg(gr.d_nd + gi), __ldg(gr.d_nd + SG + gi), __ldg(gr.d_nd + 2 * SG + gi)};
             float nlen = sqrtf(s.n[0] * s.n[0] + s.n[1] * s.n[1] + s.n[2] * s.n[2]);
             float nh[3] = {s.n[0] / nlen, s.n[1] / nlen, s.n[2] / nlen};
             float m[3];
@@ -457,19 +486,25 @@ skin_gaussians_backward_kernel(avatar_skin_args a, avatar_skin_grads gr, const V
 #pragma unroll
             for (int i = 0; i < 3; ++i) dn_g[i] = (dnh[i] - d2 * nh[i]) / nlen;
         }
-        float dag[3] = {ld_or0(gr.d_ag, g), ld_or0(gr.d_ag, G + g), ld_or0(gr.d_ag, 2 * G + g)};
-        float drg = ld_or0(gr.d_rg, g), dpg = ld_or0(gr.d_pg, g);
+        float dag[3] = {0.f, 0.f, 0.f}, drg = 0.f, dpg = 0.f;
+        if (shared_in) {
+            dag[0] = ld_or0(gr.d_ag, g);
+            dag[1] = ld_or0(gr.d_ag, G + g);
+            dag[2] = ld_or0(gr.d_ag, 2 * G + g);
+            drg = ld_or0(gr.d_rg, g);
+            dpg = ld_or0(gr.d_pg, g);
+        }
         // ---- scatter through Eq. 1 and accumulate dubar
         float dA[12] = {dM[0], dM[1], dM[2], dt[0], dM[3], dM[4], dM[5], dt[1], dM[6], dM[7], dM[8], dt[2]};
         float dub[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            const VertexRec *vr = rec + s.idx[j];
+            const VertexRec *vr = recp + s.idx[j];
             const int v = s.idx[j];
             const float u = s.ub[j];
             float4 a0 = __ldg(&vr->a0), a1 = __ldg(&vr->a1), a2 = __ldg(&vr->a2);
             float4 xr = __ldg(&vr->xr), ap = __ldg(&vr->ap), n0 = __ldg(&vr->nd0), d12 = __ldg(&vr->d12);
-            float acc = ld_or0(gr.d_ubar, (size_t)j * G + g);
+            float acc = shared_in ? ld_or0(gr.d_ubar, (size_t)j * G + g) : 0.f;
             acc += dA[0] * a0.x + dA[1] * a0.y + dA[2] * a0.z + dA[3] * a0.w;
             acc += dA[4] * a1.x + dA[5] * a1.y + dA[6] * a1.z + dA[7] * a1.w;
             acc += dA[8] * a2.x + dA[9] * a2.y + dA[10] * a2.z + dA[11] * a2.w;
@@ -477,17 +512,17 @@ skin_gaussians_backward_kernel(avatar_skin_args a, avatar_skin_grads gr, const V
             acc += dn_g[0] * n0.x + dn_g[1] * n0.y + dn_g[2] * n0.z;
             acc += dxb[0] * n0.w + dxb[1] * d12.x + dxb[2] * d12.y;
             dub[j] = acc;
-            float *dst = dAv + (size_t)v * 12;
+            float *dst = dAvp + (size_t)v * 12;
 #pragma unroll
             for (int i = 0; i < 12; ++i)
                 if (dA[i] != 0.f) atomicAdd(dst + i, u * dA[i]);
-            if (gr.d_av) {
+            if (gr.d_av && shared_in) {
                 atomicAdd(gr.d_av + v, u * dag[0]);
                 atomicAdd(gr.d_av + Nv + v, u * dag[1]);
                 atomicAdd(gr.d_av + 2 * Nv + v, u * dag[2]);
             }
-            if (gr.d_rv) atomicAdd(gr.d_rv + v, u * drg);
-            if (gr.d_pv) atomicAdd(gr.d_pv + v, u * dpg);
+            if (gr.d_rv && shared_in) atomicAdd(gr.d_rv + v, u * drg);
+            if (gr.d_pv && shared_in) atomicAdd(gr.d_pv + v, u * dpg);
             if (gr.d_dxv) {
                 atomicAdd(gr.d_dxv + v, u * dxb[0]);
                 atomicAdd(gr.d_dxv + Nv + v, u * dxb[1]);
@@ -504,7 +539,7 @@ skin_gaussians_backward_kernel(avatar_skin_args a, avatar_skin_grads gr, const V
             float du = (dub[j] - sdot) / s.usum;
             float d = s.dist[j];
             if (d > 1e-8f) {
-                float4 xr = __ldg(&rec[s.idx[j]].xr);
+                float4 xr = __ldg(&recp[s.idx[j]].xr);
                 float dd = -du / (d * d);
                 float f = dd / d;
                 dxg[0] += f * (s.x[0] - xr.x);
@@ -512,52 +547,65 @@ skin_gaussians_backward_kernel(avatar_skin_args a, avatar_skin_grads gr, const V
                 dxg[2] += f * (s.x[2] - xr.z);
             }
         }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            dxg_s[i] += dxg[i];
+            dls_s[i] += dls[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dq_s[i] += dq[i];
+        }  // poses
         if (gr.d_xg) {
-            gr.d_xg[g] = dxg[0];
-            gr.d_xg[G + g] = dxg[1];
-            gr.d_xg[2 * G + g] = dxg[2];
+            gr.d_xg[g] = dxg_s[0];
+            gr.d_xg[G + g] = dxg_s[1];
+            gr.d_xg[2 * G + g] = dxg_s[2];
         }
         if (gr.d_logscale)
 #pragma unroll
-            for (int i = 0; i < 3; ++i) gr.d_logscale[i * G + g] = dls[i];
+            for (int i = 0; i < 3; ++i) gr.d_logscale[i * G + g] = dls_s[i];
         if (gr.d_quat)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) gr.d_quat[i * G + g] = dq[i];
+            for (int i = 0; i < 4; ++i) gr.d_quat[i * G + g] = dq_s[i];
     }
 }
 
 __global__ void __launch_bounds__(SKIN_THREADS)
-skin_vertices_backward_kernel(avatar_skin_args a, avatar_skin_grads gr, const float *__restrict__ dAv)
+skin_vertices_backward_kernel(avatar_skin_args a, avatar_skin_grads gr, const float *__restrict__ dAv, int B)
 {
+    // dw_vk = sum over poses of dA_v . bone_k (bones [B][J][12], dA_v [B Nv][12])
     __shared__ float bone_s[MAX_J * 12];
-    for (int i = threadIdx.x; i < 12 * a.J; i += blockDim.x) bone_s[i] = a.bone[i];
-    __syncthreads();
     const int Nv = a.Nv, J = a.J;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < Nv; v += gridDim.x * blockDim.x) {
-        float d[12];
+    for (int pb = 0; pb < B; ++pb) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 12 * J; i += blockDim.x) bone_s[i] = a.bone[(size_t)pb * 12 * J + i];
+        __syncthreads();
+        const float *dAvp = dAv + (size_t)pb * Nv * 12;
+        for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < Nv; v += gridDim.x * blockDim.x) {
+            float d[12];
 #pragma unroll
-        for (int i = 0; i < 12; ++i) d[i] = dAv[(size_t)v * 12 + i];
-        float *out = gr.d_wv + (size_t)v * J;
-        for (int k = 0; k < J; ++k) {
-            float acc = 0.f;
+            for (int i = 0; i < 12; ++i) d[i] = dAvp[(size_t)v * 12 + i];
+            float *out = gr.d_wv + (size_t)v * J;
+            for (int k = 0; k < J; ++k) {
+                float acc = pb == 0 ? 0.f : out[k];
 #pragma unroll
-            for (int i = 0; i < 12; ++i) acc = fmaf(d[i], bone_s[12 * k + i], acc);
-            out[k] = acc;
+                for (int i = 0; i < 12; ++i) acc = fmaf(d[i], bone_s[12 * k + i], acc);
+                out[k] = acc;
+            }
         }
     }
 }
 
 template <int K>
-void launch_gauss_fwd(const avatar_skin_args &a, const VertexRec *rec, int grid, cudaStream_t st)
+void launch_gauss_fwd(const avatar_skin_args &a, const VertexRec *rec, int B, int grid, cudaStream_t st)
 {
-    skin_gaussians_kernel<K><<<grid, SKIN_THREADS, 0, st>>>(a, rec);
+    skin_gaussians_kernel<K><<<dim3(grid, B), SKIN_THREADS, 0, st>>>(a, rec);
 }
 
 template <int K>
 void launch_gauss_bwd(const avatar_skin_args &a, const avatar_skin_grads &g, const VertexRec *rec,
-                      float *dAv, int grid, cudaStream_t st)
+                      float *dAv, int B, int grid, cudaStream_t st)
 {
-    skin_gaussians_backward_kernel<K><<<grid, SKIN_THREADS, 0, st>>>(a, g, rec, dAv);
+    skin_gaussians_backward_kernel<K><<<grid, SKIN_THREADS, 0, st>>>(a, g, rec, dAv, B);
 }
 
 int check_skin_args(const avatar_skin_args *a)
@@ -586,57 +634,47 @@ int grid_for(const avatar_ctx *ctx, long n, int threads)
 
 }  // namespace
 
-extern "C" size_t avatar_skin_workspace_size(const avatar_skin_args *a)
-{
-    if (!a || a->Nv < 1) return 0;
-    return av_align256((size_t)a->Nv * sizeof(VertexRec));
-}
+namespace {
 
-extern "C" int avatar_skin(avatar_ctx *ctx, const avatar_skin_args *a, void *ws, size_t ws_bytes,
-                           avatar_stream_t stream)
+// Forward of B poses (see the batched launcher's declaration for layouts).
+int skin_run(avatar_ctx *ctx, const avatar_skin_args *a, int B, void *ws, size_t ws_bytes, cudaStream_t st)
 {
-    if (!ctx) return AVATAR_ERR_INVALID_ARG;
+    if (!ctx || B < 1 || B > 65535) return AVATAR_ERR_INVALID_ARG;
     AV_TRY(check_skin_args(a));
-    if (!ws || (((uintptr_t)ws) & 255) || ws_bytes < avatar_skin_workspace_size(a)) return AVATAR_ERR_WORKSPACE;
-    cudaStream_t st = (cudaStream_t)stream;
+    if (!ws || (((uintptr_t)ws) & 255) || ws_bytes < av_align256((size_t)B * a->Nv * sizeof(VertexRec)))
+        return AVATAR_ERR_WORKSPACE;
     VertexRec *rec = (VertexRec *)ws;
-    skin_vertices_kernel<<<grid_for(ctx, a->Nv, SKIN_THREADS), SKIN_THREADS, 0, st>>>(*a, rec);
+    skin_vertices_kernel<<<dim3(grid_for(ctx, a->Nv, SKIN_THREADS), B), SKIN_THREADS, 0, st>>>(*a, rec);
     AV_CHECK_LAUNCH();
     if (a->G > 0) {
         int grid = grid_for(ctx, a->G, SKIN_THREADS);
         switch (a->K) {
-            case 1: launch_gauss_fwd<1>(*a, rec, grid, st); break;
-            case 2: launch_gauss_fwd<2>(*a, rec, grid, st); break;
-            case 3: launch_gauss_fwd<3>(*a, rec, grid, st); break;
-            case 4: launch_gauss_fwd<4>(*a, rec, grid, st); break;
-            case 5: launch_gauss_fwd<5>(*a, rec, grid, st); break;
-            case 6: launch_gauss_fwd<6>(*a, rec, grid, st); break;
-            case 7: launch_gauss_fwd<7>(*a, rec, grid, st); break;
-            default: launch_gauss_fwd<8>(*a, rec, grid, st); break;
+            case 1: launch_gauss_fwd<1>(*a, rec, B, grid, st); break;
+            case 2: launch_gauss_fwd<2>(*a, rec, B, grid, st); break;
+            case 3: launch_gauss_fwd<3>(*a, rec, B, grid, st); break;
+            case 4: launch_gauss_fwd<4>(*a, rec, B, grid, st); break;
+            case 5: launch_gauss_fwd<5>(*a, rec, B, grid, st); break;
+            case 6: launch_gauss_fwd<6>(*a, rec, B, grid, st); break;
+            case 7: launch_gauss_fwd<7>(*a, rec, B, grid, st); break;
+            default: launch_gauss_fwd<8>(*a, rec, B, grid, st); break;
         }
         AV_CHECK_LAUNCH();
     }
     return AVATAR_OK;
 }
 
-extern "C" size_t avatar_skin_backward_workspace_size(const avatar_skin_args *a)
+int skin_bwd_run(avatar_ctx *ctx, const avatar_skin_args *a, const avatar_skin_grads *g, int B, const void *fwd_ws,
+                 void *ws, size_t ws_bytes, cudaStream_t st)
 {
-    if (!a || a->Nv < 1) return 0;
-    return av_align256((size_t)a->Nv * 12 * sizeof(float));
-}
-
-extern "C" int avatar_skin_backward(avatar_ctx *ctx, const avatar_skin_args *a, const avatar_skin_grads *g,
-                                    const void *fwd_ws, void *ws, size_t ws_bytes, avatar_stream_t stream)
-{
-    if (!ctx || !g) return AVATAR_ERR_INVALID_ARG;
+    if (!ctx || !g || B < 1) return AVATAR_ERR_INVALID_ARG;
     AV_TRY(check_skin_args(a));
+    if (B > 1 && g->d_xd2) return AVATAR_ERR_INVALID_ARG;
     if (!fwd_ws || (((uintptr_t)fwd_ws) & 255)) return AVATAR_ERR_WORKSPACE;
-    if (!ws || (((uintptr_t)ws) & 255) || ws_bytes < avatar_skin_backward_workspace_size(a))
-        return AVATAR_ERR_WORKSPACE;
-    cudaStream_t st = (cudaStream_t)stream;
     const int Nv = a->Nv, G = a->G;
+    if (!ws || (((uintptr_t)ws) & 255) || ws_bytes < av_align256((size_t)B * Nv * 12 * sizeof(float)))
+        return AVATAR_ERR_WORKSPACE;
     float *dAv = (float *)ws;
-    if (cudaMemsetAsync(dAv, 0, (size_t)Nv * 12 * sizeof(float), st) != cudaSuccess) return AVATAR_ERR_CUDA;
+    if (cudaMemsetAsync(dAv, 0, (size_t)B * Nv * 12 * sizeof(float), st) != cudaSuccess) return AVATAR_ERR_CUDA;
     if (g->d_av && cudaMemsetAsync(g->d_av, 0, (size_t)3 * Nv * sizeof(float), st) != cudaSuccess)
         return AVATAR_ERR_CUDA;
     if (g->d_rv && cudaMemsetAsync(g->d_rv, 0, (size_t)Nv * sizeof(float), st) != cudaSuccess)
@@ -649,20 +687,67 @@ extern "C" int avatar_skin_backward(avatar_ctx *ctx, const avatar_skin_args *a, 
     if (G > 0) {
         int grid = grid_for(ctx, G, SKIN_THREADS);
         switch (a->K) {
-            case 1: launch_gauss_bwd<1>(*a, *g, rec, dAv, grid, st); break;
-            case 2: launch_gauss_bwd<2>(*a, *g, rec, dAv, grid, st); break;
-            case 3: launch_gauss_bwd<3>(*a, *g, rec, dAv, grid, st); break;
-            case 4: launch_gauss_bwd<4>(*a, *g, rec, dAv, grid, st); break;
-            case 5: launch_gauss_bwd<5>(*a, *g, rec, dAv, grid, st); break;
-            case 6: launch_gauss_bwd<6>(*a, *g, rec, dAv, grid, st); break;
-            case 7: launch_gauss_bwd<7>(*a, *g, rec, dAv, grid, st); break;
-            default: launch_gauss_bwd<8>(*a, *g, rec, dAv, grid, st); break;
+            case 1: launch_gauss_bwd<1>(*a, *g, rec, dAv, B, grid, st); break;
+            case 2: launch_gauss_bwd<2>(*a, *g, rec, dAv, B, grid, st); break;
+            case 3: launch_gauss_bwd<3>(*a, *g, rec, dAv, B, grid, st); break;
+            case 4: launch_gauss_bwd<4>(*a, *g, rec, dAv, B, grid, st); break;
+            case 5: launch_gauss_bwd<5>(*a, *g, rec, dAv, B, grid, st); break;
+            case 6: launch_gauss_bwd<6>(*a, *g, rec, dAv, B, grid, st); break;
+            case 7: launch_gauss_bwd<7>(*a, *g, rec, dAv, B, grid, st); break;
+            default: launch_gauss_bwd<8>(*a, *g, rec, dAv, B, grid, st); break;
         }
         AV_CHECK_LAUNCH();
     }
     if (g->d_wv) {
-        skin_vertices_backward_kernel<<<grid_for(ctx, Nv, SKIN_THREADS), SKIN_THREADS, 0, st>>>(*a, *g, dAv);
+        skin_vertices_backward_kernel<<<grid_for(ctx, Nv, SKIN_THREADS), SKIN_THREADS, 0, st>>>(*a, *g, dAv, B);
         AV_CHECK_LAUNCH();
     }
     return AVATAR_OK;
+}
+
+}  // namespace
+
+size_t av_skin_batch_workspace_size(const avatar_skin_args *a, int B)
+{
+    if (!a || a->Nv < 1 || B < 1) return 0;
+    return av_align256((size_t)B * a->Nv * sizeof(VertexRec));
+}
+
+int av_skin_batch(avatar_ctx *ctx, const avatar_skin_args *a, int B, void *ws, size_t ws_bytes, cudaStream_t st)
+{
+    return skin_run(ctx, a, B, ws, ws_bytes, st);
+}
+
+size_t av_skin_batch_backward_workspace_size(const avatar_skin_args *a, int B)
+{
+    if (!a || a->Nv < 1 || B < 1) return 0;
+    return av_align256((size_t)B * a->Nv * 12 * sizeof(float));
+}
+
+int av_skin_batch_backward(avatar_ctx *ctx, const avatar_skin_args *a, const avatar_skin_grads *g, int B,
+                           const void *fwd_ws, void *ws, size_t ws_bytes, cudaStream_t st)
+{
+    return skin_bwd_run(ctx, a, g, B, fwd_ws, ws, ws_bytes, st);
+}
+
+extern "C" size_t avatar_skin_workspace_size(const avatar_skin_args *a)
+{
+    return av_skin_batch_workspace_size(a, 1);
+}
+
+extern "C" int avatar_skin(avatar_ctx *ctx, const avatar_skin_args *a, void *ws, size_t ws_bytes,
+                           avatar_stream_t stream)
+{
+    return skin_run(ctx, a, 1, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" size_t avatar_skin_backward_workspace_size(const avatar_skin_args *a)
+{
+    return av_skin_batch_backward_workspace_size(a, 1);
+}
+
+extern "C" int avatar_skin_backward(avatar_ctx *ctx, const avatar_skin_args *a, const avatar_skin_grads *g,
+                                    const void *fwd_ws, void *ws, size_t ws_bytes, avatar_stream_t stream)
+{
+    return skin_bwd_run(ctx, a, g, 1, fwd_ws, ws, ws_bytes, (cudaStream_t)stream);
 }

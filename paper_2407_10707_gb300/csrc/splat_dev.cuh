@@ -1,0 +1,823 @@
+// Device code of the splatting stage (d) shared by the single-view entry
+// points (splat.cu) and the batched launch over many views (batch.cu):
+// EWA projection and its adjoint, blend records, the stable onesweep radix
+// sort, the pair scan, tile ranges, and the per-tile blend and its adjoint.
+//
+// Arrays of per-Gaussian values are structure-of-arrays with an explicit
+// channel stride ("cs"): a single view uses cs = G, a batch concatenates the
+// views' Gaussians (index v * G + g) and uses cs = V * G.
+#pragma once
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int RADIX = 256;
+constexpr float NEAR_Z = 0.2f;
+constexpr float ALPHA_MIN = 1.0f / 255.0f;
+constexpr float T_MIN = 1e-4f;
+constexpr float LOG2_ALPHA_MIN = -7.99435343685886f;  // log2(1/255)
+constexpr float L2E = 1.4426950408889634f;            // log2(e)
+
+struct CamDev {
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    int W, H;
+};
+
+inline CamDev to_dev(const avatar_camera &c)
+{
+    CamDev d;
+    d.fx = c.fx;
+    d.fy = c.fy;
+    d.cx = c.cx;
+    d.cy = c.cy;
+    for (int i = 0; i < 9; ++i) d.R[i] = c.R[i];
+    for (int i = 0; i < 3; ++i) d.t[i] = c.t[i];
+    d.W = c.width;
+    d.H = c.height;
+    return d;
+}
+
+// ---------------------------------------------------------------- projection
+struct Splat2D {
+    float u, v, ca, cb, cc, z;
+    int x0, y0, x1, y1;  // inclusive pixel rect; x0 > x1 when empty
+};
+
+// EWA projection of Gaussian i of (xd [3][cs], cov [6][cs]) with opacity o:
+// mean, conic of Sigma' = T Sigma T^T + 0.3 I (T = J R), view depth, and the
+// pixel rect of the ellipse q <= 2 ln(255 o) padded by one pixel.
+__device__ __forceinline__ Splat2D project_gaussian(const float *__restrict__ xd, const float *__restrict__ cov,
+                                                    size_t cs, size_t i, float o, bool culled, const CamDev &cam)
+{
+    Splat2D s;
+    float x = xd[i], y = xd[cs + i], z = xd[2 * cs + i];
+    float px = cam.R[0] * x + cam.R[1] * y + cam.R[2] * z + cam.t[0];
+    float py = cam.R[3] * x + cam.R[4] * y + cam.R[5] * z + cam.t[1];
+    float pz = cam.R[6] * x + cam.R[7] * y + cam.R[8] * z + cam.t[2];
+    bool ok = !culled && pz > NEAR_Z && o > ALPHA_MIN;
+    float u = 0.f, v = 0.f, ca = 0.f, cb = 0.f, cc = 0.f;
+    int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
+    if (ok) {
+        float iz = 1.0f / pz;
+        u = cam.fx * px * iz + cam.cx;
+        v = cam.fy * py * iz + cam.cy;
+        float j00 = cam.fx * iz, j02 = -cam.fx * px * iz * iz;
+        float j11 = cam.fy * iz, j12 = -cam.fy * py * iz * iz;
+        float T0[3], T1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T0[k] = j00 * cam.R[k] + j02 * cam.R[6 + k];
+            T1[k] = j11 * cam.R[3 + k] + j12 * cam.R[6 + k];
+        }
+        float c0 = cov[i], c1 = cov[cs + i], c2 = cov[2 * cs + i];
+        float c3 = cov[3 * cs + i], c4 = cov[4 * cs + i], c5 = cov[5 * cs + i];
+        float S0[3] = {c0 * T0[0] + c1 * T0[1] + c2 * T0[2], c1 * T0[0] + c3 * T0[1] + c4 * T0[2],
+                       c2 * T0[0] + c4 * T0[1] + c5 * T0[2]};
+        float S1[3] = {c0 * T1[0] + c1 * T1[1] + c2 * T1[2], c1 * T1[0] + c3 * T1[1] + c4 * T1[2],
+                       c2 * T1[0] + c4 * T1[1] + c5 * T1[2]};
+        float s00 = T0[0] * S0[0] + T0[1] * S0[1] + T0[2] * S0[2] + 0.3f;
+        float s01 = T1[0] * S0[0] + T1[1] * S0[1] + T1[2] * S0[2];
+        float s11 = T1[0] * S1[0] + T1[1] * S1[1] + T1[2] * S1[2] + 0.3f;
+        float det = s00 * s11 - s01 * s01;
+        if (det > 0.f) {
+            float id = 1.0f / det;
+            ca = s11 * id;
+            cb = -s01 * id;
+            cc = s00 * id;
+            float r2 = 2.0f * logf(255.0f * o);
+            float ex = sqrtf(r2 * s00) + 1.0f, ey = sqrtf(r2 * s11) + 1.0f;
+            float fx0 = ceilf(u - ex - 0.5f), fx1 = floorf(u + ex - 0.5f);
+            float fy0 = ceilf(v - ey - 0.5f), fy1 = floorf(v + ey - 0.5f);
+            fx0 = fmaxf(fx0, 0.f);
+            fy0 = fmaxf(fy0, 0.f);
+            fx1 = fminf(fx1, (float)(cam.W - 1));
+            fy1 = fminf(fy1, (float)(cam.H - 1));
+            if (fx0 <= fx1 && fy0 <= fy1) {
+                x0 = (int)fx0;
+                x1 = (int)fx1;
+                y0 = (int)fy0;
+                y1 = (int)fy1;
+            }
+        } else {
+            ok = false;
+        }
+    }
+    if (!ok) {
+        u = v = ca = cb = cc = 0.f;
+        x0 = y0 = 0;
+        x1 = y1 = -1;
+    }
+    s.u = u;
+    s.v = v;
+    s.ca = ca;
+    s.cb = cb;
+    s.cc = cc;
+    s.z = pz;
+    s.x0 = x0;
+    s.y0 = y0;
+    s.x1 = x1;
+    s.y1 = y1;
+    return s;
+}
+
+// Writes a projection into the caller-visible buffers (mean2d [2][cs],
+// conic [3][cs], depth [cs], rect [4][cs]) at index i.
+__device__ __forceinline__ void store_splat(const Splat2D &s, size_t cs, size_t i, float *mean2d, float *conic,
+                                            float *depth, int32_t *rect)
+{
+    mean2d[i] = s.u;
+    mean2d[cs + i] = s.v;
+    conic[i] = s.ca;
+    conic[cs + i] = s.cb;
+    conic[2 * cs + i] = s.cc;
+    depth[i] = s.z;
+    rect[i] = s.x0;
+    rect[cs + i] = s.y0;
+    rect[2 * cs + i] = s.x1;
+    rect[3 * cs + i] = s.y1;
+}
+
+// Tiles of edge TS that the rect touches (0 for an empty or out-of-image rect).
+__device__ __forceinline__ int rect_tiles(int x0, int y0, int x1, int y1, int W, int H, int TS)
+{
+    if (x0 <= x1 && y0 <= y1 && x0 >= 0 && y0 >= 0 && x1 < W && y1 < H)
+        return (x1 / TS - x0 / TS + 1) * (y1 / TS - y0 / TS + 1);
+    return 0;
+}
+
+// Blend records of one Gaussian.  The conic is held in log2 units,
+//   log2(alpha_raw) = qa dx^2 + qb dx dy + qc dy^2 + log2 o
+// with qa = -a/2 log2(e), qb = -b log2(e), qc = -c/2 log2(e), so that a pixel
+// rejects a Gaussian (alpha < 1/255) with a few FMAs and no exponential.
+__device__ __forceinline__ void make_records(float mx, float my, float ca, float cb, float cc, int x0, int y0,
+                                             int x1, int y1, float r, float g, float b, float o, float4 &rec0,
+                                             float4 &rec1, float4 &rec2)
+{
+    rec0 = make_float4(mx, my, -0.5f * L2E * ca, -L2E * cb);
+    rec1 = make_float4(-0.5f * L2E * cc, o > 0.f ? log2f(o) : -1e30f, __int_as_float((x0 & 0xffff) | (y0 << 16)),
+                       __int_as_float((x1 & 0xffff) | (y1 << 16)));
+    rec2 = make_float4(r, g, b, o);
+}
+
+// ---------------------------------------------------------------- scans
+__device__ __forceinline__ int chunk_range(int n, int NB, int b, int &begin)
+{
+    int chunk = (n + NB - 1) / NB;
+    begin = b * chunk;
+    int end = begin + chunk;
+    if (end > n) end = n;
+    if (begin > n) begin = n;
+    return end;
+}
+
+// Exclusive block-wide scan of one value per thread (blockDim <= 1024).
+__device__ __forceinline__ int block_exclusive_scan(int v, int &total)
+{
+    __shared__ int wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    if (warp == 0) {
+        int s = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        wsum[lane] = s;  // inclusive warp prefix
+    }
+    __syncthreads();
+    int warp_base = warp > 0 ? wsum[warp - 1] : 0;
+    total = wsum[nw - 1];
+    __syncthreads();
+    return warp_base + x - v;
+}
+
+// ---------------------------------------------------------------- radix sort
+// Stable LSD radix sort, 8-bit digits, one kernel per digit pass:
+//   sort_hist_kernel   global digit histograms of every pass in one read
+//   onesweep_kernel    each block takes the next 2048-key tile (ticket order),
+//                      ranks its keys stably in shared memory, publishes its
+//                      digit counts and finds its global offsets by
+//                      decoupled look-back over earlier tiles, then scatters.
+// Look-back spins are bounded: a wait that expires reports
+// AVATAR_ERR_TIMEOUT and the block carries on (never hangs).
+constexpr int OS_THREADS = 256;
+constexpr int OS_WARPS = OS_THREADS / 32;
+constexpr int OS_ITEMS = 8;
+constexpr int OS_TILE = OS_THREADS * OS_ITEMS;  // 2048 keys per tile
+constexpr int OS_MAX_PASSES = 4;
+constexpr unsigned FLAG_AGG = 1u << 30, FLAG_INC = 2u << 30, FLAG_MASK = 3u << 30;
+constexpr int SPIN_LIMIT = 1 << 22;
+constexpr int OS_LOOKBACK = 16;
+
+__device__ __forceinline__ unsigned ld_volatile(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.volatile.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void st_volatile(unsigned *p, unsigned v)
+{
+    asm volatile("st.volatile.global.u32 [%0], %1;" ::"l"(p), "r"(v));
+}
+
+__global__ void __launch_bounds__(OS_THREADS)
+sort_hist_kernel(const uint32_t *__restrict__ keys, const int32_t *__restrict__ n_ptr, int cap, int passes,
+                 int32_t *__restrict__ hist)
+{
+    __shared__ int cnt[OS_MAX_PASSES][RADIX];
+    for (int i = threadIdx.x; i < OS_MAX_PASSES * RADIX; i += blockDim.x) (&cnt[0][0])[i] = 0;
+    __syncthreads();
+    const int n = min(*n_ptr, cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&cnt[p][(k >> (8 * p)) & 255u], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) {
+        int v = (&cnt[0][0])[i];
+        if (v) atomicAdd(hist + i, v);
+    }
+}
+
+__global__ void __launch_bounds__(OS_THREADS)
+onesweep_kernel(const uint32_t *__restrict__ kin, const int32_t *__restrict__ vin, uint32_t *__restrict__ kout,
+                int32_t *__restrict__ vout, const int32_t *__restrict__ n_ptr, int cap, int shift,
+                const int32_t *__restrict__ hist, unsigned *__restrict__ desc, int32_t *__restrict__ ticket,
+                int32_t *status)
+{
+    __shared__ int s_tile;
+    __shared__ int s_wcnt[OS_WARPS][RADIX];  // running, then exclusive-over-warps digit counts
+    __shared__ int s_gbase[RADIX];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(ticket, 1);
+    for (int i = tid; i < OS_WARPS * RADIX; i += OS_THREADS) (&s_wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const int tile = s_tile;
+    const int n = min(*n_ptr, cap);
+    const int base = tile * OS_TILE;
+    if (base >= n) return;  // tickets are taken in order: no later tile waits on this one
+    // warp w owns the contiguous segment [base + 256 w, base + 256 (w + 1))
+    uint32_t key[OS_ITEMS];
+    int32_t val[OS_ITEMS];
+    int rank[OS_ITEMS];
+    int dig[OS_ITEMS];
+#pragma unroll
+    for (int i = 0; i < OS_ITEMS; ++i) {
+        int idx = base + warp * (32 * OS_ITEMS) + i * 32 + lane;
+        bool ok = idx < n;
+        key[i] = ok ? kin[idx] : 0u;
+        val[i] = ok ? vin[idx] : 0;
+        dig[i] = ok ? (int)((key[i] >> shift) & 255u) : RADIX;
+    }
+#pragma unroll
+    for (int i = 0; i < OS_ITEMS; ++i) {
+        unsigned peers = __match_any_sync(0xffffffffu, dig[i]);
+        int before = dig[i] < RADIX ? s_wcnt[warp][dig[i]] : 0;
+        rank[i] = before + __popc(peers & lanemask_lt());
+        __syncwarp();
+        if (dig[i] < RADIX && (peers & lanemask_lt()) == 0) s_wcnt[warp][dig[i]] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // thread d: exclusive scan of digit d over warps, publish, look back
+    {
+        const int d = tid;
+        int sum = 0;
+#pragma unroll
+        for (int w = 0; w < OS_WARPS; ++w) {
+            int c = s_wcnt[w][d];
+            s_wcnt[w][d] = sum;
+            sum += c;
+        }
+        unsigned *my = desc + (size_t)tile * RADIX + d;
+        st_volatile(my, (tile == 0 ? FLAG_INC : FLAG_AGG) | (unsigned)sum);
+        // decoupled look-back, OS_LOOKBACK predecessors per round trip
+        int prefix = 0;
+        bool found = tile == 0;
+        for (int p = tile - 1; p >= 0 && !found; p -= OS_LOOKBACK) {
+            unsigned v[OS_LOOKBACK];
+#pragma unroll
+            for (int i = 0; i < OS_LOOKBACK; ++i)
+                v[i] = (p - i >= 0) ? ld_volatile(desc + (size_t)(p - i) * RADIX + d) : FLAG_INC;
+#pragma unroll
+            for (int i = 0; i < OS_LOOKBACK; ++i) {
+                if (found) break;
+                unsigned x = v[i];
+                if (p - i >= 0) {
+                    int spins = 0;
+                    while ((x & FLAG_MASK) == 0) {
+                        if (++spins > SPIN_LIMIT) {
+                            av_report(status, AVATAR_ERR_TIMEOUT);
+                            x = FLAG_INC;
+                            break;
+                        }
+                        __nanosleep(32);
+                        x = ld_volatile(desc + (size_t)(p - i) * RADIX + d);
+                    }
+                }
+                prefix += (int)(x & ~FLAG_MASK);
+                if ((x & FLAG_MASK) == FLAG_INC) found = true;
+            }
+        }
+        if (tile > 0) st_volatile(my, FLAG_INC | (unsigned)(prefix + sum));
+        // global base of digit d: exclusive scan of this pass's histogram
+        int tot;
+        int gex = block_exclusive_scan(hist[d], tot);
+        s_gbase[d] = gex + prefix;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < OS_ITEMS; ++i) {
+        if (dig[i] >= RADIX) continue;
+        int dst = s_gbase[dig[i]] + s_wcnt[warp][dig[i]] + rank[i];
+        kout[dst] = key[i];
+        vout[dst] = val[i];
+    }
+}
+
+// Scratch of the radix sort: [OS_MAX_PASSES][RADIX] histograms followed by
+// [OS_MAX_PASSES] tile tickets, and [passes][tiles][RADIX] look-back words.
+struct SortWs {
+    int32_t *hist;
+    unsigned *desc;
+};
+
+inline size_t sort_desc_words(size_t max_items)
+{
+    return (size_t)OS_MAX_PASSES * ((max_items + OS_TILE - 1) / OS_TILE) * RADIX;
+}
+
+// Sorts (k0, v0) of *n_ptr (<= cap) items stably on bits [0, bits) in 8-bit
+// passes, ping-ponging with (k1, v1): an even number of passes ends in
+// (k0, v0), an odd number in (k1, v1).
+inline int radix_sort(uint32_t *k0, int32_t *v0, uint32_t *k1, int32_t *v1, int bits, const int32_t *n_ptr, int cap,
+                      const SortWs &w, int32_t *status, cudaStream_t st)
+{
+    int passes = (bits + 7) / 8;
+    if (passes < 1) passes = 1;
+    if (passes > OS_MAX_PASSES) return AVATAR_ERR_INVALID_ARG;
+    const int ntiles = (cap + OS_TILE - 1) / OS_TILE;
+    if (cudaMemsetAsync(w.hist, 0, sizeof(int32_t) * (OS_MAX_PASSES * RADIX + OS_MAX_PASSES), st) != cudaSuccess ||
+        cudaMemsetAsync(w.desc, 0, sizeof(unsigned) * (size_t)passes * ntiles * RADIX, st) != cudaSuccess)
+        return AVATAR_ERR_CUDA;
+    int hgrid = (cap + OS_THREADS * 8 - 1) / (OS_THREADS * 8);
+    if (hgrid > 304) hgrid = 304;
+    if (hgrid < 1) hgrid = 1;
+    sort_hist_kernel<<<hgrid, OS_THREADS, 0, st>>>(k0, n_ptr, cap, passes, w.hist);
+    uint32_t *kin = k0, *kout = k1;
+    int32_t *vin = v0, *vout = v1;
+    int32_t *tickets = w.hist + OS_MAX_PASSES * RADIX;
+    for (int p = 0; p < passes; ++p) {
+        onesweep_kernel<<<ntiles, OS_THREADS, 0, st>>>(kin, vin, kout, vout, n_ptr, cap, 8 * p, w.hist + p * RADIX,
+                                                       w.desc + (size_t)p * ntiles * RADIX, tickets + p, status);
+        uint32_t *tk = kin;
+        kin = kout;
+        kout = tk;
+        int32_t *tv = vin;
+        vin = vout;
+        vout = tv;
+    }
+    AV_CHECK_LAUNCH();
+    return AVATAR_OK;
+}
+
+inline int bits_for(long ntiles)
+{
+    int b = 0;
+    while ((1L << b) < ntiles) ++b;
+    return b;
+}
+
+// ---------------------------------------------------------------- pair scan
+__global__ void __launch_bounds__(1024)
+pair_scan_reduce_kernel(const int32_t *__restrict__ sorted_idx, const int32_t *__restrict__ npairs, int G, int NB,
+                        int32_t *__restrict__ block_sums)
+{
+    int begin;
+    int end = chunk_range(G, NB, blockIdx.x, begin);
+    long s = 0;
+    for (int i = begin + threadIdx.x; i < end; i += blockDim.x) s += npairs[sorted_idx[i]];
+    int v = (int)min(s, (long)0x3fffffff);
+    int tot;
+    block_exclusive_scan(v, tot);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024)
+pair_scan_down_kernel(const int32_t *__restrict__ sorted_idx, const int32_t *__restrict__ npairs, int G, int NB,
+                      const int32_t *__restrict__ block_sums, int32_t *__restrict__ offsets,
+                      int32_t *__restrict__ num_pairs, long cap, int32_t *status)
+{
+    __shared__ long s_base;
+    if (threadIdx.x == 0) {
+        long b = 0, tot = 0;
+        for (int i = 0; i < NB; ++i) {
+            if (i < (int)blockIdx.x) b += block_sums[i];
+            tot += block_sums[i];
+        }
+        s_base = b;
+        if (blockIdx.x == 0) {
+            long t = tot > 0x7fffffffL ? 0x7fffffffL : tot;
+            *num_pairs = (int32_t)t;
+            if (tot > cap) av_report(status, AVATAR_ERR_OVERFLOW);
+        }
+    }
+    __syncthreads();
+    long running = s_base;
+    int begin;
+    int end = chunk_range(G, NB, blockIdx.x, begin);
+    for (int tb = begin; tb < end; tb += blockDim.x) {
+        int i = tb + threadIdx.x;
+        int v = i < end ? npairs[sorted_idx[i]] : 0;
+        int tot;
+        int ex = block_exclusive_scan(v, tot);
+        if (i < end) offsets[i] = (int32_t)min(running + ex, (long)0x7fffffff);
+        running += tot;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+tile_ranges_kernel(const uint32_t *__restrict__ keys, const int32_t *__restrict__ num_pairs, long cap, int ntiles,
+                   int2 *__restrict__ ranges)
+{
+    // after an overflow the pair list is incomplete: leave every tile empty
+    if ((long)*num_pairs > cap) return;
+    int n = *num_pairs;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t t = keys[i];
+        if (t >= (uint32_t)ntiles) continue;
+        if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
+        if (i == n - 1 || keys[i + 1] != t) ranges[t].y = i + 1;
+    }
+}
+
+// ---------------------------------------------------------------- blend
+// One CTA per TS x TS tile.  Warp w owns an 8 x (4 PPT) pixel box of the
+// tile (lane l, pixel k at (l % 8, l / 8 + 4 k) inside it); Gaussians are
+// staged NTH at a time in shared memory, and a warp skips every Gaussian
+// whose pixel rect misses its box (no pixel there can reach alpha = 1/255).
+template <int TS, int PPT>
+struct BoxMap {
+    static constexpr int BW = 8, BH = 4 * PPT, BPR = TS / BW;
+    int x0, y0;  // box origin (pixels)
+    __device__ BoxMap(int tx, int ty, int warp)
+    {
+        x0 = tx * TS + (warp % BPR) * BW;
+        y0 = ty * TS + (warp / BPR) * BH;
+    }
+    __device__ int px(int lane) const { return x0 + (lane & 7); }
+    __device__ int py(int lane, int k) const { return y0 + (lane >> 3) + 4 * k; }
+    // bit w set iff the packed rect (x0|y0<<16, x1|y1<<16) meets warp w's box
+    static __device__ unsigned mask(int tx, int ty, float lo, float hi)
+    {
+        constexpr int NB = TS * TS / (BW * BH);
+        int a = __float_as_int(lo), b = __float_as_int(hi);
+        int rx0 = (a & 0xffff) - tx * TS, ry0 = ((unsigned)a >> 16) - ty * TS;
+        int rx1 = (b & 0xffff) - tx * TS, ry1 = ((unsigned)b >> 16) - ty * TS;
+        // box columns [c0, c1] and rows [r0, r1] the rect overlaps (tile-local)
+        int c0 = max(rx0, 0) / BW, c1 = min(rx1, TS - 1) / BW;
+        int r0 = max(ry0, 0) / BH, r1 = min(ry1, TS - 1) / BH;
+        unsigned m = 0;
+#pragma unroll
+        for (int w = 0; w < NB; ++w) {
+            int c = w % BPR, r = w / BPR;
+            if (c >= c0 && c <= c1 && r >= r0 && r <= r1) m |= 1u << w;
+        }
+        return (rx1 < 0 || ry1 < 0 || rx0 >= TS || ry0 >= TS) ? 0u : m;
+    }
+};
+
+// Front-to-back blend of tile (tx, ty) of a W x H image over the sorted
+// pairs [rg.x, rg.y); writes the tile's pixels of image [3][H][W], T_final
+// and n_last.  Every thread of the CTA calls it (it synchronises the CTA).
+template <int TS, int PPT>
+__device__ __forceinline__ void blend_tile(int2 rg, const int32_t *__restrict__ pair_gauss,
+                                           const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
+                                           const float4 *__restrict__ rec2, int W, int H, int tx, int ty,
+                                           float *__restrict__ image, float *__restrict__ T_final,
+                                           int32_t *__restrict__ n_last)
+{
+    constexpr int NTH = TS * TS / PPT;
+    __shared__ float4 s0[NTH];
+    __shared__ float4 s1[NTH];
+    __shared__ float4 s2[NTH];
+    __shared__ unsigned smask[NTH];
+    const int tid = threadIdx.x;
+    const unsigned wbit = 1u << (tid >> 5);
+    const BoxMap<TS, PPT> box(tx, ty, tid >> 5);
+    float fx[PPT], fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
+    int last[PPT];
+    bool live[PPT];
+    bool done = true;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int px = box.px(tid & 31), py = box.py(tid & 31, k);
+        fx[k] = px + 0.5f;
+        fy[k] = py + 0.5f;
+        T[k] = 1.f;
+        C0[k] = C1[k] = C2[k] = 0.f;
+        last[k] = 0;
+        live[k] = px < W && py < H;
+        done = done && !live[k];
+    }
+    const int n = rg.y - rg.x;
+    for (int base = 0; base < n; base += NTH) {
+        if (__syncthreads_count(done) == NTH) break;
+        int idx = base + tid;
+        if (idx < n) {
+            int g = pair_gauss[rg.x + idx];
+            s0[tid] = rec0[g];
+            float4 r1 = rec1[g];
+            s1[tid] = r1;
+            s2[tid] = rec2[g];
+            smask[tid] = BoxMap<TS, PPT>::mask(tx, ty, r1.z, r1.w);
+        }
+        __syncthreads();
+        if (!done) {
+            const int m = min(NTH, n - base);
+            // one Gaussian's contribution to pixel k (the front-to-back step)
+            auto step = [&](int j, int k, float l2a) {
+                if (l2a < LOG2_ALPHA_MIN) return;
+                float alpha = fminf(0.99f, exp2f(l2a));
+                float test_T = T[k] * (1.f - alpha);
+                if (test_T < T_MIN) {
+                    live[k] = false;
+                    return;
+                }
+                float4 c = s2[j];
+                float wgt = alpha * T[k];
+                C0[k] = fmaf(c.x, wgt, C0[k]);
+                C1[k] = fmaf(c.y, wgt, C1[k]);
+                C2[k] = fmaf(c.z, wgt, C2[k]);
+                T[k] = test_T;
+                last[k] = base + j + 1;
+            };
+            auto l2alpha = [&](int j, int k) {
+                const float4 r0 = s0[j];
+                const float4 r1 = s1[j];
+                float dx = fx[k] - r0.x, dy = fy[k] - r0.y;
+                return fmaf(fmaf(r0.z, dx, r0.w * dy), dx, fmaf(r1.x * dy, dy, r1.y));
+            };
+            int j = 0;
+            // two Gaussians per iteration: both exponents are independent of T
+            for (; j + 1 < m; j += 2) {
+                const bool m0 = smask[j] & wbit, m1 = smask[j + 1] & wbit;  // warp-uniform
+                if (!(m0 || m1)) continue;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    if (!live[k]) continue;
+                    float a0 = m0 ? l2alpha(j, k) : -1e30f;
+                    float a1 = m1 ? l2alpha(j + 1, k) : -1e30f;
+                    step(j, k, a0);
+                    if (live[k]) step(j + 1, k, a1);
+                }
+                bool any = false;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) any = any || live[k];
+                if (!any) break;
+            }
+            if (j < m && (smask[j] & wbit)) {
+#pragma unroll
+                for (int k = 0; k < PPT; ++k)
+                    if (live[k]) step(j, k, l2alpha(j, k));
+            }
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) any = any || live[k];
+            if (!any) done = true;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int px = box.px(tid & 31), py = box.py(tid & 31, k);
+        if (px < W && py < H) {
+            const int pix = py * W + px;
+            image[pix] = C0[k];
+            image[W * H + pix] = C1[k];
+            image[2 * W * H + pix] = C2[k];
+            T_final[pix] = T[k];
+            n_last[pix] = last[k];
+        }
+    }
+}
+
+// Adjoint of blend_tile: reverse traversal from the per-pixel checkpoint
+// (T_final, n_last); per-Gaussian sums are warp-reduced and added with one
+// atomic per warp into d_color [3][cs], d_opacity [cs], d_mean2d [2][cs] and
+// d_conic [3][cs] at the Gaussian's pair value.
+template <int TS, int PPT>
+__device__ __forceinline__ void blend_backward_tile(int2 rg, const int32_t *__restrict__ pair_gauss,
+                                                    const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
+                                                    const float4 *__restrict__ rec2, int W, int H, int tx, int ty,
+                                                    const float *__restrict__ T_final,
+                                                    const int32_t *__restrict__ n_last,
+                                                    const float *__restrict__ d_image, size_t cs,
+                                                    float *__restrict__ d_mean2d, float *__restrict__ d_conic,
+                                                    float *__restrict__ d_opacity, float *__restrict__ d_color)
+{
+    constexpr int NTH = TS * TS / PPT;
+    constexpr float LN2 = 0.6931471805599453f;
+    __shared__ float4 s0[NTH];
+    __shared__ float4 s1[NTH];
+    __shared__ float4 s2[NTH];
+    __shared__ int sg[NTH];
+    __shared__ unsigned smask[NTH];
+    __shared__ int s_max;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const unsigned wbit = 1u << (tid >> 5);
+    const BoxMap<TS, PPT> box(tx, ty, tid >> 5);
+    float fx[PPT], fy[PPT], T[PPT], dC0[PPT], dC1[PPT], dC2[PPT], acc0[PPT], acc1[PPT], acc2[PPT];
+    int my_last[PPT];
+    int mx_last = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int px = box.px(lane), py = box.py(lane, k);
+        const bool inside = px < W && py < H;
+        const int pix = py * W + px;
+        fx[k] = px + 0.5f;
+        fy[k] = py + 0.5f;
+        my_last[k] = inside ? n_last[pix] : 0;
+        T[k] = inside ? T_final[pix] : 1.f;
+        dC0[k] = inside ? d_image[pix] : 0.f;
+        dC1[k] = inside ? d_image[W * H + pix] : 0.f;
+        dC2[k] = inside ? d_image[2 * W * H + pix] : 0.f;
+        acc0[k] = acc1[k] = acc2[k] = 0.f;
+        mx_last = max(mx_last, my_last[k]);
+    }
+    __syncthreads();  // every thread is done with the previous tile's s_max
+    if (tid == 0) s_max = 0;
+    __syncthreads();
+    atomicMax(&s_max, mx_last);
+    __syncthreads();
+    const int n = s_max;
+    for (int end = n; end > 0; end -= NTH) {
+        const int start = max(0, end - NTH);
+        __syncthreads();
+        int idx = start + tid;
+        if (idx < end) {
+            int g = pair_gauss[rg.x + idx];
+            sg[tid] = g;
+            s0[tid] = rec0[g];
+            float4 r1 = rec1[g];
+            s1[tid] = r1;
+            s2[tid] = rec2[g];
+            smask[tid] = BoxMap<TS, PPT>::mask(tx, ty, r1.z, r1.w);
+        }
+        __syncthreads();
+        for (int j = end - 1; j >= start; --j) {
+            const int sj = j - start;
+            if (!(smask[sj] & wbit)) continue;  // warp-uniform: rect misses this warp's box
+            const float4 r1 = s1[sj];
+            const float4 r0 = s0[sj];
+            const float4 c = s2[sj];
+            // per-thread sums over this thread's pixels
+            float g_col0 = 0.f, g_col1 = 0.f, g_col2 = 0.f, g_op = 0.f, g_mx = 0.f, g_my = 0.f, g_ca = 0.f,
+                  g_cb = 0.f, g_cc = 0.f;
+            bool contrib = false;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (j >= my_last[k]) continue;
+                float dx = fx[k] - r0.x, dy = fy[k] - r0.y;
+                float l2a = fmaf(fmaf(r0.z, dx, r0.w * dy), dx, fmaf(r1.x * dy, dy, r1.y));
+                if (l2a < LOG2_ALPHA_MIN) continue;
+                float raw = exp2f(l2a);
+                float alpha = fminf(0.99f, raw);
+                contrib = true;
+                T[k] = T[k] / (1.f - alpha);
+                float wgt = alpha * T[k];
+                g_col0 = fmaf(wgt, dC0[k], g_col0);
+                g_col1 = fmaf(wgt, dC1[k], g_col1);
+                g_col2 = fmaf(wgt, dC2[k], g_col2);
+                float dalpha = T[k] * ((c.x - acc0[k]) * dC0[k] + (c.y - acc1[k]) * dC1[k] + (c.z - acc2[k]) * dC2[k]);
+                acc0[k] = alpha * c.x + (1.f - alpha) * acc0[k];
+                acc1[k] = alpha * c.y + (1.f - alpha) * acc1[k];
+                acc2[k] = alpha * c.z + (1.f - alpha) * acc2[k];
+                if (raw < 0.99f) {
+                    float dpow = dalpha * raw;  // d alpha / d power = alpha
+                    g_op += dpow;               // d alpha / d o = alpha / o (divided once below)
+                    float ca = -2.f * LN2 * r0.z, cb = -LN2 * r0.w, cc = -2.f * LN2 * r1.x;
+                    g_mx = fmaf(dpow, ca * dx + cb * dy, g_mx);
+                    g_my = fmaf(dpow, cb * dx + cc * dy, g_my);
+                    g_ca = fmaf(-0.5f * dpow, dx * dx, g_ca);
+                    g_cb = fmaf(-dpow, dx * dy, g_cb);
+                    g_cc = fmaf(-0.5f * dpow, dy * dy, g_cc);
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+                g_col0 = warp_sum(g_col0);
+                g_col1 = warp_sum(g_col1);
+                g_col2 = warp_sum(g_col2);
+                g_op = warp_sum(g_op);
+                g_mx = warp_sum(g_mx);
+                g_my = warp_sum(g_my);
+                g_ca = warp_sum(g_ca);
+                g_cb = warp_sum(g_cb);
+                g_cc = warp_sum(g_cc);
+                if (lane == 0) {
+                    const size_t g = (size_t)sg[sj];
+                    atomicAdd(d_color + g, g_col0);
+                    atomicAdd(d_color + cs + g, g_col1);
+                    atomicAdd(d_color + 2 * cs + g, g_col2);
+                    atomicAdd(d_opacity + g, g_op / c.w);
+                    atomicAdd(d_mean2d + g, g_mx);
+                    atomicAdd(d_mean2d + cs + g, g_my);
+                    atomicAdd(d_conic + g, g_ca);
+                    atomicAdd(d_conic + cs + g, g_cb);
+                    atomicAdd(d_conic + 2 * cs + g, g_cc);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- projection adjoint
+// Gradients of the EWA projection of Gaussian i (xd [3][cs], cov [6][cs])
+// from d_mean2d (dmx, dmy) and d_conic (da, db, dc): d_xd[3], d_cov[6].
+__device__ __forceinline__ void project_adjoint(const float *__restrict__ xd, const float *__restrict__ cov, size_t cs,
+                                                size_t i, const CamDev &cam, float dmx, float dmy, float da, float db,
+                                                float dc, float (&d_xd)[3], float (&d_cov)[6])
+{
+    float x = xd[i], y = xd[cs + i], z = xd[2 * cs + i];
+    float px = cam.R[0] * x + cam.R[1] * y + cam.R[2] * z + cam.t[0];
+    float py = cam.R[3] * x + cam.R[4] * y + cam.R[5] * z + cam.t[1];
+    float pz = cam.R[6] * x + cam.R[7] * y + cam.R[8] * z + cam.t[2];
+    float iz = 1.0f / pz;
+    float j00 = cam.fx * iz, j02 = -cam.fx * px * iz * iz;
+    float j11 = cam.fy * iz, j12 = -cam.fy * py * iz * iz;
+    float T0[3], T1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        T0[k] = j00 * cam.R[k] + j02 * cam.R[6 + k];
+        T1[k] = j11 * cam.R[3 + k] + j12 * cam.R[6 + k];
+    }
+    float c[6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) c[e] = cov[e * cs + i];
+    float S[9] = {c[0], c[1], c[2], c[1], c[3], c[4], c[2], c[4], c[5]};
+    float S0[3], S1[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        S0[r] = S[3 * r] * T0[0] + S[3 * r + 1] * T0[1] + S[3 * r + 2] * T0[2];
+        S1[r] = S[3 * r] * T1[0] + S[3 * r + 1] * T1[1] + S[3 * r + 2] * T1[2];
+    }
+    float s00 = T0[0] * S0[0] + T0[1] * S0[1] + T0[2] * S0[2] + 0.3f;
+    float s01 = T1[0] * S0[0] + T1[1] * S0[1] + T1[2] * S0[2];
+    float s11 = T1[0] * S1[0] + T1[1] * S1[1] + T1[2] * S1[2] + 0.3f;
+    float det = s00 * s11 - s01 * s01;
+    float id = 1.0f / det;
+    float ca = s11 * id, cb = -s01 * id, cc = s00 * id;
+    // conic (a,b,c) -> Sigma' entries (s00, s01 (scalar, both positions), s11)
+    float ds00 = -ca * ca * da - ca * cb * db - cb * cb * dc;
+    float ds11 = -cb * cb * da - cb * cc * db - cc * cc * dc;
+    float ds01 = -2.f * ca * cb * da - (ca * cc + cb * cb) * db - 2.f * cb * cc * dc;
+    // symmetric 2x2 gradient
+    float g00 = ds00, g01 = 0.5f * ds01, g11 = ds11;
+    // dSigma = T^T Gm T (3x3 symmetric)
+    float dS[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            dS[3 * r + j] = T0[r] * (g00 * T0[j] + g01 * T1[j]) + T1[r] * (g01 * T0[j] + g11 * T1[j]);
+    d_cov[0] = dS[0];
+    d_cov[1] = dS[1] + dS[3];
+    d_cov[2] = dS[2] + dS[6];
+    d_cov[3] = dS[4];
+    d_cov[4] = dS[5] + dS[7];
+    d_cov[5] = dS[8];
+    // dT = 2 Gm T Sigma  (rows 0 and 1)
+    float dT0[3], dT1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        dT0[k] = 2.f * (g00 * S0[k] + g01 * S1[k]);
+        dT1[k] = 2.f * (g01 * S0[k] + g11 * S1[k]);
+    }
+    // T = J R -> dJ = dT R^T (only the non-zero entries of J)
+    float dj00 = dT0[0] * cam.R[0] + dT0[1] * cam.R[1] + dT0[2] * cam.R[2];
+    float dj02 = dT0[0] * cam.R[6] + dT0[1] * cam.R[7] + dT0[2] * cam.R[8];
+    float dj11 = dT1[0] * cam.R[3] + dT1[1] * cam.R[4] + dT1[2] * cam.R[5];
+    float dj12 = dT1[0] * cam.R[6] + dT1[1] * cam.R[7] + dT1[2] * cam.R[8];
+    float iz2 = iz * iz, iz3 = iz2 * iz;
+    float dpx = dmx * cam.fx * iz - dj02 * cam.fx * iz2;
+    float dpy = dmy * cam.fy * iz - dj12 * cam.fy * iz2;
+    float dpz = -dmx * cam.fx * px * iz2 - dmy * cam.fy * py * iz2 - dj00 * cam.fx * iz2 +
+                dj02 * 2.f * cam.fx * px * iz3 - dj11 * cam.fy * iz2 + dj12 * 2.f * cam.fy * py * iz3;
+    d_xd[0] = cam.R[0] * dpx + cam.R[3] * dpy + cam.R[6] * dpz;
+    d_xd[1] = cam.R[1] * dpx + cam.R[4] * dpy + cam.R[7] * dpz;
+    d_xd[2] = cam.R[2] * dpx + cam.R[5] * dpy + cam.R[8] * dpz;
+}
+
+}  // namespace

@@ -18,6 +18,7 @@
 
 #include <mutex>
 
+#include "batch_internal.h"
 #include "common.cuh"
 
 namespace cg = cooperative_groups;
@@ -28,19 +29,24 @@ constexpr int VIS_THREADS = 256;
 constexpr int EMPTY_DEPTH = 0x7fffffff;
 
 struct VisParams {
+    int B;  // poses in the launch (blockIdx.z)
     int Nv, F, D, R, NW;
     int H, M, biasq;
     int rows_per_cta;
     int inv_rows;  // ceil(2^20 / rows_per_cta): row / rows_per_cta == (row * inv_rows) >> 20 for row < 2^11
 };
 
+// blockIdx.y = pose: xp holds gridDim.y poses ([3][B Nv]), qv [B Nv].
 __global__ void vis_quantize_kernel(const float *__restrict__ xp, int Nv, int qc0, int qc1, int qc2,
                                     int4 *__restrict__ qv, int32_t *status)
 {
+    const size_t SN = (size_t)gridDim.y * Nv, op = (size_t)blockIdx.y * Nv;
+    xp += op;
+    qv += op;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < Nv; v += gridDim.x * blockDim.x) {
         int q0 = (int)rintf(xp[v] * 8192.0f) - qc0;
-        int q1 = (int)rintf(xp[Nv + v] * 8192.0f) - qc1;
-        int q2 = (int)rintf(xp[2 * Nv + v] * 8192.0f) - qc2;
+        int q1 = (int)rintf(xp[SN + v] * 8192.0f) - qc1;
+        int q2 = (int)rintf(xp[2 * SN + v] * 8192.0f) - qc2;
         int bad = (q0 <= -65536 || q0 >= 65536 || q1 <= -65536 || q1 >= 65536 || q2 <= -65536 || q2 >= 65536);
         if (bad) {
             av_report(status, AVATAR_ERR_INVALID_ARG);
@@ -230,6 +236,8 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = CL == 1 ? 0 : (int)cluster.block_rank();
     const int d = blockIdx.y;
+    qv += (size_t)blockIdx.z * p.Nv;  // pose blockIdx.z of a batch
+    dirbits += (size_t)blockIdx.z * p.D * p.NW;
     const int R = p.R;
     const int slab_elems = p.rows_per_cta * R;
     uint2 *vcache = reinterpret_cast<uint2 *>(slab + slab_elems);
@@ -355,6 +363,8 @@ __global__ void vis_transpose_kernel(const uint32_t *__restrict__ dirbits, int N
 {
     const int lane = threadIdx.x & 31;
     const long total = (long)NW * OW;
+    dirbits += (size_t)blockIdx.y * D * NW;  // pose blockIdx.y of a batch
+    bits += (size_t)blockIdx.y * Nv * OW;
     for (long t = (long)(blockIdx.x * blockDim.x + threadIdx.x) / 32; t < total;
          t += (long)gridDim.x * blockDim.x / 32) {
         int vw = (int)(t / OW), ow = (int)(t % OW);
@@ -387,7 +397,7 @@ int launch_raster(const VisParams &p, const int4 *qv, const int32_t *faces, cons
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return AVATAR_ERR_CUDA;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(CL, p.D, 1);
+    cfg.gridDim = dim3(CL, p.D, p.B);
     cfg.blockDim = dim3(VIS_THREADS, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
@@ -430,13 +440,13 @@ struct VisWs {
     int2 *vranges;
 };
 
-size_t vis_ws_layout(const avatar_vis_args *a, void *base, size_t cap, VisWs *out)
+size_t vis_ws_layout(const avatar_vis_args *a, int B, void *base, size_t cap, VisWs *out)
 {
     WsCarver c(base, cap);
     int NW = (a->Nv + 31) / 32;
     VisWs w;
-    w.qv = c.take<int4>((size_t)a->Nv);
-    w.dirbits = c.take<uint32_t>((size_t)a->D * NW);
+    w.qv = c.take<int4>((size_t)B * a->Nv);
+    w.dirbits = c.take<uint32_t>((size_t)B * a->D * NW);
     w.vranges = c.take<int2>((size_t)(a->F + VIS_CHUNK - 1) / VIS_CHUNK + 1);
     if (out) *out = w;
     return c.off;
@@ -447,18 +457,20 @@ size_t vis_ws_layout(const avatar_vis_args *a, void *base, size_t cap, VisWs *ou
 extern "C" size_t avatar_visibility_workspace_size(const avatar_vis_args *a)
 {
     if (check_vis(a) != AVATAR_OK) return 0;
-    return vis_ws_layout(a, nullptr, 0, nullptr);
+    return vis_ws_layout(a, 1, nullptr, 0, nullptr);
 }
 
-extern "C" int avatar_visibility(avatar_ctx *ctx, const avatar_vis_args *a, void *ws, size_t ws_bytes,
-                                 avatar_stream_t stream)
+namespace {
+
+// Visibility of B poses at once: xp [3][B Nv], bits [B Nv][OW] (pose p's
+// vertices at rows p Nv ...); one launch per step for the whole batch.
+int vis_run(avatar_ctx *ctx, const avatar_vis_args *a, int B, void *ws, size_t ws_bytes, cudaStream_t st)
 {
-    if (!ctx) return AVATAR_ERR_INVALID_ARG;
+    if (!ctx || B < 1) return AVATAR_ERR_INVALID_ARG;
     AV_TRY(check_vis(a));
     if (!ws || (((uintptr_t)ws) & 255)) return AVATAR_ERR_WORKSPACE;
     VisWs w;
-    if (vis_ws_layout(a, ws, ws_bytes, &w) > ws_bytes) return AVATAR_ERR_WORKSPACE;
-    cudaStream_t st = (cudaStream_t)stream;
+    if (vis_ws_layout(a, B, ws, ws_bytes, &w) > ws_bytes) return AVATAR_ERR_WORKSPACE;
 
     long long H = llrint((double)a->half_extent * 67108864.0);
     if (!(H > 16LL * a->R && H <= (1LL << 30))) return AVATAR_ERR_INVALID_ARG;
@@ -474,6 +486,7 @@ extern "C" int avatar_visibility(avatar_ctx *ctx, const avatar_vis_args *a, void
     }
 
     VisParams p;
+    p.B = B;
     p.Nv = a->Nv;
     p.F = a->F;
     p.D = a->D;
@@ -489,7 +502,7 @@ extern "C" int avatar_visibility(avatar_ctx *ctx, const avatar_vis_args *a, void
 
     int qgrid = (int)((a->Nv + 255) / 256);
     if (qgrid > ctx->sm_count * 8) qgrid = ctx->sm_count * 8;
-    vis_quantize_kernel<<<qgrid, 256, 0, st>>>(a->xp, a->Nv, qc[0], qc[1], qc[2], w.qv, a->status);
+    vis_quantize_kernel<<<dim3(qgrid, B), 256, 0, st>>>(a->xp, a->Nv, qc[0], qc[1], qc[2], w.qv, a->status);
     AV_CHECK_LAUNCH();
 
     int nchunks = (a->F + VIS_CHUNK - 1) / VIS_CHUNK;
@@ -516,10 +529,29 @@ extern "C" int avatar_visibility(avatar_ctx *ctx, const avatar_vis_args *a, void
     long warps = (long)p.NW * OW;
     long tgrid = (warps * 32 + 255) / 256;
     if (tgrid > (long)ctx->sm_count * 16) tgrid = (long)ctx->sm_count * 16;
-    vis_transpose_kernel<<<(int)tgrid, 256, 0, st>>>(w.dirbits, p.NW, a->Nv, a->D, nout, OW, a->dmap, a->bits,
-                                                      a->status);
+    vis_transpose_kernel<<<dim3((int)tgrid, B), 256, 0, st>>>(w.dirbits, p.NW, a->Nv, a->D, nout, OW, a->dmap,
+                                                               a->bits, a->status);
     AV_CHECK_LAUNCH();
     return AVATAR_OK;
+}
+
+}  // namespace
+
+size_t av_visibility_batch_workspace_size(const avatar_vis_args *a, int B)
+{
+    if (check_vis(a) != AVATAR_OK || B < 1) return 0;
+    return vis_ws_layout(a, B, nullptr, 0, nullptr);
+}
+
+int av_visibility_batch(avatar_ctx *ctx, const avatar_vis_args *a, int B, void *ws, size_t ws_bytes, cudaStream_t st)
+{
+    return vis_run(ctx, a, B, ws, ws_bytes, st);
+}
+
+extern "C" int avatar_visibility(avatar_ctx *ctx, const avatar_vis_args *a, void *ws, size_t ws_bytes,
+                                 avatar_stream_t stream)
+{
+    return vis_run(ctx, a, 1, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -567,7 +599,7 @@ extern "C" int avatar_visibility_static_scratch(avatar_ctx *ctx, const avatar_vi
 {
     if (!ctx) return AVATAR_ERR_INVALID_ARG;
     AV_TRY(check_vis(a));
-    if (vis_ws_layout(a, nullptr, 0, nullptr) > VIS_STATIC_SCRATCH_BYTES) return AVATAR_ERR_WORKSPACE;
+    if (vis_ws_layout(a, 1, nullptr, 0, nullptr) > VIS_STATIC_SCRATCH_BYTES) return AVATAR_ERR_WORKSPACE;
     void *scratch = nullptr;
     AV_TRY(vis_static_scratch(ctx, &scratch));
     // Everything the visibility kernels read from scratch is written earlier in

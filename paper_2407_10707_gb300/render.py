@@ -305,3 +305,184 @@ def render_differentiable(params, st, bits, tile=16):
     sconst = dict(A=st["light"]["A"], w=st["light"]["w"], knn=t["knn"], bits=bits, cam_center=st["cam_center"])
     color, cull = ShadeFn.apply(xd, nd, ag, rg, pg, ub, params["L"], sconst)
     return SplatFn.apply(xd, cov.reshape(6, -1), params["opacity"], color, cull, st["camera"], tile)
+
+
+# ---------------------------------------------------------------- batching
+class BatchRenderer:
+    """Many poses (each with its own light) and cameras of mixed resolution
+    rendered by avatar_render_batch: one launch per stage for the whole
+    batch, capturable in one CUDA graph.  step() adds the L1 loss over all
+    views' pixels and the batched backward (avatar_render_batch_backward).
+
+    batch: a synth.Batch; attr_dtype 'bf16' stores the learnable attributes
+    in BF16.  The pair buffer grows once if the first eager call overflows."""
+
+    def __init__(self, batch, targets=None, tile=0, pair_capacity=None, vis_cull_back=True, attr_dtype="f32",
+                 device="cuda"):
+        import ctypes as C
+        from . import _lib as L
+        self.L, self.C = L, C
+        sc = batch.scene
+        f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=device)
+        self.t = api.avatar_tensors(sc.avatar, device, attr_dtype)
+        self.frames = f(sc.frames.reshape(-1, 9))
+        self.light_A, self.light_w = f(sc.light.A), f(sc.light.w)
+        self.dmap = torch.as_tensor(sc.dmap, dtype=torch.int32, device=device)
+        self.poses = f(batch.poses)
+        self.light_L = f(batch.lights)
+        self.B, self.V = batch.B, batch.V
+        self.cameras = list(batch.cameras)
+        self.view_pose = np.asarray(batch.view_pose, np.int32)
+        self.sizes = [(c.height, c.width) for c in self.cameras]
+        self.offsets = np.concatenate([[0], np.cumsum([3 * h * w for h, w in self.sizes])]).astype(np.int64)
+        self.images = torch.empty(int(self.offsets[-1]), device=device)
+        self.num_pairs = torch.zeros(1, dtype=torch.int32, device=device)
+        self.status = api.status_word(device)
+        self.device = device
+        self.views = (L.View * self.V)()
+        for v, cam in enumerate(self.cameras):
+            self.views[v].cam = api.camera_struct(cam)
+            self.views[v].pose = int(self.view_pose[v])
+            for k in range(3):
+                self.views[v].center[k] = float(cam.center[k])
+        G = self.t["xg"].shape[1]
+        self.G = G
+        self.tile = int(tile)
+        self.cull_back = vis_cull_back
+        self.sc = sc
+        cap = pair_capacity or min(0x7FFFFFFF, max(65536, 16 * G * self.V))
+        self._alloc(cap)
+        self.targets = targets
+        self.graph = None
+        self.forward()
+        torch.cuda.synchronize()
+        need = int(self.num_pairs.item())
+        if pair_capacity is None and need > cap:
+            self._alloc(min(0x7FFFFFFF, int(need * 1.25) + 1024))
+            self.status.zero_()
+            self.forward()
+            torch.cuda.synchronize()
+        self.check()
+        if targets is not None:
+            self._alloc_grads()
+            self.step()
+            torch.cuda.synchronize()
+            self.check()
+
+    def _desc(self):
+        L = self.L
+        d = L.BatchDesc()
+        t = self.t
+        d.avatar = api._skin_struct(t, dict(bone=None, xp=None, xd=None, cov=None, nd=None, ag=None, rg=None,
+                                            pg=None, ubar=None), None)
+        d.opacity = api._p(t["opacity"])
+        d.F = t["faces"].shape[0]
+        d.faces = api._p(t["faces"])
+        d.D = self.frames.shape[0]
+        d.R = int(self.sc.depth_res)
+        d.frames = api._p(self.frames)
+        for k in range(3):
+            d.center[k] = float(self.sc.window_center[k])
+        d.half_extent = float(self.sc.window_half)
+        d.bias = float(self.sc.vis_bias)
+        d.cull_back = 1 if self.cull_back else 0
+        d.NL = self.light_A.shape[0]
+        d.light_A, d.light_w, d.dmap = api._p(self.light_A), api._p(self.light_w), api._p(self.dmap)
+        d.B = self.B
+        d.poses = api._p(self.poses)
+        d.light_L = api._p(self.light_L)
+        d.V = self.V
+        d.views = self.C.cast(self.views, self.C.c_void_p)
+        d.tile = self.tile
+        d.pair_capacity = self.cap
+        d.images = api._p(self.images)
+        d.num_pairs = api._p(self.num_pairs)
+        d.status = api._p(self.status)
+        return d
+
+    def _alloc(self, cap):
+        self.cap = int(cap)
+        self.ws = None
+        d = self._desc()
+        need = self.L.load().avatar_render_batch_workspace_size(self.C.byref(d))
+        if need == 0:
+            raise self.L.AvatarError(1, "avatar_render_batch_workspace_size")
+        self.ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+
+    def _alloc_grads(self):
+        t = self.t
+        e = lambda k: torch.empty_like(t[k], dtype=torch.float32)
+        self.grads = dict(xg=e("xg"), logscale=e("logscale"), quat=e("quat"), opacity=e("opacity"), wv=e("wv"),
+                          av=e("av"), rv=e("rv"), pv=e("pv"), L=torch.empty_like(self.light_L))
+        self.loss = torch.empty(1, device=self.device)
+        self.d_images = torch.empty_like(self.images)
+
+    def _gstruct(self, d_images):
+        g = self.L.BatchGrads()
+        g.d_images = api._p(d_images)
+        for k in ("xg", "logscale", "quat", "opacity", "wv", "av", "rv", "pv"):
+            setattr(g, "d_" + k, api._p(self.grads[k]))
+        g.d_light_L = api._p(self.grads["L"])
+        return g
+
+    def image(self, v):
+        h, w = self.sizes[v]
+        return self.images[self.offsets[v]:self.offsets[v + 1]].view(3, h, w)
+
+    def forward(self):
+        d = self._desc()
+        self.L.check(self.L.load().avatar_render_batch(api.context(), self.C.byref(d), api._p(self.ws),
+                                                        self.ws.numel(), api._stream()), "avatar_render_batch")
+        return self.images
+
+    def backward(self, d_images):
+        d = self._desc()
+        g = self._gstruct(d_images)
+        self.L.check(self.L.load().avatar_render_batch_backward(api.context(), self.C.byref(d), self.C.byref(g),
+                                                                 api._p(self.ws), self.ws.numel(), api._stream()),
+                     "avatar_render_batch_backward")
+        return self.grads
+
+    def step(self):
+        """Forward, L1 loss over every view's pixels, backward."""
+        lib = self.L.load()
+        self.forward()
+        self.L.check(lib.avatar_l1_loss(api.context(), self.images.numel(), api._p(self.images),
+                                        api._p(self.targets), api._p(self.loss), api._p(self.d_images),
+                                        api._stream()), "avatar_l1_loss")
+        self.backward(self.d_images)
+        return self.loss
+
+    def autotune(self, with_grads=None):
+        """Runs the library's autotuner on this batch; returns (tile, ppt, bwd_ppt)."""
+        with_grads = self.targets is not None if with_grads is None else with_grads
+        d = self._desc()
+        tuned = (self.C.c_int * 3)()
+        g = self._gstruct(self.d_images) if with_grads else None
+        self.L.check(self.L.load().avatar_render_batch_autotune(
+            api.context(), self.C.byref(d), self.C.byref(g) if g is not None else None, api._p(self.ws),
+            self.ws.numel(), api._stream(), tuned), "avatar_render_batch_autotune")
+        return tuple(tuned)
+
+    def capture(self, train=None):
+        """Capture forward() (or step() with train=True) in one CUDA graph."""
+        train = self.targets is not None if train is None else train
+        fn = self.step if train else self.forward
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            fn()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+        return self.images
+
+    def check(self):
+        api.raise_on_status(self.status, "render_batch")

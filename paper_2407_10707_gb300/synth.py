@@ -445,3 +445,66 @@ def config_scene(name: str, **overrides) -> Scene:
     kw = dict(CONFIGS[name])
     kw.update(overrides)
     return make_scene(**kw)
+
+
+# ---------------------------------------------------------------------------
+# Batched workloads: poses x cameras of mixed resolution, one light per pose
+# ---------------------------------------------------------------------------
+@dataclass
+class Batch:
+    scene: Scene            # the avatar, light texel geometry and visibility geometry
+    poses: np.ndarray       # [B,24,3] axis-angle (pose 0 is the scene's own pose)
+    lights: np.ndarray      # [B,K,3] radiance of each pose's environment light
+    cameras: list           # [V] Camera
+    view_pose: np.ndarray   # [V] int32, pose shown by each view
+
+    @property
+    def B(self):
+        return self.poses.shape[0]
+
+    @property
+    def V(self):
+        return len(self.cameras)
+
+
+def make_batch(scene: Scene, n_poses: int, cams_per_pose: int, resolutions, seed: int,
+               pose_deg: float = 30.0, dist: float = 3.2) -> Batch:
+    """Pose p (random joint rotations within +-pose_deg; pose 0 = the scene's)
+    lit by its own log-normal light, seen by cams_per_pose cameras orbiting
+    the body at distance dist; resolutions (width, height) cycle over the views."""
+    rng = np.random.default_rng(seed + 2000)
+    poses = [scene.avatar.pose] + [random_pose(rng, pose_deg) for _ in range(n_poses - 1)]
+    lights = [scene.light.L] + [np.exp(rng.normal(-1.0, 0.5, size=scene.light.L.shape))
+                                for _ in range(n_poses - 1)]
+    cams, vp = [], []
+    v = 0
+    for p in range(n_poses):
+        az0 = rng.uniform(0.0, 2.0 * math.pi)
+        for c in range(cams_per_pose):
+            az = az0 + 2.0 * math.pi * c / cams_per_pose
+            el = rng.uniform(-0.15, 0.25)
+            eye = (dist * math.sin(az) * math.cos(el), dist * math.sin(el) - 0.1, dist * math.cos(az) * math.cos(el))
+            w, h = resolutions[v % len(resolutions)]
+            cams.append(look_at_camera(w, h, eye))
+            vp.append(p)
+            v += 1
+    return Batch(scene=scene, poses=np.stack(poses), lights=np.stack(lights), cameras=cams,
+                 view_pose=np.asarray(vp, np.int32))
+
+
+# Batched configurations: (scene config, poses, cameras per pose, resolutions, seed)
+BATCH_CONFIGS = {
+    # 32 poses x 4 cameras cycling 512x512, 1080x1080 and 1920 wide x 1080 high
+    "c4_batch": dict(scene="c2_paper", n_poses=32, cams_per_pose=4,
+                     resolutions=[(512, 512), (1080, 1080), (1920, 1080)], seed=2),
+    # the same structure at test size, with image sizes that are no multiple of the tile edges
+    "c4_small": dict(scene="c1_small", n_poses=3, cams_per_pose=2,
+                     resolutions=[(64, 64), (100, 72), (136, 80)], seed=2),
+}
+
+
+def config_batch(name: str, **overrides) -> Batch:
+    kw = dict(BATCH_CONFIGS[name])
+    kw.update(overrides)
+    scene = config_scene(kw.pop("scene"))
+    return make_batch(scene, **kw)

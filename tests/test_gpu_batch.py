@@ -1,0 +1,163 @@
+"""The batched render (avatar_render_batch): poses x cameras of mixed
+resolution, each pose with its own light, one launch per stage.
+
+Every stage of the batch runs the same per-element arithmetic as the
+per-frame calls, and the one depth sort over all views keeps each view's
+(depth, index) order, so each view's image must equal the per-frame render of
+that view bit for bit.  Gradients are sums over views of the per-frame
+gradients (the batch loss is the mean over all views' pixels), equal up to the
+order of floating-point accumulation: 2e-4 relative.  Against the FP64
+oracle, sampled pixels of two views meet the per-frame pixel bound.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from _common import OP, rel_err, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PIX_TOL = 2e-4
+GRAD_TOL = 2e-4
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2407_10707_gb300 import api, render
+    return api, render
+
+
+@pytest.fixture(scope="module")
+def batch():
+    return synth.config_batch("c4_small")
+
+
+def view_scene(b, v):
+    """The single-frame scene of view v: its pose, its pose's light, its camera."""
+    p = int(b.view_pose[v])
+    sc = b.scene
+    av = dataclasses.replace(sc.avatar, pose=b.poses[p])
+    light = synth.Light(L=b.lights[p], A=sc.light.A, w=sc.light.w)
+    return dataclasses.replace(sc, avatar=av, light=light, camera=b.cameras[v])
+
+
+def N(t):
+    return t.detach().float().cpu().numpy()
+
+
+@pytest.mark.parametrize("attr_dtype", ["f32", "bf16"])
+def test_batch_images_equal_per_frame_renders(gpu, batch, attr_dtype):
+    api, render = gpu
+    br = render.BatchRenderer(batch, tile=16, attr_dtype=attr_dtype)
+    for v in range(batch.V):
+        r = render.Renderer(render.scene_tensors(view_scene(batch, v), attr_dtype=attr_dtype))
+        r.check()
+        diff = (br.image(v) - r.sb.image).abs()
+        assert torch.equal(br.image(v), r.sb.image), \
+            f"view {v}: {int((diff > 0).sum())} of {diff.numel()} values differ, max {float(diff.max()):.3e}"
+
+
+def test_batch_matches_oracle_on_sampled_pixels(gpu, batch):
+    api, render = gpu
+    br = render.BatchRenderer(batch, tile=16)
+    rng = np.random.default_rng(7)
+    for v in (0, 3):
+        sc = view_scene(batch, v)
+        n = sc.camera.width * sc.camera.height
+        pix = np.sort(rng.choice(n, size=min(n, 4096), replace=False)).astype(np.int32)
+        ref = OP.frame(sc, pixels=pix)
+        img = N(br.image(v)).reshape(3, -1).T[pix]
+        ok = ref["amb"] == 0
+        bad = np.abs(img - ref["rgb"]).max(axis=1) > PIX_TOL
+        print(f"view {v}: {int((bad & ok).sum())} of {len(pix)} sampled pixels > {PIX_TOL}")
+        assert (bad & ok).mean() < 0.01
+        assert np.abs(img - ref["rgb"]).max() < 0.05
+
+
+def _targets(br, seed=3):
+    rng = np.random.default_rng(seed)
+    img = N(br.images)
+    return torch.as_tensor(np.clip(img * rng.uniform(0.8, 1.2, img.shape), 0, None).astype(np.float32),
+                           device="cuda")
+
+
+def test_batch_gradients_are_the_sum_of_per_frame_gradients(gpu, batch):
+    api, render = gpu
+    probe = render.BatchRenderer(batch, tile=16)
+    targets = _targets(probe)
+    br = render.BatchRenderer(batch, targets=targets, tile=16)
+    loss_b = float(br.loss.item())
+    gb = {k: N(v) for k, v in br.grads.items()}
+    total = float(br.offsets[-1])
+    want = {k: np.zeros_like(v) for k, v in gb.items()}
+    loss_sum = 0.0
+    for v in range(batch.V):
+        h, w = br.sizes[v]
+        tgt = targets[br.offsets[v]:br.offsets[v + 1]].view(3, h, w)
+        ts = render.TrainStep(render.scene_tensors(view_scene(batch, v)), tgt)
+        torch.cuda.synchronize()
+        ts.check()
+        wgt = 3 * h * w / total
+        loss_sum += wgt * float(ts.loss.item())
+        g = {k: N(x) for k, x in ts.grads().items()}
+        for k in ("xg", "logscale", "quat", "opacity", "wv", "av", "rv", "pv"):
+            want[k] += wgt * g[k]
+        want["L"][int(batch.view_pose[v])] += wgt * g["L"]
+    assert abs(loss_b - loss_sum) < 1e-5 * abs(loss_sum)
+    for k in want:
+        e = rel_err(gb[k], want[k])
+        assert e < GRAD_TOL, f"{k}: relative error {e}"
+
+
+def test_batch_graph_replay_is_identical(gpu, batch):
+    api, render = gpu
+    probe = render.BatchRenderer(batch, tile=16)
+    br = render.BatchRenderer(batch, targets=_targets(probe), tile=16)
+    img0 = br.images.clone()
+    g0 = {k: v.clone() for k, v in br.grads.items()}
+    br.capture()
+    br.images.zero_()
+    br.replay()
+    br.replay()
+    torch.cuda.synchronize()
+    br.check()
+    assert torch.equal(br.images, img0)
+    for k, v in g0.items():
+        assert rel_err(N(br.grads[k]), N(v)) < 1e-5, k   # atomics may add in another order
+
+
+def test_pair_overflow_is_reported(gpu, batch):
+    api, render = gpu
+    from paper_2407_10707_gb300 import _lib as L
+    with pytest.raises(L.AvatarError) as e:
+        render.BatchRenderer(batch, tile=16, pair_capacity=1000)
+    assert e.value.code == 3
+
+
+def test_autotune_keeps_the_images(gpu, batch):
+    api, render = gpu
+    probe = render.BatchRenderer(batch, tile=16)
+    br = render.BatchRenderer(batch, targets=_targets(probe), tile=0)
+    img0 = br.images.clone()
+    tile, ppt, bppt = br.autotune()
+    assert tile in (8, 16, 32) and ppt in (1, 2, 4) and bppt in (1, 2, 4)
+    br.status.zero_()
+    br.step()
+    torch.cuda.synchronize()
+    br.check()
+    print(f"autotuned: tile {tile}, blend pixels/thread {ppt}, backward pixels/thread {bppt}")
+    assert torch.equal(br.images, img0)   # the image does not depend on the tile edge or the split
+    lib = L_lib()
+    for key, want in ((2, 16), (0, 1), (1, 2)):   # restore the defaults for later tests
+        lib.avatar_ctx_set_tuning(api.context(), key, want)
+
+
+def L_lib():
+    from paper_2407_10707_gb300 import _lib as L
+    return L.load()
