@@ -234,7 +234,19 @@ def stage_times(r, st, reps, flush):
     import torch
     out = {}
     stream = torch.cuda.current_stream()
-    for name, fn in (("skin", r.skin), ("visibility", r.visibility), ("shade", r.shade), ("splat", r.splat)):
+    from paper_2407_10707_gb300 import api
+    t = st["avatar"]
+    args = (r.sk["xd"], r.sk["cov"], t["opacity"], r.sh["color"], r.sh["cull"], st["camera"], r.sb)
+
+    def bin_():
+        api.avatar_splat_project(*args, status=r.status)
+        api.avatar_splat_bin(*args, status=r.status)
+
+    def blend():
+        api.avatar_splat_blend(*args, status=r.status)
+
+    for name, fn in (("skin", r.skin), ("visibility", r.visibility), ("shade", r.shade), ("bin", bin_),
+                     ("blend", blend)):
         g = _graph_of(fn)
         g.replay()
         torch.cuda.synchronize()
@@ -269,8 +281,11 @@ def workload_stats(r, sc):
         lit += int((cos & ~cull[sl][None, :]).sum().item())
     P = int(r.sb.num_pairs.item())
     Fc = sc.avatar.F
+    traversed = int(r.sb.n_last.to(torch.int64).sum().item())
+    ntiles = r.sb.tile_range.shape[0]
+    tbits = max(1, (ntiles - 1).bit_length())
     return {"front_gaussians": front, "lit_pairs_upper": lit, "pairs": P, "faces": Fc,
-            "launches_per_frame": 33}
+            "traversed_pairs": traversed, "tile_sort_passes": (tbits + 7) // 8, "launches_per_frame": 33}
 
 
 def roofline(stages, stats, sc, peaks, peak_kind, clocks):
@@ -296,11 +311,19 @@ def roofline(stages, stats, sc, peaks, peak_kind, clocks):
     sh_flops = 6.0 * stats["front_gaussians"] * NL + 50.0 * stats["lit_pairs_upper"]
     out["shade"] = {"bound": "alu", "achieved": sh_flops / (stages["shade"] * 1e-3) / 1e12, "peak": fp32_peak,
                     "unit": "TFLOP/s (fp32)", "traffic": None}
-    # splatting: bytes of inputs, projection, pair lists (write + sort passes + read) and image
+    # projection + binning: bytes of the projection (81 B per Gaussian), the
+    # blend records and keys (56 B read, 56 B written per Gaussian), the
+    # 4-pass depth sort (16 B per Gaussian and pass), the pair emission
+    # (8 B per pair), the tile sort (16 B per pair and pass) and the range pass
     P = stats["pairs"]
-    sp_bytes = 53 * G + 40 * G + P * 8 * (2 + 2 * 2) + 20 * W * H
-    out["splat"] = {"bound": "hbm", "achieved": sp_bytes / (stages["splat"] * 1e-3) / 1e9, "peak": hbm,
-                    "unit": "GB/s", "traffic": None}
+    bin_bytes = G * (81 + 112 + 4 * 16 + 8) + P * (8 + 16 * stats["tile_sort_passes"] + 4)
+    out["bin"] = {"bound": "hbm", "achieved": bin_bytes / (stages["bin"] * 1e-3) / 1e9, "peak": hbm,
+                  "unit": "GB/s", "traffic": None}
+    # blend: 15 flops per (pixel, Gaussian) pair traversed up to the pixel's
+    # last contributor (a lower bound of the traversal) + the image write
+    bl_flops = 15.0 * stats["traversed_pairs"]
+    out["blend"] = {"bound": "alu", "achieved": bl_flops / (stages["blend"] * 1e-3) / 1e12, "peak": fp32_peak,
+                    "unit": "TFLOP/s (fp32)", "traffic": None}
     for v in out.values():
         v["frac"] = round(v["achieved"] / v["peak"], 4)
         v["achieved"] = round(v["achieved"], 3)
