@@ -204,8 +204,9 @@ def run_gpu(args):
         "roofline": roof,
         "clocks": clocks,
     }
-    if not args.no_forms:
-        line["forms"] = STM.forms(r, st, sc, args, dev, flush, fwd_ms, train_ms)
+    want = set() if args.no_forms else {f for f in args.forms.split(",") if f and f != "none"}
+    if want:
+        line["forms"] = STM.forms(r, st, sc, args, dev, flush, fwd_ms, train_ms, want)
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(sc, budget_s=args.cpu_budget)
     if args.workload != WORKLOAD:
@@ -404,17 +405,26 @@ def _time_graph(g, reps, flush=None):
     return ts[len(ts) // 2]
 
 
-def forms(r, st, sc, args, dev, flush, fwd_ms, train_ms):
-    """The precision, relighting and batching forms, each beside the plain
-    FP32 single-frame form on the same GPU with its stated error."""
-    import dataclasses
-
-    import torch
-
-    from paper_2407_10707_gb300 import api, render, synth
+def forms(r, st, sc, args, dev, flush, fwd_ms, train_ms, want):
+    """The precision, relighting and batching forms (those named in want),
+    each beside the plain FP32 single-frame form on the same GPU with its
+    stated error."""
     out = {}
     reps = max(3, min(args.steps, 20))
     # (1) precision: BF16 attribute storage + tensor-core shading (BF16 D, S; FP32 accumulation)
+    if "precision" in want:
+        out["precision_bf16_tc"] = _form_precision(r, st, sc, args, dev, flush, fwd_ms, train_ms, reps)
+    if "relight" in want:
+        out["relight_tc"] = _form_relight(r, st, dev, flush, reps)
+    if "batch" in want:
+        out["batch_c4"] = _form_batch(args, dev, reps)
+    return out
+
+
+def _form_precision(r, st, sc, args, dev, flush, fwd_ms, train_ms, reps):
+    import torch
+
+    from paper_2407_10707_gb300 import render
     st16 = render.scene_tensors(sc, dev, attr_dtype="bf16")
     r16 = render.Renderer(st16, tile=args.tile, shade_tc=True)
     g16 = _graph_of(r16.forward)
@@ -431,7 +441,7 @@ def forms(r, st, sc, args, dev, flush, fwd_ms, train_ms):
     err_tc = float((r32tc.sb.image - r.sb.image).abs().max().item())
     shade_tc_ms = _time_graph(_graph_of(r32tc.shade), reps, flush)
     shade_ms = _time_graph(_graph_of(r.shade), reps, flush)
-    out["precision_bf16_tc"] = {
+    return {
         "what": "BF16 storage of albedo/roughness/tint/opacity/log-scale/rotation + shading sums on tcgen05 "
                 "tensor cores (BF16 D, S weights, FP32 accumulation in TMEM)",
         "frames_per_s": round(1000.0 / f16, 3), "train_steps_per_s": round(1000.0 / t16, 3),
@@ -440,8 +450,13 @@ def forms(r, st, sc, args, dev, flush, fwd_ms, train_ms):
         "max_abs_pixel_vs_fp32_frame": err, "max_abs_pixel_tc_only_vs_fp32_frame": err_tc,
         "error_note": "tensor-core shading alone stays within the 1e-3 bound; the BF16 rounding of the stored "
                       "attributes changes the rendered avatar itself (tests pin both against the FP64 oracle)"}
-    del r16, ts16, g16, r32tc
-    # (2) relighting under 32 environment lights at once on the tensor cores
+
+
+def _form_relight(r, st, dev, flush, reps):
+    """Relighting under 32 environment lights at once on the tensor cores."""
+    import torch
+
+    from paper_2407_10707_gb300 import api
     n_env = 32
     gen = torch.Generator(device=dev).manual_seed(11)
     NL = st["light"]["L"].shape[0]
@@ -469,7 +484,7 @@ def forms(r, st, sc, args, dev, flush, fwd_ms, train_ms):
     live = int((cull == 0).sum().item())
     mma_flops = 2.0 * 2 * live * NL * 16 * ((3 * n_env + 15) // 16)
     peaks, kind = _peaks()
-    out["relight_tc"] = {
+    return {
         "what": f"colours of every Gaussian under {n_env} environment lights (Eq. 2 linear in L): one tcgen05 "
                 f"launch vs {n_env} FP32 single-light launches",
         "us_tensor_core": round(tc_ms * 1000.0, 1), "us_fp32": round(one_ms * 1000.0, 1),
@@ -479,10 +494,17 @@ def forms(r, st, sc, args, dev, flush, fwd_ms, train_ms):
                    "frac": round(mma_flops / (tc_ms * 1e-3) / 1e12 / float(peaks["bf16_tflops"]), 4),
                    "note": f"MMA flops of the two products over live Gaussians; peak {kind}; the kernel is bound "
                            f"by the CUDA-core producer of D and S, not by the tensor pipe"}}
-    del g_tc, g1, outs, colors
+
+
+def _form_batch(args, dev, reps):
+    """Batching: 32 poses x 4 cameras at 512^2 / 1080^2 / 1920x1080, own light per pose."""
+    import dataclasses
+
+    import torch
+
+    from paper_2407_10707_gb300 import render, synth
     torch.cuda.empty_cache()
-    # (3) batching: 32 poses x 4 cameras at 512^2 / 1080^2 / 1920x1080, own light per pose
-    b = synth.config_batch("c4_batch")
+    b = synth.config_batch("c4_batch", n_poses=args.batch_poses)
     probe = render.BatchRenderer(b, tile=0, attr_dtype="bf16")
     cap = probe.cap
     targets = probe.images.detach().clone() * 0.9
@@ -509,8 +531,8 @@ def forms(r, st, sc, args, dev, flush, fwd_ms, train_ms):
         cnt[(c.width, c.height)] = cnt.get((c.width, c.height), 0) + 1
     sf = sum(cnt[k] * per[k][0] for k in cnt)
     stn = sum(cnt[k] * per[k][1] for k in cnt)
-    out["batch_c4"] = {
-        "what": "32 poses x 4 cameras (512x512, 1080x1080, 1920x1080), own 16x32 light per pose, 200k Gaussians, "
+    return {
+        "what": f"{b.B} poses x 4 cameras (512x512, 1080x1080, 1920x1080), own 16x32 light per pose, 200k Gaussians, "
                 "512 visibility directions at 256^2, BF16 storage; one launch per stage, one CUDA graph",
         "views_per_s": round(b.V * 1000.0 / bf, 1), "train_views_per_s": round(b.V * 1000.0 / bt, 1),
         "ms_per_batch": round(bf, 3), "ms_per_train_batch": round(bt, 3),
@@ -521,7 +543,6 @@ def forms(r, st, sc, args, dev, flush, fwd_ms, train_ms):
         "pairs": pairs, "l2": "inputs > L2 (15 GB working set)",
         "error_note": "each view equals its per-frame render bit for bit at the same storage type (tests); "
                       "per-frame FP32 sampled pixels meet 2e-4 against the FP64 oracle"}
-    return out
 
 
 # ----------------------------------------------------------------- CPU arm
@@ -615,6 +636,8 @@ def main():
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the precision / relighting / batching forms")
+    ap.add_argument("--forms", default="precision,relight,batch", help="comma list of forms to measure")
+    ap.add_argument("--batch-poses", type=int, default=32, help="poses of the batch form (4 cameras each)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--workload", default=WORKLOAD, help="named synthetic configuration (profiling uses smaller ones)")
     args = ap.parse_args()
