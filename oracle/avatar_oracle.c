@@ -16,6 +16,9 @@
  *   orc_fk          Sec. 3.1 (forward kinematics feeding LBS; SMPL-style tree)
  *   orc_skin        Sec. 3.1, Eq. 1 (attribute interpolation), LBS of position,
  *                   normal and covariance ("rotated accordingly")
+ *   orc_visibility_tri, orc_vis_filter
+ *                   Sec. 3.2 in the paper's own form: triangle-ID images and
+ *                   the median / median / mean vertex filters (Eqs. 3-4)
  *   orc_visibility  Sec. 3.2 (mesh rasterisation toward D directions), in its
  *                   shadow-mapping form (depth map + per-vertex depth test,
  *                   the variant Sec. 3.2 contrasts itself with); integer rules
@@ -381,6 +384,176 @@ int orc_visibility(int Nv, int F, int D, int R, const double *xp, const int *fac
 }
 
 /* ------------------------------------------------------------------ */
+/* The paper's own visibility (Sec. 3.2, Eqs. 3-4)                      */
+/*  per direction d, with the projection, window and coverage rules of  */
+/*  orc_visibility:                                                     */
+/*   - triangle-ID image: each pixel keeps the covering triangle of     */
+/*     least (depth, triangle index);                                   */
+/*   - V^d[v] = 1 iff a triangle incident to v owns at least one pixel, */
+/*     or v lies outside the window (as in orc_visibility).             */
+/*  bits: [Nv][D/32], bit d of word d/32.  tri_out: [D][R][R] owning     */
+/*  triangle or -1, may be NULL.                                        */
+/* ------------------------------------------------------------------ */
+int orc_visibility_tri(int Nv, int F, int D, int R, const double *xp, const int *faces,
+                       const double *frames, const double *center, double half_extent, int cull_back,
+                       uint32_t *bits, int32_t *tri_out)
+{
+    if (D <= 0 || D % 32 != 0 || R < 1 || R > 1024 || Nv < 0 || F < 0) return -1;
+    int64_t H = (int64_t)llrint(half_extent * 67108864.0);
+    if (!(H > 16 * (int64_t)R && H <= ((int64_t)1 << 30))) return -1;
+    int64_t Mmul = ((int64_t)R << 35) / H;
+    int64_t qc[3];
+    for (int i = 0; i < 3; ++i) qc[i] = (int64_t)llrint(center[i] * 8192.0);
+    int64_t *q = (int64_t *)malloc(sizeof(int64_t) * 3 * (size_t)(Nv > 0 ? Nv : 1));
+    for (int v = 0; v < Nv; ++v)
+        for (int i = 0; i < 3; ++i) {
+            q[3 * v + i] = (int64_t)llrint(xp[3 * v + i] * 8192.0) - qc[i];
+            if (q[3 * v + i] <= -65536 || q[3 * v + i] >= 65536) {
+                free(q);
+                return -1;
+            }
+        }
+    int DW = D / 32;
+    memset(bits, 0, sizeof(uint32_t) * (size_t)Nv * DW);
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int d = 0; d < D; ++d) {
+        int64_t B[9];
+        for (int i = 0; i < 9; ++i) B[i] = (int64_t)llrint(frames[9 * d + i] * 8192.0);
+        for (int r = 0; r < 3; ++r)
+            if (B[3 * r] * B[3 * r] + B[3 * r + 1] * B[3 * r + 1] + B[3 * r + 2] * B[3 * r + 2] >
+                (int64_t)8194 * 8194)
+                err = 1;
+        int64_t *X = (int64_t *)malloc(sizeof(int64_t) * (size_t)(Nv > 0 ? Nv : 1));
+        int64_t *Y = (int64_t *)malloc(sizeof(int64_t) * (size_t)(Nv > 0 ? Nv : 1));
+        int64_t *Z = (int64_t *)malloc(sizeof(int64_t) * (size_t)(Nv > 0 ? Nv : 1));
+        unsigned char *in = (unsigned char *)malloc((size_t)(Nv > 0 ? Nv : 1));
+        int64_t *depth = (int64_t *)malloc(sizeof(int64_t) * (size_t)R * R);
+        int32_t *owner = (int32_t *)malloc(sizeof(int32_t) * (size_t)R * R);
+        unsigned char *vis = (unsigned char *)calloc((size_t)(Nv > 0 ? Nv : 1), 1);
+        for (int p = 0; p < R * R; ++p) {
+            depth[p] = INT64_MAX;
+            owner[p] = -1;
+        }
+        for (int v = 0; v < Nv; ++v) {
+            const int64_t *qv = q + 3 * v;
+            int64_t s = B[0] * qv[0] + B[1] * qv[1] + B[2] * qv[2];
+            int64_t t = B[3] * qv[0] + B[4] * qv[1] + B[5] * qv[2];
+            int64_t z = B[6] * qv[0] + B[7] * qv[1] + B[8] * qv[2];
+            X[v] = floor_div((s + H) * Mmul, (int64_t)1 << 32);
+            Y[v] = floor_div((t + H) * Mmul, (int64_t)1 << 32);
+            Z[v] = floor_div(-z, 1024);
+            in[v] = (X[v] >= 0 && X[v] < 16 * (int64_t)R && Y[v] >= 0 && Y[v] < 16 * (int64_t)R);
+        }
+        for (int f = 0; f < F; ++f) {
+            int a = faces[3 * f], b = faces[3 * f + 1], c = faces[3 * f + 2];
+            if (!in[a] || !in[b] || !in[c]) continue;
+            int64_t area = (X[b] - X[a]) * (Y[c] - Y[a]) - (Y[b] - Y[a]) * (X[c] - X[a]);
+            if (area == 0) continue;
+            if (area < 0 && cull_back) continue;
+            if (area < 0) {
+                int tmp = b;
+                b = c;
+                c = tmp;
+                area = -area;
+            }
+            int64_t xmin = X[a], xmax = X[a], ymin = Y[a], ymax = Y[a];
+            int64_t vx[2] = {X[b], X[c]}, vy[2] = {Y[b], Y[c]};
+            for (int k = 0; k < 2; ++k) {
+                if (vx[k] < xmin) xmin = vx[k];
+                if (vx[k] > xmax) xmax = vx[k];
+                if (vy[k] < ymin) ymin = vy[k];
+                if (vy[k] > ymax) ymax = vy[k];
+            }
+            int64_t i0 = -floor_div(-(xmin - 8), 16), i1 = floor_div(xmax - 8, 16);
+            int64_t j0 = -floor_div(-(ymin - 8), 16), j1 = floor_div(ymax - 8, 16);
+            if (i0 < 0) i0 = 0;
+            if (j0 < 0) j0 = 0;
+            if (i1 > R - 1) i1 = R - 1;
+            if (j1 > R - 1) j1 = R - 1;
+            for (int64_t j = j0; j <= j1; ++j)
+                for (int64_t i = i0; i <= i1; ++i) {
+                    int64_t px = 16 * i + 8, py = 16 * j + 8;
+                    int64_t wa = (X[c] - X[b]) * (py - Y[b]) - (Y[c] - Y[b]) * (px - X[b]);
+                    int64_t wb = (X[a] - X[c]) * (py - Y[c]) - (Y[a] - Y[c]) * (px - X[c]);
+                    int64_t wc = (X[b] - X[a]) * (py - Y[a]) - (Y[b] - Y[a]) * (px - X[a]);
+                    if (wa < 0 || wb < 0 || wc < 0) continue;
+                    int64_t z = floor_div(wa * Z[a] + wb * Z[b] + wc * Z[c], area);
+                    int64_t p = j * R + i;
+                    /* triangles are visited in index order: a later one wins a tie never */
+                    if (z < depth[p]) {
+                        depth[p] = z;
+                        owner[p] = f;
+                    }
+                }
+        }
+        for (int p = 0; p < R * R; ++p)
+            if (owner[p] >= 0) {
+                const int *fv = faces + 3 * (size_t)owner[p];
+                vis[fv[0]] = vis[fv[1]] = vis[fv[2]] = 1;
+            }
+        for (int v = 0; v < Nv; ++v)
+            if (vis[v] || !in[v]) {
+#pragma omp atomic
+                bits[(size_t)v * DW + (d >> 5)] |= (uint32_t)1u << (d & 31);
+            }
+        if (tri_out)
+            for (int p = 0; p < R * R; ++p) tri_out[(size_t)d * R * R + p] = owner[p];
+        free(X);
+        free(Y);
+        free(Z);
+        free(in);
+        free(depth);
+        free(owner);
+        free(vis);
+    }
+    free(q);
+    return err ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Visibility filters on mesh vertices (Eqs. 3-4):                      */
+/*   Vbar^d = mean(median(median(V^d))), each filter over S_v, the Kv    */
+/*   nearest vertices of v (knn_v [Nv][Kv], v itself included).          */
+/*   median of Kv binary values (Kv odd) = 1 iff at least (Kv+1)/2 are  */
+/*   1; mean = (number of 1s) / Kv.  count_out [Nv][D] receives Kv *     */
+/*   Vbar, an integer in 0..Kv.                                         */
+/* ------------------------------------------------------------------ */
+int orc_vis_filter(int Nv, int D, int Kv, const int *knn_v, const uint32_t *bits_in, uint8_t *count_out)
+{
+    if (Nv < 0 || D <= 0 || D % 32 != 0 || Kv < 1 || Kv % 2 == 0 || Kv > 255) return -1;
+    for (size_t i = 0; i < (size_t)Nv * Kv; ++i)
+        if (knn_v[i] < 0 || knn_v[i] >= Nv) return -1;
+    int DW = D / 32, half = (Kv + 1) / 2;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int d = 0; d < D; ++d) {
+        unsigned char *V = (unsigned char *)malloc((size_t)(Nv > 0 ? Nv : 1));
+        unsigned char *M1 = (unsigned char *)malloc((size_t)(Nv > 0 ? Nv : 1));
+        unsigned char *M2 = (unsigned char *)malloc((size_t)(Nv > 0 ? Nv : 1));
+        for (int v = 0; v < Nv; ++v) V[v] = (bits_in[(size_t)v * DW + (d >> 5)] >> (d & 31)) & 1u;
+        for (int v = 0; v < Nv; ++v) {
+            int c = 0;
+            for (int j = 0; j < Kv; ++j) c += V[knn_v[(size_t)v * Kv + j]];
+            M1[v] = c >= half;
+        }
+        for (int v = 0; v < Nv; ++v) {
+            int c = 0;
+            for (int j = 0; j < Kv; ++j) c += M1[knn_v[(size_t)v * Kv + j]];
+            M2[v] = c >= half;
+        }
+        for (int v = 0; v < Nv; ++v) {
+            int c = 0;
+            for (int j = 0; j < Kv; ++j) c += M2[knn_v[(size_t)v * Kv + j]];
+            count_out[(size_t)v * D + d] = (uint8_t)c;
+        }
+        free(V);
+        free(M1);
+        free(M2);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* Shading (Eq. 2, App. A, Sec. 3.1)                                    */
 /*  cull  : decided in FP32 exactly as  s = fma(n2,d2, fma(n1,d1, n0*d0)) */
 /*          with d = C - x_gd (FP32 subtractions); culled iff !(s > 0)   */
@@ -394,11 +567,11 @@ int orc_visibility(int Nv, int F, int D, int R, const double *xp, const int *fac
 /*     L_o += L^k A^k vis c_i (a/pi + p f_s)                             */
 /*  colour = max(L_o, 1e-6)^(1/2.2); culled Gaussians get colour 0.      */
 /* ------------------------------------------------------------------ */
-void orc_shade(int G, int K, int NL, int D, const double *xd, const double *nd, const double *ag,
-               const double *rg, const double *pg, const double *ubar, const int *knn,
-               const uint32_t *bits, const double *light_L, const double *light_A,
-               const double *light_w, const int *dmap, const double *cam_center,
-               double *color, double *radiance, unsigned char *cull)
+static void shade_impl(int G, int K, int NL, int D, const double *xd, const double *nd, const double *ag,
+                       const double *rg, const double *pg, const double *ubar, const int *knn,
+                       const uint32_t *bits, const uint8_t *vis_count, int vis_den, const double *light_L,
+                       const double *light_A, const double *light_w, const int *dmap, const double *cam_center,
+                       double *color, double *radiance, unsigned char *cull)
 {
     int DW = D / 32;
 #pragma omp parallel for schedule(dynamic, 64)
@@ -433,8 +606,13 @@ void orc_shade(int G, int K, int NL, int D, const double *xd, const double *nd, 
             double vis = 0.0;
             for (int j = 0; j < K; ++j) {
                 int v = knn[g * K + j];
-                uint32_t word = bits[(size_t)v * DW + (d >> 5)];
-                if ((word >> (d & 31)) & 1u) vis += ubar[g * K + j];
+                if (vis_count) {
+                    /* soft visibility of the paper's filters: Vbar = count / Kv */
+                    vis += ubar[g * K + j] * (double)vis_count[(size_t)v * D + d] / (double)vis_den;
+                } else {
+                    uint32_t word = bits[(size_t)v * DW + (d >> 5)];
+                    if ((word >> (d & 31)) & 1u) vis += ubar[g * K + j];
+                }
             }
             if (vis == 0.0) continue;
             double h[3] = {wi[0] + wo[0], wi[1] + wo[1], wi[2] + wo[2]};
@@ -457,6 +635,28 @@ void orc_shade(int G, int K, int NL, int D, const double *xd, const double *nd, 
             color[3 * g + c] = pow(Lo[c] > 1e-6 ? Lo[c] : 1e-6, 1.0 / 2.2);
         }
     }
+}
+
+void orc_shade(int G, int K, int NL, int D, const double *xd, const double *nd, const double *ag,
+               const double *rg, const double *pg, const double *ubar, const int *knn,
+               const uint32_t *bits, const double *light_L, const double *light_A,
+               const double *light_w, const int *dmap, const double *cam_center,
+               double *color, double *radiance, unsigned char *cull)
+{
+    shade_impl(G, K, NL, D, xd, nd, ag, rg, pg, ubar, knn, bits, NULL, 1, light_L, light_A, light_w, dmap,
+               cam_center, color, radiance, cull);
+}
+
+/* Shading with the soft vertex visibility of the paper's filters:
+ * vis_count [Nv][D] = Kv * Vbar (orc_vis_filter), vis_den = Kv. */
+void orc_shade_soft(int G, int K, int NL, int D, const double *xd, const double *nd, const double *ag,
+                    const double *rg, const double *pg, const double *ubar, const int *knn,
+                    const uint8_t *vis_count, int vis_den, const double *light_L, const double *light_A,
+                    const double *light_w, const int *dmap, const double *cam_center,
+                    double *color, double *radiance, unsigned char *cull)
+{
+    shade_impl(G, K, NL, D, xd, nd, ag, rg, pg, ubar, knn, NULL, vis_count, vis_den, light_L, light_A, light_w,
+               dmap, cam_center, color, radiance, cull);
 }
 
 /* ------------------------------------------------------------------ */

@@ -35,6 +35,8 @@ def lib():
         _lib = ctypes.CDLL(_LIB_PATH)
         _lib.orc_bin.restype = ctypes.c_long
         _lib.orc_visibility.restype = ctypes.c_int
+        _lib.orc_visibility_tri.restype = ctypes.c_int
+        _lib.orc_vis_filter.restype = ctypes.c_int
         _lib.orc_set_threads.restype = ctypes.c_int
     return _lib
 
@@ -95,6 +97,53 @@ def visibility(xp, faces, frames, center, half_extent, bias, depth_res, want_dep
     if rc != 0:
         raise ValueError("oracle visibility: argument outside the supported range")
     return (bits, depth) if want_depth else bits
+
+
+def visibility_tri(xp, faces, frames, center, half_extent, depth_res, cull_back=False, want_tri=False):
+    """The paper's triangle-ID visibility V [Nv, D/32] (uint32 bits), Sec. 3.2."""
+    xp, faces, frames = _d(xp), _i(faces), _d(np.asarray(frames).reshape(-1, 9))
+    center = _d(center)
+    Nv, F, D = xp.shape[0], faces.shape[0], frames.shape[0]
+    bits = np.zeros((Nv, D // 32), dtype=np.uint32)
+    tri = np.zeros((D, depth_res, depth_res), dtype=np.int32) if want_tri else None
+    rc = lib().orc_visibility_tri(ctypes.c_int(Nv), ctypes.c_int(F), ctypes.c_int(D), ctypes.c_int(depth_res),
+                                  _p(xp), _p(faces), _p(frames), _p(center), ctypes.c_double(half_extent),
+                                  ctypes.c_int(1 if cull_back else 0), _p(bits), _p(tri))
+    if rc != 0:
+        raise ValueError("oracle triangle-ID visibility: argument outside the supported range")
+    return (bits, tri) if want_tri else bits
+
+
+def vis_filter(bits, knn_v):
+    """Kv * mean(median(median(V))) per vertex and direction (Eqs. 3-4), uint8 [Nv, D].
+    knn_v: [Nv, Kv] nearest vertices of each vertex (itself included)."""
+    bits = np.ascontiguousarray(bits, dtype=np.uint32)
+    knn_v = _i(knn_v)
+    Nv, DW = bits.shape
+    Kv = knn_v.shape[1]
+    out = np.zeros((Nv, DW * 32), np.uint8)
+    rc = lib().orc_vis_filter(ctypes.c_int(Nv), ctypes.c_int(DW * 32), ctypes.c_int(Kv), _p(knn_v), _p(bits),
+                              _p(out))
+    if rc != 0:
+        raise ValueError("oracle visibility filter: bad sizes or indices")
+    return out
+
+
+def shade_soft(xd, nd, ag, rg, pg, ubar, knn, vis_count, vis_den, light_L, light_A, light_w, dmap, cam_center):
+    """Shading with soft vertex visibility vis_count [Nv, D] / vis_den."""
+    xd, nd, ag, rg, pg, ubar = map(_d, (xd, nd, ag, rg, pg, ubar))
+    knn, dmap = _i(knn), _i(dmap)
+    vc = np.ascontiguousarray(vis_count, dtype=np.uint8)
+    light_L, light_A, light_w, cam_center = map(_d, (light_L, light_A, light_w, cam_center))
+    G, K, NL = xd.shape[0], knn.shape[1], light_L.shape[0]
+    color = np.zeros((G, 3))
+    radiance = np.zeros((G, 3))
+    cull = np.zeros(G, dtype=np.uint8)
+    lib().orc_shade_soft(ctypes.c_int(G), ctypes.c_int(K), ctypes.c_int(NL), ctypes.c_int(vc.shape[1]),
+                         _p(xd), _p(nd), _p(ag), _p(rg), _p(pg), _p(ubar), _p(knn), _p(vc), ctypes.c_int(vis_den),
+                         _p(light_L), _p(light_A), _p(light_w), _p(dmap), _p(cam_center), _p(color), _p(radiance),
+                         _p(cull))
+    return color, radiance, cull
 
 
 def shade(xd, nd, ag, rg, pg, ubar, knn, bits, light_L, light_A, light_w, dmap, cam_center,

@@ -280,6 +280,12 @@ def knn_indices(xv: np.ndarray, pts: np.ndarray, k: int) -> np.ndarray:
     return idx.astype(np.int32)
 
 
+def vertex_knn(xv: np.ndarray, k: int = 19) -> np.ndarray:
+    """The k nearest vertices of every vertex (itself first): the neighbourhoods
+    of the visibility filters (K_v = 19 in the paper's experiments)."""
+    return knn_indices(xv, xv, k)
+
+
 def random_pose(rng, max_deg: float = 30.0) -> np.ndarray:
     axis = rng.normal(size=(24, 3))
     axis /= np.linalg.norm(axis, axis=1, keepdims=True)

@@ -637,3 +637,142 @@ def test_bf16_rounding_helper_matches_torch():
                         [1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -(1.0 + 2.0 ** -8), 0.0, -0.0]]).astype(np.float32)
     want = torch.from_numpy(x).to(torch.bfloat16).float().numpy()
     assert np.array_equal(bf16_round(x).view(np.uint32), want.view(np.uint32))
+
+
+# ---------------------------------------------------------------- the paper's visibility (Sec. 3.2)
+def test_tri_visibility_lone_triangle_and_back_faces():
+    # a lone triangle owns pixels from both sides: all three vertices visible;
+    # with back faces culled it is invisible from its back side
+    xp = np.array([[0.0, 0, 0], [0.3, 0, 0], [0, 0.3, 0]])
+    faces = np.array([[0, 1, 2]], np.int32)
+    dirs = np.zeros((32, 3))
+    dirs[:16, 2] = 1.0
+    dirs[16:, 2] = -1.0
+    b = O.visibility_tri(xp, faces, _frames_for(dirs), [0.1, 0.1, 0], 1.0, 64)[:, 0]
+    assert np.all(b == 0xFFFFFFFF)
+    bc = O.visibility_tri(xp, faces, _frames_for(dirs), [0.1, 0.1, 0], 1.0, 64, cull_back=True)[:, 0]
+    up = bc & 0xFFFF
+    down = bc >> 16
+    # the triangle is wound counter-clockwise seen from +z; which side is "front"
+    # depends on the frame's handedness: exactly one side survives the cull
+    assert (np.all(up == 0xFFFF) and np.all(down == 0)) or (np.all(up == 0) and np.all(down == 0xFFFF))
+
+
+def test_tri_visibility_parallel_quads_and_ownership():
+    # the near quad covers the far quad's overlap: far triangles there own no
+    # pixel, so far vertices inside the overlap are invisible from above
+    def quad(x0, x1, y0, y1, z, n):
+        xs = np.linspace(x0, x1, n)
+        ys = np.linspace(y0, y1, n)
+        X, Y = np.meshgrid(xs, ys)
+        v = np.stack([X.ravel(), Y.ravel(), np.full(X.size, z)], 1)
+        f = []
+        for j in range(n - 1):
+            for i in range(n - 1):
+                a = j * n + i
+                f += [(a, a + 1, a + n), (a + 1, a + n + 1, a + n)]
+        return v, np.array(f, np.int32)
+    v1, f1 = quad(-0.5, 0.5, -0.5, 0.5, 0.2, 9)
+    v2, f2 = quad(0.0, 1.0, -0.5, 0.5, -0.2, 9)
+    xp = np.concatenate([v1, v2])
+    faces = np.concatenate([f1, f2 + len(v1)])
+    dirs = np.zeros((32, 3))
+    dirs[:, 2] = 1.0
+    bits, tri = O.visibility_tri(xp, faces, _frames_for(dirs), [0.25, 0, 0], 1.2, 128, want_tri=True)
+    up = (bits[:, 0] & 1) != 0
+    n1 = len(v1)
+    assert np.all(up[:n1])
+    # a far vertex is visible iff one of its triangles owns a pixel: those
+    # triangles all lie beyond the near quad's edge x = 0.5 (step 0.125)
+    far_x = v2[:, 0]
+    assert np.all(~up[n1:][far_x < 0.5 - 0.13])
+    assert np.all(up[n1:][far_x > 0.5 + 0.01])
+    # every owning triangle index is a real triangle, and no far triangle owns a
+    # pixel whose centre lies inside the near quad
+    t0 = tri[0]
+    assert t0.max() < len(faces) and t0.min() >= -1
+    R, half, cx = 128, 1.2, 0.25
+    jj, ii = np.nonzero(t0 >= len(f1))
+    assert len(ii) > 0
+    e1, e2, _ = _frames_for(dirs)[0].reshape(3, 3)
+    s = (ii + 0.5) / R * 2 * half - half
+    t = (jj + 0.5) / R * 2 * half - half
+    wx = cx + s * e1[0] + t * e2[0]              # world x of the pixel centres the far quad owns
+    wy = s * e1[1] + t * e2[1]
+    assert np.all((wx > 0.5 - 2 * half / R) | (np.abs(wy) > 0.5 - 2 * half / R))
+
+
+def test_tri_visibility_ties_go_to_the_lower_triangle_index():
+    # two coincident triangles with distinct vertices: the same depth at every
+    # pixel, so the lower index owns them all and only its vertices are visible
+    base = np.array([[0.0, 0, 0], [0.4, 0, 0], [0, 0.4, 0]])
+    xp = np.concatenate([base, base])
+    faces = np.array([[3, 4, 5], [0, 1, 2]], np.int32)
+    dirs = np.zeros((32, 3))
+    dirs[:, 2] = 1.0
+    bits = O.visibility_tri(xp, faces, _frames_for(dirs), [0.1, 0.1, 0], 1.0, 64)[:, 0]
+    assert np.all(bits[3:] == 0xFFFFFFFF)
+    assert np.all(bits[:3] == 0)
+
+
+def test_tri_visibility_convex_sphere_hemisphere():
+    v, f, n = synth._tessellate_capsule((0, 0, 0), (0, 0, 0), 0.5, 600)
+    dirs = synth.fibonacci_directions(128)
+    bits = O.visibility_tri(v, f, _frames_for(dirs), [0, 0, 0], 0.6, 256)
+    vb = np.unpackbits(bits.view(np.uint8), bitorder="little").reshape(len(v), -1)[:, :128]
+    cosines = n @ dirs.T
+    # front-facing triangles of a convex body are never hidden; a vertex whose
+    # triangles all face away owns nothing
+    assert np.all(vb[cosines >= 0.35] == 1)
+    assert np.all(vb[cosines <= -0.35] == 0)
+
+
+def test_vis_filters_match_numpy_median_and_mean():
+    rng = np.random.default_rng(3)
+    Nv, D, Kv = 300, 64, 19
+    pts = rng.normal(size=(Nv, 3))
+    knn_v = synth.knn_indices(pts, pts, Kv)
+    V = (rng.random((Nv, D)) < 0.6).astype(np.uint8)
+    bits = np.packbits(V, axis=1, bitorder="little").view(np.uint32)
+    got = O.vis_filter(bits, knn_v)
+    m1 = np.median(V[knn_v], axis=1)            # [Nv, D]: median over the Kv neighbours
+    m2 = np.median(m1[knn_v], axis=1)
+    mean = np.mean(m2[knn_v], axis=1)
+    np.testing.assert_array_equal(got, np.rint(mean * Kv).astype(np.uint8))
+
+
+def test_vis_filters_special_cases():
+    rng = np.random.default_rng(4)
+    Nv, Kv = 200, 19
+    pts = rng.normal(size=(Nv, 3))
+    knn_v = synth.knn_indices(pts, pts, Kv)
+    ones = np.full((Nv, 1), 0xFFFFFFFF, np.uint32)
+    assert np.all(O.vis_filter(ones, knn_v) == Kv)
+    assert np.all(O.vis_filter(np.zeros_like(ones), knn_v) == 0)
+    # a single visible vertex among invisible ones is noise: the medians remove it
+    V = np.zeros((Nv, 32), np.uint8)
+    V[17, :] = 1
+    b = np.packbits(V, axis=1, bitorder="little").view(np.uint32)
+    assert np.all(O.vis_filter(b, knn_v) == 0)
+    with pytest.raises(ValueError):
+        O.vis_filter(ones, knn_v[:, :18])        # even Kv has no unique binary median
+
+
+def test_soft_shading_reduces_to_bits_for_saturated_counts():
+    # counts of 0 or Kv are the hard bits: soft shading equals bit shading
+    sc = synth.config_scene("c3_fd")
+    av = sc.avatar
+    sk = O.skin(av, O.fk(av.parents, av.joints, av.pose))
+    rng = np.random.default_rng(5)
+    D = sc.frames.shape[0]
+    V = (rng.random((av.Nv, D)) < 0.7).astype(np.uint8)
+    bits = np.packbits(V, axis=1, bitorder="little").view(np.uint32)
+    args = (sk["xd"], sk["nd"], sk["ag"], sk["rg"], sk["pg"], sk["ubar"], av.knn)
+    light = (sc.light.L, sc.light.A, sc.light.w, sc.dmap, sc.camera.center)
+    c_bits, r_bits, _ = O.shade(*args, bits, *light, D)
+    c_soft, r_soft, _ = O.shade_soft(*args, V * 19, 19, *light)
+    np.testing.assert_allclose(r_soft, r_bits, rtol=1e-12, atol=1e-14)
+    # and soft shading is linear in the counts: halving every count halves the
+    # sums of lit, unculled Gaussians' radiance before gamma
+    _, r_half, _ = O.shade_soft(*args, V * 10, 20, *light)
+    np.testing.assert_allclose(r_half, 0.5 * r_bits, rtol=1e-12, atol=1e-14)
