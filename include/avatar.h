@@ -241,6 +241,37 @@ size_t avatar_visibility_static_scratch_bytes(void);
 int avatar_visibility_static_scratch(avatar_ctx *ctx, const avatar_vis_args *a, avatar_stream_t stream);
 
 /* ------------------------------------------------------------------ */
+/* (b') The paper's own visibility - Sec. 3.2, Eqs. 3-4                 */
+/*                                                                      */
+/* Per direction d, with the projection, window and coverage rules of   */
+/* avatar_visibility: a triangle appears in the triangle-ID image iff   */
+/* at some pixel it covers its depth is the least depth there (every    */
+/* tied triangle appears), and V^d[v] = 1 iff a triangle incident to v  */
+/* appears (or v lies outside the window).  Then                        */
+/* Vbar^d = mean(median(median(V^d))), both filters                     */
+/* over S_v, the Kv nearest vertices of v (v itself included): the      */
+/* median of Kv binary values (Kv odd) is 1 iff at least (Kv+1)/2 are 1 */
+/* and the mean is their count / Kv.  Output: the count Kv * Vbar, an   */
+/* integer in 0..Kv, per vertex and light (light k uses direction       */
+/* base.dmap[k], or direction k when base.dmap is NULL) - every step is */
+/* integer, so the result is bit-exact.  One cluster of CTAs per         */
+/* direction holds the depth map and a vertex bitmap in shared memory;  */
+/* AVATAR_ERR_UNSUPPORTED when they do not fit (very large Nv).          */
+/* A bad neighbour index is reported (AVATAR_ERR_INDEX) and skipped.    */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    avatar_vis_args base;  /* geometry as for avatar_visibility (bias unused); base.bits, if not
+                              NULL, receives the unfiltered V, [Nv][D/32] in direction order */
+    int Kv;                /* filter neighbourhood, odd, 1..63 (paper: 19) */
+    const int32_t *knn_v;  /* [Kv][Nv] nearest vertices of each vertex */
+    uint8_t *vis_count;    /* [Nv][NL] output (NL = base.NL, or D when base.dmap is NULL) */
+} avatar_vis_soft_args;
+
+size_t avatar_visibility_soft_workspace_size(const avatar_vis_soft_args *a);
+int avatar_visibility_soft(avatar_ctx *ctx, const avatar_vis_soft_args *a, void *ws, size_t ws_bytes,
+                           avatar_stream_t stream);
+
+/* ------------------------------------------------------------------ */
 /* (c) Shading - Eq. 2 with the BRDF of App. A, cull and gamma (Sec 3.1)*/
 /*                                                                      */
 /* cull: with d = C - x_gd (FP32), culled iff !(fma(n2,d2,fma(n1,d1,     */
@@ -269,6 +300,10 @@ typedef struct {
     float *radiance;       /* [3][G] output L_o before gamma (read by the backward) */
     uint8_t *cull;         /* [G] output, 1 = back-facing */
     int32_t *status;
+    /* optional soft visibility of the paper's filters (avatar_visibility_soft):
+     * when not NULL it replaces bits, vis = sum_j ubar_j vis_count[S_j][k] / vis_den */
+    const uint8_t *vis_count; /* [Nv][NL] light order */
+    int vis_den;           /* Kv of the filters, >= 1 */
 } avatar_shade_args;
 
 int avatar_shade(avatar_ctx *ctx, const avatar_shade_args *a, avatar_stream_t stream);

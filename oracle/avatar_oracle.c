@@ -387,12 +387,13 @@ int orc_visibility(int Nv, int F, int D, int R, const double *xp, const int *fac
 /* The paper's own visibility (Sec. 3.2, Eqs. 3-4)                      */
 /*  per direction d, with the projection, window and coverage rules of  */
 /*  orc_visibility:                                                     */
-/*   - triangle-ID image: each pixel keeps the covering triangle of     */
-/*     least (depth, triangle index);                                   */
-/*   - V^d[v] = 1 iff a triangle incident to v owns at least one pixel, */
-/*     or v lies outside the window (as in orc_visibility).             */
-/*  bits: [Nv][D/32], bit d of word d/32.  tri_out: [D][R][R] owning     */
-/*  triangle or -1, may be NULL.                                        */
+/*   - a triangle appears in the image iff at some pixel it covers its  */
+/*     depth is the least depth there (ties: every tied triangle        */
+/*     appears - which of them a rasteriser shows is arbitrary);        */
+/*   - V^d[v] = 1 iff a triangle incident to v appears, or v lies       */
+/*     outside the window (as in orc_visibility).                       */
+/*  bits: [Nv][D/32], bit d of word d/32.  tri_out: [D][R][R] the least  */
+/*  index among the triangles at the least depth, or -1; may be NULL.   */
 /* ------------------------------------------------------------------ */
 int orc_visibility_tri(int Nv, int F, int D, int R, const double *xp, const int *faces,
                        const double *frames, const double *center, double half_extent, int cull_back,
@@ -445,52 +446,50 @@ int orc_visibility_tri(int Nv, int F, int D, int R, const double *xp, const int 
             Z[v] = floor_div(-z, 1024);
             in[v] = (X[v] >= 0 && X[v] < 16 * (int64_t)R && Y[v] >= 0 && Y[v] < 16 * (int64_t)R);
         }
-        for (int f = 0; f < F; ++f) {
-            int a = faces[3 * f], b = faces[3 * f + 1], c = faces[3 * f + 2];
-            if (!in[a] || !in[b] || !in[c]) continue;
-            int64_t area = (X[b] - X[a]) * (Y[c] - Y[a]) - (Y[b] - Y[a]) * (X[c] - X[a]);
-            if (area == 0) continue;
-            if (area < 0 && cull_back) continue;
-            if (area < 0) {
-                int tmp = b;
-                b = c;
-                c = tmp;
-                area = -area;
-            }
-            int64_t xmin = X[a], xmax = X[a], ymin = Y[a], ymax = Y[a];
-            int64_t vx[2] = {X[b], X[c]}, vy[2] = {Y[b], Y[c]};
-            for (int k = 0; k < 2; ++k) {
-                if (vx[k] < xmin) xmin = vx[k];
-                if (vx[k] > xmax) xmax = vx[k];
-                if (vy[k] < ymin) ymin = vy[k];
-                if (vy[k] > ymax) ymax = vy[k];
-            }
-            int64_t i0 = -floor_div(-(xmin - 8), 16), i1 = floor_div(xmax - 8, 16);
-            int64_t j0 = -floor_div(-(ymin - 8), 16), j1 = floor_div(ymax - 8, 16);
-            if (i0 < 0) i0 = 0;
-            if (j0 < 0) j0 = 0;
-            if (i1 > R - 1) i1 = R - 1;
-            if (j1 > R - 1) j1 = R - 1;
-            for (int64_t j = j0; j <= j1; ++j)
-                for (int64_t i = i0; i <= i1; ++i) {
-                    int64_t px = 16 * i + 8, py = 16 * j + 8;
-                    int64_t wa = (X[c] - X[b]) * (py - Y[b]) - (Y[c] - Y[b]) * (px - X[b]);
-                    int64_t wb = (X[a] - X[c]) * (py - Y[c]) - (Y[a] - Y[c]) * (px - X[c]);
-                    int64_t wc = (X[b] - X[a]) * (py - Y[a]) - (Y[b] - Y[a]) * (px - X[a]);
-                    if (wa < 0 || wb < 0 || wc < 0) continue;
-                    int64_t z = floor_div(wa * Z[a] + wb * Z[b] + wc * Z[c], area);
-                    int64_t p = j * R + i;
-                    /* triangles are visited in index order: a later one wins a tie never */
-                    if (z < depth[p]) {
-                        depth[p] = z;
-                        owner[p] = f;
-                    }
+        /* pass 1: the depth map; pass 2: the triangles at the least depth */
+        for (int pass = 0; pass < 2; ++pass)
+            for (int f = 0; f < F; ++f) {
+                int a = faces[3 * f], b = faces[3 * f + 1], c = faces[3 * f + 2];
+                if (!in[a] || !in[b] || !in[c]) continue;
+                int64_t area = (X[b] - X[a]) * (Y[c] - Y[a]) - (Y[b] - Y[a]) * (X[c] - X[a]);
+                if (area == 0) continue;
+                if (area < 0 && cull_back) continue;
+                if (area < 0) {
+                    int tmp = b;
+                    b = c;
+                    c = tmp;
+                    area = -area;
                 }
-        }
-        for (int p = 0; p < R * R; ++p)
-            if (owner[p] >= 0) {
-                const int *fv = faces + 3 * (size_t)owner[p];
-                vis[fv[0]] = vis[fv[1]] = vis[fv[2]] = 1;
+                int64_t xmin = X[a], xmax = X[a], ymin = Y[a], ymax = Y[a];
+                int64_t vx[2] = {X[b], X[c]}, vy[2] = {Y[b], Y[c]};
+                for (int k = 0; k < 2; ++k) {
+                    if (vx[k] < xmin) xmin = vx[k];
+                    if (vx[k] > xmax) xmax = vx[k];
+                    if (vy[k] < ymin) ymin = vy[k];
+                    if (vy[k] > ymax) ymax = vy[k];
+                }
+                int64_t i0 = -floor_div(-(xmin - 8), 16), i1 = floor_div(xmax - 8, 16);
+                int64_t j0 = -floor_div(-(ymin - 8), 16), j1 = floor_div(ymax - 8, 16);
+                if (i0 < 0) i0 = 0;
+                if (j0 < 0) j0 = 0;
+                if (i1 > R - 1) i1 = R - 1;
+                if (j1 > R - 1) j1 = R - 1;
+                for (int64_t j = j0; j <= j1; ++j)
+                    for (int64_t i = i0; i <= i1; ++i) {
+                        int64_t px = 16 * i + 8, py = 16 * j + 8;
+                        int64_t wa = (X[c] - X[b]) * (py - Y[b]) - (Y[c] - Y[b]) * (px - X[b]);
+                        int64_t wb = (X[a] - X[c]) * (py - Y[c]) - (Y[a] - Y[c]) * (px - X[c]);
+                        int64_t wc = (X[b] - X[a]) * (py - Y[a]) - (Y[b] - Y[a]) * (px - X[a]);
+                        if (wa < 0 || wb < 0 || wc < 0) continue;
+                        int64_t z = floor_div(wa * Z[a] + wb * Z[b] + wc * Z[c], area);
+                        int64_t p = j * R + i;
+                        if (pass == 0) {
+                            if (z < depth[p]) depth[p] = z;
+                        } else if (z == depth[p]) {
+                            vis[faces[3 * f]] = vis[faces[3 * f + 1]] = vis[faces[3 * f + 2]] = 1;
+                            if (owner[p] < 0 || f < owner[p]) owner[p] = f;
+                        }
+                    }
             }
         for (int v = 0; v < Nv; ++v)
             if (vis[v] || !in[v]) {

@@ -55,11 +55,16 @@ class VisArgs(C.Structure):
                 ("NL", I32), ("dmap", P), ("bits", P), ("status", P), ("cull_back", I32)]
 
 
+class VisSoftArgs(C.Structure):
+    _fields_ = [("base", VisArgs), ("Kv", I32), ("knn_v", P), ("vis_count", P)]
+
+
 class ShadeArgs(C.Structure):
     _fields_ = [("G", I32), ("K", I32), ("NL", I32), ("Nv", I32),
                 ("xd", P), ("nd", P), ("ag", P), ("rg", P), ("pg", P), ("ubar", P), ("knn", P),
                 ("bits", P), ("light_L", P), ("light_A", P), ("light_w", P),
-                ("cam_center", F32 * 3), ("color", P), ("radiance", P), ("cull", P), ("status", P)]
+                ("cam_center", F32 * 3), ("color", P), ("radiance", P), ("cull", P), ("status", P),
+                ("vis_count", P), ("vis_den", I32)]
 
 
 class ShadeMultiArgs(C.Structure):
@@ -126,6 +131,8 @@ _SIGNATURES = [
     ("avatar_visibility_static_scratch", [P, C.POINTER(VisArgs), P], I32),
     ("avatar_shade", [P, C.POINTER(ShadeArgs), P], I32),
     ("avatar_shade_backward", [P, C.POINTER(ShadeArgs), C.POINTER(ShadeGrads), P], I32),
+    ("avatar_visibility_soft_workspace_size", [C.POINTER(VisSoftArgs)], C.c_size_t),
+    ("avatar_visibility_soft", [P, C.POINTER(VisSoftArgs), P, C.c_size_t, P], I32),
     ("avatar_shade_multi_workspace_size", [C.POINTER(ShadeMultiArgs)], C.c_size_t),
     ("avatar_shade_multi", [P, C.POINTER(ShadeMultiArgs), P], I32),
     ("avatar_splat_num_tiles", [C.POINTER(SplatArgs)], I32),

@@ -215,15 +215,50 @@ def avatar_visibility(xp, faces, frames, center, half_extent, bias, R, dmap=None
     return bits
 
 
+def avatar_visibility_soft(xp, faces, frames, center, half_extent, R, knn_v, dmap=None, vis_count=None,
+                           raw_bits=None, ws=None, status=None, cull_back=False):
+    """(b') The paper's visibility (Sec. 3.2, Eqs. 3-4): triangle-ID images and
+    the median/median/mean filters over the Kv nearest vertices.  knn_v
+    [Kv, Nv] int32.  Returns uint8 counts Kv * Vbar, [Nv, NL] (light order
+    when dmap is given, else [Nv, D]); raw_bits, if given ([Nv, D/32] int32),
+    receives the unfiltered V in direction order."""
+    lib = L.load()
+    ctx = context()
+    Nv = xp.shape[1]
+    nout = dmap.shape[0] if dmap is not None else frames.shape[0]
+    if vis_count is None:
+        vis_count = torch.empty(Nv, nout, dtype=torch.uint8, device=xp.device)
+    a = L.VisSoftArgs()
+    a.base = _vis_struct(xp, faces, frames, center, half_extent, 0.0, R, dmap, raw_bits, status, cull_back)
+    a.Kv = knn_v.shape[0]
+    a.knn_v = _p(knn_v)
+    a.vis_count = _p(vis_count)
+    need = lib.avatar_visibility_soft_workspace_size(C.byref(a))
+    if need == 0:
+        raise L.AvatarError(1, "avatar_visibility_soft_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, xp.device)
+    L.check(lib.avatar_visibility_soft(ctx, C.byref(a), _p(ws), ws.numel(), _stream()), "avatar_visibility_soft")
+    return vis_count
+
+
 # ---------------------------------------------------------------- (c) shading
-def _shade_struct(sk, knn, bits, light, cam_center, color, radiance, cull, status):
+def _shade_struct(sk, knn, bits, light, cam_center, color, radiance, cull, status, vis_den=None):
+    """bits: visibility words (int32) or, for the soft visibility of the
+    paper's filters, uint8 counts [Nv, NL] with vis_den = Kv."""
     a = L.ShadeArgs()
     a.G = sk["xd"].shape[1]
     a.K = knn.shape[0]
     a.NL = light["L"].shape[0]
     a.Nv = bits.shape[0]
     a.xd, a.nd, a.ag, a.rg, a.pg, a.ubar = (_p(sk[k]) for k in ("xd", "nd", "ag", "rg", "pg", "ubar"))
-    a.knn, a.bits = _p(knn), _p(bits)
+    if bits.dtype == torch.uint8:
+        if vis_den is None:
+            raise ValueError("soft visibility counts need vis_den (the filters' Kv)")
+        a.knn, a.bits = _p(knn), None
+        a.vis_count, a.vis_den = _p(bits), int(vis_den)
+    else:
+        a.knn, a.bits = _p(knn), _p(bits)
     a.light_L, a.light_A, a.light_w = _p(light["L"]), _p(light["A"]), _p(light["w"])
     for k in range(3):
         a.cam_center[k] = float(cam_center[k])
@@ -231,8 +266,9 @@ def _shade_struct(sk, knn, bits, light, cam_center, color, radiance, cull, statu
     return a
 
 
-def avatar_shade(sk, knn, bits, light, cam_center, out=None, status=None):
-    """(c) Shading (Eq. 2, App. A).  light: dict L [NL,3], A [NL], w [NL,3]."""
+def avatar_shade(sk, knn, bits, light, cam_center, out=None, status=None, vis_den=None):
+    """(c) Shading (Eq. 2, App. A).  light: dict L [NL,3], A [NL], w [NL,3];
+    bits: visibility words, or uint8 soft counts with vis_den."""
     lib = L.load()
     ctx = context()
     dev = sk["xd"].device
@@ -240,7 +276,7 @@ def avatar_shade(sk, knn, bits, light, cam_center, out=None, status=None):
     if out is None:
         out = dict(color=torch.empty(3, G, device=dev), radiance=torch.empty(3, G, device=dev),
                    cull=torch.empty(G, dtype=torch.uint8, device=dev))
-    a = _shade_struct(sk, knn, bits, light, cam_center, out["color"], out["radiance"], out["cull"], status)
+    a = _shade_struct(sk, knn, bits, light, cam_center, out["color"], out["radiance"], out["cull"], status, vis_den)
     L.check(lib.avatar_shade(ctx, C.byref(a), _stream()), "avatar_shade")
     return out
 
@@ -274,10 +310,10 @@ def avatar_shade_multi(sk, knn, bits, light, cam_center, env_L, out=None, cull=N
     return out
 
 
-def avatar_shade_backward(sk, knn, bits, light, cam_center, out, d_color):
+def avatar_shade_backward(sk, knn, bits, light, cam_center, out, d_color, vis_den=None):
     lib = L.load()
     ctx = context()
-    a = _shade_struct(sk, knn, bits, light, cam_center, out["color"], out["radiance"], out["cull"], None)
+    a = _shade_struct(sk, knn, bits, light, cam_center, out["color"], out["radiance"], out["cull"], None, vis_den)
     d_color = d_color.contiguous()
     res = dict(xd=torch.empty_like(sk["xd"]), nd=torch.empty_like(sk["nd"]), ag=torch.empty_like(sk["ag"]),
                rg=torch.empty_like(sk["rg"]), pg=torch.empty_like(sk["pg"]), ubar=torch.empty_like(sk["ubar"]),

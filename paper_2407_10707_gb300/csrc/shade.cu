@@ -150,7 +150,21 @@ __device__ __forceinline__ float lane_vis(const ChunkBits<K> &cb, const GaussIn<
     return vis;
 }
 
+// Soft visibility of light k (lane) from the filtered vertex counts.
 template <int K>
+__device__ __forceinline__ float soft_vis(const uint8_t *__restrict__ vc, int NL, const GaussIn<K> &q, int k,
+                                          float inv_den, float (&c)[K])
+{
+    float vis = 0.f;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        c[j] = (float)__ldg(vc + (size_t)q.nb[j] * NL + k) * inv_den;
+        vis = fmaf(q.ub[j], c[j], vis);
+    }
+    return vis;
+}
+
+template <int K, bool SOFT>
 __global__ void __launch_bounds__(SHADE_THREADS)
 shade_kernel(avatar_shade_args s, ShadeBatch sb)
 {
@@ -193,14 +207,23 @@ shade_kernel(avatar_shade_args s, ShadeBatch sb)
         const float ia0 = q.a[0] * (1.f / AV_PI), ia1 = q.a[1] * (1.f / AV_PI), ia2 = q.a[2] * (1.f / AV_PI);
         float L0 = 0.f, L1 = 0.f, L2 = 0.f;  // this lane's share of L_o
         for (int ch = 0; ch < OW; ++ch) {
-            ChunkBits<K> cb;
-            load_chunk<K>(bits, q, OW, ch, cb);
             const int k = ch * 32 + lane;
-            if (k >= NL || !(cb.any & bit)) continue;
+            float vis;
+            if constexpr (SOFT) {
+                if (k >= NL) continue;
+                float cj[K];
+                vis = soft_vis<K>(s.vis_count, NL, q, k, 1.0f / (float)s.vis_den, cj);
+                if (vis == 0.f) continue;
+            } else {
+                ChunkBits<K> cb;
+                load_chunk<K>(bits, q, OW, ch, cb);
+                if (k >= NL || !(cb.any & bit)) continue;
+                vis = lane_vis<K>(cb, q, bit);
+            }
             float4 w = lw[k];
             float ci = q.n[0] * w.x + q.n[1] * w.y + q.n[2] * w.z;
             if (!(ci > 0.f)) continue;
-            float fw = lane_vis<K>(cb, q, bit) * ci;
+            float fw = vis * ci;
             float4 B = lb[k];
             float dwo = w.x * f.wo[0] + w.y * f.wo[1] + w.z * f.wo[2];
             float fs = 0.f;
@@ -233,7 +256,7 @@ shade_kernel(avatar_shade_args s, ShadeBatch sb)
 }
 
 // ---------------------------------------------------------------- backward
-template <int K>
+template <int K, bool SOFT>
 __global__ void __launch_bounds__(SHADE_THREADS)
 shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr, ShadeBatch sb)
 {
@@ -302,14 +325,24 @@ shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr, ShadeBatch sb)
 #pragma unroll
         for (int j = 0; j < K; ++j) dub[j] = 0.f;
         for (int ch = 0; ch < OW; ++ch) {
-            ChunkBits<K> cb;
-            load_chunk<K>(bits, q, OW, ch, cb);
             const int k = ch * 32 + lane;
-            if (k >= NL || !(cb.any & bit)) continue;
+            float vis;
+            float cj[K];  // per-neighbour visibility of light k (0/1 for bits)
+            if constexpr (SOFT) {
+                if (k >= NL) continue;
+                vis = soft_vis<K>(s.vis_count, NL, q, k, 1.0f / (float)s.vis_den, cj);
+                if (vis == 0.f) continue;
+            } else {
+                ChunkBits<K> cb;
+                load_chunk<K>(bits, q, OW, ch, cb);
+                if (k >= NL || !(cb.any & bit)) continue;
+                vis = lane_vis<K>(cb, q, bit);
+#pragma unroll
+                for (int j = 0; j < K; ++j) cj[j] = (cb.w[j] & bit) ? 1.f : 0.f;
+            }
             float4 w = lw[k];
             float ci = q.n[0] * w.x + q.n[1] * w.y + q.n[2] * w.z;
             if (!(ci > 0.f)) continue;
-            float vis = lane_vis<K>(cb, q, bit);
             float4 B = lb[k];
             float Q = dLo[0] * B.x + dLo[1] * B.y + dLo[2] * B.z;
             float Qa = ia0 * dLo[0] * B.x + ia1 * dLo[1] * B.y + ia2 * dLo[2] * B.z;
@@ -355,8 +388,7 @@ shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr, ShadeBatch sb)
             dci += vis * term;
             float dvis = ci * term;
 #pragma unroll
-            for (int j = 0; j < K; ++j)
-                if (cb.w[j] & bit) dub[j] += dvis;
+            for (int j = 0; j < K; ++j) dub[j] = fmaf(dvis, cj[j], dub[j]);
             dnv0 = fmaf(dci, w.x, dnv0);
             dnv1 = fmaf(dci, w.y, dnv1);
             dnv2 = fmaf(dci, w.z, dnv2);
@@ -414,10 +446,11 @@ shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr, ShadeBatch sb)
 template <int K>
 int launch_shade(const avatar_shade_args &a, const ShadeBatch &sb, int grid, size_t smem, cudaStream_t st)
 {
+    auto kern = a.vis_count ? shade_kernel<K, true> : shade_kernel<K, false>;
     if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(shade_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return AVATAR_ERR_CUDA;
-    shade_kernel<K><<<dim3(grid, sb.V), SHADE_THREADS, smem, st>>>(a, sb);
+    kern<<<dim3(grid, sb.V), SHADE_THREADS, smem, st>>>(a, sb);
     AV_CHECK_LAUNCH();
     return AVATAR_OK;
 }
@@ -426,10 +459,11 @@ template <int K>
 int launch_shade_bwd(const avatar_shade_args &a, const avatar_shade_grads &g, const ShadeBatch &sb, int grid,
                      size_t smem, cudaStream_t st)
 {
-    if (smem > 48 * 1024 && cudaFuncSetAttribute(shade_backward_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem) != cudaSuccess)
+    auto kern = a.vis_count ? shade_backward_kernel<K, true> : shade_backward_kernel<K, false>;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return AVATAR_ERR_CUDA;
-    shade_backward_kernel<K><<<dim3(grid, sb.V), SHADE_THREADS, smem, st>>>(a, g, sb);
+    kern<<<dim3(grid, sb.V), SHADE_THREADS, smem, st>>>(a, g, sb);
     AV_CHECK_LAUNCH();
     return AVATAR_OK;
 }
@@ -438,9 +472,10 @@ int check_shade(const avatar_shade_args *a)
 {
     if (!a || a->G < 0 || a->K < 1 || a->K > 8 || a->NL < 1 || a->NL > 4096 || a->Nv < 1)
         return AVATAR_ERR_INVALID_ARG;
-    if (a->G > 0 && (!a->xd || !a->nd || !a->ag || !a->rg || !a->pg || !a->ubar || !a->knn || !a->bits ||
-                     !a->color))
+    if (a->G > 0 && (!a->xd || !a->nd || !a->ag || !a->rg || !a->pg || !a->ubar || !a->knn ||
+                     (!a->bits && !a->vis_count) || !a->color))
         return AVATAR_ERR_INVALID_ARG;
+    if (a->vis_count && a->vis_den < 1) return AVATAR_ERR_INVALID_ARG;
     if (!a->light_L || !a->light_A || !a->light_w) return AVATAR_ERR_INVALID_ARG;
     return AVATAR_OK;
 }

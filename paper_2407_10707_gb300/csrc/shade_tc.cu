@@ -407,6 +407,7 @@ extern "C" int avatar_shade_multi(avatar_ctx *ctx, const avatar_shade_multi_args
     if (s.G < 0 || s.K < 1 || s.K > 8 || s.Nv < 1 || m->n_env < 1 || m->n_env > TC_MAX_ENV) return AVATAR_ERR_INVALID_ARG;
     if (s.NL < TC_KC || s.NL > TC_MAX_K || s.NL % TC_KC != 0) return AVATAR_ERR_UNSUPPORTED;
     if (!m->env_L || !m->env_color || !s.light_A || !s.light_w) return AVATAR_ERR_INVALID_ARG;
+    if (s.vis_count) return AVATAR_ERR_UNSUPPORTED;  // hard visibility bits only
     if (s.G > 0 && (!s.xd || !s.nd || !s.ag || !s.rg || !s.pg || !s.ubar || !s.knn || !s.bits))
         return AVATAR_ERR_INVALID_ARG;
     if (s.G == 0) return AVATAR_OK;

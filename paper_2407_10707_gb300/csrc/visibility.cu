@@ -16,6 +16,7 @@
 // bits are reproducible bit for bit by any correct implementation.
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "batch_internal.h"
@@ -189,6 +190,65 @@ __device__ __forceinline__ void raster_triangle(uint2 pa, uint2 pb, uint2 pc, in
     }
 }
 
+// Second pass of the paper's visibility: true iff at some pixel the triangle
+// covers its depth (the same coverage and depth as raster_triangle) equals
+// the finished depth map's - the triangle appears in the image.  Stops at
+// the first such pixel.
+template <int CL, bool CULL_BACK>
+__device__ __forceinline__ bool triangle_appears(uint2 pa, uint2 pb, uint2 pc, const int *depth_slab,
+                                                 const VisParams &p, cg::cluster_group &cluster)
+{
+    if (pa.x == OUTSIDE || pb.x == OUTSIDE || pc.x == OUTSIDE) return false;
+    int ax = pa.x & 0xffff, ay = pa.x >> 16, az = (int)pa.y;
+    int bx = pb.x & 0xffff, by = pb.x >> 16, bz = (int)pb.y;
+    int cx = pc.x & 0xffff, cy = pc.x >> 16, cz = (int)pc.y;
+    const int R = p.R;
+    int i0 = max(0, (min(ax, min(bx, cx)) + 7) >> 4), i1 = min(R - 1, (max(ax, max(bx, cx)) - 8) >> 4);
+    int j0 = max(0, (min(ay, min(by, cy)) + 7) >> 4), j1 = min(R - 1, (max(ay, max(by, cy)) - 8) >> 4);
+    if (i0 > i1 || j0 > j1) return false;
+    int area = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
+    if (CULL_BACK) {
+        if (area <= 0) return false;
+    } else {
+        if (area == 0) return false;
+        if (area < 0) {
+            int t;
+            t = bx; bx = cx; cx = t;
+            t = by; by = cy; cy = t;
+            t = bz; bz = cz; cz = t;
+            area = -area;
+        }
+    }
+    const int dzb = bz - az, dzc = cz - az;
+    const bool small = area < (1 << 20) && abs(dzb) < (1 << 10) && abs(dzc) < (1 << 10);
+    for (int j = j0; j <= j1; ++j) {
+        const int py = 16 * j + 8;
+        const int *drow;
+        if (CL == 1) {
+            drow = depth_slab + j * R;
+        } else {
+            int owner = (j * p.inv_rows) >> 20;
+            drow = cluster.map_shared_rank(depth_slab, owner) + (j - owner * p.rows_per_cta) * R;
+        }
+        for (int i = i0; i <= i1; ++i) {
+            const int px = 16 * i + 8;
+            int wa = (cx - bx) * (py - by) - (cy - by) * (px - bx);
+            int wb = (ax - cx) * (py - cy) - (ay - cy) * (px - cx);
+            int wc = (bx - ax) * (py - ay) - (by - ay) * (px - ax);
+            if ((wa | wb | wc) < 0) continue;
+            int dep;
+            if (small) {
+                dep = az + floor_div_i32(wb * dzb + wc * dzc, area);
+            } else {
+                long long num = (long long)wa * az + (long long)wb * bz + (long long)wc * cz;
+                dep = floor_div_small(num, area);
+            }
+            if (dep == drow[i]) return true;
+        }
+    }
+    return false;
+}
+
 // Direction-independent per-chunk vertex range [min, max] of the indices a
 // chunk of VIS_CHUNK triangles references (x > y: a bad index, or no faces).
 __global__ void vis_chunk_ranges_kernel(const int32_t *__restrict__ faces, int F, int Nv, int2 *__restrict__ vr,
@@ -226,7 +286,7 @@ __global__ void vis_chunk_ranges_kernel(const int32_t *__restrict__ faces, int F
     }
 }
 
-template <int CL, bool CULL_BACK>
+template <int CL, bool CULL_BACK, bool BATCH>
 __global__ void __launch_bounds__(VIS_THREADS)
 vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *__restrict__ faces,
                        const int2 *__restrict__ vranges, const float *__restrict__ frames,
@@ -236,8 +296,9 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = CL == 1 ? 0 : (int)cluster.block_rank();
     const int d = blockIdx.y;
-    qv += (size_t)blockIdx.z * p.Nv;  // pose blockIdx.z of a batch
-    dirbits += (size_t)blockIdx.z * p.D * p.NW;
+    // pose blockIdx.z of a batch (its words: row z D + d below); a single pose
+    // keeps qv in the parameter bank instead of a register pair
+    if (BATCH) qv += (size_t)blockIdx.z * p.Nv;
     const int R = p.R;
     const int slab_elems = p.rows_per_cta * R;
     uint2 *vcache = reinterpret_cast<uint2 *>(slab + slab_elems);
@@ -350,7 +411,7 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
             const int w = w0 + u * wstride;
             bool vis = !pr[u].in || dep[u] == EMPTY_DEPTH || pr[u].Z <= dep[u] + p.biasq;
             unsigned word = __ballot_sync(0xffffffffu, vis && qq[u].w != 2);
-            if (lane == 0 && w < p.NW) dirbits[(size_t)d * p.NW + w] = word;
+            if (lane == 0 && w < p.NW) dirbits[((size_t)blockIdx.z * p.D + d) * p.NW + w] = word;
         }
     }
     cluster.sync();  // keep every slab alive until all remote reads are done
@@ -389,11 +450,236 @@ __global__ void vis_transpose_kernel(const uint32_t *__restrict__ dirbits, int N
     }
 }
 
+// ---------------------------------------------------------------------------
+// The paper's own visibility (Sec. 3.2, Eqs. 3-4): triangle-ID images and the
+// median / median / mean vertex filters.
+//
+// vis_tri_kernel: one cluster per direction holds the direction's R x R
+// depth map in its CTAs' shared memory.  Pass A is the depth-map raster;
+// pass B visits the triangles again and marks, in the CTA's shared-memory
+// bitmap, the vertices of every triangle that attains the least depth at a
+// pixel it covers (it appears in the triangle-ID image).  The cluster then
+// ORs the bitmaps (plus the vertices outside the window) into
+// direction-major words.
+template <int CL, bool CULL_BACK>
+__global__ void __launch_bounds__(VIS_THREADS)
+vis_tri_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *__restrict__ faces,
+               const int2 *__restrict__ vranges, const float *__restrict__ frames, uint32_t *__restrict__ dirbits,
+               int32_t *status)
+{
+    extern __shared__ int depth[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = CL == 1 ? 0 : (int)cluster.block_rank();
+    const int d = blockIdx.y;
+    const int R = p.R;
+    const int slab_elems = p.rows_per_cta * R;
+    uint2 *vcache = reinterpret_cast<uint2 *>(depth + slab_elems);
+    unsigned *bitmap = reinterpret_cast<unsigned *>(vcache + VIS_VCAP);  // [NW] vertices marked by this CTA
+
+    for (int i = threadIdx.x; i < slab_elems; i += blockDim.x) depth[i] = EMPTY_DEPTH;
+    for (int i = threadIdx.x; i < p.NW; i += blockDim.x) bitmap[i] = 0u;
+
+    int B[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) B[i] = (int)rintf(__ldg(frames + 9 * d + i) * 8192.0f);
+    bool frame_ok = true;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        long long n2 = (long long)B[3 * r] * B[3 * r] + (long long)B[3 * r + 1] * B[3 * r + 1] +
+                       (long long)B[3 * r + 2] * B[3 * r + 2];
+        if (n2 > 8194LL * 8194LL) frame_ok = false;
+    }
+    if (!frame_ok) {
+        if (threadIdx.x == 0) av_report(status, AVATAR_ERR_INVALID_ARG);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) B[i] = 0;
+    }
+    const int nchunks = (p.F + VIS_CHUNK - 1) / VIS_CHUNK;
+    cluster.sync();
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int chunk = rank; chunk < nchunks; chunk += CL) {
+            const int2 vr = __ldg(vranges + chunk);
+            const int v0 = vr.x, nv = vr.y - vr.x + 1;
+            const bool cached = nv > 0 && nv <= VIS_VCAP;
+            if (cached)
+                for (int i = threadIdx.x; i < nv; i += VIS_THREADS)
+                    vcache[i] = pack_proj(project_vertex(__ldg(qv + v0 + i), B, p));
+            __syncthreads();
+            if (nv > 0) {
+#pragma unroll
+                for (int t = 0; t < VIS_TPT; ++t) {
+                    const int f = chunk * VIS_CHUNK + t * VIS_THREADS + threadIdx.x;
+                    if (f >= p.F) continue;
+                    const int a = __ldg(faces + 3 * f), b = __ldg(faces + 3 * f + 1), c = __ldg(faces + 3 * f + 2);
+                    uint2 pa, pb, pc;
+                    if (cached) {
+                        pa = vcache[a - v0];
+                        pb = vcache[b - v0];
+                        pc = vcache[c - v0];
+                    } else {
+                        pa = pack_proj(project_vertex(__ldg(qv + a), B, p));
+                        pb = pack_proj(project_vertex(__ldg(qv + b), B, p));
+                        pc = pack_proj(project_vertex(__ldg(qv + c), B, p));
+                    }
+                    if (pass == 0) {
+                        raster_triangle<CL, CULL_BACK>(pa, pb, pc, depth, p, cluster);
+                    } else if (triangle_appears<CL, CULL_BACK>(pa, pb, pc, depth, p, cluster)) {
+                        atomicOr(bitmap + (a >> 5), 1u << (a & 31));
+                        atomicOr(bitmap + (b >> 5), 1u << (b & 31));
+                        atomicOr(bitmap + (c >> 5), 1u << (c & 31));
+                    }
+                }
+            }
+            __syncthreads();  // the next chunk overwrites the cache
+        }
+        cluster.sync();  // the depth map is complete before pass B; every bitmap before the OR
+    }
+    // one warp per 32-vertex word: OR of the cluster's bitmaps and the
+    // vertices outside the window (visible, as in the depth-map form)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = VIS_THREADS / 32;
+    for (int w = rank * nwarps + warp; w < p.NW; w += CL * nwarps) {
+        const int v = w * 32 + lane;
+        const bool outside = v < p.Nv && !project_vertex(__ldg(qv + v), B, p).in;
+        unsigned word = __ballot_sync(0xffffffffu, outside);
+        if (lane < CL) {
+            const unsigned *src = CL == 1 ? bitmap : cluster.map_shared_rank(bitmap, lane);
+            word |= src[w];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) word |= __shfl_xor_sync(0xffffffffu, word, o);
+        if (lane == 0) dirbits[(size_t)d * p.NW + w] = word;
+    }
+    cluster.sync();  // keep every bitmap alive until all remote reads are done
+}
+
+// Bit-sliced count of Kv neighbour words: planes c[0..5] hold, per bit
+// position, the count of ones in binary (Kv <= 63).
+__device__ __forceinline__ void count_neighbours(const uint32_t *__restrict__ in, const int32_t *__restrict__ knn_v,
+                                                 int Nv, int OW, int Kv, int v, int w, unsigned (&c)[6],
+                                                 int32_t *status)
+{
+#pragma unroll
+    for (int b = 0; b < 6; ++b) c[b] = 0u;
+    for (int j = 0; j < Kv; ++j) {
+        const int u = __ldg(knn_v + (size_t)j * Nv + v);
+        if ((unsigned)u >= (unsigned)Nv) {
+            av_report(status, AVATAR_ERR_INDEX);
+            continue;
+        }
+        unsigned carry = __ldg(in + (size_t)u * OW + w);
+#pragma unroll
+        for (int b = 0; b < 6; ++b) {
+            const unsigned t = c[b] & carry;
+            c[b] ^= carry;
+            carry = t;
+        }
+    }
+}
+
+// median filter: bit = (count >= (Kv + 1) / 2), per vertex and 32 directions
+__global__ void __launch_bounds__(256)
+vis_median_kernel(const uint32_t *__restrict__ in, const int32_t *__restrict__ knn_v, int Nv, int OW, int Kv,
+                  uint32_t *__restrict__ out, int32_t *status)
+{
+    const int m = (Kv + 1) / 2;
+    const long total = (long)Nv * OW;
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int v = (int)(t / OW), w = (int)(t % OW);
+        unsigned c[6];
+        count_neighbours(in, knn_v, Nv, OW, Kv, v, w, c, status);
+        // count >= m, bit-sliced from the most significant plane down
+        unsigned gt = 0u, eq = ~0u;
+#pragma unroll
+        for (int b = 5; b >= 0; --b) {
+            if ((m >> b) & 1) {
+                eq &= c[b];
+            } else {
+                gt |= eq & c[b];
+                eq &= ~c[b];
+            }
+        }
+        out[(size_t)v * OW + w] = gt | eq;
+    }
+}
+
+// mean filter: count in 0..Kv per vertex and direction, written in light
+// order (light k takes direction dmap[k]) or direction order (dmap NULL)
+__global__ void __launch_bounds__(256)
+vis_mean_kernel(const uint32_t *__restrict__ in, const int32_t *__restrict__ knn_v, int Nv, int OW, int Kv,
+                uint8_t *__restrict__ dir_count, int32_t *status)
+{
+    const long total = (long)Nv * OW;
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int v = (int)(t / OW), w = (int)(t % OW);
+        unsigned c[6];
+        count_neighbours(in, knn_v, Nv, OW, Kv, v, w, c, status);
+        uint32_t packed[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            uint32_t word = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int bit = 4 * q + k;
+                unsigned n = 0;
+#pragma unroll
+                for (int b = 0; b < 6; ++b) n |= ((c[b] >> bit) & 1u) << b;
+                word |= n << (8 * k);
+            }
+            packed[q] = word;
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(dir_count + (size_t)v * OW * 32 + (size_t)w * 32);
+        dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+vis_light_order_kernel(const uint8_t *__restrict__ dir_count, int Nv, int D, int NL, const int32_t *__restrict__ dmap,
+                       uint8_t *__restrict__ out, int32_t *status)
+{
+    const long total = (long)Nv * NL;
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int v = (int)(t / NL), k = (int)(t % NL);
+        const int d = __ldg(dmap + k);
+        uint8_t c = 0;
+        if ((unsigned)d >= (unsigned)D) av_report(status, AVATAR_ERR_INDEX);
+        else c = dir_count[(size_t)v * D + d];
+        out[t] = c;
+    }
+}
+
+template <int CL, bool CULL_BACK>
+int launch_tri(const VisParams &p, const int4 *qv, const int32_t *faces, const int2 *vranges, const float *frames,
+               uint32_t *dirbits, int32_t *status, size_t smem, cudaStream_t st)
+{
+    auto kern = vis_tri_kernel<CL, CULL_BACK>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return AVATAR_ERR_CUDA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL, p.D, 1);
+    cfg.blockDim = dim3(VIS_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, kern, p, qv, faces, vranges, frames, dirbits, status) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return AVATAR_ERR_CUDA;
+    }
+    return AVATAR_OK;
+}
+
 template <int CL, bool CULL_BACK>
 int launch_raster(const VisParams &p, const int4 *qv, const int32_t *faces, const int2 *vranges,
                   const float *frames, uint32_t *dirbits, int32_t *status, size_t smem, cudaStream_t st)
 {
-    auto kern = vis_raster_test_kernel<CL, CULL_BACK>;
+    auto kern = p.B > 1 ? vis_raster_test_kernel<CL, CULL_BACK, true> : vis_raster_test_kernel<CL, CULL_BACK, false>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return AVATAR_ERR_CUDA;
     cudaLaunchConfig_t cfg = {};
@@ -552,6 +838,155 @@ extern "C" int avatar_visibility(avatar_ctx *ctx, const avatar_vis_args *a, void
                                  avatar_stream_t stream)
 {
     return vis_run(ctx, a, 1, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// The paper's visibility with its filters (header: avatar_visibility_soft).
+namespace {
+
+struct VisSoftWs {
+    int4 *qv;
+    uint32_t *dirbits;
+    int2 *vranges;
+    uint32_t *vm, *m1, *m2;  // [Nv][D/32] vertex-major, direction order
+    uint8_t *dir_count;      // [Nv][D]
+};
+
+int check_vis_soft(const avatar_vis_soft_args *a)
+{
+    if (!a) return AVATAR_ERR_INVALID_ARG;
+    const avatar_vis_args &b = a->base;
+    if (b.Nv < 1 || b.F < 0 || b.D < 32 || b.D % 32 != 0 || b.D > 4096) return AVATAR_ERR_INVALID_ARG;
+    if (b.R < 8 || b.R > 512 || b.R % 8 != 0) return AVATAR_ERR_INVALID_ARG;
+    if (a->Kv < 1 || a->Kv > 63 || a->Kv % 2 == 0) return AVATAR_ERR_INVALID_ARG;
+    if (b.dmap && b.NL < 1) return AVATAR_ERR_INVALID_ARG;
+    return AVATAR_OK;
+}
+
+size_t vis_soft_layout(const avatar_vis_soft_args *a, void *base, size_t cap, VisSoftWs *out)
+{
+    WsCarver c(base, cap);
+    const avatar_vis_args &b = a->base;
+    const int NW = (b.Nv + 31) / 32, OW = b.D / 32;
+    VisSoftWs w;
+    w.qv = c.take<int4>((size_t)b.Nv);
+    w.dirbits = c.take<uint32_t>((size_t)b.D * NW);
+    w.vranges = c.take<int2>((size_t)(b.F + VIS_CHUNK - 1) / VIS_CHUNK + 1);
+    w.vm = c.take<uint32_t>((size_t)b.Nv * OW);
+    w.m1 = c.take<uint32_t>((size_t)b.Nv * OW);
+    w.m2 = c.take<uint32_t>((size_t)b.Nv * OW);
+    w.dir_count = c.take<uint8_t>((size_t)b.Nv * b.D);
+    if (out) *out = w;
+    return c.off;
+}
+
+// Shared memory of one CTA of the triangle-ID kernel with CL CTAs per direction.
+size_t tri_smem(int R, int CL, int Nv)
+{
+    return (size_t)(R / CL) * R * sizeof(int) + (size_t)VIS_VCAP * sizeof(uint2) +
+           (size_t)((Nv + 31) / 32) * sizeof(unsigned);
+}
+
+// CTAs per direction: as many as the depth-map form uses (32 KB of map per
+// CTA), more only if the map share and the bitmap would not fit one SM
+int tri_cluster_size(int R, int Nv, int smem_cap)
+{
+    for (int cl = cluster_size_for(R); cl <= 8; cl <<= 1)
+        if (R % cl == 0 && tri_smem(R, cl, Nv) <= (size_t)smem_cap) return cl;
+    return 0;
+}
+
+}  // namespace
+
+extern "C" size_t avatar_visibility_soft_workspace_size(const avatar_vis_soft_args *a)
+{
+    if (check_vis_soft(a) != AVATAR_OK) return 0;
+    return vis_soft_layout(a, nullptr, 0, nullptr);
+}
+
+extern "C" int avatar_visibility_soft(avatar_ctx *ctx, const avatar_vis_soft_args *a, void *ws, size_t ws_bytes,
+                                      avatar_stream_t stream)
+{
+    if (!ctx) return AVATAR_ERR_INVALID_ARG;
+    AV_TRY(check_vis_soft(a));
+    const avatar_vis_args &b = a->base;
+    if (!b.xp || (b.F > 0 && !b.faces) || !b.frames || !a->knn_v || !a->vis_count) return AVATAR_ERR_INVALID_ARG;
+    // direction-ordered counts are written 16 bytes at a time
+    if (!b.dmap && (((uintptr_t)a->vis_count) & 15)) return AVATAR_ERR_INVALID_ARG;
+    if (!ws || (((uintptr_t)ws) & 255)) return AVATAR_ERR_WORKSPACE;
+    VisSoftWs w;
+    if (vis_soft_layout(a, ws, ws_bytes, &w) > ws_bytes) return AVATAR_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    long long H = llrint((double)b.half_extent * 67108864.0);
+    if (!(H > 16LL * b.R && H <= (1LL << 30))) return AVATAR_ERR_INVALID_ARG;
+    long long M = ((long long)b.R << 35) / H;
+    if (M <= 0 || M >= (1LL << 31)) return AVATAR_ERR_INVALID_ARG;
+    int qc[3];
+    for (int i = 0; i < 3; ++i) {
+        long long q = llrint((double)b.center[i] * 8192.0);
+        if (q < -(1LL << 30) || q > (1LL << 30)) return AVATAR_ERR_INVALID_ARG;
+        qc[i] = (int)q;
+    }
+    VisParams p;
+    p.B = 1;
+    p.Nv = b.Nv;
+    p.F = b.F;
+    p.D = b.D;
+    p.R = b.R;
+    p.NW = (b.Nv + 31) / 32;
+    p.H = (int)H;
+    p.M = (int)M;
+    p.biasq = 0;
+    const int CL = tri_cluster_size(b.R, b.Nv, ctx->max_smem_optin);
+    if (CL == 0) return AVATAR_ERR_UNSUPPORTED;
+    p.rows_per_cta = b.R / CL;
+    p.inv_rows = ((1 << 20) + p.rows_per_cta - 1) / p.rows_per_cta;
+    const size_t smem = tri_smem(b.R, CL, b.Nv);
+
+    int qgrid = (int)((b.Nv + 255) / 256);
+    if (qgrid > ctx->sm_count * 8) qgrid = ctx->sm_count * 8;
+    vis_quantize_kernel<<<dim3(qgrid, 1), 256, 0, st>>>(b.xp, b.Nv, qc[0], qc[1], qc[2], w.qv, b.status);
+    AV_CHECK_LAUNCH();
+    const int nchunks = (b.F + VIS_CHUNK - 1) / VIS_CHUNK;
+    if (nchunks > 0) {
+        vis_chunk_ranges_kernel<<<nchunks, 256, 0, st>>>(b.faces, b.F, b.Nv, w.vranges, b.status);
+        AV_CHECK_LAUNCH();
+    }
+    int rc;
+    const bool cb = b.cull_back != 0;
+#define AV_TRI(CLV)                                                                                     \
+    (cb ? launch_tri<CLV, true>(p, w.qv, b.faces, w.vranges, b.frames, w.dirbits, b.status, smem, st)  \
+        : launch_tri<CLV, false>(p, w.qv, b.faces, w.vranges, b.frames, w.dirbits, b.status, smem, st))
+    switch (CL) {
+        case 1: rc = AV_TRI(1); break;
+        case 2: rc = AV_TRI(2); break;
+        case 4: rc = AV_TRI(4); break;
+        default: rc = AV_TRI(8); break;
+    }
+#undef AV_TRI
+    if (rc != AVATAR_OK) return rc;
+    // V vertex-major in direction order, then median, median, mean
+    const int OW = b.D / 32;
+    uint32_t *vm = b.bits ? b.bits : w.vm;
+    long warps = (long)p.NW * OW;
+    long tgrid = (warps * 32 + 255) / 256;
+    if (tgrid > (long)ctx->sm_count * 16) tgrid = (long)ctx->sm_count * 16;
+    vis_transpose_kernel<<<dim3((int)tgrid, 1), 256, 0, st>>>(w.dirbits, p.NW, b.Nv, b.D, b.D, OW, nullptr, vm,
+                                                               b.status);
+    long items = (long)b.Nv * OW;
+    int fgrid = (int)std::min<long>((items + 255) / 256, (long)ctx->sm_count * 16);
+    vis_median_kernel<<<fgrid, 256, 0, st>>>(vm, a->knn_v, b.Nv, OW, a->Kv, w.m1, b.status);
+    vis_median_kernel<<<fgrid, 256, 0, st>>>(w.m1, a->knn_v, b.Nv, OW, a->Kv, w.m2, b.status);
+    uint8_t *dc = b.dmap ? w.dir_count : a->vis_count;
+    vis_mean_kernel<<<fgrid, 256, 0, st>>>(w.m2, a->knn_v, b.Nv, OW, a->Kv, dc, b.status);
+    AV_CHECK_LAUNCH();
+    if (b.dmap) {
+        long n = (long)b.Nv * b.NL;
+        int lgrid = (int)std::min<long>((n + 255) / 256, (long)ctx->sm_count * 16);
+        vis_light_order_kernel<<<lgrid, 256, 0, st>>>(w.dir_count, b.Nv, b.D, b.NL, b.dmap, a->vis_count, b.status);
+        AV_CHECK_LAUNCH();
+    }
+    return AVATAR_OK;
 }
 
 // ---------------------------------------------------------------------------

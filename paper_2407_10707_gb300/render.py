@@ -44,11 +44,21 @@ class Renderer:
     sums on the tensor cores (BF16 weights, FP32 accumulation; needs a light
     count that is a multiple of 64)."""
 
-    def __init__(self, st, tile=16, pair_capacity=None, vis_cull_back=True, shade_tc=False):
+    def __init__(self, st, tile=16, pair_capacity=None, vis_cull_back=True, shade_tc=False, visibility="depth",
+                 knn_v=None):
         self.st = st
         self.vis_cull_back = vis_cull_back
         self.shade_tc = shade_tc
         self.tc_ws = None
+        # visibility: "depth" = depth maps + per-vertex depth test (exact bits);
+        # "paper" = the paper's triangle-ID images + median/median/mean filters over
+        # the Kv nearest vertices knn_v ([Kv, Nv] int32, soft visibility)
+        if visibility not in ("depth", "paper"):
+            raise ValueError("visibility must be 'depth' or 'paper'")
+        if visibility == "paper" and (knn_v is None or shade_tc):
+            raise ValueError("the paper's visibility needs knn_v and the CUDA-core shading")
+        self.visibility_mode = visibility
+        self.knn_v = knn_v
         t = st["avatar"]
         dev = t["xg"].device
         self.device = dev
@@ -60,6 +70,7 @@ class Renderer:
         Nv = t["xv"].shape[1]
         NL = st["light"]["L"].shape[0]
         self.bits = torch.empty(Nv, (NL + 31) // 32, dtype=torch.int32, device=dev)
+        self.vis_count = torch.empty(Nv, NL, dtype=torch.uint8, device=dev) if visibility == "paper" else None
         self.vis_ws = None
         self.sh = dict(color=torch.empty(3, G, device=dev), radiance=torch.empty(3, G, device=dev),
                        cull=torch.empty(G, dtype=torch.uint8, device=dev))
@@ -75,11 +86,28 @@ class Renderer:
 
     def visibility(self):
         st = self.st
+        if self.visibility_mode == "paper":
+            if self.vis_ws is None:
+                self.vis_ws = self._vis_soft_ws()
+            api.avatar_visibility_soft(self.sk["xp"], st["avatar"]["faces"], st["frames"], st["center"], st["half"],
+                                       st["depth_res"], self.knn_v, dmap=st["dmap"], vis_count=self.vis_count,
+                                       ws=self.vis_ws, status=self.status, cull_back=self.vis_cull_back)
+            return
         if self.vis_ws is None:
             self.vis_ws = self._vis_ws()
         api.avatar_visibility(self.sk["xp"], st["avatar"]["faces"], st["frames"], st["center"], st["half"],
                               st["bias"], st["depth_res"], dmap=st["dmap"], bits=self.bits, ws=self.vis_ws,
                               status=self.status, cull_back=self.vis_cull_back)
+
+    def _vis_soft_ws(self):
+        import ctypes as C
+        from . import _lib as L
+        st = self.st
+        a = L.VisSoftArgs()
+        a.base = api._vis_struct(self.sk["xp"], st["avatar"]["faces"], st["frames"], st["center"], st["half"], 0.0,
+                                 st["depth_res"], st["dmap"], None, None)
+        a.Kv = self.knn_v.shape[0]
+        return api.workspace(L.load().avatar_visibility_soft_workspace_size(C.byref(a)), self.device)
 
     def _vis_ws(self):
         import ctypes as C
@@ -98,6 +126,10 @@ class Renderer:
             api.avatar_shade_multi(self.sk, st["avatar"]["knn"], self.bits, st["light"], st["cam_center"], L1,
                                    out=self.sh["color"].unsqueeze(0), cull=self.sh["cull"], status=self.status,
                                    ws=self.tc_ws, radiance=self.sh["radiance"])
+            return
+        if self.visibility_mode == "paper":
+            api.avatar_shade(self.sk, st["avatar"]["knn"], self.vis_count, st["light"], st["cam_center"], out=self.sh,
+                             status=self.status, vis_den=self.knn_v.shape[0])
             return
         api.avatar_shade(self.sk, st["avatar"]["knn"], self.bits, st["light"], st["cam_center"], out=self.sh,
                          status=self.status)
@@ -146,9 +178,10 @@ class Renderer:
 class TrainStep(Renderer):
     """Forward frame + L1 loss + backward through every stage."""
 
-    def __init__(self, st, target, tile=16, pair_capacity=None, vis_cull_back=True, shade_tc=False):
+    def __init__(self, st, target, tile=16, pair_capacity=None, vis_cull_back=True, shade_tc=False,
+                 visibility="depth", knn_v=None):
         self.target = target
-        super().__init__(st, tile, pair_capacity, vis_cull_back, shade_tc)
+        super().__init__(st, tile, pair_capacity, vis_cull_back, shade_tc, visibility, knn_v)
         t = st["avatar"]
         self.loss = torch.empty(1, device=self.device)
         self.d_img = torch.empty_like(self.sb.image)
@@ -187,8 +220,12 @@ class TrainStep(Renderer):
         L.check(lib.avatar_splat_backward(ctx, C.byref(a), C.byref(gs), api._p(self.sb.ws), self.sb.ws.numel(), s),
                 "avatar_splat_backward")
         # shade adjoint
-        sa = api._shade_struct(self.sk, t["knn"], self.bits, st["light"], st["cam_center"], self.sh["color"],
-                               self.sh["radiance"], self.sh["cull"], None)
+        if self.visibility_mode == "paper":
+            sa = api._shade_struct(self.sk, t["knn"], self.vis_count, st["light"], st["cam_center"], self.sh["color"],
+                                   self.sh["radiance"], self.sh["cull"], None, vis_den=self.knn_v.shape[0])
+        else:
+            sa = api._shade_struct(self.sk, t["knn"], self.bits, st["light"], st["cam_center"], self.sh["color"],
+                                   self.sh["radiance"], self.sh["cull"], None)
         gh = L.ShadeGrads()
         gh.d_color = api._p(self.g_splat["color"])
         gh.d_xd, gh.d_nd, gh.d_ag, gh.d_rg, gh.d_pg, gh.d_ubar, gh.d_light_L = (

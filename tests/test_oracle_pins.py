@@ -702,17 +702,20 @@ def test_tri_visibility_parallel_quads_and_ownership():
     assert np.all((wx > 0.5 - 2 * half / R) | (np.abs(wy) > 0.5 - 2 * half / R))
 
 
-def test_tri_visibility_ties_go_to_the_lower_triangle_index():
-    # two coincident triangles with distinct vertices: the same depth at every
-    # pixel, so the lower index owns them all and only its vertices are visible
+def test_tri_visibility_tied_triangles_all_appear():
+    # two coincident triangles with distinct vertices lie at the same least
+    # depth at every pixel: both appear, so all six vertices are visible; a
+    # copy moved behind them appears nowhere
     base = np.array([[0.0, 0, 0], [0.4, 0, 0], [0, 0.4, 0]])
-    xp = np.concatenate([base, base])
-    faces = np.array([[3, 4, 5], [0, 1, 2]], np.int32)
+    behind = base - np.array([0, 0, 0.05])
+    xp = np.concatenate([base, base, behind])
+    faces = np.array([[3, 4, 5], [0, 1, 2], [6, 7, 8]], np.int32)
     dirs = np.zeros((32, 3))
     dirs[:, 2] = 1.0
-    bits = O.visibility_tri(xp, faces, _frames_for(dirs), [0.1, 0.1, 0], 1.0, 64)[:, 0]
-    assert np.all(bits[3:] == 0xFFFFFFFF)
-    assert np.all(bits[:3] == 0)
+    bits, tri = O.visibility_tri(xp, faces, _frames_for(dirs), [0.1, 0.1, 0], 1.0, 64, want_tri=True)
+    assert np.all(bits[:6, 0] == 0xFFFFFFFF)
+    assert np.all(bits[6:, 0] == 0)
+    assert set(np.unique(tri[0])) == {-1, 0}     # the reported owner is the least tied index
 
 
 def test_tri_visibility_convex_sphere_hemisphere():
@@ -722,9 +725,11 @@ def test_tri_visibility_convex_sphere_hemisphere():
     vb = np.unpackbits(bits.view(np.uint8), bitorder="little").reshape(len(v), -1)[:, :128]
     cosines = n @ dirs.T
     # front-facing triangles of a convex body are never hidden; a vertex whose
-    # triangles all face away owns nothing
+    # triangles all face away appears nowhere - except that a back triangle
+    # reaching the silhouette may tie the front surface's integer depth at a
+    # grazing pixel, so the back-side margin is wider than the front one
     assert np.all(vb[cosines >= 0.35] == 1)
-    assert np.all(vb[cosines <= -0.35] == 0)
+    assert np.all(vb[cosines <= -0.5] == 0)
 
 
 def test_vis_filters_match_numpy_median_and_mean():
