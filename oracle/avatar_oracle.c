@@ -16,6 +16,7 @@
  *   orc_fk          Sec. 3.1 (forward kinematics feeding LBS; SMPL-style tree)
  *   orc_skin        Sec. 3.1, Eq. 1 (attribute interpolation), LBS of position,
  *                   normal and covariance ("rotated accordingly")
+ *   orc_knn         Sec. 3.1 / 3.2: the K nearest vertices S_g, S_v (brute force)
  *   orc_visibility_tri, orc_vis_filter
  *                   Sec. 3.2 in the paper's own form: triangle-ID images and
  *                   the median / median / mean vertex filters (Eqs. 3-4)
@@ -508,6 +509,49 @@ int orc_visibility_tri(int Nv, int F, int D, int R, const double *xp, const int 
     }
     free(q);
     return err ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* K nearest neighbours (Sec. 3.1: S_g, the K_g nearest vertices of a    */
+/* Gaussian; Sec. 3.2: S_v, the K_v nearest vertices of a vertex), by    */
+/* brute force: every query point against every reference point,        */
+/* ordered by (squared distance, reference index) ascending.  The       */
+/* squared distance of FP32 coordinates is taken in FP64 in a fixed     */
+/* order, d2 = (d0 d0 + d1 d1) + d2 d2, every operation rounded to      */
+/* nearest (no contraction): a fully specified value, so any code that  */
+/* evaluates the same expression reaches the same order.               */
+/* x [N][3], ref [M][3] (FP32 values held in doubles); knn [N][K].      */
+/* ------------------------------------------------------------------ */
+int orc_knn(int N, int M, int K, const double *x, const double *ref, int *knn, double *dist2)
+{
+    if (N < 0 || M < 1 || K < 1 || K > M) return -1;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int i = 0; i < N; ++i) {
+        double *bd = (double *)malloc(sizeof(double) * (size_t)K);
+        int *bi = (int *)malloc(sizeof(int) * (size_t)K);
+        int n = 0;
+        for (int j = 0; j < M; ++j) {
+            double d0 = x[3 * i] - ref[3 * j], d1 = x[3 * i + 1] - ref[3 * j + 1], d2 = x[3 * i + 2] - ref[3 * j + 2];
+            double d = d0 * d0 + d1 * d1 + d2 * d2;
+            /* insert (d, j) into the sorted list of the K best so far */
+            if (n == K && !(d < bd[K - 1] || (d == bd[K - 1] && j < bi[K - 1]))) continue;
+            int pos = n < K ? n++ : K - 1;
+            while (pos > 0 && (d < bd[pos - 1] || (d == bd[pos - 1] && j < bi[pos - 1]))) {
+                bd[pos] = bd[pos - 1];
+                bi[pos] = bi[pos - 1];
+                --pos;
+            }
+            bd[pos] = d;
+            bi[pos] = j;
+        }
+        for (int k = 0; k < K; ++k) {
+            knn[(size_t)i * K + k] = bi[k];
+            if (dist2) dist2[(size_t)i * K + k] = bd[k];
+        }
+        free(bd);
+        free(bi);
+    }
+    return 0;
 }
 
 /* ------------------------------------------------------------------ */

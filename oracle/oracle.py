@@ -37,6 +37,7 @@ def lib():
         _lib.orc_visibility.restype = ctypes.c_int
         _lib.orc_visibility_tri.restype = ctypes.c_int
         _lib.orc_vis_filter.restype = ctypes.c_int
+        _lib.orc_knn.restype = ctypes.c_int
         _lib.orc_set_threads.restype = ctypes.c_int
     return _lib
 
@@ -97,6 +98,21 @@ def visibility(xp, faces, frames, center, half_extent, bias, depth_res, want_dep
     if rc != 0:
         raise ValueError("oracle visibility: argument outside the supported range")
     return (bits, depth) if want_depth else bits
+
+
+def knn(x, ref, k, want_dist=False):
+    """Indices [N, k] of the k nearest reference points of every query point,
+    ascending (squared distance, index); x, ref are rounded to FP32 first
+    (the values an FP32 stage holds), distances exact in FP64."""
+    x = _d(np.asarray(x, np.float32))
+    ref = _d(np.asarray(ref, np.float32))
+    N, M = x.shape[0], ref.shape[0]
+    out = np.zeros((N, k), np.int32)
+    d2 = np.zeros((N, k)) if want_dist else None
+    rc = lib().orc_knn(ctypes.c_int(N), ctypes.c_int(M), ctypes.c_int(k), _p(x), _p(ref), _p(out), _p(d2))
+    if rc != 0:
+        raise ValueError("oracle knn: bad sizes")
+    return (out, d2) if want_dist else out
 
 
 def visibility_tri(xp, faces, frames, center, half_extent, depth_res, cull_back=False, want_tri=False):

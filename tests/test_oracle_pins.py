@@ -781,3 +781,39 @@ def test_soft_shading_reduces_to_bits_for_saturated_counts():
     # sums of lit, unculled Gaussians' radiance before gamma
     _, r_half, _ = O.shade_soft(*args, V * 10, 20, *light)
     np.testing.assert_allclose(r_half, 0.5 * r_bits, rtol=1e-12, atol=1e-14)
+
+
+# ---------------------------------------------------------------- nearest neighbours
+def test_knn_matches_scipy_and_breaks_ties_by_index():
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(9)
+    ref = rng.normal(size=(400, 3)).astype(np.float32)
+    x = rng.normal(size=(300, 3)).astype(np.float32)
+    idx, d2 = O.knn(x, ref, 7, want_dist=True)
+    dd, ii = cKDTree(ref.astype(np.float64)).query(x.astype(np.float64), k=7)
+    np.testing.assert_allclose(np.sqrt(d2), dd, rtol=1e-12)          # the same distances as a k-d tree
+    assert np.mean(idx == ii) > 0.999                                 # and the same points (no ties here)
+    # exact ties (a lattice) go to the lower index; a point's own copy is first
+    g = np.stack(np.meshgrid(np.arange(4), np.arange(4), np.arange(4), indexing="ij"), -1).reshape(-1, 3)
+    q = np.array([[1.5, 1.5, 1.5]], np.float32)                       # 8 lattice points at equal distance
+    k8 = O.knn(q, g, 8)[0]
+    assert list(k8) == sorted(k8)
+    assert np.allclose(np.linalg.norm(g[k8] - q, axis=1), np.sqrt(0.75))
+    self_k = O.knn(g, g, 1)[:, 0]
+    assert np.array_equal(self_k, np.arange(len(g)))
+
+
+def test_knn_distances_follow_the_fp64_definition():
+    # the squared distance is the FP64 value of (d0 d0 + d1 d1) + d2 d2 of the
+    # FP32 coordinates: within 2 FP64 ulps of the exact rational value
+    from fractions import Fraction
+    rng = np.random.default_rng(10)
+    ref = rng.uniform(-1, 1, size=(50, 3)).astype(np.float32)
+    x = rng.uniform(-1, 1, size=(20, 3)).astype(np.float32)
+    idx, d2 = O.knn(x, ref, 3, want_dist=True)
+    for i in range(len(x)):
+        for k in range(3):
+            ex = sum((Fraction(float(x[i, c])) - Fraction(float(ref[idx[i, k], c]))) ** 2 for c in range(3))
+            assert abs(Fraction(d2[i, k]) - ex) <= 2 * 2.0 ** -52 * ex
+            dd = (x[i].astype(np.float64) - ref[idx[i, k]].astype(np.float64))
+            assert d2[i, k] == (dd[0] * dd[0] + dd[1] * dd[1]) + dd[2] * dd[2]
