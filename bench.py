@@ -416,10 +416,36 @@ def forms(r, st, sc, args, dev, flush, fwd_ms, train_ms, want):
         out["precision_bf16_tc"] = _form_precision(r, st, sc, args, dev, flush, fwd_ms, train_ms, reps)
     if "relight" in want:
         out["relight_tc"] = _form_relight(r, st, dev, flush, reps)
+    if "knn" in want:
+        out["knn_rebind"] = _form_knn(r, st, sc, args, dev, flush, reps, fwd_ms)
     if "paper_vis" in want:
         out["visibility_paper"] = _form_paper_vis(r, st, sc, args, dev, flush, reps)
     if "batch" in want:
         out["batch_c4"] = _form_batch(args, dev, reps)
+    return out
+
+
+def _form_knn(r, st, sc, args, dev, flush, reps, fwd_ms):
+    """GPU nearest neighbours: Eq. 1's S_g (K_g nearest vertices of each
+    Gaussian) and the filters' S_v (19 nearest vertices of each vertex), and
+    the frame that rebinds S_g before skinning."""
+    from paper_2407_10707_gb300 import api, render
+    t = st["avatar"]
+    out = {}
+    for name, xq, k in (("gaussians_k3_us", t["xg"], 3), ("gaussians_k4_us", t["xg"], 4),
+                        ("vertices_k19_us", t["xv"], 19)):
+        buf = api.avatar_knn(xq, t["xv"], k)
+        ws = api.workspace(1 << 26, dev)
+        out[name] = round(_time_graph(_graph_of(lambda: api.avatar_knn(xq, t["xv"], k, out=buf, ws=ws)), reps,
+                                      flush) * 1000.0, 1)
+    rb = render.Renderer(st, tile=args.tile, rebind=True)
+    rb.check()
+    frame_ms = _time_graph(_graph_of(rb.forward), reps, flush)
+    out.update({"what": "exact K nearest neighbours on the device (uniform grid, FP64 distances of a fixed "
+                        "operation order); the rebinding frame recomputes S_g every frame",
+                "rebinding_frames_per_s": round(1000.0 / frame_ms, 3),
+                "frames_per_s_without": round(1000.0 / fwd_ms, 3),
+                "paper_knn_ms_per_frame": "0.93 (Tab. 4, other hardware: context only)"})
     return out
 
 
@@ -660,7 +686,7 @@ def main():
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the precision / relighting / batching forms")
-    ap.add_argument("--forms", default="precision,relight,paper_vis,batch", help="comma list of forms to measure")
+    ap.add_argument("--forms", default="precision,relight,knn,paper_vis,batch", help="comma list of forms to measure")
     ap.add_argument("--batch-poses", type=int, default=32, help="poses of the batch form (4 cameras each)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--workload", default=WORKLOAD, help="named synthetic configuration (profiling uses smaller ones)")

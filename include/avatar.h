@@ -172,6 +172,33 @@ int avatar_skin_backward(avatar_ctx *ctx, const avatar_skin_args *a, const avata
                          const void *fwd_ws, void *ws, size_t ws_bytes, avatar_stream_t stream);
 
 /* ------------------------------------------------------------------ */
+/* Nearest neighbours - the sets S_g of Eq. 1 (the K_g nearest mesh     */
+/* vertices of each Gaussian, Sec. 3.1) and S_v of the visibility        */
+/* filters (Sec. 3.2), recomputed on the device when the canonical      */
+/* positions change (rebinding).                                        */
+/*                                                                      */
+/* knn[k][i] = the index of the k-th nearest reference point of query   */
+/* point i, ascending (squared distance, index), where the squared      */
+/* distance is the FP64 value of (d0 d0 + d1 d1) + d2 d2 of the FP32     */
+/* coordinates, every operation rounded to nearest: the result is that  */
+/* definition's exactly.  A uniform grid over the reference points and  */
+/* one thread per query point searching shells of cells.                */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int N;                 /* query points (>= 0) */
+    int M;                 /* reference points (>= K) */
+    int K;                 /* neighbours, 1..32 */
+    const float *x;        /* [3][N] query points */
+    const float *ref;      /* [3][M] reference points */
+    int32_t *knn;          /* [K][N] output indices */
+    float *dist2;          /* [K][N] optional output: the squared distances (rounded to FP32) */
+    int32_t *status;       /* optional device status word */
+} avatar_knn_args;
+
+size_t avatar_knn_workspace_size(const avatar_knn_args *a);
+int avatar_knn(avatar_ctx *ctx, const avatar_knn_args *a, void *ws, size_t ws_bytes, avatar_stream_t stream);
+
+/* ------------------------------------------------------------------ */
 /* (b) Visibility - Sec. 3.2, depth-map (shadow-mapping) form.          */
 /*                                                                      */
 /* Exact integer rules (any correct implementation gives the same bits):*/

@@ -55,6 +55,10 @@ class VisArgs(C.Structure):
                 ("NL", I32), ("dmap", P), ("bits", P), ("status", P), ("cull_back", I32)]
 
 
+class KnnArgs(C.Structure):
+    _fields_ = [("N", I32), ("M", I32), ("K", I32), ("x", P), ("ref", P), ("knn", P), ("dist2", P), ("status", P)]
+
+
 class VisSoftArgs(C.Structure):
     _fields_ = [("base", VisArgs), ("Kv", I32), ("knn_v", P), ("vis_count", P)]
 
@@ -131,6 +135,8 @@ _SIGNATURES = [
     ("avatar_visibility_static_scratch", [P, C.POINTER(VisArgs), P], I32),
     ("avatar_shade", [P, C.POINTER(ShadeArgs), P], I32),
     ("avatar_shade_backward", [P, C.POINTER(ShadeArgs), C.POINTER(ShadeGrads), P], I32),
+    ("avatar_knn_workspace_size", [C.POINTER(KnnArgs)], C.c_size_t),
+    ("avatar_knn", [P, C.POINTER(KnnArgs), P, C.c_size_t, P], I32),
     ("avatar_visibility_soft_workspace_size", [C.POINTER(VisSoftArgs)], C.c_size_t),
     ("avatar_visibility_soft", [P, C.POINTER(VisSoftArgs), P, C.c_size_t, P], I32),
     ("avatar_shade_multi_workspace_size", [C.POINTER(ShadeMultiArgs)], C.c_size_t),

@@ -215,6 +215,25 @@ def avatar_visibility(xp, faces, frames, center, half_extent, bias, R, dmap=None
     return bits
 
 
+def avatar_knn(x, ref, k, out=None, dist2=None, ws=None, status=None):
+    """Indices [k, N] of the k nearest reference points ([3, M]) of each
+    query point ([3, N]), ascending (FP64 squared distance, index)."""
+    lib = L.load()
+    ctx = context()
+    a = L.KnnArgs()
+    a.N, a.M, a.K = x.shape[1], ref.shape[1], int(k)
+    if out is None:
+        out = torch.empty(k, a.N, dtype=torch.int32, device=x.device)
+    a.x, a.ref, a.knn, a.dist2, a.status = _p(x), _p(ref), _p(out), _p(dist2), _p(status)
+    need = lib.avatar_knn_workspace_size(C.byref(a))
+    if need == 0:
+        raise L.AvatarError(1, "avatar_knn_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, x.device)
+    L.check(lib.avatar_knn(ctx, C.byref(a), _p(ws), ws.numel(), _stream()), "avatar_knn")
+    return out
+
+
 def avatar_visibility_soft(xp, faces, frames, center, half_extent, R, knn_v, dmap=None, vis_count=None,
                            raw_bits=None, ws=None, status=None, cull_back=False):
     """(b') The paper's visibility (Sec. 3.2, Eqs. 3-4): triangle-ID images and

@@ -45,8 +45,12 @@ class Renderer:
     count that is a multiple of 64)."""
 
     def __init__(self, st, tile=16, pair_capacity=None, vis_cull_back=True, shade_tc=False, visibility="depth",
-                 knn_v=None):
+                 knn_v=None, rebind=False):
         self.st = st
+        # rebind: recompute each Gaussian's K nearest vertices (Eq. 1's S_g) on the
+        # device before every frame, as the canonical positions may have moved
+        self.rebind = rebind
+        self.knn_ws = None
         self.vis_cull_back = vis_cull_back
         self.shade_tc = shade_tc
         self.tc_ws = None
@@ -80,7 +84,19 @@ class Renderer:
         self.forward()
         torch.cuda.synchronize()
 
+    def bind(self):
+        t = self.st["avatar"]
+        if self.knn_ws is None:
+            import ctypes as C
+            from . import _lib as L
+            a = L.KnnArgs()
+            a.N, a.M, a.K = t["xg"].shape[1], t["xv"].shape[1], t["knn"].shape[0]
+            self.knn_ws = api.workspace(L.load().avatar_knn_workspace_size(C.byref(a)), self.device)
+        api.avatar_knn(t["xg"], t["xv"], t["knn"].shape[0], out=t["knn"], ws=self.knn_ws, status=self.status)
+
     def skin(self):
+        if self.rebind:
+            self.bind()
         out = api.avatar_skin(self.st["avatar"], out=self.sk, ws=self.skin_ws, status=self.status)
         self.skin_ws = out["_ws"]
 
@@ -179,9 +195,9 @@ class TrainStep(Renderer):
     """Forward frame + L1 loss + backward through every stage."""
 
     def __init__(self, st, target, tile=16, pair_capacity=None, vis_cull_back=True, shade_tc=False,
-                 visibility="depth", knn_v=None):
+                 visibility="depth", knn_v=None, rebind=False):
         self.target = target
-        super().__init__(st, tile, pair_capacity, vis_cull_back, shade_tc, visibility, knn_v)
+        super().__init__(st, tile, pair_capacity, vis_cull_back, shade_tc, visibility, knn_v, rebind)
         t = st["avatar"]
         self.loss = torch.empty(1, device=self.device)
         self.d_img = torch.empty_like(self.sb.image)
