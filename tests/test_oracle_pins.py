@@ -817,3 +817,40 @@ def test_knn_distances_follow_the_fp64_definition():
             assert abs(Fraction(d2[i, k]) - ex) <= 2 * 2.0 ** -52 * ex
             dd = (x[i].astype(np.float64) - ref[idx[i, k]].astype(np.float64))
             assert d2[i, k] == (dd[0] * dd[0] + dd[1] * dd[1]) + dd[2] * dd[2]
+
+
+# ---------------------------------------------------------------- image loss (Eq. 5)
+def test_ssim_identity_symmetry_and_constant_images():
+    from oracle import ssim as S
+    rng = np.random.default_rng(12)
+    x = rng.uniform(0, 1, size=(3, 40, 36))
+    y = np.clip(x + rng.normal(0, 0.1, x.shape), 0, 1)
+    np.testing.assert_allclose(S.ssim_map(x, x), 1.0, atol=1e-12)                 # SSIM(x, x) = 1
+    np.testing.assert_allclose(S.ssim_map(x, y), S.ssim_map(y, x), atol=1e-14)   # symmetric
+    assert S.ssim_map(x, y).mean() < 0.99
+    # constant images a, b: away from the border the window sees only the
+    # constant, so SSIM = (2ab + C1) / (a^2 + b^2 + C1) (zero variances)
+    a, b = 0.3, 0.7
+    s = S.ssim_map(np.full((1, 32, 32), a), np.full((1, 32, 32), b))
+    inner = s[0, 5:-5, 5:-5]
+    np.testing.assert_allclose(inner, (2 * a * b + S.C1) / (a * a + b * b + S.C1), rtol=1e-12)
+    # the window is a normalised Gaussian of sigma 1.5
+    g = S.gauss_1d()
+    assert abs(g.sum() - 1) < 1e-15 and np.argmax(g) == 5
+    np.testing.assert_allclose(g[4] / g[5], np.exp(-1 / (2 * 1.5 ** 2)), rtol=1e-14)
+
+
+def test_image_loss_gradient_matches_finite_differences():
+    from oracle import ssim as S
+    rng = np.random.default_rng(13)
+    x = rng.uniform(0, 1, size=(2, 14, 13))
+    y = rng.uniform(0, 1, size=(2, 14, 13))
+    loss, g = S.image_loss_grad(x, y, 0.2)
+    assert abs(loss - S.image_loss(x, y, 0.2)) < 1e-14
+    for (c, i, j) in [(0, 0, 0), (1, 7, 6), (0, 13, 12), (1, 3, 9)]:
+        h = 1e-6
+        xp, xm = x.copy(), x.copy()
+        xp[c, i, j] += h
+        xm[c, i, j] -= h
+        fd = (S.image_loss(xp, y, 0.2) - S.image_loss(xm, y, 0.2)) / (2 * h)
+        assert abs(fd - g[c, i, j]) < 1e-7 * max(1.0, abs(fd))
