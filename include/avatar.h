@@ -543,6 +543,30 @@ int avatar_render_batch_autotune(avatar_ctx *ctx, const avatar_batch_desc *d, co
                                  void *ws, size_t ws_bytes, avatar_stream_t stream, int *tuned);
 
 /* ------------------------------------------------------------------ */
+/* Image loss of Eq. 5 (Sec. 3.3), the 3DGS form:                       */
+/*   L = (1 - lambda) mean |img - target| + lambda (1 - mean SSIM),     */
+/* SSIM per channel and pixel under an 11 x 11 Gaussian window (sigma   */
+/* 1.5, zero padding at the border), C1 = 0.01^2, C2 = 0.03^2:          */
+/*   (2 mu_x mu_y + C1)(2 s_xy + C2) / ((mu_x^2 + mu_y^2 + C1)(s_x^2 +   */
+/*   s_y^2 + C2)); means over all C H W values.  The loss is reduced in  */
+/* FP64 (deterministic); d_img = weight dL/dimg.                        */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int C, H, W;           /* channels, rows, columns */
+    const float *img;      /* [C][H][W] */
+    const float *target;   /* [C][H][W] */
+    float lambda;          /* D-SSIM weight in 0..1 (paper: 0.2) */
+    float weight;          /* scale of the loss and its gradient (1 for one image) */
+    int accumulate;        /* 0: *loss = weight L;  1: *loss += weight L (batches of images) */
+    float *loss;           /* [1] device output */
+    float *d_img;          /* [C][H][W] output, or NULL for the loss alone */
+} avatar_image_loss_args;
+
+size_t avatar_image_loss_workspace_size(const avatar_image_loss_args *a);
+int avatar_image_loss(avatar_ctx *ctx, const avatar_image_loss_args *a, void *ws, size_t ws_bytes,
+                      avatar_stream_t stream);
+
+/* ------------------------------------------------------------------ */
 /* Image loss - L1 part of Eq. 5 (Sec. 3.3): loss = mean |img - target|, */
 /* d_img = sign(img - target) / n.  loss is a device float, d_img may be */
 /* NULL.                                                                */

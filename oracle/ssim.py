@@ -53,12 +53,10 @@ def image_loss(img, target, lam=0.2):
     return (1.0 - lam) * l1 + lam * (1.0 - ssim_map(img, target).mean())
 
 
-def image_loss_grad(img, target, lam=0.2):
-    """(loss, dloss/dimg) by FP64 autograd of the same definition."""
+def image_loss_torch(x, y, lam=0.2):
+    """The same definition on FP64 torch tensors [C, H, W] (differentiable)."""
     import torch
     import torch.nn.functional as F
-    x = torch.tensor(np.asarray(img, np.float64), requires_grad=True)
-    y = torch.tensor(np.asarray(target, np.float64))
     C = x.shape[0]
     g = torch.tensor(gauss_1d(), dtype=torch.float64)
     w = torch.outer(g, g).expand(C, 1, WIN, WIN).contiguous()
@@ -71,9 +69,18 @@ def image_loss_grad(img, target, lam=0.2):
     syy = blur(y * y) - my * my
     sxy = blur(x * y) - mx * my
     s = ((2 * mx * my + C1) * (2 * sxy + C2)) / ((mx * mx + my * my + C1) * (sxx + syy + C2))
-    loss = (1.0 - lam) * (x - y).abs().mean() + lam * (1.0 - s.mean())
+    return (1.0 - lam) * (x - y).abs().mean() + lam * (1.0 - s.mean())
+
+
+def image_loss_grad(img, target, lam=0.2):
+    """(loss, dloss/dimg) by FP64 autograd of the same definition."""
+    import torch
+    x = torch.tensor(np.asarray(img, np.float64), requires_grad=True)
+    y = torch.tensor(np.asarray(target, np.float64))
+    loss = image_loss_torch(x, y, lam)
     loss.backward()
     return float(loss), x.grad.numpy()
 
 
-__all__ = ["gauss_1d", "ssim_map", "image_loss", "image_loss_grad", "WIN", "SIGMA", "C1", "C2"]
+__all__ = ["gauss_1d", "ssim_map", "image_loss", "image_loss_torch", "image_loss_grad", "WIN", "SIGMA", "C1",
+           "C2"]

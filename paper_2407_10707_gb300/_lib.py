@@ -55,6 +55,11 @@ class VisArgs(C.Structure):
                 ("NL", I32), ("dmap", P), ("bits", P), ("status", P), ("cull_back", I32)]
 
 
+class ImageLossArgs(C.Structure):
+    _fields_ = [("C", I32), ("H", I32), ("W", I32), ("img", P), ("target", P), ("lam", F32), ("weight", F32),
+                ("accumulate", I32), ("loss", P), ("d_img", P)]
+
+
 class KnnArgs(C.Structure):
     _fields_ = [("N", I32), ("M", I32), ("K", I32), ("x", P), ("ref", P), ("knn", P), ("dist2", P), ("status", P)]
 
@@ -154,6 +159,8 @@ _SIGNATURES = [
     ("avatar_render_batch_autotune", [P, C.POINTER(BatchDesc), C.POINTER(BatchGrads), P, C.c_size_t, P,
                                       C.POINTER(C.c_int)], I32),
     ("avatar_l1_loss", [P, C.c_int64, P, P, P, P, P], I32),
+    ("avatar_image_loss_workspace_size", [C.POINTER(ImageLossArgs)], C.c_size_t),
+    ("avatar_image_loss", [P, C.POINTER(ImageLossArgs), P, C.c_size_t, P], I32),
 ]
 
 EXPORTED = [s[0] for s in _SIGNATURES]

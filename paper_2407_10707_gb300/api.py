@@ -453,3 +453,29 @@ def avatar_l1_loss(img, target, want_grad=True):
     L.check(lib.avatar_l1_loss(ctx, img.numel(), _p(img), _p(target), _p(loss), _p(d_img), _stream()),
             "avatar_l1_loss")
     return loss, d_img
+
+
+def avatar_image_loss(img, target, lam=0.2, d_img=None, loss=None, ws=None, weight=1.0, accumulate=False,
+                      want_grad=True):
+    """Eq. 5's image loss (1 - lam) L1 + lam D-SSIM of img, target [C, H, W].
+    Returns (loss [1], d_img)."""
+    lib = L.load()
+    ctx = context()
+    img = img.contiguous()
+    target = target.contiguous()
+    a = L.ImageLossArgs()
+    a.C, a.H, a.W = img.shape
+    a.img, a.target = _p(img), _p(target)
+    a.lam, a.weight, a.accumulate = float(lam), float(weight), 1 if accumulate else 0
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float32, device=img.device)
+    if want_grad and d_img is None:
+        d_img = torch.empty_like(img)
+    a.loss, a.d_img = _p(loss), _p(d_img) if want_grad else None
+    need = lib.avatar_image_loss_workspace_size(C.byref(a))
+    if need == 0:
+        raise L.AvatarError(1, "avatar_image_loss_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, img.device)
+    L.check(lib.avatar_image_loss(ctx, C.byref(a), _p(ws), ws.numel(), _stream()), "avatar_image_loss")
+    return loss, d_img

@@ -195,8 +195,11 @@ class TrainStep(Renderer):
     """Forward frame + L1 loss + backward through every stage."""
 
     def __init__(self, st, target, tile=16, pair_capacity=None, vis_cull_back=True, shade_tc=False,
-                 visibility="depth", knn_v=None, rebind=False):
+                 visibility="depth", knn_v=None, rebind=False, ssim_weight=0.2):
+        # image loss of Eq. 5: (1 - ssim_weight) L1 + ssim_weight D-SSIM (the paper's 0.2)
         self.target = target
+        self.ssim_weight = float(ssim_weight)
+        self.loss_ws = None
         super().__init__(st, tile, pair_capacity, vis_cull_back, shade_tc, visibility, knn_v, rebind)
         t = st["avatar"]
         self.loss = torch.empty(1, device=self.device)
@@ -223,8 +226,13 @@ class TrainStep(Renderer):
         t = st["avatar"]
         s = api._stream()
         # loss
-        L.check(lib.avatar_l1_loss(ctx, self.sb.image.numel(), api._p(self.sb.image), api._p(self.target),
-                                   api._p(self.loss), api._p(self.d_img), s), "avatar_l1_loss")
+        if self.loss_ws is None:
+            la = L.ImageLossArgs()
+            la.C, la.H, la.W = self.sb.image.shape
+            la.lam, la.weight = self.ssim_weight, 1.0
+            self.loss_ws = api.workspace(lib.avatar_image_loss_workspace_size(C.byref(la)), self.device)
+        api.avatar_image_loss(self.sb.image, self.target, self.ssim_weight, d_img=self.d_img, loss=self.loss,
+                              ws=self.loss_ws)
         # splat adjoint
         G = t["xg"].shape[1]
         a = api._splat_struct(G, st["camera"], self.sk["xd"], self.sk["cov"], t["opacity"], self.sh["color"],
@@ -371,7 +379,7 @@ class BatchRenderer:
     in BF16.  The pair buffer grows once if the first eager call overflows."""
 
     def __init__(self, batch, targets=None, tile=0, pair_capacity=None, vis_cull_back=True, attr_dtype="f32",
-                 device="cuda"):
+                 device="cuda", ssim_weight=0.2):
         import ctypes as C
         from . import _lib as L
         self.L, self.C = L, C
@@ -406,6 +414,7 @@ class BatchRenderer:
         cap = pair_capacity or min(0x7FFFFFFF, max(65536, 16 * G * self.V))
         self._alloc(cap)
         self.targets = targets
+        self.ssim_weight = float(ssim_weight)
         self.graph = None
         self.forward()
         torch.cuda.synchronize()
@@ -497,12 +506,21 @@ class BatchRenderer:
         return self.grads
 
     def step(self):
-        """Forward, L1 loss over every view's pixels, backward."""
-        lib = self.L.load()
+        """Forward, the image loss of Eq. 5 over every view (each view's loss
+        weighted by its share of all pixels), backward."""
         self.forward()
-        self.L.check(lib.avatar_l1_loss(api.context(), self.images.numel(), api._p(self.images),
-                                        api._p(self.targets), api._p(self.loss), api._p(self.d_images),
-                                        api._stream()), "avatar_l1_loss")
+        total = float(self.offsets[-1])
+        if getattr(self, "loss_ws", None) is None:
+            la = self.L.ImageLossArgs()
+            h, w = max(self.sizes, key=lambda s: s[0] * s[1])
+            la.C, la.H, la.W, la.lam, la.weight = 3, h, w, self.ssim_weight, 1.0
+            self.loss_ws = api.workspace(self.L.load().avatar_image_loss_workspace_size(self.C.byref(la)),
+                                         self.device)
+        for v, (h, w) in enumerate(self.sizes):
+            sl = slice(int(self.offsets[v]), int(self.offsets[v + 1]))
+            api.avatar_image_loss(self.images[sl].view(3, h, w), self.targets[sl].view(3, h, w), self.ssim_weight,
+                                  d_img=self.d_images[sl].view(3, h, w), loss=self.loss, ws=self.loss_ws,
+                                  weight=3 * h * w / total, accumulate=v > 0)
         self.backward(self.d_images)
         return self.loss
 
