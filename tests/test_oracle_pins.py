@@ -854,3 +854,49 @@ def test_image_loss_gradient_matches_finite_differences():
         xm[c, i, j] -= h
         fd = (S.image_loss(xp, y, 0.2) - S.image_loss(xm, y, 0.2)) / (2 * h)
         assert abs(fd - g[c, i, j]) < 1e-7 * max(1.0, abs(fd))
+
+
+# ---------------------------------------------------------------- regularisers (Sec. 3.3)
+def test_regularizers_closed_forms():
+    from oracle import regularizers as RG
+    xv = np.array([[0.0, 0, 0], [1.0, 0, 0], [3.0, 0, 0]])
+    knn_v = np.array([[0, 1], [1, 0], [2, 1]])                 # each vertex and its nearest other vertex
+    av = np.array([[0.2, 0.2, 0.2], [0.5, 0.1, 0.2], [0.5, 0.1, 0.9]])
+    rv = np.array([0.3, 0.3, 0.6])
+    pv = np.array([0.0, 1.0, 1.0])
+    # smooth: pairs (0,1), (1,0), (2,1): |a| sums 0.4, 0.4, 0.7; |gamma| 0, 0, 0.3; |p| 1, 1, 0
+    xg = np.array([[0.0, 0, 0], [1.0, 1.0, 0]])
+    knn = np.array([[0], [1]])
+    logscale = np.log(np.array([[0.004, 0.004, 0.004], [0.01, 0.002, 0.007]]))
+    dxv = np.array([[0.0, 0, 0], [0.3, 0.4, 0], [0, 0, -2.0]])
+    total, t, _ = RG.regularizers(xg, logscale, knn, xv, av, rv, pv, knn_v, dxv)
+    assert abs(t["smooth"] - (0.4 + 0.4 + 0.7 + 0.3 + 2.0)) < 1e-12
+    assert abs(t["mdist"] - 1.0) < 1e-12                       # Gaussian 0 sits on its vertex, Gaussian 1 at 1
+    assert abs(t["disp"] - (0.5 + 2.0)) < 1e-12
+    assert abs(t["scale"] - (0.005 + 0.002)) < 1e-12          # only 0.01 and 0.007 exceed s0 = 0.005
+    w = RG.WEIGHTS
+    assert abs(total - sum(w[k] * t[k] for k in t)) < 1e-12
+
+
+def test_regularizer_gradients_match_finite_differences():
+    from oracle import regularizers as RG
+    rng = np.random.default_rng(21)
+    Nv, G = 30, 40
+    xv = rng.normal(size=(Nv, 3))
+    knn_v = synth.knn_indices(xv, xv, 5)
+    xg = xv[rng.integers(0, Nv, G)] + 0.05 * rng.normal(size=(G, 3))
+    knn = synth.knn_indices(xv, xg, 3)
+    av, rv, pv = rng.uniform(size=(Nv, 3)), rng.uniform(size=Nv), rng.uniform(size=Nv)
+    logscale = np.log(rng.uniform(0.001, 0.01, size=(G, 3)))
+    dxv = 0.01 * rng.normal(size=(Nv, 3))
+    args = dict(xg=xg, logscale=logscale, knn=knn, xv=xv, av=av, rv=rv, pv=pv, knn_v=knn_v, dxv=dxv)
+    _, _, g = RG.regularizers(**args)
+    for name, idx in (("xg", (3, 1)), ("logscale", (5, 2)), ("av", (7, 0)), ("rv", (2,)), ("pv", (11,)),
+                      ("dxv", (4, 1))):
+        h = 1e-7
+        ap = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in args.items()}
+        am = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in args.items()}
+        ap[name][idx] += h
+        am[name][idx] -= h
+        fd = (RG.regularizers(**ap)[0] - RG.regularizers(**am)[0]) / (2 * h)
+        assert abs(fd - g[name][idx]) < 1e-5 * max(1.0, abs(fd)), name
