@@ -543,6 +543,45 @@ int avatar_render_batch_autotune(avatar_ctx *ctx, const avatar_batch_desc *d, co
                                  void *ws, size_t ws_bytes, avatar_stream_t stream, int *tuned);
 
 /* ------------------------------------------------------------------ */
+/* Regularisers of Sec. 3.3 (the terms of Eq. 6 beside the image loss): */
+/*   L_smooth = sum_i sum_{k in S_v^i} |a_i - a_k|_1 + |gamma_i -        */
+/*              gamma_k| + |p_i - p_k|      (vertex materials)          */
+/*   L_mdist  = sum_i sum_{k in S_g^i} || x_g^i - x_v^k ||_2             */
+/*   L_disp   = sum_i || dx^i ||_2                                      */
+/*   L_scale  = sum_i sum_c max(0, exp(logscale_ic) - s0)               */
+/* loss (+)= w_smooth L_smooth + w_mdist L_mdist + w_disp L_disp +       */
+/* w_scale L_scale (paper: 0.002, 0.1, 0.02, 10; s0 = 0.005).  The       */
+/* gradients are ADDED to the given buffers (NULL: not wanted), so the  */
+/* call follows the image-loss backward in a training step.  Subgradient */
+/* 0 where a difference or a norm is 0.  Sums reduced in FP64.          */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int G, Nv;             /* Gaussians, vertices */
+    int Kg, Kv;            /* |S_g| (0..64), |S_v| (0..64) */
+    const float *xg;       /* [3][G] canonical Gaussian positions */
+    const void *logscale;  /* [3][G] (attr_dtype) */
+    const int32_t *knn;    /* [Kg][G] S_g */
+    const float *xv;       /* [3][Nv] canonical vertices */
+    const void *av;        /* [3][Nv] albedo (attr_dtype) */
+    const void *rv;        /* [Nv] roughness (attr_dtype) */
+    const void *pv;        /* [Nv] specular tint (attr_dtype) */
+    const int32_t *knn_v;  /* [Kv][Nv] S_v */
+    const float *dxv;      /* [3][Nv] displacement, or NULL (no displacement term) */
+    int attr_dtype;        /* AVATAR_DTYPE_F32 or _BF16 */
+    float w_smooth, w_mdist, w_disp, w_scale;
+    float s0;              /* scale threshold */
+    int accumulate;        /* 0: *loss = total;  1: *loss += total */
+    float *loss;           /* [1] device, or NULL */
+    float *terms;          /* [4] device output of the unweighted sums (smooth, mdist, disp, scale), or NULL */
+    float *d_xg, *d_logscale, *d_av, *d_rv, *d_pv, *d_dxv;  /* FP32 gradients, accumulated */
+    int32_t *status;
+} avatar_reg_args;
+
+size_t avatar_regularizers_workspace_size(const avatar_reg_args *a);
+int avatar_regularizers(avatar_ctx *ctx, const avatar_reg_args *a, void *ws, size_t ws_bytes,
+                        avatar_stream_t stream);
+
+/* ------------------------------------------------------------------ */
 /* Image loss of Eq. 5 (Sec. 3.3), the 3DGS form:                       */
 /*   L = (1 - lambda) mean |img - target| + lambda (1 - mean SSIM),     */
 /* SSIM per channel and pixel under an 11 x 11 Gaussian window (sigma   */

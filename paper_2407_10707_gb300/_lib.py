@@ -55,6 +55,14 @@ class VisArgs(C.Structure):
                 ("NL", I32), ("dmap", P), ("bits", P), ("status", P), ("cull_back", I32)]
 
 
+class RegArgs(C.Structure):
+    _fields_ = [("G", I32), ("Nv", I32), ("Kg", I32), ("Kv", I32), ("xg", P), ("logscale", P), ("knn", P),
+                ("xv", P), ("av", P), ("rv", P), ("pv", P), ("knn_v", P), ("dxv", P), ("attr_dtype", I32),
+                ("w_smooth", F32), ("w_mdist", F32), ("w_disp", F32), ("w_scale", F32), ("s0", F32),
+                ("accumulate", I32), ("loss", P), ("terms", P), ("d_xg", P), ("d_logscale", P), ("d_av", P),
+                ("d_rv", P), ("d_pv", P), ("d_dxv", P), ("status", P)]
+
+
 class ImageLossArgs(C.Structure):
     _fields_ = [("C", I32), ("H", I32), ("W", I32), ("img", P), ("target", P), ("lam", F32), ("weight", F32),
                 ("accumulate", I32), ("loss", P), ("d_img", P)]
@@ -159,6 +167,8 @@ _SIGNATURES = [
     ("avatar_render_batch_autotune", [P, C.POINTER(BatchDesc), C.POINTER(BatchGrads), P, C.c_size_t, P,
                                       C.POINTER(C.c_int)], I32),
     ("avatar_l1_loss", [P, C.c_int64, P, P, P, P, P], I32),
+    ("avatar_regularizers_workspace_size", [C.POINTER(RegArgs)], C.c_size_t),
+    ("avatar_regularizers", [P, C.POINTER(RegArgs), P, C.c_size_t, P], I32),
     ("avatar_image_loss_workspace_size", [C.POINTER(ImageLossArgs)], C.c_size_t),
     ("avatar_image_loss", [P, C.POINTER(ImageLossArgs), P, C.c_size_t, P], I32),
 ]

@@ -479,3 +479,41 @@ def avatar_image_loss(img, target, lam=0.2, d_img=None, loss=None, ws=None, weig
         ws = workspace(need, img.device)
     L.check(lib.avatar_image_loss(ctx, C.byref(a), _p(ws), ws.numel(), _stream()), "avatar_image_loss")
     return loss, d_img
+
+
+REG_WEIGHTS = dict(smooth=0.002, mdist=0.1, disp=0.02, scale=10.0)  # Sec. 3.3
+
+
+def avatar_regularizers(t, knn_v, grads=None, loss=None, terms=None, weights=None, s0=0.005, accumulate=False,
+                        ws=None, status=None):
+    """Sec. 3.3's regularisers of the avatar tensors t (avatar_tensors layout)
+    with the vertex neighbourhoods knn_v [Kv, Nv].  grads: dict of FP32
+    buffers (xg, logscale, av, rv, pv, dxv) the gradients are ADDED to.
+    Returns (loss [1], terms [4])."""
+    lib = L.load()
+    ctx = context()
+    w = dict(REG_WEIGHTS if weights is None else weights)
+    dev = t["xg"].device
+    a = L.RegArgs()
+    a.G, a.Nv = t["xg"].shape[1], t["xv"].shape[1]
+    a.Kg, a.Kv = t["knn"].shape[0], knn_v.shape[0]
+    a.xg, a.logscale, a.knn, a.xv = _p(t["xg"]), _p(t["logscale"]), _p(t["knn"]), _p(t["xv"])
+    a.av, a.rv, a.pv, a.knn_v, a.dxv = _p(t["av"]), _p(t["rv"]), _p(t["pv"]), _p(knn_v), _p(t.get("dxv"))
+    a.attr_dtype = _dtype_code(t["logscale"], t["av"], t["rv"], t["pv"])
+    a.w_smooth, a.w_mdist, a.w_disp, a.w_scale, a.s0 = w["smooth"], w["mdist"], w["disp"], w["scale"], float(s0)
+    a.accumulate = 1 if accumulate else 0
+    if loss is None:
+        loss = torch.zeros(1, device=dev)
+    if terms is None:
+        terms = torch.zeros(4, device=dev)
+    a.loss, a.terms, a.status = _p(loss), _p(terms), _p(status)
+    grads = grads or {}
+    a.d_xg, a.d_logscale, a.d_av = _p(grads.get("xg")), _p(grads.get("logscale")), _p(grads.get("av"))
+    a.d_rv, a.d_pv, a.d_dxv = _p(grads.get("rv")), _p(grads.get("pv")), _p(grads.get("dxv"))
+    need = lib.avatar_regularizers_workspace_size(C.byref(a))
+    if need == 0:
+        raise L.AvatarError(1, "avatar_regularizers_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    L.check(lib.avatar_regularizers(ctx, C.byref(a), _p(ws), ws.numel(), _stream()), "avatar_regularizers")
+    return loss, terms

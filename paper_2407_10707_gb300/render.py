@@ -195,11 +195,17 @@ class TrainStep(Renderer):
     """Forward frame + L1 loss + backward through every stage."""
 
     def __init__(self, st, target, tile=16, pair_capacity=None, vis_cull_back=True, shade_tc=False,
-                 visibility="depth", knn_v=None, rebind=False, ssim_weight=0.2):
-        # image loss of Eq. 5: (1 - ssim_weight) L1 + ssim_weight D-SSIM (the paper's 0.2)
+                 visibility="depth", knn_v=None, rebind=False, ssim_weight=0.2, regularize=False):
+        # image loss of Eq. 5: (1 - ssim_weight) L1 + ssim_weight D-SSIM (the paper's 0.2);
+        # regularize adds the regularisers of Sec. 3.3 (needs knn_v, the filters' S_v)
         self.target = target
         self.ssim_weight = float(ssim_weight)
         self.loss_ws = None
+        if regularize and knn_v is None:
+            raise ValueError("the smoothness regulariser needs knn_v")
+        self.regularize = regularize
+        self.reg_ws = None
+        self.reg_terms = None
         super().__init__(st, tile, pair_capacity, vis_cull_back, shade_tc, visibility, knn_v, rebind)
         t = st["avatar"]
         self.loss = torch.empty(1, device=self.device)
@@ -267,6 +273,12 @@ class TrainStep(Renderer):
             self._bwd_ws = api.workspace(lib.avatar_skin_backward_workspace_size(C.byref(ka)), self.device)
         L.check(lib.avatar_skin_backward(ctx, C.byref(ka), C.byref(gk), api._p(self.skin_ws), api._p(self._bwd_ws),
                                          self._bwd_ws.numel(), s), "avatar_skin_backward")
+        if self.regularize:
+            if self.reg_ws is None:
+                self.reg_ws = api.workspace(1 << 16, self.device)
+                self.reg_terms = torch.zeros(4, device=self.device)
+            api.avatar_regularizers(t, self.knn_v, grads=self.g_skin, loss=self.loss, terms=self.reg_terms,
+                                    accumulate=True, ws=self.reg_ws, status=self.status)
 
     def step(self):
         self.forward()
