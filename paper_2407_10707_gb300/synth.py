@@ -514,3 +514,23 @@ def config_batch(name: str, **overrides) -> Batch:
     kw.update(overrides)
     scene = config_scene(kw.pop("scene"))
     return make_batch(scene, **kw)
+
+
+# ---------------------------------------------------------------------------
+# Displacement MLP weights (the trained weights are not available)
+# ---------------------------------------------------------------------------
+def mlp_weights(seed: int, pose_dims: int = 72, width: int = 256, n_freq: int = 64, freq_sd: float = 2.0) -> dict:
+    """Seeded He-normal weights and small biases for the four layers, the
+    output layer scaled to millimetre displacements, Gaussian frequencies
+    (cycles per metre) for the Fourier features."""
+    rng = np.random.default_rng(seed + 3000)
+
+    def lin(o, i):
+        return rng.normal(0.0, math.sqrt(2.0 / i), size=(o, i)), rng.normal(0.0, 0.01, size=o)
+
+    W1, b1 = lin(width, 2 * n_freq + pose_dims)
+    W2, b2 = lin(width, width)
+    W3, b3 = lin(width, width)
+    W4, b4 = lin(3, width)
+    return dict(Bf=rng.normal(0.0, freq_sd, size=(n_freq, 3)), W1=W1, b1=b1, W2=W2, b2=b2, W3=W3, b3=b3,
+                W4=W4 * 1e-3, b4=b4 * 1e-3)

@@ -900,3 +900,37 @@ def test_regularizer_gradients_match_finite_differences():
         am[name][idx] -= h
         fd = (RG.regularizers(**ap)[0] - RG.regularizers(**am)[0]) / (2 * h)
         assert abs(fd - g[name][idx]) < 1e-5 * max(1.0, abs(fd)), name
+
+
+# ---------------------------------------------------------------- displacement MLP
+def test_mlp_matches_torch_layers_and_closed_forms():
+    from oracle import mlp as M
+    w = synth.mlp_weights(1)
+    rng = np.random.default_rng(31)
+    x = rng.normal(0, 0.5, size=(50, 3))
+    theta = rng.normal(0, 0.3, size=72)
+    got = M.forward(x, theta, **w)
+    # the same network from torch's own layers in FP64
+    tw = {k: torch.tensor(v, dtype=torch.float64) for k, v in w.items()}
+    p = 2 * math.pi * torch.tensor(x) @ tw["Bf"].T
+    inp = torch.cat([torch.sin(p), torch.cos(p), torch.tensor(theta).expand(len(x), -1)], 1)
+    net = torch.nn.Sequential(torch.nn.Linear(200, 256), torch.nn.ReLU(), torch.nn.Linear(256, 256),
+                              torch.nn.ReLU(), torch.nn.Linear(256, 256), torch.nn.ReLU(),
+                              torch.nn.Linear(256, 3)).double()
+    with torch.no_grad():
+        for lin, (W, b) in zip([net[0], net[2], net[4], net[6]], [("W1", "b1"), ("W2", "b2"), ("W3", "b3"),
+                                                                  ("W4", "b4")]):
+            lin.weight.copy_(tw[W])
+            lin.bias.copy_(tw[b])
+        want = net(inp).numpy()
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-15)
+    # with the last layer zero the output is its bias
+    w0 = dict(w, W4=np.zeros_like(w["W4"]))
+    np.testing.assert_allclose(M.forward(x, theta, **w0), np.broadcast_to(w["b4"], (50, 3)), atol=0)
+    # Fourier features: sin^2 + cos^2 = 1, and integer frequencies are 1-periodic
+    g = M.features(x, w["Bf"])
+    np.testing.assert_allclose(g[:, :64] ** 2 + g[:, 64:] ** 2, 1.0, atol=1e-14)
+    Bi = np.rint(w["Bf"])
+    np.testing.assert_allclose(M.features(x + np.array([1.0, 0, 0]), Bi), M.features(x, Bi), atol=1e-9)
+    # the bfloat16 rounding of the kernel's operands: nearest, ties to even
+    assert M.bf16(1 + 2.0 ** -8) == 1.0 and M.bf16(1 + 3 * 2.0 ** -8) == 1 + 2.0 ** -6
