@@ -582,6 +582,38 @@ int avatar_regularizers(avatar_ctx *ctx, const avatar_reg_args *a, void *ws, siz
                         avatar_stream_t stream);
 
 /* ------------------------------------------------------------------ */
+/* Pose-dependent displacement MLP (Sec. 3.1; design in Sec. 4: four    */
+/* layers of width 256, ReLU, random Fourier features):                 */
+/*   gamma(x) = [sin(2 pi B x), cos(2 pi B x)]     B: [64][3]            */
+/*   h1 = relu(W1 [gamma(x); theta] + b1)          W1: [256][128 + P]    */
+/*   h2 = relu(W2 h1 + b2),  h3 = relu(W3 h2 + b3) W2, W3: [256][256]    */
+/*   dx = W4 h3 + b4                               W4: [3][256]          */
+/* On the tensor cores with BF16 operands and FP32 accumulation: the    */
+/* features, the hidden activations and W1's feature part, W2, W3, W4   */
+/* are rounded to bfloat16 (nearest even); theta's part of layer 1 and  */
+/* the biases stay FP32.  All arrays are FP32, row-major as shown.  The */
+/* workspace (avatar_mlp_workspace_size, 256-byte aligned) receives the */
+/* packed BF16 weights on every call.  Asynchronous on the stream; an   */
+/* accelerator wait that runs out sets AVATAR_ERR_TIMEOUT in *status.   */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int N;                 /* points (0 allowed) */
+    int P;                 /* pose dimensions, 0..128 */
+    const float *x;        /* [3][N] points (canonical vertices) */
+    const float *theta;    /* [P] pose */
+    const float *Bf;       /* [64][3] Fourier frequencies */
+    const float *W1, *b1;  /* [256][128 + P], [256] */
+    const float *W2, *b2;  /* [256][256], [256] */
+    const float *W3, *b3;  /* [256][256], [256] */
+    const float *W4, *b4;  /* [3][256], [3] */
+    float *dx;             /* [3][N] output */
+    int32_t *status;       /* device status word, or NULL */
+} avatar_mlp_args;
+
+size_t avatar_mlp_workspace_size(const avatar_mlp_args *a);
+int avatar_mlp(avatar_ctx *ctx, const avatar_mlp_args *a, void *ws, size_t ws_bytes, avatar_stream_t stream);
+
+/* ------------------------------------------------------------------ */
 /* Image loss of Eq. 5 (Sec. 3.3), the 3DGS form:                       */
 /*   L = (1 - lambda) mean |img - target| + lambda (1 - mean SSIM),     */
 /* SSIM per channel and pixel under an 11 x 11 Gaussian window (sigma   */

@@ -63,6 +63,11 @@ class RegArgs(C.Structure):
                 ("d_rv", P), ("d_pv", P), ("d_dxv", P), ("status", P)]
 
 
+class MlpArgs(C.Structure):
+    _fields_ = [("N", I32), ("P", I32), ("x", P), ("theta", P), ("Bf", P), ("W1", P), ("b1", P), ("W2", P),
+                ("b2", P), ("W3", P), ("b3", P), ("W4", P), ("b4", P), ("dx", P), ("status", P)]
+
+
 class ImageLossArgs(C.Structure):
     _fields_ = [("C", I32), ("H", I32), ("W", I32), ("img", P), ("target", P), ("lam", F32), ("weight", F32),
                 ("accumulate", I32), ("loss", P), ("d_img", P)]
@@ -169,6 +174,8 @@ _SIGNATURES = [
     ("avatar_l1_loss", [P, C.c_int64, P, P, P, P, P], I32),
     ("avatar_regularizers_workspace_size", [C.POINTER(RegArgs)], C.c_size_t),
     ("avatar_regularizers", [P, C.POINTER(RegArgs), P, C.c_size_t, P], I32),
+    ("avatar_mlp_workspace_size", [C.POINTER(MlpArgs)], C.c_size_t),
+    ("avatar_mlp", [P, C.POINTER(MlpArgs), P, C.c_size_t, P], I32),
     ("avatar_image_loss_workspace_size", [C.POINTER(ImageLossArgs)], C.c_size_t),
     ("avatar_image_loss", [P, C.POINTER(ImageLossArgs), P, C.c_size_t, P], I32),
 ]

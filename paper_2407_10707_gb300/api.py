@@ -517,3 +517,35 @@ def avatar_regularizers(t, knn_v, grads=None, loss=None, terms=None, weights=Non
         ws = workspace(need, dev)
     L.check(lib.avatar_regularizers(ctx, C.byref(a), _p(ws), ws.numel(), _stream()), "avatar_regularizers")
     return loss, terms
+
+
+# ---------------------------------------------------------------- displacement MLP
+MLP_KEYS = ("Bf", "W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")
+
+
+def mlp_tensors(w, device):
+    """The MLP's weights (dict of arrays, MLP_KEYS) as contiguous FP32 device tensors."""
+    return {k: torch.as_tensor(np.asarray(w[k]), dtype=torch.float32).contiguous().to(device) for k in MLP_KEYS}
+
+
+def avatar_mlp(x, theta, w, dx=None, ws=None, status=None):
+    """Sec. 3.1's displacement dx [3, N] of the points x [3, N] at pose
+    theta [P], weights w from mlp_tensors."""
+    lib = L.load()
+    ctx = context()
+    x = x.contiguous()
+    theta = theta.contiguous()
+    a = L.MlpArgs()
+    a.N, a.P = x.shape[1], theta.numel()
+    if dx is None:
+        dx = torch.empty_like(x)
+    a.x, a.theta, a.dx, a.status = _p(x), _p(theta), _p(dx), _p(status)
+    for k in MLP_KEYS:
+        setattr(a, k, _p(w[k]))
+    need = lib.avatar_mlp_workspace_size(C.byref(a))
+    if need == 0:
+        raise L.AvatarError(1, "avatar_mlp_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, x.device)
+    L.check(lib.avatar_mlp(ctx, C.byref(a), _p(ws), ws.numel(), _stream()), "avatar_mlp")
+    return dx

@@ -13,9 +13,7 @@
 // stacked light matrix, which stays resident in shared memory; the epilogue
 // reads the accumulators with tcgen05.ld and writes gamma-corrected colours.
 // Persistent CTAs, one per SM, each with 256 TMEM columns.
-#include <cuda_bf16.h>
-
-#include "common.cuh"
+#include "umma.cuh"
 
 namespace {
 
@@ -25,75 +23,9 @@ constexpr int TC_KC = 64;        // lights per chunk
 constexpr int TC_MAX_ENV = 32;   // N = 3 * n_env <= 96
 constexpr int TC_MAX_K = 2048;   // resident stacked-light matrix (shared-memory size permitting)
 constexpr int TC_TMEM_COLS = 256;
-constexpr int TC_WAIT_LIMIT = 1 << 22;
 constexpr float FRES_C1 = -5.55473f;
 constexpr float FRES_C0 = -6.98316f;
 constexpr float INV_GAMMA = 1.0f / 2.2f;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Shared-memory matrix descriptor: K-major, no swizzle; LBO = distance of
-// core matrices along K, SBO = along M/N (bytes); descriptor version 1.
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
-__device__ __forceinline__ uint32_t umma_idesc(int M, int N)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// Byte offset of element (row, k) in a canonical no-swizzle K-major tile whose
-// rows hold kc8 core matrices (8 rows x 16 bytes) along K.
-__device__ __forceinline__ int canon_off(int row, int k, int kc8)
-{
-    return (((row >> 3) * kc8 + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum)
-{
-    asm volatile("{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
-                     d_tmem),
-                 "l"(a), "l"(b), "r"(idesc), "r"(accum));
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void bar_wait(uint64_t *bar, uint32_t parity, int32_t *status)
-{
-    for (int it = 0; it < TC_WAIT_LIMIT; ++it) {
-        uint32_t done;
-        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-                     : "=r"(done)
-                     : "r"(smem_u32(bar)), "r"(parity)
-                     : "memory");
-        if (done) return;
-    }
-    av_report(status, AVATAR_ERR_TIMEOUT);
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
-{
-    uint32_t r[16];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 // Exact FP32 back-face decision, identical to the single-light kernel.
 __device__ __forceinline__ bool culled_fp32(const float *x, const float *n, const float *C)
