@@ -3,9 +3,11 @@ the oracle.
 
 Tolerances.  The kernel rounds the same values to bfloat16 as the oracle's
 bf16 mode, but it forms the Fourier phases and every layer's sums in FP32
-where the oracle uses FP64; a value lying within that FP32 error of a
-bfloat16 rounding boundary rounds the other way, one bfloat16 step (2^-8
-relative) in one feature or activation.  An FP32 emulation of the kernel's
+where the oracle uses FP64 (and takes the hardware sine and cosine after an
+exact range reduction, absolute error about 4e-7, below the FP32 error of
+the phase); a value lying within that error of a bfloat16 rounding boundary
+rounds the other way, one bfloat16 step (2^-8 relative) in one feature or
+activation.  An FP32 emulation of the kernel's
 arithmetic on 4000 points of these weights puts the effect at 0.55 % of the
 output's RMS at worst and 3e-5 of it on average; the bounds below are about
 four times those (2 % worst, 2e-4 mean).  Against the plain FP64 network the
