@@ -422,6 +422,41 @@ def forms(r, st, sc, args, dev, flush, fwd_ms, train_ms, want):
         out["visibility_paper"] = _form_paper_vis(r, st, sc, args, dev, flush, reps)
     if "batch" in want:
         out["batch_c4"] = _form_batch(args, dev, reps)
+    if "mlp" in want:
+        out["displacement_mlp"] = _form_mlp(r, st, args, dev, flush, reps, fwd_ms)
+    return out
+
+
+def _form_mlp(r, st, args, dev, flush, reps, fwd_ms):
+    """The pose-dependent displacement MLP of Sec. 3.1 (four layers of width
+    256, Fourier features) on the tensor cores: on the avatar's vertices
+    every frame, and alone on a million points for its throughput."""
+    import torch
+
+    from paper_2407_10707_gb300 import api, render, synth
+    w = api.mlp_tensors(synth.mlp_weights(0), dev)
+    t = st["avatar"]
+    theta = t["pose"].reshape(-1).contiguous()
+    out = {}
+    flops_pt = 2.0 * (128 * 256 + 2 * 256 * 256 + 256 * 3)
+    peaks, kind = _peaks()
+    for name, x in (("avatar_vertices", t["xv"]),
+                    ("points_1m", torch.rand(3, 1_000_000, device=dev) * 2.0 - 1.0)):
+        dx = torch.empty_like(x)
+        ws = api.workspace(api.mlp_workspace_size(x.shape[1], theta.numel()), dev)
+        us = _time_graph(_graph_of(lambda: api.avatar_mlp(x, theta, w, dx=dx, ws=ws)), reps, flush) * 1000.0
+        tf = flops_pt * x.shape[1] / (us * 1e-6) / 1e12
+        out[name] = {"points": int(x.shape[1]), "us": round(us, 1), "achieved_tflops": round(tf, 1),
+                     "frac": round(tf / float(peaks["bf16_tflops"]), 4)}
+    rm = render.Renderer(st, tile=args.tile, mlp=w)
+    rm.check()
+    frame_ms = _time_graph(_graph_of(rm.forward), reps, flush)
+    out.update({"what": "dx = MLP(gamma(x_v), theta) before skinning: Fourier features, three ReLU layers of 256 "
+                        "and a linear output, BF16 operands, FP32 accumulation in TMEM, one fused kernel (plus "
+                        "the per-call weight packing)",
+                "frames_per_s_with_mlp": round(1000.0 / frame_ms, 3),
+                "frames_per_s_without": round(1000.0 / fwd_ms, 3),
+                "peak": float(peaks["bf16_tflops"]), "peak_note": f"dense BF16, {kind}"})
     return out
 
 
@@ -686,7 +721,8 @@ def main():
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the precision / relighting / batching forms")
-    ap.add_argument("--forms", default="precision,relight,knn,paper_vis,batch", help="comma list of forms to measure")
+    ap.add_argument("--forms", default="precision,relight,knn,paper_vis,batch,mlp",
+                    help="comma list of forms to measure")
     ap.add_argument("--batch-poses", type=int, default=32, help="poses of the batch form (4 cameras each)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--workload", default=WORKLOAD, help="named synthetic configuration (profiling uses smaller ones)")

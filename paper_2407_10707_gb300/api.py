@@ -528,6 +528,12 @@ def mlp_tensors(w, device):
     return {k: torch.as_tensor(np.asarray(w[k]), dtype=torch.float32).contiguous().to(device) for k in MLP_KEYS}
 
 
+def mlp_workspace_size(n, p):
+    a = L.MlpArgs()
+    a.N, a.P = n, p
+    return L.load().avatar_mlp_workspace_size(C.byref(a))
+
+
 def avatar_mlp(x, theta, w, dx=None, ws=None, status=None):
     """Sec. 3.1's displacement dx [3, N] of the points x [3, N] at pose
     theta [P], weights w from mlp_tensors."""

@@ -42,11 +42,21 @@ class Renderer:
     closed, outward-wound meshes such as the capsule body (set it to False
     for open or inconsistently wound meshes).  shade_tc evaluates the shading
     sums on the tensor cores (BF16 weights, FP32 accumulation; needs a light
-    count that is a multiple of 64)."""
+    count that is a multiple of 64).  mlp (weights from api.mlp_tensors)
+    evaluates the pose-dependent displacement MLP of Sec. 3.1 on the canonical
+    vertices before every skinning, in place of the avatar's fixed dxv."""
 
     def __init__(self, st, tile=16, pair_capacity=None, vis_cull_back=True, shade_tc=False, visibility="depth",
-                 knn_v=None, rebind=False):
+                 knn_v=None, rebind=False, mlp=None):
         self.st = st
+        self.mlp = mlp
+        self.mlp_ws = None
+        self.skin_t = st["avatar"]
+        if mlp is not None:
+            self.skin_t = dict(st["avatar"])
+            self.skin_t["dxv"] = torch.empty_like(st["avatar"]["xv"])
+            self.mlp_ws = api.workspace(api.mlp_workspace_size(st["avatar"]["xv"].shape[1],
+                                                               st["avatar"]["pose"].numel()), st["avatar"]["xv"].device)
         # rebind: recompute each Gaussian's K nearest vertices (Eq. 1's S_g) on the
         # device before every frame, as the canonical positions may have moved
         self.rebind = rebind
@@ -97,7 +107,10 @@ class Renderer:
     def skin(self):
         if self.rebind:
             self.bind()
-        out = api.avatar_skin(self.st["avatar"], out=self.sk, ws=self.skin_ws, status=self.status)
+        if self.mlp is not None:
+            t = self.skin_t
+            api.avatar_mlp(t["xv"], t["pose"].reshape(-1), self.mlp, dx=t["dxv"], ws=self.mlp_ws, status=self.status)
+        out = api.avatar_skin(self.skin_t, out=self.sk, ws=self.skin_ws, status=self.status)
         self.skin_ws = out["_ws"]
 
     def visibility(self):

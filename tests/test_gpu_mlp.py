@@ -107,3 +107,27 @@ def test_empty_and_invalid(gpu):
     with pytest.raises(L.AvatarError):
         api.avatar_mlp(torch.zeros(3, 4, device="cuda"), torch.zeros(129, device="cuda"),
                        api.mlp_tensors(synth.mlp_weights(0, pose_dims=129), "cuda"))
+
+
+def test_renderer_evaluates_the_mlp_before_skinning(gpu):
+    """A frame rendered with the MLP is bit-identical to the frame rendered
+    with the MLP's output supplied as the avatar's fixed displacement, and it
+    differs from the frame without displacement."""
+    api = gpu
+    from paper_2407_10707_gb300 import render
+    sc = scene("c1_small")
+    w = api.mlp_tensors(synth.mlp_weights(4), "cuda")
+    st = render.scene_tensors(sc, "cuda")
+    r_mlp = render.Renderer(st, mlp=w)
+    img_mlp = r_mlp.forward().clone()
+    r_mlp.check()
+    dx = api.avatar_mlp(st["avatar"]["xv"], st["avatar"]["pose"].reshape(-1), w)
+    st2 = render.scene_tensors(sc, "cuda")
+    st2["avatar"]["dxv"].copy_(dx)
+    img_fixed = render.Renderer(st2).forward().clone()
+    st3 = render.scene_tensors(sc, "cuda")
+    st3["avatar"]["dxv"].zero_()
+    img_zero = render.Renderer(st3).forward().clone()
+    torch.cuda.synchronize()
+    assert torch.equal(img_mlp, img_fixed)
+    assert float(dx.abs().max()) > 1e-4 and not torch.equal(img_mlp, img_zero)
