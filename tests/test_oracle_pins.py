@@ -934,3 +934,97 @@ def test_mlp_matches_torch_layers_and_closed_forms():
     np.testing.assert_allclose(M.features(x + np.array([1.0, 0, 0]), Bi), M.features(x, Bi), atol=1e-9)
     # the bfloat16 rounding of the kernel's operands: nearest, ties to even
     assert M.bf16(1 + 2.0 ** -8) == 1.0 and M.bf16(1 + 3 * 2.0 ** -8) == 1 + 2.0 ** -6
+
+
+# ---------------------------------------------------------------- densification (App. B, Alg. 1)
+def _torus(n, m, R=1.0, r=0.3):
+    """A closed n x m torus grid, each quad split in two: every vertex has
+    exactly six incident triangles (the valence Alg. 1 assumes)."""
+    i, j = np.meshgrid(np.arange(n), np.arange(m), indexing="ij")
+    th, ph = 2 * np.pi * i / n, 2 * np.pi * j / m
+    xv = np.stack([(R + r * np.cos(ph)) * np.cos(th), (R + r * np.cos(ph)) * np.sin(th), r * np.sin(ph)], -1)
+    idx = lambda a, b: (a % n) * m + (b % m)
+    faces = []
+    for a in range(n):
+        for b in range(m):
+            faces.append((idx(a, b), idx(a + 1, b), idx(a + 1, b + 1)))
+            faces.append((idx(a, b), idx(a + 1, b + 1), idx(a, b + 1)))
+    return xv.reshape(-1, 3), np.array(faces)
+
+
+def test_densify_counts_and_densities():
+    from oracle import densify as DN
+    xv, faces = _torus(12, 10)
+    nv = xv.shape[0]
+    rng = np.random.default_rng(41)
+    G, Kg = 700, 3
+    knn = np.stack([rng.choice(nv, Kg, replace=False) for _ in range(G)])
+    rand = rng.integers(0, 2 ** 32, size=(4000, 3), dtype=np.uint64)
+    out = DN.densify(knn, faces, xv, rand)
+    # D_v equals numpy's bincount of the neighbour lists
+    np.testing.assert_array_equal(out["Dv"], np.bincount(knn.ravel(), minlength=nv))
+    # valence 6 everywhere: the triangle densities sum to the number of Gaussians
+    assert abs(out["df"].sum() - G) < 1e-9
+    # P, N' and the weights against exact rationals
+    from fractions import Fraction
+    P = [max(Fraction(0), Fraction(1) - Fraction(int(s), 6 * Kg))
+         for s in out["Dv"][faces].sum(1)]
+    assert all(Fraction(int(w), 6 * Kg) == p for w, p in zip(out["w"], P))
+    assert out["n_new"] == int(Fraction(0.02) * sum(P) // 1)
+    assert out["ng"].sum() == out["n_new"] and np.all(out["ng"][out["w"] == 0] == 0)
+
+
+def test_densify_uniform_and_saturated_meshes():
+    from oracle import densify as DN
+    xv, faces = _torus(8, 8)
+    nv, Kg = xv.shape[0], 4
+    rand = np.random.default_rng(3).integers(0, 2 ** 32, size=(2000, 3), dtype=np.uint64)
+    # every vertex in S_g of exactly c Gaussians: d_f = 3c / (6 K_g) on every triangle
+    for c in (1, 3, 8):
+        knn = np.stack([np.roll(np.repeat(np.arange(nv), c), -k * c) for k in range(Kg)], 1)  # each vertex c K_g times
+        out = DN.densify(knn, faces, xv, rand)
+        assert np.all(out["Dv"] == c * Kg)
+        np.testing.assert_allclose(out["df"], 3 * c * Kg / (6 * Kg))
+        want = int(np.floor(0.02 * faces.shape[0] * max(0.0, 1.0 - 0.5 * c)))
+        assert out["n_new"] == want
+    # saturated (d_f >= d0 everywhere): nothing is added
+    assert DN.densify(knn, faces, xv, rand)["n_new"] == 0
+
+
+def test_densify_sampling_follows_the_weights():
+    from oracle import densify as DN
+    xv, faces = _torus(6, 6)
+    nv, Kg = xv.shape[0], 2
+    # a single uncovered triangle's vertices: all other vertices saturated
+    hole = faces[5]
+    others = np.setdiff1d(np.arange(nv), hole)
+    knn = np.repeat(others, 12)[:, None].repeat(Kg, 1)
+    rand = np.random.default_rng(8).integers(0, 2 ** 32, size=(20000, 3), dtype=np.uint64)
+    out = DN.densify(knn, faces, xv, rand, p0=50.0)
+    # only triangles touching no covered vertex (the hole's own) get draws
+    assert out["n_new"] > 0 and set(out["tri"]) <= set(np.flatnonzero(out["w"] > 0))
+    # the empirical frequencies match w / W (a chi-square bound at p ~ 1e-6)
+    out = DN.densify(np.arange(nv)[:, None].repeat(Kg, 1)[: nv // 2], faces, xv, rand, p0=200.0)
+    w, n = out["w"].astype(float), out["n_new"]
+    exp = n * w / w.sum()
+    m = exp > 0
+    chi2 = ((out["ng"][m] - exp[m]) ** 2 / exp[m]).sum()
+    dof = m.sum() - 1
+    assert np.all(out["ng"][~m] == 0) and chi2 < dof + 7 * np.sqrt(2 * dof)
+
+
+def test_densify_places_points_uniformly_on_the_triangle():
+    from oracle import densify as DN
+    xv = np.array([[0.0, 0, 0], [1.0, 0, 0], [0.0, 2.0, 0], [5.0, 5.0, 5.0]])
+    faces = np.array([[0, 1, 2], [1, 3, 2]])
+    knn = np.full((6, 1), 3)  # vertex 3 saturates face 1 (S = 6 = 6 K_g): face 0 gets every draw
+    rand = np.random.default_rng(12).integers(0, 2 ** 32, size=(30000, 3), dtype=np.uint64)
+    out = DN.densify(knn, faces, xv, rand, d0=1.0, p0=20000.0)
+    x = out["x"]
+    assert np.all(out["tri"] == 0) and len(x) > 10000
+    # barycentrics of the right triangle (0,0) (1,0) (0,2): u = x, v = y / 2, inside
+    u, v = x[:, 0], x[:, 1] / 2
+    assert np.all(u >= 0) and np.all(v >= 0) and np.all(u + v <= 1) and np.all(x[:, 2] == 0)
+    # uniform on the triangle: mean = centroid, and each half of the area gets half
+    np.testing.assert_allclose(x.mean(0), [1 / 3, 2 / 3, 0], atol=0.01)
+    assert abs((u + v < np.sqrt(0.5)).mean() - 0.5) < 0.01
