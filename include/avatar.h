@@ -614,6 +614,50 @@ size_t avatar_mlp_workspace_size(const avatar_mlp_args *a);
 int avatar_mlp(avatar_ctx *ctx, const avatar_mlp_args *a, void *ws, size_t ws_bytes, avatar_stream_t stream);
 
 /* ------------------------------------------------------------------ */
+/* Density-based densification (App. B, Alg. 1): positions of Gaussians */
+/* to add on under-covered mesh triangles.                              */
+/*   D_v[k] = number of Gaussians with k among their K_g nearest (S_g)   */
+/*   d_f    = (D_v[a] + D_v[b] + D_v[c]) / (6 K_g) per triangle (a,b,c)  */
+/*   P_f    = max(0, d0 - d_f),  N' = floor(p0 sum P)                    */
+/*   N' draws of a triangle with probability P_f / sum P, each placed    */
+/*   uniformly on its triangle of the canonical mesh.                   */
+/* Exact form: d0 6 K_g must be an integer (paper: d0 = 1); the weights */
+/* w_f = max(0, d0 6 K_g - S_f) are integers, W = sum w_f, and          */
+/* N' = floor((p0 W) / (6 K_g)) in IEEE FP64 in that order.  Draw j uses */
+/* three caller-supplied uniform words (rand, [3][capacity]): its       */
+/* triangle is the smallest f whose inclusive prefix sum of w exceeds    */
+/* floor(rand[0][j] W / 2^32); u = (rand[1][j] >> 8) 2^-24, v likewise  */
+/* from rand[2][j], (u, v) -> (1 - u, 1 - v) when u + v > 1 (decided    */
+/* exactly), x = a + u (b - a) + v (c - a).  *count receives N'; when it */
+/* exceeds capacity only the first capacity draws are written and       */
+/* AVATAR_ERR_OVERFLOW is set in *status.  An out-of-range index in knn */
+/* or faces sets AVATAR_ERR_INDEX and is skipped.  Asynchronous; no     */
+/* host synchronisation (the count stays on the device).                 */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int G, Nv, F;          /* Gaussians (>= 0), vertices, triangles (>= 1) */
+    int Kg;                /* |S_g|, 1..64 (paper: 3) */
+    const int32_t *knn;    /* [Kg][G] S_g */
+    const int32_t *faces;  /* [F][3] */
+    const float *xv;       /* [3][Nv] canonical vertices */
+    float d0;              /* density threshold (paper: 1) */
+    double p0;             /* fraction of sum P added per call (paper: 0.02) */
+    int capacity;          /* columns of rand, tri and x */
+    const uint32_t *rand;  /* [3][capacity] uniform 32-bit words */
+    int32_t *count;        /* [1] device: N' */
+    int32_t *tri;          /* [capacity] triangle of each added Gaussian (draw order) */
+    float *x;              /* [3][capacity] canonical positions of the added Gaussians */
+    int32_t *Dv;           /* [Nv] D_v, or NULL (kept in the workspace) */
+    float *df;             /* [F] d_f, or NULL */
+    int32_t *ng;           /* [F] draws per triangle (the multinomial sample), or NULL */
+    int32_t *status;       /* device status word, or NULL */
+} avatar_densify_args;
+
+size_t avatar_densify_workspace_size(const avatar_densify_args *a);
+int avatar_densify(avatar_ctx *ctx, const avatar_densify_args *a, void *ws, size_t ws_bytes,
+                   avatar_stream_t stream);
+
+/* ------------------------------------------------------------------ */
 /* Image loss of Eq. 5 (Sec. 3.3), the 3DGS form:                       */
 /*   L = (1 - lambda) mean |img - target| + lambda (1 - mean SSIM),     */
 /* SSIM per channel and pixel under an 11 x 11 Gaussian window (sigma   */

@@ -68,6 +68,12 @@ class MlpArgs(C.Structure):
                 ("b2", P), ("W3", P), ("b3", P), ("W4", P), ("b4", P), ("dx", P), ("status", P)]
 
 
+class DensifyArgs(C.Structure):
+    _fields_ = [("G", I32), ("Nv", I32), ("F", I32), ("Kg", I32), ("knn", P), ("faces", P), ("xv", P),
+                ("d0", F32), ("p0", C.c_double), ("capacity", I32), ("rand", P), ("count", P), ("tri", P), ("x", P),
+                ("Dv", P), ("df", P), ("ng", P), ("status", P)]
+
+
 class ImageLossArgs(C.Structure):
     _fields_ = [("C", I32), ("H", I32), ("W", I32), ("img", P), ("target", P), ("lam", F32), ("weight", F32),
                 ("accumulate", I32), ("loss", P), ("d_img", P)]
@@ -176,6 +182,8 @@ _SIGNATURES = [
     ("avatar_regularizers", [P, C.POINTER(RegArgs), P, C.c_size_t, P], I32),
     ("avatar_mlp_workspace_size", [C.POINTER(MlpArgs)], C.c_size_t),
     ("avatar_mlp", [P, C.POINTER(MlpArgs), P, C.c_size_t, P], I32),
+    ("avatar_densify_workspace_size", [C.POINTER(DensifyArgs)], C.c_size_t),
+    ("avatar_densify", [P, C.POINTER(DensifyArgs), P, C.c_size_t, P], I32),
     ("avatar_image_loss_workspace_size", [C.POINTER(ImageLossArgs)], C.c_size_t),
     ("avatar_image_loss", [P, C.POINTER(ImageLossArgs), P, C.c_size_t, P], I32),
 ]

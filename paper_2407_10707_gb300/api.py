@@ -555,3 +555,37 @@ def avatar_mlp(x, theta, w, dx=None, ws=None, status=None):
         ws = workspace(need, x.device)
     L.check(lib.avatar_mlp(ctx, C.byref(a), _p(ws), ws.numel(), _stream()), "avatar_mlp")
     return dx
+
+
+# ---------------------------------------------------------------- densification
+def avatar_densify(knn, faces, xv, rand, d0=1.0, p0=0.02, out=None, ws=None, status=None, want_stats=False):
+    """Alg. 1 (App. B): positions of the Gaussians to add.  knn [K_g, G]
+    int32, faces [F, 3] int32, xv [3, N_v], rand [3, capacity] uniform words
+    (int32 or uint32 storage).  Returns dict(count [1] device (N'), tri
+    [capacity], x [3, capacity]) and, with want_stats, Dv, df, ng."""
+    lib = L.load()
+    ctx = context()
+    dev = xv.device
+    cap = rand.shape[1]
+    a = L.DensifyArgs()
+    a.G, a.Nv, a.F, a.Kg = knn.shape[1], xv.shape[1], faces.shape[0], knn.shape[0]
+    a.knn, a.faces, a.xv = _p(knn), _p(faces), _p(xv)
+    a.d0, a.p0, a.capacity = float(d0), float(p0), cap
+    rand = rand.contiguous()
+    if out is None:
+        out = dict(count=torch.zeros(1, dtype=torch.int32, device=dev),
+                   tri=torch.empty(cap, dtype=torch.int32, device=dev),
+                   x=torch.empty(3, cap, dtype=torch.float32, device=dev))
+        if want_stats:
+            out.update(Dv=torch.empty(a.Nv, dtype=torch.int32, device=dev),
+                       df=torch.empty(a.F, dtype=torch.float32, device=dev),
+                       ng=torch.empty(a.F, dtype=torch.int32, device=dev))
+    a.rand, a.count, a.tri, a.x = _p(rand), _p(out["count"]), _p(out["tri"]), _p(out["x"])
+    a.Dv, a.df, a.ng, a.status = _p(out.get("Dv")), _p(out.get("df")), _p(out.get("ng")), _p(status)
+    need = lib.avatar_densify_workspace_size(C.byref(a))
+    if need == 0:
+        raise L.AvatarError(1, "avatar_densify_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    L.check(lib.avatar_densify(ctx, C.byref(a), _p(ws), ws.numel(), _stream()), "avatar_densify")
+    return out

@@ -582,3 +582,28 @@ class BatchRenderer:
 
     def check(self):
         api.raise_on_status(self.status, "render_batch")
+
+
+def densify(st, rand, d0=1.0, p0=0.02, logscale=-4.0, opacity=0.5, status=None):
+    """Alg. 1 (App. B) on the avatar of st: appends the Gaussians it places
+    (positions from the device; log-scale `logscale` on every axis, the
+    identity rotation, opacity `opacity`) and recomputes every Gaussian's K_g
+    nearest vertices (S_g of Eq. 1).  rand: [3, capacity] uniform 32-bit words.
+    Returns the number added.  A training-control step (the paper runs it every
+    100 iterations): it reads the count back to grow the tensors, and the
+    renderers built on st must be rebuilt."""
+    t = st["avatar"]
+    out = api.avatar_densify(t["knn"], t["faces"], t["xv"], rand, d0, p0, status=status)
+    n = min(int(out["count"].item()), rand.shape[1])
+    if n == 0:
+        return 0
+    dev = t["xg"].device
+    t["xg"] = torch.cat([t["xg"], out["x"][:, :n]], 1).contiguous()
+    t["logscale"] = torch.cat([t["logscale"], torch.full((3, n), logscale, dtype=t["logscale"].dtype, device=dev)],
+                              1).contiguous()
+    q = torch.zeros(4, n, dtype=t["quat"].dtype, device=dev)
+    q[0] = 1.0
+    t["quat"] = torch.cat([t["quat"], q], 1).contiguous()
+    t["opacity"] = torch.cat([t["opacity"], torch.full((n,), opacity, dtype=t["opacity"].dtype, device=dev)])
+    t["knn"] = api.avatar_knn(t["xg"], t["xv"], t["knn"].shape[0], status=status)
+    return n
