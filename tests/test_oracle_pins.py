@@ -1028,3 +1028,37 @@ def test_densify_places_points_uniformly_on_the_triangle():
     # uniform on the triangle: mean = centroid, and each half of the area gets half
     np.testing.assert_allclose(x.mean(0), [1 / 3, 2 / 3, 0], atol=0.01)
     assert abs((u + v < np.sqrt(0.5)).mean() - 0.5) < 0.01
+
+
+# ---------------------------------------------------------------- Adam
+def test_adam_matches_torch_and_closed_forms():
+    from oracle import adam as AD
+    rng = np.random.default_rng(51)
+    p0 = rng.normal(size=300)
+    gs = [rng.normal(size=300) * 10.0 ** rng.uniform(-3, 1) for _ in range(6)]
+    # torch.optim.Adam in FP64, same hyper-parameters
+    tp = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=0.01, betas=(0.9, 0.999), eps=1e-15)
+    p, m, v = p0.copy(), np.zeros(300), np.zeros(300)
+    for t, g in enumerate(gs, 1):
+        tp.grad = torch.tensor(g)
+        opt.step()
+        p, m, v = AD.step(p, g, m, v, t, 0.01)
+        np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-13, atol=1e-15)
+    # first step: m_hat = g, v_hat = g^2, so the step is lr g / (|g| + eps), about lr sign(g)
+    g = rng.normal(size=50)
+    p1, _, _ = AD.step(np.zeros(50), g, np.zeros(50), np.zeros(50), 1, 0.003)
+    np.testing.assert_allclose(p1, -0.003 * g / (np.abs(g) + 1e-15), rtol=1e-13)
+    # a constant gradient keeps that step for every t (the bias corrections cancel)
+    p, m, v = np.zeros(4), np.zeros(4), np.zeros(4)
+    g = np.array([2.0, -0.5, 1e-3, -7.0])
+    for t in range(1, 30):
+        q, m, v = AD.step(p, g, m, v, t, 0.1)
+        np.testing.assert_allclose(q - p, -0.1 * g / (np.abs(g) + 1e-15), rtol=1e-10)
+        p = q
+    # bfloat16 storage: the result is a bfloat16 value nearest to the FP64 update
+    # (1 - 3 2^-9 lies halfway between 1 - 2^-7 and 1 - 2^-8: ties to the even 1 - 2^-7;
+    #  1 + 3 2^-9 is nearer 1 + 2^-7 than 1)
+    pb, _, _ = AD.step(np.full(3, 1.0), np.array([1.0, -1.0, 0.0]), np.zeros(3), np.zeros(3), 1, 3 * 2.0 ** -9,
+                       bf16=True)
+    np.testing.assert_array_equal(pb, [1.0 - 2.0 ** -7, 1.0 + 2.0 ** -7, 1.0])
