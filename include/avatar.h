@@ -658,6 +658,36 @@ int avatar_densify(avatar_ctx *ctx, const avatar_densify_args *a, void *ws, size
                    avatar_stream_t stream);
 
 /* ------------------------------------------------------------------ */
+/* Adam update of the trainable parameters (Kingma and Ba; the          */
+/* optimiser of the 3DGS training the paper follows, which states no    */
+/* update rule of its own).  Step t (>= 1) of every group in one launch: */
+/*   m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2                   */
+/*   p <- p - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)         */
+/* in FP32; a BF16 parameter is updated in FP32 and rounded back to      */
+/* nearest even.  m and v (FP32, zero before step 1) and p are updated   */
+/* in place.  Asynchronous; capturable.                                  */
+/* ------------------------------------------------------------------ */
+#define AVATAR_ADAM_MAX_GROUPS 16
+
+typedef struct {
+    int64_t n;             /* elements */
+    void *param;           /* [n] AVATAR_DTYPE_F32 or _BF16 (dtype) */
+    int dtype;
+    const float *grad;     /* [n] */
+    float *m, *v;          /* [n] moments */
+    float lr;              /* learning rate of the group */
+} avatar_adam_group;
+
+typedef struct {
+    int n_groups;          /* 0..AVATAR_ADAM_MAX_GROUPS */
+    avatar_adam_group group[AVATAR_ADAM_MAX_GROUPS];
+    float beta1, beta2, eps;  /* 3DGS: 0.9, 0.999, 1e-15 */
+    int step;              /* t >= 1 */
+} avatar_adam_args;
+
+int avatar_adam(avatar_ctx *ctx, const avatar_adam_args *a, avatar_stream_t stream);
+
+/* ------------------------------------------------------------------ */
 /* Image loss of Eq. 5 (Sec. 3.3), the 3DGS form:                       */
 /*   L = (1 - lambda) mean |img - target| + lambda (1 - mean SSIM),     */
 /* SSIM per channel and pixel under an 11 x 11 Gaussian window (sigma   */

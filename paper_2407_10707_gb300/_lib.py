@@ -74,6 +74,18 @@ class DensifyArgs(C.Structure):
                 ("Dv", P), ("df", P), ("ng", P), ("status", P)]
 
 
+ADAM_MAX_GROUPS = 16
+
+
+class AdamGroup(C.Structure):
+    _fields_ = [("n", C.c_int64), ("param", P), ("dtype", I32), ("grad", P), ("m", P), ("v", P), ("lr", F32)]
+
+
+class AdamArgs(C.Structure):
+    _fields_ = [("n_groups", I32), ("group", AdamGroup * ADAM_MAX_GROUPS), ("beta1", F32), ("beta2", F32),
+                ("eps", F32), ("step", I32)]
+
+
 class ImageLossArgs(C.Structure):
     _fields_ = [("C", I32), ("H", I32), ("W", I32), ("img", P), ("target", P), ("lam", F32), ("weight", F32),
                 ("accumulate", I32), ("loss", P), ("d_img", P)]
@@ -184,6 +196,7 @@ _SIGNATURES = [
     ("avatar_mlp", [P, C.POINTER(MlpArgs), P, C.c_size_t, P], I32),
     ("avatar_densify_workspace_size", [C.POINTER(DensifyArgs)], C.c_size_t),
     ("avatar_densify", [P, C.POINTER(DensifyArgs), P, C.c_size_t, P], I32),
+    ("avatar_adam", [P, C.POINTER(AdamArgs), P], I32),
     ("avatar_image_loss_workspace_size", [C.POINTER(ImageLossArgs)], C.c_size_t),
     ("avatar_image_loss", [P, C.POINTER(ImageLossArgs), P, C.c_size_t, P], I32),
 ]

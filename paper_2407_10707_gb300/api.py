@@ -589,3 +589,42 @@ def avatar_densify(knn, faces, xv, rand, d0=1.0, p0=0.02, out=None, ws=None, sta
         ws = workspace(need, dev)
     L.check(lib.avatar_densify(ctx, C.byref(a), _p(ws), ws.numel(), _stream()), "avatar_densify")
     return out
+
+
+# ---------------------------------------------------------------- Adam
+def avatar_adam(groups, step, beta1=0.9, beta2=0.999, eps=1e-15):
+    """One Adam step over groups = [(param, grad, m, v, lr), ...] (contiguous
+    tensors of equal element count; param float32 or bfloat16, the rest
+    float32), updated in place; step t >= 1."""
+    lib = L.load()
+    ctx = context()
+    if len(groups) > L.ADAM_MAX_GROUPS:
+        raise ValueError(f"at most {L.ADAM_MAX_GROUPS} groups")
+    a = L.AdamArgs()
+    a.n_groups, a.beta1, a.beta2, a.eps, a.step = len(groups), beta1, beta2, eps, int(step)
+    for k, (p, g, m, v, lr) in enumerate(groups):
+        for x in (p, g, m, v):
+            if not x.is_contiguous() or x.numel() != p.numel():
+                raise ValueError("Adam tensors must be contiguous and of one size")
+        gr = a.group[k]
+        gr.n, gr.param, gr.grad, gr.m, gr.v, gr.lr = p.numel(), _p(p), _p(g), _p(m), _p(v), float(lr)
+        gr.dtype = _dtype_code(p)
+    L.check(lib.avatar_adam(ctx, C.byref(a), _stream()), "avatar_adam")
+
+
+class Adam:
+    """Adam state (FP32 moments) for named parameter tensors; step(grads)
+    launches one fused update of every group."""
+
+    def __init__(self, params, lr, beta1=0.9, beta2=0.999, eps=1e-15):
+        self.params = params          # name -> tensor, updated in place
+        self.lr = dict(lr)            # name -> learning rate
+        self.b = (beta1, beta2, eps)
+        self.m = {k: torch.zeros(p.shape, dtype=torch.float32, device=p.device) for k, p in params.items()}
+        self.v = {k: torch.zeros(p.shape, dtype=torch.float32, device=p.device) for k, p in params.items()}
+        self.t = 0
+
+    def step(self, grads):
+        self.t += 1
+        groups = [(self.params[k], grads[k], self.m[k], self.v[k], self.lr[k]) for k in self.params]
+        avatar_adam(groups, self.t, *self.b)

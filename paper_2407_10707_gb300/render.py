@@ -204,11 +204,21 @@ class Renderer:
         api.raise_on_status(self.status, "render")
 
 
+# Adam learning rates per parameter group: 3DGS's defaults for the Gaussians
+# (position, log-scale, rotation, opacity) and its colour rate for the
+# materials; the LBS weights and the light are not in 3DGS (the paper gives no
+# rates but the editing position rate 1.6e-6 of Sec. 4).
+ADAM_LR = dict(xg=1.6e-4, logscale=5e-3, quat=1e-3, opacity=5e-2, av=2.5e-3, rv=2.5e-3, pv=2.5e-3, wv=1e-3,
+               L=1e-2)
+
+
 class TrainStep(Renderer):
-    """Forward frame + L1 loss + backward through every stage."""
+    """Forward frame + image loss + backward through every stage; update()
+    applies one fused Adam step to every trainable tensor (adam=True for
+    ADAM_LR, or a dict of rates)."""
 
     def __init__(self, st, target, tile=16, pair_capacity=None, vis_cull_back=True, shade_tc=False,
-                 visibility="depth", knn_v=None, rebind=False, ssim_weight=0.2, regularize=False):
+                 visibility="depth", knn_v=None, rebind=False, ssim_weight=0.2, regularize=False, adam=None):
         # image loss of Eq. 5: (1 - ssim_weight) L1 + ssim_weight D-SSIM (the paper's 0.2);
         # regularize adds the regularisers of Sec. 3.3 (needs knn_v, the filters' S_v)
         self.target = target
@@ -233,6 +243,12 @@ class TrainStep(Renderer):
         self.g_skin = {k: torch.empty_like(t[k], dtype=torch.float32)
                        for k in ("xg", "logscale", "quat", "wv", "av", "rv", "pv")}
         self._bwd_ws = None
+        self.opt = None
+        if adam:
+            lr = ADAM_LR if adam is True else adam
+            params = {k: t[k] for k in ("xg", "logscale", "quat", "opacity", "wv", "av", "rv", "pv")}
+            params["L"] = st["light"]["L"]
+            self.opt = api.Adam(params, lr)
         self.step()
         torch.cuda.synchronize()
 
@@ -297,6 +313,10 @@ class TrainStep(Renderer):
         self.forward()
         self.backward()
         return self.loss
+
+    def update(self):
+        """One Adam step on the gradients of the last step()."""
+        self.opt.step(self.grads())
 
     def capture(self):
         s = torch.cuda.Stream()
