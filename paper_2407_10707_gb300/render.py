@@ -205,10 +205,12 @@ class Renderer:
 
 
 # Adam learning rates per parameter group: 3DGS's defaults for the Gaussians
-# (position, log-scale, rotation, opacity) and its colour rate for the
-# materials; the LBS weights and the light are not in 3DGS (the paper gives no
-# rates but the editing position rate 1.6e-6 of Sec. 4).
-ADAM_LR = dict(xg=1.6e-4, logscale=5e-3, quat=1e-3, opacity=5e-2, av=2.5e-3, rv=2.5e-3, pv=2.5e-3, wv=1e-3,
+# (position, log-scale, rotation) and its colour rate for the materials; 3DGS
+# steps opacity as a logit at 0.05, here it is stored directly, so the rate is
+# scaled by the logistic slope at 1/2 (1/4); the LBS weights and the light are
+# not in 3DGS (the paper gives no rates but the editing position rate 1.6e-6
+# of Sec. 4).
+ADAM_LR = dict(xg=1.6e-4, logscale=5e-3, quat=1e-3, opacity=1.25e-2, av=2.5e-3, rv=2.5e-3, pv=2.5e-3, wv=1e-3,
                L=1e-2)
 
 
