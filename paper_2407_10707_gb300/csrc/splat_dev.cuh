@@ -717,26 +717,18 @@ __device__ __forceinline__ void blend_backward_tile(int2 rg, const int32_t *__re
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-                g_col0 = warp_sum(g_col0);
-                g_col1 = warp_sum(g_col1);
-                g_col2 = warp_sum(g_col2);
-                g_op = warp_sum(g_op);
-                g_mx = warp_sum(g_mx);
-                g_my = warp_sum(g_my);
-                g_ca = warp_sum(g_ca);
-                g_cb = warp_sum(g_cb);
-                g_cc = warp_sum(g_cc);
-                if (lane == 0) {
+                // the nine sums at once; lane 2i then adds the total of value i
+                const float v[16] = {g_col0, g_col1, g_col2, g_op, g_mx, g_my, g_ca, g_cb, g_cc,
+                                     0.f,    0.f,    0.f,    0.f,  0.f,  0.f,  0.f};
+                const float tot = warp_reduce_scatter16(v);
+                const int vi = lane >> 1;
+                if (!(lane & 1) && vi < 9) {
                     const size_t g = (size_t)sg[sj];
-                    atomicAdd(d_color + g, g_col0);
-                    atomicAdd(d_color + cs + g, g_col1);
-                    atomicAdd(d_color + 2 * cs + g, g_col2);
-                    atomicAdd(d_opacity + g, g_op / c.w);
-                    atomicAdd(d_mean2d + g, g_mx);
-                    atomicAdd(d_mean2d + cs + g, g_my);
-                    atomicAdd(d_conic + g, g_ca);
-                    atomicAdd(d_conic + cs + g, g_cb);
-                    atomicAdd(d_conic + 2 * cs + g, g_cc);
+                    float *dst = vi < 3   ? d_color + (size_t)vi * cs
+                                 : vi == 3 ? d_opacity
+                                 : vi < 6  ? d_mean2d + (size_t)(vi - 4) * cs
+                                           : d_conic + (size_t)(vi - 6) * cs;
+                    atomicAdd(dst + g, vi == 3 ? tot / c.w : tot);
                 }
             }
         }
