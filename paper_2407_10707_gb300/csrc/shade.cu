@@ -34,6 +34,7 @@ struct ShadeBatch {
     int B, V;
     const int32_t *view_pose;  // [V] or NULL
     const float *view_cc;      // [V][3] or NULL (then args.cam_center)
+    int dB_copies;             // backward: light-gradient accumulator copies (1, or one per warp)
 };
 
 struct ShadeSlot {
@@ -260,7 +261,7 @@ template <int K, bool SOFT>
 __global__ void __launch_bounds__(SHADE_THREADS)
 shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr, ShadeBatch sb)
 {
-    extern __shared__ float4 lsm[];  // [NL] (w, A) ; [NL] (L*A) ; [NL][3] dL/dB accumulators
+    extern __shared__ float4 lsm[];  // [NL] (w, A) ; [NL] (L*A) ; per warp [NL] dL/dB accumulators (x, y, z, -)
     const int NL = s.NL, G = s.G;
     const ShadeSlot t = shade_slot(s, sb);
     const int OW = (NL + 31) / 32;
@@ -278,14 +279,21 @@ shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr, ShadeBatch sb)
     gr.d_ubar += t.oy;
     gr.d_light_L += (size_t)t.p * NL * 3;
     float4 *lw = lsm, *lb = lsm + NL;
-    float *dB = reinterpret_cast<float *>(lsm + 2 * NL);
+    // With one accumulator copy per warp, each warp adds dL/dB of the lights its
+    // lanes own (light k belongs to lane k % 32 in every warp) to its own slots
+    // without atomics, and the copies are summed once at the end; with a single
+    // copy (many lights) the warps add with shared-memory atomics.
+    const int copies = sb.dB_copies;
+    const bool private_dB = copies == (int)(blockDim.x >> 5);
+    float4 *dBall = lsm + 2 * NL;
+    float4 *dB = dBall + (size_t)(private_dB ? (threadIdx.x >> 5) : 0) * NL;
     for (int k = threadIdx.x; k < NL; k += blockDim.x) {
         float A = __ldg(s.light_A + k);
         lw[k] = make_float4(__ldg(s.light_w + 3 * k), __ldg(s.light_w + 3 * k + 1), __ldg(s.light_w + 3 * k + 2), A);
         lb[k] = make_float4(__ldg(light_L + 3 * k) * A, __ldg(light_L + 3 * k + 1) * A, __ldg(light_L + 3 * k + 2) * A,
                             0.f);
-        dB[3 * k] = dB[3 * k + 1] = dB[3 * k + 2] = 0.f;
     }
+    for (int i = threadIdx.x; i < copies * NL; i += blockDim.x) dBall[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const unsigned bit = 1u << lane;
@@ -394,25 +402,38 @@ shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr, ShadeBatch sb)
             dnv2 = fmaf(dci, w.z, dnv2);
             // dL/dB_kc = dLo_c vis ci (a_c/pi + p fs)
             float ps = q.p * fs;
-            atomicAdd(dB + 3 * k, dLo[0] * fw * (ia0 + ps));
-            atomicAdd(dB + 3 * k + 1, dLo[1] * fw * (ia1 + ps));
-            atomicAdd(dB + 3 * k + 2, dLo[2] * fw * (ia2 + ps));
+            if (private_dB) {
+                float4 acc = dB[k];
+                acc.x = fmaf(dLo[0] * fw, ia0 + ps, acc.x);
+                acc.y = fmaf(dLo[1] * fw, ia1 + ps, acc.y);
+                acc.z = fmaf(dLo[2] * fw, ia2 + ps, acc.z);
+                dB[k] = acc;
+            } else {
+                atomicAdd(&dB[k].x, dLo[0] * fw * (ia0 + ps));
+                atomicAdd(&dB[k].y, dLo[1] * fw * (ia1 + ps));
+                atomicAdd(&dB[k].z, dLo[2] * fw * (ia2 + ps));
+            }
         }
-        E0 = warp_sum(E0);
-        E1 = warp_sum(E1);
-        E2 = warp_sum(E2);
-        dnv0 = warp_sum(dnv0);
-        dnv1 = warp_sum(dnv1);
-        dnv2 = warp_sum(dnv2);
-        dwv0 = warp_sum(dwv0);
-        dwv1 = warp_sum(dwv1);
-        dwv2 = warp_sum(dwv2);
-        dco = warp_sum(dco);
-        da2 = warp_sum(da2);
-        dkk = warp_sum(dkk);
-        dp = warp_sum(dp);
+        {
+            // the 13 + K sums: sixteen at once by recursive halving, gathered to lane 0
+            constexpr int NV = 13 + K;
+            float vals[NV] = {E0, E1, E2, dnv0, dnv1, dnv2, dwv0, dwv1, dwv2, dco, da2, dkk, dp};
 #pragma unroll
-        for (int j = 0; j < K; ++j) dub[j] = warp_sum(dub[j]);
+            for (int j = 0; j < K; ++j) vals[13 + j] = dub[j];
+            float v16[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v16[i] = i < NV ? vals[i] : 0.f;
+            const float tot = warp_reduce_scatter16(v16);
+#pragma unroll
+            for (int i = 0; i < NV; ++i)
+                vals[i] = i < 16 ? __shfl_sync(0xffffffffu, tot, 2 * i) : warp_sum(vals[i]);
+            E0 = vals[0], E1 = vals[1], E2 = vals[2];
+            dnv0 = vals[3], dnv1 = vals[4], dnv2 = vals[5];
+            dwv0 = vals[6], dwv1 = vals[7], dwv2 = vals[8];
+            dco = vals[9], da2 = vals[10], dkk = vals[11], dp = vals[12];
+#pragma unroll
+            for (int j = 0; j < K; ++j) dub[j] = vals[13 + j];
+        }
         if (lane == 0) {
             float dn[3] = {dnv0 + dco * f.wo[0], dnv1 + dco * f.wo[1], dnv2 + dco * f.wo[2]};
             float dw[3] = {dwv0 + dco * q.n[0], dwv1 + dco * q.n[1], dwv2 + dco * q.n[2]};
@@ -434,13 +455,26 @@ shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr, ShadeBatch sb)
     }
     __syncthreads();
     for (int k = threadIdx.x; k < NL; k += blockDim.x) {
-        float A = lw[k].w;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float v = dB[3 * k + c];
-            if (v != 0.f) atomicAdd(gr.d_light_L + 3 * k + c, v * A);
+        const float A = lw[k].w;
+        float4 v = dBall[k];
+        for (int w = 1; w < copies; ++w) {
+            const float4 u = dBall[(size_t)w * NL + k];
+            v.x += u.x;
+            v.y += u.y;
+            v.z += u.z;
         }
+        if (v.x != 0.f) atomicAdd(gr.d_light_L + 3 * k, v.x * A);
+        if (v.y != 0.f) atomicAdd(gr.d_light_L + 3 * k + 1, v.y * A);
+        if (v.z != 0.f) atomicAdd(gr.d_light_L + 3 * k + 2, v.z * A);
     }
+}
+
+// Light-gradient accumulator copies of the backward: one per warp when they
+// fit in shared memory beside the light tables, else one shared copy.
+int bwd_copies(const avatar_ctx *ctx, int NL)
+{
+    const size_t per_warp = (size_t)(2 + SHADE_THREADS / 32) * NL * sizeof(float4);
+    return per_warp <= (size_t)ctx->max_smem_optin ? SHADE_THREADS / 32 : 1;
 }
 
 template <int K>
@@ -499,7 +533,7 @@ extern "C" int avatar_shade(avatar_ctx *ctx, const avatar_shade_args *a, avatar_
     size_t smem = (size_t)2 * a->NL * sizeof(float4);
     int grid = shade_grid(ctx, a->G);
     cudaStream_t st = (cudaStream_t)stream;
-    const ShadeBatch sb{1, 1, nullptr, nullptr};
+    const ShadeBatch sb{1, 1, nullptr, nullptr, 1};
     switch (a->K) {
         case 1: return launch_shade<1>(*a, sb, grid, smem, st);
         case 2: return launch_shade<2>(*a, sb, grid, smem, st);
@@ -524,9 +558,10 @@ extern "C" int avatar_shade_backward(avatar_ctx *ctx, const avatar_shade_args *a
     if (cudaMemsetAsync(g->d_light_L, 0, (size_t)a->NL * 3 * sizeof(float), st) != cudaSuccess)
         return AVATAR_ERR_CUDA;
     if (a->G == 0) return AVATAR_OK;
-    size_t smem = (size_t)2 * a->NL * sizeof(float4) + (size_t)3 * a->NL * sizeof(float);
+    const int copies = bwd_copies(ctx, a->NL);
+    size_t smem = (size_t)(2 + copies) * a->NL * sizeof(float4);
     int grid = shade_grid(ctx, a->G);
-    const ShadeBatch sb{1, 1, nullptr, nullptr};
+    const ShadeBatch sb{1, 1, nullptr, nullptr, copies};
     switch (a->K) {
         case 1: return launch_shade_bwd<1>(*a, *g, sb, grid, smem, st);
         case 2: return launch_shade_bwd<2>(*a, *g, sb, grid, smem, st);
@@ -547,7 +582,7 @@ int av_shade_batch(avatar_ctx *ctx, const avatar_shade_args *a, int B, int V, co
     if (a->G == 0) return AVATAR_OK;
     size_t smem = (size_t)2 * a->NL * sizeof(float4);
     int grid = shade_grid(ctx, a->G);
-    const ShadeBatch sb{B, V, view_pose, view_cc};
+    const ShadeBatch sb{B, V, view_pose, view_cc, 1};
     switch (a->K) {
         case 1: return launch_shade<1>(*a, sb, grid, smem, st);
         case 2: return launch_shade<2>(*a, sb, grid, smem, st);
@@ -571,9 +606,10 @@ int av_shade_batch_backward(avatar_ctx *ctx, const avatar_shade_args *a, const a
     if (cudaMemsetAsync(g->d_light_L, 0, (size_t)B * a->NL * 3 * sizeof(float), st) != cudaSuccess)
         return AVATAR_ERR_CUDA;
     if (a->G == 0) return AVATAR_OK;
-    size_t smem = (size_t)2 * a->NL * sizeof(float4) + (size_t)3 * a->NL * sizeof(float);
+    const int copies = bwd_copies(ctx, a->NL);
+    size_t smem = (size_t)(2 + copies) * a->NL * sizeof(float4);
     int grid = shade_grid(ctx, a->G);
-    const ShadeBatch sb{B, V, view_pose, view_cc};
+    const ShadeBatch sb{B, V, view_pose, view_cc, copies};
     switch (a->K) {
         case 1: return launch_shade_bwd<1>(*a, *g, sb, grid, smem, st);
         case 2: return launch_shade_bwd<2>(*a, *g, sb, grid, smem, st);
