@@ -511,10 +511,15 @@ __device__ __forceinline__ void blend_tile(int2 rg, const int32_t *__restrict__ 
                                            int32_t *__restrict__ n_last)
 {
     constexpr int NTH = TS * TS / PPT;
-    __shared__ float4 s0[NTH];
-    __shared__ float4 s1[NTH];
-    __shared__ float4 s2[NTH];
-    __shared__ unsigned smask[NTH];
+    // Two record buffers where they fit in 48 KB of static shared memory: the
+    // next batch's records are fetched into registers before the current batch
+    // is walked and stored into the other buffer after it, so one barrier per
+    // batch remains and the fetch latency overlaps the walk.
+    constexpr int NBUF = NTH <= 256 ? 2 : 1;
+    __shared__ float4 s0[NBUF][NTH];
+    __shared__ float4 s1[NBUF][NTH];
+    __shared__ float4 s2[NBUF][NTH];
+    __shared__ unsigned smask[NBUF][NTH];
     const int tid = threadIdx.x;
     const unsigned wbit = 1u << (tid >> 5);
     const BoxMap<TS, PPT> box(tx, ty, tid >> 5);
@@ -534,70 +539,113 @@ __device__ __forceinline__ void blend_tile(int2 rg, const int32_t *__restrict__ 
         done = done && !live[k];
     }
     const int n = rg.y - rg.x;
-    for (int base = 0; base < n; base += NTH) {
-        if (__syncthreads_count(done) == NTH) break;
-        int idx = base + tid;
-        if (idx < n) {
-            int g = pair_gauss[rg.x + idx];
-            s0[tid] = rec0[g];
-            float4 r1 = rec1[g];
-            s1[tid] = r1;
-            s2[tid] = rec2[g];
-            smask[tid] = BoxMap<TS, PPT>::mask(tx, ty, r1.z, r1.w);
-        }
-        __syncthreads();
-        if (!done) {
-            const int m = min(NTH, n - base);
-            // one Gaussian's contribution to pixel k (the front-to-back step)
-            auto step = [&](int j, int k, float l2a) {
-                if (l2a < LOG2_ALPHA_MIN) return;
-                float alpha = fminf(0.99f, exp2f(l2a));
-                float test_T = T[k] * (1.f - alpha);
-                if (test_T < T_MIN) {
-                    live[k] = false;
-                    return;
-                }
-                float4 c = s2[j];
-                float wgt = alpha * T[k];
-                C0[k] = fmaf(c.x, wgt, C0[k]);
-                C1[k] = fmaf(c.y, wgt, C1[k]);
-                C2[k] = fmaf(c.z, wgt, C2[k]);
-                T[k] = test_T;
-                last[k] = base + j + 1;
-            };
-            auto l2alpha = [&](int j, int k) {
-                const float4 r0 = s0[j];
-                const float4 r1 = s1[j];
-                float dx = fx[k] - r0.x, dy = fy[k] - r0.y;
-                return fmaf(fmaf(r0.z, dx, r0.w * dy), dx, fmaf(r1.x * dy, dy, r1.y));
-            };
-            int j = 0;
-            // two Gaussians per iteration: both exponents are independent of T
-            for (; j + 1 < m; j += 2) {
-                const bool m0 = smask[j] & wbit, m1 = smask[j + 1] & wbit;  // warp-uniform
-                if (!(m0 || m1)) continue;
-#pragma unroll
-                for (int k = 0; k < PPT; ++k) {
-                    if (!live[k]) continue;
-                    float a0 = m0 ? l2alpha(j, k) : -1e30f;
-                    float a1 = m1 ? l2alpha(j + 1, k) : -1e30f;
-                    step(j, k, a0);
-                    if (live[k]) step(j + 1, k, a1);
-                }
-                bool any = false;
-#pragma unroll
-                for (int k = 0; k < PPT; ++k) any = any || live[k];
-                if (!any) break;
+    // walk the m records of buffer b, which start at list position base
+    auto walk = [&](int b, int base, int m) {
+        // one Gaussian's contribution to pixel k (the front-to-back step)
+        auto step = [&](int j, int k, float l2a) {
+            if (l2a < LOG2_ALPHA_MIN) return;
+            float alpha = fminf(0.99f, exp2f(l2a));
+            float test_T = T[k] * (1.f - alpha);
+            if (test_T < T_MIN) {
+                live[k] = false;
+                return;
             }
-            if (j < m && (smask[j] & wbit)) {
+            float4 c = s2[b][j];
+            float wgt = alpha * T[k];
+            C0[k] = fmaf(c.x, wgt, C0[k]);
+            C1[k] = fmaf(c.y, wgt, C1[k]);
+            C2[k] = fmaf(c.z, wgt, C2[k]);
+            T[k] = test_T;
+            last[k] = base + j + 1;
+        };
+        auto l2alpha = [&](int j, int k) {
+            const float4 r0 = s0[b][j];
+            const float4 r1 = s1[b][j];
+            float dx = fx[k] - r0.x, dy = fy[k] - r0.y;
+            return fmaf(fmaf(r0.z, dx, r0.w * dy), dx, fmaf(r1.x * dy, dy, r1.y));
+        };
+        int j = 0;
+        // two Gaussians per iteration: both exponents are independent of T
+        for (; j + 1 < m; j += 2) {
+            const bool m0 = smask[b][j] & wbit, m1 = smask[b][j + 1] & wbit;  // warp-uniform
+            if (!(m0 || m1)) continue;
 #pragma unroll
-                for (int k = 0; k < PPT; ++k)
-                    if (live[k]) step(j, k, l2alpha(j, k));
+            for (int k = 0; k < PPT; ++k) {
+                if (!live[k]) continue;
+                float a0 = m0 ? l2alpha(j, k) : -1e30f;
+                float a1 = m1 ? l2alpha(j + 1, k) : -1e30f;
+                step(j, k, a0);
+                if (live[k]) step(j + 1, k, a1);
             }
             bool any = false;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) any = any || live[k];
-            if (!any) done = true;
+            if (!any) break;
+        }
+        if (j < m && (smask[b][j] & wbit)) {
+#pragma unroll
+            for (int k = 0; k < PPT; ++k)
+                if (live[k]) step(j, k, l2alpha(j, k));
+        }
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) any = any || live[k];
+        if (!any) done = true;
+    };
+    if constexpr (NBUF == 2) {
+        // the records go to shared memory by asynchronous copies; only the
+        // rect (for the warp mask) passes through registers
+        float2 prect = make_float2(0.f, 0.f);
+        bool have = false;
+        auto fetch = [&](int base, int b) {
+            const int idx = base + tid;
+            have = idx < n;
+            if (have) {
+                const int g = pair_gauss[rg.x + idx];
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s0[b][tid])),
+                             "l"(rec0 + g)
+                             : "memory");
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s1[b][tid])),
+                             "l"(rec1 + g)
+                             : "memory");
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s2[b][tid])),
+                             "l"(rec2 + g)
+                             : "memory");
+                prect = __ldg(reinterpret_cast<const float2 *>(rec1 + g) + 1);
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        auto stash = [&](int b) {
+            if (have) smask[b][tid] = BoxMap<TS, PPT>::mask(tx, ty, prect.x, prect.y);
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        };
+        if (n > 0) {
+            fetch(0, 0);
+            stash(0);
+        }
+        int b = 0;
+        for (int base = 0; base < n; base += NTH, b ^= 1) {
+            // batch b is in place, and every warp is done with buffer b ^ 1
+            if (__syncthreads_count(done) == NTH) break;
+            const bool more = base + NTH < n;
+            if (more) fetch(base + NTH, b ^ 1);
+            if (!done) walk(b, base, min(NTH, n - base));
+            if (more) stash(b ^ 1);
+        }
+    } else {
+        for (int base = 0; base < n; base += NTH) {
+            if (__syncthreads_count(done) == NTH) break;
+            int idx = base + tid;
+            if (idx < n) {
+                int g = pair_gauss[rg.x + idx];
+                s0[0][tid] = rec0[g];
+                float4 r1 = rec1[g];
+                s1[0][tid] = r1;
+                s2[0][tid] = rec2[g];
+                smask[0][tid] = BoxMap<TS, PPT>::mask(tx, ty, r1.z, r1.w);
+            }
+            __syncthreads();
+            if (!done) walk(0, base, min(NTH, n - base));
         }
     }
 #pragma unroll
