@@ -678,11 +678,14 @@ __device__ __forceinline__ void blend_backward_tile(int2 rg, const int32_t *__re
 {
     constexpr int NTH = TS * TS / PPT;
     constexpr float LN2 = 0.6931471805599453f;
-    __shared__ float4 s0[NTH];
-    __shared__ float4 s1[NTH];
-    __shared__ float4 s2[NTH];
-    __shared__ int sg[NTH];
-    __shared__ unsigned smask[NTH];
+    // double-buffered record batches (asynchronous copies) where they fit in
+    // 48 KB of static shared memory, as in the forward
+    constexpr int NBUF = NTH <= 256 ? 2 : 1;
+    __shared__ float4 s0[NBUF][NTH];
+    __shared__ float4 s1[NBUF][NTH];
+    __shared__ float4 s2[NBUF][NTH];
+    __shared__ int sg[NBUF][NTH];
+    __shared__ unsigned smask[NBUF][NTH];
     __shared__ int s_max;
     const int tid = threadIdx.x, lane = tid & 31;
     const unsigned wbit = 1u << (tid >> 5);
@@ -711,26 +714,14 @@ __device__ __forceinline__ void blend_backward_tile(int2 rg, const int32_t *__re
     atomicMax(&s_max, mx_last);
     __syncthreads();
     const int n = s_max;
-    for (int end = n; end > 0; end -= NTH) {
-        const int start = max(0, end - NTH);
-        __syncthreads();
-        int idx = start + tid;
-        if (idx < end) {
-            int g = pair_gauss[rg.x + idx];
-            sg[tid] = g;
-            s0[tid] = rec0[g];
-            float4 r1 = rec1[g];
-            s1[tid] = r1;
-            s2[tid] = rec2[g];
-            smask[tid] = BoxMap<TS, PPT>::mask(tx, ty, r1.z, r1.w);
-        }
-        __syncthreads();
+    // walk buffer b (list positions start .. end - 1) from back to front
+    auto walk = [&](int b, int start, int end) {
         for (int j = end - 1; j >= start; --j) {
             const int sj = j - start;
-            if (!(smask[sj] & wbit)) continue;  // warp-uniform: rect misses this warp's box
-            const float4 r1 = s1[sj];
-            const float4 r0 = s0[sj];
-            const float4 c = s2[sj];
+            if (!(smask[b][sj] & wbit)) continue;  // warp-uniform: rect misses this warp's box
+            const float4 r1 = s1[b][sj];
+            const float4 r0 = s0[b][sj];
+            const float4 c = s2[b][sj];
             // per-thread sums over this thread's pixels
             float g_col0 = 0.f, g_col1 = 0.f, g_col2 = 0.f, g_op = 0.f, g_mx = 0.f, g_my = 0.f, g_ca = 0.f,
                   g_cb = 0.f, g_cc = 0.f;
@@ -771,7 +762,7 @@ __device__ __forceinline__ void blend_backward_tile(int2 rg, const int32_t *__re
                 const float tot = warp_reduce_scatter16(v);
                 const int vi = lane >> 1;
                 if (!(lane & 1) && vi < 9) {
-                    const size_t g = (size_t)sg[sj];
+                    const size_t g = (size_t)sg[b][sj];
                     float *dst = vi < 3   ? d_color + (size_t)vi * cs
                                  : vi == 3 ? d_opacity
                                  : vi < 6  ? d_mean2d + (size_t)(vi - 4) * cs
@@ -779,6 +770,66 @@ __device__ __forceinline__ void blend_backward_tile(int2 rg, const int32_t *__re
                     atomicAdd(dst + g, vi == 3 ? tot / c.w : tot);
                 }
             }
+        }
+    };
+    if constexpr (NBUF == 2) {
+        float2 prect = make_float2(0.f, 0.f);
+        int pg = 0;
+        bool have = false;
+        // the batch that ends at list position end (exclusive) into buffer b
+        auto fetch = [&](int end, int b) {
+            const int idx = max(0, end - NTH) + tid;
+            have = idx < end;
+            if (have) {
+                pg = pair_gauss[rg.x + idx];
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s0[b][tid])),
+                             "l"(rec0 + pg)
+                             : "memory");
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s1[b][tid])),
+                             "l"(rec1 + pg)
+                             : "memory");
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s2[b][tid])),
+                             "l"(rec2 + pg)
+                             : "memory");
+                prect = __ldg(reinterpret_cast<const float2 *>(rec1 + pg) + 1);
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        auto stash = [&](int b) {
+            if (have) {
+                sg[b][tid] = pg;
+                smask[b][tid] = BoxMap<TS, PPT>::mask(tx, ty, prect.x, prect.y);
+            }
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        };
+        if (n > 0) {
+            fetch(n, 0);
+            stash(0);
+        }
+        int b = 0;
+        for (int end = n; end > 0; end -= NTH, b ^= 1) {
+            const int start = max(0, end - NTH);
+            __syncthreads();  // batch b is in place, and every warp is done with buffer b ^ 1
+            if (start > 0) fetch(start, b ^ 1);
+            walk(b, start, end);
+            if (start > 0) stash(b ^ 1);
+        }
+    } else {
+        for (int end = n; end > 0; end -= NTH) {
+            const int start = max(0, end - NTH);
+            __syncthreads();
+            int idx = start + tid;
+            if (idx < end) {
+                int g = pair_gauss[rg.x + idx];
+                sg[0][tid] = g;
+                s0[0][tid] = rec0[g];
+                float4 r1 = rec1[g];
+                s1[0][tid] = r1;
+                s2[0][tid] = rec2[g];
+                smask[0][tid] = BoxMap<TS, PPT>::mask(tx, ty, r1.z, r1.w);
+            }
+            __syncthreads();
+            walk(0, start, end);
         }
     }
 }
