@@ -492,12 +492,21 @@ def _form_mlp(r, st, args, dev, flush, reps, fwd_ms):
         tf = flops_pt * x.shape[1] / (us * 1e-6) / 1e12
         out[name] = {"points": int(x.shape[1]), "us": round(us, 1), "achieved_tflops": round(tf, 1),
                      "frac": round(tf / float(peaks["bf16_tflops"]), 4)}
+    # Sec. 4: novel poses use the mean displacement over the training poses (64 here)
+    poses = (torch.randn(64, 72, device=dev) * 0.3).contiguous()
+    dxm = torch.empty_like(t["xv"])
+    wsm = api.workspace(api.mlp_workspace_size(t["xv"].shape[1], 72, 64), dev)
+    us = _time_graph(_graph_of(lambda: api.avatar_mlp(t["xv"], poses, w, dx=dxm, ws=wsm)), reps, flush) * 1000.0
+    tf = flops_pt * t["xv"].shape[1] * 64 / (us * 1e-6) / 1e12
+    out["average_over_64_poses"] = {"points": int(t["xv"].shape[1]), "poses": 64, "us": round(us, 1),
+                                    "achieved_tflops": round(tf, 1), "frac": round(tf / float(peaks["bf16_tflops"]), 4)}
     rm = render.Renderer(st, tile=args.tile, mlp=w)
     rm.check()
     frame_ms = _time_graph(_graph_of(rm.forward), reps, flush)
-    out.update({"what": "dx = MLP(gamma(x_v), theta) before skinning: Fourier features, three ReLU layers of 256 "
-                        "and a linear output, BF16 operands, FP32 accumulation in TMEM, one fused kernel (plus "
-                        "the per-call weight packing)",
+    out.update({"what": "dx = MLP(gamma(x_v), theta): Fourier features, three ReLU layers of 256 and a linear "
+                        "output, BF16 operands, FP32 accumulation in TMEM, one fused kernel (plus the per-call "
+                        "weight packing); per pose (training, or the frame with the MLP) and averaged over poses "
+                        "(the fixed displacement of novel-pose rendering)",
                 "frames_per_s_with_mlp": round(1000.0 / frame_ms, 3),
                 "frames_per_s_without": round(1000.0 / fwd_ms, 3),
                 "peak": float(peaks["bf16_tflops"]), "peak_note": f"dense BF16, {kind}"})

@@ -588,19 +588,26 @@ int avatar_regularizers(avatar_ctx *ctx, const avatar_reg_args *a, void *ws, siz
 /*   h1 = relu(W1 [gamma(x); theta] + b1)          W1: [256][128 + P]    */
 /*   h2 = relu(W2 h1 + b2),  h3 = relu(W3 h2 + b3) W2, W3: [256][256]    */
 /*   dx = W4 h3 + b4                               W4: [3][256]          */
-/* On the tensor cores with BF16 operands and FP32 accumulation: the    */
-/* features, the hidden activations and W1's feature part, W2, W3, W4   */
-/* are rounded to bfloat16 (nearest even); theta's part of layer 1 and  */
-/* the biases stay FP32.  All arrays are FP32, row-major as shown.  The */
-/* workspace (avatar_mlp_workspace_size, 256-byte aligned) receives the */
-/* packed BF16 weights on every call.  Asynchronous on the stream; an   */
+/* With T poses the output is the mean over them,                      */
+/*   dx = (1/T) sum_t d(x, theta_t),                                    */
+/* the average displacement over the training poses that replaces the   */
+/* per-pose displacement when rendering novel poses (Sec. 4); T = 1 is  */
+/* the displacement at one pose.  On the tensor cores with BF16         */
+/* operands and FP32 accumulation: the features, the hidden activations */
+/* and W1's feature part, W2, W3, W4 are rounded to bfloat16 (nearest   */
+/* even); theta's part of layer 1, the biases and the mean stay FP32     */
+/* (the mean sums the poses in order, deterministic).  All arrays are   */
+/* FP32, row-major as shown.  The workspace (avatar_mlp_workspace_size, */
+/* 256-byte aligned) receives the packed BF16 weights and the poses'    */
+/* layer-1 biases on every call.  Asynchronous on the stream; an        */
 /* accelerator wait that runs out sets AVATAR_ERR_TIMEOUT in *status.   */
 /* ------------------------------------------------------------------ */
 typedef struct {
     int N;                 /* points (0 allowed) */
     int P;                 /* pose dimensions, 0..128 */
+    int T;                 /* poses, >= 1 */
     const float *x;        /* [3][N] points (canonical vertices) */
-    const float *theta;    /* [P] pose */
+    const float *theta;    /* [T][P] poses */
     const float *Bf;       /* [64][3] Fourier frequencies */
     const float *W1, *b1;  /* [256][128 + P], [256] */
     const float *W2, *b2;  /* [256][256], [256] */

@@ -64,7 +64,7 @@ class RegArgs(C.Structure):
 
 
 class MlpArgs(C.Structure):
-    _fields_ = [("N", I32), ("P", I32), ("x", P), ("theta", P), ("Bf", P), ("W1", P), ("b1", P), ("W2", P),
+    _fields_ = [("N", I32), ("P", I32), ("T", I32), ("x", P), ("theta", P), ("Bf", P), ("W1", P), ("b1", P), ("W2", P),
                 ("b2", P), ("W3", P), ("b3", P), ("W4", P), ("b4", P), ("dx", P), ("status", P)]
 
 

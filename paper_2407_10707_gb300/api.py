@@ -528,21 +528,24 @@ def mlp_tensors(w, device):
     return {k: torch.as_tensor(np.asarray(w[k]), dtype=torch.float32).contiguous().to(device) for k in MLP_KEYS}
 
 
-def mlp_workspace_size(n, p):
+def mlp_workspace_size(n, p, t=1):
     a = L.MlpArgs()
-    a.N, a.P = n, p
+    a.N, a.P, a.T = n, p, t
     return L.load().avatar_mlp_workspace_size(C.byref(a))
 
 
 def avatar_mlp(x, theta, w, dx=None, ws=None, status=None):
     """Sec. 3.1's displacement dx [3, N] of the points x [3, N] at pose
-    theta [P], weights w from mlp_tensors."""
+    theta [P], or its mean over the poses theta [T, P] (Sec. 4's average
+    displacement); weights w from mlp_tensors."""
     lib = L.load()
     ctx = context()
     x = x.contiguous()
     theta = theta.contiguous()
+    if theta.dim() == 1:
+        theta = theta.unsqueeze(0)
     a = L.MlpArgs()
-    a.N, a.P = x.shape[1], theta.numel()
+    a.N, a.P, a.T = x.shape[1], theta.shape[1], theta.shape[0]
     if dx is None:
         dx = torch.empty_like(x)
     a.x, a.theta, a.dx, a.status = _p(x), _p(theta), _p(dx), _p(status)

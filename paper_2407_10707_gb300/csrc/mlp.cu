@@ -52,8 +52,8 @@ constexpr int SMALL_BYTES = 16 * MLP_KC * 2;         // a layer-4 chunk
 constexpr int ACT_BYTES = MLP_M * MLP_W * 2;         // 64 KB activations per slot
 constexpr int A_KC8 = MLP_W / 8;                     // core matrices along K (activations)
 constexpr int B_KC8 = MLP_KC / 8;                    // (weight chunks)
-// ring, two activation buffers, biases (layers 1..3 and 4), frequencies
-constexpr size_t MLP_SMEM = (size_t)MLP_STAGES * STAGE_BYTES + 2 * ACT_BYTES + 3 * MLP_W * 4 + 16 * 4 + MLP_NF * 16;
+// ring, two activation buffers, biases (layer 1 per slot, layers 2, 3 and 4), frequencies
+constexpr size_t MLP_SMEM = (size_t)MLP_STAGES * STAGE_BYTES + 2 * ACT_BYTES + 4 * MLP_W * 4 + 16 * 4 + MLP_NF * 16;
 static_assert(PART_COLS % 32 == 0 && F_PER % 8 == 0, "epilogue and feature work split");
 static_assert(MATH_THREADS >= MLP_W, "bias setup");
 
@@ -105,12 +105,28 @@ mlp_pack_kernel(const float *__restrict__ W1, int in1, const float *__restrict__
 }
 
 struct MlpParams {
-    int N, P;
-    const float *x, *theta, *Bf, *W1, *b1, *b2, *b3, *b4;
+    int N, T;                // points, poses
+    float inv_T;
+    const float *x, *Bf, *b2, *b3, *b4;
+    const float *c1;         // [T][256] layer-1 bias with each pose folded in
     const unsigned char *packed;
     float *dx;
     int32_t *status;
 };
+
+// Layer-1 bias of every pose: c1[t][n] = b1[n] + sum_p W1[n][128 + p] theta[t][p].
+__global__ void __launch_bounds__(MLP_W)
+mlp_pose_bias_kernel(const float *__restrict__ W1, const float *__restrict__ b1, const float *__restrict__ theta,
+                     int P, int T, float *__restrict__ c1)
+{
+    const int n = threadIdx.x, in1 = 2 * MLP_NF + P;
+    for (int t = blockIdx.x; t < T; t += gridDim.x) {
+        float acc = __ldg(b1 + n);
+        for (int p = 0; p < P; ++p)
+            acc = fmaf(__ldg(W1 + (size_t)n * in1 + 2 * MLP_NF + p), __ldg(theta + (size_t)t * P + p), acc);
+        c1[(size_t)t * MLP_W + n] = acc;
+    }
+}
 
 struct MlpBars {
     uint64_t full[MLP_STAGES], empty[MLP_STAGES];  // weight ring: copy landed / MMAs done with the stage
@@ -192,8 +208,8 @@ mlp_forward_kernel(MlpParams P)
     extern __shared__ __align__(1024) unsigned char mlp_smem[];
     unsigned char *ring = mlp_smem;                                   // [5][16 KB] weight chunks
     unsigned char *act = ring + MLP_STAGES * STAGE_BYTES;             // [2][128][256] BF16 activations
-    float *sbias = reinterpret_cast<float *>(act + 2 * ACT_BYTES);    // [3][256] layer-1 bias with the pose, b2, b3
-    float *sb4 = sbias + 3 * MLP_W;                                   // [16]
+    float *sbias = reinterpret_cast<float *>(act + 2 * ACT_BYTES);    // [2][256] slot's layer-1 bias; b2; b3
+    float *sb4 = sbias + 4 * MLP_W;                                   // [16]
     float4 *sfreq = reinterpret_cast<float4 *>(sb4 + 16);             // [64] frequencies (x, y, z, 0)
     __shared__ MlpBars bars;
     __shared__ uint32_t tmem_base;
@@ -202,15 +218,17 @@ mlp_forward_kernel(MlpParams P)
     const int ntiles = (P.N + MLP_M - 1) / MLP_M;
     const int grid = gridDim.x;
     volatile int *abort = &abort_flag;
+    // Work items (point tile, pose): this CTA's point tiles blockIdx.x + k grid,
+    // each with all T poses in order (so a point tile's mean stays on one CTA).
+    const int my_tiles = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + grid - 1) / grid : 0;
+    const int n_items = my_tiles * P.T;
+    auto item_tile = [&](int i) { return (int)blockIdx.x + (i / P.T) * grid; };
+    auto item_pose = [&](int i) { return i % P.T; };
 
-    if (warp >= 2 && tid - 64 < MLP_W) {  // layer-1 bias with the pose folded in, the other biases, the frequencies
+    if (warp >= 2 && tid - 64 < MLP_W) {  // the pose-independent biases, the frequencies
         const int n = tid - 64;
-        const int in1 = 2 * MLP_NF + P.P;
-        float acc = __ldg(P.b1 + n);
-        for (int p = 0; p < P.P; ++p) acc = fmaf(__ldg(P.W1 + (size_t)n * in1 + 2 * MLP_NF + p), __ldg(P.theta + p), acc);
-        sbias[n] = acc;
-        sbias[MLP_W + n] = __ldg(P.b2 + n);
-        sbias[2 * MLP_W + n] = __ldg(P.b3 + n);
+        sbias[2 * MLP_W + n] = __ldg(P.b2 + n);
+        sbias[3 * MLP_W + n] = __ldg(P.b3 + n);
         if (n < 16) sb4[n] = n < 3 ? __ldg(P.b4 + n) : 0.f;
         if (n < MLP_NF) sfreq[n] = make_float4(__ldg(P.Bf + 3 * n), __ldg(P.Bf + 3 * n + 1), __ldg(P.Bf + 3 * n + 2), 0.f);
     }
@@ -238,15 +256,14 @@ mlp_forward_kernel(MlpParams P)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tbase = tmem_base;
 
-    // Tiles go in pairs: pair m holds tiles t0 = blockIdx.x + 2 m grid (slot 0)
-    // and t0 + grid (slot 1, if it exists).  Per pair and layer, slot 0 then
-    // slot 1, in all three roles.
+    // Items go in pairs: pair m holds items 2 m (slot 0) and 2 m + 1 (slot 1,
+    // if it exists).  Per pair and layer, slot 0 then slot 1, in all three roles.
     if (warp == 0) {
         // ---------------------------------------------------------------- weight producer
         if (lane == 0) {
             int c = 0;
-            for (int t0 = blockIdx.x; t0 < ntiles; t0 += 2 * grid) {
-                const int ns = t0 + grid < ntiles ? 2 : 1;
+            for (int i0 = 0; i0 < n_items; i0 += 2) {
+                const int ns = i0 + 1 < n_items ? 2 : 1;
                 for (int L = 0; L < 4; ++L)
                     for (int s = 0; s < ns; ++s)
                         for (int k = 0; k < layer_chunks(L); ++k, ++c) {
@@ -274,8 +291,8 @@ mlp_forward_kernel(MlpParams P)
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
             int c = 0, m = 0;
-            for (int t0 = blockIdx.x; t0 < ntiles; t0 += 2 * grid, ++m) {
-                const int ns = t0 + grid < ntiles ? 2 : 1;
+            for (int i0 = 0; i0 < n_items; i0 += 2, ++m) {
+                const int ns = i0 + 1 < n_items ? 2 : 1;
                 for (int L = 0; L < 4; ++L) {
                     const uint32_t idesc = umma_idesc(MLP_M, L == 3 ? 16 : MLP_W);
                     for (int s = 0; s < ns; ++s) {
@@ -311,22 +328,35 @@ mlp_forward_kernel(MlpParams P)
         const int quarter = warp & 3, part = (warp - 2) >> 2;
         const int row = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-        for (int s = 0; s < 2; ++s)
-            if ((int)blockIdx.x + s * grid < ntiles) {
-                write_features(P, blockIdx.x + s * grid, mt, sfreq, act + s * ACT_BYTES);
-                bar_arrive(&bars.feat[s]);
-            }
-        for (int t0 = blockIdx.x; t0 < ntiles; t0 += 2 * grid) {
-            const int ns = t0 + grid < ntiles ? 2 : 1;
+        // a slot's input: the point tile's features and the pose's layer-1 bias
+        // (a named barrier of the math warps makes the bias row visible to all)
+        auto prepare = [&](int i, int s) {
+            write_features(P, item_tile(i), mt, sfreq, act + s * ACT_BYTES);
+            if (mt < MLP_W) sbias[s * MLP_W + mt] = __ldg(P.c1 + (size_t)item_pose(i) * MLP_W + mt);
+            asm volatile("bar.sync 1, %0;" ::"r"(MATH_THREADS) : "memory");
+            bar_arrive(&bars.feat[s]);
+        };
+        for (int s = 0; s < 2 && s < n_items; ++s) prepare(s, s);
+        float mean[3] = {0.f, 0.f, 0.f};  // running sum over the poses of the current point tile
+        int cur_tile = n_items > 0 ? item_tile(0) : -1;
+        auto flush = [&]() {
+            const int gr = cur_tile * MLP_M + row;
+            if (part == 0 && gr < P.N)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) P.dx[(size_t)j * P.N + gr] = mean[j] * P.inv_T;
+            mean[0] = mean[1] = mean[2] = 0.f;
+        };
+        for (int i0 = 0; i0 < n_items; i0 += 2) {
+            const int ns = i0 + 1 < n_items ? 2 : 1;
             for (int L = 0; L < 4; ++L)
                 for (int s = 0; s < ns; ++s) {
-                    const int tile = t0 + s * grid;
+                    const int item = i0 + s;
                     unsigned char *buf = act + s * ACT_BYTES;
                     wait_or_abort(&bars.acc[s], L & 1, P.status, abort);
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t acc = tbase + lane_off + (uint32_t)(s * MLP_W);
                     if (L < 3) {
-                        const float *bias = sbias + L * MLP_W;
+                        const float *bias = sbias + (L == 0 ? s : L + 1) * MLP_W;
 #pragma unroll 1
                         for (int c0 = part * PART_COLS; c0 < (part + 1) * PART_COLS; c0 += 32) {
                             float v[32];
@@ -354,18 +384,17 @@ mlp_forward_kernel(MlpParams P)
                         float v[16];
                         tmem_ld16(acc, v);  // read before the next tile's MMAs may overwrite the accumulator
                         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                        const int next = tile + 2 * grid;
-                        if (next < ntiles) {  // the output layer's MMAs no longer read the buffer
-                            write_features(P, next, mt, sfreq, buf);
-                            bar_arrive(&bars.feat[s]);
+                        if (item + 2 < n_items) prepare(item + 2, s);  // the output layer's MMAs no longer read the buffer
+                        if (item_tile(item) != cur_tile) {
+                            flush();
+                            cur_tile = item_tile(item);
                         }
-                        const int gr = tile * MLP_M + row;
-                        if (part == 0 && gr < P.N)
 #pragma unroll
-                            for (int j = 0; j < 3; ++j) P.dx[(size_t)j * P.N + gr] = v[j] + sb4[j];
+                        for (int j = 0; j < 3; ++j) mean[j] += v[j] + sb4[j];
                     }
                 }
         }
+        if (n_items > 0) flush();
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -375,8 +404,15 @@ mlp_forward_kernel(MlpParams P)
 
 int check_mlp(const avatar_mlp_args *a)
 {
-    if (!a || a->N < 0 || a->P < 0 || a->P > MLP_MAX_P) return AVATAR_ERR_INVALID_ARG;
+    if (!a || a->N < 0 || a->P < 0 || a->P > MLP_MAX_P || a->T < 1 || a->T > (1 << 20)) return AVATAR_ERR_INVALID_ARG;
     return AVATAR_OK;
+}
+
+size_t mlp_ws(const avatar_mlp_args *a, size_t *c1_off)
+{
+    const size_t packed = av_align256(MLP_PACKED_BYTES);
+    if (c1_off) *c1_off = packed;
+    return packed + av_align256((size_t)a->T * MLP_W * sizeof(float));
 }
 
 }  // namespace
@@ -384,7 +420,7 @@ int check_mlp(const avatar_mlp_args *a)
 extern "C" size_t avatar_mlp_workspace_size(const avatar_mlp_args *a)
 {
     if (check_mlp(a) != AVATAR_OK) return 0;
-    return av_align256(MLP_PACKED_BYTES);
+    return mlp_ws(a, nullptr);
 }
 
 extern "C" int avatar_mlp(avatar_ctx *ctx, const avatar_mlp_args *a, void *ws, size_t ws_bytes,
@@ -396,26 +432,30 @@ extern "C" int avatar_mlp(avatar_ctx *ctx, const avatar_mlp_args *a, void *ws, s
     if (!a->x || !a->Bf || !a->W1 || !a->b1 || !a->W2 || !a->b2 || !a->W3 || !a->b3 || !a->W4 || !a->b4 || !a->dx ||
         (a->P > 0 && !a->theta))
         return AVATAR_ERR_INVALID_ARG;
-    if (!ws || (((uintptr_t)ws) & 255) || ws_bytes < av_align256(MLP_PACKED_BYTES)) return AVATAR_ERR_WORKSPACE;
+    size_t c1_off;
+    if (!ws || (((uintptr_t)ws) & 255) || ws_bytes < mlp_ws(a, &c1_off)) return AVATAR_ERR_WORKSPACE;
     if (MLP_SMEM + 1024 > (size_t)ctx->max_smem_optin) return AVATAR_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char *packed = (unsigned char *)ws;
+    float *c1 = (float *)((unsigned char *)ws + c1_off);
     mlp_pack_kernel<<<ctx->sm_count * 2, 256, 0, st>>>(a->W1, 2 * MLP_NF + a->P, a->W2, a->W3, a->W4, packed);
+    AV_CHECK_LAUNCH();
+    const int pgrid = a->T < ctx->sm_count * 4 ? a->T : ctx->sm_count * 4;
+    mlp_pose_bias_kernel<<<pgrid, MLP_W, 0, st>>>(a->W1, a->b1, a->theta, a->P, a->T, c1);
     AV_CHECK_LAUNCH();
     if (cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MLP_SMEM) !=
         cudaSuccess)
         return AVATAR_ERR_CUDA;
     MlpParams p;
     p.N = a->N;
-    p.P = a->P;
+    p.T = a->T;
+    p.inv_T = 1.0f / (float)a->T;
     p.x = a->x;
-    p.theta = a->theta;
     p.Bf = a->Bf;
-    p.W1 = a->W1;
-    p.b1 = a->b1;
     p.b2 = a->b2;
     p.b3 = a->b3;
     p.b4 = a->b4;
+    p.c1 = c1;
     p.packed = packed;
     p.dx = a->dx;
     p.status = a->status;

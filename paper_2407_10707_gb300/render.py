@@ -629,3 +629,12 @@ def densify(st, rand, d0=1.0, p0=0.02, logscale=-4.0, opacity=0.5, status=None):
     t["opacity"] = torch.cat([t["opacity"], torch.full((n,), opacity, dtype=t["opacity"].dtype, device=dev)])
     t["knn"] = api.avatar_knn(t["xg"], t["xv"], t["knn"].shape[0], status=status)
     return n
+
+
+def average_displacement(st, mlp, poses, status=None):
+    """Sec. 4's displacement for novel poses: the mean of the MLP's
+    displacement over the training poses (poses [T, 72], weights from
+    api.mlp_tensors), stored as the avatar's fixed displacement dxv."""
+    t = st["avatar"]
+    api.avatar_mlp(t["xv"], poses.reshape(poses.shape[0], -1), mlp, dx=t["dxv"], status=status)
+    return t["dxv"]

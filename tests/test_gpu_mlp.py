@@ -42,7 +42,8 @@ def _oracle(x, theta, w, bf):
 def _run(api, x, theta, w, status=None):
     wt = api.mlp_tensors(w, "cuda")
     xt = torch.as_tensor(np.asarray(x, np.float32).T.copy(), device="cuda")
-    tt = torch.as_tensor(np.asarray(theta, np.float32).ravel(), device="cuda")
+    th = np.asarray(theta, np.float32)
+    tt = torch.as_tensor(th.reshape(th.shape[0], -1) if th.ndim == 2 else th.ravel(), device="cuda")
     dx = api.avatar_mlp(xt, tt, wt, status=status)
     torch.cuda.synchronize()
     return dx.cpu().numpy().T.astype(np.float64)
@@ -131,3 +132,40 @@ def test_renderer_evaluates_the_mlp_before_skinning(gpu):
     torch.cuda.synchronize()
     assert torch.equal(img_mlp, img_fixed)
     assert float(dx.abs().max()) > 1e-4 and not torch.equal(img_mlp, img_zero)
+
+
+@pytest.mark.parametrize("n,T", [(1000, 5), (300, 4), (513, 7), (128, 2)])
+def test_mlp_mean_over_poses_matches_oracle(gpu, n, T):
+    """The mean displacement over T poses (Sec. 4's average over the training
+    poses): the oracle's mean of the per-pose networks, with the per-pose
+    bounds scaled by the per-pose RMS."""
+    api = gpu
+    rng = np.random.default_rng(n * 7 + T)
+    w = synth.mlp_weights(3)
+    x = rng.uniform(-1.0, 1.0, size=(n, 3))
+    poses = rng.normal(0.0, 0.3, size=(T, 72))
+    st = api.status_word("cuda")
+    got = _run(api, x, poses, w, status=st)
+    assert int(st.item()) == 0
+    per = [_oracle(x, th, w, bf=True) for th in poses]
+    want = np.mean(per, axis=0)
+    rms = np.sqrt(np.mean([np.mean(p ** 2) for p in per]))
+    d = np.abs(got - want)
+    assert d.max() <= 2e-2 * rms and d.mean() <= 2e-4 * rms, (d.max() / rms, d.mean() / rms)
+
+
+def test_average_displacement_sets_the_avatar_displacement(gpu):
+    api = gpu
+    from paper_2407_10707_gb300 import render
+    sc = scene("c1_small")
+    st = render.scene_tensors(sc, "cuda")
+    w = api.mlp_tensors(synth.mlp_weights(5), "cuda")
+    poses = torch.as_tensor(np.random.default_rng(2).normal(0, 0.3, size=(6, 24, 3)), dtype=torch.float32,
+                            device="cuda")
+    dx = render.average_displacement(st, w, poses)
+    want = api.avatar_mlp(st["avatar"]["xv"], poses.reshape(6, 72), w)
+    torch.cuda.synchronize()
+    assert dx.data_ptr() == st["avatar"]["dxv"].data_ptr() and torch.equal(dx, want)
+    r = render.Renderer(st)
+    r.forward()
+    r.check()
