@@ -447,6 +447,49 @@ def forms(r, st, sc, args, dev, flush, fwd_ms, train_ms, want):
         out["displacement_mlp"] = _form_mlp(r, st, args, dev, flush, reps, fwd_ms)
     if "densify" in want:
         out["densify"] = _form_densify(st, dev, flush, reps)
+    if "stress" in want:
+        out["stress_c5"] = _form_stress(args, dev, flush, reps)
+    return out
+
+
+def _form_stress(args, dev, flush, reps):
+    """The stress configuration: 200k-vertex mesh, 1M Gaussians, 32 x 64 light,
+    1,024 directions at 512^2, 2048 x 2048; tensor-core shading (BF16 D and S,
+    FP32 accumulation) beside the FP32 CUDA-core shading, frame and training
+    step, with FP32 and BF16 attribute storage."""
+    import torch
+
+    from paper_2407_10707_gb300 import render, synth
+    torch.cuda.empty_cache()
+    sc = synth.config_scene("c5_stress")
+    out = {"what": "frames/s and train steps/s (forward on the tensor cores, FP32 adjoints) against the FP32 "
+                   "CUDA-core shading of the same frame; max-abs pixel difference (target <= 1e-3)"}
+    for dt in ("f32", "bf16"):
+        st = render.scene_tensors(sc, dev, attr_dtype=dt)
+        cap = 96 * sc.avatar.G  # about fifty 16-pixel tiles per Gaussian at 2048^2
+        r32 = render.Renderer(st, tile=args.tile, pair_capacity=cap)
+        rtc = render.Renderer(st, tile=args.tile, shade_tc=True, pair_capacity=cap)
+        f32_ms = _time_graph(_graph_of(r32.forward), reps, flush)
+        tc_ms = _time_graph(_graph_of(rtc.forward), reps, flush)
+        r32.forward()
+        rtc.forward()
+        torch.cuda.synchronize()
+        err = float((rtc.sb.image - r32.sb.image).abs().max().item())
+        r32.check()
+        rtc.check()
+        res = {"frames_per_s_fp32_shading": round(1000.0 / f32_ms, 3), "frames_per_s_tensor_core": round(1000.0 / tc_ms, 3),
+               "max_abs_pixel_diff": err, "pairs": int(r32.sb.num_pairs.item())}
+        if dt == "f32":
+            target = (r32.sb.image.detach().clone() * 0.9).contiguous()
+            del r32, rtc
+            for name, tc in (("train_steps_per_s_fp32_shading", False), ("train_steps_per_s_tensor_core", True)):
+                ts = render.TrainStep(st, target, tile=args.tile, shade_tc=tc, pair_capacity=cap)
+                res[name] = round(1000.0 / _time_graph(_graph_of(ts.step), reps, flush), 3)
+                ts.check()
+                del ts
+        out[dt + "_storage"] = res
+        del st
+        torch.cuda.empty_cache()
     return out
 
 
@@ -774,7 +817,7 @@ def main():
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the precision / relighting / batching forms")
-    ap.add_argument("--forms", default="precision,relight,knn,paper_vis,batch,mlp,densify",
+    ap.add_argument("--forms", default="precision,relight,knn,paper_vis,batch,mlp,densify,stress",
                     help="comma list of forms to measure")
     ap.add_argument("--batch-poses", type=int, default=32, help="poses of the batch form (4 cameras each)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
