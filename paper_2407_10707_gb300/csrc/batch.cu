@@ -340,21 +340,26 @@ emit_batch_kernel(const BatchView *__restrict__ views, int G, long long VG, int 
                   uint32_t *__restrict__ keys, int32_t *__restrict__ vals)
 {
     const size_t cs = (size_t)VG;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < VG; k += (long long)gridDim.x * blockDim.x) {
-        const int gi = sorted_idx[k];
-        const int n = npairs[gi];
-        if (n == 0) continue;
-        long off = offsets[k];
-        if (off + n > cap) continue;
-        const int v = gi / G;
-        const int ntx = views[v].ntx, base = views[v].tile_base;
-        int tx0 = rect[gi] / TS, ty0 = rect[cs + gi] / TS, tx1 = rect[2 * cs + gi] / TS, ty1 = rect[3 * cs + gi] / TS;
-        for (int ty = ty0; ty <= ty1; ++ty)
-            for (int tx = tx0; tx <= tx1; ++tx) {
-                keys[off] = (uint32_t)(base + ty * ntx + tx);
-                vals[off] = gi;
-                ++off;
+    const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long base = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < VG;
+         base += warps * 32) {
+        const long long k = base + (threadIdx.x & 31);
+        int gi = 0, n = 0, tx0 = 0, ty0 = 0, w = 1, kbase = 0, ntx = 1;
+        long off = 0;
+        if (k < VG) {
+            gi = sorted_idx[k];
+            n = npairs[gi];
+            off = offsets[k];
+            if (n > 0) {
+                const int v = gi / G;
+                ntx = views[v].ntx;
+                kbase = views[v].tile_base;
+                tx0 = rect[gi] / TS;
+                ty0 = rect[cs + gi] / TS;
+                w = rect[2 * cs + gi] / TS - tx0 + 1;
             }
+        }
+        emit_pairs_warp(n, off, gi, tx0, ty0, w, kbase, ntx, cap, keys, vals);
     }
 }
 

@@ -113,19 +113,22 @@ emit_pairs_kernel(const int32_t *__restrict__ sorted_idx, const int32_t *__restr
                   const int32_t *__restrict__ npairs, const int32_t *__restrict__ rect, int G, int TS, int ntx,
                   long cap, uint32_t *__restrict__ keys, int32_t *__restrict__ vals)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G; i += gridDim.x * blockDim.x) {
-        int g = sorted_idx[i];
-        int n = npairs[g];
-        if (n == 0) continue;
-        long off = offsets[i];
-        if (off + n > cap) continue;
-        int tx0 = rect[g] / TS, ty0 = rect[G + g] / TS, tx1 = rect[2 * G + g] / TS, ty1 = rect[3 * G + g] / TS;
-        for (int ty = ty0; ty <= ty1; ++ty)
-            for (int tx = tx0; tx <= tx1; ++tx) {
-                keys[off] = (uint32_t)(ty * ntx + tx);
-                vals[off] = g;
-                ++off;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < G; base += warps * 32) {
+        const int i = base + (threadIdx.x & 31);
+        int g = 0, n = 0, tx0 = 0, ty0 = 0, w = 1;
+        long off = 0;
+        if (i < G) {
+            g = sorted_idx[i];
+            n = npairs[g];
+            off = offsets[i];
+            if (n > 0) {
+                tx0 = rect[g] / TS;
+                ty0 = rect[G + g] / TS;
+                w = rect[2 * G + g] / TS - tx0 + 1;
             }
+        }
+        emit_pairs_warp(n, off, g, tx0, ty0, w, 0, ntx, cap, keys, vals);
     }
 }
 

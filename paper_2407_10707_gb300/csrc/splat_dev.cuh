@@ -241,9 +241,19 @@ sort_hist_kernel(const uint32_t *__restrict__ keys, const int32_t *__restrict__ 
     for (int i = threadIdx.x; i < OS_MAX_PASSES * RADIX; i += blockDim.x) (&cnt[0][0])[i] = 0;
     __syncthreads();
     const int n = min(*n_ptr, cap);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        uint32_t k = keys[i];
-        for (int p = 0; p < passes; ++p) atomicAdd(&cnt[p][(k >> (8 * p)) & 255u], 1);
+    // warp-aggregated counts: the lanes that share a digit add once (keys of
+    // one frame often share their high digits, which would serialise the
+    // shared-memory atomics)
+    const int stride = gridDim.x * blockDim.x;
+    const int nw = (n + 31) & ~31;  // whole warps iterate together
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += stride) {
+        const bool in = i < n;
+        const uint32_t k = in ? keys[i] : 0u;
+        for (int p = 0; p < passes; ++p) {
+            const unsigned d = in ? (k >> (8 * p)) & 255u : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (in && (peers & lanemask_lt()) == 0) atomicAdd(&cnt[p][d], __popc(peers));
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) {
@@ -503,6 +513,53 @@ struct BoxMap {
 // Front-to-back blend of tile (tx, ty) of a W x H image over the sorted
 // pairs [rg.x, rg.y); writes the tile's pixels of image [3][H][W], T_final
 // and n_last.  Every thread of the CTA calls it (it synchronises the CTA).
+// Pair emission by one warp for 32 consecutive Gaussians of the depth order
+// (lane j: n pairs starting at output offset off; an offset scan in that
+// order makes the warp's pairs one contiguous range).  The warp writes the
+// range slot by slot: lane j takes slot c + j, finds the Gaussian owning it
+// by a binary search over the lanes' inclusive counts, and its tile from the
+// slot's place in that Gaussian's tile rectangle (w tiles wide, row-major
+// from (tx0, ty0)); key = kbase + ty kstride + tx, value gval.  Every store
+// is coalesced; slots at or beyond cap are not written.
+__device__ __forceinline__ void emit_pairs_warp(int n, long off, int gval, int tx0, int ty0, int w, int kbase,
+                                                int kstride, long cap, uint32_t *__restrict__ keys,
+                                                int32_t *__restrict__ vals)
+{
+    const int lane = threadIdx.x & 31;
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const long start = __shfl_sync(0xffffffffu, off, 0);
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int c = 0; c < total; c += 32) {
+        const int sl = c + lane;
+        int own = 0;  // lanes whose inclusive count is <= sl
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int v = __shfl_sync(0xffffffffu, incl, own + step - 1);
+            if (v <= sl) own += step;
+        }
+        own = min(own, 31);
+        const int o_g = __shfl_sync(0xffffffffu, gval, own);
+        const int o_excl = __shfl_sync(0xffffffffu, incl - n, own);
+        const int o_tx0 = __shfl_sync(0xffffffffu, tx0, own);
+        const int o_ty0 = __shfl_sync(0xffffffffu, ty0, own);
+        const int o_w = __shfl_sync(0xffffffffu, w, own);
+        const int o_base = __shfl_sync(0xffffffffu, kbase, own);
+        const int o_stride = __shfl_sync(0xffffffffu, kstride, own);
+        const long dst = start + sl;
+        if (sl < total && dst < cap) {
+            const int local = sl - o_excl;
+            const int q = (int)__fdividef((float)local + 0.5f, (float)o_w);  // exact for local < 2^22
+            keys[dst] = (uint32_t)(o_base + (o_ty0 + q) * o_stride + o_tx0 + (local - q * o_w));
+            vals[dst] = o_g;
+        }
+    }
+}
+
 template <int TS, int PPT>
 __device__ __forceinline__ void blend_tile(int2 rg, const int32_t *__restrict__ pair_gauss,
                                            const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
