@@ -244,15 +244,28 @@ sort_hist_kernel(const uint32_t *__restrict__ keys, const int32_t *__restrict__ 
     // warp-aggregated counts: the lanes that share a digit add once (keys of
     // one frame often share their high digits, which would serialise the
     // shared-memory atomics)
+    // eight independent key loads in flight per thread per round; a warp's
+    // lanes stay together (whole 32-key groups), so the matches are uniform
+    constexpr int U = 8;
     const int stride = gridDim.x * blockDim.x;
-    const int nw = (n + 31) & ~31;  // whole warps iterate together
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += stride) {
-        const bool in = i < n;
-        const uint32_t k = in ? keys[i] : 0u;
-        for (int p = 0; p < passes; ++p) {
-            const unsigned d = in ? (k >> (8 * p)) & 255u : 256u;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            if (in && (peers & lanemask_lt()) == 0) atomicAdd(&cnt[p][d], __popc(peers));
+    const int lane = threadIdx.x & 31;
+    for (int w0 = blockIdx.x * blockDim.x + threadIdx.x - lane; w0 < n; w0 += U * stride) {  // warp-uniform
+        uint32_t k[U];
+        bool in[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = w0 + lane + u * stride;
+            in[u] = i < n;
+            k[u] = in[u] ? keys[i] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!__any_sync(0xffffffffu, in[u])) break;
+            for (int p = 0; p < passes; ++p) {
+                const unsigned d = in[u] ? (k[u] >> (8 * p)) & 255u : 256u;
+                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                if (in[u] && (peers & lanemask_lt()) == 0) atomicAdd(&cnt[p][d], __popc(peers));
+            }
         }
     }
     __syncthreads();
