@@ -115,16 +115,29 @@ struct MlpParams {
 };
 
 // Layer-1 bias of every pose: c1[t][n] = b1[n] + sum_p W1[n][128 + p] theta[t][p].
+// One block per pose (grid-stride over poses); a warp takes a row n, its lanes
+// the pose dimensions (coalesced), four rows in flight, and reduces by shuffles.
 __global__ void __launch_bounds__(MLP_W)
 mlp_pose_bias_kernel(const float *__restrict__ W1, const float *__restrict__ b1, const float *__restrict__ theta,
                      int P, int T, float *__restrict__ c1)
 {
-    const int n = threadIdx.x, in1 = 2 * MLP_NF + P;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int in1 = 2 * MLP_NF + P;
     for (int t = blockIdx.x; t < T; t += gridDim.x) {
-        float acc = __ldg(b1 + n);
-        for (int p = 0; p < P; ++p)
-            acc = fmaf(__ldg(W1 + (size_t)n * in1 + 2 * MLP_NF + p), __ldg(theta + (size_t)t * P + p), acc);
-        c1[(size_t)t * MLP_W + n] = acc;
+        const float *th = theta + (size_t)t * P;
+        for (int n0 = warp * 4; n0 < MLP_W; n0 += nw * 4) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int p = lane; p < P; p += 32) {
+                const float tp = __ldg(th + p);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) acc[r] = fmaf(__ldg(W1 + (size_t)(n0 + r) * in1 + 2 * MLP_NF + p), tp, acc[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float v = warp_sum(acc[r]);
+                if (lane == 0) c1[(size_t)t * MLP_W + n0 + r] = __ldg(b1 + n0 + r) + v;
+            }
+        }
     }
 }
 
