@@ -199,14 +199,26 @@ __device__ __forceinline__ double dist2_rn(float x0, float x1, float x2, float r
     return __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
 }
 
+// Queries in grid-cell order: query i goes to position order[...] of its cell,
+// so the 32 queries of a warp search the same few cells (coherent loops and
+// loads); their results do not depend on the order.
+__global__ void __launch_bounds__(KNN_THREADS)
+knn_order_kernel(const int *__restrict__ cell_of, int N, int *__restrict__ cursor, int *__restrict__ order)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        order[atomicAdd(cursor + cell_of[i], 1)] = i;
+}
+
 template <int KMAX>
 __global__ void __launch_bounds__(KNN_THREADS)
 knn_query_kernel(const float *__restrict__ x, int N, const float *__restrict__ ref, int M, int K,
                  const GridDev *__restrict__ gp, const int *__restrict__ start, const int *__restrict__ count,
-                 const float4 *__restrict__ pts, int32_t *__restrict__ knn, float *__restrict__ dist2)
+                 const float4 *__restrict__ pts, const int *__restrict__ order, int32_t *__restrict__ knn,
+                 float *__restrict__ dist2)
 {
     const GridDev g = *gp;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < N; o += gridDim.x * blockDim.x) {
+        const int i = __ldg(order + o);
         const float x0 = __ldg(x + i), x1 = __ldg(x + (size_t)N + i), x2 = __ldg(x + (size_t)2 * N + i);
         const int cx = cell_coord(x0, g.ox, g.inv_h, g.nx);
         const int cy = cell_coord(x1, g.oy, g.inv_h, g.ny);
@@ -269,6 +281,10 @@ struct KnnWs {
     int *totals;    // [ceil(cap / SCAN_BLOCK)]
     int *cell_of;   // [M]
     float4 *pts;    // [M] reference points in cell order (x, y, z, index)
+    int *qcount, *qstart, *qcursor;  // [cap] queries per cell
+    int *qtotals;   // [ceil(cap / SCAN_BLOCK)]
+    int *qcell;     // [N]
+    int *order;     // [N] queries in cell order
 };
 
 int cells_cap(int M) { return std::max(64, 2 * M); }
@@ -286,6 +302,12 @@ size_t knn_layout(const avatar_knn_args *a, void *base, size_t cap, KnnWs *out)
     w.totals = c.take<int>((C + SCAN_BLOCK - 1) / SCAN_BLOCK);
     w.cell_of = c.take<int>(a->M);
     w.pts = c.take<float4>(a->M);
+    w.qcount = c.take<int>(C);
+    w.qstart = c.take<int>(C);
+    w.qcursor = c.take<int>(C);
+    w.qtotals = c.take<int>((C + SCAN_BLOCK - 1) / SCAN_BLOCK);
+    w.qcell = c.take<int>((size_t)std::max(a->N, 1));
+    w.order = c.take<int>((size_t)std::max(a->N, 1));
     if (out) *out = w;
     return c.off;
 }
@@ -300,7 +322,7 @@ template <int KMAX>
 void launch_query(const avatar_knn_args *a, const KnnWs &w, int grid, cudaStream_t st)
 {
     knn_query_kernel<KMAX><<<grid, KNN_THREADS, 0, st>>>(a->x, a->N, a->ref, a->M, a->K, w.grid, w.start, w.count,
-                                                         w.pts, a->knn, a->dist2);
+                                                         w.pts, w.order, a->knn, a->dist2);
 }
 
 }  // namespace
@@ -340,6 +362,13 @@ extern "C" int avatar_knn(avatar_ctx *ctx, const avatar_knn_args *a, void *ws, s
     AV_CHECK_LAUNCH();
     if (a->N == 0) return AVATAR_OK;
     const int gN = std::min((a->N + KNN_THREADS - 1) / KNN_THREADS, ctx->sm_count * 16);
+    // the queries in cell order (counting sort on the same grid)
+    if (cudaMemsetAsync(w.qcount, 0, (size_t)C * sizeof(int), st) != cudaSuccess) return AVATAR_ERR_CUDA;
+    knn_count_kernel<<<gN, KNN_THREADS, 0, st>>>(a->x, a->N, w.grid, w.qcount, w.qcell);
+    scan_totals_kernel<<<nb, SCAN_BLOCK, 0, st>>>(w.qcount, C, w.qtotals);
+    scan_offsets_kernel<<<1, SCAN_BLOCK, 0, st>>>(w.qtotals, nb);
+    scan_apply_kernel<<<nb, SCAN_BLOCK, 0, st>>>(w.qcount, C, w.qtotals, w.qstart, w.qcursor);
+    knn_order_kernel<<<gN, KNN_THREADS, 0, st>>>(w.qcell, a->N, w.qcursor, w.order);
     if (a->K <= 4) launch_query<4>(a, w, gN, st);
     else if (a->K <= 8) launch_query<8>(a, w, gN, st);
     else if (a->K <= 20) launch_query<20>(a, w, gN, st);
