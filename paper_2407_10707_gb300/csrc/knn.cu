@@ -223,8 +223,16 @@ knn_query_kernel(const float *__restrict__ x, int N, const float *__restrict__ r
         const int cx = cell_coord(x0, g.ox, g.inv_h, g.nx);
         const int cy = cell_coord(x1, g.oy, g.inv_h, g.ny);
         const int cz = cell_coord(x2, g.oz, g.inv_h, g.nz);
-        double bd[KMAX];
+        // The list keeps FP32 distances; the FP64 value of the fixed operation
+        // order (which defines the order, with the index for ties) is formed
+        // only when two FP32 values lie within 1e-6 relative of each other: the
+        // FP32 value of (d0 d0 + d1 d1) + d2 d2 is within 3e-7 relative of it,
+        // so outside that margin the FP32 comparison already decides.
+        float bf[KMAX];
         int bi[KMAX];
+        float4 bp[KMAX];
+        double bD[KMAX];
+        bool bh[KMAX];
         int n = 0;
         float thr = INFINITY;  // FP32 rejection threshold: above it a candidate cannot enter
         const int smax = max(g.nx, max(g.ny, g.nz));
@@ -244,19 +252,44 @@ knn_query_kernel(const float *__restrict__ x, int N, const float *__restrict__ r
                         for (int t = b; t < e; ++t) {
                             const float4 q = __ldg(pts + t);
                             const float e0 = x0 - q.x, e1 = x1 - q.y, e2 = x2 - q.z;
-                            if (fmaf(e2, e2, fmaf(e1, e1, e0 * e0)) > thr) continue;
+                            const float df = fmaf(e2, e2, fmaf(e1, e1, e0 * e0));
+                            if (df > thr && df >= 1e-30f) continue;
                             const int j = __float_as_int(q.w);
-                            const double d = dist2_rn(x0, x1, x2, q.x, q.y, q.z);
-                            if (n == K && !(d < bd[K - 1] || (d == bd[K - 1] && j < bi[K - 1]))) continue;
+                            double D = 0.0;
+                            bool hasD = false;
+                            // does the candidate precede list entry m?
+                            auto precedes = [&](int m) -> bool {
+                                // (values near FP32 underflow lose the relative bound: exact)
+                                if (df >= 1e-30f && bf[m] >= 1e-30f) {
+                                    if (df < bf[m] * (1.0f - 1e-6f)) return true;
+                                    if (df > bf[m] * (1.0f + 1e-6f)) return false;
+                                }
+                                if (!hasD) {
+                                    D = dist2_rn(x0, x1, x2, q.x, q.y, q.z);
+                                    hasD = true;
+                                }
+                                if (!bh[m]) {
+                                    bD[m] = dist2_rn(x0, x1, x2, bp[m].x, bp[m].y, bp[m].z);
+                                    bh[m] = true;
+                                }
+                                return D < bD[m] || (D == bD[m] && j < bi[m]);
+                            };
+                            if (n == K && !precedes(K - 1)) continue;
                             int pos = n < K ? n++ : K - 1;
-                            while (pos > 0 && (d < bd[pos - 1] || (d == bd[pos - 1] && j < bi[pos - 1]))) {
-                                bd[pos] = bd[pos - 1];
+                            while (pos > 0 && precedes(pos - 1)) {
+                                bf[pos] = bf[pos - 1];
                                 bi[pos] = bi[pos - 1];
+                                bp[pos] = bp[pos - 1];
+                                bD[pos] = bD[pos - 1];
+                                bh[pos] = bh[pos - 1];
                                 --pos;
                             }
-                            bd[pos] = d;
+                            bf[pos] = df;
                             bi[pos] = j;
-                            if (n == K) thr = __double2float_ru(bd[K - 1]) * (1.0f + 1e-6f);
+                            bp[pos] = q;
+                            bD[pos] = D;
+                            bh[pos] = hasD;
+                            if (n == K) thr = bf[K - 1] * (1.0f + 1e-6f);
                         }
                     }
                 }
@@ -264,12 +297,17 @@ knn_query_kernel(const float *__restrict__ x, int N, const float *__restrict__ r
             // margin); strictly closer K-th best: no unvisited point can precede it
             if (n == K) {
                 const double bound = fmax(0.0, ((double)s - 1e-3) * (double)g.h);
-                if (bd[K - 1] < bound * bound) break;
+                // an upper bound of the K-th distance's FP64 value
+                const double kth = bh[K - 1] ? bD[K - 1] : (double)bf[K - 1] * (1.0 + 1e-6);
+                if (kth < bound * bound) break;
             }
         }
         for (int k = 0; k < K; ++k) {
             knn[(size_t)k * N + i] = k < n ? bi[k] : -1;
-            if (dist2) dist2[(size_t)k * N + i] = k < n ? (float)bd[k] : INFINITY;
+            if (dist2) {
+                if (k < n && !bh[k]) bD[k] = dist2_rn(x0, x1, x2, bp[k].x, bp[k].y, bp[k].z);
+                dist2[(size_t)k * N + i] = k < n ? (float)bD[k] : INFINITY;
+            }
         }
     }
 }
