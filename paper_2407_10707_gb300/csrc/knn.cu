@@ -228,11 +228,9 @@ knn_query_kernel(const float *__restrict__ x, int N, const float *__restrict__ r
         // only when two FP32 values lie within 1e-6 relative of each other: the
         // FP32 value of (d0 d0 + d1 d1) + d2 d2 is within 3e-7 relative of it,
         // so outside that margin the FP32 comparison already decides.
-        float bf[KMAX];
-        int bi[KMAX];
-        float4 bp[KMAX];
-        double bD[KMAX];
-        bool bh[KMAX];
+        float bf[KMAX];  // FP32 distance
+        int bi[KMAX];    // reference index
+        int bt[KMAX];    // position of the reference point in pts (its coordinates for an exact comparison)
         int n = 0;
         float thr = INFINITY;  // FP32 rejection threshold: above it a candidate cannot enter
         const int smax = max(g.nx, max(g.ny, g.nz));
@@ -255,8 +253,7 @@ knn_query_kernel(const float *__restrict__ x, int N, const float *__restrict__ r
                             const float df = fmaf(e2, e2, fmaf(e1, e1, e0 * e0));
                             if (df > thr && df >= 1e-30f) continue;
                             const int j = __float_as_int(q.w);
-                            double D = 0.0;
-                            bool hasD = false;
+                            double D = -1.0;  // the candidate's FP64 value, formed on first need
                             // does the candidate precede list entry m?
                             auto precedes = [&](int m) -> bool {
                                 // (values near FP32 underflow lose the relative bound: exact)
@@ -264,31 +261,22 @@ knn_query_kernel(const float *__restrict__ x, int N, const float *__restrict__ r
                                     if (df < bf[m] * (1.0f - 1e-6f)) return true;
                                     if (df > bf[m] * (1.0f + 1e-6f)) return false;
                                 }
-                                if (!hasD) {
-                                    D = dist2_rn(x0, x1, x2, q.x, q.y, q.z);
-                                    hasD = true;
-                                }
-                                if (!bh[m]) {
-                                    bD[m] = dist2_rn(x0, x1, x2, bp[m].x, bp[m].y, bp[m].z);
-                                    bh[m] = true;
-                                }
-                                return D < bD[m] || (D == bD[m] && j < bi[m]);
+                                if (D < 0.0) D = dist2_rn(x0, x1, x2, q.x, q.y, q.z);
+                                const float4 r = __ldg(pts + bt[m]);
+                                const double Dm = dist2_rn(x0, x1, x2, r.x, r.y, r.z);
+                                return D < Dm || (D == Dm && j < bi[m]);
                             };
                             if (n == K && !precedes(K - 1)) continue;
                             int pos = n < K ? n++ : K - 1;
                             while (pos > 0 && precedes(pos - 1)) {
                                 bf[pos] = bf[pos - 1];
                                 bi[pos] = bi[pos - 1];
-                                bp[pos] = bp[pos - 1];
-                                bD[pos] = bD[pos - 1];
-                                bh[pos] = bh[pos - 1];
+                                bt[pos] = bt[pos - 1];
                                 --pos;
                             }
                             bf[pos] = df;
                             bi[pos] = j;
-                            bp[pos] = q;
-                            bD[pos] = D;
-                            bh[pos] = hasD;
+                            bt[pos] = t;
                             if (n == K) thr = bf[K - 1] * (1.0f + 1e-6f);
                         }
                     }
@@ -298,15 +286,19 @@ knn_query_kernel(const float *__restrict__ x, int N, const float *__restrict__ r
             if (n == K) {
                 const double bound = fmax(0.0, ((double)s - 1e-3) * (double)g.h);
                 // an upper bound of the K-th distance's FP64 value
-                const double kth = bh[K - 1] ? bD[K - 1] : (double)bf[K - 1] * (1.0 + 1e-6);
+                const double kth = (double)bf[K - 1] * (1.0 + 1e-6);
                 if (kth < bound * bound) break;
             }
         }
         for (int k = 0; k < K; ++k) {
             knn[(size_t)k * N + i] = k < n ? bi[k] : -1;
             if (dist2) {
-                if (k < n && !bh[k]) bD[k] = dist2_rn(x0, x1, x2, bp[k].x, bp[k].y, bp[k].z);
-                dist2[(size_t)k * N + i] = k < n ? (float)bD[k] : INFINITY;
+                float dk = INFINITY;
+                if (k < n) {
+                    const float4 r = __ldg(pts + bt[k]);
+                    dk = (float)dist2_rn(x0, x1, x2, r.x, r.y, r.z);
+                }
+                dist2[(size_t)k * N + i] = dk;
             }
         }
     }
