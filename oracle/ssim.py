@@ -79,7 +79,7 @@ def image_loss_grad(img, target, lam=0.2):
     y = torch.tensor(np.asarray(target, np.float64))
     loss = image_loss_torch(x, y, lam)
     loss.backward()
-    return float(loss), x.grad.numpy()
+    return float(loss.detach()), x.grad.numpy()
 
 
 __all__ = ["gauss_1d", "ssim_map", "image_loss", "image_loss_torch", "image_loss_grad", "WIN", "SIGMA", "C1",

@@ -105,3 +105,23 @@ def test_train_step_update_applies_adam_to_every_group(gpu):
         want, _, _ = AD.step(before[k], grads[k], 0.0, 0.0, 1, f32(render.ADAM_LR[k]), **HP)
         got = p.detach().float().cpu().numpy()
         assert np.all(np.abs(got - want) <= 2.0 ** -22 * np.abs(want) + 1e-5 * render.ADAM_LR[k]), k
+
+
+def test_adam_edge_cases(gpu):
+    api = gpu
+    from paper_2407_10707_gb300 import _lib as L
+    api.avatar_adam([], 1)  # no groups: nothing to do
+    e = torch.zeros(0, device="cuda")
+    api.avatar_adam([(e, e, e, e, 0.1)], 1)  # an empty group
+    # sixteen groups (the limit) in one launch, each a one-element tensor
+    ps = [torch.full((1,), float(k), device="cuda") for k in range(16)]
+    gs = [torch.ones(1, device="cuda") for _ in range(16)]
+    ms = [torch.zeros(1, device="cuda") for _ in range(16)]
+    vs = [torch.zeros(1, device="cuda") for _ in range(16)]
+    api.avatar_adam([(ps[k], gs[k], ms[k], vs[k], 0.5) for k in range(16)], 1)
+    torch.cuda.synchronize()
+    assert all(abs(float(ps[k]) - (k - 0.5)) < 1e-6 for k in range(16))  # first step: lr sign(g)
+    with pytest.raises(ValueError):
+        api.avatar_adam([(ps[0], gs[0], ms[0], vs[0], 0.5)] * 17, 1)
+    with pytest.raises(L.AvatarError):
+        api.avatar_adam([(ps[0], gs[0], ms[0], vs[0], 0.5)], 0)  # steps count from 1

@@ -133,3 +133,14 @@ def test_densify_grows_the_avatar(gpu):
     r = render.Renderer(st)
     r.forward()
     r.check()
+
+
+def test_densify_zero_capacity_reports_the_count(gpu):
+    api = gpu
+    sc = scene("c1_small")
+    av = sc.avatar
+    st = api.status_word("cuda")
+    words = _words(0, 1).reshape(3, 0)
+    got = _run(api, np.zeros((0, 3), np.int64), av.faces, av.xv, words, status=st)
+    assert int(got["count"][0]) == int(np.floor(0.02 * len(av.faces)))
+    assert int(st.item()) == 3 and got["ng"].sum() == 0  # overflow flagged, nothing drawn

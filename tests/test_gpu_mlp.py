@@ -169,3 +169,19 @@ def test_average_displacement_sets_the_avatar_displacement(gpu):
     r = render.Renderer(st)
     r.forward()
     r.check()
+
+
+def test_mlp_many_poses_on_one_tile(gpu):
+    """100 points (one tile, one CTA) averaged over 300 poses: one CTA walks
+    a long list of (tile, pose) items through both slots."""
+    api = gpu
+    rng = np.random.default_rng(17)
+    w = synth.mlp_weights(6)
+    x = rng.uniform(-1.0, 1.0, size=(100, 3))
+    poses = rng.normal(0.0, 0.3, size=(300, 72))
+    got = _run(api, x, poses, w)
+    per = [_oracle(x, th, w, bf=True) for th in poses]
+    want = np.mean(per, axis=0)
+    rms = np.sqrt(np.mean([np.mean(p ** 2) for p in per]))
+    d = np.abs(got - want)
+    assert d.max() <= 2e-2 * rms and d.mean() <= 2e-4 * rms, (d.max() / rms, d.mean() / rms)
