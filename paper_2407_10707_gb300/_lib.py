@@ -25,6 +25,7 @@ DTYPE_BF16 = 1
 TUNE_BLEND_PPT = 0
 TUNE_BLEND_BWD_PPT = 1
 TUNE_BATCH_TILE = 2
+TUNE_VIS_CLUSTER = 3
 
 
 class AvatarError(RuntimeError):

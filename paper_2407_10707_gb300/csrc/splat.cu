@@ -143,17 +143,30 @@ blend_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_g
                         n_last);
 }
 
+// Four independent warps per CTA, each one (tile, pixel box) item.
+constexpr int BWD_WARPS = 4;
+
 template <int TS, int PPT>
-__global__ void __launch_bounds__(TS *TS / PPT)
+__global__ void __launch_bounds__(BWD_WARPS * 32)
 blend_backward_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_gauss,
                       const float4 *__restrict__ rec0, const float4 *__restrict__ rec1, const float4 *__restrict__ rec2,
-                      int W, int H, int ntx, const float *__restrict__ T_final, const int32_t *__restrict__ n_last,
-                      const float *__restrict__ d_image, int G, float *__restrict__ d_mean2d,
-                      float *__restrict__ d_conic, float *__restrict__ d_opacity, float *__restrict__ d_color)
+                      int W, int H, int ntx, int ntiles, const float *__restrict__ T_final,
+                      const int32_t *__restrict__ n_last, const float *__restrict__ d_image, int G,
+                      float *__restrict__ d_mean2d, float *__restrict__ d_conic, float *__restrict__ d_opacity,
+                      float *__restrict__ d_color)
 {
-    const int tile = blockIdx.x;
-    blend_backward_tile<TS, PPT>(ranges[tile], pair_gauss, rec0, rec1, rec2, W, H, tile % ntx, tile / ntx, T_final,
-                                 n_last, d_image, (size_t)G, d_mean2d, d_conic, d_opacity, d_color);
+    constexpr int NB = TS * TS / (32 * PPT);  // pixel boxes per tile
+    __shared__ float4 s0[BWD_WARPS][2][32];
+    __shared__ float4 s1[BWD_WARPS][2][32];
+    __shared__ float4 s2[BWD_WARPS][2][32];
+    __shared__ int sg[BWD_WARPS][2][32];
+    const int warp = threadIdx.x >> 5;
+    const int item = blockIdx.x * BWD_WARPS + warp;
+    if (item >= ntiles * NB) return;  // warp-uniform; the kernel has no CTA barrier
+    const int tile = item / NB;
+    blend_backward_box<TS, PPT>(ranges[tile], pair_gauss, rec0, rec1, rec2, W, H, tile % ntx, tile / ntx, item % NB,
+                                T_final, n_last, d_image, (size_t)G, d_mean2d, d_conic, d_opacity, d_color, s0[warp],
+                                s1[warp], s2[warp], sg[warp]);
 }
 
 __global__ void __launch_bounds__(256)
@@ -347,8 +360,10 @@ template <int TS, int PPT>
 void launch_blend_bwd(const avatar_splat_args *a, const avatar_splat_grads *g, const SplatWs &w, int ntiles, int ntx,
                       int G, cudaStream_t st)
 {
-    blend_backward_kernel<TS, PPT><<<ntiles, TS * TS / PPT, 0, st>>>(
-        (const int2 *)a->tile_range, a->pair_gauss, w.rec0, w.rec1, w.rec2, a->cam.width, a->cam.height, ntx,
+    constexpr int NB = TS * TS / (32 * PPT);
+    const int blocks = (int)(((long long)ntiles * NB + BWD_WARPS - 1) / BWD_WARPS);
+    blend_backward_kernel<TS, PPT><<<blocks, BWD_WARPS * 32, 0, st>>>(
+        (const int2 *)a->tile_range, a->pair_gauss, w.rec0, w.rec1, w.rec2, a->cam.width, a->cam.height, ntx, ntiles,
         a->T_final, a->n_last, g->d_image, G, w.d_mean2d, w.d_conic, g->d_opacity, g->d_color);
 }
 

@@ -904,6 +904,144 @@ __device__ __forceinline__ void blend_backward_tile(int2 rg, const int32_t *__re
     }
 }
 
+// The same adjoint with every warp on its own: warp box wbox of tile (tx, ty)
+// walks the tile's list back to front from its own pixels' largest n_last,
+// 32 entries at a time.  Each batch's records go to the warp's two buffers
+// (s0/s1/s2/sg [2][32]) by asynchronous copies while the previous batch is
+// walked, and the lanes test the batch's rects against the box for a hit
+// mask, so no warp waits for another.  The per-pixel arithmetic and the
+// per-Gaussian sums are those of blend_backward_tile.
+template <int TS, int PPT>
+__device__ __forceinline__ void blend_backward_box(int2 rg, const int32_t *__restrict__ pair_gauss,
+                                                   const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
+                                                   const float4 *__restrict__ rec2, int W, int H, int tx, int ty,
+                                                   int wbox, const float *__restrict__ T_final,
+                                                   const int32_t *__restrict__ n_last,
+                                                   const float *__restrict__ d_image, size_t cs,
+                                                   float *__restrict__ d_mean2d, float *__restrict__ d_conic,
+                                                   float *__restrict__ d_opacity, float *__restrict__ d_color,
+                                                   float4 (*s0)[32], float4 (*s1)[32], float4 (*s2)[32],
+                                                   int (*sg)[32])
+{
+    using Box = BoxMap<TS, PPT>;
+    constexpr float LN2 = 0.6931471805599453f;
+    const int lane = threadIdx.x & 31;
+    const Box box(tx, ty, wbox);
+    const int bx0 = box.x0, by0 = box.y0, bx1 = bx0 + Box::BW - 1, by1 = by0 + Box::BH - 1;
+    float fx[PPT], fy[PPT], T[PPT], dC0[PPT], dC1[PPT], dC2[PPT], acc0[PPT], acc1[PPT], acc2[PPT];
+    int my_last[PPT];
+    int mx_last = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int px = box.px(lane), py = box.py(lane, k);
+        const bool inside = px < W && py < H;
+        const int pix = py * W + px;
+        fx[k] = px + 0.5f;
+        fy[k] = py + 0.5f;
+        my_last[k] = inside ? n_last[pix] : 0;
+        T[k] = inside ? T_final[pix] : 1.f;
+        dC0[k] = inside ? d_image[pix] : 0.f;
+        dC1[k] = inside ? d_image[W * H + pix] : 0.f;
+        dC2[k] = inside ? d_image[2 * W * H + pix] : 0.f;
+        acc0[k] = acc1[k] = acc2[k] = 0.f;
+        mx_last = max(mx_last, my_last[k]);
+    }
+    const int n = (int)__reduce_max_sync(0xffffffffu, (unsigned)mx_last);
+    // batch [end - 32, end) into buffer b; returns the mask of its entries
+    // whose rect meets the box
+    auto fetch = [&](int end, int b) -> unsigned {
+        const int idx = end - 32 + lane;
+        bool hit = false;
+        if (idx >= 0) {
+            const int g = pair_gauss[rg.x + idx];
+            sg[b][lane] = g;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s0[b][lane])),
+                         "l"(rec0 + g)
+                         : "memory");
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s1[b][lane])),
+                         "l"(rec1 + g)
+                         : "memory");
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s2[b][lane])),
+                         "l"(rec2 + g)
+                         : "memory");
+            const float2 rr = __ldg(reinterpret_cast<const float2 *>(rec1 + g) + 1);
+            const int a = __float_as_int(rr.x), c = __float_as_int(rr.y);
+            hit = (c & 0xffff) >= bx0 && (a & 0xffff) <= bx1 && (int)((unsigned)c >> 16) >= by0 &&
+                  (int)((unsigned)a >> 16) <= by1;
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        return __ballot_sync(0xffffffffu, hit);
+    };
+    if (n == 0) return;
+    unsigned hits = fetch(n, 0);
+    int b = 0;
+    for (int end = n; end > 0; end -= 32, b ^= 1) {
+        const bool more = end > 32;
+        const unsigned hits_next = more ? fetch(end - 32, b ^ 1) : 0u;
+        if (more)
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        else
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncwarp();
+        while (hits) {
+            const int sj = 31 - __clz(hits);
+            hits &= ~(1u << sj);
+            const int j = end - 32 + sj;
+            const float4 r1 = s1[b][sj];
+            const float4 r0 = s0[b][sj];
+            const float4 c = s2[b][sj];
+            float g_col0 = 0.f, g_col1 = 0.f, g_col2 = 0.f, g_op = 0.f, g_mx = 0.f, g_my = 0.f, g_ca = 0.f,
+                  g_cb = 0.f, g_cc = 0.f;
+            bool contrib = false;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (j >= my_last[k]) continue;
+                float dx = fx[k] - r0.x, dy = fy[k] - r0.y;
+                float l2a = fmaf(fmaf(r0.z, dx, r0.w * dy), dx, fmaf(r1.x * dy, dy, r1.y));
+                if (l2a < LOG2_ALPHA_MIN) continue;
+                float raw = exp2f(l2a);
+                float alpha = fminf(0.99f, raw);
+                contrib = true;
+                T[k] = T[k] / (1.f - alpha);
+                float wgt = alpha * T[k];
+                g_col0 = fmaf(wgt, dC0[k], g_col0);
+                g_col1 = fmaf(wgt, dC1[k], g_col1);
+                g_col2 = fmaf(wgt, dC2[k], g_col2);
+                float dalpha = T[k] * ((c.x - acc0[k]) * dC0[k] + (c.y - acc1[k]) * dC1[k] + (c.z - acc2[k]) * dC2[k]);
+                acc0[k] = alpha * c.x + (1.f - alpha) * acc0[k];
+                acc1[k] = alpha * c.y + (1.f - alpha) * acc1[k];
+                acc2[k] = alpha * c.z + (1.f - alpha) * acc2[k];
+                if (raw < 0.99f) {
+                    float dpow = dalpha * raw;
+                    g_op += dpow;
+                    float ca = -2.f * LN2 * r0.z, cb = -LN2 * r0.w, cc = -2.f * LN2 * r1.x;
+                    g_mx = fmaf(dpow, ca * dx + cb * dy, g_mx);
+                    g_my = fmaf(dpow, cb * dx + cc * dy, g_my);
+                    g_ca = fmaf(-0.5f * dpow, dx * dx, g_ca);
+                    g_cb = fmaf(-dpow, dx * dy, g_cb);
+                    g_cc = fmaf(-0.5f * dpow, dy * dy, g_cc);
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+                const float v[16] = {g_col0, g_col1, g_col2, g_op, g_mx, g_my, g_ca, g_cb, g_cc,
+                                     0.f,    0.f,    0.f,    0.f,  0.f,  0.f,  0.f};
+                const float tot = warp_reduce_scatter16(v);
+                const int vi = lane >> 1;
+                if (!(lane & 1) && vi < 9) {
+                    const size_t g = (size_t)sg[b][sj];
+                    float *dst = vi < 3   ? d_color + (size_t)vi * cs
+                                 : vi == 3 ? d_opacity
+                                 : vi < 6  ? d_mean2d + (size_t)(vi - 4) * cs
+                                           : d_conic + (size_t)(vi - 6) * cs;
+                    atomicAdd(dst + g, vi == 3 ? tot / c.w : tot);
+                }
+            }
+        }
+        __syncwarp();  // every lane is done with buffer b before it is refilled
+        hits = hits_next;
+    }
+}
+
 // ---------------------------------------------------------------- projection adjoint
 // Gradients of the EWA projection of Gaussian i (xd [3][cs], cov [6][cs])
 // from d_mean2d (dmx, dmy) and d_conic (da, db, dc): d_xd[3], d_cov[6].

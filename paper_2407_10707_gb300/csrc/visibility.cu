@@ -781,7 +781,10 @@ int vis_run(avatar_ctx *ctx, const avatar_vis_args *a, int B, void *ws, size_t w
     p.H = (int)H;
     p.M = (int)M;
     p.biasq = (int)biasq;
-    int CL = cluster_size_for(a->R);
+    int CL = ctx->tune[AVATAR_TUNE_VIS_CLUSTER] ? ctx->tune[AVATAR_TUNE_VIS_CLUSTER] : cluster_size_for(a->R);
+    while (CL < 8 && (size_t)(a->R / CL) * a->R * sizeof(int) + (size_t)VIS_VCAP * sizeof(uint2) >
+                         (size_t)ctx->max_smem_optin)
+        CL <<= 1;
     p.rows_per_cta = a->R / CL;
     p.inv_rows = ((1 << 20) + p.rows_per_cta - 1) / p.rows_per_cta;
     size_t smem = (size_t)p.rows_per_cta * a->R * sizeof(int) + (size_t)VIS_VCAP * sizeof(uint2);

@@ -128,6 +128,35 @@ def test_visibility_bits_bit_exact(gpu, name, over):
     assert np.array_equal(N(bits_l).view(np.uint32), light_ordered_bits(ref, sc.dmap))
 
 
+@pytest.mark.parametrize("cl", [2, 4, 8])
+def test_visibility_cluster_size_knob_keeps_the_bits(gpu, cl):
+    """CTAs per direction are a work split only: at 64^2 (one CTA by
+    default) and 128^2 the bits at 2, 4 and 8 CTAs per direction are the
+    oracle's."""
+    api, render = gpu
+    from paper_2407_10707_gb300 import _lib as L
+    lib = L.load()
+    ctx = api.context()
+    assert lib.avatar_ctx_set_tuning(ctx, L.TUNE_VIS_CLUSTER, 3) != 0     # not a power of two
+    assert lib.avatar_ctx_set_tuning(ctx, L.TUNE_VIS_CLUSTER, 16) != 0    # above the portable cluster size
+    try:
+        for over in ({}, dict(n_vertices=1_003, n_dirs=32, depth_res=128)):
+            sc = synth.config_scene("c1_small", **over)
+            sk = O.skin(sc.avatar, O.fk(sc.avatar.parents, sc.avatar.joints, sc.avatar.pose))
+            ref = _oracle_bits(sc, sk["xp"])
+            c = _vis_case(sc, sk["xp"])
+            assert lib.avatar_ctx_set_tuning(ctx, L.TUNE_VIS_CLUSTER, cl) == 0
+            assert lib.avatar_ctx_get_tuning(ctx, L.TUNE_VIS_CLUSTER) == cl
+            status = api.status_word("cuda")
+            bits = api.avatar_visibility(c["xp"], c["faces"], c["frames"], c["center"], c["half"], c["bias"],
+                                         c["R"], status=status, cull_back=True)
+            torch.cuda.synchronize()
+            api.raise_on_status(status)
+            assert np.array_equal(N(bits).view(np.uint32), ref)
+    finally:
+        assert lib.avatar_ctx_set_tuning(ctx, L.TUNE_VIS_CLUSTER, 0) == 0
+
+
 def test_visibility_edge_cases(gpu):
     api, render = gpu
     rng = np.random.default_rng(3)
