@@ -85,7 +85,7 @@ int avatar_ctx_sm_count(const avatar_ctx *ctx);
  * the choices on the actual workload and sets the fastest. */
 enum avatar_tune_key {
     AVATAR_TUNE_BLEND_PPT = 0,     /* pixels per thread in the blend: 1, 2 or 4 (default 1) */
-    AVATAR_TUNE_BLEND_BWD_PPT = 1, /* pixels per thread in the blend backward: 1, 2 or 4 (default 2) */
+    AVATAR_TUNE_BLEND_BWD_PPT = 1, /* pixels per thread in the blend backward: 1, 2 or 4 (default 1) */
     AVATAR_TUNE_BATCH_TILE = 2,    /* tile edge of the batched render when its desc says 0 (default 16) */
     AVATAR_TUNE_VIS_CLUSTER = 3,   /* CTAs per direction of avatar_visibility: 0 (default: 32 KB depth-map
                                       slabs, at most 8), 2, 4 or 8; raised where the slab would not fit */

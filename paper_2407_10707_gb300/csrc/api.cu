@@ -68,7 +68,7 @@ extern "C" int avatar_ctx_create(avatar_ctx **out, int device)
     c->cluster_ok = cluster;
     for (int i = 0; i < AVATAR_TUNE_COUNT; ++i) c->tune[i] = 0;
     c->tune[AVATAR_TUNE_BLEND_PPT] = 1;
-    c->tune[AVATAR_TUNE_BLEND_BWD_PPT] = 2;
+    c->tune[AVATAR_TUNE_BLEND_BWD_PPT] = 1;
     c->tune[AVATAR_TUNE_BATCH_TILE] = 16;
     *out = c;
     return AVATAR_OK;

@@ -399,7 +399,7 @@ blend_batch_kernel(const BatchView *__restrict__ views, int V, int T, const int2
 }
 
 template <int TS, int PPT>
-__global__ void __launch_bounds__(TS *TS / PPT)
+__global__ void __launch_bounds__(BWD_WARPS * 32)
 blend_backward_batch_kernel(const BatchView *__restrict__ views, int V, int T, const int2 *__restrict__ ranges,
                             const int32_t *__restrict__ pairs, const float4 *__restrict__ rec0,
                             const float4 *__restrict__ rec1, const float4 *__restrict__ rec2,
@@ -407,20 +407,27 @@ blend_backward_batch_kernel(const BatchView *__restrict__ views, int V, int T, c
                             const float *__restrict__ d_images, long long VG, float *d_mean2d, float *d_conic,
                             float *d_opacity, float *d_color, int32_t *counter)
 {
-    __shared__ int s_t;
+    // persistent warps take (tile, pixel box) items from the device counter
+    constexpr int NB = TS * TS / (32 * PPT);
+    __shared__ float4 s0[BWD_WARPS][2][32];
+    __shared__ float4 s1[BWD_WARPS][2][32];
+    __shared__ float4 s2[BWD_WARPS][2][32];
+    __shared__ int sg[BWD_WARPS][2][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int items = T * NB;
     for (;;) {
-        if (threadIdx.x == 0) s_t = atomicAdd(counter, 1);
-        __syncthreads();
-        const int t = s_t;
-        __syncthreads();
-        if (t >= T) break;
+        int it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= items) break;
+        const int t = it / NB;
         const int v = view_of_tile(views, V, t);
         const int W = views[v].cam.W, H = views[v].cam.H, ntx = views[v].ntx;
         const int local = t - views[v].tile_base;
         const size_t po = (size_t)views[v].pix_off;
-        blend_backward_tile<TS, PPT>(ranges[t], pairs, rec0, rec1, rec2, W, H, local % ntx, local / ntx, T_final + po,
-                                     n_last + po, d_images + 3 * po, (size_t)VG, d_mean2d, d_conic, d_opacity,
-                                     d_color);
+        blend_backward_box<TS, PPT>(ranges[t], pairs, rec0, rec1, rec2, W, H, local % ntx, local / ntx, it % NB,
+                                    T_final + po, n_last + po, d_images + 3 * po, (size_t)VG, d_mean2d, d_conic,
+                                    d_opacity, d_color, s0[warp], s1[warp], s2[warp], sg[warp]);
     }
 }
 
@@ -574,11 +581,13 @@ int launch_blend_bwd_batch(const avatar_ctx *ctx, const avatar_batch_desc *d, co
                            const BatchWs &w, const BatchDims &m, int T, cudaStream_t st)
 {
     auto kern = blend_backward_batch_kernel<TS, PPT>;
+    constexpr int NB = TS * TS / (32 * PPT);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TS * TS / PPT, 0) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BWD_WARPS * 32, 0) != cudaSuccess || per_sm < 1)
         per_sm = 1;
-    const int grid = std::min<long long>((long long)ctx->sm_count * per_sm, std::max(T, 1));
-    kern<<<grid, TS * TS / PPT, 0, st>>>(w.views, d->V, T, w.ranges, w.pval_a, w.rec0, w.rec1, w.rec2, w.T_final,
+    const long long wblocks = ((long long)std::max(T, 1) * NB + BWD_WARPS - 1) / BWD_WARPS;
+    const int grid = (int)std::min<long long>((long long)ctx->sm_count * per_sm, wblocks);
+    kern<<<grid, BWD_WARPS * 32, 0, st>>>(w.views, d->V, T, w.ranges, w.pval_a, w.rec0, w.rec1, w.rec2, w.T_final,
                                          w.n_last, g->d_images, m.VG, w.d_mean2d, w.d_conic, w.d_opacity_v,
                                          w.d_color, w.counter);
     AV_CHECK_LAUNCH();

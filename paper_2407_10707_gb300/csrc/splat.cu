@@ -143,9 +143,7 @@ blend_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_g
                         n_last);
 }
 
-// Four independent warps per CTA, each one (tile, pixel box) item.
-constexpr int BWD_WARPS = 4;
-
+// BWD_WARPS independent warps per CTA, each one (tile, pixel box) item.
 template <int TS, int PPT>
 __global__ void __launch_bounds__(BWD_WARPS * 32)
 blend_backward_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_gauss,

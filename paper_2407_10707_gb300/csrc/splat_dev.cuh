@@ -732,185 +732,19 @@ __device__ __forceinline__ void blend_tile(int2 rg, const int32_t *__restrict__ 
     }
 }
 
-// Adjoint of blend_tile: reverse traversal from the per-pixel checkpoint
-// (T_final, n_last); per-Gaussian sums are warp-reduced and added with one
-// atomic per warp into d_color [3][cs], d_opacity [cs], d_mean2d [2][cs] and
-// d_conic [3][cs] at the Gaussian's pair value.
-template <int TS, int PPT>
-__device__ __forceinline__ void blend_backward_tile(int2 rg, const int32_t *__restrict__ pair_gauss,
-                                                    const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
-                                                    const float4 *__restrict__ rec2, int W, int H, int tx, int ty,
-                                                    const float *__restrict__ T_final,
-                                                    const int32_t *__restrict__ n_last,
-                                                    const float *__restrict__ d_image, size_t cs,
-                                                    float *__restrict__ d_mean2d, float *__restrict__ d_conic,
-                                                    float *__restrict__ d_opacity, float *__restrict__ d_color)
-{
-    constexpr int NTH = TS * TS / PPT;
-    constexpr float LN2 = 0.6931471805599453f;
-    // double-buffered record batches (asynchronous copies) where they fit in
-    // 48 KB of static shared memory, as in the forward
-    constexpr int NBUF = NTH <= 256 ? 2 : 1;
-    __shared__ float4 s0[NBUF][NTH];
-    __shared__ float4 s1[NBUF][NTH];
-    __shared__ float4 s2[NBUF][NTH];
-    __shared__ int sg[NBUF][NTH];
-    __shared__ unsigned smask[NBUF][NTH];
-    __shared__ int s_max;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const unsigned wbit = 1u << (tid >> 5);
-    const BoxMap<TS, PPT> box(tx, ty, tid >> 5);
-    float fx[PPT], fy[PPT], T[PPT], dC0[PPT], dC1[PPT], dC2[PPT], acc0[PPT], acc1[PPT], acc2[PPT];
-    int my_last[PPT];
-    int mx_last = 0;
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const int px = box.px(lane), py = box.py(lane, k);
-        const bool inside = px < W && py < H;
-        const int pix = py * W + px;
-        fx[k] = px + 0.5f;
-        fy[k] = py + 0.5f;
-        my_last[k] = inside ? n_last[pix] : 0;
-        T[k] = inside ? T_final[pix] : 1.f;
-        dC0[k] = inside ? d_image[pix] : 0.f;
-        dC1[k] = inside ? d_image[W * H + pix] : 0.f;
-        dC2[k] = inside ? d_image[2 * W * H + pix] : 0.f;
-        acc0[k] = acc1[k] = acc2[k] = 0.f;
-        mx_last = max(mx_last, my_last[k]);
-    }
-    __syncthreads();  // every thread is done with the previous tile's s_max
-    if (tid == 0) s_max = 0;
-    __syncthreads();
-    atomicMax(&s_max, mx_last);
-    __syncthreads();
-    const int n = s_max;
-    // walk buffer b (list positions start .. end - 1) from back to front
-    auto walk = [&](int b, int start, int end) {
-        for (int j = end - 1; j >= start; --j) {
-            const int sj = j - start;
-            if (!(smask[b][sj] & wbit)) continue;  // warp-uniform: rect misses this warp's box
-            const float4 r1 = s1[b][sj];
-            const float4 r0 = s0[b][sj];
-            const float4 c = s2[b][sj];
-            // per-thread sums over this thread's pixels
-            float g_col0 = 0.f, g_col1 = 0.f, g_col2 = 0.f, g_op = 0.f, g_mx = 0.f, g_my = 0.f, g_ca = 0.f,
-                  g_cb = 0.f, g_cc = 0.f;
-            bool contrib = false;
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                if (j >= my_last[k]) continue;
-                float dx = fx[k] - r0.x, dy = fy[k] - r0.y;
-                float l2a = fmaf(fmaf(r0.z, dx, r0.w * dy), dx, fmaf(r1.x * dy, dy, r1.y));
-                if (l2a < LOG2_ALPHA_MIN) continue;
-                float raw = exp2f(l2a);
-                float alpha = fminf(0.99f, raw);
-                contrib = true;
-                T[k] = T[k] / (1.f - alpha);
-                float wgt = alpha * T[k];
-                g_col0 = fmaf(wgt, dC0[k], g_col0);
-                g_col1 = fmaf(wgt, dC1[k], g_col1);
-                g_col2 = fmaf(wgt, dC2[k], g_col2);
-                float dalpha = T[k] * ((c.x - acc0[k]) * dC0[k] + (c.y - acc1[k]) * dC1[k] + (c.z - acc2[k]) * dC2[k]);
-                acc0[k] = alpha * c.x + (1.f - alpha) * acc0[k];
-                acc1[k] = alpha * c.y + (1.f - alpha) * acc1[k];
-                acc2[k] = alpha * c.z + (1.f - alpha) * acc2[k];
-                if (raw < 0.99f) {
-                    float dpow = dalpha * raw;  // d alpha / d power = alpha
-                    g_op += dpow;               // d alpha / d o = alpha / o (divided once below)
-                    float ca = -2.f * LN2 * r0.z, cb = -LN2 * r0.w, cc = -2.f * LN2 * r1.x;
-                    g_mx = fmaf(dpow, ca * dx + cb * dy, g_mx);
-                    g_my = fmaf(dpow, cb * dx + cc * dy, g_my);
-                    g_ca = fmaf(-0.5f * dpow, dx * dx, g_ca);
-                    g_cb = fmaf(-dpow, dx * dy, g_cb);
-                    g_cc = fmaf(-0.5f * dpow, dy * dy, g_cc);
-                }
-            }
-            if (__any_sync(0xffffffffu, contrib)) {
-                // the nine sums at once; lane 2i then adds the total of value i
-                const float v[16] = {g_col0, g_col1, g_col2, g_op, g_mx, g_my, g_ca, g_cb, g_cc,
-                                     0.f,    0.f,    0.f,    0.f,  0.f,  0.f,  0.f};
-                const float tot = warp_reduce_scatter16(v);
-                const int vi = lane >> 1;
-                if (!(lane & 1) && vi < 9) {
-                    const size_t g = (size_t)sg[b][sj];
-                    float *dst = vi < 3   ? d_color + (size_t)vi * cs
-                                 : vi == 3 ? d_opacity
-                                 : vi < 6  ? d_mean2d + (size_t)(vi - 4) * cs
-                                           : d_conic + (size_t)(vi - 6) * cs;
-                    atomicAdd(dst + g, vi == 3 ? tot / c.w : tot);
-                }
-            }
-        }
-    };
-    if constexpr (NBUF == 2) {
-        float2 prect = make_float2(0.f, 0.f);
-        int pg = 0;
-        bool have = false;
-        // the batch that ends at list position end (exclusive) into buffer b
-        auto fetch = [&](int end, int b) {
-            const int idx = max(0, end - NTH) + tid;
-            have = idx < end;
-            if (have) {
-                pg = pair_gauss[rg.x + idx];
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s0[b][tid])),
-                             "l"(rec0 + pg)
-                             : "memory");
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s1[b][tid])),
-                             "l"(rec1 + pg)
-                             : "memory");
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s2[b][tid])),
-                             "l"(rec2 + pg)
-                             : "memory");
-                prect = __ldg(reinterpret_cast<const float2 *>(rec1 + pg) + 1);
-            }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-        };
-        auto stash = [&](int b) {
-            if (have) {
-                sg[b][tid] = pg;
-                smask[b][tid] = BoxMap<TS, PPT>::mask(tx, ty, prect.x, prect.y);
-            }
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-        };
-        if (n > 0) {
-            fetch(n, 0);
-            stash(0);
-        }
-        int b = 0;
-        for (int end = n; end > 0; end -= NTH, b ^= 1) {
-            const int start = max(0, end - NTH);
-            __syncthreads();  // batch b is in place, and every warp is done with buffer b ^ 1
-            if (start > 0) fetch(start, b ^ 1);
-            walk(b, start, end);
-            if (start > 0) stash(b ^ 1);
-        }
-    } else {
-        for (int end = n; end > 0; end -= NTH) {
-            const int start = max(0, end - NTH);
-            __syncthreads();
-            int idx = start + tid;
-            if (idx < end) {
-                int g = pair_gauss[rg.x + idx];
-                sg[0][tid] = g;
-                s0[0][tid] = rec0[g];
-                float4 r1 = rec1[g];
-                s1[0][tid] = r1;
-                s2[0][tid] = rec2[g];
-                smask[0][tid] = BoxMap<TS, PPT>::mask(tx, ty, r1.z, r1.w);
-            }
-            __syncthreads();
-            walk(0, start, end);
-        }
-    }
-}
+// Warps per CTA of the kernels built on blend_backward_box.
+constexpr int BWD_WARPS = 4;
 
-// The same adjoint with every warp on its own: warp box wbox of tile (tx, ty)
-// walks the tile's list back to front from its own pixels' largest n_last,
-// 32 entries at a time.  Each batch's records go to the warp's two buffers
+// Adjoint of blend_tile for pixel box wbox of tile (tx, ty), by one warp on
+// its own: reverse traversal of the tile's list from the per-pixel
+// checkpoint (T_final, n_last), starting at the box's largest n_last, 32
+// entries at a time.  Each batch's records go to the warp's two buffers
 // (s0/s1/s2/sg [2][32]) by asynchronous copies while the previous batch is
 // walked, and the lanes test the batch's rects against the box for a hit
-// mask, so no warp waits for another.  The per-pixel arithmetic and the
-// per-Gaussian sums are those of blend_backward_tile.
+// mask, so no warp waits for another.  Per hit Gaussian the warp's nine sums
+// (d_color [3][cs], d_opacity [cs], d_mean2d [2][cs], d_conic [3][cs] at the
+// Gaussian's pair value) are reduced together by recursive halving and added
+// by nine lanes with one atomic each.
 template <int TS, int PPT>
 __device__ __forceinline__ void blend_backward_box(int2 rg, const int32_t *__restrict__ pair_gauss,
                                                    const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,

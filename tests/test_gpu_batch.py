@@ -154,7 +154,7 @@ def test_autotune_keeps_the_images(gpu, batch):
     print(f"autotuned: tile {tile}, blend pixels/thread {ppt}, backward pixels/thread {bppt}")
     assert torch.equal(br.images, img0)   # the image does not depend on the tile edge or the split
     lib = L_lib()
-    for key, want in ((2, 16), (0, 1), (1, 2)):   # restore the defaults for later tests
+    for key, want in ((2, 16), (0, 1), (1, 1)):   # restore the defaults for later tests
         lib.avatar_ctx_set_tuning(api.context(), key, want)
 
 
