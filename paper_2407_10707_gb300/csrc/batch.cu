@@ -9,9 +9,9 @@
 //   bin         one depth sort over all V G Gaussians, one pair scan, pairs
 //               keyed by a global tile id (view tiles back to back), one
 //               stable tile sort, one range pass
-//   blend       persistent CTAs take global tiles from a device counter, so
-//               views of different size and tiles of different load balance
-//               without host involvement
+//   blend       persistent warps take (global tile, pixel box) items from a
+//               device counter, so views of different size and tiles of
+//               different load balance without host involvement
 // The backward mirrors it: one persistent blend adjoint, the shading adjoint
 // over the views, a per-Gaussian pass that applies the projection adjoint
 // and sums every view's gradients into its pose (and the pose-independent
@@ -377,24 +377,30 @@ __device__ __forceinline__ int view_of_tile(const BatchView *__restrict__ views,
 
 // Persistent blend over every tile of every view.
 template <int TS, int PPT>
-__global__ void __launch_bounds__(TS *TS / PPT)
+__global__ void __launch_bounds__(BWD_WARPS * 32)
 blend_batch_kernel(const BatchView *__restrict__ views, int V, int T, const int2 *__restrict__ ranges,
                    const int32_t *__restrict__ pairs, const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
                    const float4 *__restrict__ rec2, float *images, float *T_final, int32_t *n_last, int32_t *counter)
 {
-    __shared__ int s_t;
+    // persistent warps take (tile, pixel box) items from the device counter
+    constexpr int NB = TS * TS / (32 * PPT);
+    __shared__ float4 s0[BWD_WARPS][2][32];
+    __shared__ float4 s1[BWD_WARPS][2][32];
+    __shared__ float4 s2[BWD_WARPS][2][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int items = T * NB;
     for (;;) {
-        if (threadIdx.x == 0) s_t = atomicAdd(counter, 1);
-        __syncthreads();
-        const int t = s_t;
-        __syncthreads();
-        if (t >= T) break;
+        int it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= items) break;
+        const int t = it / NB;
         const int v = view_of_tile(views, V, t);
         const int W = views[v].cam.W, H = views[v].cam.H, ntx = views[v].ntx;
         const int local = t - views[v].tile_base;
         const size_t po = (size_t)views[v].pix_off;
-        blend_tile<TS, PPT>(ranges[t], pairs, rec0, rec1, rec2, W, H, local % ntx, local / ntx, images + 3 * po,
-                            T_final + po, n_last + po);
+        blend_box<TS, PPT>(ranges[t], pairs, rec0, rec1, rec2, W, H, local % ntx, local / ntx, it % NB,
+                           images + 3 * po, T_final + po, n_last + po, s0[warp], s1[warp], s2[warp]);
     }
 }
 
@@ -566,11 +572,13 @@ template <int TS, int PPT>
 int launch_blend_batch(const avatar_ctx *ctx, const avatar_batch_desc *d, const BatchWs &w, int T, cudaStream_t st)
 {
     auto kern = blend_batch_kernel<TS, PPT>;
+    constexpr int NB = TS * TS / (32 * PPT);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TS * TS / PPT, 0) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BWD_WARPS * 32, 0) != cudaSuccess || per_sm < 1)
         per_sm = 1;
-    const int grid = std::min<long long>((long long)ctx->sm_count * per_sm, std::max(T, 1));
-    kern<<<grid, TS * TS / PPT, 0, st>>>(w.views, d->V, T, w.ranges, w.pval_a, w.rec0, w.rec1, w.rec2, d->images,
+    const long long wblocks = ((long long)std::max(T, 1) * NB + BWD_WARPS - 1) / BWD_WARPS;
+    const int grid = (int)std::min<long long>((long long)ctx->sm_count * per_sm, wblocks);
+    kern<<<grid, BWD_WARPS * 32, 0, st>>>(w.views, d->V, T, w.ranges, w.pval_a, w.rec0, w.rec1, w.rec2, d->images,
                                          w.T_final, w.n_last, w.counter);
     AV_CHECK_LAUNCH();
     return AVATAR_OK;

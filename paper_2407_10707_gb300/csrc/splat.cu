@@ -12,9 +12,10 @@
 //   tile sort stable LSD radix sort of the pairs on the tile id only; with
 //             the depth-ordered emission this yields (tile, depth, index).
 //   ranges    begin/end of every tile's run.
-//   blend     one CTA per tile, one thread per pixel, Gaussians staged in
-//             shared memory one CTA-width batch at a time; the CTA leaves
-//             as soon as every pixel is saturated.
+//   blend     one warp per (tile, pixel box), independent of the others:
+//             32-entry record batches prefetched into the warp's own
+//             shared-memory buffers; the warp leaves as soon as its pixels
+//             are saturated.
 // Backward: reverse traversal from the per-pixel checkpoint (T_final,
 // n_last) with warp-reduced atomics, then a per-Gaussian projection adjoint.
 #include "splat_dev.cuh"
@@ -133,14 +134,21 @@ emit_pairs_kernel(const int32_t *__restrict__ sorted_idx, const int32_t *__restr
 }
 
 template <int TS, int PPT>
-__global__ void __launch_bounds__(TS *TS / PPT)
+__global__ void __launch_bounds__(BWD_WARPS * 32)
 blend_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_gauss, const float4 *__restrict__ rec0,
-             const float4 *__restrict__ rec1, const float4 *__restrict__ rec2, int W, int H, int ntx,
+             const float4 *__restrict__ rec1, const float4 *__restrict__ rec2, int W, int H, int ntx, int ntiles,
              float *__restrict__ image, float *__restrict__ T_final, int32_t *__restrict__ n_last)
 {
-    const int tile = blockIdx.x;
-    blend_tile<TS, PPT>(ranges[tile], pair_gauss, rec0, rec1, rec2, W, H, tile % ntx, tile / ntx, image, T_final,
-                        n_last);
+    constexpr int NB = TS * TS / (32 * PPT);  // pixel boxes per tile
+    __shared__ float4 s0[BWD_WARPS][2][32];
+    __shared__ float4 s1[BWD_WARPS][2][32];
+    __shared__ float4 s2[BWD_WARPS][2][32];
+    const int warp = threadIdx.x >> 5;
+    const int item = blockIdx.x * BWD_WARPS + warp;
+    if (item >= ntiles * NB) return;  // warp-uniform; the kernel has no CTA barrier
+    const int tile = item / NB;
+    blend_box<TS, PPT>(ranges[tile], pair_gauss, rec0, rec1, rec2, W, H, tile % ntx, tile / ntx, item % NB, image,
+                       T_final, n_last, s0[warp], s1[warp], s2[warp]);
 }
 
 // BWD_WARPS independent warps per CTA, each one (tile, pixel box) item.
@@ -314,9 +322,11 @@ extern "C" int avatar_splat_bin(avatar_ctx *ctx, const avatar_splat_args *a, voi
 template <int TS, int PPT>
 void launch_blend(const avatar_splat_args *a, const SplatWs &w, int ntiles, int ntx, cudaStream_t st)
 {
-    blend_kernel<TS, PPT><<<ntiles, TS * TS / PPT, 0, st>>>((const int2 *)a->tile_range, a->pair_gauss, w.rec0,
-                                                            w.rec1, w.rec2, a->cam.width, a->cam.height, ntx,
-                                                            a->image, a->T_final, a->n_last);
+    constexpr int NB = TS * TS / (32 * PPT);
+    const int blocks = (int)(((long long)ntiles * NB + BWD_WARPS - 1) / BWD_WARPS);
+    blend_kernel<TS, PPT><<<blocks, BWD_WARPS * 32, 0, st>>>((const int2 *)a->tile_range, a->pair_gauss, w.rec0,
+                                                             w.rec1, w.rec2, a->cam.width, a->cam.height, ntx, ntiles,
+                                                             a->image, a->T_final, a->n_last);
 }
 
 template <int TS>

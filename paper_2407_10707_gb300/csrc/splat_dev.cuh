@@ -503,29 +503,145 @@ struct BoxMap {
     }
     __device__ int px(int lane) const { return x0 + (lane & 7); }
     __device__ int py(int lane, int k) const { return y0 + (lane >> 3) + 4 * k; }
-    // bit w set iff the packed rect (x0|y0<<16, x1|y1<<16) meets warp w's box
-    static __device__ unsigned mask(int tx, int ty, float lo, float hi)
-    {
-        constexpr int NB = TS * TS / (BW * BH);
-        int a = __float_as_int(lo), b = __float_as_int(hi);
-        int rx0 = (a & 0xffff) - tx * TS, ry0 = ((unsigned)a >> 16) - ty * TS;
-        int rx1 = (b & 0xffff) - tx * TS, ry1 = ((unsigned)b >> 16) - ty * TS;
-        // box columns [c0, c1] and rows [r0, r1] the rect overlaps (tile-local)
-        int c0 = max(rx0, 0) / BW, c1 = min(rx1, TS - 1) / BW;
-        int r0 = max(ry0, 0) / BH, r1 = min(ry1, TS - 1) / BH;
-        unsigned m = 0;
-#pragma unroll
-        for (int w = 0; w < NB; ++w) {
-            int c = w % BPR, r = w / BPR;
-            if (c >= c0 && c <= c1 && r >= r0 && r <= r1) m |= 1u << w;
-        }
-        return (rx1 < 0 || ry1 < 0 || rx0 >= TS || ry0 >= TS) ? 0u : m;
-    }
 };
 
-// Front-to-back blend of tile (tx, ty) of a W x H image over the sorted
-// pairs [rg.x, rg.y); writes the tile's pixels of image [3][H][W], T_final
-// and n_last.  Every thread of the CTA calls it (it synchronises the CTA).
+// Warps per CTA of the kernels built on blend_box and blend_backward_box.
+constexpr int BWD_WARPS = 4;
+
+// Front-to-back blend of pixel box wbox of tile (tx, ty) of a W x H image
+// over the tile's sorted pairs [rg.x, rg.y), by one warp on its own; writes
+// the box's pixels of image [3][H][W], T_final and n_last.  The list is
+// walked 32 entries at a time: each batch's records go to the warp's two
+// buffers (s0/s1/s2 [2][32]) by asynchronous copies while the previous batch
+// is walked, the lanes test the batch's rects against the box for a hit
+// mask (a Gaussian whose rect misses the box cannot reach alpha = 1/255 in
+// it), hits are evaluated two at a time (their exponents are independent of
+// T), and the warp leaves as soon as its own pixels are saturated.
+template <int TS, int PPT>
+__device__ __forceinline__ void blend_box(int2 rg, const int32_t *__restrict__ pair_gauss,
+                                          const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
+                                          const float4 *__restrict__ rec2, int W, int H, int tx, int ty, int wbox,
+                                          float *__restrict__ image, float *__restrict__ T_final,
+                                          int32_t *__restrict__ n_last, float4 (*s0)[32], float4 (*s1)[32],
+                                          float4 (*s2)[32])
+{
+    using Box = BoxMap<TS, PPT>;
+    const int lane = threadIdx.x & 31;
+    const Box box(tx, ty, wbox);
+    const int bx0 = box.x0, by0 = box.y0, bx1 = bx0 + Box::BW - 1, by1 = by0 + Box::BH - 1;
+    float fx[PPT], fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
+    int last[PPT];
+    bool live[PPT];
+    bool any_live = false;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int px = box.px(lane), py = box.py(lane, k);
+        fx[k] = px + 0.5f;
+        fy[k] = py + 0.5f;
+        T[k] = 1.f;
+        C0[k] = C1[k] = C2[k] = 0.f;
+        last[k] = 0;
+        live[k] = px < W && py < H;
+        any_live = any_live || live[k];
+    }
+    const int n = rg.y - rg.x;
+    // batch [base, base + 32) into buffer b; returns its hit mask
+    auto fetch = [&](int base, int b) -> unsigned {
+        const int idx = base + lane;
+        bool hit = false;
+        if (idx < n) {
+            const int g = pair_gauss[rg.x + idx];
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s0[b][lane])),
+                         "l"(rec0 + g)
+                         : "memory");
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s1[b][lane])),
+                         "l"(rec1 + g)
+                         : "memory");
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s2[b][lane])),
+                         "l"(rec2 + g)
+                         : "memory");
+            const float2 rr = __ldg(reinterpret_cast<const float2 *>(rec1 + g) + 1);
+            const int a = __float_as_int(rr.x), c = __float_as_int(rr.y);
+            hit = (c & 0xffff) >= bx0 && (a & 0xffff) <= bx1 && (int)((unsigned)c >> 16) >= by0 &&
+                  (int)((unsigned)a >> 16) <= by1;
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        return __ballot_sync(0xffffffffu, hit);
+    };
+    if (n > 0 && __any_sync(0xffffffffu, any_live)) {
+        unsigned hits = fetch(0, 0);
+        int b = 0;
+        for (int base = 0; base < n; base += 32, b ^= 1) {
+            const bool more = base + 32 < n;
+            const unsigned hits_next = more ? fetch(base + 32, b ^ 1) : 0u;
+            if (more)
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            else
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncwarp();
+            // one Gaussian's contribution to pixel k (the front-to-back step)
+            auto step = [&](int sj, int k, float l2a) {
+                if (l2a < LOG2_ALPHA_MIN) return;
+                float alpha = fminf(0.99f, exp2f(l2a));
+                float test_T = T[k] * (1.f - alpha);
+                if (test_T < T_MIN) {
+                    live[k] = false;
+                    return;
+                }
+                const float4 c = s2[b][sj];
+                float wgt = alpha * T[k];
+                C0[k] = fmaf(c.x, wgt, C0[k]);
+                C1[k] = fmaf(c.y, wgt, C1[k]);
+                C2[k] = fmaf(c.z, wgt, C2[k]);
+                T[k] = test_T;
+                last[k] = base + sj + 1;
+            };
+            auto l2alpha = [&](int sj, int k) {
+                const float4 r0 = s0[b][sj];
+                const float4 r1 = s1[b][sj];
+                float dx = fx[k] - r0.x, dy = fy[k] - r0.y;
+                return fmaf(fmaf(r0.z, dx, r0.w * dy), dx, fmaf(r1.x * dy, dy, r1.y));
+            };
+            // two Gaussians per iteration: both exponents are independent of T
+            while (hits) {
+                const int j0 = __ffs(hits) - 1;
+                hits &= hits - 1;
+                const bool two = hits != 0;
+                const int j1 = two ? __ffs(hits) - 1 : j0;
+                if (two) hits &= hits - 1;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    if (!live[k]) continue;
+                    const float a0 = l2alpha(j0, k);
+                    const float a1 = two ? l2alpha(j1, k) : -1e30f;
+                    step(j0, k, a0);
+                    if (live[k]) step(j1, k, a1);
+                }
+                any_live = false;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) any_live = any_live || live[k];
+                if (!__any_sync(0xffffffffu, any_live)) break;
+            }
+            __syncwarp();  // every lane is done with buffer b before it is refilled
+            if (!__any_sync(0xffffffffu, any_live)) break;
+            hits = hits_next;
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy outlives the walk
+    }
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int px = box.px(lane), py = box.py(lane, k);
+        if (px < W && py < H) {
+            const int pix = py * W + px;
+            image[pix] = C0[k];
+            image[W * H + pix] = C1[k];
+            image[2 * W * H + pix] = C2[k];
+            T_final[pix] = T[k];
+            n_last[pix] = last[k];
+        }
+    }
+}
+
 // Pair emission by one warp for 32 consecutive Gaussians of the depth order
 // (lane j: n pairs starting at output offset off; an offset scan in that
 // order makes the warp's pairs one contiguous range).  The warp writes the
@@ -573,169 +689,7 @@ __device__ __forceinline__ void emit_pairs_warp(int n, long off, int gval, int t
     }
 }
 
-template <int TS, int PPT>
-__device__ __forceinline__ void blend_tile(int2 rg, const int32_t *__restrict__ pair_gauss,
-                                           const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
-                                           const float4 *__restrict__ rec2, int W, int H, int tx, int ty,
-                                           float *__restrict__ image, float *__restrict__ T_final,
-                                           int32_t *__restrict__ n_last)
-{
-    constexpr int NTH = TS * TS / PPT;
-    // Two record buffers where they fit in 48 KB of static shared memory: the
-    // next batch's records are fetched into registers before the current batch
-    // is walked and stored into the other buffer after it, so one barrier per
-    // batch remains and the fetch latency overlaps the walk.
-    constexpr int NBUF = NTH <= 256 ? 2 : 1;
-    __shared__ float4 s0[NBUF][NTH];
-    __shared__ float4 s1[NBUF][NTH];
-    __shared__ float4 s2[NBUF][NTH];
-    __shared__ unsigned smask[NBUF][NTH];
-    const int tid = threadIdx.x;
-    const unsigned wbit = 1u << (tid >> 5);
-    const BoxMap<TS, PPT> box(tx, ty, tid >> 5);
-    float fx[PPT], fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
-    int last[PPT];
-    bool live[PPT];
-    bool done = true;
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const int px = box.px(tid & 31), py = box.py(tid & 31, k);
-        fx[k] = px + 0.5f;
-        fy[k] = py + 0.5f;
-        T[k] = 1.f;
-        C0[k] = C1[k] = C2[k] = 0.f;
-        last[k] = 0;
-        live[k] = px < W && py < H;
-        done = done && !live[k];
-    }
-    const int n = rg.y - rg.x;
-    // walk the m records of buffer b, which start at list position base
-    auto walk = [&](int b, int base, int m) {
-        // one Gaussian's contribution to pixel k (the front-to-back step)
-        auto step = [&](int j, int k, float l2a) {
-            if (l2a < LOG2_ALPHA_MIN) return;
-            float alpha = fminf(0.99f, exp2f(l2a));
-            float test_T = T[k] * (1.f - alpha);
-            if (test_T < T_MIN) {
-                live[k] = false;
-                return;
-            }
-            float4 c = s2[b][j];
-            float wgt = alpha * T[k];
-            C0[k] = fmaf(c.x, wgt, C0[k]);
-            C1[k] = fmaf(c.y, wgt, C1[k]);
-            C2[k] = fmaf(c.z, wgt, C2[k]);
-            T[k] = test_T;
-            last[k] = base + j + 1;
-        };
-        auto l2alpha = [&](int j, int k) {
-            const float4 r0 = s0[b][j];
-            const float4 r1 = s1[b][j];
-            float dx = fx[k] - r0.x, dy = fy[k] - r0.y;
-            return fmaf(fmaf(r0.z, dx, r0.w * dy), dx, fmaf(r1.x * dy, dy, r1.y));
-        };
-        int j = 0;
-        // two Gaussians per iteration: both exponents are independent of T
-        for (; j + 1 < m; j += 2) {
-            const bool m0 = smask[b][j] & wbit, m1 = smask[b][j + 1] & wbit;  // warp-uniform
-            if (!(m0 || m1)) continue;
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                if (!live[k]) continue;
-                float a0 = m0 ? l2alpha(j, k) : -1e30f;
-                float a1 = m1 ? l2alpha(j + 1, k) : -1e30f;
-                step(j, k, a0);
-                if (live[k]) step(j + 1, k, a1);
-            }
-            bool any = false;
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) any = any || live[k];
-            if (!any) break;
-        }
-        if (j < m && (smask[b][j] & wbit)) {
-#pragma unroll
-            for (int k = 0; k < PPT; ++k)
-                if (live[k]) step(j, k, l2alpha(j, k));
-        }
-        bool any = false;
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) any = any || live[k];
-        if (!any) done = true;
-    };
-    if constexpr (NBUF == 2) {
-        // the records go to shared memory by asynchronous copies; only the
-        // rect (for the warp mask) passes through registers
-        float2 prect = make_float2(0.f, 0.f);
-        bool have = false;
-        auto fetch = [&](int base, int b) {
-            const int idx = base + tid;
-            have = idx < n;
-            if (have) {
-                const int g = pair_gauss[rg.x + idx];
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s0[b][tid])),
-                             "l"(rec0 + g)
-                             : "memory");
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s1[b][tid])),
-                             "l"(rec1 + g)
-                             : "memory");
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s2[b][tid])),
-                             "l"(rec2 + g)
-                             : "memory");
-                prect = __ldg(reinterpret_cast<const float2 *>(rec1 + g) + 1);
-            }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-        };
-        auto stash = [&](int b) {
-            if (have) smask[b][tid] = BoxMap<TS, PPT>::mask(tx, ty, prect.x, prect.y);
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-        };
-        if (n > 0) {
-            fetch(0, 0);
-            stash(0);
-        }
-        int b = 0;
-        for (int base = 0; base < n; base += NTH, b ^= 1) {
-            // batch b is in place, and every warp is done with buffer b ^ 1
-            if (__syncthreads_count(done) == NTH) break;
-            const bool more = base + NTH < n;
-            if (more) fetch(base + NTH, b ^ 1);
-            if (!done) walk(b, base, min(NTH, n - base));
-            if (more) stash(b ^ 1);
-        }
-    } else {
-        for (int base = 0; base < n; base += NTH) {
-            if (__syncthreads_count(done) == NTH) break;
-            int idx = base + tid;
-            if (idx < n) {
-                int g = pair_gauss[rg.x + idx];
-                s0[0][tid] = rec0[g];
-                float4 r1 = rec1[g];
-                s1[0][tid] = r1;
-                s2[0][tid] = rec2[g];
-                smask[0][tid] = BoxMap<TS, PPT>::mask(tx, ty, r1.z, r1.w);
-            }
-            __syncthreads();
-            if (!done) walk(0, base, min(NTH, n - base));
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const int px = box.px(tid & 31), py = box.py(tid & 31, k);
-        if (px < W && py < H) {
-            const int pix = py * W + px;
-            image[pix] = C0[k];
-            image[W * H + pix] = C1[k];
-            image[2 * W * H + pix] = C2[k];
-            T_final[pix] = T[k];
-            n_last[pix] = last[k];
-        }
-    }
-}
-
-// Warps per CTA of the kernels built on blend_backward_box.
-constexpr int BWD_WARPS = 4;
-
-// Adjoint of blend_tile for pixel box wbox of tile (tx, ty), by one warp on
+// Adjoint of blend_box for pixel box wbox of tile (tx, ty), by one warp on
 // its own: reverse traversal of the tile's list from the per-pixel
 // checkpoint (T_final, n_last), starting at the box's largest n_last, 32
 // entries at a time.  Each batch's records go to the warp's two buffers
