@@ -545,12 +545,10 @@ __device__ __forceinline__ void blend_box(int2 rg, const int32_t *__restrict__ p
         any_live = any_live || live[k];
     }
     const int n = rg.y - rg.x;
-    // batch [base, base + 32) into buffer b; returns its hit mask
-    auto fetch = [&](int base, int b) -> unsigned {
-        const int idx = base + lane;
-        bool hit = false;
-        if (idx < n) {
-            const int g = pair_gauss[rg.x + idx];
+    // the records of list entries [base, base + 32) into buffer b, Gaussian
+    // g for this lane's entry
+    auto issue = [&](int base, int b, int g) {
+        if (base + lane < n) {
             asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s0[b][lane])),
                          "l"(rec0 + g)
                          : "memory");
@@ -560,25 +558,34 @@ __device__ __forceinline__ void blend_box(int2 rg, const int32_t *__restrict__ p
             asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s2[b][lane])),
                          "l"(rec2 + g)
                          : "memory");
-            const float2 rr = __ldg(reinterpret_cast<const float2 *>(rec1 + g) + 1);
-            const int a = __float_as_int(rr.x), c = __float_as_int(rr.y);
-            hit = (c & 0xffff) >= bx0 && (a & 0xffff) <= bx1 && (int)((unsigned)c >> 16) >= by0 &&
-                  (int)((unsigned)a >> 16) <= by1;
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
-        return __ballot_sync(0xffffffffu, hit);
     };
+    auto gauss = [&](int idx) { return idx < n ? pair_gauss[rg.x + idx] : 0; };
     if (n > 0 && __any_sync(0xffffffffu, any_live)) {
-        unsigned hits = fetch(0, 0);
+        // indices run two batches ahead of the walk and records one, so
+        // neither load's latency is waited for in the loop
+        int g_next = gauss(32 + lane);
+        issue(0, 0, gauss(lane));
         int b = 0;
         for (int base = 0; base < n; base += 32, b ^= 1) {
             const bool more = base + 32 < n;
-            const unsigned hits_next = more ? fetch(base + 32, b ^ 1) : 0u;
+            if (more) issue(base + 32, b ^ 1, g_next);
+            g_next = gauss(base + 64 + lane);
             if (more)
                 asm volatile("cp.async.wait_group 1;" ::: "memory");
             else
                 asm volatile("cp.async.wait_group 0;" ::: "memory");
-            __syncwarp();
+            __syncwarp();  // every lane's copies of batch b are visible to the warp
+            // the batch's hit mask from the rects now in shared memory
+            bool hit = false;
+            if (base + lane < n) {
+                const float4 r1 = s1[b][lane];
+                const int ra = __float_as_int(r1.z), rc = __float_as_int(r1.w);
+                hit = (rc & 0xffff) >= bx0 && (ra & 0xffff) <= bx1 && (int)((unsigned)rc >> 16) >= by0 &&
+                      (int)((unsigned)ra >> 16) <= by1;
+            }
+            unsigned hits = __ballot_sync(0xffffffffu, hit);
             // one Gaussian's contribution to pixel k (the front-to-back step)
             auto step = [&](int sj, int k, float l2a) {
                 if (l2a < LOG2_ALPHA_MIN) return;
@@ -624,7 +631,6 @@ __device__ __forceinline__ void blend_box(int2 rg, const int32_t *__restrict__ p
             }
             __syncwarp();  // every lane is done with buffer b before it is refilled
             if (!__any_sync(0xffffffffu, any_live)) break;
-            hits = hits_next;
         }
         asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy outlives the walk
     }
@@ -735,13 +741,10 @@ __device__ __forceinline__ void blend_backward_box(int2 rg, const int32_t *__res
         mx_last = max(mx_last, my_last[k]);
     }
     const int n = (int)__reduce_max_sync(0xffffffffu, (unsigned)mx_last);
-    // batch [end - 32, end) into buffer b; returns the mask of its entries
-    // whose rect meets the box
-    auto fetch = [&](int end, int b) -> unsigned {
-        const int idx = end - 32 + lane;
-        bool hit = false;
-        if (idx >= 0) {
-            const int g = pair_gauss[rg.x + idx];
+    // the records of list entries [end - 32, end) into buffer b, Gaussian g
+    // for this lane's entry
+    auto issue = [&](int end, int b, int g) {
+        if (end - 32 + lane >= 0) {
             sg[b][lane] = g;
             asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s0[b][lane])),
                          "l"(rec0 + g)
@@ -752,25 +755,33 @@ __device__ __forceinline__ void blend_backward_box(int2 rg, const int32_t *__res
             asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(&s2[b][lane])),
                          "l"(rec2 + g)
                          : "memory");
-            const float2 rr = __ldg(reinterpret_cast<const float2 *>(rec1 + g) + 1);
-            const int a = __float_as_int(rr.x), c = __float_as_int(rr.y);
-            hit = (c & 0xffff) >= bx0 && (a & 0xffff) <= bx1 && (int)((unsigned)c >> 16) >= by0 &&
-                  (int)((unsigned)a >> 16) <= by1;
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
-        return __ballot_sync(0xffffffffu, hit);
     };
+    auto gauss = [&](int idx) { return idx >= 0 ? pair_gauss[rg.x + idx] : 0; };
     if (n == 0) return;
-    unsigned hits = fetch(n, 0);
+    // indices run two batches ahead of the walk and records one
+    int g_next = gauss(n - 64 + lane);
+    issue(n, 0, gauss(n - 32 + lane));
     int b = 0;
     for (int end = n; end > 0; end -= 32, b ^= 1) {
         const bool more = end > 32;
-        const unsigned hits_next = more ? fetch(end - 32, b ^ 1) : 0u;
+        if (more) issue(end - 32, b ^ 1, g_next);
+        g_next = gauss(end - 96 + lane);
         if (more)
             asm volatile("cp.async.wait_group 1;" ::: "memory");
         else
             asm volatile("cp.async.wait_group 0;" ::: "memory");
-        __syncwarp();
+        __syncwarp();  // every lane's copies of batch b are visible to the warp
+        // the batch's hit mask from the rects now in shared memory
+        bool hit = false;
+        if (end - 32 + lane >= 0) {
+            const float4 q1 = s1[b][lane];
+            const int ra = __float_as_int(q1.z), rc = __float_as_int(q1.w);
+            hit = (rc & 0xffff) >= bx0 && (ra & 0xffff) <= bx1 && (int)((unsigned)rc >> 16) >= by0 &&
+                  (int)((unsigned)ra >> 16) <= by1;
+        }
+        unsigned hits = __ballot_sync(0xffffffffu, hit);
         while (hits) {
             const int sj = 31 - __clz(hits);
             hits &= ~(1u << sj);
@@ -826,7 +837,6 @@ __device__ __forceinline__ void blend_backward_box(int2 rg, const int32_t *__res
             }
         }
         __syncwarp();  // every lane is done with buffer b before it is refilled
-        hits = hits_next;
     }
 }
 
