@@ -107,7 +107,8 @@ __device__ __forceinline__ int floor_div_small(long long num, int den)
 constexpr unsigned OUTSIDE = 0xffffffffu;
 constexpr int VIS_CHUNK = 1024;                 // triangles per CTA per chunk
 constexpr int VIS_TPT = VIS_CHUNK / VIS_THREADS; // triangles per thread per chunk
-constexpr int VIS_VCAP = 2048;                   // cached projected vertices per chunk
+constexpr int VIS_VCAP = 1024;                   // cached projected vertices per chunk (10-bit offsets)
+static_assert(VIS_VCAP == 1024, "packed face offsets are 10 bits");
 constexpr int VIS_SLAB_BYTES = 32 * 1024;        // depth-map share of one CTA (R <= 256)
 
 __device__ __forceinline__ uint2 pack_proj(const Proj &q)
@@ -251,8 +252,10 @@ __device__ __forceinline__ bool triangle_appears(uint2 pa, uint2 pb, uint2 pc, c
 
 // Direction-independent per-chunk vertex range [min, max] of the indices a
 // chunk of VIS_CHUNK triangles references (x > y: a bad index, or no faces).
+// With pf, the chunk's faces as offsets from the range's first vertex, 10
+// bits each (a | b << 10 | c << 20), where the range fits the vertex cache.
 __global__ void vis_chunk_ranges_kernel(const int32_t *__restrict__ faces, int F, int Nv, int2 *__restrict__ vr,
-                                        int32_t *status)
+                                        int32_t *__restrict__ pf, int32_t *status)
 {
     const int c = blockIdx.x;
     int vmin = 0x7fffffff, vmax = -1;
@@ -284,13 +287,17 @@ __global__ void vis_chunk_ranges_kernel(const int32_t *__restrict__ faces, int F
             vr[c] = make_int2(smin, smax);
         }
     }
+    if (pf && !sbad && smax >= smin && smax - smin < VIS_VCAP)
+        for (int f = c * VIS_CHUNK + threadIdx.x; f < min(F, (c + 1) * VIS_CHUNK); f += blockDim.x)
+            pf[f] = (__ldg(faces + 3 * f) - smin) | ((__ldg(faces + 3 * f + 1) - smin) << 10) |
+                    ((__ldg(faces + 3 * f + 2) - smin) << 20);
 }
 
 template <int CL, bool CULL_BACK, bool BATCH>
 __global__ void __launch_bounds__(VIS_THREADS)
 vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *__restrict__ faces,
-                       const int2 *__restrict__ vranges, const float *__restrict__ frames,
-                       uint32_t *__restrict__ dirbits, int32_t *status)
+                       const int32_t *__restrict__ pfaces, const int2 *__restrict__ vranges,
+                       const float *__restrict__ frames, uint32_t *__restrict__ dirbits, int32_t *status)
 {
     extern __shared__ int slab[];
     cg::cluster_group cluster = cg::this_cluster();
@@ -321,20 +328,14 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
         for (int i = 0; i < 9; ++i) B[i] = 0;
     }
 
-    // faces of this CTA's first chunk (the next chunk's are prefetched while
-    // the current one is rasterised)
-    int cur[VIS_TPT][3];
-    auto load_faces = [&](int chunk, int (&dst)[VIS_TPT][3]) {
+    // packed faces of this CTA's first chunk (the next chunk's are prefetched
+    // while the current one is rasterised); -1 past the last face
+    int cur[VIS_TPT];
+    auto load_faces = [&](int chunk, int (&dst)[VIS_TPT]) {
 #pragma unroll
         for (int t = 0; t < VIS_TPT; ++t) {
-            int f = chunk * VIS_CHUNK + t * VIS_THREADS + threadIdx.x;
-            if (f < p.F) {
-                dst[t][0] = __ldg(faces + 3 * f);
-                dst[t][1] = __ldg(faces + 3 * f + 1);
-                dst[t][2] = __ldg(faces + 3 * f + 2);
-            } else {
-                dst[t][0] = -1;
-            }
+            const int f = chunk * VIS_CHUNK + t * VIS_THREADS + threadIdx.x;
+            dst[t] = f < p.F ? __ldg(pfaces + f) : -1;
         }
     };
     const int nchunks = (p.F + VIS_CHUNK - 1) / VIS_CHUNK;
@@ -345,39 +346,38 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
     for (; chunk < nchunks; chunk += CL) {
         const int2 vr = __ldg(vranges + chunk);
         const int v0 = vr.x, nv = vr.y - vr.x + 1;
+        // nv <= 0: a bad index (reported) or no faces; the packed offsets
+        // exist only where the range fits the cache
         const bool cached = nv > 0 && nv <= VIS_VCAP;
         if (cached) {
 #pragma unroll 4
             for (int i = threadIdx.x; i < nv; i += VIS_THREADS)
                 vcache[i] = pack_proj(project_vertex(__ldg(qv + v0 + i), B, p));
         }
-        int nxt[VIS_TPT][3];
+        int nxt[VIS_TPT];
         if (chunk + CL < nchunks) load_faces(chunk + CL, nxt);
         __syncthreads();
         if (nv > 0) {
 #pragma unroll
             for (int t = 0; t < VIS_TPT; ++t) {
-                if (cur[t][0] < 0) continue;
+                const int f = chunk * VIS_CHUNK + t * VIS_THREADS + threadIdx.x;
+                if (f >= p.F) continue;
                 uint2 pa, pb, pc;
                 if (cached) {
-                    pa = vcache[cur[t][0] - v0];
-                    pb = vcache[cur[t][1] - v0];
-                    pc = vcache[cur[t][2] - v0];
+                    pa = vcache[cur[t] & 1023];
+                    pb = vcache[(cur[t] >> 10) & 1023];
+                    pc = vcache[(cur[t] >> 20) & 1023];
                 } else {
-                    pa = pack_proj(project_vertex(__ldg(qv + cur[t][0]), B, p));
-                    pb = pack_proj(project_vertex(__ldg(qv + cur[t][1]), B, p));
-                    pc = pack_proj(project_vertex(__ldg(qv + cur[t][2]), B, p));
+                    pa = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f)), B, p));
+                    pb = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f + 1)), B, p));
+                    pc = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f + 2)), B, p));
                 }
                 raster_triangle<CL, CULL_BACK>(pa, pb, pc, slab, p, cluster);
             }
         }
         __syncthreads();  // the next chunk overwrites the cache
 #pragma unroll
-        for (int t = 0; t < VIS_TPT; ++t) {
-            cur[t][0] = nxt[t][0];
-            cur[t][1] = nxt[t][1];
-            cur[t][2] = nxt[t][2];
-        }
+        for (int t = 0; t < VIS_TPT; ++t) cur[t] = nxt[t];
     }
     cluster.sync();
 
@@ -676,8 +676,9 @@ int launch_tri(const VisParams &p, const int4 *qv, const int32_t *faces, const i
 }
 
 template <int CL, bool CULL_BACK>
-int launch_raster(const VisParams &p, const int4 *qv, const int32_t *faces, const int2 *vranges,
-                  const float *frames, uint32_t *dirbits, int32_t *status, size_t smem, cudaStream_t st)
+int launch_raster(const VisParams &p, const int4 *qv, const int32_t *faces, const int32_t *pfaces,
+                  const int2 *vranges, const float *frames, uint32_t *dirbits, int32_t *status, size_t smem,
+                  cudaStream_t st)
 {
     auto kern = p.B > 1 ? vis_raster_test_kernel<CL, CULL_BACK, true> : vis_raster_test_kernel<CL, CULL_BACK, false>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -694,7 +695,7 @@ int launch_raster(const VisParams &p, const int4 *qv, const int32_t *faces, cons
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, kern, p, qv, faces, vranges, frames, dirbits, status) != cudaSuccess) {
+    if (cudaLaunchKernelEx(&cfg, kern, p, qv, faces, pfaces, vranges, frames, dirbits, status) != cudaSuccess) {
         (void)cudaGetLastError();
         return AVATAR_ERR_CUDA;
     }
@@ -724,6 +725,7 @@ struct VisWs {
     int4 *qv;
     uint32_t *dirbits;
     int2 *vranges;
+    int32_t *pfaces;  // [F] packed chunk-relative faces
 };
 
 size_t vis_ws_layout(const avatar_vis_args *a, int B, void *base, size_t cap, VisWs *out)
@@ -734,6 +736,7 @@ size_t vis_ws_layout(const avatar_vis_args *a, int B, void *base, size_t cap, Vi
     w.qv = c.take<int4>((size_t)B * a->Nv);
     w.dirbits = c.take<uint32_t>((size_t)B * a->D * NW);
     w.vranges = c.take<int2>((size_t)(a->F + VIS_CHUNK - 1) / VIS_CHUNK + 1);
+    w.pfaces = c.take<int32_t>((size_t)a->F + 1);
     if (out) *out = w;
     return c.off;
 }
@@ -796,14 +799,16 @@ int vis_run(avatar_ctx *ctx, const avatar_vis_args *a, int B, void *ws, size_t w
 
     int nchunks = (a->F + VIS_CHUNK - 1) / VIS_CHUNK;
     if (nchunks > 0) {
-        vis_chunk_ranges_kernel<<<nchunks, 256, 0, st>>>(a->faces, a->F, a->Nv, w.vranges, a->status);
+        vis_chunk_ranges_kernel<<<nchunks, 256, 0, st>>>(a->faces, a->F, a->Nv, w.vranges, w.pfaces, a->status);
         AV_CHECK_LAUNCH();
     }
     int rc;
     const bool cb = a->cull_back != 0;
 #define AV_RASTER(CLV)                                                                                          \
-    (cb ? launch_raster<CLV, true>(p, w.qv, a->faces, w.vranges, a->frames, w.dirbits, a->status, smem, st)     \
-        : launch_raster<CLV, false>(p, w.qv, a->faces, w.vranges, a->frames, w.dirbits, a->status, smem, st))
+    (cb ? launch_raster<CLV, true>(p, w.qv, a->faces, w.pfaces, w.vranges, a->frames, w.dirbits, a->status, smem,   \
+                                   st)                                                                              \
+        : launch_raster<CLV, false>(p, w.qv, a->faces, w.pfaces, w.vranges, a->frames, w.dirbits, a->status, smem, \
+                                    st))
     switch (CL) {
         case 1: rc = AV_RASTER(1); break;
         case 2: rc = AV_RASTER(2); break;
@@ -952,7 +957,7 @@ extern "C" int avatar_visibility_soft(avatar_ctx *ctx, const avatar_vis_soft_arg
     AV_CHECK_LAUNCH();
     const int nchunks = (b.F + VIS_CHUNK - 1) / VIS_CHUNK;
     if (nchunks > 0) {
-        vis_chunk_ranges_kernel<<<nchunks, 256, 0, st>>>(b.faces, b.F, b.Nv, w.vranges, b.status);
+        vis_chunk_ranges_kernel<<<nchunks, 256, 0, st>>>(b.faces, b.F, b.Nv, w.vranges, nullptr, b.status);
         AV_CHECK_LAUNCH();
     }
     int rc;
