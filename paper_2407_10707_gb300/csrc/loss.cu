@@ -3,7 +3,9 @@
 // with SSIM under an 11 x 11 Gaussian window (sigma 1.5, zero padding),
 // C1 = 0.01^2, C2 = 0.03^2, per channel and pixel.
 //
-// Two fused tile kernels (32 x 32 pixels, separable blurs in shared memory):
+// Two fused tile kernels (32 x 32 pixels, separable blurs in shared memory;
+// each thread slides an 11-tap register window along 8 outputs of a row or
+// 4 of a column, so a tap costs an FMA and no shared-memory load):
 //   forward   blurs x, y, x^2, y^2, x y; per pixel the SSIM, |x - y| and the
 //             coefficients of dSSIM with respect to the blurred x, x^2, x y
 //             (A, B, C below); per-block partial sums
@@ -18,6 +20,8 @@ constexpr int TS = 32;            // output tile edge
 constexpr int R = 5;              // window radius
 constexpr int WT = TS + 2 * R;    // tile with halo
 constexpr int LOSS_THREADS = 256;
+constexpr int RBH = 8;            // outputs per thread of a horizontal blur (register window)
+constexpr int RBV = 4;            // outputs per thread of a vertical blur
 constexpr float C1 = 0.01f * 0.01f;
 constexpr float C2 = 0.03f * 0.03f;
 
@@ -62,53 +66,79 @@ ssim_forward_kernel(const float *__restrict__ img, const float *__restrict__ tgt
         sy[r][q] = load_or0(Y, d.H, d.W, y0 - R + r, x0 - R + q);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < WT * TS; i += LOSS_THREADS) {
-        const int r = i / TS, q = i % TS;
-        float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+    float wt[2 * R + 1];
 #pragma unroll
-        for (int k = 0; k <= 2 * R; ++k) {
-            const float w = c_w[k], u = sx[r][q + k], v = sy[r][q + k];
-            a = fmaf(w, u, a);
-            b = fmaf(w, v, b);
-            aa = fmaf(w, u * u, aa);
-            bb = fmaf(w, v * v, bb);
-            ab = fmaf(w, u * v, ab);
+    for (int k = 0; k <= 2 * R; ++k) wt[k] = c_w[k];
+    // horizontal blurs: a thread slides the window along RBH outputs of a row
+    for (int i = threadIdx.x; i < WT * (TS / RBH); i += LOSS_THREADS) {
+        const int r = i / (TS / RBH), q0 = (i % (TS / RBH)) * RBH;
+        float u[RBH + 2 * R], v[RBH + 2 * R];
+#pragma unroll
+        for (int k = 0; k < RBH + 2 * R; ++k) {
+            u[k] = sx[r][q0 + k];
+            v[k] = sy[r][q0 + k];
         }
-        h[0][r][q] = a;
-        h[1][r][q] = b;
-        h[2][r][q] = aa;
-        h[3][r][q] = bb;
-        h[4][r][q] = ab;
+#pragma unroll
+        for (int o = 0; o < RBH; ++o) {
+            float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+#pragma unroll
+            for (int k = 0; k <= 2 * R; ++k) {
+                const float uu = u[o + k], vv = v[o + k];
+                a = fmaf(wt[k], uu, a);
+                b = fmaf(wt[k], vv, b);
+                aa = fmaf(wt[k], uu * uu, aa);
+                bb = fmaf(wt[k], vv * vv, bb);
+                ab = fmaf(wt[k], uu * vv, ab);
+            }
+            h[0][r][q0 + o] = a;
+            h[1][r][q0 + o] = b;
+            h[2][r][q0 + o] = aa;
+            h[3][r][q0 + o] = bb;
+            h[4][r][q0 + o] = ab;
+        }
     }
     __syncthreads();
     double s_ssim = 0.0, s_l1 = 0.0;
-    for (int i = threadIdx.x; i < TS * TS; i += LOSS_THREADS) {
-        const int r = i / TS, q = i % TS;
-        const int y = y0 + r, x = x0 + q;
-        if (y >= d.H || x >= d.W) continue;
-        float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    // vertical blurs: a thread slides the window down RBV outputs of a column
+    // (one map at a time, so the window stays in registers)
+    for (int i = threadIdx.x; i < (TS / RBV) * TS; i += LOSS_THREADS) {
+        const int r0 = (i / TS) * RBV, q = i % TS;
+        float m[5][RBV];
 #pragma unroll
-        for (int k = 0; k <= 2 * R; ++k) {
-            const float w = c_w[k];
+        for (int e = 0; e < 5; ++e) {
+            float col[RBV + 2 * R];
 #pragma unroll
-            for (int e = 0; e < 5; ++e) m[e] = fmaf(w, h[e][r + k][q], m[e]);
+            for (int k = 0; k < RBV + 2 * R; ++k) col[k] = h[e][r0 + k][q];
+#pragma unroll
+            for (int o = 0; o < RBV; ++o) {
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k <= 2 * R; ++k) acc = fmaf(wt[k], col[o + k], acc);
+                m[e][o] = acc;
+            }
         }
-        const float mx = m[0], my = m[1];
-        const float sxx = m[2] - mx * mx, syy = m[3] - my * my, sxy = m[4] - mx * my;
-        const float A1 = 2.f * mx * my + C1, A2 = 2.f * sxy + C2;
-        const float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
-        const float inv = 1.f / (B1 * B2);
-        const float S = A1 * A2 * inv;
-        // derivatives with respect to mu_x, E[x^2], E[x y] (through s_xx, s_xy)
-        const float dS_dsxx = -S / B2;
-        const float dS_dsxy = 2.f * A1 * inv;
-        const float dS_dmx = 2.f * my * A2 * inv - S * 2.f * mx / B1;
-        const size_t o = c * plane + (size_t)y * d.W + x;
-        coefA[o] = dS_dmx - 2.f * mx * dS_dsxx - my * dS_dsxy;
-        coefB[o] = dS_dsxx;
-        coefC[o] = dS_dsxy;
-        s_ssim += S;
-        s_l1 += fabsf(sx[r + R][q + R] - sy[r + R][q + R]);
+#pragma unroll
+        for (int t = 0; t < RBV; ++t) {
+            const int r = r0 + t;
+            const int y = y0 + r, x = x0 + q;
+            if (y >= d.H || x >= d.W) continue;
+            const float mx = m[0][t], my = m[1][t];
+            const float sxx = m[2][t] - mx * mx, syy = m[3][t] - my * my, sxy = m[4][t] - mx * my;
+            const float A1 = 2.f * mx * my + C1, A2 = 2.f * sxy + C2;
+            const float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
+            const float inv = 1.f / (B1 * B2);
+            const float S = A1 * A2 * inv;
+            // derivatives with respect to mu_x, E[x^2], E[x y] (through s_xx, s_xy)
+            const float dS_dsxx = -S / B2;
+            const float dS_dsxy = 2.f * A1 * inv;
+            const float dS_dmx = 2.f * my * A2 * inv - S * 2.f * mx / B1;
+            const size_t o = c * plane + (size_t)y * d.W + x;
+            coefA[o] = dS_dmx - 2.f * mx * dS_dsxx - my * dS_dsxy;
+            coefB[o] = dS_dsxx;
+            coefC[o] = dS_dsxy;
+            s_ssim += S;
+            s_l1 += fabsf(sx[r + R][q + R] - sy[r + R][q + R]);
+        }
     }
     // block sums in FP64
 #pragma unroll
@@ -152,38 +182,58 @@ ssim_backward_kernel(const float *__restrict__ img, const float *__restrict__ tg
         for (int e = 0; e < 3; ++e) sa[e][r][q] = load_or0(P[e], d.H, d.W, y0 - R + r, x0 - R + q);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < WT * TS; i += LOSS_THREADS) {
-        const int r = i / TS, q = i % TS;
-        float acc[3] = {0.f, 0.f, 0.f};
+    float wt[2 * R + 1];
 #pragma unroll
-        for (int k = 0; k <= 2 * R; ++k) {
-            const float w = c_w[k];
+    for (int k = 0; k <= 2 * R; ++k) wt[k] = c_w[k];
+    // horizontal blurs of A, B, C: a register window along RBH outputs of a row
+    for (int i = threadIdx.x; i < WT * (TS / RBH); i += LOSS_THREADS) {
+        const int r = i / (TS / RBH), q0 = (i % (TS / RBH)) * RBH;
 #pragma unroll
-            for (int e = 0; e < 3; ++e) acc[e] = fmaf(w, sa[e][r][q + k], acc[e]);
+        for (int e = 0; e < 3; ++e) {
+            float u[RBH + 2 * R];
+#pragma unroll
+            for (int k = 0; k < RBH + 2 * R; ++k) u[k] = sa[e][r][q0 + k];
+#pragma unroll
+            for (int o = 0; o < RBH; ++o) {
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k <= 2 * R; ++k) acc = fmaf(wt[k], u[o + k], acc);
+                h[e][r][q0 + o] = acc;
+            }
         }
-#pragma unroll
-        for (int e = 0; e < 3; ++e) h[e][r][q] = acc[e];
     }
     __syncthreads();
     const float n = (float)((double)d.C * d.H * d.W);
     const float k_l1 = weight * (1.f - lambda) / n, k_ss = -weight * lambda / n;
-    for (int i = threadIdx.x; i < TS * TS; i += LOSS_THREADS) {
-        const int r = i / TS, q = i % TS;
-        const int y = y0 + r, x = x0 + q;
-        if (y >= d.H || x >= d.W) continue;
-        float acc[3] = {0.f, 0.f, 0.f};
+    // vertical blurs and the per-pixel combination: a register window down
+    // RBV outputs of a column
+    for (int i = threadIdx.x; i < (TS / RBV) * TS; i += LOSS_THREADS) {
+        const int r0 = (i / TS) * RBV, q = i % TS;
+        float acc[3][RBV];
 #pragma unroll
-        for (int k = 0; k <= 2 * R; ++k) {
-            const float w = c_w[k];
+        for (int e = 0; e < 3; ++e) {
+            float col[RBV + 2 * R];
 #pragma unroll
-            for (int e = 0; e < 3; ++e) acc[e] = fmaf(w, h[e][r + k][q], acc[e]);
+            for (int k = 0; k < RBV + 2 * R; ++k) col[k] = h[e][r0 + k][q];
+#pragma unroll
+            for (int t = 0; t < RBV; ++t) {
+                float a = 0.f;
+#pragma unroll
+                for (int k = 0; k <= 2 * R; ++k) a = fmaf(wt[k], col[t + k], a);
+                acc[e][t] = a;
+            }
         }
-        const size_t o = c * plane + (size_t)y * d.W + x;
-        const float xv = __ldg(img + o), yv = __ldg(tgt + o);
-        const float diff = xv - yv;
-        const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-        const float dssim = acc[0] + 2.f * xv * acc[1] + yv * acc[2];
-        d_img[o] = k_l1 * sgn + k_ss * dssim;
+#pragma unroll
+        for (int t = 0; t < RBV; ++t) {
+            const int y = y0 + r0 + t, x = x0 + q;
+            if (y >= d.H || x >= d.W) continue;
+            const size_t o = c * plane + (size_t)y * d.W + x;
+            const float xv = __ldg(img + o), yv = __ldg(tgt + o);
+            const float diff = xv - yv;
+            const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+            const float dssim = acc[0][t] + 2.f * xv * acc[1][t] + yv * acc[2][t];
+            d_img[o] = k_l1 * sgn + k_ss * dssim;
+        }
     }
 }
 

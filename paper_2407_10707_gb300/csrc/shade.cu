@@ -9,6 +9,8 @@
 // backward pass finds the lit lights the same way, queues them per warp and
 // evaluates their adjoint terms 32 at a time; per-light gradients accumulate
 // in shared memory and are flushed once per block.
+#include <algorithm>
+
 #include "batch_internal.h"
 #include "common.cuh"
 
@@ -537,12 +539,19 @@ int launch_shade(const avatar_shade_args &a, const ShadeBatch &sb, int grid, siz
 
 template <int K>
 int launch_shade_bwd(const avatar_shade_args &a, const avatar_shade_grads &g, const ShadeBatch &sb, int grid,
-                     size_t smem, cudaStream_t st)
+                     size_t smem, int sm_count, cudaStream_t st)
 {
     auto kern = a.vis_count ? shade_backward_kernel<K, true> : shade_backward_kernel<K, false>;
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return AVATAR_ERR_CUDA;
+    // One wave of resident blocks: every block ends with a barrier before its
+    // light-gradient flush, so many Gaussians per warp (whose cost ranges from
+    // a culled one's few instructions to a lit one's thousands) keep the
+    // block's warps finishing together, and fewer blocks flush.
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SHADE_THREADS, smem) == cudaSuccess && per_sm > 0)
+        grid = std::min(grid, per_sm * sm_count);
     kern<<<dim3(grid, sb.V), SHADE_THREADS, smem, st>>>(a, g, sb);
     AV_CHECK_LAUNCH();
     return AVATAR_OK;
@@ -609,14 +618,14 @@ extern "C" int avatar_shade_backward(avatar_ctx *ctx, const avatar_shade_args *a
     int grid = shade_grid(ctx, a->G);
     const ShadeBatch sb{1, 1, nullptr, nullptr, copies};
     switch (a->K) {
-        case 1: return launch_shade_bwd<1>(*a, *g, sb, grid, smem, st);
-        case 2: return launch_shade_bwd<2>(*a, *g, sb, grid, smem, st);
-        case 3: return launch_shade_bwd<3>(*a, *g, sb, grid, smem, st);
-        case 4: return launch_shade_bwd<4>(*a, *g, sb, grid, smem, st);
-        case 5: return launch_shade_bwd<5>(*a, *g, sb, grid, smem, st);
-        case 6: return launch_shade_bwd<6>(*a, *g, sb, grid, smem, st);
-        case 7: return launch_shade_bwd<7>(*a, *g, sb, grid, smem, st);
-        default: return launch_shade_bwd<8>(*a, *g, sb, grid, smem, st);
+        case 1: return launch_shade_bwd<1>(*a, *g, sb, grid, smem, ctx->sm_count, st);
+        case 2: return launch_shade_bwd<2>(*a, *g, sb, grid, smem, ctx->sm_count, st);
+        case 3: return launch_shade_bwd<3>(*a, *g, sb, grid, smem, ctx->sm_count, st);
+        case 4: return launch_shade_bwd<4>(*a, *g, sb, grid, smem, ctx->sm_count, st);
+        case 5: return launch_shade_bwd<5>(*a, *g, sb, grid, smem, ctx->sm_count, st);
+        case 6: return launch_shade_bwd<6>(*a, *g, sb, grid, smem, ctx->sm_count, st);
+        case 7: return launch_shade_bwd<7>(*a, *g, sb, grid, smem, ctx->sm_count, st);
+        default: return launch_shade_bwd<8>(*a, *g, sb, grid, smem, ctx->sm_count, st);
     }
 }
 
@@ -657,13 +666,13 @@ int av_shade_batch_backward(avatar_ctx *ctx, const avatar_shade_args *a, const a
     int grid = shade_grid(ctx, a->G);
     const ShadeBatch sb{B, V, view_pose, view_cc, copies};
     switch (a->K) {
-        case 1: return launch_shade_bwd<1>(*a, *g, sb, grid, smem, st);
-        case 2: return launch_shade_bwd<2>(*a, *g, sb, grid, smem, st);
-        case 3: return launch_shade_bwd<3>(*a, *g, sb, grid, smem, st);
-        case 4: return launch_shade_bwd<4>(*a, *g, sb, grid, smem, st);
-        case 5: return launch_shade_bwd<5>(*a, *g, sb, grid, smem, st);
-        case 6: return launch_shade_bwd<6>(*a, *g, sb, grid, smem, st);
-        case 7: return launch_shade_bwd<7>(*a, *g, sb, grid, smem, st);
-        default: return launch_shade_bwd<8>(*a, *g, sb, grid, smem, st);
+        case 1: return launch_shade_bwd<1>(*a, *g, sb, grid, smem, ctx->sm_count, st);
+        case 2: return launch_shade_bwd<2>(*a, *g, sb, grid, smem, ctx->sm_count, st);
+        case 3: return launch_shade_bwd<3>(*a, *g, sb, grid, smem, ctx->sm_count, st);
+        case 4: return launch_shade_bwd<4>(*a, *g, sb, grid, smem, ctx->sm_count, st);
+        case 5: return launch_shade_bwd<5>(*a, *g, sb, grid, smem, ctx->sm_count, st);
+        case 6: return launch_shade_bwd<6>(*a, *g, sb, grid, smem, ctx->sm_count, st);
+        case 7: return launch_shade_bwd<7>(*a, *g, sb, grid, smem, ctx->sm_count, st);
+        default: return launch_shade_bwd<8>(*a, *g, sb, grid, smem, ctx->sm_count, st);
     }
 }

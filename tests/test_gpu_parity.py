@@ -178,6 +178,45 @@ def test_visibility_edge_cases(gpu):
         api.avatar_visibility(T(f32(xp).T), T(faces, torch.int32), T(fr[:30]), [0, 0, 0], 1.0, 0.03, 64)
 
 
+def test_visibility_wide_chunks_and_bad_index(gpu):
+    """Chunks of 1024 triangles whose vertex range exceeds the raster's
+    1024-entry vertex cache take the uncached path (the triangles project
+    their own vertices); the bits are still the oracle's.  A face with an
+    out-of-range index reports AVATAR_ERR_INDEX and its chunk is skipped
+    (never read out of bounds)."""
+    api, render = gpu
+    rng = np.random.default_rng(11)
+    nv = 3000
+    xp = rng.uniform(-0.6, 0.6, size=(nv, 3))
+    # 2,500 triangles: the first two chunks span ~3,000 vertices each (uncached),
+    # the ragged third is local (cached)
+    far = rng.integers(0, nv, size=(2048, 3))
+    near = 100 + rng.integers(0, 40, size=(452, 3))
+    faces = np.concatenate([far, near]).astype(np.int32)
+    dirs = synth.fibonacci_directions(64)
+    fr = f32(synth.direction_frames(dirs).reshape(-1, 9))
+    ref = O.visibility(f32(xp).astype(np.float64), faces, fr.astype(np.float64), [0, 0, 0], 1.0, 0.05, 64)
+    for cb in (False, True):
+        status = api.status_word("cuda")
+        bits = api.avatar_visibility(T(f32(xp).T), T(faces, torch.int32), T(fr), [0, 0, 0], 1.0, 0.05, 64,
+                                     status=status, cull_back=cb)
+        torch.cuda.synchronize()
+        api.raise_on_status(status)
+        if not cb:
+            assert np.array_equal(N(bits).view(np.uint32), ref)
+        else:
+            ref1 = O.visibility(f32(xp).astype(np.float64), faces, fr.astype(np.float64), [0, 0, 0], 1.0, 0.05, 64,
+                                cull_back=True)
+            assert np.array_equal(N(bits).view(np.uint32), ref1)
+    bad = faces.copy()
+    bad[1500, 2] = nv + 5
+    status = api.status_word("cuda")
+    api.avatar_visibility(T(f32(xp).T), T(bad, torch.int32), T(fr), [0, 0, 0], 1.0, 0.05, 64, status=status,
+                          cull_back=True)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 7
+
+
 # ---------------------------------------------------------------- (c) shading
 @pytest.mark.parametrize("name", ["c1_small", "c3_fd"])
 def test_shade_matches_oracle(gpu, name):
