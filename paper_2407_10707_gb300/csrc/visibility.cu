@@ -339,11 +339,24 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
         }
     };
     const int nchunks = (p.F + VIS_CHUNK - 1) / VIS_CHUNK;
+    // Chunks after the first CL are handed out by a counter in rank 0's
+    // shared memory (one remote atomic per chunk), so a CTA that draws cheap
+    // chunks (mostly back-facing) takes more and the cluster reaches its
+    // barrier together; the depth map is a minimum, so the order is free.
+    __shared__ int s_chunk_ctr, s_next;
     int chunk = rank;
+    if (CL > 1 && rank == 0 && threadIdx.x == 0) s_chunk_ctr = CL;
     if (chunk < nchunks) load_faces(chunk, cur);
     cluster.sync();
 
-    for (; chunk < nchunks; chunk += CL) {
+    while (chunk < nchunks) {
+        int taken = 0;
+        if (threadIdx.x == 0) {
+            if constexpr (CL == 1)
+                taken = chunk + 1;
+            else
+                taken = atomicAdd(cluster.map_shared_rank(&s_chunk_ctr, 0), 1);
+        }
         const int2 vr = __ldg(vranges + chunk);
         const int v0 = vr.x, nv = vr.y - vr.x + 1;
         // nv <= 0: a bad index (reported) or no faces; the packed offsets
@@ -354,9 +367,11 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
             for (int i = threadIdx.x; i < nv; i += VIS_THREADS)
                 vcache[i] = pack_proj(project_vertex(__ldg(qv + v0 + i), B, p));
         }
-        int nxt[VIS_TPT];
-        if (chunk + CL < nchunks) load_faces(chunk + CL, nxt);
+        if (threadIdx.x == 0) s_next = taken;
         __syncthreads();
+        const int next = s_next;
+        int nxt[VIS_TPT];
+        if (next < nchunks) load_faces(next, nxt);
         if (nv > 0) {
 #pragma unroll
             for (int t = 0; t < VIS_TPT; ++t) {
@@ -375,9 +390,10 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
                 raster_triangle<CL, CULL_BACK>(pa, pb, pc, slab, p, cluster);
             }
         }
-        __syncthreads();  // the next chunk overwrites the cache
+        __syncthreads();  // the next chunk overwrites the cache (and s_next)
 #pragma unroll
         for (int t = 0; t < VIS_TPT; ++t) cur[t] = nxt[t];
+        chunk = next;
     }
     cluster.sync();
 
