@@ -337,6 +337,13 @@ typedef struct {
 
 int avatar_shade(avatar_ctx *ctx, const avatar_shade_args *a, avatar_stream_t stream);
 
+/* The cull flags of avatar_shade alone (the same FP32 rule on xd, nd and
+ * cam_center; reads nothing else and writes only a->cull[G]): splatting
+ * needs them before shading ends, so a caller can project and bin on one
+ * stream while visibility and shading run on another.  For valid inputs the
+ * flags equal the ones avatar_shade writes. */
+int avatar_cull(avatar_ctx *ctx, const avatar_shade_args *a, avatar_stream_t stream);
+
 /* Relighting under many environment lights at once (the relighting use of
  * Sec. 3.5 applied to Eq. 2): every light l shares the texel geometry of
  * `base` (light_w, light_A) and has its own radiance env_L[l].  Because the
@@ -434,7 +441,10 @@ int avatar_splat_num_tiles(const avatar_splat_args *a);
 /* Workspace shared by all splat calls of one frame; keep it intact from
  * avatar_splat to avatar_splat_backward. */
 size_t avatar_splat_workspace_size(const avatar_splat_args *a);
-/* The three steps, and all three in order. */
+/* The three steps, and all three in order.  project reads xd, cov, opacity
+ * and cull; bin reads the projection buffers and opacity; only blend reads
+ * color (it completes the per-Gaussian blend records), so project and bin
+ * may run before shading has finished. */
 int avatar_splat_project(avatar_ctx *ctx, const avatar_splat_args *a, void *ws, size_t ws_bytes,
                          avatar_stream_t stream);
 int avatar_splat_bin(avatar_ctx *ctx, const avatar_splat_args *a, void *ws, size_t ws_bytes,

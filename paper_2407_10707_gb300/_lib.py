@@ -171,6 +171,7 @@ _SIGNATURES = [
     ("avatar_visibility_static_scratch_bytes", [], C.c_size_t),
     ("avatar_visibility_static_scratch", [P, C.POINTER(VisArgs), P], I32),
     ("avatar_shade", [P, C.POINTER(ShadeArgs), P], I32),
+    ("avatar_cull", [P, C.POINTER(ShadeArgs), P], I32),
     ("avatar_shade_backward", [P, C.POINTER(ShadeArgs), C.POINTER(ShadeGrads), P], I32),
     ("avatar_knn_workspace_size", [C.POINTER(KnnArgs)], C.c_size_t),
     ("avatar_knn", [P, C.POINTER(KnnArgs), P, C.c_size_t, P], I32),

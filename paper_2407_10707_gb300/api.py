@@ -300,6 +300,24 @@ def avatar_shade(sk, knn, bits, light, cam_center, out=None, status=None, vis_de
     return out
 
 
+def avatar_cull(sk, cam_center, cull=None):
+    """The back-face flags of avatar_shade alone (the same FP32 rule on the
+    skinned xd, nd and the camera centre), [G] uint8, 1 = culled."""
+    lib = L.load()
+    ctx = context()
+    G = sk["xd"].shape[1]
+    if cull is None:
+        cull = torch.empty(G, dtype=torch.uint8, device=sk["xd"].device)
+    a = L.ShadeArgs()
+    a.G = G
+    a.xd, a.nd = _p(sk["xd"]), _p(sk["nd"])
+    for k in range(3):
+        a.cam_center[k] = float(cam_center[k])
+    a.cull = _p(cull)
+    L.check(lib.avatar_cull(ctx, C.byref(a), _stream()), "avatar_cull")
+    return cull
+
+
 def avatar_shade_multi(sk, knn, bits, light, cam_center, env_L, out=None, cull=None, status=None, ws=None,
                        radiance=None):
     """Colours under n_env environment lights sharing light['A'], light['w']

@@ -578,7 +578,32 @@ int shade_grid(const avatar_ctx *ctx, int G)
     return blocks < 1 ? 1 : (int)blocks;
 }
 
+__global__ void __launch_bounds__(256)
+cull_kernel(const float *__restrict__ xd, const float *__restrict__ nd, int G, float c0, float c1, float c2,
+            uint8_t *__restrict__ cull)
+{
+    const float C[3] = {c0, c1, c2};
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        const float x[3] = {__ldg(xd + g), __ldg(xd + (size_t)G + g), __ldg(xd + 2 * (size_t)G + g)};
+        const float n[3] = {__ldg(nd + g), __ldg(nd + (size_t)G + g), __ldg(nd + 2 * (size_t)G + g)};
+        cull[g] = is_culled(x, n, C) ? 1 : 0;
+    }
+}
+
 }  // namespace
+
+extern "C" int avatar_cull(avatar_ctx *ctx, const avatar_shade_args *a, avatar_stream_t stream)
+{
+    if (!ctx || !a || a->G < 0) return AVATAR_ERR_INVALID_ARG;
+    if (a->G == 0) return AVATAR_OK;
+    if (!a->xd || !a->nd || !a->cull) return AVATAR_ERR_INVALID_ARG;
+    long blocks = ((long)a->G + 255) / 256;
+    if (blocks > (long)ctx->sm_count * 8) blocks = (long)ctx->sm_count * 8;
+    cull_kernel<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(a->xd, a->nd, a->G, a->cam_center[0], a->cam_center[1],
+                                                               a->cam_center[2], a->cull);
+    AV_CHECK_LAUNCH();
+    return AVATAR_OK;
+}
 
 extern "C" int avatar_shade(avatar_ctx *ctx, const avatar_shade_args *a, avatar_stream_t stream)
 {

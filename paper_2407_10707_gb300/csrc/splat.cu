@@ -89,9 +89,10 @@ project_kernel(avatar_splat_args a, CamDev cam)
     }
 }
 
-// Per-Gaussian pair count, depth key and packed blend record, from the
-// caller-visible projection buffers (rect, depth, mean2d, conic) and the
-// opacity and colour.
+// Per-Gaussian pair count, depth key and the geometric blend records (rec0,
+// rec1), from the caller-visible projection buffers (rect, depth, mean2d,
+// conic) and the opacity; the colour record is completed by the blend call,
+// so binning does not wait for shading.
 __global__ void __launch_bounds__(256)
 bin_keys_kernel(avatar_splat_args a, int TS, SplatWs w)
 {
@@ -103,10 +104,21 @@ bin_keys_kernel(avatar_splat_args a, int TS, SplatWs w)
         w.dkey_a[g] = n > 0 ? __float_as_uint(a.depth[g]) : 0xffffffffu;
         w.dval_a[g] = g;
         float o = ld_attr(a.opacity, g, a.attr_dtype);
+        float4 r2;
         make_records(a.mean2d[g], a.mean2d[G + g], a.conic[g], a.conic[G + g], a.conic[2 * G + g], x0, y0, x1, y1,
-                     a.color[g], a.color[G + g], a.color[2 * G + g], o, w.rec0[g], w.rec1[g], w.rec2[g]);
+                     0.f, 0.f, 0.f, o, w.rec0[g], w.rec1[g], r2);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *w.count_g = G;
+}
+
+// The colour blend record (r, g, b, opacity) of every Gaussian.
+__global__ void __launch_bounds__(256)
+color_records_kernel(avatar_splat_args a, SplatWs w)
+{
+    const int G = a.G;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
+        w.rec2[g] = make_float4(__ldg(a.color + g), __ldg(a.color + G + g), __ldg(a.color + 2 * (size_t)G + g),
+                                ld_attr(a.opacity, g, a.attr_dtype));
 }
 
 __global__ void __launch_bounds__(256)
@@ -347,6 +359,10 @@ extern "C" int avatar_splat_blend(avatar_ctx *ctx, const avatar_splat_args *a, v
     const int ntx = (a->cam.width + ts - 1) / ts;
     const int ntiles = ntiles_of(a);
     const int ppt = ctx->tune[AVATAR_TUNE_BLEND_PPT];
+    if (a->G > 0) {
+        color_records_kernel<<<grid_cap(ctx, a->G, 256, 8), 256, 0, st>>>(*a, w);
+        AV_CHECK_LAUNCH();
+    }
     switch (ts) {
         case 8: launch_blend_ppt<8>(ppt > 2 ? 2 : ppt, a, w, ntiles, ntx, st); break;
         case 32: launch_blend_ppt<32>(ppt, a, w, ntiles, ntx, st); break;

@@ -47,8 +47,13 @@ class Renderer:
     vertices before every skinning, in place of the avatar's fixed dxv."""
 
     def __init__(self, st, tile=16, pair_capacity=None, vis_cull_back=True, shade_tc=False, visibility="depth",
-                 knn_v=None, rebind=False, mlp=None):
+                 knn_v=None, rebind=False, mlp=None, overlap=True):
         self.st = st
+        # overlap: after skinning, cull + project + bin run on a second
+        # (high-priority) stream while visibility and shading run on the
+        # calling one; the blend joins them (splatting needs only the cull
+        # flags and, in the blend, the colours from shading)
+        self.overlap = overlap
         self.mlp = mlp
         self.mlp_ws = None
         self.skin_t = st["avatar"]
@@ -89,6 +94,8 @@ class Renderer:
         self.sh = dict(color=torch.empty(3, G, device=dev), radiance=torch.empty(3, G, device=dev),
                        cull=torch.empty(G, dtype=torch.uint8, device=dev))
         self.sb = api.alloc_splat(G, st["camera"], tile, pair_capacity, dev)
+        self.cull_b = torch.empty(G, dtype=torch.uint8, device=dev)  # the binning branch's cull flags
+        self._side = torch.cuda.Stream(device=dev, priority=-1) if overlap else None
         self.graph = None
         # first eager call sizes the workspaces
         self.forward()
@@ -177,9 +184,24 @@ class Renderer:
 
     def forward(self):
         self.skin()
+        if not self.overlap:
+            self.visibility()
+            self.shade()
+            self.splat()
+            return self.sb.image
+        t = self.st["avatar"]
+        args = (self.sk["xd"], self.sk["cov"], t["opacity"], self.sh["color"], self.cull_b, self.st["camera"], self.sb,
+                self.status)
+        main, side = torch.cuda.current_stream(), self._side
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            api.avatar_cull(self.sk, self.st["cam_center"], cull=self.cull_b)
+            api.avatar_splat_project(*args)
+            api.avatar_splat_bin(*args)
         self.visibility()
         self.shade()
-        self.splat()
+        main.wait_stream(side)
+        api.avatar_splat_blend(*args)
         return self.sb.image
 
     def capture(self):

@@ -178,6 +178,30 @@ def test_visibility_edge_cases(gpu):
         api.avatar_visibility(T(f32(xp).T), T(faces, torch.int32), T(fr[:30]), [0, 0, 0], 1.0, 0.03, 64)
 
 
+def test_overlapped_frame_equals_serial_frame(gpu):
+    """Projection and binning on a second stream beside visibility and
+    shading (avatar_cull's flags, colour records completed by the blend)
+    give the serial frame bit for bit, eagerly and from a CUDA graph."""
+    api, render = gpu
+    st = render.scene_tensors(scene("c1_small"))
+    serial = render.Renderer(st, overlap=False)
+    img0 = serial.forward().clone()
+    torch.cuda.synchronize()
+    serial.check()
+    r = render.Renderer(st, overlap=True)
+    img1 = r.forward().clone()
+    torch.cuda.synchronize()
+    r.check()
+    assert torch.equal(img1, img0)
+    assert torch.equal(r.cull_b, serial.sh["cull"])
+    assert torch.equal(r.cull_b, r.sh["cull"])
+    r.sb.image.zero_()
+    r.capture()
+    r.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(r.sb.image, img0)
+
+
 def test_visibility_wide_chunks_and_bad_index(gpu):
     """Chunks of 1024 triangles whose vertex range exceeds the raster's
     1024-entry vertex cache take the uncached path (the triangles project
