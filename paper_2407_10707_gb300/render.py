@@ -37,7 +37,9 @@ def scene_tensors(scene, device="cuda", attr_dtype="f32"):
 
 class Renderer:
     """Preallocated forward frame.  forward() launches exactly the library's
-    kernels on the current stream.  vis_cull_back rasterises only light-facing
+    kernels: on the current stream, except that with overlap (the default)
+    cull, projection and binning run on a second stream forked after skinning
+    and joined before the blend (same images).  vis_cull_back rasterises only light-facing
     triangles for visibility; it gives the same bits as the two-sided rule for
     closed, outward-wound meshes such as the capsule body (set it to False
     for open or inconsistently wound meshes).  shade_tc evaluates the shading
