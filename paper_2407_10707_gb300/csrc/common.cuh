@@ -82,30 +82,11 @@ __device__ __forceinline__ float warp_reduce_scatter16(const float (&v)[16])
     return s + __shfl_xor_sync(0xffffffffu, s, 1);
 }
 
-__device__ __forceinline__ int warp_sum_i(int v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
-
 __device__ __forceinline__ unsigned lanemask_lt()
 {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
-}
-
-// Loads through the read-only path with an L1 no-allocate hint for streamed data.
-__device__ __forceinline__ float4 ldg_stream4(const float4 *p)
-{
-    float4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(p));
-    return v;
 }
 
 // Element i of an attribute array stored as FP32 or BF16 (attr_dtype).
