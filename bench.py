@@ -352,11 +352,12 @@ def roofline(stages, stats, sc, peaks, peak_kind, clocks):
     out["shade"] = {"bound": "alu", "achieved": sh_flops / (stages["shade"] * 1e-3) / 1e12, "peak": fp32_peak,
                     "unit": "TFLOP/s (fp32)", "traffic": None}
     # projection + binning: bytes of the projection (81 B per Gaussian), the
-    # blend records and keys (56 B read, 56 B written per Gaussian), the
-    # 4-pass depth sort (16 B per Gaussian and pass), the pair emission
-    # (8 B per pair), the tile sort (16 B per pair and pass) and the range pass
+    # geometric blend records and keys (44 B read, 44 B written per Gaussian;
+    # the colour record is written by the blend call), the 4-pass depth sort
+    # (16 B per Gaussian and pass), the pair emission (8 B per pair), the tile
+    # sort (16 B per pair and pass) and the range pass
     P = stats["pairs"]
-    bin_bytes = G * (81 + 112 + 4 * 16 + 8) + P * (8 + 16 * stats["tile_sort_passes"] + 4)
+    bin_bytes = G * (81 + 88 + 4 * 16 + 8) + P * (8 + 16 * stats["tile_sort_passes"] + 4)
     out["bin"] = {"bound": "hbm", "achieved": bin_bytes / (stages["bin"] * 1e-3) / 1e9, "peak": hbm,
                   "unit": "GB/s", "traffic": None}
     # blend: 15 flops per (pixel, Gaussian) pair traversed up to the pixel's
