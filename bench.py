@@ -324,8 +324,15 @@ def workload_stats(r, sc):
     traversed = int(r.sb.n_last.to(torch.int64).sum().item())
     ntiles = r.sb.tile_range.shape[0]
     tbits = max(1, (ntiles - 1).bit_length())
+    tile_passes = (tbits + 7) // 8
+    # the frame's kernels: skin (vertices, Gaussians); cull, project, keys, the
+    # depth sort (histograms + 4 passes), the pair scan (2), emission, the tile
+    # sort (histograms + one pass per 8 bits of the tile id), ranges;
+    # visibility (quantise, chunk ranges, raster + test, transpose); shading;
+    # colour records and blend (the ncu launch list shows the same sequence)
+    launches = 2 + 3 + 5 + 2 + 1 + (1 + tile_passes) + 1 + 4 + 1 + 2
     return {"front_gaussians": front, "lit_pairs_upper": lit, "pairs": P, "faces": Fc,
-            "traversed_pairs": traversed, "tile_sort_passes": (tbits + 7) // 8, "launches_per_frame": 33}
+            "traversed_pairs": traversed, "tile_sort_passes": tile_passes, "launches_per_frame": launches}
 
 
 def roofline(stages, stats, sc, peaks, peak_kind, clocks):
