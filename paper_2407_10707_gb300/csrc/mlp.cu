@@ -37,7 +37,6 @@ constexpr int MLP_KC = 32;          // K chunk of the weight stream
 constexpr int MLP_MAX_P = 128;      // pose dimensions
 constexpr int L1_CHUNKS = 2 * MLP_NF / MLP_KC;       // layer 1 (K = 128)
 constexpr int LW_CHUNKS = MLP_W / MLP_KC;            // layers 2..4 (K = 256)
-constexpr int MLP_CHUNKS = L1_CHUNKS + 3 * LW_CHUNKS;
 constexpr int BIG_CHUNKS = L1_CHUNKS + 2 * LW_CHUNKS;  // N = 256 (layers 1..3); layer 4 has N = 16
 constexpr int MLP_STAGES = 5;       // weight ring depth
 constexpr int MATH_WARPS = 8;       // epilogue / feature warps (a multiple of 4)

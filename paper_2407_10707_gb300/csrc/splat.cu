@@ -157,9 +157,10 @@ blend_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_g
     __shared__ float4 s2[BWD_WARPS][2][32];
     const int warp = threadIdx.x >> 5;
     const int item = blockIdx.x * BWD_WARPS + warp;
-    if (item >= ntiles * NB) return;  // warp-uniform; the kernel has no CTA barrier
-    const int tile = item / NB;
-    blend_box<TS, PPT>(ranges[tile], pair_gauss, rec0, rec1, rec2, W, H, tile % ntx, tile / ntx, item % NB, image,
+    constexpr int NBD = NB > 0 ? NB : 1;  // NB = 0: a split the tile cannot hold (never launched)
+    if (item >= ntiles * NB) return;      // warp-uniform; the kernel has no CTA barrier
+    const int tile = item / NBD;
+    blend_box<TS, PPT>(ranges[tile], pair_gauss, rec0, rec1, rec2, W, H, tile % ntx, tile / ntx, item % NBD, image,
                        T_final, n_last, s0[warp], s1[warp], s2[warp]);
 }
 
@@ -180,9 +181,10 @@ blend_backward_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict
     __shared__ int sg[BWD_WARPS][2][32];
     const int warp = threadIdx.x >> 5;
     const int item = blockIdx.x * BWD_WARPS + warp;
-    if (item >= ntiles * NB) return;  // warp-uniform; the kernel has no CTA barrier
-    const int tile = item / NB;
-    blend_backward_box<TS, PPT>(ranges[tile], pair_gauss, rec0, rec1, rec2, W, H, tile % ntx, tile / ntx, item % NB,
+    constexpr int NBD = NB > 0 ? NB : 1;  // NB = 0: a split the tile cannot hold (never launched)
+    if (item >= ntiles * NB) return;      // warp-uniform; the kernel has no CTA barrier
+    const int tile = item / NBD;
+    blend_backward_box<TS, PPT>(ranges[tile], pair_gauss, rec0, rec1, rec2, W, H, tile % ntx, tile / ntx, item % NBD,
                                 T_final, n_last, d_image, (size_t)G, d_mean2d, d_conic, d_opacity, d_color, s0[warp],
                                 s1[warp], s2[warp], sg[warp]);
 }

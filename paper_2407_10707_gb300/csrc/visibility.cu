@@ -434,35 +434,66 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
 }
 
 // bits[v][ow] bit l = dirbits[src(32 ow + l)][v/32] bit (v%32), src = dmap or identity.
-__global__ void vis_transpose_kernel(const uint32_t *__restrict__ dirbits, int NW, int Nv, int D, int nout,
-                                     int OW, const int32_t *__restrict__ dmap, uint32_t *__restrict__ bits,
-                                     int32_t *status)
+// A block takes TR_VW consecutive vertex words; for TR_ROWS outputs (lights)
+// at a time it stages, per output, the source direction's TR_VW words (one
+// 32-byte sector) in shared memory; warp w then transposes word w by ballots
+// and every lane writes its vertex's words of the span, four per 16-byte store
+// when OW is a multiple of four.
+constexpr int TR_VW = 8, TR_ROWS = 512, TR_THREADS = 256;
+
+__global__ void __launch_bounds__(TR_THREADS)
+vis_transpose_kernel(const uint32_t *__restrict__ dirbits, int NW, int Nv, int D, int nout, int OW,
+                     const int32_t *__restrict__ dmap, uint32_t *__restrict__ bits, int32_t *status)
 {
-    const int lane = threadIdx.x & 31;
-    const long total = (long)NW * OW;
+    __shared__ uint32_t tile[TR_ROWS][TR_VW + 1];  // padded: a column read is conflict-free
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     dirbits += (size_t)blockIdx.y * D * NW;  // pose blockIdx.y of a batch
     bits += (size_t)blockIdx.y * Nv * OW;
-    for (long t = (long)(blockIdx.x * blockDim.x + threadIdx.x) / 32; t < total;
-         t += (long)gridDim.x * blockDim.x / 32) {
-        int vw = (int)(t / OW), ow = (int)(t % OW);
-        int k = ow * 32 + lane;
-        unsigned src = 0;
-        if (k < nout) {
-            int dsrc = dmap ? __ldg(dmap + k) : k;
-            if ((unsigned)dsrc >= (unsigned)D) {
-                av_report(status, AVATAR_ERR_INDEX);
-            } else {
-                src = __ldg(dirbits + (size_t)dsrc * NW + vw);
+    const bool vec = (OW & 3) == 0 && (reinterpret_cast<uintptr_t>(bits) & 15) == 0;
+    for (int vw0 = blockIdx.x * TR_VW; vw0 < NW; vw0 += gridDim.x * TR_VW) {
+        const int vw = vw0 + warp, v = vw * 32 + lane;
+        for (int k0 = 0; k0 < OW * 32; k0 += TR_ROWS) {
+            __syncthreads();  // the previous span's tile is consumed
+            for (int i = threadIdx.x; i < TR_ROWS * TR_VW; i += TR_THREADS) {
+                const int r = i / TR_VW, c = i % TR_VW, k = k0 + r;
+                uint32_t word = 0;
+                if (k < nout && vw0 + c < NW) {
+                    const int dsrc = dmap ? __ldg(dmap + k) : k;
+                    if ((unsigned)dsrc >= (unsigned)D) {
+                        if (c == 0) av_report(status, AVATAR_ERR_INDEX);
+                    } else {
+                        word = __ldg(dirbits + (size_t)dsrc * NW + vw0 + c);
+                    }
+                }
+                tile[r][c] = word;
+            }
+            __syncthreads();
+            if (vw >= NW) continue;
+            const int ow0 = k0 / 32, nspan = min(TR_ROWS / 32, OW - ow0);
+            for (int j4 = 0; j4 < nspan; j4 += 4) {
+                uint32_t out[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (j4 + q >= nspan) break;  // warp-uniform
+                    const uint32_t src = tile[(j4 + q) * 32 + lane][warp];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const uint32_t word = __ballot_sync(0xffffffffu, (src >> i) & 1u);
+                        if (lane == i) out[q] = word;
+                    }
+                }
+                if (v < Nv) {
+                    uint32_t *dst = bits + (size_t)v * OW + ow0 + j4;
+                    if (vec) {
+                        *reinterpret_cast<uint4 *>(dst) = make_uint4(out[0], out[1], out[2], out[3]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (j4 + q < nspan) dst[q] = out[q];
+                    }
+                }
             }
         }
-        unsigned mine = 0;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            unsigned word = __ballot_sync(0xffffffffu, (src >> i) & 1u);
-            if (lane == i) mine = word;
-        }
-        int v = vw * 32 + lane;
-        if (v < Nv) bits[(size_t)v * OW + ow] = mine;
     }
 }
 
@@ -836,10 +867,9 @@ int vis_run(avatar_ctx *ctx, const avatar_vis_args *a, int B, void *ws, size_t w
 
     int nout = a->dmap ? a->NL : a->D;
     int OW = (nout + 31) / 32;
-    long warps = (long)p.NW * OW;
-    long tgrid = (warps * 32 + 255) / 256;
-    if (tgrid > (long)ctx->sm_count * 16) tgrid = (long)ctx->sm_count * 16;
-    vis_transpose_kernel<<<dim3((int)tgrid, B), 256, 0, st>>>(w.dirbits, p.NW, a->Nv, a->D, nout, OW, a->dmap,
+    long tgrid = ((long)p.NW + TR_VW - 1) / TR_VW;
+    if (tgrid > (long)ctx->sm_count * 8) tgrid = (long)ctx->sm_count * 8;
+    vis_transpose_kernel<<<dim3((int)tgrid, B), TR_THREADS, 0, st>>>(w.dirbits, p.NW, a->Nv, a->D, nout, OW, a->dmap,
                                                                a->bits, a->status);
     AV_CHECK_LAUNCH();
     return AVATAR_OK;
@@ -992,10 +1022,9 @@ extern "C" int avatar_visibility_soft(avatar_ctx *ctx, const avatar_vis_soft_arg
     // V vertex-major in direction order, then median, median, mean
     const int OW = b.D / 32;
     uint32_t *vm = b.bits ? b.bits : w.vm;
-    long warps = (long)p.NW * OW;
-    long tgrid = (warps * 32 + 255) / 256;
-    if (tgrid > (long)ctx->sm_count * 16) tgrid = (long)ctx->sm_count * 16;
-    vis_transpose_kernel<<<dim3((int)tgrid, 1), 256, 0, st>>>(w.dirbits, p.NW, b.Nv, b.D, b.D, OW, nullptr, vm,
+    long tgrid = ((long)p.NW + TR_VW - 1) / TR_VW;
+    if (tgrid > (long)ctx->sm_count * 8) tgrid = (long)ctx->sm_count * 8;
+    vis_transpose_kernel<<<dim3((int)tgrid, 1), TR_THREADS, 0, st>>>(w.dirbits, p.NW, b.Nv, b.D, b.D, OW, nullptr, vm,
                                                                b.status);
     long items = (long)b.Nv * OW;
     int fgrid = (int)std::min<long>((items + 255) / 256, (long)ctx->sm_count * 16);
