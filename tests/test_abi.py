@@ -45,6 +45,50 @@ def test_host_only_calls_without_a_gpu():
     assert lib.avatar_visibility_workspace_size(ctypes.byref(v)) == 0   # D not a multiple of 32
 
 
+def test_workspace_queries_validate_on_the_host():
+    """Size queries need no GPU: invalid arguments give 0, valid ones a size
+    that grows with the problem (pointers are never dereferenced on the host,
+    so dummy non-null values stand in for device buffers)."""
+    from paper_2407_10707_gb300 import _lib
+    lib = _lib.load()
+    dummy = ctypes.c_void_p(4096)
+
+    def vis(**kw):
+        v = _lib.VisArgs()
+        v.Nv, v.F, v.D, v.R = 50_000, 100_000, 512, 256
+        v.xp = v.faces = v.frames = v.bits = dummy
+        for k, x in kw.items():
+            setattr(v, k, x)
+        return lib.avatar_visibility_workspace_size(ctypes.byref(v))
+
+    base = vis()
+    assert base > 0
+    for bad in (dict(R=260), dict(R=1024), dict(D=4128), dict(D=0), dict(Nv=0), dict(bits=None)):
+        assert vis(**bad) == 0, bad
+    # per face: at least the packed chunk-relative word the raster reads
+    assert vis(F=200_000) - base >= 100_000 * 4
+    # per vertex and direction: at least one bit
+    assert vis(D=1024) - base >= 50_000 * 512 // 8
+
+    la = _lib.ImageLossArgs()
+    la.C, la.H, la.W, la.lam, la.weight = 3, 1024, 1024, 0.2, 1.0
+    n = lib.avatar_image_loss_workspace_size(ctypes.byref(la))
+    assert n >= 3 * 3 * 1024 * 1024 * 4          # the three dSSIM coefficient maps
+    for k, x in (("lam", 1.5), ("weight", -1.0), ("H", 0)):
+        bad = _lib.ImageLossArgs.from_buffer_copy(la)
+        setattr(bad, k, x)
+        assert lib.avatar_image_loss_workspace_size(ctypes.byref(bad)) == 0, k
+
+    a = _lib.SplatArgs()
+    a.G, a.tile, a.pair_capacity = 200_000, 16, 1 << 22
+    a.cam.width, a.cam.height = 1024, 1024
+    assert lib.avatar_splat_num_tiles(ctypes.byref(a)) == 64 * 64
+    s16 = lib.avatar_splat_workspace_size(ctypes.byref(a))
+    assert s16 > 0
+    a.pair_capacity = 1 << 23
+    assert lib.avatar_splat_workspace_size(ctypes.byref(a)) > s16      # pair buffers scale with capacity
+
+
 def test_product_path_refuses_to_run_without_cuda(monkeypatch):
     import pytest
     import torch
