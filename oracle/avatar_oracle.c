@@ -25,6 +25,9 @@
  *                   the variant Sec. 3.2 contrasts itself with); integer rules
  *   orc_shade       Eq. 2 (discrete rendering equation) with the BRDF of App. A,
  *                   back-face cull and gamma of Sec. 3.1
+ *   orc_brdf_terms  App. A: the GGX distribution, the Fresnel term, the
+ *                   Smith-Schlick geometry term and the specular f_s that
+ *                   orc_shade sums
  *   orc_project     Sec. 3.1 (3DGS rasteriser input): EWA projection
  *   orc_composite   Sec. 3.1 (3DGS rasteriser): front-to-back alpha blending,
  *                   brute force per pixel over all Gaussians
@@ -603,13 +606,32 @@ int orc_vis_filter(int Nv, int D, int Kv, const int *knn_v, const uint32_t *bits
 /*  w_o   = normalize(C - x_gd), c_o = max(n.w_o, 0)                     */
 /*  per light k with c_i = n.w_k > 0:                                   */
 /*     vis = sum_j ubar_j bit(S_j, d(k))          (Eq. 1 on visibility)  */
-/*     h = normalize(w_k + w_o), alpha = gamma^2, kk = (gamma+1)^2/8     */
-/*     D = alpha^2 / (pi ((n.h)^2 (alpha^2-1) + 1)^2)                    */
-/*     F = 0.04 + 0.96 * 2^((-5.55473 (w_o.h) - 6.98316)(w_o.h))         */
-/*     f_s = D F / (4 (c_i(1-kk)+kk) (c_o(1-kk)+kk))   (G cancelled)     */
+/*     h = normalize(w_k + w_o); D, F, f_s from orc_brdf_terms below      */
 /*     L_o += L^k A^k vis c_i (a/pi + p f_s)                             */
 /*  colour = max(L_o, 1e-6)^(1/2.2); culled Gaussians get colour 0.      */
 /* ------------------------------------------------------------------ */
+
+/* The specular terms of App. A at roughness gamma, as functions of the
+ * cosines n.h (nh), w_o.h (voh), n.w_i (ci) and n.w_o (co):
+ *   alpha = gamma^2, k = (gamma+1)^2/8
+ *   D   = alpha^2 / (pi ((n.h)^2 (alpha^2-1) + 1)^2)          (GGX)
+ *   F   = 0.04 + 0.96 * 2^((-5.55473 (w_o.h) - 6.98316)(w_o.h))
+ *   G   = G1(ci) G1(co),  G1(c) = c / (c (1-k) + k)
+ *   f_s = D F / (4 (ci(1-k)+k) (co(1-k)+k))
+ * f_s equals D F G / (4 ci co) wherever ci, co > 0 (the cosines cancel), and
+ * is the form the shading sums use.  out = {D, F, G, f_s}. */
+void orc_brdf_terms(double gamma, double nh, double voh, double ci, double co, double *out)
+{
+    double alpha = gamma * gamma, a2 = alpha * alpha, kk = (gamma + 1.0) * (gamma + 1.0) / 8.0;
+    double den = nh * nh * (a2 - 1.0) + 1.0;
+    double Dn = a2 / (ORC_PI * den * den);
+    double Fr = 0.04 + 0.96 * pow(2.0, (-5.55473 * voh - 6.98316) * voh);
+    double gi = ci * (1.0 - kk) + kk, go = co * (1.0 - kk) + kk;
+    out[0] = Dn;
+    out[1] = Fr;
+    out[2] = (ci / gi) * (co / go);
+    out[3] = Dn * Fr / (4.0 * gi * go);
+}
 static void shade_impl(int G, int K, int NL, int D, const double *xd, const double *nd, const double *ag,
                        const double *rg, const double *pg, const double *ubar, const int *knn,
                        const uint32_t *bits, const uint8_t *vis_count, int vis_den, const double *light_L,
@@ -639,7 +661,6 @@ static void shade_impl(int G, int K, int NL, int D, const double *xd, const doub
         double co = n[0] * wo[0] + n[1] * wo[1] + n[2] * wo[2];
         if (co < 0.0) co = 0.0;
         double gam = rg[g], p = pg[g];
-        double alpha = gam * gam, a2 = alpha * alpha, kk = (gam + 1.0) * (gam + 1.0) / 8.0;
         double Lo[3] = {0, 0, 0};
         for (int k = 0; k < NL; ++k) {
             const double *wi = light_w + 3 * k;
@@ -665,10 +686,9 @@ static void shade_impl(int G, int K, int NL, int D, const double *xd, const doub
                 for (int i = 0; i < 3; ++i) h[i] /= hl;
                 double nh = n[0] * h[0] + n[1] * h[1] + n[2] * h[2];
                 double voh = wo[0] * h[0] + wo[1] * h[1] + wo[2] * h[2];
-                double den = nh * nh * (a2 - 1.0) + 1.0;
-                double Dn = a2 / (ORC_PI * den * den);
-                double Fr = 0.04 + 0.96 * pow(2.0, (-5.55473 * voh - 6.98316) * voh);
-                fsp = Dn * Fr / (4.0 * (ci * (1.0 - kk) + kk) * (co * (1.0 - kk) + kk));
+                double terms[4];
+                orc_brdf_terms(gam, nh, voh, ci, co, terms);
+                fsp = terms[3];
             }
             for (int c = 0; c < 3; ++c)
                 Lo[c] += light_L[3 * k + c] * light_A[k] * vis * ci * (ag[3 * g + c] / ORC_PI + p * fsp);

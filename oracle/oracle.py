@@ -145,6 +145,17 @@ def vis_filter(bits, knn_v):
     return out
 
 
+def brdf_terms(gamma, nh, voh, ci, co, library=None):
+    """App. A terms (D, F, G, f_s) of the specular BRDF at roughness gamma for
+    the cosines n.h, w_o.h, n.w_i, n.w_o; f_s is the value the shading sums.
+    library: another build of the oracle source (a ctypes CDLL), else this one."""
+    L = library if library is not None else lib()
+    out = np.zeros(4)
+    L.orc_brdf_terms(ctypes.c_double(gamma), ctypes.c_double(nh), ctypes.c_double(voh), ctypes.c_double(ci),
+                     ctypes.c_double(co), _p(out))
+    return out
+
+
 def shade_soft(xd, nd, ag, rg, pg, ubar, knn, vis_count, vis_den, light_L, light_A, light_w, dmap, cam_center):
     """Shading with soft vertex visibility vis_count [Nv, D] / vis_den."""
     xd, nd, ag, rg, pg, ubar = map(_d, (xd, nd, ag, rg, pg, ubar))

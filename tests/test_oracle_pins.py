@@ -373,6 +373,109 @@ def test_shade_brdf_reciprocity_and_furnace_bound():
             assert 0.0 < rad[0, 0] <= 1.0
 
 
+# ---------------------------------------------------------------- App. A terms against mathematics
+def _check_ggx_normalised(brdf):
+    """A microfacet distribution has unit projected area: the integral of
+    D(h) (n.h) over the hemisphere of h is 1.  With mu = n.h and t = mu^2 the
+    integral 2 pi int_0^1 D(mu) mu dmu becomes pi int_0^1 D(sqrt t) dt, taken
+    by adaptive FP64 quadrature (breakpoints where the lobe of width ~alpha^2
+    sits)."""
+    from scipy import integrate
+    for gamma in (0.3, 0.6, 0.9):
+        a2 = gamma ** 4
+        val, _ = integrate.quad(lambda t: brdf(gamma, math.sqrt(t), 1.0, 1.0, 1.0)[0], 0.0, 1.0, limit=400,
+                                epsabs=1e-13, epsrel=1e-11, points=[1.0 - a2, 1.0 - 10.0 * a2])
+        assert abs(math.pi * val - 1.0) < 1e-8, f"gamma {gamma}: projected area {math.pi * val}"
+
+
+def _check_smith_g1(brdf):
+    """G1 by hand from App. A's k = (gamma + 1)^2 / 8 and G1(c) = c / (c (1 - k) + k):
+    gamma = 1/2: k = 9/32, G1(1/2) = (1/2) / (23/64 + 18/64) = 32/41;
+    gamma = 0.9: k = 361/800, G1(1/2) = (1/2) / (439/1600 + 722/1600) = 800/1161;
+    G1(1) = 1 for every k, so G(1/2, 1) = G1(1/2) and G(1/2, 1/2) = G1(1/2)^2."""
+    for gamma, g1 in ((0.5, 32.0 / 41.0), (0.9, 800.0 / 1161.0)):
+        assert abs(brdf(gamma, 1.0, 1.0, 0.5, 1.0)[2] - g1) < 1e-14, gamma
+        assert abs(brdf(gamma, 1.0, 1.0, 1.0, 0.5)[2] - g1) < 1e-14, gamma
+        assert abs(brdf(gamma, 1.0, 1.0, 0.5, 0.5)[2] - g1 * g1) < 1e-14, gamma
+        assert abs(brdf(gamma, 1.0, 1.0, 1.0, 1.0)[2] - 1.0) < 1e-15, gamma
+
+
+def _check_fresnel_schlick(brdf):
+    """App. A's Fresnel term is the spherical-Gaussian fit of Schlick's
+    F0 + (1 - F0)(1 - x)^5 (x = w_o.h, F0 = 0.04): within 1e-2 of it over
+    [0, 1] (the fit's worst case is 3.6e-3), exactly 1 at x = 0."""
+    x = np.linspace(0.0, 1.0, 1001)
+    F = np.array([brdf(0.5, 1.0, xi, 1.0, 1.0)[1] for xi in x])
+    assert np.abs(F - (0.04 + 0.96 * (1.0 - x) ** 5)).max() < 1e-2
+    assert F[0] == 1.0
+
+
+def _check_cancelled_form(brdf):
+    """The shading sums use f_s = D F / (4 (c_i(1-k)+k)(c_o(1-k)+k)); it must
+    equal the printed D F G / (4 c_i c_o) with the pinned D, F, G wherever both
+    cosines are positive."""
+    rng = np.random.default_rng(4)
+    for _ in range(50):
+        gamma, nh, voh, ci, co = rng.uniform(0.3, 0.9), *rng.uniform(0.05, 1.0, size=4)
+        D, F, G, fs = brdf(gamma, nh, voh, ci, co)
+        assert abs(fs - D * F * G / (4.0 * ci * co)) <= 1e-12 * abs(fs)
+
+
+BRDF_CHECKS = (_check_ggx_normalised, _check_smith_g1, _check_fresnel_schlick, _check_cancelled_form)
+
+
+@pytest.mark.parametrize("check", BRDF_CHECKS, ids=lambda f: f.__name__[7:])
+def test_brdf_terms_against_mathematics(check):
+    check(lambda *a: O.brdf_terms(*a))
+
+
+def test_shade_sums_the_pinned_brdf_terms():
+    """One Gaussian, one light, albedo 0, tint 1: the radiance is
+    L A c_i f_s with f_s the pinned App. A term at this geometry's cosines."""
+    rng = np.random.default_rng(6)
+    for _ in range(8):
+        n = rng.normal(size=3); n /= np.linalg.norm(n)
+        wi = rng.normal(size=3); wi += (0.3 - wi @ n) * n if wi @ n < 0.3 else 0; wi /= np.linalg.norm(wi)
+        wo = rng.normal(size=3); wo += (0.3 - wo @ n) * n if wo @ n < 0.3 else 0; wo /= np.linalg.norm(wo)
+        gamma = rng.uniform(0.3, 0.9)
+        xd, nd, a, r, p, ub, knn = _one_gaussian(n, a=(0, 0, 0), rough=gamma, spec=1.0)
+        L = np.array([[0.7, 1.1, 2.0]])
+        A = np.array([0.02])
+        _, rad, _ = O.shade(xd, nd, a, r, p, ub, knn, np.full((1, 1), 1, np.uint32), L, A, wi[None],
+                            np.zeros(1, np.int32), 1e7 * wo, 32)
+        h = (wi + wo) / np.linalg.norm(wi + wo)
+        fs = O.brdf_terms(gamma, n @ h, wo @ h, n @ wi, n @ wo)[3]
+        np.testing.assert_allclose(rad[0], L[0] * A[0] * (n @ wi) * fs, rtol=1e-6)
+
+
+@pytest.mark.parametrize("old,new,expect", [
+    ("kk = (gamma + 1.0) * (gamma + 1.0) / 8.0;", "kk = (gamma + 1.0) * (gamma + 1.0) / 4.0;", "smith_g1"),
+    ("double den = nh * nh * (a2 - 1.0) + 1.0;", "double den = nh * (a2 - 1.0) + 1.0;", "ggx_normalised"),
+    ("(-5.55473 * voh - 6.98316) * voh", "(-5.55473 * voh + 6.98316) * voh", "fresnel_schlick"),
+    ("out[3] = Dn * Fr / (4.0 * gi * go);", "out[3] = Dn * Fr / (4.0 * gi);", "cancelled_form"),
+], ids=["k_over_4", "D_linear_in_nh", "F_sign", "fs_drops_G1o"])
+def test_brdf_pins_catch_planted_mistakes(tmp_path, old, new, expect):
+    """Plants a plausible mistake in a copy of the oracle source (never in the
+    oracle itself), builds it and checks that some App. A pin fails on it."""
+    import ctypes
+    import subprocess
+    src = open(O._SRC).read()
+    assert src.count(old) == 1
+    path = tmp_path / "mutant.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O1", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-o", str(so),
+                           str(path), "-lm"])
+    mut = ctypes.CDLL(str(so))
+    failed = []
+    for check in BRDF_CHECKS:
+        try:
+            check(lambda *a: O.brdf_terms(*a, library=mut))
+        except AssertionError:
+            failed.append(check.__name__[7:])
+    assert expect in failed, f"the {expect} pin passes the planted mistake {new!r} (failed: {failed})"
+
+
 def test_shade_backface_cull():
     n = np.array([0.0, 0.0, 1.0])
     xd, nd, a, r, p, ub, knn = _one_gaussian(n)
