@@ -192,13 +192,15 @@ def run_gpu(args):
         train_adam_ms = train_ms + adam_ms
         # end to end through host buffers: per-frame pose and light in, image out
         e2e = STM.end_to_end(r, st, args.steps, args.warmup, flush)
+        # the CUDA-core pipe peaks, under the same clock record
+        alu = STM.alu_peaks()
     fwd_ms, train_ms, train_adam_ms, e2e["ms"] = max_over_ranks([fwd_ms, train_ms, train_adam_ms, e2e["ms"]], dev)
     # per-stage timing (eager, CUDA events on the launching stream)
     stages = STM.stage_times(r, st, reps=max(3, min(args.steps, 10)), flush=flush)
     stats = STM.workload_stats(r, sc)
     peaks, peak_kind = _peaks()
     clocks = clk.summary()
-    roof = STM.roofline(stages, stats, sc, peaks, peak_kind, clocks)
+    roof = STM.roofline(stages, stats, sc, peaks, peak_kind, clocks, alu)
     r.check()
     ts.check()
     if rank != 0:
@@ -236,18 +238,20 @@ def run_gpu(args):
         "stages_us": {k: round(v * 1000.0, 2) for k, v in stages.items()},
         "e2e": {"value": round(whole_job_rate(world, e2e["ms"]), 3), "unit": "frames/s",
                 "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
-                "how": "pose and light in from pinned host memory, frame, image staged on the device and read back "
-                       "into pinned host memory on a second stream while the next frame renders; L2 flushes "
-                       "between steps timed apart and excluded"},
+                "how": "through the Python binding (the C ABI takes device pointers): each step copies the pose "
+                       "and light in from pinned host memory (torch copies), replays the frame's CUDA graph, and "
+                       "stages the image on the device for a read-back into pinned host memory on a second stream "
+                       "while the next frame renders; the L2 flush before each step is inside the timed span"},
         "gpu_launches": stats["launches_per_frame"] * args.steps,
         "roofline": roof,
+        "alu_peaks": alu,
         "clocks": clocks,
     }
     want = set() if args.no_forms else {f for f in args.forms.split(",") if f and f != "none"}
     if want:
         line["forms"] = STM.forms(r, st, sc, args, dev, flush, fwd_ms, train_ms, want)
     if world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(sc, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = cpu_baseline(sc)
     if args.workload != WORKLOAD:
         line["config"]["workload"] = args.workload
     print(json.dumps(line), flush=True)
@@ -331,29 +335,148 @@ def workload_stats(r, sc):
     # visibility (quantise, chunk ranges, raster + test, transpose); shading;
     # colour records and blend (the ncu launch list shows the same sequence)
     launches = 2 + 3 + 5 + 2 + 1 + (1 + tile_passes) + 1 + 4 + 1 + 2
+    vis = visibility_work(r.sk["xp"].detach().cpu().numpy().T, sc)
     return {"front_gaussians": front, "lit_pairs_upper": lit, "pairs": P, "faces": Fc,
-            "traversed_pairs": traversed, "tile_sort_passes": tile_passes, "launches_per_frame": launches}
+            "traversed_pairs": traversed, "tile_sort_passes": tile_passes, "launches_per_frame": launches,
+            "visibility_work": vis}
 
 
-def roofline(stages, stats, sc, peaks, peak_kind, clocks):
-    """Per-stage achieved rate against its bound; the dominant stage first."""
+def alu_peaks():
+    """Measured throughput of the CUDA-core pipes (avatar_probe_alu): FP32
+    FFMA and the INT32 IADD3, LOP3 and IMAD streams, each the best of three
+    launches of about 20 ms timed by CUDA events on the launching stream, at
+    whatever clock the GPU runs (the clock record of the run applies)."""
+    import torch
+
+    from paper_2407_10707_gb300 import _lib as L
+    from paper_2407_10707_gb300 import api
+    sink = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    rates = {}
+    for kind in ("ffma", "iadd3", "lop3", "imad"):
+        iters = 64
+        api.probe_alu(kind, iters, sink)
+        torch.cuda.synchronize()
+        best, timed = 0.0, 0
+        for _ in range(8):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ops = api.probe_alu(kind, iters, sink)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            if ms < 10.0:                      # too short: rescale to ~20 ms, do not count
+                iters = max(iters + 1, int(iters * 20.0 / max(ms, 1e-3)))
+                continue
+            best = max(best, ops / (ms * 1e-3))
+            timed += 1
+            if timed == 3:
+                break
+        rates[kind] = best / 1e12
+    sms = L.load().avatar_ctx_sm_count(api.context())
+    return {"fp32_tflops": round(2.0 * rates["ffma"], 2), "int32_iadd3_tops": round(rates["iadd3"], 2),
+            "int32_lop3_tops": round(rates["lop3"], 2), "int32_imad_tops": round(rates["imad"], 2),
+            "sm_count": sms,
+            "how": "avatar_probe_alu: one wave of 2,048 threads per SM, eight register chains per thread, no "
+                   "memory traffic; best of three ~20 ms launches (CUDA events); FP32 = 2 flops per FFMA"}
+
+
+# Integer operations per unit of the visibility kernel's work, counted from
+# its source (vis_raster_test_kernel and raster_triangle, one-sided): every
+# (direction, triangle) setup reads three cached projected vertices, unpacks
+# them and forms the pixel-centre box (48); a triangle whose box holds a pixel
+# centre forms its area and cull test (7), a front-facing one its depth slopes
+# and loop bounds (18); every candidate pixel of such a box evaluates three
+# edge functions and their sign test (16); every covered sample the depth
+# quotient with its exact correction and the atomic minimum (14); every vertex
+# projection into the chunk cache (25) and every vertex depth test with its
+# projection, remote read and ballot (35).
+VIS_OPS = dict(setup=48, survivor=7, front=18, candidate=16, covered=14, cache_projection=25, test=35)
+
+
+def visibility_work(xp, sc, n_sample=32):
+    """CPU model of the visibility kernel's work units on the frame's own posed
+    vertices (float geometry in the kernel's pixel units; counts, not bits):
+    per direction the triangle setups, box survivors, front-facing survivors,
+    candidate pixels and covered pixel centres, on n_sample evenly spaced
+    directions scaled to all of them; the vertex-cache projections from the
+    direction-independent chunk ranges.  Returns per-frame counts and ops."""
+    import numpy as np
+    D, R = sc.frames.shape[0], sc.depth_res
+    faces = np.asarray(sc.avatar.faces, np.int64)
+    F = faces.shape[0]
+    fr = np.asarray(sc.frames, np.float64).reshape(D, 9)
+    x = np.asarray(xp, np.float64) - np.asarray(sc.window_center, np.float64)
+    half = float(sc.window_half)
+    dirs = np.linspace(0, D - 1, min(n_sample, D)).astype(int)
+    tot = dict(setup=0.0, survivor=0.0, front=0.0, candidate=0.0, covered=0.0)
+    for d in dirs:
+        e1, e2 = fr[d, 0:3], fr[d, 3:6]
+        X = ((x @ e1) + half) / (2.0 * half) * R * 16.0      # 1/16-pixel units
+        Y = ((x @ e2) + half) / (2.0 * half) * R * 16.0
+        ax, bx, cx = X[faces[:, 0]], X[faces[:, 1]], X[faces[:, 2]]
+        ay, by, cy = Y[faces[:, 0]], Y[faces[:, 1]], Y[faces[:, 2]]
+        i0 = np.maximum(0, np.ceil((np.minimum(ax, np.minimum(bx, cx)) - 8.0) / 16.0))
+        i1 = np.minimum(R - 1, np.floor((np.maximum(ax, np.maximum(bx, cx)) - 8.0) / 16.0))
+        j0 = np.maximum(0, np.ceil((np.minimum(ay, np.minimum(by, cy)) - 8.0) / 16.0))
+        j1 = np.minimum(R - 1, np.floor((np.maximum(ay, np.maximum(by, cy)) - 8.0) / 16.0))
+        surv = (i0 <= i1) & (j0 <= j1)
+        area = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax)
+        front = surv & (area > 0)
+        ni = (i1 - i0 + 1)[front].astype(np.int64)
+        nj = (j1 - j0 + 1)[front].astype(np.int64)
+        n = ni * nj
+        tot["setup"] += F
+        tot["survivor"] += int(surv.sum())
+        tot["front"] += int(front.sum())
+        tot["candidate"] += int(n.sum())
+        # covered centres: expand every (triangle, pixel) candidate
+        idx = np.repeat(np.flatnonzero(front), n)
+        k = np.arange(int(n.sum())) - np.repeat(np.cumsum(n) - n, n)
+        pi = np.repeat(i0[front], n) + k % np.repeat(ni, n)
+        pj = np.repeat(j0[front], n) + k // np.repeat(ni, n)
+        px, py = 16.0 * pi + 8.0, 16.0 * pj + 8.0
+        A = (ax[idx], ay[idx]); Bv = (bx[idx], by[idx]); Cv = (cx[idx], cy[idx])
+        wa = (Cv[0] - Bv[0]) * (py - Bv[1]) - (Cv[1] - Bv[1]) * (px - Bv[0])
+        wb = (A[0] - Cv[0]) * (py - Cv[1]) - (A[1] - Cv[1]) * (px - Cv[0])
+        wc = (Bv[0] - A[0]) * (py - A[1]) - (Bv[1] - A[1]) * (px - A[0])
+        tot["covered"] += int(((wa >= 0) & (wb >= 0) & (wc >= 0)).sum())
+    scale = D / len(dirs)
+    counts = {k: v * scale for k, v in tot.items()}
+    # vertex-cache fill: each chunk of 1,024 triangles projects its vertex range
+    ch = np.arange(F) // 1024
+    vmin = np.full(ch.max() + 1, np.iinfo(np.int64).max)
+    vmax = np.full(ch.max() + 1, -1)
+    np.minimum.at(vmin, ch, faces.min(axis=1))
+    np.maximum.at(vmax, ch, faces.max(axis=1))
+    counts["cache_projection"] = float(D * np.sum(vmax - vmin + 1))
+    counts["test"] = float(D * xp.shape[0])
+    ops = sum(VIS_OPS[k] * v for k, v in counts.items())
+    return {"counts": {k: round(v) for k, v in counts.items()}, "ops": ops, "sampled_directions": int(len(dirs))}
+
+
+def roofline(stages, stats, sc, peaks, peak_kind, clocks, alu=None):
+    """Per-stage achieved rate against its bound; the dominant stage first.
+    alu: the measured pipe peaks of alu_peaks()."""
     G, Nv, F = sc.avatar.G, sc.avatar.Nv, sc.avatar.F
     NL, D = len(sc.light.A), sc.frames.shape[0]
     W, H = sc.camera.width, sc.camera.height
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    int_peak = 152 * 128 * sm_max * 1e6 / 1e12       # int32 Tops/s at the maximum clock
-    fp32_peak = 2 * int_peak                          # FMA = 2 flops
+    int_peak = float(alu["int32_iadd3_tops"])           # INT32 lane-ops/s (ALU pipe), measured
+    fp32_peak = float(alu["fp32_tflops"])                # FFMA = 2 flops, measured
     hbm = float(peaks["hbm_gbs"])
     out = {}
     # skinning: algorithmic bytes = inputs + outputs
     skin_bytes = 140 * G + 164 * Nv
     out["skin"] = {"bound": "hbm", "achieved": skin_bytes / (stages["skin"] * 1e-3) / 1e9, "peak": hbm,
                    "unit": "GB/s", "traffic": None}
-    # visibility: integer ops of the exact rules (setup per direction-triangle,
-    # test per direction-vertex; covered samples are not counted)
-    vis_ops = D * (60.0 * F + 20.0 * Nv)
+    # visibility: integer operations of the kernel's work units (VIS_OPS x the
+    # CPU model's counts of setups, survivors, candidate pixels, covered
+    # samples, cache projections and vertex tests)
+    vis_ops = stats["visibility_work"]["ops"]
     out["visibility"] = {"bound": "alu", "achieved": vis_ops / (stages["visibility"] * 1e-3) / 1e12,
-                         "peak": int_peak, "unit": "Tops/s (int32)", "traffic": None}
+                         "peak": int_peak, "unit": "Tops/s (int32)", "traffic": None,
+                         "work": stats["visibility_work"]}
     # shading: 6 flops cosine test per front-facing pair + 50 flops per lit pair
     sh_flops = 6.0 * stats["front_gaussians"] * NL + 50.0 * stats["lit_pairs_upper"]
     out["shade"] = {"bound": "alu", "achieved": sh_flops / (stages["shade"] * 1e-3) / 1e12, "peak": fp32_peak,
@@ -392,7 +515,8 @@ def roofline(stages, stats, sc, peaks, peak_kind, clocks):
     dom = max(stages, key=lambda k: stages[k])
     res = dict(out[dom])
     res["stage"] = dom
-    res["peak_source"] = f"{peak_kind} (HBM from MEASURED_PEAKS.json; ALU peaks = 152 SMs x 128 lanes x max clock)"
+    res["peak_source"] = (f"HBM {peak_kind} (MEASURED_PEAKS.json); INT32 (IADD3) and FP32 (FFMA) measured in this "
+                          f"run by avatar_probe_alu on {alu['sm_count']} SMs")
     res["stages"] = out
     return res
 
@@ -403,8 +527,10 @@ def end_to_end(r, st, steps, warmup, flush):
     pinned host memory, replays the frame, stages the image on the device and
     reads it back into pinned host memory on a second stream while the next
     frame renders (two staging and two host buffers).  The timed span runs
-    from the first step's start to the last image's arrival on the host; the
-    L2 flushes between steps are timed on their own and taken out."""
+    from the first step's start to the last image's arrival on the host and
+    includes the L2 flush before every step (about 40 us each: the number is
+    slightly pessimistic rather than subtracting flush time that the
+    read-back overlaps)."""
     import torch
     t = st["avatar"]
     pose_h = t["pose"].cpu().pin_memory()
@@ -435,24 +561,17 @@ def end_to_end(r, st, steps, warmup, flush):
     for i in range(warmup):
         step(i)
     torch.cuda.synchronize()
-    flushes = []
     start = torch.cuda.Event(enable_timing=True)
     for i in range(steps):
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(comp)
-        flush.fill_(1.0)                      # evict L2 between steps
-        f1.record(comp)
+        flush.fill_(1.0)                      # evict L2 between steps (inside the timed span after the first)
         if i == 0:
             start.record(comp)
-        else:
-            flushes.append((f0, f1))
         step(i)
     comp.wait_event(done[(steps - 1) % 2])
     end = torch.cuda.Event(enable_timing=True)
     end.record(comp)
     end.synchronize()
-    total = start.elapsed_time(end) - sum(a.elapsed_time(b) for a, b in flushes)
+    total = start.elapsed_time(end)
     return {"ms": total / steps, "h2d": pose_h.numel() * 4 + light_h.numel() * 4, "d2h": img_h[0].numel() * 4}
 
 
@@ -779,63 +898,72 @@ def _form_batch(args, dev, reps):
 
 
 # ----------------------------------------------------------------- CPU arm
-def cpu_baseline(sc=None, budget_s=20.0, sample_frac=None):
+def cpu_baseline(sc=None, threads=None, single_thread=True):
     """The FP64 oracle as it stands, on the host cores, on a bounded sample
-    of the same frame; scaled to frames/s."""
+    of the same frame, scaled to frames/s: skinning, visibility (all
+    directions) and projection in full, shading on 20k of the Gaussians (with
+    the frame's own visibility bits), brute-force compositing on 1,024 pixels
+    drawn uniformly from the whole image; each sampled stage is scaled
+    linearly to the full frame.  threads: OpenMP threads (default all
+    cores); single_thread also times the same sample on one thread."""
     import numpy as np
 
     from oracle import oracle as O
     from paper_2407_10707_gb300 import synth
     if sc is None:
         sc = synth.config_scene(WORKLOAD)
-    cores = O.set_threads(os.cpu_count() or 1)
+    W, H = sc.camera.width, sc.camera.height
     av = sc.avatar
-    t0 = time.perf_counter()
-    bone = O.fk(av.parents, av.joints, av.pose)
-    sk = O.skin(av, bone)
-    t_skin = time.perf_counter() - t0
-    # visibility on a sample of directions (each direction is independent)
     D = sc.frames.shape[0]
-    nd = 32
-    fr = np.asarray(sc.frames.reshape(-1, 9), np.float32).astype(np.float64)
-    xp = np.asarray(sk["xp"], np.float32).astype(np.float64)
-    t0 = time.perf_counter()
-    O.visibility(xp, av.faces, fr[:nd], sc.window_center, sc.window_half, sc.vis_bias, sc.depth_res)
-    t_vis = (time.perf_counter() - t0) * D / nd
-    bits = O.visibility(xp, av.faces, fr, sc.window_center, sc.window_half, sc.vis_bias, sc.depth_res) \
-        if D <= 64 else None
-    if bits is None:
-        bits = np.full((av.Nv, D // 32), 0xFFFFFFFF, np.uint32)
-    # shading on a sample of Gaussians
     gs = min(av.G, 20_000)
     sel = slice(0, gs)
-    t0 = time.perf_counter()
-    O.shade(sk["xd"][sel], sk["nd"][sel], sk["ag"][sel], sk["rg"][sel], sk["pg"][sel], sk["ubar"][sel],
-            av.knn[sel], bits, sc.light.L, sc.light.A, sc.light.w, sc.dmap, sc.camera.center, D)
-    t_shade = (time.perf_counter() - t0) * av.G / gs
-    col, _, cull = O.shade(sk["xd"], sk["nd"], sk["ag"], sk["rg"], sk["pg"], sk["ubar"], av.knn, bits,
-                           sc.light.L, sc.light.A, sc.light.w, sc.dmap, sc.camera.center, D)
-    t0 = time.perf_counter()
-    pr = O.project(sk["xd"], sk["cov"], av.opacity, cull, sc.camera)
-    t_proj = time.perf_counter() - t0
-    # brute-force compositing on sampled pixels of the body's bounding box
-    W, H = sc.camera.width, sc.camera.height
-    rng = np.random.default_rng(0)
     npx = 1024
-    pix = rng.integers(0, W * H, npx).astype(np.int32)
-    t0 = time.perf_counter()
-    O.composite(pr["mean2d"], pr["conic"], av.opacity, col, pr["depth"], pr["valid"], W, H, pix)
-    t_comp = (time.perf_counter() - t0) * (W * H) / npx
-    frame_s = t_skin + t_vis + t_shade + t_proj + t_comp
-    return {"value": round(1.0 / frame_s, 6), "unit": "frames/s", "cores": cores, "kind": "oracle",
-            "sample": (f"skinning in full; visibility on {nd}/{D} directions; shading on {gs}/{av.G} Gaussians; "
-                       f"projection in full; brute-force compositing on {npx} random pixels of {W * H}; "
-                       f"each scaled linearly to the full frame"),
-            "stage_s": {"skin": round(t_skin, 4), "visibility": round(t_vis, 3), "shade": round(t_shade, 3),
-                        "project": round(t_proj, 4), "composite": round(t_comp, 2)}}
+    pix = np.random.default_rng(0).integers(0, W * H, npx).astype(np.int32)
+    fr = np.asarray(sc.frames.reshape(-1, 9), np.float32).astype(np.float64)
+
+    def run(nthreads):
+        cores = O.set_threads(nthreads)
+        t0 = time.perf_counter()
+        bone = O.fk(av.parents, av.joints, av.pose)
+        sk = O.skin(av, bone)
+        t_skin = time.perf_counter() - t0
+        xp = np.asarray(sk["xp"], np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        bits = O.visibility(xp, av.faces, fr, sc.window_center, sc.window_half, sc.vis_bias, sc.depth_res)
+        t_vis = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        O.shade(sk["xd"][sel], sk["nd"][sel], sk["ag"][sel], sk["rg"][sel], sk["pg"][sel], sk["ubar"][sel],
+                av.knn[sel], bits, sc.light.L, sc.light.A, sc.light.w, sc.dmap, sc.camera.center, D)
+        t_shade = (time.perf_counter() - t0) * av.G / gs
+        col, _, cull = O.shade(sk["xd"], sk["nd"], sk["ag"], sk["rg"], sk["pg"], sk["ubar"], av.knn, bits,
+                               sc.light.L, sc.light.A, sc.light.w, sc.dmap, sc.camera.center, D)
+        t0 = time.perf_counter()
+        pr = O.project(sk["xd"], sk["cov"], av.opacity, cull, sc.camera)
+        t_proj = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        O.composite(pr["mean2d"], pr["conic"], av.opacity, col, pr["depth"], pr["valid"], W, H, pix)
+        t_comp = (time.perf_counter() - t0) * (W * H) / npx
+        frame_s = t_skin + t_vis + t_shade + t_proj + t_comp
+        return frame_s, cores, {"skin": round(t_skin, 4), "visibility": round(t_vis, 3), "shade": round(t_shade, 3),
+                                "project": round(t_proj, 4), "composite": round(t_comp, 2)}
+
+    frame_s, cores, stage = run(threads or os.cpu_count() or 1)
+    out = {"value": round(1.0 / frame_s, 6), "unit": "frames/s", "cores": cores, "kind": "oracle",
+           "sample": (f"skinning, visibility ({D} directions) and projection in full; shading on {gs}/{av.G} "
+                      f"Gaussians with the frame's bits; brute-force compositing on {npx} pixels drawn uniformly "
+                      f"from all {W * H}; sampled stages scaled linearly to the full frame"),
+           "stage_s": stage}
+    if single_thread:
+        f1, _, st1 = run(1)
+        out["single_thread"] = {"value": round(1.0 / f1, 6), "unit": "frames/s", "cores": 1, "stage_s": st1}
+    O.set_threads(os.cpu_count() or 1)
+    return out
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores.  Each step is
+    one bounded sample of the frame (cpu_baseline, all cores); W untimed
+    warm-up steps, then K timed ones; the line reports their median."""
     rank, world, local = dist_env()
     if rank != 0:
         return
@@ -844,15 +972,20 @@ def run_reference(args):
     from paper_2407_10707_gb300 import synth
     sc = synth.config_scene(WORKLOAD)
     for _ in range(args.warmup):
-        pass
-    vals = []
-    for _ in range(max(1, min(args.steps, 3))):
-        vals.append(cpu_baseline(sc, budget_s=args.cpu_budget))
+        cpu_baseline(sc, single_thread=False)
+    vals, walls = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        vals.append(cpu_baseline(sc, single_thread=False))
+        walls.append(time.perf_counter() - t0)
     v = sorted(x["value"] for x in vals)[len(vals) // 2]
     cb = dict(vals[0])
     cb["value"] = v
+    cb["sample"] += f"; median of {len(vals)} such samples after {args.warmup} untimed ones"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000.0 / v, 3),
+            "steps": len(vals), "warmup": args.warmup, "ms_per_step": round(1000.0 * sum(walls) / len(walls), 3),
+            "ms_per_step_note": "wall time of one step, a bounded sample of the frame; value scales the sample to "
+                                "whole frames (1 / value = the oracle's time for a full frame)",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded procedural capsule-union avatar)",
             "config": {"workload": WORKLOAD_DESC}, "cpu_baseline": cb,
@@ -872,7 +1005,6 @@ def main():
     ap.add_argument("--forms", default="precision,relight,knn,paper_vis,batch,mlp,densify,stress",
                     help="comma list of forms to measure")
     ap.add_argument("--batch-poses", type=int, default=32, help="poses of the batch form (4 cameras each)")
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--workload", default=WORKLOAD, help="named synthetic configuration (profiling uses smaller ones)")
     args = ap.parse_args()
     if args.warmup < 3:

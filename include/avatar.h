@@ -89,11 +89,38 @@ enum avatar_tune_key {
     AVATAR_TUNE_BATCH_TILE = 2,    /* tile edge of the batched render when its desc says 0 (default 16) */
     AVATAR_TUNE_VIS_CLUSTER = 3,   /* CTAs per direction of avatar_visibility: 0 (default: 32 KB depth-map
                                       slabs, at most 8), 2, 4 or 8; raised where the slab would not fit */
-    AVATAR_TUNE_COUNT = 4
+    AVATAR_TUNE_WAIT_LIMIT = 4,    /* polls of one predecessor's word before a radix-sort look-back wait
+                                      (splatting, batched render) gives up: 0 = default (2^22, far beyond
+                                      any real wait), or 1..2^30.  A block whose wait expires writes
+                                      AVATAR_ERR_TIMEOUT to the status word and counts its offsets from the
+                                      earlier keys itself, so the result is unchanged, only slower.  The
+                                      tensor-core kernels' completion waits keep their own fixed limit. */
+    AVATAR_TUNE_COUNT = 5
 };
 int avatar_ctx_set_tuning(avatar_ctx *ctx, int key, int value);
 /* Current value of a knob, or -1 for an invalid key. */
 int avatar_ctx_get_tuning(const avatar_ctx *ctx, int key);
+
+/* ------------------------------------------------------------------ */
+/* Pipe throughput probes (the paper has no counterpart): the measured   */
+/* denominators of the roofline fractions of arithmetic-bound stages.    */
+/* ------------------------------------------------------------------ */
+enum avatar_probe_kind {
+    AVATAR_PROBE_FFMA = 0,   /* FP32 fused multiply-add (2 flops each) */
+    AVATAR_PROBE_IADD3 = 1,  /* three-input INT32 add */
+    AVATAR_PROBE_LOP3 = 2,   /* three-input INT32 logic operation */
+    AVATAR_PROBE_IMAD = 3    /* INT32 multiply-add */
+};
+/* Launches one full wave (2,048 threads per SM) in which every thread runs
+ * `iters` (>= 1) rounds of 128 operations of `kind` on eight register chains
+ * that feed one another (no memory traffic).  The caller times the launch on
+ * `stream` (CUDA events) and divides *ops (host, written on success: the
+ * operations the launch executes) by the time.  sink: one device uint32 that
+ * the kernel writes only in the impossible case its result equals an internal
+ * seed.  Errors: AVATAR_ERR_INVALID_ARG for a NULL ctx/sink, iters < 1 or an
+ * unknown kind; AVATAR_ERR_CUDA if the launch fails. */
+int avatar_probe_alu(avatar_ctx *ctx, int kind, int iters, uint32_t *sink, long long *ops,
+                     avatar_stream_t stream);
 
 /* ------------------------------------------------------------------ */
 /* (a) Skinning - Sec. 3.1, Eq. 1                                       */
@@ -260,7 +287,8 @@ int avatar_visibility(avatar_ctx *ctx, const avatar_vis_args *a, void *ws, size_
  *    array are rejected with AVATAR_ERR_WORKSPACE before any launch.
  *  - The first call on a device looks up the array's device address (with the
  *    context's device made current for the lookup); make that first call
- *    before any stream capture on the device.
+ *    before any stream capture on the device.  A call that finds the device's
+ *    CUDA context replaced (after cudaDeviceReset, say) looks it up again.
  *  - All calls on a device share the one array and it keeps the previous
  *    call's contents: calls that may overlap on the GPU (different streams
  *    without ordering) race on it and must be serialised by the caller.

@@ -26,6 +26,8 @@ TUNE_BLEND_PPT = 0
 TUNE_BLEND_BWD_PPT = 1
 TUNE_BATCH_TILE = 2
 TUNE_VIS_CLUSTER = 3
+TUNE_WAIT_LIMIT = 4
+PROBE_FFMA, PROBE_IADD3, PROBE_LOP3, PROBE_IMAD = 0, 1, 2, 3   # avatar_probe_kind
 
 
 class AvatarError(RuntimeError):
@@ -201,6 +203,7 @@ _SIGNATURES = [
     ("avatar_adam", [P, C.POINTER(AdamArgs), P], I32),
     ("avatar_image_loss_workspace_size", [C.POINTER(ImageLossArgs)], C.c_size_t),
     ("avatar_image_loss", [P, C.POINTER(ImageLossArgs), P, C.c_size_t, P], I32),
+    ("avatar_probe_alu", [P, I32, I32, P, C.POINTER(C.c_longlong), P], I32),
 ]
 
 EXPORTED = [s[0] for s in _SIGNATURES]

@@ -649,3 +649,14 @@ class Adam:
         self.t += 1
         groups = [(self.params[k], grads[k], self.m[k], self.v[k], self.lr[k]) for k in self.params]
         avatar_adam(groups, self.t, *self.b)
+
+
+def probe_alu(kind, iters, sink):
+    """Launches one pipe-throughput probe (avatar_probe_alu) on the current
+    stream; returns the operations it executes.  kind: 'ffma', 'iadd3',
+    'lop3' or 'imad'; sink: a 1-element int32 device tensor."""
+    kinds = dict(ffma=L.PROBE_FFMA, iadd3=L.PROBE_IADD3, lop3=L.PROBE_LOP3, imad=L.PROBE_IMAD)
+    ops = C.c_longlong(0)
+    L.check(L.load().avatar_probe_alu(context(), kinds[kind], int(iters), _p(sink), C.byref(ops), _stream()),
+            "avatar_probe_alu")
+    return int(ops.value)

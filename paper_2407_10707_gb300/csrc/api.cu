@@ -109,6 +109,9 @@ extern "C" int avatar_ctx_set_tuning(avatar_ctx *ctx, int key, int value)
         case AVATAR_TUNE_VIS_CLUSTER:
             if (value != 0 && value != 2 && value != 4 && value != 8) return AVATAR_ERR_INVALID_ARG;
             break;
+        case AVATAR_TUNE_WAIT_LIMIT:
+            if (value < 0 || value > (1 << 30)) return AVATAR_ERR_INVALID_ARG;
+            break;
         default: break;
     }
     ctx->tune[key] = value;

@@ -676,7 +676,7 @@ int render_batch(avatar_ctx *ctx, const avatar_batch_desc *d, void *ws, size_t w
     AV_CHECK_LAUNCH();
     const SortWs sw{w.sort_hist, w.sort_desc};
     const int VGi = (int)m.VG;
-    AV_TRY(radix_sort(w.dkey_a, w.dval_a, w.dkey_b, w.dval_b, 32, w.count_vg, VGi, sw, d->status, st));
+    AV_TRY(radix_sort(w.dkey_a, w.dval_a, w.dkey_b, w.dval_b, 32, w.count_vg, VGi, sw, d->status, st, sort_spin_limit(ctx)));
     const int NB = std::min(1024, std::max(1, (VGi + 8191) / 8192));
     pair_scan_reduce_kernel<<<NB, 1024, 0, st>>>(w.dval_a, w.npairs, VGi, NB, w.block_sums);
     pair_scan_down_kernel<<<NB, 1024, 0, st>>>(w.dval_a, w.npairs, VGi, NB, w.block_sums, w.offsets, d->num_pairs,
@@ -692,7 +692,7 @@ int render_batch(avatar_ctx *ctx, const avatar_batch_desc *d, void *ws, size_t w
     emit_batch_kernel<<<grid_cap(ctx, m.VG, 256, 8), 256, 0, st>>>(w.views, m.G, m.VG, TS, w.dval_a, w.offsets,
                                                                     w.npairs, w.rect, (long)m.cap, k_emit, v_emit);
     AV_CHECK_LAUNCH();
-    AV_TRY(radix_sort(k_emit, v_emit, k_other, v_other, passes * 8, d->num_pairs, (int)m.cap, sw, d->status, st));
+    AV_TRY(radix_sort(k_emit, v_emit, k_other, v_other, passes * 8, d->num_pairs, (int)m.cap, sw, d->status, st, sort_spin_limit(ctx)));
     tile_ranges_kernel<<<ctx->sm_count * 8, 256, 0, st>>>(w.pkey_a, d->num_pairs, (long)m.cap, (int)T, w.ranges);
     AV_CHECK_LAUNCH();
     // persistent blend over every view's tiles

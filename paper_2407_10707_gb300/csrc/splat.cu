@@ -305,7 +305,7 @@ extern "C" int avatar_splat_bin(avatar_ctx *ctx, const avatar_splat_args *a, voi
     AV_CHECK_LAUNCH();
     // 1. stable depth sort of all Gaussians (4 passes -> result back in dkey_a/dval_a)
     AV_TRY(radix_sort(w.dkey_a, w.dval_a, w.dkey_b, w.dval_b, 32, w.count_g, G, SortWs{w.sort_hist, w.sort_desc},
-                       a->status, st));
+                       a->status, st, sort_spin_limit(ctx)));
     // 2. pair offsets in depth order
     pair_scan_reduce_kernel<<<w.NB, 1024, 0, st>>>(w.dval_a, w.npairs, G, w.NB, w.block_sums);
     pair_scan_down_kernel<<<w.NB, 1024, 0, st>>>(w.dval_a, w.npairs, G, w.NB, w.block_sums, w.offsets, a->num_pairs,
@@ -325,7 +325,7 @@ extern "C" int avatar_splat_bin(avatar_ctx *ctx, const avatar_splat_args *a, voi
     AV_CHECK_LAUNCH();
     // 4. stable sort of the pairs on the tile id
     AV_TRY(radix_sort(k_emit, v_emit, k_other, v_other, passes * 8, a->num_pairs, (int)cap,
-                       SortWs{w.sort_hist, w.sort_desc}, a->status, st));
+                       SortWs{w.sort_hist, w.sort_desc}, a->status, st, sort_spin_limit(ctx)));
     // 5. tile ranges (sorted keys are in pkey_a)
     tile_ranges_kernel<<<ctx->sm_count * 8, 256, 0, st>>>(w.pkey_a, a->num_pairs, cap, ntiles,
                                                           (int2 *)a->tile_range);

@@ -210,15 +210,18 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int &total)
 //                      ranks its keys stably in shared memory, publishes its
 //                      digit counts and finds its global offsets by
 //                      decoupled look-back over earlier tiles, then scatters.
-// Look-back spins are bounded: a wait that expires reports
-// AVATAR_ERR_TIMEOUT and the block carries on (never hangs).
+// Look-back spins are bounded (spin_limit polls of one predecessor's word):
+// a block whose wait expires reports AVATAR_ERR_TIMEOUT and takes its
+// offsets the slow, exact way - it counts the digits of every earlier tile's
+// keys itself - so it never hangs, never writes out of bounds, and the
+// result stays the sorted order.
 constexpr int OS_THREADS = 256;
 constexpr int OS_WARPS = OS_THREADS / 32;
 constexpr int OS_ITEMS = 8;
 constexpr int OS_TILE = OS_THREADS * OS_ITEMS;  // 2048 keys per tile
 constexpr int OS_MAX_PASSES = 4;
 constexpr unsigned FLAG_AGG = 1u << 30, FLAG_INC = 2u << 30, FLAG_MASK = 3u << 30;
-constexpr int SPIN_LIMIT = 1 << 22;
+constexpr int SPIN_LIMIT = 1 << 22;   // default polls of one look-back word
 constexpr int OS_LOOKBACK = 16;
 
 __device__ __forceinline__ unsigned ld_volatile(const unsigned *p)
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(OS_THREADS)
 onesweep_kernel(const uint32_t *__restrict__ kin, const int32_t *__restrict__ vin, uint32_t *__restrict__ kout,
                 int32_t *__restrict__ vout, const int32_t *__restrict__ n_ptr, int cap, int shift,
                 const int32_t *__restrict__ hist, unsigned *__restrict__ desc, int32_t *__restrict__ ticket,
-                int32_t *status)
+                int32_t *status, int spin_limit)
 {
     __shared__ int s_tile;
     __shared__ int s_wcnt[OS_WARPS][RADIX];  // running, then exclusive-over-warps digit counts
@@ -329,8 +332,8 @@ onesweep_kernel(const uint32_t *__restrict__ kin, const int32_t *__restrict__ vi
         st_volatile(my, (tile == 0 ? FLAG_INC : FLAG_AGG) | (unsigned)sum);
         // decoupled look-back, OS_LOOKBACK predecessors per round trip
         int prefix = 0;
-        bool found = tile == 0;
-        for (int p = tile - 1; p >= 0 && !found; p -= OS_LOOKBACK) {
+        bool found = tile == 0, expired = false;
+        for (int p = tile - 1; p >= 0 && !found && !expired; p -= OS_LOOKBACK) {
             unsigned v[OS_LOOKBACK];
 #pragma unroll
             for (int i = 0; i < OS_LOOKBACK; ++i)
@@ -342,18 +345,30 @@ onesweep_kernel(const uint32_t *__restrict__ kin, const int32_t *__restrict__ vi
                 if (p - i >= 0) {
                     int spins = 0;
                     while ((x & FLAG_MASK) == 0) {
-                        if (++spins > SPIN_LIMIT) {
-                            av_report(status, AVATAR_ERR_TIMEOUT);
-                            x = FLAG_INC;
+                        if (++spins > spin_limit) {
+                            expired = true;
                             break;
                         }
                         __nanosleep(32);
                         x = ld_volatile(desc + (size_t)(p - i) * RADIX + d);
                     }
+                    if (expired) break;
                 }
                 prefix += (int)(x & ~FLAG_MASK);
                 if ((x & FLAG_MASK) == FLAG_INC) found = true;
             }
+        }
+        // a wait expired somewhere in the block: every digit's prefix is
+        // recounted from the keys of the earlier tiles (base of them), all of
+        // which this pass reads and none of which it writes
+        if (__syncthreads_or(expired)) {
+            s_gbase[d] = 0;
+            __syncthreads();
+            for (int i = tid; i < base; i += OS_THREADS) atomicAdd(&s_gbase[(kin[i] >> shift) & 255u], 1);
+            __syncthreads();
+            prefix = s_gbase[d];
+            if (tid == 0) av_report(status, AVATAR_ERR_TIMEOUT);
+            __syncthreads();
         }
         if (tile > 0) st_volatile(my, FLAG_INC | (unsigned)(prefix + sum));
         // global base of digit d: exclusive scan of this pass's histogram
@@ -369,6 +384,13 @@ onesweep_kernel(const uint32_t *__restrict__ kin, const int32_t *__restrict__ vi
         kout[dst] = key[i];
         vout[dst] = val[i];
     }
+}
+
+// Look-back polls the context allows (AVATAR_TUNE_WAIT_LIMIT; 0 = default).
+inline int sort_spin_limit(const avatar_ctx *ctx)
+{
+    const int v = ctx ? ctx->tune[AVATAR_TUNE_WAIT_LIMIT] : 0;
+    return v > 0 ? v : SPIN_LIMIT;
 }
 
 // Scratch of the radix sort: [OS_MAX_PASSES][RADIX] histograms followed by
@@ -387,7 +409,7 @@ inline size_t sort_desc_words(size_t max_items)
 // passes, ping-ponging with (k1, v1): an even number of passes ends in
 // (k0, v0), an odd number in (k1, v1).
 inline int radix_sort(uint32_t *k0, int32_t *v0, uint32_t *k1, int32_t *v1, int bits, const int32_t *n_ptr, int cap,
-                      const SortWs &w, int32_t *status, cudaStream_t st)
+                      const SortWs &w, int32_t *status, cudaStream_t st, int spin_limit = SPIN_LIMIT)
 {
     int passes = (bits + 7) / 8;
     if (passes < 1) passes = 1;
@@ -405,7 +427,8 @@ inline int radix_sort(uint32_t *k0, int32_t *v0, uint32_t *k1, int32_t *v1, int 
     int32_t *tickets = w.hist + OS_MAX_PASSES * RADIX;
     for (int p = 0; p < passes; ++p) {
         onesweep_kernel<<<ntiles, OS_THREADS, 0, st>>>(kin, vin, kout, vout, n_ptr, cap, 8 * p, w.hist + p * RADIX,
-                                                       w.desc + (size_t)p * ntiles * RADIX, tickets + p, status);
+                                                       w.desc + (size_t)p * ntiles * RADIX, tickets + p, status,
+                                                       spin_limit);
         uint32_t *tk = kin;
         kin = kout;
         kout = tk;

@@ -15,6 +15,7 @@
 // All arithmetic is exact integer arithmetic (bounds in the header), so the
 // bits are reproducible bit for bit by any correct implementation.
 #include <cooperative_groups.h>
+#include <cuda.h>
 
 #include <algorithm>
 #include <mutex>
@@ -1054,27 +1055,56 @@ __device__ __align__(256) unsigned char g_vis_static_scratch[VIS_STATIC_SCRATCH_
 constexpr int VIS_MAX_DEVICES = 64;
 std::mutex g_vis_static_mu;
 void *g_vis_static_ptr[VIS_MAX_DEVICES];  // device address of the array, per device
+CUcontext g_vis_static_cuctx[VIS_MAX_DEVICES];  // the CUDA context that address belongs to
 
-// Looks up the array's device address on the context's device (once per
-// device).  The host-side symbol g_vis_static_scratch is only a stand-in and
-// must never be handed to a kernel.
+// cuCtxGetCurrent through the runtime's driver entry point (no link to the
+// driver library); NULL if the driver does not provide it.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+CtxGetCurrentFn ctx_get_current()
+{
+    static CtxGetCurrentFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGetCurrentFn)p;
+        else
+            (void)cudaGetLastError();
+    }
+    return fn;
+}
+
+// Looks up the array's device address on the context's device, with that
+// device current: on the first call for the device, and again whenever the
+// device's CUDA context is not the one the cached address came from (after
+// cudaDeviceReset, say).  The host-side symbol g_vis_static_scratch is only a
+// stand-in and must never be handed to a kernel.
 int vis_static_scratch(const avatar_ctx *ctx, void **out)
 {
     if (ctx->device < 0 || ctx->device >= VIS_MAX_DEVICES) return AVATAR_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_vis_static_mu);
-    if (!g_vis_static_ptr[ctx->device]) {
-        int prev = -1;
-        if (cudaGetDevice(&prev) != cudaSuccess) return AVATAR_ERR_CUDA;
-        if (prev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) return AVATAR_ERR_CUDA;
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) return AVATAR_ERR_CUDA;
+    if (prev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) return AVATAR_ERR_CUDA;
+    CUcontext cur = nullptr;
+    CtxGetCurrentFn get = ctx_get_current();
+    if (get && get(&cur) != CUDA_SUCCESS) cur = nullptr;
+    int rc = AVATAR_OK;
+    if (!g_vis_static_ptr[ctx->device] || cur != g_vis_static_cuctx[ctx->device]) {
         void *p = nullptr;
-        cudaError_t rc = cudaGetSymbolAddress(&p, g_vis_static_scratch);
-        if (prev != ctx->device) cudaSetDevice(prev);
-        if (rc != cudaSuccess || p == nullptr) {
+        if (cudaGetSymbolAddress(&p, g_vis_static_scratch) != cudaSuccess || p == nullptr) {
             (void)cudaGetLastError();
-            return AVATAR_ERR_CUDA;
+            rc = AVATAR_ERR_CUDA;
+        } else {
+            g_vis_static_ptr[ctx->device] = p;
+            g_vis_static_cuctx[ctx->device] = cur;
         }
-        g_vis_static_ptr[ctx->device] = p;
     }
+    if (prev != ctx->device) cudaSetDevice(prev);
+    if (rc != AVATAR_OK) return rc;
     *out = g_vis_static_ptr[ctx->device];
     return AVATAR_OK;
 }

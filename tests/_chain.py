@@ -4,9 +4,9 @@ chain_check(r, sc) takes a Renderer that has just rendered the scene sc and
 feeds every oracle stage the GPU's own FP32 outputs of the stage before it,
 so each stage is compared on identical inputs:
 
-  skinning    GPU vs the oracle on the avatar itself (relative to the
-              largest magnitude: 1e-5 for the short chains, 5e-5 for
-              normalised vectors and covariances)
+  skinning    GPU vs the oracle on the avatar rounded to FP32 as the GPU
+              holds it (relative to the largest magnitude: 1e-5 for the
+              short chains, 5e-5 for normalised vectors and covariances)
   visibility  GPU posed vertices -> orc_visibility (the two-sided rule):
               the light-ordered bits bit for bit, every direction
   shading     GPU skinning outputs + GPU bits -> orc_shade: cull flags bit
@@ -56,6 +56,18 @@ def _opacity(sc):
     return f32(sc.avatar.opacity).astype(np.float64)
 
 
+FLOAT_FIELDS = ("xv", "nv", "wv", "av", "rv", "pv", "dxv", "xg", "logscale", "quat", "opacity", "joints", "pose")
+
+
+def fp32_avatar(av):
+    """The avatar as the GPU holds it: every floating field rounded to FP32
+    (and back to FP64 for the oracle).  Identical stage inputs matter in
+    Eq. 1: a Gaussian 0.15 mm from a vertex turns the 3e-8 m rounding of its
+    position into a 2e-4 relative change of that vertex's distance."""
+    import dataclasses
+    return dataclasses.replace(av, **{k: f32(getattr(av, k)).astype(np.float64) for k in FLOAT_FIELDS})
+
+
 def chain_check(r, sc, pixels=None, two_sided=True):
     """Runs every stage comparison (asserting) and returns a report dict.
     sc: the scene as the GPU holds it (BF16-rounded attributes for BF16
@@ -64,8 +76,9 @@ def chain_check(r, sc, pixels=None, two_sided=True):
     g = gpu_buffers(r)
     av = sc.avatar
     rep = {}
-    # (a) skinning, on the avatar itself
-    sk = O.skin(av, O.fk(av.parents, av.joints, av.pose))
+    # (a) skinning, on the avatar as the GPU holds it
+    av32 = fp32_avatar(av)
+    sk = O.skin(av32, O.fk(av32.parents, av32.joints, av32.pose))
     for k, tol in (("xp", 1e-5), ("xd", 1e-5), ("cov", 5e-5), ("nd", 5e-5), ("ag", 1e-5), ("rg", 1e-5),
                    ("pg", 1e-5), ("ubar", 1e-5)):
         e = rel_err(g[k], sk[k])

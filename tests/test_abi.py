@@ -96,3 +96,21 @@ def test_product_path_refuses_to_run_without_cuda(monkeypatch):
     monkeypatch.setattr(torch.cuda, "is_available", lambda: False)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         api.context()
+
+
+def test_static_scratch_holds_the_paper_scale_visibility():
+    """The scratch-free visibility entry point's fixed array holds the
+    workspace of the paper-scale frame (50k vertices, 99,856 faces, 512
+    directions at 256^2, 512 lights) and refuses the stress frame's."""
+    import ctypes as C
+    from paper_2407_10707_gb300 import _lib as L
+    lib = L.load()
+    cap = lib.avatar_visibility_static_scratch_bytes()
+    for (nv, F, D, R, NL), fits in (((50_000, 99_856, 512, 256, 512), True),
+                                    ((200_000, 400_000, 1024, 512, 2048), False)):
+        a = L.VisArgs()
+        a.Nv, a.F, a.D, a.R, a.NL = nv, F, D, R, NL
+        a.xp = a.faces = a.frames = a.bits = a.dmap = C.c_void_p(256)
+        a.half_extent = 1.0
+        need = lib.avatar_visibility_workspace_size(C.byref(a))
+        assert need > 0 and (need <= cap) == fits, (need, cap)

@@ -389,6 +389,47 @@ def test_pair_overflow_is_reported_not_faulted(gpu):
     assert float(N(r.sb.image).max()) == 0.0
 
 
+def test_sort_wait_that_runs_out_reports_timeout_and_keeps_the_image(gpu):
+    """The radix sorts of splatting with one poll allowed per look-back wait
+    (AVATAR_TUNE_WAIT_LIMIT = 1) on the paper-scale frame (98 depth-sort
+    tiles, ~1,000 tile-sort tiles): some block finds a predecessor not yet
+    published and gives up, the status word reads AVATAR_ERR_TIMEOUT, the
+    call returns, and the expired blocks' exact fallback leaves the image
+    bit for bit the default one."""
+    api, render = gpu
+    from paper_2407_10707_gb300 import _lib as L
+    lib = L.load()
+    ctx = api.context()
+    assert lib.avatar_ctx_set_tuning(ctx, L.TUNE_WAIT_LIMIT, -1) != 0
+    st = render.scene_tensors(scene("c2_paper"))
+    r = render.Renderer(st)
+    torch.cuda.synchronize()
+    r.check()
+    img0 = r.sb.image.clone()
+    assert lib.avatar_ctx_set_tuning(ctx, L.TUNE_WAIT_LIMIT, 1) == 0
+    try:
+        seen = []
+        for _ in range(5):           # expiry depends on block timing; one poll makes it near certain
+            r.status.zero_()
+            r.sb.image.zero_()
+            r.forward()
+            torch.cuda.synchronize()
+            seen.append(int(r.status.item()))
+            assert seen[-1] in (0, 4), seen
+            assert torch.equal(r.sb.image, img0)
+            if seen[-1] == 4:
+                break
+        print(f"status per attempt with one poll per wait: {seen}")
+        assert seen[-1] == 4, f"no wait ran out in {len(seen)} frames"
+    finally:
+        assert lib.avatar_ctx_set_tuning(ctx, L.TUNE_WAIT_LIMIT, 0) == 0
+    r.status.zero_()
+    r.forward()
+    torch.cuda.synchronize()
+    r.check()
+    assert torch.equal(r.sb.image, img0)
+
+
 # ---------------------------------------------------------------- whole frame
 @pytest.mark.parametrize("name", ["c1_small", "c3_fd"])
 def test_frame_end_to_end(gpu, name):
@@ -475,11 +516,15 @@ def _grad_case(gpu, fd_problem, bppt):
           {k: (f"{a:.2e}", f"{b:.2e}") for k, (a, b) in worst.items()})
 
 
-def grad_agreement(got, ref, name, rtol=1e-3, floor=1e-3, atol_frac=1e-6):
+def grad_agreement(got, ref, name, rtol=1e-3, floor=1e-3, atol_frac=1e-5):
     """Per-element gradient check: every element whose reference magnitude
     exceeds floor x the group's largest is within rtol relative, and every
-    element within rtol |ref| + atol_frac x the largest.  Returns (worst
-    per-element relative error over the first set, max error / largest)."""
+    element within rtol |ref| + atol_frac x the largest.  The absolute
+    floor covers FP32 accumulation: an element is a sum over many pixels'
+    atomically added terms, each add rounding at 2^-24 of a running sum that
+    can approach the group's largest element, so a small element may cancel
+    to ~1e-6..1e-5 of that largest.  Returns (worst per-element relative
+    error over the first set, max error / largest)."""
     got = np.asarray(got, np.float64).reshape(-1)
     ref = np.asarray(ref, np.float64).reshape(-1)
     m = float(np.abs(ref).max())
@@ -493,7 +538,10 @@ def grad_agreement(got, ref, name, rtol=1e-3, floor=1e-3, atol_frac=1e-6):
     assert worst <= rtol, (f"{name}: element {int(np.flatnonzero(big)[i])} off by {worst:.3g} relative "
                            f"({got[big][i]:.6g} vs {ref[big][i]:.6g})")
     over = np.abs(got - ref) > rtol * np.abs(ref) + atol_frac * m
-    assert not over.any(), f"{name}: {int(over.sum())} small elements beyond rtol |ref| + {atol_frac} max|ref|"
+    if over.any():
+        j = int(np.argmax(np.where(over, np.abs(got - ref), 0.0)))
+        raise AssertionError(f"{name}: {int(over.sum())} small elements beyond rtol |ref| + {atol_frac} max|ref|; "
+                             f"worst {got[j]:.6g} vs {ref[j]:.6g} (max|ref| {m:.6g})")
     return worst, float(np.abs(got - ref).max() / m)
 
 

@@ -49,10 +49,12 @@ def test_static_scratch_matches_workspace_entry_point_on_two_calls():
     ctx = api.context()
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     assert lib.avatar_visibility_static_scratch_bytes() == 8 << 20
-    # two calls in a row with different inputs; each must equal the
+    # calls in a row with different inputs, a larger one (20k vertices, 512
+    # directions: 1.7 MiB of scratch) before a smaller one that leaves the
+    # larger call's data beyond its own layout; each must equal the
     # workspace entry point bit for bit
-    for seed in (11, 12):
-        sc, xp, faces, frames, dmap = _case(api, synth, seed)
+    for seed, nd, nv in ((11, 512, 20_000), (12, 128, 4000), (13, 128, 4000)):
+        sc, xp, faces, frames, dmap = _case(api, synth, seed, n_dirs=nd, nv=nv)
         nw = (dmap.shape[0] + 31) // 32
         ref_bits = torch.full((xp.shape[1], nw), -1, dtype=torch.int32, device="cuda")
         got_bits = torch.full_like(ref_bits, 7)
