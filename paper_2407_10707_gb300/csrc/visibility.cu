@@ -135,6 +135,55 @@ __device__ __forceinline__ int floor_div_i32(int num, int den)
     return q;
 }
 
+// Box-test words of a projected vertex inside the window: the last pixel
+// centre at or before its coordinate and the first at or after it, per axis,
+// biased by VB so both stay positive 16-bit halves:
+//   t.x = (floor((X - 8) / 16) + VB) | (floor((Y - 8) / 16) + VB) << 16
+//   t.y = ( ceil((X - 8) / 16) + VB) | ( ceil((Y - 8) / 16) + VB) << 16
+// A triangle's pixel-centre box [max(0, min ceil), min(R - 1, max floor)] is
+// non-empty iff the halfwise max of its t.x is >= the halfwise min of its t.y
+// (inside the window ceil >= 0 and floor <= R - 1, so the clamps are void).
+// An outside vertex gets t.x = 0x7fff7fff: the test passes and the full
+// path, which skips triangles with an outside vertex, decides.
+constexpr int VB = 0x100;
+
+__device__ __forceinline__ uint2 box_words(const Proj &q)
+{
+    if (!q.in) return make_uint2(0x7fff7fffu, 0u);
+    const int ex = q.X - 8, ey = q.Y - 8;
+    const int fx = ex >> 4, fy = ey >> 4;  // floor (arithmetic shift)
+    const int cx = fx + ((ex & 15) != 0), cy = fy + ((ey & 15) != 0);
+    return make_uint2((unsigned)(fx + VB) | ((unsigned)(fy + VB) << 16),
+                      (unsigned)(cx + VB) | ((unsigned)(cy + VB) << 16));
+}
+
+__device__ __forceinline__ unsigned max_s16x2(unsigned a, unsigned b)
+{
+    unsigned d;
+    asm("max.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+__device__ __forceinline__ unsigned min_s16x2(unsigned a, unsigned b)
+{
+    unsigned d;
+    asm("min.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+// Both halves of mx >= the matching halves of mn (all halves in [0, 0x7fff]):
+// (0x8000 | mx_h) - mn_h never borrows out of its half and keeps bit 15 iff
+// mx_h >= mn_h.
+__device__ __forceinline__ bool box_has_centre(unsigned mx, unsigned mn)
+{
+    return (((mx | 0x80008000u) - mn) & 0x80008000u) == 0x80008000u;
+}
+
+template <int CL, bool CULL_BACK>
+__device__ __forceinline__ void raster_span(int ax, int ay, int az, int bx, int by, int bz, int cx, int cy, int cz,
+                                            int i0, int i1, int j0, int j1, int *slab, const VisParams &p,
+                                            cg::cluster_group &cluster);
+
 template <int CL, bool CULL_BACK>
 __device__ __forceinline__ void raster_triangle(uint2 pa, uint2 pb, uint2 pc, int *slab, const VisParams &p,
                                                 cg::cluster_group &cluster)
@@ -148,6 +197,29 @@ __device__ __forceinline__ void raster_triangle(uint2 pa, uint2 pb, uint2 pc, in
     int i0 = max(0, (min(ax, min(bx, cx)) + 7) >> 4), i1 = min(R - 1, (max(ax, max(bx, cx)) - 8) >> 4);
     int j0 = max(0, (min(ay, min(by, cy)) + 7) >> 4), j1 = min(R - 1, (max(ay, max(by, cy)) - 8) >> 4);
     if (i0 > i1 || j0 > j1) return;
+    raster_span<CL, CULL_BACK>(ax, ay, az, bx, by, bz, cx, cy, cz, i0, i1, j0, j1, slab, p, cluster);
+}
+
+// The same triangle when the box test already ran on its box words (mx, mn:
+// the halfwise max of t.x and min of t.y): the box is read off them.
+template <int CL, bool CULL_BACK>
+__device__ __forceinline__ void raster_boxed(uint2 pa, uint2 pb, uint2 pc, unsigned mx, unsigned mn, int *slab,
+                                             const VisParams &p, cg::cluster_group &cluster)
+{
+    if (pa.x == OUTSIDE || pb.x == OUTSIDE || pc.x == OUTSIDE) return;
+    raster_span<CL, CULL_BACK>(pa.x & 0xffff, pa.x >> 16, (int)pa.y, pb.x & 0xffff, pb.x >> 16, (int)pb.y,
+                               pc.x & 0xffff, pc.x >> 16, (int)pc.y, (int)(mn & 0xffff) - VB, (int)(mx & 0xffff) - VB,
+                               (int)(mn >> 16) - VB, (int)(mx >> 16) - VB, slab, p, cluster);
+}
+
+// Coverage and depth of one triangle over the pixel-centre box [i0, i1] x
+// [j0, j1] (non-empty, inside the map): the minimum into the owning slab.
+template <int CL, bool CULL_BACK>
+__device__ __forceinline__ void raster_span(int ax, int ay, int az, int bx, int by, int bz, int cx, int cy, int cz,
+                                            int i0, int i1, int j0, int j1, int *slab, const VisParams &p,
+                                            cg::cluster_group &cluster)
+{
+    const int R = p.R;
     int area = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
     if (CULL_BACK) {
         if (area <= 0) return;  // faces away from the light (outward winding)
@@ -309,7 +381,8 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
     if (BATCH) qv += (size_t)blockIdx.z * p.Nv;
     const int R = p.R;
     const int slab_elems = p.rows_per_cta * R;
-    uint2 *vcache = reinterpret_cast<uint2 *>(slab + slab_elems);
+    uint2 *vcache = reinterpret_cast<uint2 *>(slab + slab_elems);  // packed projection (X | Y << 16, Z)
+    uint2 *vbox = vcache + VIS_VCAP;                                // box-test words (box_words)
 
     for (int i = threadIdx.x; i < slab_elems; i += blockDim.x) slab[i] = EMPTY_DEPTH;
 
@@ -365,8 +438,11 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
         const bool cached = nv > 0 && nv <= VIS_VCAP;
         if (cached) {
 #pragma unroll 4
-            for (int i = threadIdx.x; i < nv; i += VIS_THREADS)
-                vcache[i] = pack_proj(project_vertex(__ldg(qv + v0 + i), B, p));
+            for (int i = threadIdx.x; i < nv; i += VIS_THREADS) {
+                const Proj q = project_vertex(__ldg(qv + v0 + i), B, p);
+                vcache[i] = pack_proj(q);
+                vbox[i] = box_words(q);
+            }
         }
         if (threadIdx.x == 0) s_next = taken;
         __syncthreads();
@@ -378,17 +454,21 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
             for (int t = 0; t < VIS_TPT; ++t) {
                 const int f = chunk * VIS_CHUNK + t * VIS_THREADS + threadIdx.x;
                 if (f >= p.F) continue;
-                uint2 pa, pb, pc;
                 if (cached) {
-                    pa = vcache[cur[t] & 1023];
-                    pb = vcache[(cur[t] >> 10) & 1023];
-                    pc = vcache[(cur[t] >> 20) & 1023];
+                    // most triangles have no pixel centre in their box: decide
+                    // that on the box words alone
+                    const int oa = cur[t] & 1023, ob = (cur[t] >> 10) & 1023, oc = (cur[t] >> 20) & 1023;
+                    const uint2 ta = vbox[oa], tb = vbox[ob], tc = vbox[oc];
+                    const unsigned mx = max_s16x2(max_s16x2(ta.x, tb.x), tc.x);
+                    const unsigned mn = min_s16x2(min_s16x2(ta.y, tb.y), tc.y);
+                    if (!box_has_centre(mx, mn)) continue;
+                    raster_boxed<CL, CULL_BACK>(vcache[oa], vcache[ob], vcache[oc], mx, mn, slab, p, cluster);
                 } else {
-                    pa = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f)), B, p));
-                    pb = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f + 1)), B, p));
-                    pc = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f + 2)), B, p));
+                    const uint2 pa = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f)), B, p));
+                    const uint2 pb = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f + 1)), B, p));
+                    const uint2 pc = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f + 2)), B, p));
+                    raster_triangle<CL, CULL_BACK>(pa, pb, pc, slab, p, cluster);
                 }
-                raster_triangle<CL, CULL_BACK>(pa, pb, pc, slab, p, cluster);
             }
         }
         __syncthreads();  // the next chunk overwrites the cache (and s_next)
@@ -435,12 +515,29 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
 }
 
 // bits[v][ow] bit l = dirbits[src(32 ow + l)][v/32] bit (v%32), src = dmap or identity.
-// A block takes TR_VW consecutive vertex words; for TR_ROWS outputs (lights)
-// at a time it stages, per output, the source direction's TR_VW words (one
-// 32-byte sector) in shared memory; warp w then transposes word w by ballots
-// and every lane writes its vertex's words of the span, four per 16-byte store
-// when OW is a multiple of four.
-constexpr int TR_VW = 8, TR_ROWS = 512, TR_THREADS = 256;
+// A block takes TR_VW consecutive vertex words and TR_ROWS outputs (lights):
+// blockIdx.x the vertex words, blockIdx.y the outputs, blockIdx.z the pose of
+// a batch.  It stages, per output, the source direction's TR_VW words (one
+// 32-byte sector) in shared memory with all its loads in flight at once; warp
+// w then transposes the 32 x 32 bit blocks of vertex word w by five
+// shuffle-xor exchange rounds (a lane starts with one output's 32 vertex bits
+// and ends with its vertex's 32 output bits), and every lane writes its
+// vertex's TR_ROWS / 32 words, in one 16-byte store when OW is a multiple of
+// four.
+constexpr int TR_VW = 8, TR_ROWS = 128, TR_THREADS = 256;
+constexpr int TR_PER = TR_ROWS * TR_VW / TR_THREADS;  // staged words per thread
+
+__device__ __forceinline__ uint32_t transpose32_lane(uint32_t x, int lane)
+{
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) {
+        const uint32_t m = j == 16 ? 0x0000ffffu : j == 8 ? 0x00ff00ffu : j == 4 ? 0x0f0f0f0fu
+                         : j == 2 ? 0x33333333u : 0x55555555u;
+        const uint32_t t = __shfl_xor_sync(0xffffffffu, x, j);
+        x = (lane & j) ? ((x & ~m) | ((t & ~m) >> j)) : ((x & m) | ((t & m) << j));
+    }
+    return x;
+}
 
 __global__ void __launch_bounds__(TR_THREADS)
 vis_transpose_kernel(const uint32_t *__restrict__ dirbits, int NW, int Nv, int D, int nout, int OW,
@@ -448,53 +545,47 @@ vis_transpose_kernel(const uint32_t *__restrict__ dirbits, int NW, int Nv, int D
 {
     __shared__ uint32_t tile[TR_ROWS][TR_VW + 1];  // padded: a column read is conflict-free
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    dirbits += (size_t)blockIdx.y * D * NW;  // pose blockIdx.y of a batch
-    bits += (size_t)blockIdx.y * Nv * OW;
-    const bool vec = (OW & 3) == 0 && (reinterpret_cast<uintptr_t>(bits) & 15) == 0;
-    for (int vw0 = blockIdx.x * TR_VW; vw0 < NW; vw0 += gridDim.x * TR_VW) {
-        const int vw = vw0 + warp, v = vw * 32 + lane;
-        for (int k0 = 0; k0 < OW * 32; k0 += TR_ROWS) {
-            __syncthreads();  // the previous span's tile is consumed
-            for (int i = threadIdx.x; i < TR_ROWS * TR_VW; i += TR_THREADS) {
-                const int r = i / TR_VW, c = i % TR_VW, k = k0 + r;
-                uint32_t word = 0;
-                if (k < nout && vw0 + c < NW) {
-                    const int dsrc = dmap ? __ldg(dmap + k) : k;
-                    if ((unsigned)dsrc >= (unsigned)D) {
-                        if (c == 0) av_report(status, AVATAR_ERR_INDEX);
-                    } else {
-                        word = __ldg(dirbits + (size_t)dsrc * NW + vw0 + c);
-                    }
-                }
-                tile[r][c] = word;
-            }
-            __syncthreads();
-            if (vw >= NW) continue;
-            const int ow0 = k0 / 32, nspan = min(TR_ROWS / 32, OW - ow0);
-            for (int j4 = 0; j4 < nspan; j4 += 4) {
-                uint32_t out[4] = {0u, 0u, 0u, 0u};
+    dirbits += (size_t)blockIdx.z * D * NW;  // pose blockIdx.z of a batch
+    bits += (size_t)blockIdx.z * Nv * OW;
+    const int vw0 = blockIdx.x * TR_VW, k0 = blockIdx.y * TR_ROWS;
+    int dsrc[TR_PER];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (j4 + q >= nspan) break;  // warp-uniform
-                    const uint32_t src = tile[(j4 + q) * 32 + lane][warp];
+    for (int u = 0; u < TR_PER; ++u) {
+        const int k = k0 + (threadIdx.x + u * TR_THREADS) / TR_VW;
+        dsrc[u] = k < nout ? (dmap ? __ldg(dmap + k) : k) : D;   // D: no output there (a zero word)
+    }
+    uint32_t word[TR_PER];
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const uint32_t word = __ballot_sync(0xffffffffu, (src >> i) & 1u);
-                        if (lane == i) out[q] = word;
-                    }
-                }
-                if (v < Nv) {
-                    uint32_t *dst = bits + (size_t)v * OW + ow0 + j4;
-                    if (vec) {
-                        *reinterpret_cast<uint4 *>(dst) = make_uint4(out[0], out[1], out[2], out[3]);
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            if (j4 + q < nspan) dst[q] = out[q];
-                    }
-                }
-            }
+    for (int u = 0; u < TR_PER; ++u) {
+        const int i = threadIdx.x + u * TR_THREADS, c = i % TR_VW, k = k0 + i / TR_VW;
+        word[u] = 0u;
+        if ((unsigned)dsrc[u] < (unsigned)D) {
+            if (vw0 + c < NW) word[u] = __ldg(dirbits + (size_t)dsrc[u] * NW + vw0 + c);
+        } else if (k < nout && c == 0) {
+            av_report(status, AVATAR_ERR_INDEX);
         }
+    }
+#pragma unroll
+    for (int u = 0; u < TR_PER; ++u) {
+        const int i = threadIdx.x + u * TR_THREADS;
+        tile[i / TR_VW][i % TR_VW] = word[u];
+    }
+    __syncthreads();
+    const int vw = vw0 + warp, v = vw * 32 + lane;
+    if (vw >= NW) return;
+    const int ow0 = k0 / 32, nspan = min(TR_ROWS / 32, OW - ow0);
+    uint32_t out[TR_ROWS / 32];
+#pragma unroll
+    for (int q = 0; q < TR_ROWS / 32; ++q)
+        out[q] = q < nspan ? transpose32_lane(tile[q * 32 + lane][warp], lane) : 0u;  // nspan is warp-uniform
+    if (v >= Nv) return;
+    uint32_t *dst = bits + (size_t)v * OW + ow0;
+    if (nspan == 4 && (OW & 3) == 0 && (reinterpret_cast<uintptr_t>(bits) & 15) == 0) {
+        *reinterpret_cast<uint4 *>(dst) = make_uint4(out[0], out[1], out[2], out[3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < TR_ROWS / 32; ++q)
+            if (q < nspan) dst[q] = out[q];
     }
 }
 
@@ -833,12 +924,13 @@ int vis_run(avatar_ctx *ctx, const avatar_vis_args *a, int B, void *ws, size_t w
     p.M = (int)M;
     p.biasq = (int)biasq;
     int CL = ctx->tune[AVATAR_TUNE_VIS_CLUSTER] ? ctx->tune[AVATAR_TUNE_VIS_CLUSTER] : cluster_size_for(a->R);
-    while (CL < 8 && (size_t)(a->R / CL) * a->R * sizeof(int) + (size_t)VIS_VCAP * sizeof(uint2) >
+    // dynamic shared memory: the depth slab and the two vertex-cache arrays
+    while (CL < 8 && (size_t)(a->R / CL) * a->R * sizeof(int) + (size_t)2 * VIS_VCAP * sizeof(uint2) >
                          (size_t)ctx->max_smem_optin)
         CL <<= 1;
     p.rows_per_cta = a->R / CL;
     p.inv_rows = ((1 << 20) + p.rows_per_cta - 1) / p.rows_per_cta;
-    size_t smem = (size_t)p.rows_per_cta * a->R * sizeof(int) + (size_t)VIS_VCAP * sizeof(uint2);
+    size_t smem = (size_t)p.rows_per_cta * a->R * sizeof(int) + (size_t)2 * VIS_VCAP * sizeof(uint2);
 
     int qgrid = (int)((a->Nv + 255) / 256);
     if (qgrid > ctx->sm_count * 8) qgrid = ctx->sm_count * 8;
@@ -868,9 +960,8 @@ int vis_run(avatar_ctx *ctx, const avatar_vis_args *a, int B, void *ws, size_t w
 
     int nout = a->dmap ? a->NL : a->D;
     int OW = (nout + 31) / 32;
-    long tgrid = ((long)p.NW + TR_VW - 1) / TR_VW;
-    if (tgrid > (long)ctx->sm_count * 8) tgrid = (long)ctx->sm_count * 8;
-    vis_transpose_kernel<<<dim3((int)tgrid, B), TR_THREADS, 0, st>>>(w.dirbits, p.NW, a->Nv, a->D, nout, OW, a->dmap,
+    const int tgrid = (p.NW + TR_VW - 1) / TR_VW, tspans = (nout + TR_ROWS - 1) / TR_ROWS;
+    vis_transpose_kernel<<<dim3(tgrid, tspans, B), TR_THREADS, 0, st>>>(w.dirbits, p.NW, a->Nv, a->D, nout, OW, a->dmap,
                                                                a->bits, a->status);
     AV_CHECK_LAUNCH();
     return AVATAR_OK;
@@ -1023,9 +1114,8 @@ extern "C" int avatar_visibility_soft(avatar_ctx *ctx, const avatar_vis_soft_arg
     // V vertex-major in direction order, then median, median, mean
     const int OW = b.D / 32;
     uint32_t *vm = b.bits ? b.bits : w.vm;
-    long tgrid = ((long)p.NW + TR_VW - 1) / TR_VW;
-    if (tgrid > (long)ctx->sm_count * 8) tgrid = (long)ctx->sm_count * 8;
-    vis_transpose_kernel<<<dim3((int)tgrid, 1), TR_THREADS, 0, st>>>(w.dirbits, p.NW, b.Nv, b.D, b.D, OW, nullptr, vm,
+    const int tgrid = (p.NW + TR_VW - 1) / TR_VW, tspans = (b.D + TR_ROWS - 1) / TR_ROWS;
+    vis_transpose_kernel<<<dim3(tgrid, tspans, 1), TR_THREADS, 0, st>>>(w.dirbits, p.NW, b.Nv, b.D, b.D, OW, nullptr, vm,
                                                                b.status);
     long items = (long)b.Nv * OW;
     int fgrid = (int)std::min<long>((items + 255) / 256, (long)ctx->sm_count * 16);
