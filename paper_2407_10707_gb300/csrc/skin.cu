@@ -12,8 +12,6 @@
 //                    and normal.
 // Backward: per-Gaussian adjoint with atomic scatter into per-vertex
 // accumulators, then a per-vertex pass turning dA_v into dw_v.
-#include <cuda.h>
-
 #include "batch_internal.h"
 #include "common.cuh"
 
@@ -203,18 +201,28 @@ struct GaussState {
     float a[3], r, p, n[3], dx[3];
 };
 
-// Eq. 1 over the K neighbour records: distances and normalised weights from
-// the canonical positions, then the weighted sums of every interpolated
-// attribute and of the blended transform.  rec_of(j) returns neighbour j's
-// record (global or shared memory); the arithmetic and its order do not
-// depend on where the records come from.
-template <int K, class RecOf>
-__device__ __forceinline__ void gauss_interpolate(RecOf rec_of, GaussState<K> &s)
+template <int K>
+__device__ __forceinline__ bool gauss_gather(const avatar_skin_args &a, const VertexRec *__restrict__ rec,
+                                             int g, GaussState<K> &s)
 {
+    const int G = a.G;
+    s.x[0] = a.xg[g];
+    s.x[1] = a.xg[G + g];
+    s.x[2] = a.xg[2 * G + g];
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        int v = a.knn[j * G + g];
+        if (v < 0 || v >= a.Nv) {
+            ok = false;
+            v = 0;
+        }
+        s.idx[j] = v;
+    }
     s.usum = 0.f;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-        float4 xr = rec_of(j)[3];
+        float4 xr = __ldg(&rec[s.idx[j]].xr);
         float ex = s.x[0] - xr.x, ey = s.x[1] - xr.y, ez = s.x[2] - xr.z;
         float d = sqrtf(ex * ex + ey * ey + ez * ez);
         s.dist[j] = d;
@@ -231,10 +239,10 @@ __device__ __forceinline__ void gauss_interpolate(RecOf rec_of, GaussState<K> &s
     s.n[0] = s.n[1] = s.n[2] = s.dx[0] = s.dx[1] = s.dx[2] = 0.f;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-        auto vr = rec_of(j);
+        const VertexRec *vr = rec + s.idx[j];
         float u = s.ub[j];
-        float4 a0 = vr[0], a1 = vr[1], a2 = vr[2];
-        float4 xr = vr[3], ap = vr[4], n0 = vr[5], d12 = vr[6];
+        float4 a0 = __ldg(&vr->a0), a1 = __ldg(&vr->a1), a2 = __ldg(&vr->a2);
+        float4 xr = __ldg(&vr->xr), ap = __ldg(&vr->ap), n0 = __ldg(&vr->nd0), d12 = __ldg(&vr->d12);
         s.A[0] = fmaf(u, a0.x, s.A[0]);
         s.A[1] = fmaf(u, a0.y, s.A[1]);
         s.A[2] = fmaf(u, a0.z, s.A[2]);
@@ -259,94 +267,7 @@ __device__ __forceinline__ void gauss_interpolate(RecOf rec_of, GaussState<K> &s
         s.dx[1] = fmaf(u, d12.x, s.dx[1]);
         s.dx[2] = fmaf(u, d12.y, s.dx[2]);
     }
-}
-
-// Read-only global view of a record as seven float4 (loaded through the
-// non-coherent path).
-struct GlobalRec {
-    const float4 *p;
-    __device__ __forceinline__ float4 operator[](int i) const { return __ldg(p + i); }
-};
-
-template <int K>
-__device__ __forceinline__ bool gauss_gather(const avatar_skin_args &a, const VertexRec *__restrict__ rec,
-                                             int g, GaussState<K> &s)
-{
-    const int G = a.G;
-    s.x[0] = a.xg[g];
-    s.x[1] = a.xg[G + g];
-    s.x[2] = a.xg[2 * G + g];
-    bool ok = true;
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-        int v = a.knn[j * G + g];
-        if (v < 0 || v >= a.Nv) {
-            ok = false;
-            v = 0;
-        }
-        s.idx[j] = v;
-    }
-    gauss_interpolate<K>([&](int j) { return GlobalRec{reinterpret_cast<const float4 *>(rec + s.idx[j])}; }, s);
     return ok;
-}
-
-// Posed mean, covariance and normal of Gaussian g from its interpolated
-// state, and (pose 0 of a batch) the interpolated materials and weights.
-template <int K>
-__device__ __forceinline__ void gauss_finish(const avatar_skin_args &a, const GaussState<K> &s, int g, size_t SG,
-                                             bool shared_out)
-{
-    const int G = a.G;
-    const float *A = s.A;
-    float xb0 = s.x[0] + s.dx[0], xb1 = s.x[1] + s.dx[1], xb2 = s.x[2] + s.dx[2];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-        a.xd[i * SG + g] = fmaf(A[4 * i], xb0, fmaf(A[4 * i + 1], xb1, fmaf(A[4 * i + 2], xb2, A[4 * i + 3])));
-    // covariance
-    const int dt = a.attr_dtype;
-    float qw = ld_attr(a.quat, g, dt), qx = ld_attr(a.quat, (size_t)G + g, dt),
-          qy = ld_attr(a.quat, (size_t)2 * G + g, dt), qz = ld_attr(a.quat, (size_t)3 * G + g, dt);
-    float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-    float R[9];
-    quat_to_rot(qw * qn, qx * qn, qy * qn, qz * qn, R);
-    float s2[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) s2[i] = expf(2.f * ld_attr(a.logscale, (size_t)i * G + g, dt));
-    // MR = M * R * diag(s):  cov = (MR)(MR)^T
-    float MR[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-            MR[3 * i + k] = A[4 * i] * R[k] + A[4 * i + 1] * R[3 + k] + A[4 * i + 2] * R[6 + k];
-    float c[6];
-    const int ii[6] = {0, 0, 0, 1, 1, 2}, jj[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-    for (int e = 0; e < 6; ++e) {
-        int i = ii[e], j = jj[e];
-        c[e] = MR[3 * i] * MR[3 * j] * s2[0] + MR[3 * i + 1] * MR[3 * j + 1] * s2[1] +
-               MR[3 * i + 2] * MR[3 * j + 2] * s2[2];
-    }
-#pragma unroll
-    for (int e = 0; e < 6; ++e) a.cov[e * SG + g] = c[e];
-    // normal
-    float nl = rsqrtf(s.n[0] * s.n[0] + s.n[1] * s.n[1] + s.n[2] * s.n[2]);
-    float n0 = s.n[0] * nl, n1 = s.n[1] * nl, n2 = s.n[2] * nl;
-    float m0 = A[0] * n0 + A[1] * n1 + A[2] * n2;
-    float m1 = A[4] * n0 + A[5] * n1 + A[6] * n2;
-    float m2 = A[8] * n0 + A[9] * n1 + A[10] * n2;
-    float ml = rsqrtf(m0 * m0 + m1 * m1 + m2 * m2);
-    a.nd[g] = m0 * ml;
-    a.nd[SG + g] = m1 * ml;
-    a.nd[2 * SG + g] = m2 * ml;
-    if (!shared_out) return;
-    a.ag[g] = s.a[0];
-    a.ag[G + g] = s.a[1];
-    a.ag[2 * G + g] = s.a[2];
-    a.rg[g] = s.r;
-    a.pg[g] = s.p;
-#pragma unroll
-    for (int j = 0; j < K; ++j) a.ubar[j * G + g] = s.ub[j];
 }
 
 template <int K>
@@ -362,140 +283,60 @@ skin_gaussians_kernel(avatar_skin_args a, const VertexRec *__restrict__ rec)
     a.cov += (size_t)pb * G;
     a.nd += (size_t)pb * G;
     rec += (size_t)pb * a.Nv;
+    const bool shared_out = pb == 0;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
         GaussState<K> s;
         if (!gauss_gather<K>(a, rec, g, s)) av_report(a.status, AVATAR_ERR_INDEX);
-        gauss_finish<K>(a, s, g, SG, pb == 0);
-    }
-}
-
-// ---------------------------------------------------------------- forward, K <= 4, records by TMA
-// One warp takes 32 consecutive Gaussians.  Their K x 32 neighbour records
-// come into the warp's shared memory by tensor-memory-access gathers: lane
-// l issues one tile::gather4 of the rows of neighbour j = l / 8 of Gaussians
-// 4q .. 4q + 3, q = l % 8 (112-byte rows, no swizzle), into its own 512-byte
-// slot (a tensor copy's shared destination is 128-byte aligned), so
-// neighbour j of the warp's Gaussian i sits at 4096 j + 512 (i / 4) +
-// 112 (i % 4) bytes.  The 7 x 16-byte row stride leaves the lanes' float4
-// reads of their own rows at most 2-way bank conflicted.  The gathers
-// complete on one mbarrier per warp (expected bytes, bounded wait); the next
-// round's neighbour indices are loaded while they fly.  Same arithmetic as
-// skin_gaussians_kernel, same results.
-constexpr int ST_WARPS = 4;
-constexpr int REC_FLOATS = (int)(sizeof(VertexRec) / sizeof(float));   // 28
-constexpr int ST_SLOT = 512;                                            // bytes per gather4 (4 rows + pad)
-constexpr int ST_WARP_BYTES = 4 * 8 * ST_SLOT;                          // 4 neighbours x 8 slots
-static_assert(sizeof(VertexRec) == 112 && 4 * sizeof(VertexRec) <= ST_SLOT, "gather rows are 112-byte records");
-
-__device__ __forceinline__ int st_row_offset(int j, int i) { return 4096 * j + ST_SLOT * (i >> 2) + 112 * (i & 3); }
-constexpr int SKIN_WAIT_LIMIT = 1 << 22;
-
-__device__ __forceinline__ uint32_t st_smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Polls the mbarrier phase with the given parity, at most `limit` times.
-__device__ __forceinline__ bool st_wait(uint32_t bar, uint32_t parity, int limit)
-{
-    for (int it = 0; it < limit; ++it) {
-        uint32_t done;
-        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-                     : "=r"(done)
-                     : "r"(bar), "r"(parity)
-                     : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-// Shared-memory view of a gathered record.
-struct SharedRec {
-    const float4 *p;
-    __device__ __forceinline__ float4 operator[](int i) const { return p[i]; }
-};
-
-template <int K>
-__global__ void __launch_bounds__(ST_WARPS * 32)
-skin_gaussians_tma_kernel(avatar_skin_args a, const __grid_constant__ CUtensorMap tmap)
-{
-    extern __shared__ unsigned char st_raw[];  // ST_WARPS x ST_WARP_BYTES after rounding up to 128 bytes
-    __shared__ __align__(8) uint64_t st_bar[ST_WARPS];
-    __shared__ int st_idx[ST_WARPS][4][32];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char *rows = reinterpret_cast<unsigned char *>(((uintptr_t)st_raw + 127) & ~(uintptr_t)127) +
-                          (size_t)warp * ST_WARP_BYTES;
-    const uint32_t bar = st_smem_u32(&st_bar[warp]);
-    if (lane == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncwarp();
-    const int G = a.G, pb = blockIdx.y;
-    const size_t SG = (size_t)gridDim.y * G;
-    a.xd += (size_t)pb * G;
-    a.cov += (size_t)pb * G;
-    a.nd += (size_t)pb * G;
-    const int rowoff = pb * a.Nv;  // this pose's records in the tensor
-    const int stride = gridDim.x * ST_WARPS * 32;
-    int base = (blockIdx.x * ST_WARPS + warp) * 32;
-    // neighbour indices of this lane's Gaussian (row 0 for a bad index, reported)
-    auto load_idx = [&](int b, int (&idx)[K]) {
-        const int g = b + lane;
+        const float *A = s.A;
+        float xb0 = s.x[0] + s.dx[0], xb1 = s.x[1] + s.dx[1], xb2 = s.x[2] + s.dx[2];
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
-            int v = g < G ? __ldg(a.knn + (size_t)j * G + g) : 0;
-            if ((unsigned)v >= (unsigned)a.Nv) {
-                if (g < G) av_report(a.status, AVATAR_ERR_INDEX);
-                v = 0;
-            }
-            idx[j] = v;
-        }
-    };
-    int idx[K];
-    if (base < G) load_idx(base, idx);
-    uint32_t parity = 0;
-    for (; base < G; base += stride) {
+        for (int i = 0; i < 3; ++i)
+            a.xd[i * SG + g] = fmaf(A[4 * i], xb0, fmaf(A[4 * i + 1], xb1, fmaf(A[4 * i + 2], xb2, A[4 * i + 3])));
+        // covariance
+        const int dt = a.attr_dtype;
+        float qw = ld_attr(a.quat, g, dt), qx = ld_attr(a.quat, (size_t)G + g, dt),
+              qy = ld_attr(a.quat, (size_t)2 * G + g, dt), qz = ld_attr(a.quat, (size_t)3 * G + g, dt);
+        float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+        float R[9];
+        quat_to_rot(qw * qn, qx * qn, qy * qn, qz * qn, R);
+        float s2[3];
 #pragma unroll
-        for (int j = 0; j < K; ++j) st_idx[warp][j][lane] = idx[j];
-        __syncwarp();
-        if (lane == 0)
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                         "r"((uint32_t)(K * 32 * sizeof(VertexRec)))
-                         : "memory");
-        {
-            const int j = lane >> 3, q = lane & 7;
-            if (j < K) {
-                // the rows this gather overwrites were last read by the generic proxy
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                const int r0 = st_idx[warp][j][4 * q] + rowoff, r1 = st_idx[warp][j][4 * q + 1] + rowoff;
-                const int r2 = st_idx[warp][j][4 * q + 2] + rowoff, r3 = st_idx[warp][j][4 * q + 3] + rowoff;
-                asm volatile(
-                    "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes "
-                    "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(st_smem_u32(rows + st_row_offset(j, 4 * q))),
-                    "l"(&tmap), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(bar)
-                    : "memory");
-            }
+        for (int i = 0; i < 3; ++i) s2[i] = expf(2.f * ld_attr(a.logscale, (size_t)i * G + g, dt));
+        // MR = M * R * diag(s):  cov = (MR)(MR)^T
+        float MR[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                MR[3 * i + k] = A[4 * i] * R[k] + A[4 * i + 1] * R[3 + k] + A[4 * i + 2] * R[6 + k];
+        float c[6];
+        const int ii[6] = {0, 0, 0, 1, 1, 2}, jj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+        for (int e = 0; e < 6; ++e) {
+            int i = ii[e], j = jj[e];
+            c[e] = MR[3 * i] * MR[3 * j] * s2[0] + MR[3 * i + 1] * MR[3 * j + 1] * s2[1] +
+                   MR[3 * i + 2] * MR[3 * j + 2] * s2[2];
         }
-        const int g = base + lane;
-        GaussState<K> s;
-        if (g < G) {
-            s.x[0] = a.xg[g];
-            s.x[1] = a.xg[G + g];
-            s.x[2] = a.xg[2 * G + g];
-        }
-        if (base + stride < G) load_idx(base + stride, idx);  // the next round's, in flight meanwhile
-        if (!__all_sync(0xffffffffu, st_wait(bar, parity, SKIN_WAIT_LIMIT))) {
-            // give the gathers a second bounded wait before leaving (they write this warp's rows)
-            av_report(a.status, AVATAR_ERR_TIMEOUT);
-            st_wait(bar, parity, SKIN_WAIT_LIMIT);
-            return;
-        }
-        parity ^= 1u;
-        if (g < G) {
-            gauss_interpolate<K>(
-                [&](int j) { return SharedRec{reinterpret_cast<const float4 *>(rows + st_row_offset(j, lane))}; },
-                s);
-            gauss_finish<K>(a, s, g, SG, pb == 0);
-        }
-        __syncwarp();  // every lane is done with the rows and indices before they are reused
+#pragma unroll
+        for (int e = 0; e < 6; ++e) a.cov[e * SG + g] = c[e];
+        // normal
+        float nl = rsqrtf(s.n[0] * s.n[0] + s.n[1] * s.n[1] + s.n[2] * s.n[2]);
+        float n0 = s.n[0] * nl, n1 = s.n[1] * nl, n2 = s.n[2] * nl;
+        float m0 = A[0] * n0 + A[1] * n1 + A[2] * n2;
+        float m1 = A[4] * n0 + A[5] * n1 + A[6] * n2;
+        float m2 = A[8] * n0 + A[9] * n1 + A[10] * n2;
+        float ml = rsqrtf(m0 * m0 + m1 * m1 + m2 * m2);
+        a.nd[g] = m0 * ml;
+        a.nd[SG + g] = m1 * ml;
+        a.nd[2 * SG + g] = m2 * ml;
+        if (!shared_out) continue;
+        a.ag[g] = s.a[0];
+        a.ag[G + g] = s.a[1];
+        a.ag[2 * G + g] = s.a[2];
+        a.rg[g] = s.r;
+        a.pg[g] = s.p;
+#pragma unroll
+        for (int j = 0; j < K; ++j) a.ubar[j * G + g] = s.ub[j];
     }
 }
 
@@ -754,67 +595,6 @@ skin_vertices_backward_kernel(avatar_skin_args a, avatar_skin_grads gr, const fl
     }
 }
 
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
-// to the driver library); NULL if the driver does not provide it.
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-EncodeTiledFn encode_tiled()
-{
-    static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)p;
-        else
-            (void)cudaGetLastError();
-    }
-    return fn;
-}
-
-// The records [rows][28 floats] as a 2-D tensor whose boxes are one whole
-// record (the row a gather4 fetches).  False if the driver cannot encode it.
-bool record_tensor_map(const VertexRec *rec, long rows, CUtensorMap *out)
-{
-    EncodeTiledFn enc = encode_tiled();
-    if (!enc || rows < 1 || rows > 0x7fffffffL || (((uintptr_t)rec) & 15)) return false;
-    const cuuint64_t dims[2] = {(cuuint64_t)REC_FLOATS, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)sizeof(VertexRec)};
-    const cuuint32_t box[2] = {(cuuint32_t)REC_FLOATS, 1u};
-    const cuuint32_t estr[2] = {1u, 1u};
-    return enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)rec, dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-constexpr size_t ST_SMEM = (size_t)ST_WARPS * ST_WARP_BYTES + 128;
-
-// Forward Gaussian skinning with TMA-gathered records (K <= 4); false if
-// the tensor map or the launch setup is unavailable (the caller then uses
-// skin_gaussians_kernel).
-template <int K>
-bool launch_gauss_fwd_tma(const avatar_ctx *ctx, const avatar_skin_args &a, const VertexRec *rec, int B,
-                          cudaStream_t st)
-{
-    CUtensorMap tm;
-    if (!record_tensor_map(rec, (long)B * a.Nv, &tm)) return false;
-    if (cudaFuncSetAttribute(skin_gaussians_tma_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)ST_SMEM) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return false;
-    }
-    long blocks = ((long)a.G + ST_WARPS * 32 - 1) / (ST_WARPS * 32);
-    const long cap = (long)ctx->sm_count * 3;   // three 64 KB blocks per SM
-    if (blocks > cap) blocks = cap;
-    skin_gaussians_tma_kernel<K><<<dim3((unsigned)blocks, B), ST_WARPS * 32, ST_SMEM, st>>>(a, tm);
-    return true;
-}
-
 template <int K>
 void launch_gauss_fwd(const avatar_skin_args &a, const VertexRec *rec, int B, int grid, cudaStream_t st)
 {
@@ -867,18 +647,6 @@ int skin_run(avatar_ctx *ctx, const avatar_skin_args *a, int B, void *ws, size_t
     skin_vertices_kernel<<<dim3(grid_for(ctx, a->Nv, SKIN_THREADS), B), SKIN_THREADS, 0, st>>>(*a, rec);
     AV_CHECK_LAUNCH();
     if (a->G > 0) {
-        bool done = false;
-        switch (a->K) {
-            case 1: done = launch_gauss_fwd_tma<1>(ctx, *a, rec, B, st); break;
-            case 2: done = launch_gauss_fwd_tma<2>(ctx, *a, rec, B, st); break;
-            case 3: done = launch_gauss_fwd_tma<3>(ctx, *a, rec, B, st); break;
-            case 4: done = launch_gauss_fwd_tma<4>(ctx, *a, rec, B, st); break;
-            default: break;
-        }
-        if (done) {
-            AV_CHECK_LAUNCH();
-            return AVATAR_OK;
-        }
         int grid = grid_for(ctx, a->G, SKIN_THREADS);
         switch (a->K) {
             case 1: launch_gauss_fwd<1>(*a, rec, B, grid, st); break;

@@ -135,55 +135,6 @@ __device__ __forceinline__ int floor_div_i32(int num, int den)
     return q;
 }
 
-// Box-test words of a projected vertex inside the window: the last pixel
-// centre at or before its coordinate and the first at or after it, per axis,
-// biased by VB so both stay positive 16-bit halves:
-//   t.x = (floor((X - 8) / 16) + VB) | (floor((Y - 8) / 16) + VB) << 16
-//   t.y = ( ceil((X - 8) / 16) + VB) | ( ceil((Y - 8) / 16) + VB) << 16
-// A triangle's pixel-centre box [max(0, min ceil), min(R - 1, max floor)] is
-// non-empty iff the halfwise max of its t.x is >= the halfwise min of its t.y
-// (inside the window ceil >= 0 and floor <= R - 1, so the clamps are void).
-// An outside vertex gets t.x = 0x7fff7fff: the test passes and the full
-// path, which skips triangles with an outside vertex, decides.
-constexpr int VB = 0x100;
-
-__device__ __forceinline__ uint2 box_words(const Proj &q)
-{
-    if (!q.in) return make_uint2(0x7fff7fffu, 0u);
-    const int ex = q.X - 8, ey = q.Y - 8;
-    const int fx = ex >> 4, fy = ey >> 4;  // floor (arithmetic shift)
-    const int cx = fx + ((ex & 15) != 0), cy = fy + ((ey & 15) != 0);
-    return make_uint2((unsigned)(fx + VB) | ((unsigned)(fy + VB) << 16),
-                      (unsigned)(cx + VB) | ((unsigned)(cy + VB) << 16));
-}
-
-__device__ __forceinline__ unsigned max_s16x2(unsigned a, unsigned b)
-{
-    unsigned d;
-    asm("max.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-    return d;
-}
-
-__device__ __forceinline__ unsigned min_s16x2(unsigned a, unsigned b)
-{
-    unsigned d;
-    asm("min.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-    return d;
-}
-
-// Both halves of mx >= the matching halves of mn (all halves in [0, 0x7fff]):
-// (0x8000 | mx_h) - mn_h never borrows out of its half and keeps bit 15 iff
-// mx_h >= mn_h.
-__device__ __forceinline__ bool box_has_centre(unsigned mx, unsigned mn)
-{
-    return (((mx | 0x80008000u) - mn) & 0x80008000u) == 0x80008000u;
-}
-
-template <int CL, bool CULL_BACK>
-__device__ __forceinline__ void raster_span(int ax, int ay, int az, int bx, int by, int bz, int cx, int cy, int cz,
-                                            int i0, int i1, int j0, int j1, int *slab, const VisParams &p,
-                                            cg::cluster_group &cluster);
-
 template <int CL, bool CULL_BACK>
 __device__ __forceinline__ void raster_triangle(uint2 pa, uint2 pb, uint2 pc, int *slab, const VisParams &p,
                                                 cg::cluster_group &cluster)
@@ -197,29 +148,6 @@ __device__ __forceinline__ void raster_triangle(uint2 pa, uint2 pb, uint2 pc, in
     int i0 = max(0, (min(ax, min(bx, cx)) + 7) >> 4), i1 = min(R - 1, (max(ax, max(bx, cx)) - 8) >> 4);
     int j0 = max(0, (min(ay, min(by, cy)) + 7) >> 4), j1 = min(R - 1, (max(ay, max(by, cy)) - 8) >> 4);
     if (i0 > i1 || j0 > j1) return;
-    raster_span<CL, CULL_BACK>(ax, ay, az, bx, by, bz, cx, cy, cz, i0, i1, j0, j1, slab, p, cluster);
-}
-
-// The same triangle when the box test already ran on its box words (mx, mn:
-// the halfwise max of t.x and min of t.y): the box is read off them.
-template <int CL, bool CULL_BACK>
-__device__ __forceinline__ void raster_boxed(uint2 pa, uint2 pb, uint2 pc, unsigned mx, unsigned mn, int *slab,
-                                             const VisParams &p, cg::cluster_group &cluster)
-{
-    if (pa.x == OUTSIDE || pb.x == OUTSIDE || pc.x == OUTSIDE) return;
-    raster_span<CL, CULL_BACK>(pa.x & 0xffff, pa.x >> 16, (int)pa.y, pb.x & 0xffff, pb.x >> 16, (int)pb.y,
-                               pc.x & 0xffff, pc.x >> 16, (int)pc.y, (int)(mn & 0xffff) - VB, (int)(mx & 0xffff) - VB,
-                               (int)(mn >> 16) - VB, (int)(mx >> 16) - VB, slab, p, cluster);
-}
-
-// Coverage and depth of one triangle over the pixel-centre box [i0, i1] x
-// [j0, j1] (non-empty, inside the map): the minimum into the owning slab.
-template <int CL, bool CULL_BACK>
-__device__ __forceinline__ void raster_span(int ax, int ay, int az, int bx, int by, int bz, int cx, int cy, int cz,
-                                            int i0, int i1, int j0, int j1, int *slab, const VisParams &p,
-                                            cg::cluster_group &cluster)
-{
-    const int R = p.R;
     int area = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
     if (CULL_BACK) {
         if (area <= 0) return;  // faces away from the light (outward winding)
@@ -262,6 +190,23 @@ __device__ __forceinline__ void raster_span(int ax, int ay, int az, int bx, int 
             atomicMin(dst + i, dep);
         }
     }
+}
+
+// True iff raster_triangle would touch the depth map at all: all three
+// vertices inside the window, non-degenerate (and facing the light with
+// CULL_BACK), and a pixel centre inside the bounding box.  The cull test
+// comes first: it needs only the area.
+template <bool CULL_BACK>
+__device__ __forceinline__ bool triangle_survives(uint2 pa, uint2 pb, uint2 pc, int R)
+{
+    if (pa.x == OUTSIDE || pb.x == OUTSIDE || pc.x == OUTSIDE) return false;
+    const int ax = pa.x & 0xffff, ay = pa.x >> 16, bx = pb.x & 0xffff, by = pb.x >> 16;
+    const int cx = pc.x & 0xffff, cy = pc.x >> 16;
+    const int area = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
+    if (CULL_BACK ? area <= 0 : area == 0) return false;
+    const int i0 = max(0, (min(ax, min(bx, cx)) + 7) >> 4), i1 = min(R - 1, (max(ax, max(bx, cx)) - 8) >> 4);
+    const int j0 = max(0, (min(ay, min(by, cy)) + 7) >> 4), j1 = min(R - 1, (max(ay, max(by, cy)) - 8) >> 4);
+    return i0 <= i1 && j0 <= j1;
 }
 
 // Second pass of the paper's visibility: true iff at some pixel the triangle
@@ -381,8 +326,7 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
     if (BATCH) qv += (size_t)blockIdx.z * p.Nv;
     const int R = p.R;
     const int slab_elems = p.rows_per_cta * R;
-    uint2 *vcache = reinterpret_cast<uint2 *>(slab + slab_elems);  // packed projection (X | Y << 16, Z)
-    uint2 *vbox = vcache + VIS_VCAP;                                // box-test words (box_words)
+    uint2 *vcache = reinterpret_cast<uint2 *>(slab + slab_elems);
 
     for (int i = threadIdx.x; i < slab_elems; i += blockDim.x) slab[i] = EMPTY_DEPTH;
 
@@ -438,37 +382,47 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
         const bool cached = nv > 0 && nv <= VIS_VCAP;
         if (cached) {
 #pragma unroll 4
-            for (int i = threadIdx.x; i < nv; i += VIS_THREADS) {
-                const Proj q = project_vertex(__ldg(qv + v0 + i), B, p);
-                vcache[i] = pack_proj(q);
-                vbox[i] = box_words(q);
-            }
+            for (int i = threadIdx.x; i < nv; i += VIS_THREADS)
+                vcache[i] = pack_proj(project_vertex(__ldg(qv + v0 + i), B, p));
         }
         if (threadIdx.x == 0) s_next = taken;
         __syncthreads();
         const int next = s_next;
         int nxt[VIS_TPT];
         if (next < nchunks) load_faces(next, nxt);
-        if (nv > 0) {
+        if (cached) {
+            // the thread's triangles that reach the depth map (most do not:
+            // back-facing, or no pixel centre in the box), then those alone,
+            // so the warp runs the coverage loop about max-over-lanes times
+            // instead of once per triangle slot; the map is a minimum, so the
+            // order does not matter
+            unsigned todo = 0u;
+#pragma unroll
+            for (int t = 0; t < VIS_TPT; ++t) {
+                const int f = chunk * VIS_CHUNK + t * VIS_THREADS + threadIdx.x;
+                if (f < p.F && triangle_survives<CULL_BACK>(vcache[cur[t] & 1023], vcache[(cur[t] >> 10) & 1023],
+                                                           vcache[(cur[t] >> 20) & 1023], R))
+                    todo |= 1u << t;
+            }
+            while (todo) {
+                const int t = __ffs(todo) - 1;
+                todo &= todo - 1u;
+                int c = cur[0];
+#pragma unroll
+                for (int u = 1; u < VIS_TPT; ++u)
+                    if (t == u) c = cur[u];
+                raster_triangle<CL, CULL_BACK>(vcache[c & 1023], vcache[(c >> 10) & 1023], vcache[(c >> 20) & 1023],
+                                               slab, p, cluster);
+            }
+        } else if (nv > 0) {
 #pragma unroll
             for (int t = 0; t < VIS_TPT; ++t) {
                 const int f = chunk * VIS_CHUNK + t * VIS_THREADS + threadIdx.x;
                 if (f >= p.F) continue;
-                if (cached) {
-                    // most triangles have no pixel centre in their box: decide
-                    // that on the box words alone
-                    const int oa = cur[t] & 1023, ob = (cur[t] >> 10) & 1023, oc = (cur[t] >> 20) & 1023;
-                    const uint2 ta = vbox[oa], tb = vbox[ob], tc = vbox[oc];
-                    const unsigned mx = max_s16x2(max_s16x2(ta.x, tb.x), tc.x);
-                    const unsigned mn = min_s16x2(min_s16x2(ta.y, tb.y), tc.y);
-                    if (!box_has_centre(mx, mn)) continue;
-                    raster_boxed<CL, CULL_BACK>(vcache[oa], vcache[ob], vcache[oc], mx, mn, slab, p, cluster);
-                } else {
-                    const uint2 pa = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f)), B, p));
-                    const uint2 pb = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f + 1)), B, p));
-                    const uint2 pc = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f + 2)), B, p));
-                    raster_triangle<CL, CULL_BACK>(pa, pb, pc, slab, p, cluster);
-                }
+                const uint2 pa = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f)), B, p));
+                const uint2 pb = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f + 1)), B, p));
+                const uint2 pc = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f + 2)), B, p));
+                raster_triangle<CL, CULL_BACK>(pa, pb, pc, slab, p, cluster);
             }
         }
         __syncthreads();  // the next chunk overwrites the cache (and s_next)
@@ -924,13 +878,12 @@ int vis_run(avatar_ctx *ctx, const avatar_vis_args *a, int B, void *ws, size_t w
     p.M = (int)M;
     p.biasq = (int)biasq;
     int CL = ctx->tune[AVATAR_TUNE_VIS_CLUSTER] ? ctx->tune[AVATAR_TUNE_VIS_CLUSTER] : cluster_size_for(a->R);
-    // dynamic shared memory: the depth slab and the two vertex-cache arrays
-    while (CL < 8 && (size_t)(a->R / CL) * a->R * sizeof(int) + (size_t)2 * VIS_VCAP * sizeof(uint2) >
+    while (CL < 8 && (size_t)(a->R / CL) * a->R * sizeof(int) + (size_t)VIS_VCAP * sizeof(uint2) >
                          (size_t)ctx->max_smem_optin)
         CL <<= 1;
     p.rows_per_cta = a->R / CL;
     p.inv_rows = ((1 << 20) + p.rows_per_cta - 1) / p.rows_per_cta;
-    size_t smem = (size_t)p.rows_per_cta * a->R * sizeof(int) + (size_t)2 * VIS_VCAP * sizeof(uint2);
+    size_t smem = (size_t)p.rows_per_cta * a->R * sizeof(int) + (size_t)VIS_VCAP * sizeof(uint2);
 
     int qgrid = (int)((a->Nv + 255) / 256);
     if (qgrid > ctx->sm_count * 8) qgrid = ctx->sm_count * 8;
