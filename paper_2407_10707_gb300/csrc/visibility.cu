@@ -192,23 +192,6 @@ __device__ __forceinline__ void raster_triangle(uint2 pa, uint2 pb, uint2 pc, in
     }
 }
 
-// True iff raster_triangle would touch the depth map at all: all three
-// vertices inside the window, non-degenerate (and facing the light with
-// CULL_BACK), and a pixel centre inside the bounding box.  The cull test
-// comes first: it needs only the area.
-template <bool CULL_BACK>
-__device__ __forceinline__ bool triangle_survives(uint2 pa, uint2 pb, uint2 pc, int R)
-{
-    if (pa.x == OUTSIDE || pb.x == OUTSIDE || pc.x == OUTSIDE) return false;
-    const int ax = pa.x & 0xffff, ay = pa.x >> 16, bx = pb.x & 0xffff, by = pb.x >> 16;
-    const int cx = pc.x & 0xffff, cy = pc.x >> 16;
-    const int area = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
-    if (CULL_BACK ? area <= 0 : area == 0) return false;
-    const int i0 = max(0, (min(ax, min(bx, cx)) + 7) >> 4), i1 = min(R - 1, (max(ax, max(bx, cx)) - 8) >> 4);
-    const int j0 = max(0, (min(ay, min(by, cy)) + 7) >> 4), j1 = min(R - 1, (max(ay, max(by, cy)) - 8) >> 4);
-    return i0 <= i1 && j0 <= j1;
-}
-
 // Second pass of the paper's visibility: true iff at some pixel the triangle
 // covers its depth (the same coverage and depth as raster_triangle) equals
 // the finished depth map's - the triangle appears in the image.  Stops at
@@ -390,38 +373,21 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
         const int next = s_next;
         int nxt[VIS_TPT];
         if (next < nchunks) load_faces(next, nxt);
-        if (cached) {
-            // the thread's triangles that reach the depth map (most do not:
-            // back-facing, or no pixel centre in the box), then those alone,
-            // so the warp runs the coverage loop about max-over-lanes times
-            // instead of once per triangle slot; the map is a minimum, so the
-            // order does not matter
-            unsigned todo = 0u;
-#pragma unroll
-            for (int t = 0; t < VIS_TPT; ++t) {
-                const int f = chunk * VIS_CHUNK + t * VIS_THREADS + threadIdx.x;
-                if (f < p.F && triangle_survives<CULL_BACK>(vcache[cur[t] & 1023], vcache[(cur[t] >> 10) & 1023],
-                                                           vcache[(cur[t] >> 20) & 1023], R))
-                    todo |= 1u << t;
-            }
-            while (todo) {
-                const int t = __ffs(todo) - 1;
-                todo &= todo - 1u;
-                int c = cur[0];
-#pragma unroll
-                for (int u = 1; u < VIS_TPT; ++u)
-                    if (t == u) c = cur[u];
-                raster_triangle<CL, CULL_BACK>(vcache[c & 1023], vcache[(c >> 10) & 1023], vcache[(c >> 20) & 1023],
-                                               slab, p, cluster);
-            }
-        } else if (nv > 0) {
+        if (nv > 0) {
 #pragma unroll
             for (int t = 0; t < VIS_TPT; ++t) {
                 const int f = chunk * VIS_CHUNK + t * VIS_THREADS + threadIdx.x;
                 if (f >= p.F) continue;
-                const uint2 pa = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f)), B, p));
-                const uint2 pb = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f + 1)), B, p));
-                const uint2 pc = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f + 2)), B, p));
+                uint2 pa, pb, pc;
+                if (cached) {
+                    pa = vcache[cur[t] & 1023];
+                    pb = vcache[(cur[t] >> 10) & 1023];
+                    pc = vcache[(cur[t] >> 20) & 1023];
+                } else {
+                    pa = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f)), B, p));
+                    pb = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f + 1)), B, p));
+                    pc = pack_proj(project_vertex(__ldg(qv + __ldg(faces + 3 * f + 2)), B, p));
+                }
                 raster_triangle<CL, CULL_BACK>(pa, pb, pc, slab, p, cluster);
             }
         }
