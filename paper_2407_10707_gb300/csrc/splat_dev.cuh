@@ -286,7 +286,9 @@ onesweep_kernel(const uint32_t *__restrict__ kin, const int32_t *__restrict__ vi
 {
     __shared__ int s_tile;
     __shared__ int s_wcnt[OS_WARPS][RADIX];  // running, then exclusive-over-warps digit counts
-    __shared__ int s_gbase[RADIX];
+    __shared__ int s_gbase[RADIX];           // global offset of digit d, less its offset within the tile
+    __shared__ uint32_t s_key[OS_TILE];      // the tile's keys and values in tile-sorted order
+    __shared__ int32_t s_val[OS_TILE];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(ticket, 1);
     for (int i = tid; i < OS_WARPS * RADIX; i += OS_THREADS) (&s_wcnt[0][0])[i] = 0;
@@ -371,18 +373,39 @@ onesweep_kernel(const uint32_t *__restrict__ kin, const int32_t *__restrict__ vi
             __syncthreads();
         }
         if (tile > 0) st_volatile(my, FLAG_INC | (unsigned)(prefix + sum));
-        // global base of digit d: exclusive scan of this pass's histogram
+        // global base of digit d (exclusive scan of this pass's histogram plus
+        // the earlier tiles' count) less its base within the tile (exclusive
+        // scan of the tile's counts), so a key at tile position j goes to
+        // s_gbase[d] + j
         int tot;
-        int gex = block_exclusive_scan(hist[d], tot);
-        s_gbase[d] = gex + prefix;
+        const int gex = block_exclusive_scan(hist[d], tot);
+        const int tex = block_exclusive_scan(sum, tot);
+        s_gbase[d] = gex + prefix - tex;
+        s_wcnt[0][d] = tex;  // every warp's exclusive offsets are read below before this row is
     }
     __syncthreads();
+    // stage the tile in tile-sorted order, then write each digit's run with
+    // consecutive threads on consecutive addresses
+    const int tile_n = min(OS_TILE, n - base);
+    {
+        int pos[OS_ITEMS];
 #pragma unroll
-    for (int i = 0; i < OS_ITEMS; ++i) {
-        if (dig[i] >= RADIX) continue;
-        int dst = s_gbase[dig[i]] + s_wcnt[warp][dig[i]] + rank[i];
-        kout[dst] = key[i];
-        vout[dst] = val[i];
+        for (int i = 0; i < OS_ITEMS; ++i)
+            pos[i] = dig[i] < RADIX ? s_wcnt[0][dig[i]] + (warp == 0 ? 0 : s_wcnt[warp][dig[i]]) + rank[i] : -1;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < OS_ITEMS; ++i)
+            if (pos[i] >= 0) {
+                s_key[pos[i]] = key[i];
+                s_val[pos[i]] = val[i];
+            }
+    }
+    __syncthreads();
+    for (int j = tid; j < tile_n; j += OS_THREADS) {
+        const uint32_t k = s_key[j];
+        const int dst = s_gbase[(k >> shift) & 255u] + j;
+        kout[dst] = k;
+        vout[dst] = s_val[j];
     }
 }
 
@@ -805,57 +828,86 @@ __device__ __forceinline__ void blend_backward_box(int2 rg, const int32_t *__res
                   (int)((unsigned)ra >> 16) <= by1;
         }
         unsigned hits = __ballot_sync(0xffffffffu, hit);
+        // hits are taken back to front, up to three at a time: each pixel's
+        // T and colour updates run in list order, and the three hits' nine
+        // gradient sums go through one 32-slot reduction (31 shuffles for
+        // three hits instead of 16 each) and one atomic instruction
         while (hits) {
-            const int sj = 31 - __clz(hits);
-            hits &= ~(1u << sj);
-            const int j = end - 32 + sj;
-            const float4 r1 = s1[b][sj];
-            const float4 r0 = s0[b][sj];
-            const float4 c = s2[b][sj];
-            float g_col0 = 0.f, g_col1 = 0.f, g_col2 = 0.f, g_op = 0.f, g_mx = 0.f, g_my = 0.f, g_ca = 0.f,
-                  g_cb = 0.f, g_cc = 0.f;
-            bool contrib = false;
+            int sjs[3];
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                if (j >= my_last[k]) continue;
-                float dx = fx[k] - r0.x, dy = fy[k] - r0.y;
-                float l2a = fmaf(fmaf(r0.z, dx, r0.w * dy), dx, fmaf(r1.x * dy, dy, r1.y));
-                if (l2a < LOG2_ALPHA_MIN) continue;
-                float raw = exp2f(l2a);
-                float alpha = fminf(0.99f, raw);
-                contrib = true;
-                T[k] = T[k] / (1.f - alpha);
-                float wgt = alpha * T[k];
-                g_col0 = fmaf(wgt, dC0[k], g_col0);
-                g_col1 = fmaf(wgt, dC1[k], g_col1);
-                g_col2 = fmaf(wgt, dC2[k], g_col2);
-                float dalpha = T[k] * ((c.x - acc0[k]) * dC0[k] + (c.y - acc1[k]) * dC1[k] + (c.z - acc2[k]) * dC2[k]);
-                acc0[k] = alpha * c.x + (1.f - alpha) * acc0[k];
-                acc1[k] = alpha * c.y + (1.f - alpha) * acc1[k];
-                acc2[k] = alpha * c.z + (1.f - alpha) * acc2[k];
-                if (raw < 0.99f) {
-                    float dpow = dalpha * raw;
-                    g_op += dpow;
-                    float ca = -2.f * LN2 * r0.z, cb = -LN2 * r0.w, cc = -2.f * LN2 * r1.x;
-                    g_mx = fmaf(dpow, ca * dx + cb * dy, g_mx);
-                    g_my = fmaf(dpow, cb * dx + cc * dy, g_my);
-                    g_ca = fmaf(-0.5f * dpow, dx * dx, g_ca);
-                    g_cb = fmaf(-dpow, dx * dy, g_cb);
-                    g_cc = fmaf(-0.5f * dpow, dy * dy, g_cc);
-                }
+            for (int h = 0; h < 3; ++h) {
+                sjs[h] = hits ? 31 - __clz(hits) : -1;
+                if (hits) hits &= ~(1u << sjs[h]);
             }
-            if (__any_sync(0xffffffffu, contrib)) {
-                const float v[16] = {g_col0, g_col1, g_col2, g_op, g_mx, g_my, g_ca, g_cb, g_cc,
-                                     0.f,    0.f,    0.f,    0.f,  0.f,  0.f,  0.f};
-                const float tot = warp_reduce_scatter16(v);
-                const int vi = lane >> 1;
-                if (!(lane & 1) && vi < 9) {
+            float v[32];
+            bool any[3];
+#pragma unroll
+            for (int h = 0; h < 3; ++h) {
+                float g_col0 = 0.f, g_col1 = 0.f, g_col2 = 0.f, g_op = 0.f, g_mx = 0.f, g_my = 0.f, g_ca = 0.f,
+                      g_cb = 0.f, g_cc = 0.f;
+                bool contrib = false;
+                const int sj = sjs[h];  // warp-uniform
+                if (sj >= 0) {
+                    const int j = end - 32 + sj;
+                    const float4 r1 = s1[b][sj];
+                    const float4 r0 = s0[b][sj];
+                    const float4 c = s2[b][sj];
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) {
+                        if (j >= my_last[k]) continue;
+                        float dx = fx[k] - r0.x, dy = fy[k] - r0.y;
+                        float l2a = fmaf(fmaf(r0.z, dx, r0.w * dy), dx, fmaf(r1.x * dy, dy, r1.y));
+                        if (l2a < LOG2_ALPHA_MIN) continue;
+                        float raw = exp2f(l2a);
+                        float alpha = fminf(0.99f, raw);
+                        contrib = true;
+                        T[k] = T[k] / (1.f - alpha);
+                        float wgt = alpha * T[k];
+                        g_col0 = fmaf(wgt, dC0[k], g_col0);
+                        g_col1 = fmaf(wgt, dC1[k], g_col1);
+                        g_col2 = fmaf(wgt, dC2[k], g_col2);
+                        float dalpha =
+                            T[k] * ((c.x - acc0[k]) * dC0[k] + (c.y - acc1[k]) * dC1[k] + (c.z - acc2[k]) * dC2[k]);
+                        acc0[k] = alpha * c.x + (1.f - alpha) * acc0[k];
+                        acc1[k] = alpha * c.y + (1.f - alpha) * acc1[k];
+                        acc2[k] = alpha * c.z + (1.f - alpha) * acc2[k];
+                        if (raw < 0.99f) {
+                            float dpow = dalpha * raw;
+                            g_op += dpow;
+                            float ca = -2.f * LN2 * r0.z, cb = -LN2 * r0.w, cc = -2.f * LN2 * r1.x;
+                            g_mx = fmaf(dpow, ca * dx + cb * dy, g_mx);
+                            g_my = fmaf(dpow, cb * dx + cc * dy, g_my);
+                            g_ca = fmaf(-0.5f * dpow, dx * dx, g_ca);
+                            g_cb = fmaf(-dpow, dx * dy, g_cb);
+                            g_cc = fmaf(-0.5f * dpow, dy * dy, g_cc);
+                        }
+                    }
+                }
+                v[9 * h + 0] = g_col0;
+                v[9 * h + 1] = g_col1;
+                v[9 * h + 2] = g_col2;
+                v[9 * h + 3] = g_op;
+                v[9 * h + 4] = g_mx;
+                v[9 * h + 5] = g_my;
+                v[9 * h + 6] = g_ca;
+                v[9 * h + 7] = g_cb;
+                v[9 * h + 8] = g_cc;
+                any[h] = __any_sync(0xffffffffu, contrib);
+            }
+#pragma unroll
+            for (int i = 27; i < 32; ++i) v[i] = 0.f;
+            if (any[0] || any[1] || any[2]) {
+                const float tot = warp_reduce_scatter32(v);  // lane i: the total of v[i]
+                const int h = lane / 9, vi = lane - 9 * h;
+                const int sj = h == 0 ? sjs[0] : (h == 1 ? sjs[1] : sjs[2]);
+                const bool live = h == 0 ? any[0] : (h == 1 ? any[1] : any[2]);
+                if (lane < 27 && live) {
                     const size_t g = (size_t)sg[b][sj];
                     float *dst = vi < 3   ? d_color + (size_t)vi * cs
                                  : vi == 3 ? d_opacity
                                  : vi < 6  ? d_mean2d + (size_t)(vi - 4) * cs
                                            : d_conic + (size_t)(vi - 6) * cs;
-                    atomicAdd(dst + g, vi == 3 ? tot / c.w : tot);
+                    atomicAdd(dst + g, vi == 3 ? tot / s2[b][sj].w : tot);
                 }
             }
         }
