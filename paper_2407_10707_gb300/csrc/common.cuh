@@ -82,28 +82,6 @@ __device__ __forceinline__ float warp_reduce_scatter16(const float (&v)[16])
     return s + __shfl_xor_sync(0xffffffffu, s, 1);
 }
 
-// The same for 32 values: five halving rounds (31 shuffles) leave lane i
-// with the warp total of v[i].
-__device__ __forceinline__ float warp_reduce_scatter32(const float (&v)[32])
-{
-    const unsigned lane = threadIdx.x & 31u;
-    const bool b4 = lane & 16u, b3 = lane & 8u, b2 = lane & 4u, b1 = lane & 2u, b0 = lane & 1u;
-    float x[16], w[8], u[4], t[2];
-#pragma unroll
-    for (int i = 0; i < 16; ++i)
-        x[i] = (b4 ? v[16 + i] : v[i]) + __shfl_xor_sync(0xffffffffu, b4 ? v[i] : v[16 + i], 16);
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-        w[i] = (b3 ? x[8 + i] : x[i]) + __shfl_xor_sync(0xffffffffu, b3 ? x[i] : x[8 + i], 8);
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-        u[i] = (b2 ? w[4 + i] : w[i]) + __shfl_xor_sync(0xffffffffu, b2 ? w[i] : w[4 + i], 4);
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-        t[i] = (b1 ? u[2 + i] : u[i]) + __shfl_xor_sync(0xffffffffu, b1 ? u[i] : u[2 + i], 2);
-    return (b0 ? t[1] : t[0]) + __shfl_xor_sync(0xffffffffu, b0 ? t[0] : t[1], 1);
-}
-
 __device__ __forceinline__ unsigned lanemask_lt()
 {
     unsigned m;

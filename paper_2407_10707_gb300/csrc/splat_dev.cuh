@@ -828,86 +828,57 @@ __device__ __forceinline__ void blend_backward_box(int2 rg, const int32_t *__res
                   (int)((unsigned)ra >> 16) <= by1;
         }
         unsigned hits = __ballot_sync(0xffffffffu, hit);
-        // hits are taken back to front, up to three at a time: each pixel's
-        // T and colour updates run in list order, and the three hits' nine
-        // gradient sums go through one 32-slot reduction (31 shuffles for
-        // three hits instead of 16 each) and one atomic instruction
         while (hits) {
-            int sjs[3];
+            const int sj = 31 - __clz(hits);
+            hits &= ~(1u << sj);
+            const int j = end - 32 + sj;
+            const float4 r1 = s1[b][sj];
+            const float4 r0 = s0[b][sj];
+            const float4 c = s2[b][sj];
+            float g_col0 = 0.f, g_col1 = 0.f, g_col2 = 0.f, g_op = 0.f, g_mx = 0.f, g_my = 0.f, g_ca = 0.f,
+                  g_cb = 0.f, g_cc = 0.f;
+            bool contrib = false;
 #pragma unroll
-            for (int h = 0; h < 3; ++h) {
-                sjs[h] = hits ? 31 - __clz(hits) : -1;
-                if (hits) hits &= ~(1u << sjs[h]);
-            }
-            float v[32];
-            bool any[3];
-#pragma unroll
-            for (int h = 0; h < 3; ++h) {
-                float g_col0 = 0.f, g_col1 = 0.f, g_col2 = 0.f, g_op = 0.f, g_mx = 0.f, g_my = 0.f, g_ca = 0.f,
-                      g_cb = 0.f, g_cc = 0.f;
-                bool contrib = false;
-                const int sj = sjs[h];  // warp-uniform
-                if (sj >= 0) {
-                    const int j = end - 32 + sj;
-                    const float4 r1 = s1[b][sj];
-                    const float4 r0 = s0[b][sj];
-                    const float4 c = s2[b][sj];
-#pragma unroll
-                    for (int k = 0; k < PPT; ++k) {
-                        if (j >= my_last[k]) continue;
-                        float dx = fx[k] - r0.x, dy = fy[k] - r0.y;
-                        float l2a = fmaf(fmaf(r0.z, dx, r0.w * dy), dx, fmaf(r1.x * dy, dy, r1.y));
-                        if (l2a < LOG2_ALPHA_MIN) continue;
-                        float raw = exp2f(l2a);
-                        float alpha = fminf(0.99f, raw);
-                        contrib = true;
-                        T[k] = T[k] / (1.f - alpha);
-                        float wgt = alpha * T[k];
-                        g_col0 = fmaf(wgt, dC0[k], g_col0);
-                        g_col1 = fmaf(wgt, dC1[k], g_col1);
-                        g_col2 = fmaf(wgt, dC2[k], g_col2);
-                        float dalpha =
-                            T[k] * ((c.x - acc0[k]) * dC0[k] + (c.y - acc1[k]) * dC1[k] + (c.z - acc2[k]) * dC2[k]);
-                        acc0[k] = alpha * c.x + (1.f - alpha) * acc0[k];
-                        acc1[k] = alpha * c.y + (1.f - alpha) * acc1[k];
-                        acc2[k] = alpha * c.z + (1.f - alpha) * acc2[k];
-                        if (raw < 0.99f) {
-                            float dpow = dalpha * raw;
-                            g_op += dpow;
-                            float ca = -2.f * LN2 * r0.z, cb = -LN2 * r0.w, cc = -2.f * LN2 * r1.x;
-                            g_mx = fmaf(dpow, ca * dx + cb * dy, g_mx);
-                            g_my = fmaf(dpow, cb * dx + cc * dy, g_my);
-                            g_ca = fmaf(-0.5f * dpow, dx * dx, g_ca);
-                            g_cb = fmaf(-dpow, dx * dy, g_cb);
-                            g_cc = fmaf(-0.5f * dpow, dy * dy, g_cc);
-                        }
-                    }
+            for (int k = 0; k < PPT; ++k) {
+                if (j >= my_last[k]) continue;
+                float dx = fx[k] - r0.x, dy = fy[k] - r0.y;
+                float l2a = fmaf(fmaf(r0.z, dx, r0.w * dy), dx, fmaf(r1.x * dy, dy, r1.y));
+                if (l2a < LOG2_ALPHA_MIN) continue;
+                float raw = exp2f(l2a);
+                float alpha = fminf(0.99f, raw);
+                contrib = true;
+                T[k] = T[k] / (1.f - alpha);
+                float wgt = alpha * T[k];
+                g_col0 = fmaf(wgt, dC0[k], g_col0);
+                g_col1 = fmaf(wgt, dC1[k], g_col1);
+                g_col2 = fmaf(wgt, dC2[k], g_col2);
+                float dalpha = T[k] * ((c.x - acc0[k]) * dC0[k] + (c.y - acc1[k]) * dC1[k] + (c.z - acc2[k]) * dC2[k]);
+                acc0[k] = alpha * c.x + (1.f - alpha) * acc0[k];
+                acc1[k] = alpha * c.y + (1.f - alpha) * acc1[k];
+                acc2[k] = alpha * c.z + (1.f - alpha) * acc2[k];
+                if (raw < 0.99f) {
+                    float dpow = dalpha * raw;
+                    g_op += dpow;
+                    float ca = -2.f * LN2 * r0.z, cb = -LN2 * r0.w, cc = -2.f * LN2 * r1.x;
+                    g_mx = fmaf(dpow, ca * dx + cb * dy, g_mx);
+                    g_my = fmaf(dpow, cb * dx + cc * dy, g_my);
+                    g_ca = fmaf(-0.5f * dpow, dx * dx, g_ca);
+                    g_cb = fmaf(-dpow, dx * dy, g_cb);
+                    g_cc = fmaf(-0.5f * dpow, dy * dy, g_cc);
                 }
-                v[9 * h + 0] = g_col0;
-                v[9 * h + 1] = g_col1;
-                v[9 * h + 2] = g_col2;
-                v[9 * h + 3] = g_op;
-                v[9 * h + 4] = g_mx;
-                v[9 * h + 5] = g_my;
-                v[9 * h + 6] = g_ca;
-                v[9 * h + 7] = g_cb;
-                v[9 * h + 8] = g_cc;
-                any[h] = __any_sync(0xffffffffu, contrib);
             }
-#pragma unroll
-            for (int i = 27; i < 32; ++i) v[i] = 0.f;
-            if (any[0] || any[1] || any[2]) {
-                const float tot = warp_reduce_scatter32(v);  // lane i: the total of v[i]
-                const int h = lane / 9, vi = lane - 9 * h;
-                const int sj = h == 0 ? sjs[0] : (h == 1 ? sjs[1] : sjs[2]);
-                const bool live = h == 0 ? any[0] : (h == 1 ? any[1] : any[2]);
-                if (lane < 27 && live) {
+            if (__any_sync(0xffffffffu, contrib)) {
+                const float v[16] = {g_col0, g_col1, g_col2, g_op, g_mx, g_my, g_ca, g_cb, g_cc,
+                                     0.f,    0.f,    0.f,    0.f,  0.f,  0.f,  0.f};
+                const float tot = warp_reduce_scatter16(v);
+                const int vi = lane >> 1;
+                if (!(lane & 1) && vi < 9) {
                     const size_t g = (size_t)sg[b][sj];
                     float *dst = vi < 3   ? d_color + (size_t)vi * cs
                                  : vi == 3 ? d_opacity
                                  : vi < 6  ? d_mean2d + (size_t)(vi - 4) * cs
                                            : d_conic + (size_t)(vi - 6) * cs;
-                    atomicAdd(dst + g, vi == 3 ? tot / s2[b][sj].w : tot);
+                    atomicAdd(dst + g, vi == 3 ? tot / c.w : tot);
                 }
             }
         }
