@@ -123,6 +123,31 @@ int avatar_probe_alu(avatar_ctx *ctx, int kind, int iters, uint32_t *sink, long 
                      avatar_stream_t stream);
 
 /* ------------------------------------------------------------------ */
+/* Storage order of the Gaussians (a layout step; the paper has no      */
+/* counterpart).  The per-Gaussian kernels gather their nearest mesh     */
+/* vertices' records; stored in the order of their nearest vertex, the  */
+/* 32 Gaussians of a warp share those records.  No result depends on    */
+/* the order: reorder every per-Gaussian array of an avatar with the    */
+/* same order, once, before rendering.                                   */
+/* ------------------------------------------------------------------ */
+/* Workspace bytes of avatar_gaussian_order for G Gaussians (0 if G < 0). */
+size_t avatar_gaussian_order_workspace_size(int G);
+/* order [G] (device, written): the stable order of the Gaussians by their
+ * nearest vertex nearest [G] (device; row 0 of the avatar's knn, each in
+ * [0, Nv)): order[i] is the i-th Gaussian by (nearest, index).  A nearest
+ * index outside [0, Nv) is reported in *status (AVATAR_ERR_INDEX) and sorts
+ * as Nv - 1.  Errors: AVATAR_ERR_INVALID_ARG (NULL pointers, G < 0,
+ * Nv < 1), AVATAR_ERR_WORKSPACE (missing, misaligned or too small). */
+int avatar_gaussian_order(avatar_ctx *ctx, int G, int Nv, const int32_t *nearest, int32_t *order, void *ws,
+                          size_t ws_bytes, int32_t *status, avatar_stream_t stream);
+/* dst[r][i] = src[r][order[i]] for rows r < rows (<= 65535) of n columns of
+ * elem_bytes (2 or 4) bytes each, both device arrays [rows][n] that must not
+ * overlap.  An order entry outside [0, n) is reported in *status
+ * (AVATAR_ERR_INDEX) and writes 0.  Errors: AVATAR_ERR_INVALID_ARG. */
+int avatar_gather_columns(avatar_ctx *ctx, int rows, int n, int elem_bytes, const void *src, void *dst,
+                          const int32_t *order, int32_t *status, avatar_stream_t stream);
+
+/* ------------------------------------------------------------------ */
 /* (a) Skinning - Sec. 3.1, Eq. 1                                       */
 /*                                                                      */
 /* Forward kinematics: bone_j = T_j * translate(-J_j) with               */

@@ -204,6 +204,9 @@ _SIGNATURES = [
     ("avatar_image_loss_workspace_size", [C.POINTER(ImageLossArgs)], C.c_size_t),
     ("avatar_image_loss", [P, C.POINTER(ImageLossArgs), P, C.c_size_t, P], I32),
     ("avatar_probe_alu", [P, I32, I32, P, C.POINTER(C.c_longlong), P], I32),
+    ("avatar_gaussian_order_workspace_size", [I32], C.c_size_t),
+    ("avatar_gaussian_order", [P, I32, I32, P, P, P, C.c_size_t, P, P], I32),
+    ("avatar_gather_columns", [P, I32, I32, I32, P, P, P, P, P], I32),
 ]
 
 EXPORTED = [s[0] for s in _SIGNATURES]

@@ -660,3 +660,29 @@ def probe_alu(kind, iters, sink):
     L.check(L.load().avatar_probe_alu(context(), kinds[kind], int(iters), _p(sink), C.byref(ops), _stream()),
             "avatar_probe_alu")
     return int(ops.value)
+
+
+def gaussian_order(knn, Nv, status=None):
+    """Stable order of the Gaussians by their nearest vertex (knn row 0)
+    (avatar_gaussian_order); int32 [G]."""
+    lib = L.load()
+    _need_cuda(knn, "knn")
+    G = knn.shape[-1]
+    order = torch.empty(G, dtype=torch.int32, device=knn.device)
+    ws = workspace(lib.avatar_gaussian_order_workspace_size(G), knn.device)
+    nearest = knn[0] if knn.dim() == 2 else knn
+    L.check(lib.avatar_gaussian_order(context(), G, int(Nv), _p(nearest), _p(order), _p(ws), ws.numel(), _p(status),
+                                      _stream()), "avatar_gaussian_order")
+    return order
+
+
+def gather_columns(src, order, status=None):
+    """dst[..., i] = src[..., order[i]] over the last dimension
+    (avatar_gather_columns); src holds 2- or 4-byte elements."""
+    _need_cuda(src, "src")
+    n = src.shape[-1]
+    dst = torch.empty_like(src)
+    rows = src.numel() // max(n, 1)
+    L.check(L.load().avatar_gather_columns(context(), rows, n, src.element_size(), _p(src), _p(dst), _p(order),
+                                           _p(status), _stream()), "avatar_gather_columns")
+    return dst

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libavatar.so")
-SOURCES = ["api.cu", "skin.cu", "visibility.cu", "shade.cu", "shade_tc.cu", "splat.cu", "batch.cu", "knn.cu", "loss.cu", "regularizers.cu", "mlp.cu", "densify.cu", "adam.cu", "probe.cu"]
+SOURCES = ["api.cu", "skin.cu", "visibility.cu", "shade.cu", "shade_tc.cu", "splat.cu", "batch.cu", "knn.cu", "loss.cu", "regularizers.cu", "mlp.cu", "densify.cu", "adam.cu", "probe.cu", "order.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -35,6 +35,28 @@ def scene_tensors(scene, device="cuda", attr_dtype="f32"):
                 cam_center=[float(c) for c in scene.camera.center])
 
 
+GAUSSIAN_KEYS = ("xg", "logscale", "quat", "opacity", "knn")
+
+
+def spatially_ordered(st, status=None):
+    """The scene with its Gaussians stored in the order of their nearest
+    vertex (avatar_gaussian_order, applied to every per-Gaussian array by
+    avatar_gather_columns): a setup step, once per avatar, that lets the
+    32 Gaussians of a warp share their neighbours' records.  Rendered images
+    are the same (Gaussians of equal depth keys blend in index order, so a
+    pixel can differ only where two depths tie exactly in FP32).  Returns
+    (scene tensors, order): Gaussian i of the result is Gaussian order[i] of
+    st."""
+    t = st["avatar"]
+    order = api.gaussian_order(t["knn"], t["xv"].shape[1], status)
+    t2 = dict(t)
+    for k in GAUSSIAN_KEYS:
+        t2[k] = api.gather_columns(t[k], order, status)
+    st2 = dict(st)
+    st2["avatar"] = t2
+    return st2, order
+
+
 class Renderer:
     """Preallocated forward frame.  forward() launches exactly the library's
     kernels: on the current stream, except that with overlap (the default)

@@ -435,6 +435,23 @@ def make_scene(n_vertices, n_gaussians, light_rows, light_cols, n_dirs, depth_re
 
 
 # Paper-shaped configurations: (Nv, G, light rows, light cols, D, depth res, W, H, seed)
+def permute_gaussians(scene: Scene, order) -> Scene:
+    """The scene with Gaussian i taken from Gaussian order[i] (positions,
+    log-scales, rotations, opacities and neighbour lists); everything else as
+    is.  A storage order, not a change of the avatar."""
+    import dataclasses
+    o = np.asarray(order)
+    av = scene.avatar
+    av2 = dataclasses.replace(av, xg=av.xg[o], logscale=av.logscale[o], quat=av.quat[o], opacity=av.opacity[o],
+                              knn=av.knn[o])
+    return dataclasses.replace(scene, avatar=av2)
+
+
+def nearest_vertex_order(scene: Scene) -> np.ndarray:
+    """Stable order of the Gaussians by their nearest vertex (knn column 0)."""
+    return np.argsort(scene.avatar.knn[:, 0], kind="stable").astype(np.int32)
+
+
 CONFIGS = {
     "c1_small": dict(n_vertices=2562, n_gaussians=10_000, light_rows=8, light_cols=16,
                      n_dirs=64, depth_res=64, width=256, height=256, seed=0),

@@ -1,0 +1,82 @@
+"""The Gaussians' storage order (avatar_gaussian_order, avatar_gather_columns)
+through the C ABI: the order is the stable sort by nearest vertex, bit for
+bit; the gather is numpy's fancy indexing; a frame of the reordered avatar
+meets the oracle run on the same reordered avatar, stage by stage."""
+import numpy as np
+import pytest
+
+from _common import scene, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2407_10707_gb300 import api, render
+    return api, render
+
+
+@pytest.mark.parametrize("G,Nv", [(1, 1), (5000, 200), (70_001, 300), (100_000, 70_000), (3, 2 ** 20)])
+def test_order_is_the_stable_sort_by_nearest_vertex(gpu, G, Nv):
+    """One, two and three radix passes (Nv up to 2^8, 2^16, 2^24), ragged
+    tile counts, many ties (few vertices)."""
+    api, render = gpu
+    rng = np.random.default_rng(G + Nv)
+    nearest = rng.integers(0, Nv, size=G).astype(np.int32)
+    status = api.status_word("cuda")
+    got = api.gaussian_order(torch.as_tensor(nearest, device="cuda"), Nv, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert np.array_equal(got.cpu().numpy(), np.argsort(nearest, kind="stable"))
+
+
+def test_order_reports_a_bad_index_and_stays_a_permutation(gpu):
+    api, render = gpu
+    nearest = np.array([3, 9, 1, 3, 0], np.int32)  # 9 is outside [0, 5)
+    status = api.status_word("cuda")
+    got = api.gaussian_order(torch.as_tensor(nearest, device="cuda"), 5, status).cpu().numpy()
+    torch.cuda.synchronize()
+    assert int(status.item()) == 7
+    assert np.array_equal(np.sort(got), np.arange(5))
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.int32])
+def test_gather_columns_is_fancy_indexing(gpu, dtype):
+    api, render = gpu
+    rng = np.random.default_rng(7)
+    n = 10_007
+    src = torch.as_tensor(rng.normal(size=(4, n)).astype(np.float32) * 1000).to(dtype).cuda()
+    order = torch.as_tensor(rng.permutation(n).astype(np.int32), device="cuda")
+    status = api.status_word("cuda")
+    dst = api.gather_columns(src, order, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert torch.equal(dst.cpu(), src.cpu()[:, order.cpu().long()])
+    bad = order.clone()
+    bad[17] = n
+    dst = api.gather_columns(src, bad, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 7 and float(dst[:, 17].float().abs().max()) == 0.0
+
+
+def test_reordered_frame_meets_the_oracle_on_the_reordered_avatar(gpu):
+    """The small frame of the avatar stored in nearest-vertex order: the GPU
+    order equals numpy's, and every stage meets the oracle run on the same
+    reordered avatar (tests/_chain.py, every pixel)."""
+    from _chain import chain_check
+    api, render = gpu
+    sc = scene("c1_small")
+    st, order = render.spatially_ordered(render.scene_tensors(sc))
+    np_order = synth.nearest_vertex_order(sc)
+    assert np.array_equal(order.cpu().numpy(), np_order)
+    r = render.Renderer(st)
+    torch.cuda.synchronize()
+    r.check()
+    rep = chain_check(r, synth.permute_gaussians(sc, np_order))
+    rep.pop("gpu")
+    print("reordered c1_small stage chain:", rep)
