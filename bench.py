@@ -861,11 +861,11 @@ def _form_batch(args, dev, reps):
     from paper_2407_10707_gb300 import render, synth
     torch.cuda.empty_cache()
     b = synth.config_batch("c4_batch", n_poses=args.batch_poses)
-    probe = render.BatchRenderer(b, tile=0, attr_dtype="bf16")
+    probe = render.BatchRenderer(b, tile=0, attr_dtype="bf16", spatial_order=True)
     cap = probe.cap
     targets = probe.images.detach().clone() * 0.9
     del probe
-    br = render.BatchRenderer(b, targets=targets, tile=0, attr_dtype="bf16", pair_capacity=cap)
+    br = render.BatchRenderer(b, targets=targets, tile=0, attr_dtype="bf16", pair_capacity=cap, spatial_order=True)
     tuned = br.autotune()
     bf = _time_graph(_graph_of(br.forward), max(3, reps // 4))
     bt = _time_graph(_graph_of(br.step), max(3, reps // 4))
@@ -877,7 +877,7 @@ def _form_batch(args, dev, reps):
         scv = dataclasses.replace(b.scene, avatar=dataclasses.replace(b.scene.avatar, pose=b.poses[p]),
                                   light=synth.Light(L=b.lights[p], A=b.scene.light.A, w=b.scene.light.w),
                                   camera=b.cameras[v])
-        stv = render.scene_tensors(scv, dev)
+        stv, _ = render.spatially_ordered(render.scene_tensors(scv, dev))
         rv = render.Renderer(stv, tile=args.tile)
         tv = render.TrainStep(stv, rv.sb.image.detach().clone() * 0.9, tile=args.tile)
         per[(b.cameras[v].width, b.cameras[v].height)] = (_time_graph(_graph_of(rv.forward), reps),
@@ -889,7 +889,8 @@ def _form_batch(args, dev, reps):
     stn = sum(cnt[k] * per[k][1] for k in cnt)
     return {
         "what": f"{b.B} poses x 4 cameras (512x512, 1080x1080, 1920x1080), own 16x32 light per pose, 200k Gaussians, "
-                "512 visibility directions at 256^2, BF16 storage; one launch per stage, one CUDA graph",
+                "512 visibility directions at 256^2, BF16 storage, Gaussians in nearest-vertex order; one launch "
+                "per stage, one CUDA graph",
         "views_per_s": round(b.V * 1000.0 / bf, 1), "train_views_per_s": round(b.V * 1000.0 / bt, 1),
         "ms_per_batch": round(bf, 3), "ms_per_train_batch": round(bt, 3),
         "per_frame_fp32_views_per_s": round(b.V * 1000.0 / sf, 1),

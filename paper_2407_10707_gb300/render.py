@@ -469,16 +469,23 @@ class BatchRenderer:
     views' pixels and the batched backward (avatar_render_batch_backward).
 
     batch: a synth.Batch; attr_dtype 'bf16' stores the learnable attributes
-    in BF16.  The pair buffer grows once if the first eager call overflows."""
+    in BF16; spatial_order stores the Gaussians in the order of their
+    nearest vertex (as spatially_ordered; self.order then maps Gaussian i
+    to the batch avatar's Gaussian self.order[i]).  The pair buffer grows
+    once if the first eager call overflows."""
 
     def __init__(self, batch, targets=None, tile=0, pair_capacity=None, vis_cull_back=True, attr_dtype="f32",
-                 device="cuda", ssim_weight=0.2):
+                 device="cuda", ssim_weight=0.2, spatial_order=False):
         import ctypes as C
         from . import _lib as L
         self.L, self.C = L, C
         sc = batch.scene
         f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=device)
         self.t = api.avatar_tensors(sc.avatar, device, attr_dtype)
+        self.order = None
+        if spatial_order:
+            st, self.order = spatially_ordered({"avatar": self.t})
+            self.t = st["avatar"]
         self.frames = f(sc.frames.reshape(-1, 9))
         self.light_A, self.light_w = f(sc.light.A), f(sc.light.w)
         self.dmap = torch.as_tensor(sc.dmap, dtype=torch.int32, device=device)
