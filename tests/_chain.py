@@ -111,9 +111,13 @@ def chain_check(r, sc, pixels=None, two_sided=True):
     rep["shaded_gaussians"] = int(keep.sum())
     assert e < PIX_TOL, f"shading colours: {e:.3g} max-abs (bound {PIX_TOL})"
     assert np.all(g["color"][~keep] == 0.0)
+    # L_o relative to its largest value: the GGX peak is the ill-conditioned
+    # term - den = (n.h)^2 (alpha^2 - 1) + 1 falls to alpha^2 = gamma^4 >=
+    # 0.0081 (roughness >= 0.3), so a few-ulp error in n.h (about 4 x 2^-24)
+    # is 2 x 4 x 2^-24 / 0.0081 ~ 6e-5 relative in den and twice that in D
     e = rel_err(g["radiance"][keep], rad[keep]) if keep.any() else 0.0
     rep["shade_radiance_rel"] = e
-    assert e < 5e-5
+    assert e < 2e-4, f"shading radiance: {e:.3g} relative to its largest value (bound 2e-4)"
     # (d1) projection from the GPU's skinning outputs and cull flags
     op = _opacity(sc)
     pr = O.project(f32(g["xd"]).astype(np.float64), f32(g["cov"]).astype(np.float64), op, g["cull"], sc.camera)
