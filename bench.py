@@ -138,9 +138,10 @@ def run_gpu(args):
 
     dev = torch.device("cuda", local)
     sc = synth.config_scene(args.workload)
-    # the Gaussians stored in the order of their nearest vertex (a setup step,
-    # outside every timed region; the rendered images are the same)
-    st, _ = render.spatially_ordered(render.scene_tensors(sc, dev))
+    # the Gaussians stored in the order of their nearest vertex and the light
+    # texels in 4 x 8 patches (setup steps, outside every timed region; the
+    # rendered images are the same)
+    st = STM.stored_for_speed(render, synth, sc, dev)
     G, Nv, F = sc.avatar.G, sc.avatar.Nv, sc.avatar.F
     NL, D, R = len(sc.light.A), sc.frames.shape[0], sc.depth_res
     W, H = sc.camera.width, sc.camera.height
@@ -226,8 +227,8 @@ def run_gpu(args):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "flushed (256 MB write) between timed steps", "graph": "CUDA graph replay",
                    "visibility": "one-sided raster of the closed capsule body (same bits as two-sided)",
-                   "gaussian_order": "stored in the order of their nearest vertex (render.spatially_ordered, "
-                                     "once before timing)"},
+                   "storage_order": "Gaussians in nearest-vertex order, light texels in 4 x 8 patches "
+                                    "(render.spatially_ordered, render.light_ordered; once before timing)"},
         "train": {"value": round(whole_job_rate(world, train_ms), 3), "unit": "train steps/s", "ms_per_step":
                   round(train_ms, 5),
                   "what": "frame + image loss (L1 + 0.2 D-SSIM) + backward of every stage",
@@ -262,6 +263,14 @@ def run_gpu(args):
 
 
 # ----------------------------------------------------------------- measurement helpers
+def stored_for_speed(render, synth, sc, dev, attr_dtype="f32"):
+    """Scene tensors with the Gaussians in nearest-vertex order and the light
+    texels in 4 x 8 patches (render.spatially_ordered, render.light_ordered)."""
+    st, _ = render.spatially_ordered(render.scene_tensors(sc, dev, attr_dtype=attr_dtype))
+    st, _ = render.light_ordered(st, synth.latlong_patch_order(sc.light.rows, sc.light.cols))
+    return st
+
+
 def _graph_of(fn):
     import torch
     s = torch.cuda.Stream()
@@ -640,7 +649,7 @@ def _form_stress(args, dev, flush, reps):
     out = {"what": "frames/s and train steps/s (forward on the tensor cores, FP32 adjoints) against the FP32 "
                    "CUDA-core shading of the same frame; max-abs pixel difference (target <= 1e-3)"}
     for dt in ("f32", "bf16"):
-        st, _ = render.spatially_ordered(render.scene_tensors(sc, dev, attr_dtype=dt))
+        st = stored_for_speed(render, synth, sc, dev, attr_dtype=dt)
         cap = 96 * sc.avatar.G  # about fifty 16-pixel tiles per Gaussian at 2048^2
         r32 = render.Renderer(st, tile=args.tile, pair_capacity=cap)
         rtc = render.Renderer(st, tile=args.tile, shade_tc=True, pair_capacity=cap)
@@ -780,8 +789,8 @@ def _form_paper_vis(r, st, sc, args, dev, flush, reps):
 def _form_precision(r, st, sc, args, dev, flush, fwd_ms, train_ms, reps):
     import torch
 
-    from paper_2407_10707_gb300 import render
-    st16, _ = render.spatially_ordered(render.scene_tensors(sc, dev, attr_dtype="bf16"))
+    from paper_2407_10707_gb300 import render, synth
+    st16 = stored_for_speed(render, synth, sc, dev, attr_dtype="bf16")
     r16 = render.Renderer(st16, tile=args.tile, shade_tc=True)
     g16 = _graph_of(r16.forward)
     f16 = _time_graph(g16, reps, flush)
@@ -861,11 +870,13 @@ def _form_batch(args, dev, reps):
     from paper_2407_10707_gb300 import render, synth
     torch.cuda.empty_cache()
     b = synth.config_batch("c4_batch", n_poses=args.batch_poses)
-    probe = render.BatchRenderer(b, tile=0, attr_dtype="bf16", spatial_order=True)
+    lorder = synth.latlong_patch_order(b.scene.light.rows, b.scene.light.cols)
+    probe = render.BatchRenderer(b, tile=0, attr_dtype="bf16", spatial_order=True, light_order=lorder)
     cap = probe.cap
     targets = probe.images.detach().clone() * 0.9
     del probe
-    br = render.BatchRenderer(b, targets=targets, tile=0, attr_dtype="bf16", pair_capacity=cap, spatial_order=True)
+    br = render.BatchRenderer(b, targets=targets, tile=0, attr_dtype="bf16", pair_capacity=cap, spatial_order=True,
+                              light_order=lorder)
     tuned = br.autotune()
     bf = _time_graph(_graph_of(br.forward), max(3, reps // 4))
     bt = _time_graph(_graph_of(br.step), max(3, reps // 4))
@@ -877,7 +888,7 @@ def _form_batch(args, dev, reps):
         scv = dataclasses.replace(b.scene, avatar=dataclasses.replace(b.scene.avatar, pose=b.poses[p]),
                                   light=synth.Light(L=b.lights[p], A=b.scene.light.A, w=b.scene.light.w),
                                   camera=b.cameras[v])
-        stv, _ = render.spatially_ordered(render.scene_tensors(scv, dev))
+        stv = stored_for_speed(render, synth, scv, dev)
         rv = render.Renderer(stv, tile=args.tile)
         tv = render.TrainStep(stv, rv.sb.image.detach().clone() * 0.9, tile=args.tile)
         per[(b.cameras[v].width, b.cameras[v].height)] = (_time_graph(_graph_of(rv.forward), reps),
@@ -889,8 +900,8 @@ def _form_batch(args, dev, reps):
     stn = sum(cnt[k] * per[k][1] for k in cnt)
     return {
         "what": f"{b.B} poses x 4 cameras (512x512, 1080x1080, 1920x1080), own 16x32 light per pose, 200k Gaussians, "
-                "512 visibility directions at 256^2, BF16 storage, Gaussians in nearest-vertex order; one launch "
-                "per stage, one CUDA graph",
+                "512 visibility directions at 256^2, BF16 storage, Gaussians in nearest-vertex order, light "
+                "texels in 4 x 8 patches; one launch per stage, one CUDA graph",
         "views_per_s": round(b.V * 1000.0 / bf, 1), "train_views_per_s": round(b.V * 1000.0 / bt, 1),
         "ms_per_batch": round(bf, 3), "ms_per_train_batch": round(bt, 3),
         "per_frame_fp32_views_per_s": round(b.V * 1000.0 / sf, 1),

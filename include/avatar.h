@@ -140,10 +140,12 @@ size_t avatar_gaussian_order_workspace_size(int G);
  * Nv < 1), AVATAR_ERR_WORKSPACE (missing, misaligned or too small). */
 int avatar_gaussian_order(avatar_ctx *ctx, int G, int Nv, const int32_t *nearest, int32_t *order, void *ws,
                           size_t ws_bytes, int32_t *status, avatar_stream_t stream);
-/* dst[r][i] = src[r][order[i]] for rows r < rows (<= 65535) of n columns of
- * elem_bytes (2 or 4) bytes each, both device arrays [rows][n] that must not
- * overlap.  An order entry outside [0, n) is reported in *status
- * (AVATAR_ERR_INDEX) and writes 0.  Errors: AVATAR_ERR_INVALID_ARG. */
+/* dst[r][i] = src[r][order[i]] for rows r < rows (<= 65535) of n elements
+ * of elem_bytes (2, 4, 8, 12 or 16) bytes each - columns of a
+ * structure-of-arrays, or records such as a light's 3 floats - both device
+ * arrays [rows][n] aligned to 2 bytes (elem_bytes 2) or 4 (the others) that
+ * must not overlap.  An order entry outside [0, n) is reported in *status
+ * (AVATAR_ERR_INDEX) and writes zeros.  Errors: AVATAR_ERR_INVALID_ARG. */
 int avatar_gather_columns(avatar_ctx *ctx, int rows, int n, int elem_bytes, const void *src, void *dst,
                           const int32_t *order, int32_t *status, avatar_stream_t stream);
 

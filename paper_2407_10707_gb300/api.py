@@ -678,11 +678,18 @@ def gaussian_order(knn, Nv, status=None):
 
 def gather_columns(src, order, status=None):
     """dst[..., i] = src[..., order[i]] over the last dimension
-    (avatar_gather_columns); src holds 2- or 4-byte elements."""
+    (avatar_gather_columns); src holds 2- or 4-byte elements.  A 3-d src
+    [rows][n][m] of 4-byte elements (m <= 4) is gathered by its n records
+    of m elements."""
     _need_cuda(src, "src")
-    n = src.shape[-1]
+    if src.dim() == 3:
+        rows, n, m = src.shape
+        elem = m * src.element_size()
+    else:
+        n = src.shape[-1]
+        rows = src.numel() // max(n, 1)
+        elem = src.element_size()
     dst = torch.empty_like(src)
-    rows = src.numel() // max(n, 1)
-    L.check(L.load().avatar_gather_columns(context(), rows, n, src.element_size(), _p(src), _p(dst), _p(order),
-                                           _p(status), _stream()), "avatar_gather_columns")
+    L.check(L.load().avatar_gather_columns(context(), rows, n, elem, _p(src), _p(dst), _p(order), _p(status),
+                                           _stream()), "avatar_gather_columns")
     return dst

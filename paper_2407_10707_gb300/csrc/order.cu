@@ -10,6 +10,7 @@
 //   avatar_gaussian_order   stable order of the Gaussians by nearest vertex
 //                           (the device radix sort of the splatting path)
 //   avatar_gather_columns   applies an order to structure-of-arrays columns
+//                           (or to the rows of an array of small records)
 #include "splat_dev.cuh"
 
 namespace {
@@ -101,20 +102,62 @@ extern "C" int avatar_gaussian_order(avatar_ctx *ctx, int G, int Nv, const int32
     return radix_sort(w.k0, v0, w.k1, v1, passes * 8, w.count, G, w.sort, status, st, sort_spin_limit(ctx));
 }
 
+// A w-word element (w 32-bit words) copied as a unit.
+template <int W>
+struct Words {
+    uint32_t v[W];
+    __host__ __device__ Words() {}
+    __host__ __device__ explicit Words(int) {
+        for (int i = 0; i < W; ++i) v[i] = 0u;
+    }
+};
+
+template <int W>
+__global__ void gather_words_kernel(int rows, int n, const Words<W> *__restrict__ src, Words<W> *__restrict__ dst,
+                                    const int32_t *__restrict__ order, int32_t *status)
+{
+    const size_t r = blockIdx.y;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int j = __ldg(order + i);
+        if ((unsigned)j >= (unsigned)n) {
+            av_report(status, AVATAR_ERR_INDEX);
+            dst[r * n + i] = Words<W>(0);
+            continue;
+        }
+        dst[r * n + i] = src[r * n + j];
+    }
+}
+
 extern "C" int avatar_gather_columns(avatar_ctx *ctx, int rows, int n, int elem_bytes, const void *src, void *dst,
                                      const int32_t *order, int32_t *status, avatar_stream_t stream)
 {
-    if (!ctx || rows < 0 || rows > 65535 || n < 0 || (elem_bytes != 2 && elem_bytes != 4)) return AVATAR_ERR_INVALID_ARG;
+    if (!ctx || rows < 0 || rows > 65535 || n < 0) return AVATAR_ERR_INVALID_ARG;
+    if (elem_bytes != 2 && elem_bytes != 4 && elem_bytes != 8 && elem_bytes != 12 && elem_bytes != 16)
+        return AVATAR_ERR_INVALID_ARG;
     if (rows == 0 || n == 0) return AVATAR_OK;
     if (!src || !dst || !order || src == dst) return AVATAR_ERR_INVALID_ARG;
+    if ((((uintptr_t)src) | ((uintptr_t)dst)) & (elem_bytes == 2 ? 1 : 3)) return AVATAR_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const dim3 grid(order_grid(ctx, n), rows);
-    if (elem_bytes == 4)
-        gather_columns_kernel<uint32_t><<<grid, 256, 0, st>>>(rows, n, (const uint32_t *)src, (uint32_t *)dst, order,
-                                                              status);
-    else
-        gather_columns_kernel<uint16_t><<<grid, 256, 0, st>>>(rows, n, (const uint16_t *)src, (uint16_t *)dst, order,
-                                                              status);
+    switch (elem_bytes) {
+        case 2:
+            gather_columns_kernel<uint16_t><<<grid, 256, 0, st>>>(rows, n, (const uint16_t *)src, (uint16_t *)dst,
+                                                                  order, status);
+            break;
+        case 4:
+            gather_columns_kernel<uint32_t><<<grid, 256, 0, st>>>(rows, n, (const uint32_t *)src, (uint32_t *)dst,
+                                                                  order, status);
+            break;
+        case 8:
+            gather_words_kernel<2><<<grid, 256, 0, st>>>(rows, n, (const Words<2> *)src, (Words<2> *)dst, order, status);
+            break;
+        case 12:
+            gather_words_kernel<3><<<grid, 256, 0, st>>>(rows, n, (const Words<3> *)src, (Words<3> *)dst, order, status);
+            break;
+        default:
+            gather_words_kernel<4><<<grid, 256, 0, st>>>(rows, n, (const Words<4> *)src, (Words<4> *)dst, order, status);
+            break;
+    }
     AV_CHECK_LAUNCH();
     return AVATAR_OK;
 }

@@ -57,6 +57,24 @@ def spatially_ordered(st, status=None):
     return st2, order
 
 
+def light_ordered(st, order, status=None):
+    """The scene with its light texels stored in `order` (int32 [NL], e.g.
+    synth.latlong_patch_order): radiance, solid angles, directions and the
+    viewpoint map d(k) reordered by avatar_gather_columns, so the visibility
+    bits and the shading's 32-light chunks follow it.  Texel s of the result
+    is texel order[s] of st; the images are the same (the shading sums run
+    in another order) and light gradients come back in the new order."""
+    dev = st["light"]["L"].device
+    o = torch.as_tensor(np.ascontiguousarray(order, dtype=np.int32), device=dev)
+    lt = st["light"]
+    st2 = dict(st)
+    st2["light"] = dict(L=api.gather_columns(lt["L"].reshape(1, -1, 3), o, status).reshape(lt["L"].shape),
+                        A=api.gather_columns(lt["A"], o, status),
+                        w=api.gather_columns(lt["w"].reshape(1, -1, 3), o, status).reshape(lt["w"].shape))
+    st2["dmap"] = api.gather_columns(st["dmap"], o, status)
+    return st2, o
+
+
 class Renderer:
     """Preallocated forward frame.  forward() launches exactly the library's
     kernels: on the current stream, except that with overlap (the default)
@@ -471,11 +489,12 @@ class BatchRenderer:
     batch: a synth.Batch; attr_dtype 'bf16' stores the learnable attributes
     in BF16; spatial_order stores the Gaussians in the order of their
     nearest vertex (as spatially_ordered; self.order then maps Gaussian i
-    to the batch avatar's Gaussian self.order[i]).  The pair buffer grows
-    once if the first eager call overflows."""
+    to the batch avatar's Gaussian self.order[i]); light_order (int32 [NL])
+    stores every pose's light texels in that order (as light_ordered).  The
+    pair buffer grows once if the first eager call overflows."""
 
     def __init__(self, batch, targets=None, tile=0, pair_capacity=None, vis_cull_back=True, attr_dtype="f32",
-                 device="cuda", ssim_weight=0.2, spatial_order=False):
+                 device="cuda", ssim_weight=0.2, spatial_order=False, light_order=None):
         import ctypes as C
         from . import _lib as L
         self.L, self.C = L, C
@@ -492,6 +511,15 @@ class BatchRenderer:
         self.poses = f(batch.poses)
         self.light_L = f(batch.lights)
         self.B, self.V = batch.B, batch.V
+        self.light_order = None
+        if light_order is not None:
+            # every pose's light texels, their geometry and d(k) in the given order (as light_ordered)
+            o = torch.as_tensor(np.ascontiguousarray(light_order, dtype=np.int32), device=device)
+            self.light_L = api.gather_columns(self.light_L, o)
+            self.light_A = api.gather_columns(self.light_A, o)
+            self.light_w = api.gather_columns(self.light_w.reshape(1, -1, 3), o).reshape(self.light_w.shape)
+            self.dmap = api.gather_columns(self.dmap, o)
+            self.light_order = o
         self.cameras = list(batch.cameras)
         self.view_pose = np.asarray(batch.view_pose, np.int32)
         self.sizes = [(c.height, c.width) for c in self.cameras]

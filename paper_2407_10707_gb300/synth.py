@@ -323,6 +323,8 @@ class Light:
     L: np.ndarray    # [K,3] radiance
     A: np.ndarray    # [K] solid angle of each texel
     w: np.ndarray    # [K,3] unit direction towards the light
+    rows: int = 0    # lat-long grid shape (0: not a grid)
+    cols: int = 0
 
 
 def latlong_light(rng, rows: int, cols: int, mu: float = -1.0, sd: float = 0.5) -> Light:
@@ -337,7 +339,29 @@ def latlong_light(rng, rows: int, cols: int, mu: float = -1.0, sd: float = 0.5) 
     band = (np.cos(i * math.pi / rows) - np.cos((i + 1) * math.pi / rows)) * 2.0 * math.pi / cols
     A = np.repeat(band, cols)
     L = np.exp(rng.normal(mu, sd, size=(rows * cols, 3)))
-    return Light(L=L, A=A, w=w)
+    return Light(L=L, A=A, w=w, rows=rows, cols=cols)
+
+
+def latlong_patch_order(rows: int, cols: int, pr: int = 4, pc: int = 8) -> np.ndarray:
+    """A storage order of a rows x cols lat-long light grid (row-major texel
+    index) that lists the texels patch by patch, pr rows by pc columns per
+    patch (32 texels: one 32-light chunk of the shading kernels), patches in
+    row-major order; the identity when the grid does not split into patches."""
+    if rows <= 0 or cols <= 0 or rows % pr or cols % pc:
+        return np.arange(max(rows * cols, 0), dtype=np.int32)
+    idx = np.arange(rows * cols).reshape(rows // pr, pr, cols // pc, pc)
+    return np.ascontiguousarray(idx.transpose(0, 2, 1, 3)).reshape(-1).astype(np.int32)
+
+
+def permute_lights(scene, order):
+    """The scene with light texel s taken from texel order[s] (radiance,
+    solid angle, direction, and the viewpoint d(k) of each texel); a storage
+    order of the same light."""
+    import dataclasses
+    o = np.asarray(order)
+    lt = scene.light
+    light = dataclasses.replace(lt, L=lt.L[o], A=lt.A[o], w=lt.w[o], rows=0, cols=0)
+    return dataclasses.replace(scene, light=light, dmap=np.asarray(scene.dmap)[o])
 
 
 def fibonacci_directions(n: int) -> np.ndarray:

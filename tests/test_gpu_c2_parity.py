@@ -1,11 +1,13 @@
 """Parity at the paper-scale frame, in the configuration the benchmark times.
 
 The frame: 50k-vertex body mesh, 200k Gaussians stored in the order of their
-nearest vertex (render.spatially_ordered), 16 x 32 environment light, 512
+nearest vertex (render.spatially_ordered), 16 x 32 environment light stored
+in 4 x 8 patches (render.light_ordered), 512
 visibility directions at 256^2 (one-sided raster of the closed body), one
 1024 x 1024 camera, 16-pixel tiles; the overlapped frame (cull, projection and
 binning on a second stream) replayed from its CUDA graph.  The oracle runs on
-the same reordered avatar (the order checked equal to numpy's stable sort).
+the same reordered avatar and light (the Gaussian order checked equal to
+numpy's stable sort).
 
 Every stage is compared with the FP64 oracle on the GPU's own inputs (the
 stage chain of tests/_chain.py): the visibility bits of all 512 directions
@@ -34,10 +36,12 @@ def frame():
     from paper_2407_10707_gb300 import render
     from _common import synth
     sc0 = scene("c2_paper")
-    st, order = render.spatially_ordered(render.scene_tensors(sc0))   # the benchmark's storage order
+    st, order = render.spatially_ordered(render.scene_tensors(sc0))   # the benchmark's storage orders
     np_order = synth.nearest_vertex_order(sc0)
     assert np.array_equal(order.cpu().numpy(), np_order)
-    sc = synth.permute_gaussians(sc0, np_order)
+    lorder = synth.latlong_patch_order(sc0.light.rows, sc0.light.cols)
+    st, _ = render.light_ordered(st, lorder)
+    sc = synth.permute_lights(synth.permute_gaussians(sc0, np_order), lorder)
     r = render.Renderer(st, tile=16)              # the benchmark's renderer and tile edge
     r.capture()
     for _ in range(3):

@@ -80,3 +80,46 @@ def test_reordered_frame_meets_the_oracle_on_the_reordered_avatar(gpu):
     rep = chain_check(r, synth.permute_gaussians(sc, np_order))
     rep.pop("gpu")
     print("reordered c1_small stage chain:", rep)
+
+
+@pytest.mark.parametrize("m", [2, 3, 4])
+def test_gather_records(gpu, m):
+    """Records of m 4-byte words (8, 12, 16 bytes), several rows."""
+    api, render = gpu
+    rng = np.random.default_rng(m)
+    src = torch.as_tensor(rng.normal(size=(3, 513, m)).astype(np.float32), device="cuda")
+    order = torch.as_tensor(rng.permutation(513).astype(np.int32), device="cuda")
+    dst = api.gather_columns(src, order)
+    torch.cuda.synchronize()
+    assert torch.equal(dst.cpu(), src.cpu()[:, order.cpu().long(), :])
+
+
+def test_patch_order_is_a_permutation_of_4x8_blocks():
+    o = synth.latlong_patch_order(16, 32)
+    assert np.array_equal(np.sort(o), np.arange(512))
+    first = o[:32]
+    assert np.array_equal(np.unique(first // 32), np.arange(4)) and np.array_equal(np.unique(first % 32), np.arange(8))
+    assert np.array_equal(synth.latlong_patch_order(6, 10), np.arange(60))   # no 4 x 8 split: identity
+
+
+def test_light_ordered_frame_meets_the_oracle_on_the_reordered_light(gpu):
+    """The small frame (8 x 16 light) with its texels in 4 x 8 patches and
+    the Gaussians in nearest-vertex order: every stage meets the oracle run
+    on the same reordered scene (every pixel), and the image is the one the
+    original order renders, up to the summation order of the shading."""
+    from _chain import chain_check
+    api, render = gpu
+    sc = scene("c1_small")
+    st0 = render.scene_tensors(sc)
+    img0 = render.Renderer(st0).sb.image.clone()
+    st, order = render.spatially_ordered(st0)
+    lorder = synth.latlong_patch_order(sc.light.rows, sc.light.cols)
+    st, _ = render.light_ordered(st, lorder)
+    r = render.Renderer(st)
+    torch.cuda.synchronize()
+    r.check()
+    sc2 = synth.permute_lights(synth.permute_gaussians(sc, synth.nearest_vertex_order(sc)), lorder)
+    rep = chain_check(r, sc2)
+    rep.pop("gpu")
+    print("reordered lights and Gaussians, c1_small:", rep)
+    assert float((r.sb.image - img0).abs().max()) < 2e-4
