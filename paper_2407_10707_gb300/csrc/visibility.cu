@@ -294,12 +294,16 @@ __global__ void vis_chunk_ranges_kernel(const int32_t *__restrict__ faces, int F
                     ((__ldg(faces + 3 * f + 2) - smin) << 20);
 }
 
-template <int CL, bool CULL_BACK, bool BATCH>
-__global__ void __launch_bounds__(VIS_THREADS)
+// NT threads per CTA: 256, or 512 with 4-CTA clusters (their 64 KB slabs hold
+// two CTAs per SM, so 512 threads keep the resident warps of 8-CTA clusters
+// of 256); at most 64 registers either way.
+template <int CL, bool CULL_BACK, bool BATCH, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT)
 vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *__restrict__ faces,
                        const int32_t *__restrict__ pfaces, const int2 *__restrict__ vranges,
                        const float *__restrict__ frames, uint32_t *__restrict__ dirbits, int32_t *status)
 {
+    constexpr int TPT = VIS_CHUNK / NT;  // triangles per thread per chunk
     extern __shared__ int slab[];
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = CL == 1 ? 0 : (int)cluster.block_rank();
@@ -331,11 +335,11 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
 
     // packed faces of this CTA's first chunk (the next chunk's are prefetched
     // while the current one is rasterised); -1 past the last face
-    int cur[VIS_TPT];
-    auto load_faces = [&](int chunk, int (&dst)[VIS_TPT]) {
+    int cur[TPT];
+    auto load_faces = [&](int chunk, int (&dst)[TPT]) {
 #pragma unroll
-        for (int t = 0; t < VIS_TPT; ++t) {
-            const int f = chunk * VIS_CHUNK + t * VIS_THREADS + threadIdx.x;
+        for (int t = 0; t < TPT; ++t) {
+            const int f = chunk * VIS_CHUNK + t * NT + threadIdx.x;
             dst[t] = f < p.F ? __ldg(pfaces + f) : -1;
         }
     };
@@ -365,18 +369,18 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
         const bool cached = nv > 0 && nv <= VIS_VCAP;
         if (cached) {
 #pragma unroll 4
-            for (int i = threadIdx.x; i < nv; i += VIS_THREADS)
+            for (int i = threadIdx.x; i < nv; i += NT)
                 vcache[i] = pack_proj(project_vertex(__ldg(qv + v0 + i), B, p));
         }
         if (threadIdx.x == 0) s_next = taken;
         __syncthreads();
         const int next = s_next;
-        int nxt[VIS_TPT];
+        int nxt[TPT];
         if (next < nchunks) load_faces(next, nxt);
         if (nv > 0) {
 #pragma unroll
-            for (int t = 0; t < VIS_TPT; ++t) {
-                const int f = chunk * VIS_CHUNK + t * VIS_THREADS + threadIdx.x;
+            for (int t = 0; t < TPT; ++t) {
+                const int f = chunk * VIS_CHUNK + t * NT + threadIdx.x;
                 if (f >= p.F) continue;
                 uint2 pa, pb, pc;
                 if (cached) {
@@ -393,7 +397,7 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
         }
         __syncthreads();  // the next chunk overwrites the cache (and s_next)
 #pragma unroll
-        for (int t = 0; t < VIS_TPT; ++t) cur[t] = nxt[t];
+        for (int t = 0; t < TPT; ++t) cur[t] = nxt[t];
         chunk = next;
     }
     cluster.sync();
@@ -401,7 +405,7 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
     // ---- depth-test vertices: one warp -> 32-bit words of this direction,
     // four words in flight per iteration
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nwarps = VIS_THREADS / 32;
+    const int nwarps = NT / 32;
     const int wstride = CL * nwarps;
     for (int w0 = rank * nwarps + warp; w0 < p.NW; w0 += 4 * wstride) {
         int4 qq[4];
@@ -739,12 +743,13 @@ int launch_raster(const VisParams &p, const int4 *qv, const int32_t *faces, cons
                   const int2 *vranges, const float *frames, uint32_t *dirbits, int32_t *status, size_t smem,
                   cudaStream_t st)
 {
-    auto kern = p.B > 1 ? vis_raster_test_kernel<CL, CULL_BACK, true> : vis_raster_test_kernel<CL, CULL_BACK, false>;
+    constexpr int NT = CL == 4 ? 512 : 256;
+    auto kern = p.B > 1 ? vis_raster_test_kernel<CL, CULL_BACK, true, NT> : vis_raster_test_kernel<CL, CULL_BACK, false, NT>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return AVATAR_ERR_CUDA;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CL, p.D, p.B);
-    cfg.blockDim = dim3(VIS_THREADS, 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
