@@ -143,47 +143,6 @@ __device__ __forceinline__ void load_chunk(const uint32_t *__restrict__ bits, co
     }
 }
 
-// Bounding cone of each 32-light chunk: its lights' mean direction c and
-// the threshold -sin(theta) - 1e-4, theta the largest angle between c and a
-// light of the chunk (no skip, threshold -2, when theta is near or above
-// 90 degrees).  A Gaussian with n.c below the threshold has every light of
-// the chunk below its horizon: angle(n, w) >= angle(n, c) - theta > 90
-// degrees + 1e-4, so n.w < -1e-4 in exact and (well inside) FP32
-// arithmetic, and the chunk, which would add nothing, is skipped before its
-// visibility words are loaded.  One warp per chunk, once per block.
-constexpr int SHADE_MAX_CHUNKS = 4096 / 32;
-
-__device__ __forceinline__ void chunk_cones(const float4 *lw, int NL, float4 *cone)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int OW = (NL + 31) / 32;
-    for (int ch = warp; ch < OW; ch += nw) {
-        const int k = ch * 32 + lane;
-        const float4 w = k < NL ? lw[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float sx = warp_sum(w.x), sy = warp_sum(w.y), sz = warp_sum(w.z);
-        const float len = sqrtf(sx * sx + sy * sy + sz * sz);
-        float thr = -2.f;
-        float cx = 0.f, cy = 0.f, cz = 0.f;
-        if (len > 1e-3f) {
-            cx = sx / len;
-            cy = sy / len;
-            cz = sz / len;
-            float cm = k < NL ? cx * w.x + cy * w.y + cz * w.z : 1.f;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) cm = fminf(cm, __shfl_xor_sync(0xffffffffu, cm, o));
-            if (cm > 0.05f) thr = -sqrtf(fmaxf(0.f, 1.f - cm * cm)) - 1e-4f;
-        }
-        if (lane == 0) cone[ch] = make_float4(cx, cy, cz, thr);
-    }
-}
-
-template <int K>
-__device__ __forceinline__ bool chunk_below_horizon(const float4 *cone, int ch, const GaussIn<K> &q)
-{
-    const float4 c = cone[ch];
-    return q.n[0] * c.x + q.n[1] * c.y + q.n[2] * c.z < c.w;
-}
-
 // vis = sum_j ubar_j bit_j for this lane's light (Eq. 1 applied to v).
 template <int K>
 __device__ __forceinline__ float lane_vis(const ChunkBits<K> &cb, const GaussIn<K> &q, unsigned bit)
@@ -225,15 +184,12 @@ shade_kernel(avatar_shade_args s, ShadeBatch sb)
     float *radiance = s.radiance ? s.radiance + t.oy : nullptr;
     uint8_t *cull = s.cull ? s.cull + t.oy : nullptr;
     float4 *lw = lsm, *lb = lsm + NL;
-    __shared__ float4 cone[SHADE_MAX_CHUNKS];
     for (int k = threadIdx.x; k < NL; k += blockDim.x) {
         float A = __ldg(s.light_A + k);
         lw[k] = make_float4(__ldg(s.light_w + 3 * k), __ldg(s.light_w + 3 * k + 1), __ldg(s.light_w + 3 * k + 2), 0.f);
         lb[k] = make_float4(__ldg(light_L + 3 * k) * A, __ldg(light_L + 3 * k + 1) * A, __ldg(light_L + 3 * k + 2) * A,
                             0.f);
     }
-    __syncthreads();
-    chunk_cones(lw, NL, cone);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const unsigned bit = 1u << lane;
@@ -257,7 +213,6 @@ shade_kernel(avatar_shade_args s, ShadeBatch sb)
         const float ia0 = q.a[0] * (1.f / AV_PI), ia1 = q.a[1] * (1.f / AV_PI), ia2 = q.a[2] * (1.f / AV_PI);
         float L0 = 0.f, L1 = 0.f, L2 = 0.f;  // this lane's share of L_o
         for (int ch = 0; ch < OW; ++ch) {
-            if (chunk_below_horizon<K>(cone, ch, q)) continue;  // warp-uniform
             const int k = ch * 32 + lane;
             float vis;
             if constexpr (SOFT) {
@@ -344,9 +299,6 @@ shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr, ShadeBatch sb)
                             0.f);
     }
     for (int i = threadIdx.x; i < copies * NL; i += blockDim.x) dBall[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    __shared__ float4 cone[SHADE_MAX_CHUNKS];
-    __syncthreads();
-    chunk_cones(lw, NL, cone);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const unsigned bit = 1u << lane;
@@ -454,7 +406,6 @@ shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr, ShadeBatch sb)
         };
         if constexpr (SOFT) {
             for (int ch = 0; ch < OW; ++ch) {
-                if (chunk_below_horizon<K>(cone, ch, q)) continue;  // warp-uniform
                 const int k = ch * 32 + lane;
                 if (k >= NL) continue;
                 float cj[K];
@@ -482,7 +433,6 @@ shade_backward_kernel(avatar_shade_args s, avatar_shade_grads gr, ShadeBatch sb)
             };
             int qn = 0;  // warp-uniform
             for (int ch = 0; ch < OW; ++ch) {
-                if (chunk_below_horizon<K>(cone, ch, q)) continue;  // warp-uniform
                 const int k = ch * 32 + lane;
                 ChunkBits<K> cb;
                 load_chunk<K>(bits, q, OW, ch, cb);

@@ -298,7 +298,7 @@ __global__ void vis_chunk_ranges_kernel(const int32_t *__restrict__ faces, int F
 // two CTAs per SM, so 512 threads keep the resident warps of 8-CTA clusters
 // of 256); at most 64 registers either way.
 template <int CL, bool CULL_BACK, bool BATCH, int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT)
+__global__ void __launch_bounds__(NT, NT == 512 ? 2 : 4)
 vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *__restrict__ faces,
                        const int32_t *__restrict__ pfaces, const int2 *__restrict__ vranges,
                        const float *__restrict__ frames, uint32_t *__restrict__ dirbits, int32_t *status)
