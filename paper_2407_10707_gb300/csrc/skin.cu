@@ -18,6 +18,11 @@
 namespace {
 
 constexpr int SKIN_THREADS = 256;
+// The vertex kernel recomputes forward kinematics in every block, then each
+// thread blends one vertex's transform; small blocks spread the 50k
+// vertices of the paper-scale mesh over every SM (196 blocks of 256 would
+// leave most SMs with one).
+constexpr int SKIN_VTX_THREADS = 64;
 constexpr int MAX_J = 64;
 
 struct VertexRec {  // 7 x float4 = 112 bytes
@@ -117,7 +122,7 @@ __device__ void fk_shared(int J, const int32_t *parents, const float *joints, co
 
 // blockIdx.y = pose of a batch of gridDim.y poses (pose [B][J][3], bone
 // [B][J][12], xp [3][B Nv], records [B Nv]).
-__global__ void __launch_bounds__(SKIN_THREADS)
+__global__ void __launch_bounds__(SKIN_VTX_THREADS)
 skin_vertices_kernel(avatar_skin_args a, VertexRec *__restrict__ rec)
 {
     __shared__ float bone_s[MAX_J * 12];
@@ -644,7 +649,7 @@ int skin_run(avatar_ctx *ctx, const avatar_skin_args *a, int B, void *ws, size_t
     if (!ws || (((uintptr_t)ws) & 255) || ws_bytes < av_align256((size_t)B * a->Nv * sizeof(VertexRec)))
         return AVATAR_ERR_WORKSPACE;
     VertexRec *rec = (VertexRec *)ws;
-    skin_vertices_kernel<<<dim3(grid_for(ctx, a->Nv, SKIN_THREADS), B), SKIN_THREADS, 0, st>>>(*a, rec);
+    skin_vertices_kernel<<<dim3(grid_for(ctx, a->Nv, SKIN_VTX_THREADS), B), SKIN_VTX_THREADS, 0, st>>>(*a, rec);
     AV_CHECK_LAUNCH();
     if (a->G > 0) {
         int grid = grid_for(ctx, a->G, SKIN_THREADS);
