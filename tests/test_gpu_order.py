@@ -94,14 +94,6 @@ def test_gather_records(gpu, m):
     assert torch.equal(dst.cpu(), src.cpu()[:, order.cpu().long(), :])
 
 
-def test_patch_order_is_a_permutation_of_4x8_blocks():
-    o = synth.latlong_patch_order(16, 32)
-    assert np.array_equal(np.sort(o), np.arange(512))
-    first = o[:32]
-    assert np.array_equal(np.unique(first // 32), np.arange(4)) and np.array_equal(np.unique(first % 32), np.arange(8))
-    assert np.array_equal(synth.latlong_patch_order(6, 10), np.arange(60))   # no 4 x 8 split: identity
-
-
 def test_light_ordered_frame_meets_the_oracle_on_the_reordered_light(gpu):
     """The small frame (8 x 16 light) with its texels in 4 x 8 patches and
     the Gaussians in nearest-vertex order: every stage meets the oracle run
