@@ -886,7 +886,7 @@ def _form_batch(args, dev, reps):
     for v in range(3):
         p = int(b.view_pose[v])
         scv = dataclasses.replace(b.scene, avatar=dataclasses.replace(b.scene.avatar, pose=b.poses[p]),
-                                  light=synth.Light(L=b.lights[p], A=b.scene.light.A, w=b.scene.light.w),
+                                  light=dataclasses.replace(b.scene.light, L=b.lights[p]),
                                   camera=b.cameras[v])
         stv = stored_for_speed(render, synth, scv, dev)
         rv = render.Renderer(stv, tile=args.tile)

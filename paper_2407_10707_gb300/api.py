@@ -689,6 +689,8 @@ def gather_columns(src, order, status=None):
         n = src.shape[-1]
         rows = src.numel() // max(n, 1)
         elem = src.element_size()
+    if order.dim() != 1 or order.numel() != n:
+        raise ValueError(f"order of {order.numel()} entries for {n} columns")
     dst = torch.empty_like(src)
     L.check(L.load().avatar_gather_columns(context(), rows, n, elem, _p(src), _p(dst), _p(order), _p(status),
                                            _stream()), "avatar_gather_columns")

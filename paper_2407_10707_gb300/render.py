@@ -67,6 +67,8 @@ def light_ordered(st, order, status=None):
     dev = st["light"]["L"].device
     o = torch.as_tensor(np.ascontiguousarray(order, dtype=np.int32), device=dev)
     lt = st["light"]
+    if o.dim() != 1 or o.numel() != lt["A"].numel():
+        raise ValueError(f"light order of {o.numel()} entries for {lt['A'].numel()} texels")
     st2 = dict(st)
     st2["light"] = dict(L=api.gather_columns(lt["L"].reshape(1, -1, 3), o, status).reshape(lt["L"].shape),
                         A=api.gather_columns(lt["A"], o, status),

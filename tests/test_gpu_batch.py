@@ -44,7 +44,7 @@ def view_scene(b, v):
     p = int(b.view_pose[v])
     sc = b.scene
     av = dataclasses.replace(sc.avatar, pose=b.poses[p])
-    light = synth.Light(L=b.lights[p], A=sc.light.A, w=sc.light.w)
+    light = dataclasses.replace(sc.light, L=b.lights[p])
     return dataclasses.replace(sc, avatar=av, light=light, camera=b.cameras[v])
 
 
