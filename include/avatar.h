@@ -206,18 +206,6 @@ size_t avatar_skin_workspace_size(const avatar_skin_args *a);
 int avatar_skin(avatar_ctx *ctx, const avatar_skin_args *a, void *ws, size_t ws_bytes,
                 avatar_stream_t stream);
 
-/* The two halves of avatar_skin for a caller that schedules them apart.
- * AVATAR_SKIN_VERTICES: bones, posed vertices xp and the per-vertex records
- * in ws (everything the visibility pass reads is ready after this half).
- * AVATAR_SKIN_GAUSSIANS: every per-Gaussian output (xd, cov, nd, ag, rg,
- * pg, ubar) from the records in ws; the vertex half must have completed on
- * the device first (the same stream, or an event the stream waits for).
- * parts = AVATAR_SKIN_VERTICES | AVATAR_SKIN_GAUSSIANS is avatar_skin.
- * AVATAR_ERR_INVALID_ARG for parts outside 1..3; otherwise as avatar_skin. */
-enum { AVATAR_SKIN_VERTICES = 1, AVATAR_SKIN_GAUSSIANS = 2 };
-int avatar_skin_parts(avatar_ctx *ctx, const avatar_skin_args *a, int parts, void *ws, size_t ws_bytes,
-                      avatar_stream_t stream);
-
 typedef struct {
     /* upstream gradients ([.][G]); NULL = zero.  d_xd2 is a second upstream
      * gradient of x_gd (splatting and shading both reach x_gd); it is added

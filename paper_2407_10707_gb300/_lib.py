@@ -27,7 +27,6 @@ TUNE_BLEND_BWD_PPT = 1
 TUNE_BATCH_TILE = 2
 TUNE_VIS_CLUSTER = 3
 TUNE_WAIT_LIMIT = 4
-SKIN_VERTICES, SKIN_GAUSSIANS = 1, 2   # the halves of avatar_skin_parts
 PROBE_FFMA, PROBE_IADD3, PROBE_LOP3, PROBE_IMAD = 0, 1, 2, 3   # avatar_probe_kind
 
 
@@ -167,7 +166,6 @@ _SIGNATURES = [
     ("avatar_ctx_get_tuning", [P, I32], I32),
     ("avatar_skin_workspace_size", [C.POINTER(SkinArgs)], C.c_size_t),
     ("avatar_skin", [P, C.POINTER(SkinArgs), P, C.c_size_t, P], I32),
-    ("avatar_skin_parts", [P, C.POINTER(SkinArgs), I32, P, C.c_size_t, P], I32),
     ("avatar_skin_backward_workspace_size", [C.POINTER(SkinArgs)], C.c_size_t),
     ("avatar_skin_backward", [P, C.POINTER(SkinArgs), C.POINTER(SkinGrads), P, P, C.c_size_t, P], I32),
     ("avatar_visibility_workspace_size", [C.POINTER(VisArgs)], C.c_size_t),

@@ -133,25 +133,17 @@ def alloc_skin_outputs(t):
                 ubar=e(K, G))
 
 
-def avatar_skin(t, out=None, ws=None, status=None, parts=None):
+def avatar_skin(t, out=None, ws=None, status=None):
     """(a) Skinning (Sec. 3.1, Eq. 1).  Returns the output dict; out['_ws']
-    holds the workspace the backward needs.  parts = L.SKIN_VERTICES or
-    L.SKIN_GAUSSIANS runs one half (avatar_skin_parts): the Gaussian half
-    reads the records the vertex half left in ws, so pass the same ws."""
+    holds the workspace the backward needs."""
     lib = L.load()
     ctx = context()
     out = alloc_skin_outputs(t) if out is None else out
     a = _skin_struct(t, out, status)
     need = lib.avatar_skin_workspace_size(C.byref(a))
     if ws is None or ws.numel() < need:
-        if parts == L.SKIN_GAUSSIANS:
-            raise ValueError("the Gaussian half of skinning needs the vertex half's workspace")
         ws = workspace(need, t["xg"].device)
-    if parts is None:
-        L.check(lib.avatar_skin(ctx, C.byref(a), _p(ws), ws.numel(), _stream()), "avatar_skin")
-    else:
-        L.check(lib.avatar_skin_parts(ctx, C.byref(a), int(parts), _p(ws), ws.numel(), _stream()),
-                "avatar_skin_parts")
+    L.check(lib.avatar_skin(ctx, C.byref(a), _p(ws), ws.numel(), _stream()), "avatar_skin")
     out["_ws"] = ws
     return out
 

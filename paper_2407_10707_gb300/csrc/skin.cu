@@ -642,19 +642,16 @@ int grid_for(const avatar_ctx *ctx, long n, int threads)
 namespace {
 
 // Forward of B poses (see the batched launcher's declaration for layouts).
-int skin_run(avatar_ctx *ctx, const avatar_skin_args *a, int B, void *ws, size_t ws_bytes, cudaStream_t st,
-             int parts = AVATAR_SKIN_VERTICES | AVATAR_SKIN_GAUSSIANS)
+int skin_run(avatar_ctx *ctx, const avatar_skin_args *a, int B, void *ws, size_t ws_bytes, cudaStream_t st)
 {
-    if (!ctx || B < 1 || B > 65535 || parts < 1 || parts > 3) return AVATAR_ERR_INVALID_ARG;
+    if (!ctx || B < 1 || B > 65535) return AVATAR_ERR_INVALID_ARG;
     AV_TRY(check_skin_args(a));
     if (!ws || (((uintptr_t)ws) & 255) || ws_bytes < av_align256((size_t)B * a->Nv * sizeof(VertexRec)))
         return AVATAR_ERR_WORKSPACE;
     VertexRec *rec = (VertexRec *)ws;
-    if (parts & AVATAR_SKIN_VERTICES) {
-        skin_vertices_kernel<<<dim3(grid_for(ctx, a->Nv, SKIN_VTX_THREADS), B), SKIN_VTX_THREADS, 0, st>>>(*a, rec);
-        AV_CHECK_LAUNCH();
-    }
-    if ((parts & AVATAR_SKIN_GAUSSIANS) && a->G > 0) {
+    skin_vertices_kernel<<<dim3(grid_for(ctx, a->Nv, SKIN_VTX_THREADS), B), SKIN_VTX_THREADS, 0, st>>>(*a, rec);
+    AV_CHECK_LAUNCH();
+    if (a->G > 0) {
         int grid = grid_for(ctx, a->G, SKIN_THREADS);
         switch (a->K) {
             case 1: launch_gauss_fwd<1>(*a, rec, B, grid, st); break;
@@ -747,12 +744,6 @@ extern "C" int avatar_skin(avatar_ctx *ctx, const avatar_skin_args *a, void *ws,
                            avatar_stream_t stream)
 {
     return skin_run(ctx, a, 1, ws, ws_bytes, (cudaStream_t)stream);
-}
-
-extern "C" int avatar_skin_parts(avatar_ctx *ctx, const avatar_skin_args *a, int parts, void *ws, size_t ws_bytes,
-                                 avatar_stream_t stream)
-{
-    return skin_run(ctx, a, 1, ws, ws_bytes, (cudaStream_t)stream, parts);
 }
 
 extern "C" size_t avatar_skin_backward_workspace_size(const avatar_skin_args *a)

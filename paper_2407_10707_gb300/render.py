@@ -80,9 +80,8 @@ def light_ordered(st, order, status=None):
 class Renderer:
     """Preallocated forward frame.  forward() launches exactly the library's
     kernels: on the current stream, except that with overlap (the default)
-    the Gaussian half of the skinning, cull, projection and binning run on a
-    second stream forked after the vertex half and joined before the blend
-    (same images).  vis_cull_back rasterises only light-facing
+    cull, projection and binning run on a second stream forked after skinning
+    and joined before the blend (same images).  vis_cull_back rasterises only light-facing
     triangles for visibility; it gives the same bits as the two-sided rule for
     closed, outward-wound meshes such as the capsule body (set it to False
     for open or inconsistently wound meshes).  shade_tc evaluates the shading
@@ -94,11 +93,10 @@ class Renderer:
     def __init__(self, st, tile=16, pair_capacity=None, vis_cull_back=True, shade_tc=False, visibility="depth",
                  knn_v=None, rebind=False, mlp=None, overlap=True):
         self.st = st
-        # overlap: after the vertex half of the skinning, the Gaussian half,
-        # cull, project and bin run on a second (high-priority) stream while
-        # visibility and shading run on the calling one; shading waits for
-        # the Gaussian half, the blend joins the streams (splatting needs
-        # only the cull flags and, in the blend, the colours from shading)
+        # overlap: after skinning, cull + project + bin run on a second
+        # (high-priority) stream while visibility and shading run on the
+        # calling one; the blend joins them (splatting needs only the cull
+        # flags and, in the blend, the colours from shading)
         self.overlap = overlap
         self.mlp = mlp
         self.mlp_ws = None
@@ -142,7 +140,6 @@ class Renderer:
         self.sb = api.alloc_splat(G, st["camera"], tile, pair_capacity, dev)
         self.cull_b = torch.empty(G, dtype=torch.uint8, device=dev)  # the binning branch's cull flags
         self._side = torch.cuda.Stream(device=dev, priority=-1) if overlap else None
-        self._skinned = torch.cuda.Event() if overlap else None
         self.graph = None
         # first eager call sizes the workspaces
         self.forward()
@@ -158,18 +155,13 @@ class Renderer:
             self.knn_ws = api.workspace(L.load().avatar_knn_workspace_size(C.byref(a)), self.device)
         api.avatar_knn(t["xg"], t["xv"], t["knn"].shape[0], out=t["knn"], ws=self.knn_ws, status=self.status)
 
-    def skin(self, parts=None):
-        """Skinning; parts = L.SKIN_VERTICES or L.SKIN_GAUSSIANS runs one half
-        (the rebinding and the displacement MLP go with the vertex half)."""
-        from . import _lib as L
-        if parts != L.SKIN_GAUSSIANS:
-            if self.rebind:
-                self.bind()
-            if self.mlp is not None:
-                t = self.skin_t
-                api.avatar_mlp(t["xv"], t["pose"].reshape(-1), self.mlp, dx=t["dxv"], ws=self.mlp_ws,
-                               status=self.status)
-        out = api.avatar_skin(self.skin_t, out=self.sk, ws=self.skin_ws, status=self.status, parts=parts)
+    def skin(self):
+        if self.rebind:
+            self.bind()
+        if self.mlp is not None:
+            t = self.skin_t
+            api.avatar_mlp(t["xv"], t["pose"].reshape(-1), self.mlp, dx=t["dxv"], ws=self.mlp_ws, status=self.status)
+        out = api.avatar_skin(self.skin_t, out=self.sk, ws=self.skin_ws, status=self.status)
         self.skin_ws = out["_ws"]
 
     def visibility(self):
@@ -235,30 +227,22 @@ class Renderer:
                          self.st["camera"], b=self.sb, status=self.status)
 
     def forward(self):
+        self.skin()
         if not self.overlap:
-            self.skin()
             self.visibility()
             self.shade()
             self.splat()
             return self.sb.image
-        from . import _lib as L
         t = self.st["avatar"]
         args = (self.sk["xd"], self.sk["cov"], t["opacity"], self.sh["color"], self.cull_b, self.st["camera"], self.sb,
                 self.status)
-        # visibility reads only the posed vertices: the Gaussian half of the
-        # skinning, projection and binning run on the side stream beside it,
-        # and shading waits for the Gaussian half alone
         main, side = torch.cuda.current_stream(), self._side
-        self.skin(parts=L.SKIN_VERTICES)
         side.wait_stream(main)
         with torch.cuda.stream(side):
-            self.skin(parts=L.SKIN_GAUSSIANS)
-            self._skinned.record(side)
             api.avatar_cull(self.sk, self.st["cam_center"], cull=self.cull_b)
             api.avatar_splat_project(*args)
             api.avatar_splat_bin(*args)
         self.visibility()
-        main.wait_event(self._skinned)
         self.shade()
         main.wait_stream(side)
         api.avatar_splat_blend(*args)

@@ -65,29 +65,6 @@ def test_skin_matches_oracle(gpu, name):
     assert rel_err(N(out["ubar"]).T, sk["ubar"]) < 1e-5
 
 
-def test_skin_halves_equal_the_whole(gpu):
-    """avatar_skin_parts: the vertex half then the Gaussian half (the same
-    workspace) write what avatar_skin writes, bit for bit; parts outside
-    1..3 are refused."""
-    api, render = gpu
-    from paper_2407_10707_gb300 import _lib as L
-    t = render.scene_tensors(scene("c3_fd"))["avatar"]
-    whole = api.avatar_skin(t)
-    halves = api.avatar_skin(t, parts=L.SKIN_VERTICES)
-    api.avatar_skin(t, out=halves, ws=halves["_ws"], parts=L.SKIN_GAUSSIANS)
-    torch.cuda.synchronize()
-    for k in ("bone", "xp", "xd", "cov", "nd", "ag", "rg", "pg", "ubar"):
-        assert torch.equal(whole[k], halves[k]), k
-    with pytest.raises(ValueError):
-        api.avatar_skin(t, parts=L.SKIN_GAUSSIANS)     # no records to read
-    a = api._skin_struct(t, halves, None)
-    import ctypes as C
-    for parts in (0, 4):
-        rc = L.load().avatar_skin_parts(api.context(), C.byref(a), parts, api._p(halves["_ws"]),
-                                        halves["_ws"].numel(), api._stream())
-        assert L.STATUS[rc] == "AVATAR_ERR_INVALID_ARG"
-
-
 def test_skin_bad_neighbour_index_sets_status(gpu):
     api, render = gpu
     st = render.scene_tensors(scene("c3_fd"))
@@ -203,10 +180,9 @@ def test_visibility_edge_cases(gpu):
 
 
 def test_overlapped_frame_equals_serial_frame(gpu):
-    """The Gaussian half of the skinning, projection and binning on a
-    second stream beside visibility and shading (avatar_cull's flags, colour
-    records completed by the blend) give the serial frame bit for bit,
-    eagerly and from a CUDA graph."""
+    """Projection and binning on a second stream beside visibility and
+    shading (avatar_cull's flags, colour records completed by the blend)
+    give the serial frame bit for bit, eagerly and from a CUDA graph."""
     api, render = gpu
     st = render.scene_tensors(scene("c1_small"))
     serial = render.Renderer(st, overlap=False)
