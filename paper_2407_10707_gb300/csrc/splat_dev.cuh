@@ -278,7 +278,11 @@ sort_hist_kernel(const uint32_t *__restrict__ keys, const int32_t *__restrict__ 
     }
 }
 
-__global__ void __launch_bounds__(OS_THREADS)
+// Four blocks per SM (64 registers, no spills): the pass is latency-bound on
+// its loads and look-back, and at the 119 registers it takes unbounded only
+// two blocks fit (paper-scale frame 1,058 -> 1,036 us, 128-view batch 56.8 ->
+// 55.3 ms, measured alternately in one session).
+__global__ void __launch_bounds__(OS_THREADS, 4)
 onesweep_kernel(const uint32_t *__restrict__ kin, const int32_t *__restrict__ vin, uint32_t *__restrict__ kout,
                 int32_t *__restrict__ vout, const int32_t *__restrict__ n_ptr, int cap, int shift,
                 const int32_t *__restrict__ hist, unsigned *__restrict__ desc, int32_t *__restrict__ ticket,

@@ -75,6 +75,90 @@ def test_fk_chain_closed_form():
     np.testing.assert_allclose(apply(2, joints[2]), [-1, 1, 0], atol=1e-14)
 
 
+def test_fk_chain_noncommuting_rotations():
+    """The parent's rotation acts after the child's (T_j = T_parent [R_j | J_j - J_parent]):
+    joint 0 turns 90 degrees about x, joint 1 (rest (1,0,0)) 90 degrees about z.
+    A point at (2,0,0) bound to joint 1 goes to J0 + R0 (R1 (x - J1) + (J1 - J0))
+    = R0 ((0,1,0) + (1,0,0)) = (1,0,1); the reversed product R1 R0 would give (1,1,0)."""
+    parents = np.array([-1, 0], np.int32)
+    joints = np.array([[0.0, 0, 0], [1.0, 0, 0]])
+    pose = np.array([[math.pi / 2, 0, 0], [0, 0, math.pi / 2]])
+    bone = O.fk(parents, joints, pose)
+    x = np.array([2.0, 0.0, 0.0])
+    np.testing.assert_allclose(bone[1, :, :3] @ x + bone[1, :, 3], [1, 0, 1], atol=1e-14)
+    np.testing.assert_allclose(bone[1, :, :3], rot([1, 0, 0], math.pi / 2) @ rot([0, 0, 1], math.pi / 2),
+                               atol=1e-14)
+
+
+def test_skin_eq1_inverse_distance_weights(small_avatar):
+    """Eq. 1: u_j = 1 / |x_g - x_j| over S_g, normalised.  Gaussian 0's four
+    neighbours are moved to distances 1, 2, 4 and 4 cm from it (in different
+    directions): ubar = (1, 1/2, 1/4, 1/4) / 2, and each interpolated
+    attribute is that mix of the neighbours' values (identity pose)."""
+    av = copy.deepcopy(small_avatar)
+    av.pose = np.zeros((24, 3))
+    nb = av.knn[0]
+    assert av.K == 4 and len(set(nb.tolist())) == 4
+    dirs = np.array([[1.0, 0, 0], [0, 1.0, 0], [0, 0, 1.0], [-1.0, 0, 0]])
+    for j, d in enumerate((1.0, 2.0, 4.0, 4.0)):
+        av.xv[nb[j]] = av.xg[0] + 0.01 * d * dirs[j]
+    sk = O.skin(av, O.fk(av.parents, av.joints, av.pose))
+    want = np.array([1.0, 0.5, 0.25, 0.25]) / 2.0
+    np.testing.assert_allclose(sk["ubar"][0], want, rtol=1e-13)
+    np.testing.assert_allclose(sk["ag"][0], want @ av.av[nb], rtol=1e-13)
+    np.testing.assert_allclose(sk["rg"][0], want @ av.rv[nb], rtol=1e-13)
+    np.testing.assert_allclose(sk["pg"][0], want @ av.pv[nb], rtol=1e-13)
+    np.testing.assert_allclose(sk["wg"][0], want @ av.wv[nb], rtol=1e-12, atol=1e-15)
+
+
+def test_skin_covariance_of_a_known_rotation(small_avatar):
+    """Sigma = R(q) S^2 R(q)^T, q = (w, x, y, z) in the 3DGS convention:
+    q = (cos t/2, 0, 0, sin t/2) turns by +t about +z.  At t = 45 degrees with
+    scales s1 != s2 the xy term is (s1^2 - s2^2) / 2 (its sign fixes the
+    direction of the turn); a quaternion of norm 3 gives the same (identity
+    pose, so the blended transform is the identity)."""
+    av = copy.deepcopy(small_avatar)
+    av.pose = np.zeros((24, 3))
+    s = np.array([0.02, 0.005, 0.01])
+    q = np.array([math.cos(math.pi / 8), 0.0, 0.0, math.sin(math.pi / 8)])
+    av.logscale[0] = av.logscale[1] = np.log(s)
+    av.quat[0], av.quat[1] = q, 3.0 * q
+    sk = O.skin(av, O.fk(av.parents, av.joints, av.pose))
+    a, b, c = s ** 2
+    want = [(a + b) / 2, (a - b) / 2, 0.0, (a + b) / 2, 0.0, c]
+    for g in (0, 1):
+        np.testing.assert_allclose(sk["cov"][g], want, rtol=1e-12, atol=1e-19)
+
+
+def test_skin_displacement_moves_vertices_and_gaussians(small_avatar):
+    """The displacement is interpolated by Eq. 1 like every attribute, and
+    skinning moves x + dx: at the identity pose xp = x_v + dx_v and
+    x_gd = x_g + sum_j ubar_j dx_j (ubar pinned above)."""
+    av = copy.deepcopy(small_avatar)
+    av.pose = np.zeros((24, 3))
+    av.dxv = np.random.default_rng(8).normal(scale=0.01, size=av.xv.shape)
+    sk = O.skin(av, O.fk(av.parents, av.joints, av.pose))
+    np.testing.assert_allclose(sk["xp"], av.xv + av.dxv, atol=1e-14)
+    want = av.xg + np.einsum("gk,gkc->gc", sk["ubar"], av.dxv[av.knn])
+    np.testing.assert_allclose(sk["xd"], want, atol=1e-14)
+
+
+def test_skin_normals_under_a_blended_pose(small_avatar):
+    """Under a pose whose blended transforms are not rotations (the avatar's
+    random +-30 degree pose), n_gd is still a unit vector along M n_g with M
+    the blended linear part sum_k w_gk G_k and n_g = normalize(sum_j ubar_j
+    n_j) (Eq. 1; w_g and ubar pinned above)."""
+    av = small_avatar
+    bone = O.fk(av.parents, av.joints, av.pose)
+    sk = O.skin(av, bone)
+    nbar = np.einsum("gk,gkc->gc", sk["ubar"], av.nv[av.knn])
+    M = np.einsum("gk,kij->gij", sk["wg"], bone[:, :, :3])
+    m = np.einsum("gij,gj->gi", M, nbar)
+    assert np.max(np.abs(np.linalg.norm(m, axis=1) / np.linalg.norm(nbar, axis=1) - 1)) > 1e-3   # not rotations
+    np.testing.assert_allclose(np.linalg.norm(sk["nd"], axis=1), 1.0, atol=1e-14)
+    np.testing.assert_allclose(sk["nd"], m / np.linalg.norm(m, axis=1, keepdims=True), atol=1e-13)
+
+
 def test_skin_identity_pose(small_avatar):
     av = copy.deepcopy(small_avatar)
     av.pose = np.zeros((24, 3))
@@ -256,6 +340,37 @@ def test_visibility_depth_map_of_a_plane():
     assert np.max(np.abs(d0[jj, ii] - expect)) < 40.0   # ~0.6 mm: fixed-point steps
 
 
+def test_visibility_covers_exactly_the_pixel_centres_inside():
+    """A triangle covers a depth-map pixel iff the pixel's centre lies inside
+    it (all three edge functions >= 0): compared with an FP64 barycentric
+    test of every centre, leaving out centres within 0.1 pixel of an edge
+    (the vertices are placed in 1/16-pixel steps, which decide those)."""
+    xp = np.array([[-0.41, -0.37, 0.0], [0.45, -0.12, 0.1], [-0.08, 0.43, -0.1]])
+    faces = np.array([[0, 1, 2]], np.int32)
+    dirs = np.zeros((32, 3))
+    dirs[:, 2] = 1
+    fr = _frames_for(dirs)
+    R, half = 64, 0.75
+    _, depth = O.visibility(xp, faces, fr, [0, 0, 0], half, 0.0, R, want_depth=True)
+    covered = depth[0] != np.iinfo(np.int32).max
+    e1, e2, _ = fr[0].reshape(3, 3)
+    st = np.c_[xp @ e1, xp @ e2] / (2 * half / R)            # vertices in pixel units
+    st += R / 2
+    jj, ii = np.mgrid[0:R, 0:R]
+    P = np.stack([ii + 0.5, jj + 0.5], -1)
+
+    def edge(a, b):
+        d = st[b] - st[a]
+        return (d[0] * (P[..., 1] - st[a][1]) - d[1] * (P[..., 0] - st[a][0])) / np.hypot(*d)
+    E = np.stack([edge(1, 2), edge(2, 0), edge(0, 1)])
+    if np.sum(E > 0) < np.sum(E < 0):
+        E = -E
+    inside = np.all(E >= 0, axis=0)
+    sure = np.all(np.abs(E) > 0.1, axis=0)
+    assert inside.sum() > 300
+    np.testing.assert_array_equal(covered[sure], inside[sure])
+
+
 def test_visibility_rejects_unsupported_arguments():
     xp = np.zeros((3, 3))
     faces = np.array([[0, 1, 2]], np.int32)
@@ -326,6 +441,36 @@ def test_shade_visibility_is_linear_in_the_bits():
     bits2 = np.concatenate([mask, ~mask])
     _, r_mix, _ = O.shade(xd, nd, a, r, p, ub2, knn2, bits2, lt.L, lt.A, lt.w, dmap, cam, 128)
     np.testing.assert_allclose(r_mix, 0.25 * r_m + 0.75 * r_c, rtol=1e-13)
+
+
+def test_shade_light_reads_the_bit_of_its_viewpoint():
+    """Light k takes bit d(k) = dmap[k] of each neighbour's words (word d/32,
+    bit d%32).  One light whose viewpoint is direction 77 of 128 is lit with
+    bit 77 alone set and dark with every bit but 77; and shading under a
+    permuted dmap equals shading under the identity map of words whose bit k
+    is bit dmap[k] of the original."""
+    n = np.array([0.3, 0.2, 0.9])
+    n /= np.linalg.norm(n)
+    xd, nd, a, r, p, ub, knn = _one_gaussian(n, spec=0.5)
+    cam = 4.0 * n
+    L, A, w = np.array([[1.0, 0.5, 0.25]]), np.array([0.1]), n[None]
+    only = np.zeros((1, 4), np.uint32)
+    only[0, 77 // 32] = np.uint32(1 << (77 % 32))
+    _, lit, _ = O.shade(xd, nd, a, r, p, ub, knn, only, L, A, w, np.array([77], np.int32), cam, 128)
+    _, dark, _ = O.shade(xd, nd, a, r, p, ub, knn, ~only, L, A, w, np.array([77], np.int32), cam, 128)
+    _, full, _ = O.shade(xd, nd, a, r, p, ub, knn, np.full((1, 4), 0xFFFFFFFF, np.uint32), L, A, w,
+                         np.array([77], np.int32), cam, 128)
+    assert np.all(lit[0] > 0) and np.all(dark[0] == 0)
+    np.testing.assert_array_equal(lit, full)
+    rng = np.random.default_rng(9)
+    lt = synth.latlong_light(rng, 8, 16)
+    perm = rng.permutation(128).astype(np.int32)
+    words = rng.integers(0, 2 ** 32, size=(1, 4), dtype=np.uint64).astype(np.uint32)
+    bitv = np.unpackbits(words.view(np.uint8), bitorder="little")
+    moved = np.packbits(bitv[perm], bitorder="little").view(np.uint32)[None]
+    _, r1, _ = O.shade(xd, nd, a, r, p, ub, knn, words, lt.L, lt.A, lt.w, perm, cam, 128)
+    _, r2, _ = O.shade(xd, nd, a, r, p, ub, knn, moved, lt.L, lt.A, lt.w, np.arange(128, dtype=np.int32), cam, 128)
+    np.testing.assert_allclose(r1, r2, rtol=1e-13)
 
 
 def test_shade_normal_incidence_closed_form():
@@ -591,6 +736,17 @@ def test_composite_one_and_two_gaussians_closed_form():
         np.testing.assert_allclose(rgb[0], col[f] * af + col[b] * ab * (1 - af), rtol=1e-14)
         np.testing.assert_allclose(T[0], (1 - af) * (1 - ab), rtol=1e-14)
         assert cnt[0] == 2
+
+
+def test_composite_alpha_is_clamped_at_0_99():
+    """An opaque Gaussian (o = 1) centred on a pixel centre: alpha =
+    min(0.99, 1) = 0.99, so that pixel's colour is 0.99 c and T = 0.01."""
+    col = np.array([[0.4, 0.8, 0.2]])
+    rgb, T, cnt, _ = O.composite(np.array([[8.5, 8.5]]), np.array([[0.2, 0.0, 0.2]]), np.array([1.0]), col,
+                                 np.array([1.0]), [1], 16, 16, np.array([8 * 16 + 8]))
+    np.testing.assert_allclose(rgb[0], 0.99 * col[0], rtol=1e-15)
+    np.testing.assert_allclose(T[0], 0.01, rtol=1e-13)
+    assert cnt[0] == 1
 
 
 def test_composite_weights_sum_to_at_most_one_and_stop_rule():
