@@ -167,3 +167,115 @@ def test_every_unmutated_pin_passes_through_the_same_loader(tmp_path, monkeypatc
     monkeypatch.setattr(O, "_lib", None)
     for name in sorted({p for m in MUTATIONS for p in m[3]}):
         _run_pin(name)
+
+
+# ---------------------------------------------------------------- the Python oracles
+# (module, id, source text, planted text, pins to run, pin that must fail)
+ADJ_PINS = ("test_adjoint_forward_agrees_with_c_oracle", "test_adjoint_matches_central_finite_differences")
+SSIM_PINS = ("test_ssim_identity_symmetry_and_constant_images", "test_ssim_of_a_constant_against_a_checkerboard",
+             "test_image_loss_weights_and_the_paper_lambda", "test_image_loss_gradient_matches_finite_differences")
+REG_PINS = ("test_regularizers_closed_forms", "test_regularizer_weights_are_the_papers",
+            "test_regularizer_gradients_match_finite_differences")
+MLP_PINS = ("test_mlp_matches_torch_layers_and_closed_forms",)
+DENS_PINS = ("test_densify_counts_and_densities", "test_densify_uniform_and_saturated_meshes",
+             "test_densify_sampling_follows_the_weights", "test_densify_places_points_uniformly_on_the_triangle")
+ADAM_PINS = ("test_adam_matches_torch_and_closed_forms",)
+
+PY_MUTATIONS = [
+    ("adjoint", "eq1_inverse_square", "u = 1.0 / torch.clamp(d, min=1e-8)", "u = 1.0 / torch.clamp(d * d, min=1e-8)",
+     ADJ_PINS, "test_adjoint_forward_agrees_with_c_oracle"),
+    ("adjoint", "specular_without_G1o", "(co[:, None] * (1.0 - kk) + kk))", "1.0)", ADJ_PINS,
+     "test_adjoint_forward_agrees_with_c_oracle"),
+    ("adjoint", "low_pass_dropped", "s00 = S2[:, 0, 0] + 0.3", "s00 = S2[:, 0, 0]", ADJ_PINS,
+     "test_adjoint_forward_agrees_with_c_oracle"),
+    ("adjoint", "transmittance_detached", "w = ai * Tex", "w = ai * Tex.detach()", ADJ_PINS,
+     "test_adjoint_matches_central_finite_differences"),
+    ("adjoint", "gamma_curve_detached", "col = torch.pow(torch.clamp(Lo, min=1e-6), 1.0 / 2.2)",
+     "col = torch.pow(torch.clamp(Lo.detach(), min=1e-6), 1.0 / 2.2) + 0.0 * Lo", ADJ_PINS,
+     "test_adjoint_matches_central_finite_differences"),
+    ("ssim", "c2_tenfold", "C2 = 0.03 ** 2", "C2 = 0.3 ** 2", SSIM_PINS,
+     "test_ssim_of_a_constant_against_a_checkerboard"),
+    ("ssim", "covariance_without_means", "sxy = _blur(x * y) - mx * my", "sxy = _blur(x * y)", SSIM_PINS,
+     "test_ssim_identity_symmetry_and_constant_images"),
+    ("ssim", "window_sigma", "SIGMA = 1.5", "SIGMA = 2.5", SSIM_PINS, "test_ssim_identity_symmetry_and_constant_images"),
+    ("ssim", "lambda_swapped", "return (1.0 - lam) * l1 + lam * (1.0 - ssim_map(img, target).mean())",
+     "return lam * l1 + (1.0 - lam) * (1.0 - ssim_map(img, target).mean())", SSIM_PINS,
+     "test_image_loss_weights_and_the_paper_lambda"),
+    ("ssim", "torch_loss_halved_dssim", "+ lam * (1.0 - s.mean())", "+ lam * (1.0 - s.mean()) / 2", SSIM_PINS,
+     "test_image_loss_gradient_matches_finite_differences"),
+    ("regularizers", "smooth_squared", "(av[:, None, :] - av[kv]).abs().sum()", "(av[:, None, :] - av[kv]).pow(2).sum()",
+     REG_PINS, "test_regularizers_closed_forms"),
+    ("regularizers", "scale_unclamped", "scale = torch.clamp(torch.exp(logscale) - s0, min=0.0).sum()",
+     "scale = (torch.exp(logscale) - s0).sum()", REG_PINS, "test_regularizers_closed_forms"),
+    ("regularizers", "mdist_squared", "mdist = torch.linalg.vector_norm(xg[:, None, :] - xv[kg], dim=-1).sum()",
+     "mdist = ((xg[:, None, :] - xv[kg]) ** 2).sum()", REG_PINS, "test_regularizers_closed_forms"),
+    ("regularizers", "smooth_weight", "WEIGHTS = dict(smooth=0.002,", "WEIGHTS = dict(smooth=0.02,", REG_PINS,
+     "test_regularizer_weights_are_the_papers"),
+    ("mlp", "fourier_without_2pi", "p = 2.0 * np.pi * (", "p = np.pi * (", MLP_PINS,
+     "test_mlp_matches_torch_layers_and_closed_forms"),
+    ("mlp", "cos_before_sin", "np.concatenate([np.sin(p), np.cos(p)], axis=1)",
+     "np.concatenate([np.cos(p), np.sin(p)], axis=1)", MLP_PINS, "test_mlp_matches_torch_layers_and_closed_forms"),
+    ("mlp", "last_layer_relu", "return r(h) @ r(W4).T + np.asarray(b4, np.float64)",
+     "return np.maximum(r(h) @ r(W4).T + np.asarray(b4, np.float64), 0.0)", MLP_PINS,
+     "test_mlp_matches_torch_layers_and_closed_forms"),
+    ("densify", "density_over_3kg", "df = S / (6.0 * Kg)", "df = S / (3.0 * Kg)", DENS_PINS,
+     "test_densify_counts_and_densities"),
+    ("densify", "triangle_search_left", 'i = int(np.searchsorted(cum, s, side="right"))',
+     'i = int(np.searchsorted(cum, s, side="left"))', DENS_PINS, "test_densify_sampling_follows_the_weights"),
+    ("densify", "no_fold_back", "if u + v > 1.0:", "if u + v > 2.0:", DENS_PINS,
+     "test_densify_places_points_uniformly_on_the_triangle"),
+    ("adam", "no_bias_correction", "mh = m / (1.0 - b1 ** t)", "mh = m", ADAM_PINS,
+     "test_adam_matches_torch_and_closed_forms"),
+    ("adam", "second_moment_unsquared", "v = b2 * np.asarray(v, np.float64) + (1.0 - b2) * g * g",
+     "v = b2 * np.asarray(v, np.float64) + (1.0 - b2) * np.abs(g)", ADAM_PINS,
+     "test_adam_matches_torch_and_closed_forms"),
+]
+
+
+def _mutant_module(modname, old, new):
+    import importlib.util
+    import types
+    spec = importlib.util.find_spec(f"oracle.{modname}")
+    src = open(spec.origin).read()
+    assert old == "" or src.count(old) == 1, f"{modname}: the source text to mutate is not unique"
+    mod = types.ModuleType(f"oracle.{modname}")
+    mod.__file__ = spec.origin
+    mod.__package__ = "oracle"
+    exec(compile(src.replace(old, new) if old else src, spec.origin, "exec"), mod.__dict__)
+    return mod
+
+
+@pytest.mark.parametrize("case", PY_MUTATIONS, ids=[f"{m[0]}-{m[1]}" for m in PY_MUTATIONS])
+def test_pins_catch_the_planted_mistake_in_the_python_oracles(case, monkeypatch):
+    import sys
+    import oracle as pkg
+    modname, mid, old, new, pins, expect = case
+    assert expect in pins
+    mut = _mutant_module(modname, old, new)
+    monkeypatch.setitem(sys.modules, f"oracle.{modname}", mut)
+    monkeypatch.setattr(pkg, modname, mut, raising=False)
+    if modname == "adjoint":
+        monkeypatch.setattr(PINS, "AJ", mut)
+    failed = []
+    for name in pins:
+        try:
+            _run_pin(name)
+        except (AssertionError, ValueError, FloatingPointError, ZeroDivisionError, RuntimeError):
+            failed.append(name)
+    assert expect in failed, f"{modname}/{mid}: {expect} passes the planted mistake (pins that failed: {failed})"
+
+
+def test_the_python_pins_pass_on_reloaded_unchanged_modules(monkeypatch):
+    """The harness itself: each module re-executed unchanged the same way
+    passes its pins."""
+    import sys
+    import oracle as pkg
+    for modname, pins in (("adjoint", ADJ_PINS), ("ssim", SSIM_PINS), ("regularizers", REG_PINS), ("mlp", MLP_PINS),
+                          ("densify", DENS_PINS), ("adam", ADAM_PINS)):
+        mod = _mutant_module(modname, "", "")
+        monkeypatch.setitem(sys.modules, f"oracle.{modname}", mod)
+        monkeypatch.setattr(pkg, modname, mod, raising=False)
+        if modname == "adjoint":
+            monkeypatch.setattr(PINS, "AJ", mod)
+        for name in pins:
+            _run_pin(name)

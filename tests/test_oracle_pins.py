@@ -21,9 +21,9 @@ from paper_2407_10707_gb300 import synth
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-def golden_constants():
+def golden_constants(name="app_a_brdf_constants.txt"):
     vals = {}
-    with open(os.path.join(GOLDEN, "app_a_brdf_constants.txt")) as f:
+    with open(os.path.join(GOLDEN, name)) as f:
         for line in f:
             line = line.split("#")[0].strip()
             if line:
@@ -1099,6 +1099,43 @@ def test_ssim_identity_symmetry_and_constant_images():
     np.testing.assert_allclose(g[4] / g[5], np.exp(-1 / (2 * 1.5 ** 2)), rtol=1e-14)
 
 
+def test_ssim_of_a_constant_against_a_checkerboard():
+    """x = a (constant), y = a + b (-1)^(i+j): with the normalised window's
+    alternating sum A = sum_k (-1)^k g_k, at an interior pixel of parity p
+    mu_y = a + b p A^2, sigma_y^2 = b^2 (1 - A^4), sigma_x = sigma_xy = 0, so
+    SSIM = (2 a mu_y + C1) C2 / ((a^2 + mu_y^2 + C1)(sigma_y^2 + C2)) with
+    C1 = 0.01^2 and C2 = 0.03^2 (the 3DGS constants, dynamic range 1)."""
+    from oracle import ssim as S
+    a, b, n = 0.5, 0.2, 40
+    ii, jj = np.mgrid[0:n, 0:n]
+    par = np.where((ii + jj) % 2 == 0, 1.0, -1.0)
+    x = np.full((1, n, n), a)
+    y = (a + b * par)[None]
+    g = S.gauss_1d()
+    A = np.sum(g * (-1.0) ** np.arange(len(g)))
+    mu = a + b * par * A * A
+    var = b * b * (1 - A ** 4)
+    c1, c2 = 0.01 ** 2, 0.03 ** 2
+    want = (2 * a * mu + c1) * c2 / ((a * a + mu * mu + c1) * (var + c2))
+    np.testing.assert_allclose(S.ssim_map(x, y)[0, 6:-6, 6:-6], want[6:-6, 6:-6], rtol=1e-10)
+
+
+def test_image_loss_weights_and_the_paper_lambda():
+    """L_img = (1 - lambda) L1 + lambda (1 - SSIM): lambda = 0 gives the mean
+    absolute error alone, lambda = 1 the D-SSIM alone, and the default is the
+    paper's lambda_img (tests/golden/sec33_loss_weights.txt)."""
+    import inspect
+    from oracle import ssim as S
+    rng = np.random.default_rng(14)
+    x = rng.uniform(0, 1, size=(3, 24, 20))
+    y = rng.uniform(0, 1, size=(3, 24, 20))
+    assert abs(S.image_loss(x, y, 0.0) - np.abs(x - y).mean()) < 1e-15
+    assert abs(S.image_loss(x, y, 1.0) - (1.0 - S.ssim_map(x, y).mean())) < 1e-15
+    lam = golden_constants("sec33_loss_weights.txt")["lambda_img"]
+    assert inspect.signature(S.image_loss).parameters["lam"].default == lam
+    assert abs(S.image_loss(x, y) - ((1 - lam) * np.abs(x - y).mean() + lam * (1 - S.ssim_map(x, y).mean()))) < 1e-15
+
+
 def test_image_loss_gradient_matches_finite_differences():
     from oracle import ssim as S
     rng = np.random.default_rng(13)
@@ -1124,17 +1161,26 @@ def test_regularizers_closed_forms():
     rv = np.array([0.3, 0.3, 0.6])
     pv = np.array([0.0, 1.0, 1.0])
     # smooth: pairs (0,1), (1,0), (2,1): |a| sums 0.4, 0.4, 0.7; |gamma| 0, 0, 0.3; |p| 1, 1, 0
-    xg = np.array([[0.0, 0, 0], [1.0, 1.0, 0]])
+    xg = np.array([[0.0, 0, 0], [1.0, 2.0, 0]])
     knn = np.array([[0], [1]])
     logscale = np.log(np.array([[0.004, 0.004, 0.004], [0.01, 0.002, 0.007]]))
     dxv = np.array([[0.0, 0, 0], [0.3, 0.4, 0], [0, 0, -2.0]])
     total, t, _ = RG.regularizers(xg, logscale, knn, xv, av, rv, pv, knn_v, dxv)
     assert abs(t["smooth"] - (0.4 + 0.4 + 0.7 + 0.3 + 2.0)) < 1e-12
-    assert abs(t["mdist"] - 1.0) < 1e-12                       # Gaussian 0 sits on its vertex, Gaussian 1 at 1
+    assert abs(t["mdist"] - 2.0) < 1e-12                       # Gaussian 0 sits on its vertex, Gaussian 1 at 2
     assert abs(t["disp"] - (0.5 + 2.0)) < 1e-12
     assert abs(t["scale"] - (0.005 + 0.002)) < 1e-12          # only 0.01 and 0.007 exceed s0 = 0.005
     w = RG.WEIGHTS
     assert abs(total - sum(w[k] * t[k] for k in t)) < 1e-12
+
+
+def test_regularizer_weights_are_the_papers():
+    """The weights and the scale threshold printed in Sec. 3.3
+    (tests/golden/sec33_loss_weights.txt)."""
+    from oracle import regularizers as RG
+    gc = golden_constants("sec33_loss_weights.txt")
+    assert RG.S0 == gc["s0"]
+    assert RG.WEIGHTS == {k: gc["lambda_" + k] for k in ("smooth", "mdist", "disp", "scale")}
 
 
 def test_regularizer_gradients_match_finite_differences():
