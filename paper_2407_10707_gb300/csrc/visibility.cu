@@ -144,10 +144,9 @@ __device__ __forceinline__ void raster_triangle(uint2 pa, uint2 pb, uint2 pc, in
     int bx = pb.x & 0xffff, by = pb.x >> 16, bz = (int)pb.y;
     int cx = pc.x & 0xffff, cy = pc.x >> 16, cz = (int)pc.y;
     const int R = p.R;
-    // pixel centres 16i+8 inside the bounding box; most triangles have none
-    int i0 = max(0, (min(ax, min(bx, cx)) + 7) >> 4), i1 = min(R - 1, (max(ax, max(bx, cx)) - 8) >> 4);
-    int j0 = max(0, (min(ay, min(by, cy)) + 7) >> 4), j1 = min(R - 1, (max(ay, max(by, cy)) - 8) >> 4);
-    if (i0 > i1 || j0 > j1) return;
+    // orientation first (two products: it drops the half of the triangles
+    // that face away before the costlier box), then the pixel centres 16i+8
+    // inside the bounding box (most triangles have none)
     int area = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
     if (CULL_BACK) {
         if (area <= 0) return;  // faces away from the light (outward winding)
@@ -161,6 +160,9 @@ __device__ __forceinline__ void raster_triangle(uint2 pa, uint2 pb, uint2 pc, in
             area = -area;
         }
     }
+    int i0 = max(0, (min(ax, min(bx, cx)) + 7) >> 4), i1 = min(R - 1, (max(ax, max(bx, cx)) - 8) >> 4);
+    int j0 = max(0, (min(ay, min(by, cy)) + 7) >> 4), j1 = min(R - 1, (max(ay, max(by, cy)) - 8) >> 4);
+    if (i0 > i1 || j0 > j1) return;
     // depth = az + floor((wb (bz - az) + wc (cz - az)) / area) since wa + wb + wc = area;
     // 32-bit arithmetic when the products provably fit, else 64-bit
     const int dzb = bz - az, dzc = cz - az;
