@@ -82,6 +82,31 @@ __device__ __forceinline__ float warp_reduce_scatter16(const float (&v)[16])
     return s + __shfl_xor_sync(0xffffffffu, s, 1);
 }
 
+// Warp sums of nine per-lane values: v[0..7] by recursive halving (lanes
+// 4i .. 4i + 3 end with the total of v[i], i = lane / 4) and v[8] by a
+// butterfly (every lane ends with its total): 14 shuffles, where padding to
+// sixteen slots for warp_reduce_scatter16 takes 16 and twice the selects.
+__device__ __forceinline__ float warp_reduce_scatter9(const float (&v)[9], float &tot8)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const bool b4 = lane & 16u, b3 = lane & 8u, b2 = lane & 4u;
+    float w[4], u[2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        w[i] = (b4 ? v[4 + i] : v[i]) + __shfl_xor_sync(0xffffffffu, b4 ? v[i] : v[4 + i], 16);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        u[i] = (b3 ? w[2 + i] : w[i]) + __shfl_xor_sync(0xffffffffu, b3 ? w[i] : w[2 + i], 8);
+    float t = (b2 ? u[1] : u[0]) + __shfl_xor_sync(0xffffffffu, b2 ? u[0] : u[1], 4);
+    t += __shfl_xor_sync(0xffffffffu, t, 2);
+    t += __shfl_xor_sync(0xffffffffu, t, 1);
+    float e = v[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    tot8 = e;
+    return t;
+}
+
 __device__ __forceinline__ unsigned lanemask_lt()
 {
     unsigned m;

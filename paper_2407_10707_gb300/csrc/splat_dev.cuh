@@ -753,8 +753,8 @@ __device__ __forceinline__ void emit_pairs_warp(int n, long off, int gval, int t
 // walked, and the lanes test the batch's rects against the box for a hit
 // mask, so no warp waits for another.  Per hit Gaussian the warp's nine sums
 // (d_color [3][cs], d_opacity [cs], d_mean2d [2][cs], d_conic [3][cs] at the
-// Gaussian's pair value) are reduced together by recursive halving and added
-// by nine lanes with one atomic each.
+// Gaussian's pair value) are reduced together (eight by recursive halving,
+// the ninth by a butterfly) and added by nine lanes with one atomic each.
 template <int TS, int PPT>
 __device__ __forceinline__ void blend_backward_box(int2 rg, const int32_t *__restrict__ pair_gauss,
                                                    const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
@@ -851,7 +851,7 @@ __device__ __forceinline__ void blend_backward_box(int2 rg, const int32_t *__res
                 float raw = exp2f(l2a);
                 float alpha = fminf(0.99f, raw);
                 contrib = true;
-                T[k] = T[k] / (1.f - alpha);
+                T[k] = __fdividef(T[k], 1.f - alpha);  // 1 - alpha >= 0.01: the fast form is within 2 ulp
                 float wgt = alpha * T[k];
                 g_col0 = fmaf(wgt, dC0[k], g_col0);
                 g_col1 = fmaf(wgt, dC1[k], g_col1);
@@ -872,17 +872,19 @@ __device__ __forceinline__ void blend_backward_box(int2 rg, const int32_t *__res
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-                const float v[16] = {g_col0, g_col1, g_col2, g_op, g_mx, g_my, g_ca, g_cb, g_cc,
-                                     0.f,    0.f,    0.f,    0.f,  0.f,  0.f,  0.f};
-                const float tot = warp_reduce_scatter16(v);
-                const int vi = lane >> 1;
-                if (!(lane & 1) && vi < 9) {
-                    const size_t g = (size_t)sg[b][sj];
+                const float v[9] = {g_col0, g_col1, g_col2, g_op, g_mx, g_my, g_ca, g_cb, g_cc};
+                float tot_cc;
+                const float tot = warp_reduce_scatter9(v, tot_cc);
+                const size_t g = (size_t)sg[b][sj];
+                if ((lane & 3) == 0) {
+                    const int vi = lane >> 2;
                     float *dst = vi < 3   ? d_color + (size_t)vi * cs
                                  : vi == 3 ? d_opacity
                                  : vi < 6  ? d_mean2d + (size_t)(vi - 4) * cs
                                            : d_conic + (size_t)(vi - 6) * cs;
                     atomicAdd(dst + g, vi == 3 ? tot / c.w : tot);
+                } else if (lane == 1) {
+                    atomicAdd(d_conic + 2 * cs + g, tot_cc);
                 }
             }
         }
