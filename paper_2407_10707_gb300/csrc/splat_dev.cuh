@@ -636,22 +636,24 @@ __device__ __forceinline__ void blend_box(int2 rg, const int32_t *__restrict__ p
                       (int)((unsigned)ra >> 16) <= by1;
             }
             unsigned hits = __ballot_sync(0xffffffffu, hit);
-            // one Gaussian's contribution to pixel k (the front-to-back step)
+            // one Gaussian's contribution to pixel k (the front-to-back step),
+            // without branches: a lane that does not take the Gaussian adds
+            // zero weight and keeps its T and last index (the same values the
+            // branching form leaves)
             auto step = [&](int sj, int k, float l2a) {
-                if (l2a < LOG2_ALPHA_MIN) return;
-                float alpha = fminf(0.99f, exp2f(l2a));
-                float test_T = T[k] * (1.f - alpha);
-                if (test_T < T_MIN) {
-                    live[k] = false;
-                    return;
-                }
+                const bool reach = live[k] && l2a >= LOG2_ALPHA_MIN;
+                const float alpha = fminf(0.99f, exp2f(l2a));
+                const float test_T = T[k] * (1.f - alpha);
+                const bool stop = test_T < T_MIN;
+                const bool take = reach && !stop;
+                live[k] = live[k] && !(reach && stop);
                 const float4 c = s2[b][sj];
-                float wgt = alpha * T[k];
+                const float wgt = take ? alpha * T[k] : 0.f;
                 C0[k] = fmaf(c.x, wgt, C0[k]);
                 C1[k] = fmaf(c.y, wgt, C1[k]);
                 C2[k] = fmaf(c.z, wgt, C2[k]);
-                T[k] = test_T;
-                last[k] = base + sj + 1;
+                T[k] = take ? test_T : T[k];
+                last[k] = take ? base + sj + 1 : last[k];
             };
             auto l2alpha = [&](int sj, int k) {
                 const float4 r0 = s0[b][sj];
@@ -668,11 +670,12 @@ __device__ __forceinline__ void blend_box(int2 rg, const int32_t *__restrict__ p
                 if (two) hits &= hits - 1;
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    if (!live[k]) continue;
                     const float a0 = l2alpha(j0, k);
                     const float a1 = two ? l2alpha(j1, k) : -1e30f;
+                    // the warp skips the pair where no live pixel reaches alpha 1/255
+                    if (!__any_sync(0xffffffffu, live[k] && fmaxf(a0, a1) >= LOG2_ALPHA_MIN)) continue;
                     step(j0, k, a0);
-                    if (live[k]) step(j1, k, a1);
+                    step(j1, k, a1);
                 }
                 any_live = false;
 #pragma unroll
