@@ -387,7 +387,10 @@ def num_tiles(width, height, tile):
 def alloc_splat(G, cam, tile=16, pair_capacity=None, device="cuda"):
     tile = tile or 16
     W, H = int(cam.width), int(cam.height)
-    cap = int(pair_capacity or max(1 << 16, 32 * G))
+    # default pair capacity: 32 tiles per Gaussian at 16-pixel tiles, four
+    # times that at 8 (a Gaussian's tile count grows with the inverse square
+    # of the tile edge); overflow is reported on the status word, not written
+    cap = int(pair_capacity or max(1 << 16, 32 * G * (4 if tile == 8 else 1)))
     e = lambda *s, dt=torch.float32: torch.empty(*s, dtype=dt, device=device)
     b = SplatBuffers(mean2d=e(2, G), conic=e(3, G), depth=e(G), rect=e(4, G, dt=torch.int32),
                      tile_range=e(num_tiles(W, H, tile), 2, dt=torch.int32), pair_gauss=e(cap, dt=torch.int32),
