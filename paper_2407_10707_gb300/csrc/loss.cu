@@ -98,7 +98,7 @@ ssim_forward_kernel(const float *__restrict__ img, const float *__restrict__ tgt
         }
     }
     __syncthreads();
-    double s_ssim = 0.0, s_l1 = 0.0;
+    float f_ssim = 0.f, f_l1 = 0.f;  // a thread's few pixels in FP32, the block's sums in FP64
     // vertical blurs: a thread slides the window down RBV outputs of a column
     // (one map at a time, so the window stays in registers)
     for (int i = threadIdx.x; i < (TS / RBV) * TS; i += LOSS_THREADS) {
@@ -126,20 +126,22 @@ ssim_forward_kernel(const float *__restrict__ img, const float *__restrict__ tgt
             const float sxx = m[2][t] - mx * mx, syy = m[3][t] - my * my, sxy = m[4][t] - mx * my;
             const float A1 = 2.f * mx * my + C1, A2 = 2.f * sxy + C2;
             const float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
-            const float inv = 1.f / (B1 * B2);
+            // B1 >= C1 and B2 >= C2: the fast reciprocals are within 2 ulp
+            const float inv = __fdividef(1.f, B1 * B2);
             const float S = A1 * A2 * inv;
             // derivatives with respect to mu_x, E[x^2], E[x y] (through s_xx, s_xy)
-            const float dS_dsxx = -S / B2;
+            const float dS_dsxx = -S * __fdividef(1.f, B2);
             const float dS_dsxy = 2.f * A1 * inv;
-            const float dS_dmx = 2.f * my * A2 * inv - S * 2.f * mx / B1;
+            const float dS_dmx = 2.f * my * A2 * inv - S * 2.f * mx * __fdividef(1.f, B1);
             const size_t o = c * plane + (size_t)y * d.W + x;
             coefA[o] = dS_dmx - 2.f * mx * dS_dsxx - my * dS_dsxy;
             coefB[o] = dS_dsxx;
             coefC[o] = dS_dsxy;
-            s_ssim += S;
-            s_l1 += fabsf(sx[r + R][q + R] - sy[r + R][q + R]);
+            f_ssim += S;
+            f_l1 += fabsf(sx[r + R][q + R] - sy[r + R][q + R]);
         }
     }
+    double s_ssim = f_ssim, s_l1 = f_l1;
     // block sums in FP64
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
