@@ -468,17 +468,18 @@ skin_gaussians_backward_kernel(avatar_skin_args a, avatar_skin_grads gr, const V
         float dn_g[3] = {0, 0, 0};
         if (gr.d_nd) {
             float dnd[3] = {__ldg(gr.d_nd + gi), __ldg(gr.d_nd + SG + gi), __ldg(gr.d_nd + 2 * SG + gi)};
-            float nlen = sqrtf(s.n[0] * s.n[0] + s.n[1] * s.n[1] + s.n[2] * s.n[2]);
-            float nh[3] = {s.n[0] / nlen, s.n[1] / nlen, s.n[2] / nlen};
+            // one reciprocal per length, then products (the divisions were IEEE)
+            float inl = 1.f / sqrtf(s.n[0] * s.n[0] + s.n[1] * s.n[1] + s.n[2] * s.n[2]);
+            float nh[3] = {s.n[0] * inl, s.n[1] * inl, s.n[2] * inl};
             float m[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) m[i] = A[4 * i] * nh[0] + A[4 * i + 1] * nh[1] + A[4 * i + 2] * nh[2];
-            float mlen = sqrtf(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
-            float nd[3] = {m[0] / mlen, m[1] / mlen, m[2] / mlen};
+            float iml = 1.f / sqrtf(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+            float nd[3] = {m[0] * iml, m[1] * iml, m[2] * iml};
             float dd = dnd[0] * nd[0] + dnd[1] * nd[1] + dnd[2] * nd[2];
             float dm[3];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) dm[i] = (dnd[i] - dd * nd[i]) / mlen;
+            for (int i = 0; i < 3; ++i) dm[i] = (dnd[i] - dd * nd[i]) * iml;
             float dnh[3] = {0, 0, 0};
 #pragma unroll
             for (int i = 0; i < 3; ++i)
@@ -489,7 +490,7 @@ skin_gaussians_backward_kernel(avatar_skin_args a, avatar_skin_grads gr, const V
                 }
             float d2 = dnh[0] * nh[0] + dnh[1] * nh[1] + dnh[2] * nh[2];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) dn_g[i] = (dnh[i] - d2 * nh[i]) / nlen;
+            for (int i = 0; i < 3; ++i) dn_g[i] = (dnh[i] - d2 * nh[i]) * inl;
         }
         float dag[3] = {0.f, 0.f, 0.f}, drg = 0.f, dpg = 0.f;
         if (shared_in) {
@@ -540,13 +541,14 @@ skin_gaussians_backward_kernel(avatar_skin_args a, avatar_skin_grads gr, const V
         for (int j = 0; j < K; ++j) sdot += dub[j] * s.ub[j];
         float dxg[3] = {dxb[0], dxb[1], dxb[2]};
 #pragma unroll
+        const float ius = 1.f / s.usum;
         for (int j = 0; j < K; ++j) {
-            float du = (dub[j] - sdot) / s.usum;
+            float du = (dub[j] - sdot) * ius;
             float d = s.dist[j];
             if (d > 1e-8f) {
                 float4 xr = __ldg(&recp[s.idx[j]].xr);
-                float dd = -du / (d * d);
-                float f = dd / d;
+                const float id = 1.f / d;
+                float f = -du * id * id * id;  // d(1/d)/dd = -1/d^2, and d|x - y| / dx = (x - y) / d
                 dxg[0] += f * (s.x[0] - xr.x);
                 dxg[1] += f * (s.x[1] - xr.y);
                 dxg[2] += f * (s.x[2] - xr.z);
