@@ -138,9 +138,10 @@ def run_gpu(args):
 
     dev = torch.device("cuda", local)
     sc = synth.config_scene(args.workload)
-    # the Gaussians stored in the order of their nearest vertex and the light
-    # texels in 4 x 8 patches (setup steps, outside every timed region; the
-    # rendered images are the same)
+    # the Gaussians stored in the order of their nearest vertex, the light
+    # texels in 4 x 8 patches and the faces by normal within raster chunks
+    # (setup steps, outside every timed region; the rendered images are the
+    # same)
     st = STM.stored_for_speed(render, synth, sc, dev)
     G, Nv, F = sc.avatar.G, sc.avatar.Nv, sc.avatar.F
     NL, D, R = len(sc.light.A), sc.frames.shape[0], sc.depth_res
@@ -227,8 +228,9 @@ def run_gpu(args):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "flushed (256 MB write) between timed steps", "graph": "CUDA graph replay",
                    "visibility": "one-sided raster of the closed capsule body (same bits as two-sided)",
-                   "storage_order": "Gaussians in nearest-vertex order, light texels in 4 x 8 patches "
-                                    "(render.spatially_ordered, render.light_ordered; once before timing)"},
+                   "storage_order": "Gaussians in nearest-vertex order, light texels in 4 x 8 patches, "
+                                    "faces by normal within each raster chunk (render.spatially_ordered, "
+                                    "render.light_ordered, render.faces_ordered; once before timing)"},
         "train": {"value": round(whole_job_rate(world, train_ms), 3), "unit": "train steps/s", "ms_per_step":
                   round(train_ms, 5),
                   "what": "frame + image loss (L1 + 0.2 D-SSIM) + backward of every stage",
@@ -264,10 +266,12 @@ def run_gpu(args):
 
 # ----------------------------------------------------------------- measurement helpers
 def stored_for_speed(render, synth, sc, dev, attr_dtype="f32"):
-    """Scene tensors with the Gaussians in nearest-vertex order and the light
-    texels in 4 x 8 patches (render.spatially_ordered, render.light_ordered)."""
+    """Scene tensors with the Gaussians in nearest-vertex order, the light
+    texels in 4 x 8 patches and the faces by normal within each raster chunk
+    (render.spatially_ordered, render.light_ordered, render.faces_ordered)."""
     st, _ = render.spatially_ordered(render.scene_tensors(sc, dev, attr_dtype=attr_dtype))
     st, _ = render.light_ordered(st, synth.latlong_patch_order(sc.light.rows, sc.light.cols))
+    st, _ = render.faces_ordered(st, synth.face_normal_order(sc.avatar.xv, sc.avatar.faces))
     return st
 
 
@@ -871,12 +875,14 @@ def _form_batch(args, dev, reps):
     torch.cuda.empty_cache()
     b = synth.config_batch("c4_batch", n_poses=args.batch_poses)
     lorder = synth.latlong_patch_order(b.scene.light.rows, b.scene.light.cols)
-    probe = render.BatchRenderer(b, tile=0, attr_dtype="bf16", spatial_order=True, light_order=lorder)
+    forder = synth.face_normal_order(b.scene.avatar.xv, b.scene.avatar.faces)
+    probe = render.BatchRenderer(b, tile=0, attr_dtype="bf16", spatial_order=True, light_order=lorder,
+                                 face_order=forder)
     cap = probe.cap
     targets = probe.images.detach().clone() * 0.9
     del probe
     br = render.BatchRenderer(b, targets=targets, tile=0, attr_dtype="bf16", pair_capacity=cap, spatial_order=True,
-                              light_order=lorder)
+                              light_order=lorder, face_order=forder)
     tuned = br.autotune()
     bf = _time_graph(_graph_of(br.forward), max(3, reps // 4))
     bt = _time_graph(_graph_of(br.step), max(3, reps // 4))
@@ -901,7 +907,8 @@ def _form_batch(args, dev, reps):
     return {
         "what": f"{b.B} poses x 4 cameras (512x512, 1080x1080, 1920x1080), own 16x32 light per pose, 200k Gaussians, "
                 "512 visibility directions at 256^2, BF16 storage, Gaussians in nearest-vertex order, light "
-                "texels in 4 x 8 patches; one launch per stage, one CUDA graph",
+                "texels in 4 x 8 patches, faces by normal within raster chunks; one launch per stage, one CUDA "
+                "graph",
         "views_per_s": round(b.V * 1000.0 / bf, 1), "train_views_per_s": round(b.V * 1000.0 / bt, 1),
         "ms_per_batch": round(bf, 3), "ms_per_train_batch": round(bt, 3),
         "per_frame_fp32_views_per_s": round(b.V * 1000.0 / sf, 1),

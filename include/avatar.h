@@ -269,12 +269,18 @@ int avatar_knn(avatar_ctx *ctx, const avatar_knn_args *a, void *ws, size_t ws_by
 /*  bit(v,d) = 1 iff v is outside the window, its pixel is empty, or      */
 /*  zd_v <= depth[pixel(v)] + rint(bias*2^16).                            */
 /* (cull_back = 1 keeps only triangles of positive area, see the field.) */
+/* The faces are rasterised in chunks of AVATAR_VIS_FACE_CHUNK in array  */
+/* order; the bits do not depend on the order of the faces, and an order  */
+/* that permutes faces only within these chunks keeps every chunk's       */
+/* vertex range (a chunk's vertices are projected once into a cache).     */
 /* Output bit layout: vertex-major words.  With dmap == NULL the word     */
 /* index is d>>5 over the D viewpoints ([Nv][D/32]); with a light->view   */
 /* map dmap[NL] the bits are re-ordered per light: bit k of vertex v is  */
 /* bit(v, dmap[k]) in words [Nv][ceil(NL/32)] (the form avatar_shade     */
 /* reads).                                                              */
 /* ------------------------------------------------------------------ */
+enum { AVATAR_VIS_FACE_CHUNK = 1024 };
+
 typedef struct {
     int Nv;                /* vertices */
     int F;                 /* triangles */

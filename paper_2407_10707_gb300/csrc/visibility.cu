@@ -106,7 +106,7 @@ __device__ __forceinline__ int floor_div_small(long long num, int den)
 // Packed projected vertex for the shared-memory cache: X | Y << 16 (0xffffffff
 // = outside the window) and Z.
 constexpr unsigned OUTSIDE = 0xffffffffu;
-constexpr int VIS_CHUNK = 1024;                 // triangles per CTA per chunk
+constexpr int VIS_CHUNK = AVATAR_VIS_FACE_CHUNK;  // triangles per CTA per chunk
 constexpr int VIS_TPT = VIS_CHUNK / VIS_THREADS; // triangles per thread per chunk
 constexpr int VIS_VCAP = 1024;                   // cached projected vertices per chunk (10-bit offsets)
 static_assert(VIS_VCAP == 1024, "packed face offsets are 10 bits");

@@ -57,6 +57,23 @@ def spatially_ordered(st, status=None):
     return st2, order
 
 
+def faces_ordered(st, order, status=None):
+    """The scene with its mesh faces stored in `order` (int32 [F], e.g.
+    synth.face_normal_order, a permutation within the raster's chunks of
+    _lib.VIS_FACE_CHUNK faces): the rows of faces [F][3] gathered by
+    avatar_gather_columns.  The visibility bits, and so every image, are
+    the same."""
+    f = st["avatar"]["faces"]
+    o = torch.as_tensor(np.ascontiguousarray(order, dtype=np.int32), device=f.device)
+    if o.dim() != 1 or o.numel() != f.shape[0]:
+        raise ValueError(f"face order of {o.numel()} entries for {f.shape[0]} faces")
+    t2 = dict(st["avatar"])
+    t2["faces"] = api.gather_columns(f.reshape(1, -1, 3), o, status).reshape(f.shape)
+    st2 = dict(st)
+    st2["avatar"] = t2
+    return st2, o
+
+
 def light_ordered(st, order, status=None):
     """The scene with its light texels stored in `order` (int32 [NL], e.g.
     synth.latlong_patch_order): radiance, solid angles, directions and the
@@ -492,11 +509,13 @@ class BatchRenderer:
     in BF16; spatial_order stores the Gaussians in the order of their
     nearest vertex (as spatially_ordered; self.order then maps Gaussian i
     to the batch avatar's Gaussian self.order[i]); light_order (int32 [NL])
-    stores every pose's light texels in that order (as light_ordered).  The
-    pair buffer grows once if the first eager call overflows."""
+    stores every pose's light texels in that order (as light_ordered);
+    face_order (int32 [F]) stores the mesh faces in that order (as
+    faces_ordered).  The pair buffer grows once if the first eager call
+    overflows."""
 
     def __init__(self, batch, targets=None, tile=0, pair_capacity=None, vis_cull_back=True, attr_dtype="f32",
-                 device="cuda", ssim_weight=0.2, spatial_order=False, light_order=None):
+                 device="cuda", ssim_weight=0.2, spatial_order=False, light_order=None, face_order=None):
         import ctypes as C
         from . import _lib as L
         self.L, self.C = L, C
@@ -507,6 +526,8 @@ class BatchRenderer:
         if spatial_order:
             st, self.order = spatially_ordered({"avatar": self.t})
             self.t = st["avatar"]
+        if face_order is not None:
+            self.t = faces_ordered({"avatar": self.t}, face_order)[0]["avatar"]
         self.frames = f(sc.frames.reshape(-1, 9))
         self.light_A, self.light_w = f(sc.light.A), f(sc.light.w)
         self.dmap = torch.as_tensor(sc.dmap, dtype=torch.int32, device=device)

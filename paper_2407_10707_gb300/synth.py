@@ -471,6 +471,39 @@ def permute_gaussians(scene: Scene, order) -> Scene:
     return dataclasses.replace(scene, avatar=av2)
 
 
+def face_normal_order(xv: np.ndarray, faces: np.ndarray, chunk: int = 1024, bins: int = 8) -> np.ndarray:
+    """A storage order of a mesh's faces for the visibility raster: within
+    each run of `chunk` faces (the raster's chunk, so every chunk keeps its
+    faces and vertex range) the faces are listed by the octahedral bin
+    (bins x bins) of their canonical normal, stably.  A warp's 32 faces then
+    face the same way, so toward most lights they are all back faces (left
+    at the orientation test) or mostly front faces; the bits do not depend
+    on the order."""
+    xv = np.asarray(xv, np.float64)
+    f = np.asarray(faces, np.int64)
+    n = np.cross(xv[f[:, 1]] - xv[f[:, 0]], xv[f[:, 2]] - xv[f[:, 0]])
+    n = n / np.maximum(np.linalg.norm(n, axis=1, keepdims=True), 1e-300)
+    p = n[:, :2] / np.maximum(np.abs(n).sum(1, keepdims=True), 1e-300)
+    q = p.copy()
+    lower = n[:, 2] < 0                                   # fold the lower hemisphere (octahedral map)
+    q[lower] = (1.0 - np.abs(p[lower][:, ::-1])) * np.where(p[lower] >= 0, 1.0, -1.0)
+    cell = np.clip(np.floor((q + 1.0) * 0.5 * bins), 0, bins - 1).astype(np.int64)
+    key = cell[:, 0] * bins + cell[:, 1]
+    order = np.arange(len(f), dtype=np.int64)
+    for c in range(0, len(f), chunk):
+        idx = order[c:c + chunk]
+        order[c:c + chunk] = idx[np.argsort(key[c:c + chunk], kind="stable")]
+    return order.astype(np.int32)
+
+
+def permute_faces(scene: Scene, order) -> Scene:
+    """The scene with face s taken from face order[s] (a storage order of
+    the same mesh)."""
+    import dataclasses
+    av = dataclasses.replace(scene.avatar, faces=np.asarray(scene.avatar.faces)[np.asarray(order)])
+    return dataclasses.replace(scene, avatar=av)
+
+
 def nearest_vertex_order(scene: Scene) -> np.ndarray:
     """Stable order of the Gaussians by their nearest vertex (knn column 0)."""
     return np.argsort(scene.avatar.knn[:, 0], kind="stable").astype(np.int32)

@@ -168,7 +168,8 @@ def L_lib():
 def test_full_c4_batch_bf16_matches_oracle_stage_by_stage(gpu):
     """The C4 batch as the benchmark runs it - 32 poses x 4 cameras at 512^2,
     1080^2 and 1920 x 1080, the 200k-Gaussian avatar with a light per pose,
-    BF16 attribute storage, Gaussians in nearest-vertex order, autotuned tile
+    BF16 attribute storage, Gaussians in nearest-vertex order, faces by
+    normal within raster chunks, autotuned tile
     edge and pixel splits.  A 1080^2 and a 1920 x 1080 view equal, bit for
     bit, the per-frame renders of those views with the same choices, and each
     per-frame render meets the FP64 oracle stage by stage (tests/_chain.py)
@@ -178,7 +179,8 @@ def test_full_c4_batch_bf16_matches_oracle_stage_by_stage(gpu):
     from _common import bf16_scene
     api, render = gpu
     b = synth.config_batch("c4_batch")
-    br = render.BatchRenderer(b, tile=0, attr_dtype="bf16", spatial_order=True)
+    forder = synth.face_normal_order(b.scene.avatar.xv, b.scene.avatar.faces)
+    br = render.BatchRenderer(b, tile=0, attr_dtype="bf16", spatial_order=True, face_order=forder)
     lib = L_lib()
     try:
         tile, ppt, bppt = br.autotune()
@@ -192,13 +194,15 @@ def test_full_c4_batch_bf16_matches_oracle_stage_by_stage(gpu):
         for v in (1, 2):
             scv = view_scene(b, v)
             stv, _ = render.spatially_ordered(render.scene_tensors(scv, attr_dtype="bf16"))
+            stv, _ = render.faces_ordered(stv, forder)
             rv = render.Renderer(stv, tile=tile)
             torch.cuda.synchronize()
             rv.check()
             assert torch.equal(rv.sb.image, br.image(v)), f"view {v} differs from its per-frame render"
             n = scv.camera.width * scv.camera.height
             pix = np.sort(rng.choice(n, size=4096, replace=False)).astype(np.int32)
-            rep = chain_check(rv, bf16_scene(synth.permute_gaussians(scv, np_order)), pixels=pix)
+            rep = chain_check(rv, bf16_scene(synth.permute_faces(synth.permute_gaussians(scv, np_order), forder)),
+                              pixels=pix)
             rep.pop("gpu")
             print(f"view {v} ({scv.camera.width}x{scv.camera.height}), tile {tile}, blend split {ppt}:", rep)
             del rv

@@ -2,12 +2,13 @@
 
 The frame: 50k-vertex body mesh, 200k Gaussians stored in the order of their
 nearest vertex (render.spatially_ordered), 16 x 32 environment light stored
-in 4 x 8 patches (render.light_ordered), 512
+in 4 x 8 patches (render.light_ordered), the faces by normal within each
+raster chunk (render.faces_ordered), 512
 visibility directions at 256^2 (one-sided raster of the closed body), one
 1024 x 1024 camera, 16-pixel tiles; the overlapped frame (cull, projection and
 binning on a second stream) replayed from its CUDA graph.  The oracle runs on
-the same reordered avatar and light (the Gaussian order checked equal to
-numpy's stable sort).
+the same reordered avatar, light and faces (the Gaussian order checked
+equal to numpy's stable sort).
 
 Every stage is compared with the FP64 oracle on the GPU's own inputs (the
 stage chain of tests/_chain.py): the visibility bits of all 512 directions
@@ -41,7 +42,9 @@ def frame():
     assert np.array_equal(order.cpu().numpy(), np_order)
     lorder = synth.latlong_patch_order(sc0.light.rows, sc0.light.cols)
     st, _ = render.light_ordered(st, lorder)
-    sc = synth.permute_lights(synth.permute_gaussians(sc0, np_order), lorder)
+    forder = synth.face_normal_order(sc0.avatar.xv, sc0.avatar.faces)
+    st, _ = render.faces_ordered(st, forder)
+    sc = synth.permute_faces(synth.permute_lights(synth.permute_gaussians(sc0, np_order), lorder), forder)
     r = render.Renderer(st, tile=16)              # the benchmark's renderer and tile edge
     r.capture()
     for _ in range(3):

@@ -115,3 +115,43 @@ def test_light_ordered_frame_meets_the_oracle_on_the_reordered_light(gpu):
     rep.pop("gpu")
     print("reordered lights and Gaussians, c1_small:", rep)
     assert float((r.sb.image - img0).abs().max()) < 2e-4
+
+
+@pytest.mark.parametrize("cull_back", [True, False])
+def test_faces_ordered_keep_the_bits_and_the_image(gpu, cull_back):
+    """Faces stored by normal within each raster chunk: the visibility bits
+    (both raster rules, and the paper's triangle-ID form) and the image are
+    the original order's bit for bit, and the gathered faces are the
+    permuted rows."""
+    api, render = gpu
+    sc = scene("c1_small")
+    st0 = render.scene_tensors(sc)
+    forder = synth.face_normal_order(sc.avatar.xv, sc.avatar.faces)
+    assert not np.array_equal(forder, np.arange(len(forder)))
+    st, o = render.faces_ordered(st0, forder)
+    assert np.array_equal(st["avatar"]["faces"].cpu().numpy(), sc.avatar.faces[forder])
+    r0 = render.Renderer(st0, vis_cull_back=cull_back)
+    r1 = render.Renderer(st, vis_cull_back=cull_back)
+    torch.cuda.synchronize()
+    r0.check()
+    r1.check()
+    assert torch.equal(r0.bits, r1.bits)
+    assert torch.equal(r0.sb.image, r1.sb.image)
+    with pytest.raises(ValueError):
+        render.faces_ordered(st0, forder[:-1])
+
+
+def test_faces_ordered_paper_visibility_keeps_the_counts(gpu):
+    api, render = gpu
+    sc = scene("c1_small")
+    st0 = render.scene_tensors(sc)
+    knn_v = torch.as_tensor(np.ascontiguousarray(synth.vertex_knn(sc.avatar.xv, 19).T), dtype=torch.int32,
+                            device="cuda")
+    st, _ = render.faces_ordered(st0, synth.face_normal_order(sc.avatar.xv, sc.avatar.faces))
+    r0 = render.Renderer(st0, visibility="paper", knn_v=knn_v)
+    r1 = render.Renderer(st, visibility="paper", knn_v=knn_v)
+    torch.cuda.synchronize()
+    r0.check()
+    r1.check()
+    assert torch.equal(r0.vis_count, r1.vis_count)
+    assert torch.equal(r0.sb.image, r1.sb.image)

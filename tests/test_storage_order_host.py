@@ -34,3 +34,29 @@ def test_nearest_vertex_order_and_scene_permutations():
     sl = synth.permute_lights(sc, lo)
     assert np.array_equal(sl.light.L, sc.light.L[lo]) and np.array_equal(sl.light.w, sc.light.w[lo])
     assert np.array_equal(sl.light.A, sc.light.A[lo]) and np.array_equal(sl.dmap, np.asarray(sc.dmap)[lo])
+
+
+def test_face_normal_order_permutes_within_raster_chunks():
+    """The faces' storage order keeps every raster chunk's faces (so each
+    chunk's vertex range) and lists them by octahedral normal bin, stably;
+    the chunk is the library's."""
+    from paper_2407_10707_gb300 import _lib as L
+    sc = synth.config_scene("c1_small")
+    xv, faces = sc.avatar.xv, sc.avatar.faces
+    o = synth.face_normal_order(xv, faces, chunk=L.VIS_FACE_CHUNK)
+    F = len(faces)
+    assert np.array_equal(np.sort(o), np.arange(F))
+    for c in range(0, F, L.VIS_FACE_CHUNK):
+        blk = o[c:c + L.VIS_FACE_CHUNK]
+        assert blk.min() >= c and blk.max() < min(F, c + L.VIS_FACE_CHUNK)
+    # faces of a sphere in random order: listed by normal bin, neighbours in
+    # the order face nearly the same way
+    v, f, _ = synth._tessellate_capsule((0, 0, 0), (0, 0, 0), 0.5, 600)
+    f = f[np.random.default_rng(3).permutation(len(f))]
+    o2 = synth.face_normal_order(v, f, chunk=L.VIS_FACE_CHUNK)
+    n = np.cross(v[f[:, 1]] - v[f[:, 0]], v[f[:, 2]] - v[f[:, 0]])
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    step = lambda nn: float(np.mean(np.sum(nn[1:] * nn[:-1], axis=1)))   # mean cosine of consecutive normals
+    assert step(n) < 0.1 and step(n[o2]) > 0.7
+    sp = synth.permute_faces(sc, o)
+    assert np.array_equal(sp.avatar.faces, faces[o])
