@@ -471,14 +471,34 @@ def permute_gaussians(scene: Scene, order) -> Scene:
     return dataclasses.replace(scene, avatar=av2)
 
 
-def face_normal_order(xv: np.ndarray, faces: np.ndarray, chunk: int = 1024, bins: int = 8) -> np.ndarray:
+def _hilbert_index(x: np.ndarray, y: np.ndarray, n: int) -> np.ndarray:
+    """Index along the Hilbert curve of cells (x, y) of an n x n grid (n a power
+    of two): consecutive indices are neighbouring cells."""
+    x = np.array(x, np.int64)
+    y = np.array(y, np.int64)
+    d = np.zeros_like(x)
+    s = n // 2
+    while s > 0:
+        rx = (x & s) > 0
+        ry = (y & s) > 0
+        d += s * s * ((3 * rx.astype(np.int64)) ^ ry.astype(np.int64))
+        turn = ~ry                                       # rotate the quadrant into the curve's frame
+        flip = turn & rx
+        x[flip] = s - 1 - x[flip]
+        y[flip] = s - 1 - y[flip]
+        x[turn], y[turn] = y[turn].copy(), x[turn].copy()
+        s //= 2
+    return d
+
+
+def face_normal_order(xv: np.ndarray, faces: np.ndarray, chunk: int = 1024, bins: int = 32) -> np.ndarray:
     """A storage order of a mesh's faces for the visibility raster: within
     each run of `chunk` faces (the raster's chunk, so every chunk keeps its
-    faces and vertex range) the faces are listed by the octahedral bin
-    (bins x bins) of their canonical normal, stably.  A warp's 32 faces then
-    face the same way, so toward most lights they are all back faces (left
-    at the orientation test) or mostly front faces; the bits do not depend
-    on the order."""
+    faces and vertex range) the faces are listed stably by the position of
+    their canonical normal's cell (bins x bins, octahedral map) along a
+    Hilbert curve.  A warp's 32 faces then face nearly the same way, so
+    toward most lights they are all back faces (left at the orientation
+    test) or mostly front faces; the bits do not depend on the order."""
     xv = np.asarray(xv, np.float64)
     f = np.asarray(faces, np.int64)
     n = np.cross(xv[f[:, 1]] - xv[f[:, 0]], xv[f[:, 2]] - xv[f[:, 0]])
@@ -488,7 +508,7 @@ def face_normal_order(xv: np.ndarray, faces: np.ndarray, chunk: int = 1024, bins
     lower = n[:, 2] < 0                                   # fold the lower hemisphere (octahedral map)
     q[lower] = (1.0 - np.abs(p[lower][:, ::-1])) * np.where(p[lower] >= 0, 1.0, -1.0)
     cell = np.clip(np.floor((q + 1.0) * 0.5 * bins), 0, bins - 1).astype(np.int64)
-    key = cell[:, 0] * bins + cell[:, 1]
+    key = _hilbert_index(cell[:, 0], cell[:, 1], bins)
     order = np.arange(len(f), dtype=np.int64)
     for c in range(0, len(f), chunk):
         idx = order[c:c + chunk]

@@ -60,3 +60,15 @@ def test_face_normal_order_permutes_within_raster_chunks():
     assert step(n) < 0.1 and step(n[o2]) > 0.7
     sp = synth.permute_faces(sc, o)
     assert np.array_equal(sp.avatar.faces, faces[o])
+
+
+def test_hilbert_index_walks_neighbouring_cells():
+    """The face order's curve: on an 8 x 8 grid the index is a bijection
+    onto 0..63 and consecutive indices are edge-adjacent cells."""
+    n = 8
+    x, y = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    d = synth._hilbert_index(x.ravel(), y.ravel(), n)
+    assert np.array_equal(np.sort(d), np.arange(n * n))
+    pos = np.empty((n * n, 2), np.int64)
+    pos[d] = np.c_[x.ravel(), y.ravel()]
+    assert np.all(np.abs(np.diff(pos, axis=0)).sum(axis=1) == 1)
