@@ -352,8 +352,10 @@ struct SkinBwdWs {
 
 __device__ __forceinline__ float ld_or0(const float *p, size_t i) { return p ? __ldg(p + i) : 0.f; }
 
+// Two blocks per SM: unbounded the adjoint takes 180 registers and one
+// block; at 128 (8 bytes spilled) twice the warps hide its gathers and atomics.
 template <int K>
-__global__ void __launch_bounds__(SKIN_THREADS)
+__global__ void __launch_bounds__(SKIN_THREADS, 2)
 skin_gaussians_backward_kernel(avatar_skin_args a, avatar_skin_grads gr, const VertexRec *__restrict__ rec,
                                float *__restrict__ dAv, int B)
 {
