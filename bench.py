@@ -348,10 +348,11 @@ def workload_stats(r, sc):
     tile_passes = (tbits + 7) // 8
     # the frame's kernels: skin (vertices, Gaussians); cull, project, keys, the
     # depth sort (histograms + 4 passes), the pair scan (2), emission, the tile
-    # sort (histograms + one pass per 8 bits of the tile id), ranges;
+    # sort (histograms + one pass per 8 bits of the tile id), ranges, the
+    # blend's tile order;
     # visibility (quantise, chunk ranges, raster + test, transpose); shading;
     # colour records and blend (the ncu launch list shows the same sequence)
-    launches = 2 + 3 + 5 + 2 + 1 + (1 + tile_passes) + 1 + 4 + 1 + 2
+    launches = 2 + 3 + 5 + 2 + 1 + (1 + tile_passes) + 2 + 4 + 1 + 2
     vis = visibility_work(r.sk["xp"].detach().cpu().numpy().T, sc)
     return {"front_gaussians": front, "lit_pairs_upper": lit, "pairs": P, "faces": Fc,
             "traversed_pairs": traversed, "tile_sort_passes": tile_passes, "launches_per_frame": launches,

@@ -505,7 +505,9 @@ size_t avatar_splat_workspace_size(const avatar_splat_args *a);
 /* The three steps, and all three in order.  project reads xd, cov, opacity
  * and cull; bin reads the projection buffers and opacity; only blend reads
  * color (it completes the per-Gaussian blend records), so project and bin
- * may run before shading has finished. */
+ * may run before shading has finished.  bin also leaves in the workspace the
+ * order in which blend and the backward visit the tiles (longest lists
+ * first); the image does not depend on it. */
 int avatar_splat_project(avatar_ctx *ctx, const avatar_splat_args *a, void *ws, size_t ws_bytes,
                          avatar_stream_t stream);
 int avatar_splat_bin(avatar_ctx *ctx, const avatar_splat_args *a, void *ws, size_t ws_bytes,

@@ -38,6 +38,7 @@ struct SplatWs {
     int32_t *count_g;            // [1] = G on the device
     float *d_mean2d;             // [2][G]
     float *d_conic;              // [3][G]
+    int32_t *tile_order;         // [ntiles] tiles by descending list length (bucketed)
     int NB;
 };
 
@@ -72,6 +73,11 @@ size_t splat_ws_layout(const avatar_splat_args *a, int NB, void *base, size_t ca
     w.count_g = c.take<int32_t>(1);
     w.d_mean2d = c.take<float>(2 * G);
     w.d_conic = c.take<float>(3 * G);
+    {
+        const int ts = a->tile == 0 ? 16 : a->tile;
+        const size_t nt = (size_t)((a->cam.width + ts - 1) / ts) * ((a->cam.height + ts - 1) / ts);
+        w.tile_order = c.take<int32_t>(nt > 0 ? nt : 1);
+    }
     w.NB = NB;
     if (out) *out = w;
     return c.off;
@@ -145,11 +151,44 @@ emit_pairs_kernel(const int32_t *__restrict__ sorted_idx, const int32_t *__restr
     }
 }
 
+// The blend kernels' tile order: tiles by the bit length of their list
+// length, longest first (one block; the order within a length class is
+// arbitrary).  Blocks start in index order, so the costly tiles start first
+// and the last wave holds the cheap ones.
+__global__ void __launch_bounds__(1024)
+tile_order_kernel(const int2 *__restrict__ ranges, int ntiles, int32_t *__restrict__ order)
+{
+    __shared__ int cnt[33];
+    if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        const int2 r = __ldg(ranges + t);
+        const int len = max(r.y - r.x, 0);
+        atomicAdd(&cnt[len > 0 ? __clz(len) : 32], 1);  // class 0 = the longest lists
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int k = 0; k < 33; ++k) {
+            const int n = cnt[k];
+            cnt[k] = run;
+            run += n;
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        const int2 r = __ldg(ranges + t);
+        const int len = max(r.y - r.x, 0);
+        order[atomicAdd(&cnt[len > 0 ? __clz(len) : 32], 1)] = t;
+    }
+}
+
 template <int TS, int PPT>
 __global__ void __launch_bounds__(BWD_WARPS * 32)
 blend_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_gauss, const float4 *__restrict__ rec0,
              const float4 *__restrict__ rec1, const float4 *__restrict__ rec2, int W, int H, int ntx, int ntiles,
-             float *__restrict__ image, float *__restrict__ T_final, int32_t *__restrict__ n_last)
+             float *__restrict__ image, float *__restrict__ T_final, int32_t *__restrict__ n_last,
+             const int32_t *__restrict__ torder)
 {
     constexpr int NB = TS * TS / (32 * PPT);  // pixel boxes per tile
     __shared__ float4 s0[BWD_WARPS][2][32];
@@ -159,7 +198,7 @@ blend_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_g
     const int item = blockIdx.x * BWD_WARPS + warp;
     constexpr int NBD = NB > 0 ? NB : 1;  // NB = 0: a split the tile cannot hold (never launched)
     if (item >= ntiles * NB) return;      // warp-uniform; the kernel has no CTA barrier
-    const int tile = item / NBD;
+    const int tile = __ldg(torder + item / NBD);
     blend_box<TS, PPT>(ranges[tile], pair_gauss, rec0, rec1, rec2, W, H, tile % ntx, tile / ntx, item % NBD, image,
                        T_final, n_last, s0[warp], s1[warp], s2[warp]);
 }
@@ -172,7 +211,7 @@ blend_backward_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict
                       int W, int H, int ntx, int ntiles, const float *__restrict__ T_final,
                       const int32_t *__restrict__ n_last, const float *__restrict__ d_image, int G,
                       float *__restrict__ d_mean2d, float *__restrict__ d_conic, float *__restrict__ d_opacity,
-                      float *__restrict__ d_color)
+                      float *__restrict__ d_color, const int32_t *__restrict__ torder)
 {
     constexpr int NB = TS * TS / (32 * PPT);  // pixel boxes per tile
     __shared__ float4 s0[BWD_WARPS][2][32];
@@ -183,7 +222,7 @@ blend_backward_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict
     const int item = blockIdx.x * BWD_WARPS + warp;
     constexpr int NBD = NB > 0 ? NB : 1;  // NB = 0: a split the tile cannot hold (never launched)
     if (item >= ntiles * NB) return;      // warp-uniform; the kernel has no CTA barrier
-    const int tile = item / NBD;
+    const int tile = __ldg(torder + item / NBD);
     blend_backward_box<TS, PPT>(ranges[tile], pair_gauss, rec0, rec1, rec2, W, H, tile % ntx, tile / ntx, item % NBD,
                                 T_final, n_last, d_image, (size_t)G, d_mean2d, d_conic, d_opacity, d_color, s0[warp],
                                 s1[warp], s2[warp], sg[warp]);
@@ -296,6 +335,8 @@ extern "C" int avatar_splat_bin(avatar_ctx *ctx, const avatar_splat_args *a, voi
         return AVATAR_ERR_CUDA;
     if (a->G == 0) {
         if (cudaMemsetAsync(a->num_pairs, 0, sizeof(int32_t), st) != cudaSuccess) return AVATAR_ERR_CUDA;
+        tile_order_kernel<<<1, 1024, 0, st>>>((const int2 *)a->tile_range, ntiles, w.tile_order);
+        AV_CHECK_LAUNCH();
         return AVATAR_OK;
     }
     const int G = a->G;
@@ -329,6 +370,8 @@ extern "C" int avatar_splat_bin(avatar_ctx *ctx, const avatar_splat_args *a, voi
     // 5. tile ranges (sorted keys are in pkey_a)
     tile_ranges_kernel<<<ctx->sm_count * 8, 256, 0, st>>>(w.pkey_a, a->num_pairs, cap, ntiles,
                                                           (int2 *)a->tile_range);
+    // 6. the blend's tile order, longest lists first
+    tile_order_kernel<<<1, 1024, 0, st>>>((const int2 *)a->tile_range, ntiles, w.tile_order);
     AV_CHECK_LAUNCH();
     return AVATAR_OK;
 }
@@ -340,7 +383,7 @@ void launch_blend(const avatar_splat_args *a, const SplatWs &w, int ntiles, int 
     const int blocks = (int)(((long long)ntiles * NB + BWD_WARPS - 1) / BWD_WARPS);
     blend_kernel<TS, PPT><<<blocks, BWD_WARPS * 32, 0, st>>>((const int2 *)a->tile_range, a->pair_gauss, w.rec0,
                                                              w.rec1, w.rec2, a->cam.width, a->cam.height, ntx, ntiles,
-                                                             a->image, a->T_final, a->n_last);
+                                                             a->image, a->T_final, a->n_last, w.tile_order);
 }
 
 template <int TS>
@@ -390,7 +433,7 @@ void launch_blend_bwd(const avatar_splat_args *a, const avatar_splat_grads *g, c
     const int blocks = (int)(((long long)ntiles * NB + BWD_WARPS - 1) / BWD_WARPS);
     blend_backward_kernel<TS, PPT><<<blocks, BWD_WARPS * 32, 0, st>>>(
         (const int2 *)a->tile_range, a->pair_gauss, w.rec0, w.rec1, w.rec2, a->cam.width, a->cam.height, ntx, ntiles,
-        a->T_final, a->n_last, g->d_image, G, w.d_mean2d, w.d_conic, g->d_opacity, g->d_color);
+        a->T_final, a->n_last, g->d_image, G, w.d_mean2d, w.d_conic, g->d_opacity, g->d_color, w.tile_order);
 }
 
 template <int TS>
