@@ -344,7 +344,7 @@ def workload_stats(r, sc):
     Fc = sc.avatar.F
     traversed = int(r.sb.n_last.to(torch.int64).sum().item())
     ntiles = r.sb.tile_range.shape[0]
-    tbits = max(1, (ntiles - 1).bit_length())
+    tbits = max(1, ntiles.bit_length())   # 2^bits > ntiles: the no-tile key sorts last
     tile_passes = (tbits + 7) // 8
     # the frame's kernels: skin (vertices, Gaussians); cull, project, keys, the
     # depth sort (histograms + 4 passes), the pair scan (2), emission, the tile

@@ -458,8 +458,10 @@ int avatar_shade_backward(avatar_ctx *ctx, const avatar_shade_args *a, const ava
 /*   T^T + 0.3 I with T = J R (EWA); conic = inverse(Sigma');            */
 /*   rect = pixels whose centre (i+1/2) lies in the AABB of the ellipse   */
 /*   q <= 2 ln(255 o) padded by 1 pixel (tile-size independent).         */
-/* bin: Gaussian g belongs to every tile its rect meets; each tile's     */
-/*   list is ordered by (depth bits, g) - a stable device radix sort.    */
+/* bin: one pair per tile that g's rect meets (num_pairs counts them);  */
+/*   a tile's list holds the pairs whose ellipse q <= 2 ln(255 o) comes  */
+/*   within one pixel of the tile (the others cannot reach its pixels),  */
+/*   ordered by (depth bits, g) - a stable device radix sort.            */
 /* blend: per pixel centre, front to back: alpha = min(0.99, o e^{-q/2}),*/
 /*   skip alpha < 1/255, stop before T(1-alpha) < 1e-4, C += c alpha T.   */
 /* ------------------------------------------------------------------ */
@@ -488,7 +490,7 @@ typedef struct {
     int32_t *tile_range;   /* [ntiles][2] begin, end into pair_gauss */
     int32_t *pair_gauss;   /* [pair_capacity] Gaussian index of each sorted pair */
     int64_t pair_capacity; /* capacity of pair_gauss, >= 1 */
-    int32_t *num_pairs;    /* [1] total pairs (the required capacity on overflow) */
+    int32_t *num_pairs;    /* [1] pairs emitted, listed or not (the required capacity on overflow) */
     /* image (written by blend) */
     float *image;          /* [3][H][W] */
     float *T_final;        /* [H][W] final transmittance */

@@ -336,7 +336,8 @@ bin_keys_batch_kernel(const BatchView *__restrict__ views, int G, long long VG, 
 __global__ void __launch_bounds__(256)
 emit_batch_kernel(const BatchView *__restrict__ views, int G, long long VG, int TS,
                   const int32_t *__restrict__ sorted_idx, const int32_t *__restrict__ offsets,
-                  const int32_t *__restrict__ npairs, const int32_t *__restrict__ rect, long cap,
+                  const int32_t *__restrict__ npairs, const int32_t *__restrict__ rect,
+                  const float4 *__restrict__ rec0, const float4 *__restrict__ rec1, long cap,
                   uint32_t *__restrict__ keys, int32_t *__restrict__ vals)
 {
     const size_t cs = (size_t)VG;
@@ -346,6 +347,7 @@ emit_batch_kernel(const BatchView *__restrict__ views, int G, long long VG, int 
         const long long k = base + (threadIdx.x & 31);
         int gi = 0, n = 0, tx0 = 0, ty0 = 0, w = 1, kbase = 0, ntx = 1;
         long off = 0;
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
         if (k < VG) {
             gi = sorted_idx[k];
             n = npairs[gi];
@@ -357,9 +359,11 @@ emit_batch_kernel(const BatchView *__restrict__ views, int G, long long VG, int 
                 tx0 = rect[gi] / TS;
                 ty0 = rect[cs + gi] / TS;
                 w = rect[2 * cs + gi] / TS - tx0 + 1;
+                r0 = rec0[gi];
+                r1 = rec1[gi];
             }
         }
-        emit_pairs_warp(n, off, gi, tx0, ty0, w, kbase, ntx, cap, keys, vals);
+        emit_pairs_warp(n, off, gi, tx0, ty0, w, kbase, ntx, tile_reach_of(r0, r1), TS, cap, keys, vals);
     }
 }
 
@@ -690,7 +694,8 @@ int render_batch(avatar_ctx *ctx, const avatar_batch_desc *d, void *ws, size_t w
     uint32_t *k_other = (passes % 2 == 0) ? w.pkey_b : w.pkey_a;
     int32_t *v_other = (passes % 2 == 0) ? w.pval_b : w.pval_a;
     emit_batch_kernel<<<grid_cap(ctx, m.VG, 256, 8), 256, 0, st>>>(w.views, m.G, m.VG, TS, w.dval_a, w.offsets,
-                                                                    w.npairs, w.rect, (long)m.cap, k_emit, v_emit);
+                                                                    w.npairs, w.rect, w.rec0, w.rec1, (long)m.cap,
+                                                                    k_emit, v_emit);
     AV_CHECK_LAUNCH();
     AV_TRY(radix_sort(k_emit, v_emit, k_other, v_other, passes * 8, d->num_pairs, (int)m.cap, sw, d->status, st, sort_spin_limit(ctx)));
     tile_ranges_kernel<<<ctx->sm_count * 8, 256, 0, st>>>(w.pkey_a, d->num_pairs, (long)m.cap, (int)T, w.ranges);

@@ -129,7 +129,8 @@ color_records_kernel(avatar_splat_args a, SplatWs w)
 
 __global__ void __launch_bounds__(256)
 emit_pairs_kernel(const int32_t *__restrict__ sorted_idx, const int32_t *__restrict__ offsets,
-                  const int32_t *__restrict__ npairs, const int32_t *__restrict__ rect, int G, int TS, int ntx,
+                  const int32_t *__restrict__ npairs, const int32_t *__restrict__ rect,
+                  const float4 *__restrict__ rec0, const float4 *__restrict__ rec1, int G, int TS, int ntx,
                   long cap, uint32_t *__restrict__ keys, int32_t *__restrict__ vals)
 {
     const int warps = (gridDim.x * blockDim.x) >> 5;
@@ -137,6 +138,7 @@ emit_pairs_kernel(const int32_t *__restrict__ sorted_idx, const int32_t *__restr
         const int i = base + (threadIdx.x & 31);
         int g = 0, n = 0, tx0 = 0, ty0 = 0, w = 1;
         long off = 0;
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
         if (i < G) {
             g = sorted_idx[i];
             n = npairs[g];
@@ -145,9 +147,11 @@ emit_pairs_kernel(const int32_t *__restrict__ sorted_idx, const int32_t *__restr
                 tx0 = rect[g] / TS;
                 ty0 = rect[G + g] / TS;
                 w = rect[2 * G + g] / TS - tx0 + 1;
+                r0 = rec0[g];
+                r1 = rec1[g];
             }
         }
-        emit_pairs_warp(n, off, g, tx0, ty0, w, 0, ntx, cap, keys, vals);
+        emit_pairs_warp(n, off, g, tx0, ty0, w, 0, ntx, tile_reach_of(r0, r1), TS, cap, keys, vals);
     }
 }
 
@@ -361,8 +365,8 @@ extern "C" int avatar_splat_bin(avatar_ctx *ctx, const avatar_splat_args *a, voi
     int32_t *v_emit = (passes % 2 == 0) ? a->pair_gauss : w.pval_b;
     uint32_t *k_other = (passes % 2 == 0) ? w.pkey_b : w.pkey_a;
     int32_t *v_other = (passes % 2 == 0) ? w.pval_b : a->pair_gauss;
-    emit_pairs_kernel<<<grid_cap(ctx, G, 256, 8), 256, 0, st>>>(w.dval_a, w.offsets, w.npairs, a->rect, G, ts, ntx,
-                                                                 cap, k_emit, v_emit);
+    emit_pairs_kernel<<<grid_cap(ctx, G, 256, 8), 256, 0, st>>>(w.dval_a, w.offsets, w.npairs, a->rect, w.rec0,
+                                                                 w.rec1, G, ts, ntx, cap, k_emit, v_emit);
     AV_CHECK_LAUNCH();
     // 4. stable sort of the pairs on the tile id
     AV_TRY(radix_sort(k_emit, v_emit, k_other, v_other, passes * 8, a->num_pairs, (int)cap,

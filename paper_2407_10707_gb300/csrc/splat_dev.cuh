@@ -467,8 +467,11 @@ inline int radix_sort(uint32_t *k0, int32_t *v0, uint32_t *k1, int32_t *v1, int 
     return AVATAR_OK;
 }
 
+// Bits of a tile sort over ntiles tiles: 2^bits >= ntiles + 1, so that
+// KEY_NO_TILE's sorted bits (all ones) order after every tile.
 inline int bits_for(long ntiles)
 {
+    ++ntiles;
     int b = 0;
     while ((1L << b) < ntiles) ++b;
     return b;
@@ -701,17 +704,82 @@ __device__ __forceinline__ void blend_box(int2 rg, const int32_t *__restrict__ p
     }
 }
 
+// Key of a pair whose Gaussian cannot reach its tile: it sorts after every
+// tile (the tile sort covers bits_for(ntiles) bits, 2^bits > ntiles) and the
+// tile ranges skip it, so no list holds it.
+constexpr uint32_t KEY_NO_TILE = 0xffffffffu;
+
+// The set a Gaussian can reach in the blend, from its blend records: the
+// pixel centres d = p - mean with qa dx^2 + qb dx dy + qc dy^2 + log2 o >=
+// log2(1/255), i.e. the ellipse A dx^2 + 2 Bh dx dy + C dy^2 <= R with
+// A = -qa, Bh = -qb / 2, C = -qc, R = log2 o - log2(1/255).  Held as what
+// the tile test needs: the centre, 1/A, Bh, det = A C - Bh^2, A R, the
+// ellipse's half height ey and dyR, the height of its rightmost point.  A
+// Gaussian whose ellipse is degenerate (or not finite) keeps every tile of
+// its rect: AR = 3e38 makes the test pass.
+struct TileReach {
+    float u, v, iA, Bh, det, AR, ey, dyR;
+};
+
+__device__ __forceinline__ TileReach tile_reach_of(float4 r0, float4 r1)
+{
+    TileReach t;
+    t.u = r0.x;
+    t.v = r0.y;
+    const float A = -r0.z, Bh = -0.5f * r0.w, C = -r1.x, R = r1.y - LOG2_ALPHA_MIN;
+    const float det = A * C - Bh * Bh;
+    if (A > 0.f && C > 0.f && R > 0.f && det > 1e-6f * A * C && det < 3e38f && R < 3e38f) {
+        const float ex = sqrtf(R * C / det);
+        t.ey = sqrtf(R * A / det);
+        t.dyR = -Bh * ex / C;
+        t.iA = 1.f / A;
+        t.Bh = Bh;
+        t.det = det;
+        t.AR = A * R;
+    } else {
+        t.ey = 3e38f;
+        t.dyR = 0.f;
+        t.iA = 1.f;
+        t.Bh = 0.f;
+        t.det = 0.f;
+        t.AR = 3e38f;
+    }
+    return t;
+}
+
+// Whether the ellipse comes within one pixel of tile (tx, ty)'s pixel
+// square [TS tx, TS (tx + 1)] x [TS ty, TS (ty + 1)] (pixel edges).  The band
+// of the padded square's rows, clipped to the ellipse's height, holds the
+// ellipse's x range [xl, xr]: the right boundary dx = (-Bh dy + sqrt(AR -
+// det dy^2)) / A is concave in dy, so its maximum over the band is at dyR
+// clamped into it (the left boundary's minimum at -dyR likewise).  The
+// padding keeps the test conservative by 1.5 pixels beyond every pixel
+// centre of the tile, far above the FP32 rounding of either side.
+__device__ __forceinline__ bool tile_reached(const TileReach &t, int tx, int ty, int TS)
+{
+    const float lo = fmaxf((float)(TS * ty) - 1.f - t.v, -t.ey);
+    const float hi = fminf((float)(TS * ty + TS) + 1.f - t.v, t.ey);
+    if (lo > hi) return false;
+    const float dr = fminf(fmaxf(t.dyR, lo), hi), dl = fminf(fmaxf(-t.dyR, lo), hi);
+    const float xr = (-t.Bh * dr + sqrtf(fmaxf(0.f, t.AR - t.det * dr * dr))) * t.iA;
+    const float xl = (-t.Bh * dl - sqrtf(fmaxf(0.f, t.AR - t.det * dl * dl))) * t.iA;
+    return xr >= (float)(TS * tx) - 1.f - t.u && xl <= (float)(TS * tx + TS) + 1.f - t.u;
+}
+
 // Pair emission by one warp for 32 consecutive Gaussians of the depth order
 // (lane j: n pairs starting at output offset off; an offset scan in that
 // order makes the warp's pairs one contiguous range).  The warp writes the
 // range slot by slot: lane j takes slot c + j, finds the Gaussian owning it
 // by a binary search over the lanes' inclusive counts, and its tile from the
 // slot's place in that Gaussian's tile rectangle (w tiles wide, row-major
-// from (tx0, ty0)); key = kbase + ty kstride + tx, value gval.  Every store
-// is coalesced; slots at or beyond cap are not written.
+// from (tx0, ty0)); key = kbase + ty kstride + tx, value gval, or
+// KEY_NO_TILE where the Gaussian's ellipse cannot reach the tile (the rect
+// is the ellipse's bounding box: about a fifth of its tiles lie in the
+// corners the ellipse misses).  Every store is coalesced; slots at or beyond
+// cap are not written.
 __device__ __forceinline__ void emit_pairs_warp(int n, long off, int gval, int tx0, int ty0, int w, int kbase,
-                                                int kstride, long cap, uint32_t *__restrict__ keys,
-                                                int32_t *__restrict__ vals)
+                                                int kstride, const TileReach &tr, int TS, long cap,
+                                                uint32_t *__restrict__ keys, int32_t *__restrict__ vals)
 {
     const int lane = threadIdx.x & 31;
     int incl = n;
@@ -738,11 +806,21 @@ __device__ __forceinline__ void emit_pairs_warp(int n, long off, int gval, int t
         const int o_w = __shfl_sync(0xffffffffu, w, own);
         const int o_base = __shfl_sync(0xffffffffu, kbase, own);
         const int o_stride = __shfl_sync(0xffffffffu, kstride, own);
+        TileReach o_tr;
+        o_tr.u = __shfl_sync(0xffffffffu, tr.u, own);
+        o_tr.v = __shfl_sync(0xffffffffu, tr.v, own);
+        o_tr.iA = __shfl_sync(0xffffffffu, tr.iA, own);
+        o_tr.Bh = __shfl_sync(0xffffffffu, tr.Bh, own);
+        o_tr.det = __shfl_sync(0xffffffffu, tr.det, own);
+        o_tr.AR = __shfl_sync(0xffffffffu, tr.AR, own);
+        o_tr.ey = __shfl_sync(0xffffffffu, tr.ey, own);
+        o_tr.dyR = __shfl_sync(0xffffffffu, tr.dyR, own);
         const long dst = start + sl;
         if (sl < total && dst < cap) {
             const int local = sl - o_excl;
             const int q = (int)__fdividef((float)local + 0.5f, (float)o_w);  // exact for local < 2^22
-            keys[dst] = (uint32_t)(o_base + (o_ty0 + q) * o_stride + o_tx0 + (local - q * o_w));
+            const int tx = o_tx0 + (local - q * o_w), ty = o_ty0 + q;
+            keys[dst] = tile_reached(o_tr, tx, ty, TS) ? (uint32_t)(o_base + ty * o_stride + tx) : KEY_NO_TILE;
             vals[dst] = o_g;
         }
     }

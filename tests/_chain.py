@@ -13,7 +13,9 @@ so each stage is compared on identical inputs:
               for bit, colours within 2e-4 for every Gaussian
   projection  GPU positions and covariances -> orc_project: means, conics and
               depths relative, rects exactly away from flagged bounds
-  binning     GPU rects + depth keys -> orc_bin: the pair list bit for bit
+  binning     GPU rects + depth keys -> orc_bin: the pair count bit for bit,
+              each tile list the oracle's in order less pairs whose ellipse
+              misses the tile, complete at every checked pixel
   compositing GPU projection + colours -> orc_composite (brute force over
               all Gaussians): colours and final transmittance within 2e-4,
               except the pixels the oracle flags ambiguous, counted
@@ -28,7 +30,7 @@ Inputs come from the seeded generator; expected values from the oracle only.
 """
 import numpy as np
 
-from _common import O, f32, light_ordered_bits, rel_err
+from _common import O, check_tile_lists, f32, light_ordered_bits, rel_err
 
 PIX_TOL = 2e-4
 
@@ -131,16 +133,17 @@ def chain_check(r, sc, pixels=None, two_sided=True):
     rep["rects_flagged"] = int((valid & ~sure).sum())
     assert bad == 0, f"{bad} unflagged rects differ"
     assert np.all(g["rect"][~valid, 2] < g["rect"][~valid, 0]), "an invalid Gaussian has a non-empty rect"
-    # (d2, d3) tile lists from the GPU's rects and depth keys
+    # (d2, d3) tile lists from the GPU's rects and depth keys: the pair count
+    # bit for bit, each list the oracle's in its order less pairs whose
+    # ellipse cannot reach the tile, complete at the checked pixels
     W, H = sc.camera.width, sc.camera.height
     start, lst = O.bin_tiles(g["rect"], g["depth"].astype(np.float32).view(np.uint32).copy(), W, H, g["tile"])
     rep["pairs"] = int(len(lst))
     assert len(g["pairs"]) == len(lst), f"{len(g['pairs'])} pairs against the oracle's {len(lst)}"
-    assert np.array_equal(g["pairs"], lst), f"{int((g['pairs'] != lst).sum())} pair entries differ"
-    cnt = g["tile_range"][:, 1] - g["tile_range"][:, 0]
-    assert np.array_equal(cnt, np.diff(start))
-    ne = np.diff(start) > 0
-    assert np.array_equal(g["tile_range"][ne, 0], start[:-1][ne])
+    kept, _, need = check_tile_lists(g["pairs"], g["tile_range"], start, lst, g["mean2d"], g["conic"],
+                                     f32(_opacity(sc)), W, H, g["tile"], pixels)
+    rep["pairs_listed"] = kept
+    rep["pair_reaches_checked"] = need
     # (d4) compositing from the GPU's projection and colours, brute force
     rgb, T, count, amb = O.composite(f32(g["mean2d"]).astype(np.float64), f32(g["conic"]).astype(np.float64), op,
                                      f32(g["color"]).astype(np.float64), f32(g["depth"]).astype(np.float64),

@@ -70,8 +70,10 @@ def test_workload_counts_follow_their_definitions():
     assert st["traversed_pairs"] == int(r.sb.n_last.sum())
 
 
-@pytest.mark.parametrize("ntiles,passes", [(4096, 2), (256, 1), (257, 2), (70000, 3)])
+@pytest.mark.parametrize("ntiles,passes", [(4096, 2), (255, 1), (256, 2), (70000, 3)])
 def test_tile_sort_passes_and_launch_count(ntiles, passes):
+    """The tile sort covers the tile ids and the no-tile key above them
+    (2^bits > ntiles): 255 tiles fit one 8-bit pass, 256 take two."""
     r, sc = _frame(ntiles=ntiles)
     st = bench.workload_stats(r, sc)
     assert st["tile_sort_passes"] == passes

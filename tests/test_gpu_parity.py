@@ -16,7 +16,7 @@ normalised vectors, covariances and the 512-term shading sums.
 import numpy as np
 import pytest
 
-from _common import O, OP, f32, light_ordered_bits, oracle_frame, rel_err, scene, synth
+from _common import O, OP, check_tile_lists, f32, light_ordered_bits, oracle_frame, rel_err, scene, synth
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -296,7 +296,10 @@ def test_project_matches_oracle(gpu, name):
 
 
 @pytest.mark.parametrize("tile", [8, 16, 32])
-def test_bin_tile_lists_bit_exact(gpu, tile):
+def test_bin_tile_lists_against_oracle(gpu, tile):
+    """The pair count bit for bit; each tile list the oracle's rect list of
+    that tile in its (depth, index) order less pairs whose ellipse cannot
+    reach the tile, and complete at every pixel (tests/_common.py)."""
     api, render = gpu
     sc, ref, xd, cov, op, col, cull = _splat_inputs("c1_small")
     pr = O.project(xd.astype(np.float64), cov.astype(np.float64), op.astype(np.float64), cull, sc.camera)
@@ -315,11 +318,11 @@ def test_bin_tile_lists_bit_exact(gpu, tile):
     api.raise_on_status(status)
     P = int(N(b.num_pairs)[0])
     assert P == len(lst)
-    assert np.array_equal(N(b.pair_gauss)[:P], lst)
-    rng_ = N(b.tile_range)
-    assert np.array_equal(rng_[:, 1] - rng_[:, 0], np.diff(start))
-    nonempty = np.diff(start) > 0
-    assert np.array_equal(rng_[nonempty, 0], start[:-1][nonempty])
+    kept, total, need = check_tile_lists(N(b.pair_gauss)[:P], N(b.tile_range), start, lst, f32(pr["mean2d"]),
+                                         f32(pr["conic"]), op.astype(np.float32), sc.camera.width,
+                                         sc.camera.height, tile)
+    print(f"tile {tile}: {kept} of {total} pairs listed, {need} (pixel, Gaussian) reaches checked")
+    assert 0 < kept <= total and need > 0
 
 
 @pytest.mark.parametrize("name,tile,ppt", [("c1_small", 16, 1), ("c3_fd", 8, 1), ("c1_small", 32, 1),
