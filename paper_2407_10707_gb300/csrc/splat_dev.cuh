@@ -162,6 +162,69 @@ __device__ __forceinline__ void make_records(float mx, float my, float ca, float
     rec2 = make_float4(r, g, b, o);
 }
 
+// The set a Gaussian can reach in the blend, from its blend records: the
+// pixel centres d = p - mean with qa dx^2 + qb dx dy + qc dy^2 + log2 o >=
+// log2(1/255), i.e. the ellipse A dx^2 + 2 Bh dx dy + C dy^2 <= R with
+// A = -qa, Bh = -qb / 2, C = -qc, R = log2 o - log2(1/255).  Held as what
+// the tile test needs: the centre, 1/A, Bh, det = A C - Bh^2, A R, the
+// ellipse's half height ey and dyR, the height of its rightmost point.  A
+// Gaussian whose ellipse is degenerate (or not finite) keeps every tile of
+// its rect: AR = 3e38 makes the test pass.
+struct TileReach {
+    float u, v, iA, Bh, det, AR, ey, dyR;
+};
+
+__device__ __forceinline__ TileReach tile_reach_of(float4 r0, float4 r1)
+{
+    TileReach t;
+    t.u = r0.x;
+    t.v = r0.y;
+    const float A = -r0.z, Bh = -0.5f * r0.w, C = -r1.x, R = r1.y - LOG2_ALPHA_MIN;
+    const float det = A * C - Bh * Bh;
+    if (A > 0.f && C > 0.f && R > 0.f && det > 1e-6f * A * C && det < 3e38f && R < 3e38f) {
+        const float ex = sqrtf(R * C / det);
+        t.ey = sqrtf(R * A / det);
+        t.dyR = -Bh * ex / C;
+        t.iA = 1.f / A;
+        t.Bh = Bh;
+        t.det = det;
+        t.AR = A * R;
+    } else {
+        t.ey = 3e38f;
+        t.dyR = 0.f;
+        t.iA = 1.f;
+        t.Bh = 0.f;
+        t.det = 0.f;
+        t.AR = 3e38f;
+    }
+    return t;
+}
+
+// Whether the ellipse comes within one pixel of the pixel rectangle [x0, x1]
+// x [y0, y1] (pixel edges).  The band of the padded rectangle's rows,
+// clipped to the ellipse's height, holds the ellipse's x range [xl, xr]: the
+// right boundary dx = (-Bh dy + sqrt(AR - det dy^2)) / A is concave in dy,
+// so its maximum over the band is at dyR clamped into it (the left
+// boundary's minimum at -dyR likewise).  The padding keeps the test
+// conservative by 1.5 pixels beyond every pixel centre of the rectangle, far
+// above the FP32 rounding of either side.
+__device__ __forceinline__ bool rect_reached(const TileReach &t, float x0, float x1, float y0, float y1)
+{
+    const float lo = fmaxf(y0 - 1.f - t.v, -t.ey);
+    const float hi = fminf(y1 + 1.f - t.v, t.ey);
+    if (lo > hi) return false;
+    const float dr = fminf(fmaxf(t.dyR, lo), hi), dl = fminf(fmaxf(-t.dyR, lo), hi);
+    const float xr = (-t.Bh * dr + sqrtf(fmaxf(0.f, t.AR - t.det * dr * dr))) * t.iA;
+    const float xl = (-t.Bh * dl - sqrtf(fmaxf(0.f, t.AR - t.det * dl * dl))) * t.iA;
+    return xr >= x0 - 1.f - t.u && xl <= x1 + 1.f - t.u;
+}
+
+// Tile (tx, ty)'s pixel square [TS tx, TS (tx + 1)] x [TS ty, TS (ty + 1)].
+__device__ __forceinline__ bool tile_reached(const TileReach &t, int tx, int ty, int TS)
+{
+    return rect_reached(t, (float)(TS * tx), (float)(TS * tx + TS), (float)(TS * ty), (float)(TS * ty + TS));
+}
+
 // ---------------------------------------------------------------- scans
 __device__ __forceinline__ int chunk_range(int n, int NB, int b, int &begin)
 {
@@ -544,7 +607,8 @@ tile_ranges_kernel(const uint32_t *__restrict__ keys, const int32_t *__restrict_
 // One CTA per TS x TS tile.  Warp w owns an 8 x (4 PPT) pixel box of the
 // tile (lane l, pixel k at (l % 8, l / 8 + 4 k) inside it); Gaussians are
 // staged NTH at a time in shared memory, and a warp skips every Gaussian
-// whose pixel rect misses its box (no pixel there can reach alpha = 1/255).
+// whose pixel rect misses its box, or whose ellipse (alpha >= 1/255) cannot
+// come within a pixel of it (no pixel there can reach alpha = 1/255).
 template <int TS, int PPT>
 struct BoxMap {
     static constexpr int BW = 8, BH = 4 * PPT, BPR = TS / BW;
@@ -566,9 +630,10 @@ constexpr int BWD_WARPS = 4;
 // the box's pixels of image [3][H][W], T_final and n_last.  The list is
 // walked 32 entries at a time: each batch's records go to the warp's two
 // buffers (s0/s1/s2 [2][32]) by asynchronous copies while the previous batch
-// is walked, the lanes test the batch's rects against the box for a hit
-// mask (a Gaussian whose rect misses the box cannot reach alpha = 1/255 in
-// it), hits are evaluated two at a time (their exponents are independent of
+// is walked, the lanes test the batch's rects and ellipses against the box
+// for a hit mask (a Gaussian whose rect misses the box, or whose ellipse
+// does not come within a pixel of it, cannot reach alpha = 1/255 in it; a
+// fifth of the rect hits are such), hits are evaluated two at a time (their exponents are independent of
 // T), and the warp leaves as soon as its own pixels are saturated.
 template <int TS, int PPT>
 __device__ __forceinline__ void blend_box(int2 rg, const int32_t *__restrict__ pair_gauss,
@@ -637,6 +702,8 @@ __device__ __forceinline__ void blend_box(int2 rg, const int32_t *__restrict__ p
                 const int ra = __float_as_int(r1.z), rc = __float_as_int(r1.w);
                 hit = (rc & 0xffff) >= bx0 && (ra & 0xffff) <= bx1 && (int)((unsigned)rc >> 16) >= by0 &&
                       (int)((unsigned)ra >> 16) <= by1;
+                hit = hit && rect_reached(tile_reach_of(s0[b][lane], r1), (float)bx0, (float)(bx1 + 1), (float)by0,
+                                          (float)(by1 + 1));
             }
             unsigned hits = __ballot_sync(0xffffffffu, hit);
             // one Gaussian's contribution to pixel k (the front-to-back step),
@@ -709,63 +776,6 @@ __device__ __forceinline__ void blend_box(int2 rg, const int32_t *__restrict__ p
 // tile ranges skip it, so no list holds it.
 constexpr uint32_t KEY_NO_TILE = 0xffffffffu;
 
-// The set a Gaussian can reach in the blend, from its blend records: the
-// pixel centres d = p - mean with qa dx^2 + qb dx dy + qc dy^2 + log2 o >=
-// log2(1/255), i.e. the ellipse A dx^2 + 2 Bh dx dy + C dy^2 <= R with
-// A = -qa, Bh = -qb / 2, C = -qc, R = log2 o - log2(1/255).  Held as what
-// the tile test needs: the centre, 1/A, Bh, det = A C - Bh^2, A R, the
-// ellipse's half height ey and dyR, the height of its rightmost point.  A
-// Gaussian whose ellipse is degenerate (or not finite) keeps every tile of
-// its rect: AR = 3e38 makes the test pass.
-struct TileReach {
-    float u, v, iA, Bh, det, AR, ey, dyR;
-};
-
-__device__ __forceinline__ TileReach tile_reach_of(float4 r0, float4 r1)
-{
-    TileReach t;
-    t.u = r0.x;
-    t.v = r0.y;
-    const float A = -r0.z, Bh = -0.5f * r0.w, C = -r1.x, R = r1.y - LOG2_ALPHA_MIN;
-    const float det = A * C - Bh * Bh;
-    if (A > 0.f && C > 0.f && R > 0.f && det > 1e-6f * A * C && det < 3e38f && R < 3e38f) {
-        const float ex = sqrtf(R * C / det);
-        t.ey = sqrtf(R * A / det);
-        t.dyR = -Bh * ex / C;
-        t.iA = 1.f / A;
-        t.Bh = Bh;
-        t.det = det;
-        t.AR = A * R;
-    } else {
-        t.ey = 3e38f;
-        t.dyR = 0.f;
-        t.iA = 1.f;
-        t.Bh = 0.f;
-        t.det = 0.f;
-        t.AR = 3e38f;
-    }
-    return t;
-}
-
-// Whether the ellipse comes within one pixel of tile (tx, ty)'s pixel
-// square [TS tx, TS (tx + 1)] x [TS ty, TS (ty + 1)] (pixel edges).  The band
-// of the padded square's rows, clipped to the ellipse's height, holds the
-// ellipse's x range [xl, xr]: the right boundary dx = (-Bh dy + sqrt(AR -
-// det dy^2)) / A is concave in dy, so its maximum over the band is at dyR
-// clamped into it (the left boundary's minimum at -dyR likewise).  The
-// padding keeps the test conservative by 1.5 pixels beyond every pixel
-// centre of the tile, far above the FP32 rounding of either side.
-__device__ __forceinline__ bool tile_reached(const TileReach &t, int tx, int ty, int TS)
-{
-    const float lo = fmaxf((float)(TS * ty) - 1.f - t.v, -t.ey);
-    const float hi = fminf((float)(TS * ty + TS) + 1.f - t.v, t.ey);
-    if (lo > hi) return false;
-    const float dr = fminf(fmaxf(t.dyR, lo), hi), dl = fminf(fmaxf(-t.dyR, lo), hi);
-    const float xr = (-t.Bh * dr + sqrtf(fmaxf(0.f, t.AR - t.det * dr * dr))) * t.iA;
-    const float xl = (-t.Bh * dl - sqrtf(fmaxf(0.f, t.AR - t.det * dl * dl))) * t.iA;
-    return xr >= (float)(TS * tx) - 1.f - t.u && xl <= (float)(TS * tx + TS) + 1.f - t.u;
-}
-
 // Pair emission by one warp for 32 consecutive Gaussians of the depth order
 // (lane j: n pairs starting at output offset off; an offset scan in that
 // order makes the warp's pairs one contiguous range).  The warp writes the
@@ -831,8 +841,8 @@ __device__ __forceinline__ void emit_pairs_warp(int n, long off, int gval, int t
 // checkpoint (T_final, n_last), starting at the box's largest n_last, 32
 // entries at a time.  Each batch's records go to the warp's two buffers
 // (s0/s1/s2/sg [2][32]) by asynchronous copies while the previous batch is
-// walked, and the lanes test the batch's rects against the box for a hit
-// mask, so no warp waits for another.  Per hit Gaussian the warp's nine sums
+// walked, and the lanes test the batch's rects and ellipses against the box
+// for a hit mask, so no warp waits for another.  Per hit Gaussian the warp's nine sums
 // (d_color [3][cs], d_opacity [cs], d_mean2d [2][cs], d_conic [3][cs] at the
 // Gaussian's pair value) are reduced together (eight by recursive halving,
 // the ninth by a butterfly) and added by nine lanes with one atomic each.
@@ -911,6 +921,8 @@ __device__ __forceinline__ void blend_backward_box(int2 rg, const int32_t *__res
             const int ra = __float_as_int(q1.z), rc = __float_as_int(q1.w);
             hit = (rc & 0xffff) >= bx0 && (ra & 0xffff) <= bx1 && (int)((unsigned)rc >> 16) >= by0 &&
                   (int)((unsigned)ra >> 16) <= by1;
+            hit = hit && rect_reached(tile_reach_of(s0[b][lane], q1), (float)bx0, (float)(bx1 + 1), (float)by0,
+                                      (float)(by1 + 1));
         }
         unsigned hits = __ballot_sync(0xffffffffu, hit);
         while (hits) {
