@@ -200,29 +200,54 @@ __device__ __forceinline__ TileReach tile_reach_of(float4 r0, float4 r1)
     return t;
 }
 
-// Whether the ellipse comes within one pixel of the pixel rectangle [x0, x1]
-// x [y0, y1] (pixel edges).  The band of the padded rectangle's rows,
-// clipped to the ellipse's height, holds the ellipse's x range [xl, xr]: the
-// right boundary dx = (-Bh dy + sqrt(AR - det dy^2)) / A is concave in dy,
-// so its maximum over the band is at dyR clamped into it (the left
-// boundary's minimum at -dyR likewise).  The padding keeps the test
-// conservative by 1.5 pixels beyond every pixel centre of the rectangle, far
-// above the FP32 rounding of either side.
-__device__ __forceinline__ bool rect_reached(const TileReach &t, float x0, float x1, float y0, float y1)
+// The regions of a tile that a Gaussian's ellipse comes within one pixel
+// of: the tile split into 2 columns x 4 rows of (TS / 2) x (TS / 4) pixels,
+// bit 2 ry + rx.  Per row band (padded by one pixel, clipped to the
+// ellipse's height) the ellipse's x range [xl, xr]: the right boundary
+// dx = (-Bh dy + sqrt(AR - det dy^2)) / A is concave in dy, so its maximum
+// over the band is at dyR clamped into it (the left boundary's minimum at
+// -dyR likewise); a column is reached where that range meets it, padded by
+// one pixel.  The padding keeps the test conservative by 1.5 pixels beyond
+// every pixel centre of a region, far above the FP32 rounding of either
+// side.  At 16-pixel tiles a region is exactly one blend pixel box of one
+// pixel per thread, so the blend's hit test becomes a bit test.
+constexpr int REGION_SHIFT = 24;  // the mask's place in a pair key (tile ids below 2^24)
+__device__ __forceinline__ unsigned tile_regions(const TileReach &t, int tx, int ty, int TS)
 {
-    const float lo = fmaxf(y0 - 1.f - t.v, -t.ey);
-    const float hi = fminf(y1 + 1.f - t.v, t.ey);
-    if (lo > hi) return false;
-    const float dr = fminf(fmaxf(t.dyR, lo), hi), dl = fminf(fmaxf(-t.dyR, lo), hi);
-    const float xr = (-t.Bh * dr + sqrtf(fmaxf(0.f, t.AR - t.det * dr * dr))) * t.iA;
-    const float xl = (-t.Bh * dl - sqrtf(fmaxf(0.f, t.AR - t.det * dl * dl))) * t.iA;
-    return xr >= x0 - 1.f - t.u && xl <= x1 + 1.f - t.u;
+    unsigned m = 0u;
+    // xa, xb: the tile's padded left and right edges, xm its middle (relative to the centre)
+    const float xa = (float)(TS * tx) - 1.f - t.u, xm = xa + 1.f + 0.5f * TS, xb = (float)(TS * tx + TS) + 1.f - t.u;
+#pragma unroll
+    for (int ry = 0; ry < 4; ++ry) {
+        const float y0 = (float)(TS * ty) + 0.25f * TS * ry;
+        const float lo = fmaxf(y0 - 1.f - t.v, -t.ey);
+        const float hi = fminf(y0 + 0.25f * TS + 1.f - t.v, t.ey);
+        if (lo > hi) continue;
+        const float dr = fminf(fmaxf(t.dyR, lo), hi), dl = fminf(fmaxf(-t.dyR, lo), hi);
+        const float xr = (-t.Bh * dr + sqrtf(fmaxf(0.f, t.AR - t.det * dr * dr))) * t.iA;
+        const float xl = (-t.Bh * dl - sqrtf(fmaxf(0.f, t.AR - t.det * dl * dl))) * t.iA;
+        // column 0 spans [xa, xm + 1], column 1 [xm - 1, xb] (each padded by one pixel)
+        if (xr >= xa && xl <= xm + 1.f) m |= 1u << (2 * ry);
+        if (xr >= xm - 1.f && xl <= xb) m |= 2u << (2 * ry);
+    }
+    return m;
 }
 
-// Tile (tx, ty)'s pixel square [TS tx, TS (tx + 1)] x [TS ty, TS (ty + 1)].
-__device__ __forceinline__ bool tile_reached(const TileReach &t, int tx, int ty, int TS)
+// The regions (bits as in tile_regions) that blend pixel box wbox of a TS
+// tile overlaps: the box is 8 x 4 PPT pixels, BoxMap's layout.
+template <int TS, int PPT>
+__device__ __forceinline__ unsigned box_regions(int wbox)
 {
-    return rect_reached(t, (float)(TS * tx), (float)(TS * tx + TS), (float)(TS * ty), (float)(TS * ty + TS));
+    constexpr int BW = 8, BH = 4 * PPT, BPR = TS / BW, RW = TS / 2, RH = TS / 4;
+    const int x0 = (wbox % BPR) * BW, y0 = (wbox / BPR) * BH;
+    unsigned m = 0u;
+#pragma unroll
+    for (int ry = 0; ry < 4; ++ry)
+#pragma unroll
+        for (int rx = 0; rx < 2; ++rx)
+            if (rx * RW < x0 + BW && x0 < (rx + 1) * RW && ry * RH < y0 + BH && y0 < (ry + 1) * RH)
+                m |= 1u << (2 * ry + rx);
+    return m;
 }
 
 // ---------------------------------------------------------------- scans
@@ -540,6 +565,15 @@ inline int bits_for(long ntiles)
     return b;
 }
 
+// Pair keys carry region masks above the tile id where the tile sort's
+// passes stay below REGION_SHIFT (always for one frame: at most 2^22 tiles).
+inline bool has_regions(long ntiles)
+{
+    const int tb = bits_for(ntiles);
+    return (tb <= 8 ? 8 : (tb + 7) / 8 * 8) <= REGION_SHIFT;
+}
+inline uint32_t tile_key_mask(long ntiles) { return has_regions(ntiles) ? (1u << REGION_SHIFT) - 1u : 0xffffffffu; }
+
 // ---------------------------------------------------------------- pair scan
 __global__ void __launch_bounds__(1024)
 pair_scan_reduce_kernel(const int32_t *__restrict__ sorted_idx, const int32_t *__restrict__ npairs, int G, int NB,
@@ -590,16 +624,16 @@ pair_scan_down_kernel(const int32_t *__restrict__ sorted_idx, const int32_t *__r
 
 __global__ void __launch_bounds__(256)
 tile_ranges_kernel(const uint32_t *__restrict__ keys, const int32_t *__restrict__ num_pairs, long cap, int ntiles,
-                   int2 *__restrict__ ranges)
+                   uint32_t tile_mask, int2 *__restrict__ ranges)
 {
     // after an overflow the pair list is incomplete: leave every tile empty
     if ((long)*num_pairs > cap) return;
     int n = *num_pairs;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        uint32_t t = keys[i];
+        uint32_t t = keys[i] & tile_mask;  // the tile id below the region mask
         if (t >= (uint32_t)ntiles) continue;
-        if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
-        if (i == n - 1 || keys[i + 1] != t) ranges[t].y = i + 1;
+        if (i == 0 || (keys[i - 1] & tile_mask) != t) ranges[t].x = i;
+        if (i == n - 1 || (keys[i + 1] & tile_mask) != t) ranges[t].y = i + 1;
     }
 }
 
@@ -607,8 +641,9 @@ tile_ranges_kernel(const uint32_t *__restrict__ keys, const int32_t *__restrict_
 // One CTA per TS x TS tile.  Warp w owns an 8 x (4 PPT) pixel box of the
 // tile (lane l, pixel k at (l % 8, l / 8 + 4 k) inside it); Gaussians are
 // staged NTH at a time in shared memory, and a warp skips every Gaussian
-// whose pixel rect misses its box, or whose ellipse (alpha >= 1/255) cannot
-// come within a pixel of it (no pixel there can reach alpha = 1/255).
+// whose pixel rect misses its box, or whose ellipse (alpha >= 1/255) reaches
+// none of the tile regions the box overlaps (the region mask in the pair's
+// key): no pixel there can reach alpha = 1/255.
 template <int TS, int PPT>
 struct BoxMap {
     static constexpr int BW = 8, BH = 4 * PPT, BPR = TS / BW;
@@ -630,15 +665,16 @@ constexpr int BWD_WARPS = 4;
 // the box's pixels of image [3][H][W], T_final and n_last.  The list is
 // walked 32 entries at a time: each batch's records go to the warp's two
 // buffers (s0/s1/s2 [2][32]) by asynchronous copies while the previous batch
-// is walked, the lanes test the batch's rects and ellipses against the box
-// for a hit mask (a Gaussian whose rect misses the box, or whose ellipse
-// does not come within a pixel of it, cannot reach alpha = 1/255 in it; a
-// fifth of the rect hits are such), hits are evaluated two at a time (their exponents are independent of
+// is walked, the lanes test the batch's rects and region masks against the
+// box for a hit mask (a Gaussian whose rect misses the box, or whose ellipse
+// reaches none of the regions the box overlaps, cannot reach alpha = 1/255
+// in it; a fifth of the rect hits are such), hits are evaluated two at a time (their exponents are independent of
 // T), and the warp leaves as soon as its own pixels are saturated.
 template <int TS, int PPT>
 __device__ __forceinline__ void blend_box(int2 rg, const int32_t *__restrict__ pair_gauss,
                                           const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
                                           const float4 *__restrict__ rec2, int W, int H, int tx, int ty, int wbox,
+                                          const uint32_t *__restrict__ pkeys, bool regions,
                                           float *__restrict__ image, float *__restrict__ T_final,
                                           int32_t *__restrict__ n_last, float4 (*s0)[32], float4 (*s1)[32],
                                           float4 (*s2)[32])
@@ -680,16 +716,24 @@ __device__ __forceinline__ void blend_box(int2 rg, const int32_t *__restrict__ p
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
     auto gauss = [&](int idx) { return idx < n ? pair_gauss[rg.x + idx] : 0; };
+    // the entry's key: its region mask above REGION_SHIFT (all ones without
+    // masks), tested against the regions this box overlaps
+    auto keyat = [&](int idx) { return regions && idx < n ? pkeys[rg.x + idx] : 0xffffffffu; };
+    const unsigned bmask = box_regions<TS, PPT>(wbox);
     if (n > 0 && __any_sync(0xffffffffu, any_live)) {
-        // indices run two batches ahead of the walk and records one, so
-        // neither load's latency is waited for in the loop
+        // indices and keys run two batches ahead of the walk and records one,
+        // so no load's latency is waited for in the loop
         int g_next = gauss(32 + lane);
+        uint32_t k_next = keyat(32 + lane);
         issue(0, 0, gauss(lane));
+        uint32_t k_cur = keyat(lane);
         int b = 0;
         for (int base = 0; base < n; base += 32, b ^= 1) {
             const bool more = base + 32 < n;
             if (more) issue(base + 32, b ^ 1, g_next);
+            const uint32_t k_issued = k_next;
             g_next = gauss(base + 64 + lane);
+            k_next = keyat(base + 64 + lane);
             if (more)
                 asm volatile("cp.async.wait_group 1;" ::: "memory");
             else
@@ -701,9 +745,7 @@ __device__ __forceinline__ void blend_box(int2 rg, const int32_t *__restrict__ p
                 const float4 r1 = s1[b][lane];
                 const int ra = __float_as_int(r1.z), rc = __float_as_int(r1.w);
                 hit = (rc & 0xffff) >= bx0 && (ra & 0xffff) <= bx1 && (int)((unsigned)rc >> 16) >= by0 &&
-                      (int)((unsigned)ra >> 16) <= by1;
-                hit = hit && rect_reached(tile_reach_of(s0[b][lane], r1), (float)bx0, (float)(bx1 + 1), (float)by0,
-                                          (float)(by1 + 1));
+                      (int)((unsigned)ra >> 16) <= by1 && ((k_cur >> REGION_SHIFT) & bmask) != 0u;
             }
             unsigned hits = __ballot_sync(0xffffffffu, hit);
             // one Gaussian's contribution to pixel k (the front-to-back step),
@@ -754,6 +796,7 @@ __device__ __forceinline__ void blend_box(int2 rg, const int32_t *__restrict__ p
             }
             __syncwarp();  // every lane is done with buffer b before it is refilled
             if (!__any_sync(0xffffffffu, any_live)) break;
+            k_cur = k_issued;
         }
         asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy outlives the walk
     }
@@ -785,10 +828,13 @@ constexpr uint32_t KEY_NO_TILE = 0xffffffffu;
 // from (tx0, ty0)); key = kbase + ty kstride + tx, value gval, or
 // KEY_NO_TILE where the Gaussian's ellipse cannot reach the tile (the rect
 // is the ellipse's bounding box: about a fifth of its tiles lie in the
-// corners the ellipse misses).  Every store is coalesced; slots at or beyond
-// cap are not written.
+// corners the ellipse misses).  With regions (tile ids below 2^24), the key
+// carries above REGION_SHIFT the mask of the tile's regions the ellipse
+// reaches, which the blend tests instead of evaluating the ellipse per box;
+// the tile sort covers only the tile bits and moves the mask with the key.
+// Every store is coalesced; slots at or beyond cap are not written.
 __device__ __forceinline__ void emit_pairs_warp(int n, long off, int gval, int tx0, int ty0, int w, int kbase,
-                                                int kstride, const TileReach &tr, int TS, long cap,
+                                                int kstride, const TileReach &tr, int TS, bool regions, long cap,
                                                 uint32_t *__restrict__ keys, int32_t *__restrict__ vals)
 {
     const int lane = threadIdx.x & 31;
@@ -830,7 +876,8 @@ __device__ __forceinline__ void emit_pairs_warp(int n, long off, int gval, int t
             const int local = sl - o_excl;
             const int q = (int)__fdividef((float)local + 0.5f, (float)o_w);  // exact for local < 2^22
             const int tx = o_tx0 + (local - q * o_w), ty = o_ty0 + q;
-            keys[dst] = tile_reached(o_tr, tx, ty, TS) ? (uint32_t)(o_base + ty * o_stride + tx) : KEY_NO_TILE;
+            const unsigned m = tile_regions(o_tr, tx, ty, TS);
+            keys[dst] = m ? (uint32_t)(o_base + ty * o_stride + tx) | (regions ? m << REGION_SHIFT : 0u) : KEY_NO_TILE;
             vals[dst] = o_g;
         }
     }
@@ -841,8 +888,8 @@ __device__ __forceinline__ void emit_pairs_warp(int n, long off, int gval, int t
 // checkpoint (T_final, n_last), starting at the box's largest n_last, 32
 // entries at a time.  Each batch's records go to the warp's two buffers
 // (s0/s1/s2/sg [2][32]) by asynchronous copies while the previous batch is
-// walked, and the lanes test the batch's rects and ellipses against the box
-// for a hit mask, so no warp waits for another.  Per hit Gaussian the warp's nine sums
+// walked, and the lanes test the batch's rects and region masks against the
+// box for a hit mask, so no warp waits for another.  Per hit Gaussian the warp's nine sums
 // (d_color [3][cs], d_opacity [cs], d_mean2d [2][cs], d_conic [3][cs] at the
 // Gaussian's pair value) are reduced together (eight by recursive halving,
 // the ninth by a butterfly) and added by nine lanes with one atomic each.
@@ -850,7 +897,8 @@ template <int TS, int PPT>
 __device__ __forceinline__ void blend_backward_box(int2 rg, const int32_t *__restrict__ pair_gauss,
                                                    const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
                                                    const float4 *__restrict__ rec2, int W, int H, int tx, int ty,
-                                                   int wbox, const float *__restrict__ T_final,
+                                                   int wbox, const uint32_t *__restrict__ pkeys, bool regions,
+                                                   const float *__restrict__ T_final,
                                                    const int32_t *__restrict__ n_last,
                                                    const float *__restrict__ d_image, size_t cs,
                                                    float *__restrict__ d_mean2d, float *__restrict__ d_conic,
@@ -900,15 +948,21 @@ __device__ __forceinline__ void blend_backward_box(int2 rg, const int32_t *__res
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
     auto gauss = [&](int idx) { return idx >= 0 ? pair_gauss[rg.x + idx] : 0; };
+    auto keyat = [&](int idx) { return regions && idx >= 0 ? pkeys[rg.x + idx] : 0xffffffffu; };
+    const unsigned bmask = box_regions<TS, PPT>(wbox);
     if (n == 0) return;
-    // indices run two batches ahead of the walk and records one
+    // indices and keys run two batches ahead of the walk and records one
     int g_next = gauss(n - 64 + lane);
+    uint32_t k_next = keyat(n - 64 + lane);
     issue(n, 0, gauss(n - 32 + lane));
+    uint32_t k_cur = keyat(n - 32 + lane);
     int b = 0;
     for (int end = n; end > 0; end -= 32, b ^= 1) {
         const bool more = end > 32;
         if (more) issue(end - 32, b ^ 1, g_next);
+        const uint32_t k_issued = k_next;
         g_next = gauss(end - 96 + lane);
+        k_next = keyat(end - 96 + lane);
         if (more)
             asm volatile("cp.async.wait_group 1;" ::: "memory");
         else
@@ -920,9 +974,7 @@ __device__ __forceinline__ void blend_backward_box(int2 rg, const int32_t *__res
             const float4 q1 = s1[b][lane];
             const int ra = __float_as_int(q1.z), rc = __float_as_int(q1.w);
             hit = (rc & 0xffff) >= bx0 && (ra & 0xffff) <= bx1 && (int)((unsigned)rc >> 16) >= by0 &&
-                  (int)((unsigned)ra >> 16) <= by1;
-            hit = hit && rect_reached(tile_reach_of(s0[b][lane], q1), (float)bx0, (float)(bx1 + 1), (float)by0,
-                                      (float)(by1 + 1));
+                  (int)((unsigned)ra >> 16) <= by1 && ((k_cur >> REGION_SHIFT) & bmask) != 0u;
         }
         unsigned hits = __ballot_sync(0xffffffffu, hit);
         while (hits) {
@@ -982,6 +1034,7 @@ __device__ __forceinline__ void blend_backward_box(int2 rg, const int32_t *__res
             }
         }
         __syncwarp();  // every lane is done with buffer b before it is refilled
+        k_cur = k_issued;
     }
 }
 
