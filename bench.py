@@ -148,7 +148,11 @@ def run_gpu(args):
     W, H = sc.camera.width, sc.camera.height
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
-    r = render.Renderer(st, tile=args.tile)
+    # tile edge: the fastest of 16 and 32 pixels over ten flushed graph
+    # replays each, chosen apart for the frame and the training step (the
+    # image does not depend on it); setup, before every timed region
+    args.frame_tile, args.train_tile, tile_trials = choose_tiles(render, st, args.tile, flush)
+    r = render.Renderer(st, tile=args.frame_tile)
     r.check()
     r.capture()
     stream = torch.cuda.current_stream()
@@ -177,7 +181,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         # training step: frame + L1 loss + backward of every stage
         tgt = r.sb.image.detach().clone() * 0.9
-        ts = render.TrainStep(st, tgt, tile=args.tile, adam=True)
+        ts = render.TrainStep(st, tgt, tile=args.train_tile, adam=True)
         ts.check()
         ts.capture()
         train_ms = timed(ts.graph.replay, args.steps, args.warmup)
@@ -224,7 +228,9 @@ def run_gpu(args):
         "dtype": "f32",
         "data": "synthetic (seeded procedural capsule-union avatar; paper datasets are not available)",
         "config": {"workload": WORKLOAD_DESC, "gaussians": G, "mesh_vertices": Nv, "faces": F, "lights": NL,
-                   "vis_dirs": D, "vis_res": R, "image": [W, H], "tile": args.tile,
+                   "vis_dirs": D, "vis_res": R, "image": [W, H],
+                   "tile": {"frame": args.frame_tile, "train": args.train_tile, "trial_us": tile_trials,
+                            "how": "fastest of 16 and 32 over ten flushed graph replays each, before timing"},
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "flushed (256 MB write) between timed steps", "graph": "CUDA graph replay",
                    "visibility": "one-sided raster of the closed capsule body (same bits as two-sided)",
@@ -273,6 +279,28 @@ def stored_for_speed(render, synth, sc, dev, attr_dtype="f32"):
     st, _ = render.light_ordered(st, synth.latlong_patch_order(sc.light.rows, sc.light.cols))
     st, _ = render.faces_ordered(st, synth.face_normal_order(sc.avatar.xv, sc.avatar.faces))
     return st
+
+
+def choose_tiles(render, st, tile, flush, reps=10):
+    """(frame tile, train tile, trial times in us): the given edge for both,
+    or per workload the faster of 16 and 32 pixels (graph replays with the L2
+    flushed before each, as the timed region runs them)."""
+    import torch
+    if tile:
+        return tile, tile, None
+    trials = {}
+    for t in (16, 32):
+        r = render.Renderer(st, tile=t)
+        r.check()
+        trials[f"frame_t{t}"] = round(_time_graph(_graph_of(r.forward), reps, flush) * 1000.0, 1)
+        ts = render.TrainStep(st, r.sb.image.detach().clone() * 0.9, tile=t)
+        ts.check()
+        trials[f"train_t{t}"] = round(_time_graph(_graph_of(ts.step), reps, flush) * 1000.0, 1)
+        del r, ts
+    torch.cuda.empty_cache()
+    ft = min((16, 32), key=lambda t: trials[f"frame_t{t}"])
+    tt = min((16, 32), key=lambda t: trials[f"train_t{t}"])
+    return ft, tt, trials
 
 
 def _graph_of(fn):
@@ -656,8 +684,8 @@ def _form_stress(args, dev, flush, reps):
     for dt in ("f32", "bf16"):
         st = stored_for_speed(render, synth, sc, dev, attr_dtype=dt)
         cap = 96 * sc.avatar.G  # about fifty 16-pixel tiles per Gaussian at 2048^2
-        r32 = render.Renderer(st, tile=args.tile, pair_capacity=cap)
-        rtc = render.Renderer(st, tile=args.tile, shade_tc=True, pair_capacity=cap)
+        r32 = render.Renderer(st, tile=args.frame_tile, pair_capacity=cap)
+        rtc = render.Renderer(st, tile=args.frame_tile, shade_tc=True, pair_capacity=cap)
         f32_ms = _time_graph(_graph_of(r32.forward), reps, flush)
         tc_ms = _time_graph(_graph_of(rtc.forward), reps, flush)
         r32.forward()
@@ -672,7 +700,7 @@ def _form_stress(args, dev, flush, reps):
             target = (r32.sb.image.detach().clone() * 0.9).contiguous()
             del r32, rtc
             for name, tc in (("train_steps_per_s_fp32_shading", False), ("train_steps_per_s_tensor_core", True)):
-                ts = render.TrainStep(st, target, tile=args.tile, shade_tc=tc, pair_capacity=cap)
+                ts = render.TrainStep(st, target, tile=args.train_tile, shade_tc=tc, pair_capacity=cap)
                 res[name] = round(1000.0 / _time_graph(_graph_of(ts.step), reps, flush), 3)
                 ts.check()
                 del ts
@@ -732,7 +760,7 @@ def _form_mlp(r, st, args, dev, flush, reps, fwd_ms):
     tf = flops_pt * t["xv"].shape[1] * 64 / (us * 1e-6) / 1e12
     out["average_over_64_poses"] = {"points": int(t["xv"].shape[1]), "poses": 64, "us": round(us, 1),
                                     "achieved_tflops": round(tf, 1), "frac": round(tf / float(peaks["bf16_tflops"]), 4)}
-    rm = render.Renderer(st, tile=args.tile, mlp=w)
+    rm = render.Renderer(st, tile=args.frame_tile, mlp=w)
     rm.check()
     frame_ms = _time_graph(_graph_of(rm.forward), reps, flush)
     out.update({"what": "dx = MLP(gamma(x_v), theta): Fourier features, three ReLU layers of 256 and a linear "
@@ -758,7 +786,7 @@ def _form_knn(r, st, sc, args, dev, flush, reps, fwd_ms):
         ws = api.workspace(1 << 26, dev)
         out[name] = round(_time_graph(_graph_of(lambda: api.avatar_knn(xq, t["xv"], k, out=buf, ws=ws)), reps,
                                       flush) * 1000.0, 1)
-    rb = render.Renderer(st, tile=args.tile, rebind=True)
+    rb = render.Renderer(st, tile=args.frame_tile, rebind=True)
     rb.check()
     frame_ms = _time_graph(_graph_of(rb.forward), reps, flush)
     out.update({"what": "exact K nearest neighbours on the device (uniform grid, FP64 distances of a fixed "
@@ -776,7 +804,7 @@ def _form_paper_vis(r, st, sc, args, dev, flush, reps):
 
     from paper_2407_10707_gb300 import render, synth
     knn_v = torch.as_tensor(synth.vertex_knn(sc.avatar.xv, 19).T.copy(), dtype=torch.int32, device=dev)
-    rp = render.Renderer(st, tile=args.tile, visibility="paper", knn_v=knn_v)
+    rp = render.Renderer(st, tile=args.frame_tile, visibility="paper", knn_v=knn_v)
     rp.check()
     vis_ms = _time_graph(_graph_of(rp.visibility), reps, flush)
     frame_ms = _time_graph(_graph_of(rp.forward), reps, flush)
@@ -796,10 +824,10 @@ def _form_precision(r, st, sc, args, dev, flush, fwd_ms, train_ms, reps):
 
     from paper_2407_10707_gb300 import render, synth
     st16 = stored_for_speed(render, synth, sc, dev, attr_dtype="bf16")
-    r16 = render.Renderer(st16, tile=args.tile, shade_tc=True)
+    r16 = render.Renderer(st16, tile=args.frame_tile, shade_tc=True)
     g16 = _graph_of(r16.forward)
     f16 = _time_graph(g16, reps, flush)
-    ts16 = render.TrainStep(st16, r.sb.image.detach().clone() * 0.9, tile=args.tile, shade_tc=True)
+    ts16 = render.TrainStep(st16, r.sb.image.detach().clone() * 0.9, tile=args.train_tile, shade_tc=True)
     t16 = _time_graph(_graph_of(ts16.step), reps, flush)
     r16.check()
     ts16.check()
@@ -807,7 +835,7 @@ def _form_precision(r, st, sc, args, dev, flush, fwd_ms, train_ms, reps):
     g16.replay()
     torch.cuda.synchronize()
     err = float((r16.sb.image - r.sb.image).abs().max().item())
-    r32tc = render.Renderer(st, tile=args.tile, shade_tc=True)
+    r32tc = render.Renderer(st, tile=args.frame_tile, shade_tc=True)
     err_tc = float((r32tc.sb.image - r.sb.image).abs().max().item())
     shade_tc_ms = _time_graph(_graph_of(r32tc.shade), reps, flush)
     shade_ms = _time_graph(_graph_of(r.shade), reps, flush)
@@ -896,8 +924,8 @@ def _form_batch(args, dev, reps):
                                   light=dataclasses.replace(b.scene.light, L=b.lights[p]),
                                   camera=b.cameras[v])
         stv = stored_for_speed(render, synth, scv, dev)
-        rv = render.Renderer(stv, tile=args.tile)
-        tv = render.TrainStep(stv, rv.sb.image.detach().clone() * 0.9, tile=args.tile)
+        rv = render.Renderer(stv, tile=args.frame_tile)
+        tv = render.TrainStep(stv, rv.sb.image.detach().clone() * 0.9, tile=args.train_tile)
         per[(b.cameras[v].width, b.cameras[v].height)] = (_time_graph(_graph_of(rv.forward), reps),
                                                           _time_graph(_graph_of(tv.step), reps))
     cnt = {}
@@ -1023,7 +1051,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--tile", type=int, default=0, help="tile edge (8, 16, 32); 0 = the faster of 16 and 32")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the precision / relighting / batching forms")
     ap.add_argument("--forms", default="precision,relight,knn,paper_vis,batch,mlp,densify,stress",
