@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(256)
 emit_batch_kernel(const BatchView *__restrict__ views, int G, long long VG, int TS,
                   const int32_t *__restrict__ sorted_idx, const int32_t *__restrict__ offsets,
                   const int32_t *__restrict__ npairs, const int32_t *__restrict__ rect,
-                  const float4 *__restrict__ rec0, const float4 *__restrict__ rec1, bool regions, long cap,
+                  const float4 *__restrict__ rec0, const float4 *__restrict__ rec1, int rmode, long cap,
                   uint32_t *__restrict__ keys, int32_t *__restrict__ vals)
 {
     const size_t cs = (size_t)VG;
@@ -363,7 +363,7 @@ emit_batch_kernel(const BatchView *__restrict__ views, int G, long long VG, int 
                 r1 = rec1[gi];
             }
         }
-        emit_pairs_warp(n, off, gi, tx0, ty0, w, kbase, ntx, tile_reach_of(r0, r1), TS, regions, cap, keys, vals);
+        emit_pairs_warp(n, off, gi, tx0, ty0, w, kbase, ntx, tile_reach_of(r0, r1), TS, rmode, cap, keys, vals);
     }
 }
 
@@ -384,7 +384,7 @@ template <int TS, int PPT>
 __global__ void __launch_bounds__(BWD_WARPS * 32)
 blend_batch_kernel(const BatchView *__restrict__ views, int V, int T, const int2 *__restrict__ ranges,
                    const int32_t *__restrict__ pairs, const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
-                   const float4 *__restrict__ rec2, const uint32_t *__restrict__ pkeys, bool regions, float *images,
+                   const float4 *__restrict__ rec2, const uint32_t *__restrict__ pkeys, int rmode, float *images,
                    float *T_final, int32_t *n_last, int32_t *counter)
 {
     // persistent warps take (tile, pixel box) items from the device counter
@@ -405,7 +405,7 @@ blend_batch_kernel(const BatchView *__restrict__ views, int V, int T, const int2
         const int local = t - views[v].tile_base;
         const size_t po = (size_t)views[v].pix_off;
         blend_box<TS, PPT>(ranges[t], pairs, rec0, rec1, rec2, W, H, local % ntx, local / ntx, it % NB, pkeys,
-                           regions, images + 3 * po, T_final + po, n_last + po, s0[warp], s1[warp], s2[warp]);
+                           rmode, images + 3 * po, T_final + po, n_last + po, s0[warp], s1[warp], s2[warp]);
     }
 }
 
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(BWD_WARPS * 32)
 blend_backward_batch_kernel(const BatchView *__restrict__ views, int V, int T, const int2 *__restrict__ ranges,
                             const int32_t *__restrict__ pairs, const float4 *__restrict__ rec0,
                             const float4 *__restrict__ rec1, const float4 *__restrict__ rec2,
-                            const uint32_t *__restrict__ pkeys, bool regions,
+                            const uint32_t *__restrict__ pkeys, int rmode,
                             const float *__restrict__ T_final, const int32_t *__restrict__ n_last,
                             const float *__restrict__ d_images, long long VG, float *d_mean2d, float *d_conic,
                             float *d_opacity, float *d_color, int32_t *counter)
@@ -438,8 +438,8 @@ blend_backward_batch_kernel(const BatchView *__restrict__ views, int V, int T, c
         const int local = t - views[v].tile_base;
         const size_t po = (size_t)views[v].pix_off;
         blend_backward_box<TS, PPT>(ranges[t], pairs, rec0, rec1, rec2, W, H, local % ntx, local / ntx, it % NB,
-                                    pkeys, regions, T_final + po, n_last + po, d_images + 3 * po, (size_t)VG, d_mean2d, d_conic,
-                                    d_opacity, d_color, s0[warp], s1[warp], s2[warp], sg[warp]);
+                                    pkeys, rmode, T_final + po, n_last + po, d_images + 3 * po, (size_t)VG,
+                                    d_mean2d, d_conic, d_opacity, d_color, s0[warp], s1[warp], s2[warp], sg[warp]);
     }
 }
 
@@ -585,7 +585,7 @@ int launch_blend_batch(const avatar_ctx *ctx, const avatar_batch_desc *d, const 
     const long long wblocks = ((long long)std::max(T, 1) * NB + BWD_WARPS - 1) / BWD_WARPS;
     const int grid = (int)std::min<long long>((long long)ctx->sm_count * per_sm, wblocks);
     kern<<<grid, BWD_WARPS * 32, 0, st>>>(w.views, d->V, T, w.ranges, w.pval_a, w.rec0, w.rec1, w.rec2, w.pkey_a,
-                                         has_regions(T), d->images, w.T_final, w.n_last, w.counter);
+                                         region_mode(T, TS), d->images, w.T_final, w.n_last, w.counter);
     AV_CHECK_LAUNCH();
     return AVATAR_OK;
 }
@@ -602,8 +602,8 @@ int launch_blend_bwd_batch(const avatar_ctx *ctx, const avatar_batch_desc *d, co
     const long long wblocks = ((long long)std::max(T, 1) * NB + BWD_WARPS - 1) / BWD_WARPS;
     const int grid = (int)std::min<long long>((long long)ctx->sm_count * per_sm, wblocks);
     kern<<<grid, BWD_WARPS * 32, 0, st>>>(w.views, d->V, T, w.ranges, w.pval_a, w.rec0, w.rec1, w.rec2, w.pkey_a,
-                                         has_regions(T), w.T_final, w.n_last, g->d_images, m.VG, w.d_mean2d, w.d_conic, w.d_opacity_v,
-                                         w.d_color, w.counter);
+                                         region_mode(T, TS), w.T_final, w.n_last, g->d_images, m.VG, w.d_mean2d,
+                                         w.d_conic, w.d_opacity_v, w.d_color, w.counter);
     AV_CHECK_LAUNCH();
     return AVATAR_OK;
 }
@@ -696,12 +696,12 @@ int render_batch(avatar_ctx *ctx, const avatar_batch_desc *d, void *ws, size_t w
     uint32_t *k_other = (passes % 2 == 0) ? w.pkey_b : w.pkey_a;
     int32_t *v_other = (passes % 2 == 0) ? w.pval_b : w.pval_a;
     emit_batch_kernel<<<grid_cap(ctx, m.VG, 256, 8), 256, 0, st>>>(w.views, m.G, m.VG, TS, w.dval_a, w.offsets,
-                                                                    w.npairs, w.rect, w.rec0, w.rec1, has_regions(T),
-                                                                    (long)m.cap, k_emit, v_emit);
+                                                                    w.npairs, w.rect, w.rec0, w.rec1,
+                                                                    region_mode(T, TS), (long)m.cap, k_emit, v_emit);
     AV_CHECK_LAUNCH();
     AV_TRY(radix_sort(k_emit, v_emit, k_other, v_other, passes * 8, d->num_pairs, (int)m.cap, sw, d->status, st, sort_spin_limit(ctx)));
     tile_ranges_kernel<<<ctx->sm_count * 8, 256, 0, st>>>(w.pkey_a, d->num_pairs, (long)m.cap, (int)T,
-                                                          tile_key_mask(T), w.ranges);
+                                                          tile_key_mask(T, TS), w.ranges);
     AV_CHECK_LAUNCH();
     // persistent blend over every view's tiles
     if (cudaMemsetAsync(w.counter, 0, sizeof(int32_t), st) != cudaSuccess) return AVATAR_ERR_CUDA;

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(256)
 emit_pairs_kernel(const int32_t *__restrict__ sorted_idx, const int32_t *__restrict__ offsets,
                   const int32_t *__restrict__ npairs, const int32_t *__restrict__ rect,
                   const float4 *__restrict__ rec0, const float4 *__restrict__ rec1, int G, int TS, int ntx,
-                  bool regions, long cap, uint32_t *__restrict__ keys, int32_t *__restrict__ vals)
+                  int rmode, long cap, uint32_t *__restrict__ keys, int32_t *__restrict__ vals)
 {
     const int warps = (gridDim.x * blockDim.x) >> 5;
     for (int base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < G; base += warps * 32) {
@@ -151,7 +151,7 @@ emit_pairs_kernel(const int32_t *__restrict__ sorted_idx, const int32_t *__restr
                 r1 = rec1[g];
             }
         }
-        emit_pairs_warp(n, off, g, tx0, ty0, w, 0, ntx, tile_reach_of(r0, r1), TS, regions, cap, keys, vals);
+        emit_pairs_warp(n, off, g, tx0, ty0, w, 0, ntx, tile_reach_of(r0, r1), TS, rmode, cap, keys, vals);
     }
 }
 
@@ -191,7 +191,7 @@ template <int TS, int PPT>
 __global__ void __launch_bounds__(BWD_WARPS * 32)
 blend_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_gauss, const float4 *__restrict__ rec0,
              const float4 *__restrict__ rec1, const float4 *__restrict__ rec2, int W, int H, int ntx, int ntiles,
-             const uint32_t *__restrict__ pkeys, bool regions, float *__restrict__ image,
+             const uint32_t *__restrict__ pkeys, int rmode, float *__restrict__ image,
              float *__restrict__ T_final, int32_t *__restrict__ n_last, const int32_t *__restrict__ torder)
 {
     constexpr int NB = TS * TS / (32 * PPT);  // pixel boxes per tile
@@ -204,7 +204,7 @@ blend_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_g
     if (item >= ntiles * NB) return;      // warp-uniform; the kernel has no CTA barrier
     const int tile = __ldg(torder + item / NBD);
     blend_box<TS, PPT>(ranges[tile], pair_gauss, rec0, rec1, rec2, W, H, tile % ntx, tile / ntx, item % NBD, pkeys,
-                       regions, image, T_final, n_last, s0[warp], s1[warp], s2[warp]);
+                       rmode, image, T_final, n_last, s0[warp], s1[warp], s2[warp]);
 }
 
 // BWD_WARPS independent warps per CTA, each one (tile, pixel box) item.
@@ -212,7 +212,7 @@ template <int TS, int PPT>
 __global__ void __launch_bounds__(BWD_WARPS * 32)
 blend_backward_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict__ pair_gauss,
                       const float4 *__restrict__ rec0, const float4 *__restrict__ rec1, const float4 *__restrict__ rec2,
-                      int W, int H, int ntx, int ntiles, const uint32_t *__restrict__ pkeys, bool regions,
+                      int W, int H, int ntx, int ntiles, const uint32_t *__restrict__ pkeys, int rmode,
                       const float *__restrict__ T_final, const int32_t *__restrict__ n_last,
                       const float *__restrict__ d_image, int G,
                       float *__restrict__ d_mean2d, float *__restrict__ d_conic, float *__restrict__ d_opacity,
@@ -229,8 +229,8 @@ blend_backward_kernel(const int2 *__restrict__ ranges, const int32_t *__restrict
     if (item >= ntiles * NB) return;      // warp-uniform; the kernel has no CTA barrier
     const int tile = __ldg(torder + item / NBD);
     blend_backward_box<TS, PPT>(ranges[tile], pair_gauss, rec0, rec1, rec2, W, H, tile % ntx, tile / ntx, item % NBD,
-                                pkeys, regions, T_final, n_last, d_image, (size_t)G, d_mean2d, d_conic, d_opacity, d_color, s0[warp],
-                                s1[warp], s2[warp], sg[warp]);
+                                pkeys, rmode, T_final, n_last, d_image, (size_t)G, d_mean2d, d_conic, d_opacity,
+                                d_color, s0[warp], s1[warp], s2[warp], sg[warp]);
 }
 
 __global__ void __launch_bounds__(256)
@@ -362,20 +362,20 @@ extern "C" int avatar_splat_bin(avatar_ctx *ctx, const avatar_splat_args *a, voi
     const int ntx = (a->cam.width + ts - 1) / ts;
     int tbits = bits_for(ntiles);
     int passes = tbits <= 8 ? 1 : (tbits + 7) / 8;
-    const bool regions = has_regions(ntiles);
+    const int rmode = region_mode(ntiles, ts);
     uint32_t *k_emit = (passes % 2 == 0) ? w.pkey_a : w.pkey_b;
     int32_t *v_emit = (passes % 2 == 0) ? a->pair_gauss : w.pval_b;
     uint32_t *k_other = (passes % 2 == 0) ? w.pkey_b : w.pkey_a;
     int32_t *v_other = (passes % 2 == 0) ? w.pval_b : a->pair_gauss;
     emit_pairs_kernel<<<grid_cap(ctx, G, 256, 8), 256, 0, st>>>(w.dval_a, w.offsets, w.npairs, a->rect, w.rec0,
-                                                                 w.rec1, G, ts, ntx, regions, cap, k_emit, v_emit);
+                                                                 w.rec1, G, ts, ntx, rmode, cap, k_emit, v_emit);
     AV_CHECK_LAUNCH();
     // 4. stable sort of the pairs on the tile id
     AV_TRY(radix_sort(k_emit, v_emit, k_other, v_other, passes * 8, a->num_pairs, (int)cap,
                        SortWs{w.sort_hist, w.sort_desc}, a->status, st, sort_spin_limit(ctx)));
     // 5. tile ranges (sorted keys are in pkey_a)
-    tile_ranges_kernel<<<ctx->sm_count * 8, 256, 0, st>>>(w.pkey_a, a->num_pairs, cap, ntiles, tile_key_mask(ntiles),
-                                                          (int2 *)a->tile_range);
+    tile_ranges_kernel<<<ctx->sm_count * 8, 256, 0, st>>>(w.pkey_a, a->num_pairs, cap, ntiles,
+                                                          tile_key_mask(ntiles, ts), (int2 *)a->tile_range);
     // 6. the blend's tile order, longest lists first
     tile_order_kernel<<<1, 1024, 0, st>>>((const int2 *)a->tile_range, ntiles, w.tile_order);
     AV_CHECK_LAUNCH();
@@ -389,7 +389,7 @@ void launch_blend(const avatar_splat_args *a, const SplatWs &w, int ntiles, int 
     const int blocks = (int)(((long long)ntiles * NB + BWD_WARPS - 1) / BWD_WARPS);
     blend_kernel<TS, PPT><<<blocks, BWD_WARPS * 32, 0, st>>>((const int2 *)a->tile_range, a->pair_gauss, w.rec0,
                                                              w.rec1, w.rec2, a->cam.width, a->cam.height, ntx, ntiles,
-                                                             w.pkey_a, has_regions(ntiles), a->image, a->T_final,
+                                                             w.pkey_a, region_mode(ntiles, TS), a->image, a->T_final,
                                                              a->n_last, w.tile_order);
 }
 
@@ -440,7 +440,7 @@ void launch_blend_bwd(const avatar_splat_args *a, const avatar_splat_grads *g, c
     const int blocks = (int)(((long long)ntiles * NB + BWD_WARPS - 1) / BWD_WARPS);
     blend_backward_kernel<TS, PPT><<<blocks, BWD_WARPS * 32, 0, st>>>(
         (const int2 *)a->tile_range, a->pair_gauss, w.rec0, w.rec1, w.rec2, a->cam.width, a->cam.height, ntx, ntiles,
-        w.pkey_a, has_regions(ntiles), a->T_final, a->n_last, g->d_image, G, w.d_mean2d, w.d_conic, g->d_opacity,
+        w.pkey_a, region_mode(ntiles, TS), a->T_final, a->n_last, g->d_image, G, w.d_mean2d, w.d_conic, g->d_opacity,
         g->d_color, w.tile_order);
 }
 

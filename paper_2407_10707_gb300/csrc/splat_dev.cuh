@@ -201,22 +201,26 @@ __device__ __forceinline__ TileReach tile_reach_of(float4 r0, float4 r1)
 }
 
 // The regions of a tile that a Gaussian's ellipse comes within one pixel
-// of: the tile split into 2 columns x 4 rows of (TS / 2) x (TS / 4) pixels,
-// bit 2 ry + rx.  Per row band (padded by one pixel, clipped to the
+// of: the tile split into C columns x 4 rows of (TS / C) x (TS / 4) pixels,
+// bit C ry + rx.  Per row band (padded by one pixel, clipped to the
 // ellipse's height) the ellipse's x range [xl, xr]: the right boundary
 // dx = (-Bh dy + sqrt(AR - det dy^2)) / A is concave in dy, so its maximum
 // over the band is at dyR clamped into it (the left boundary's minimum at
 // -dyR likewise); a column is reached where that range meets it, padded by
 // one pixel.  The padding keeps the test conservative by 1.5 pixels beyond
 // every pixel centre of a region, far above the FP32 rounding of either
-// side.  At 16-pixel tiles a region is exactly one blend pixel box of one
-// pixel per thread, so the blend's hit test becomes a bit test.
-constexpr int REGION_SHIFT = 24;  // the mask's place in a pair key (tile ids below 2^24)
-__device__ __forceinline__ unsigned tile_regions(const TileReach &t, int tx, int ty, int TS)
+// side.  Pair keys carry the mask above the tile id: region mode 2 (tile
+// ids below 2^16) a 16-bit mask of 4 x 4 regions at bit 16, mode 1 (below
+// 2^24) an 8-bit mask of 2 x 4 regions at bit 24, mode 0 none.  A blend
+// pixel box of one pixel per thread (8 x 4) is exactly two regions at
+// 16-pixel tiles and half of one at 32.
+__host__ __device__ __forceinline__ int region_shift(int rmode) { return rmode == 2 ? 16 : 24; }
+__host__ __device__ __forceinline__ int region_cols(int rmode) { return rmode == 2 ? 4 : 2; }
+
+__device__ __forceinline__ unsigned tile_regions(const TileReach &t, int tx, int ty, int TS, int cols)
 {
     unsigned m = 0u;
-    // xa, xb: the tile's padded left and right edges, xm its middle (relative to the centre)
-    const float xa = (float)(TS * tx) - 1.f - t.u, xm = xa + 1.f + 0.5f * TS, xb = (float)(TS * tx + TS) + 1.f - t.u;
+    const float x0 = (float)(TS * tx) - t.u, cw = (float)TS / (float)cols;
 #pragma unroll
     for (int ry = 0; ry < 4; ++ry) {
         const float y0 = (float)(TS * ty) + 0.25f * TS * ry;
@@ -226,9 +230,10 @@ __device__ __forceinline__ unsigned tile_regions(const TileReach &t, int tx, int
         const float dr = fminf(fmaxf(t.dyR, lo), hi), dl = fminf(fmaxf(-t.dyR, lo), hi);
         const float xr = (-t.Bh * dr + sqrtf(fmaxf(0.f, t.AR - t.det * dr * dr))) * t.iA;
         const float xl = (-t.Bh * dl - sqrtf(fmaxf(0.f, t.AR - t.det * dl * dl))) * t.iA;
-        // column 0 spans [xa, xm + 1], column 1 [xm - 1, xb] (each padded by one pixel)
-        if (xr >= xa && xl <= xm + 1.f) m |= 1u << (2 * ry);
-        if (xr >= xm - 1.f && xl <= xb) m |= 2u << (2 * ry);
+        // column c spans [x0 + c cw - 1, x0 + (c + 1) cw + 1] (padded by one pixel)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (c < cols && xr >= x0 + c * cw - 1.f && xl <= x0 + (c + 1) * cw + 1.f) m |= 1u << (cols * ry + c);
     }
     return m;
 }
@@ -236,17 +241,18 @@ __device__ __forceinline__ unsigned tile_regions(const TileReach &t, int tx, int
 // The regions (bits as in tile_regions) that blend pixel box wbox of a TS
 // tile overlaps: the box is 8 x 4 PPT pixels, BoxMap's layout.
 template <int TS, int PPT>
-__device__ __forceinline__ unsigned box_regions(int wbox)
+__device__ __forceinline__ unsigned box_regions(int wbox, int cols)
 {
-    constexpr int BW = 8, BH = 4 * PPT, BPR = TS / BW, RW = TS / 2, RH = TS / 4;
+    constexpr int BW = 8, BH = 4 * PPT, BPR = TS / BW, RH = TS / 4;
+    const int RW = TS / cols;
     const int x0 = (wbox % BPR) * BW, y0 = (wbox / BPR) * BH;
     unsigned m = 0u;
 #pragma unroll
     for (int ry = 0; ry < 4; ++ry)
 #pragma unroll
-        for (int rx = 0; rx < 2; ++rx)
-            if (rx * RW < x0 + BW && x0 < (rx + 1) * RW && ry * RH < y0 + BH && y0 < (ry + 1) * RH)
-                m |= 1u << (2 * ry + rx);
+        for (int rx = 0; rx < 4; ++rx)
+            if (rx < cols && rx * RW < x0 + BW && x0 < (rx + 1) * RW && ry * RH < y0 + BH && y0 < (ry + 1) * RH)
+                m |= 1u << (cols * ry + rx);
     return m;
 }
 
@@ -565,14 +571,22 @@ inline int bits_for(long ntiles)
     return b;
 }
 
-// Pair keys carry region masks above the tile id where the tile sort's
-// passes stay below REGION_SHIFT (always for one frame: at most 2^22 tiles).
-inline bool has_regions(long ntiles)
+// The region mode of a tile sort over ntiles tiles of edge TS: the mask
+// sits above the bits the sort's passes cover.  32-pixel tiles take the
+// 4 x 4 grid (mode 2) where the sort covers at most 16 bits, so that a blend
+// box is half a region; other tiles take the 2 x 4 grid (mode 1, exact boxes
+// at 16 pixels, and cheaper to emit) where it covers at most 24; else none.
+inline int region_mode(long ntiles, int TS)
 {
     const int tb = bits_for(ntiles);
-    return (tb <= 8 ? 8 : (tb + 7) / 8 * 8) <= REGION_SHIFT;
+    const int sorted = tb <= 8 ? 8 : (tb + 7) / 8 * 8;
+    return TS == 32 && sorted <= 16 ? 2 : sorted <= 24 ? 1 : 0;
 }
-inline uint32_t tile_key_mask(long ntiles) { return has_regions(ntiles) ? (1u << REGION_SHIFT) - 1u : 0xffffffffu; }
+inline uint32_t tile_key_mask(long ntiles, int TS)
+{
+    const int rm = region_mode(ntiles, TS);
+    return rm ? (1u << region_shift(rm)) - 1u : 0xffffffffu;
+}
 
 // ---------------------------------------------------------------- pair scan
 __global__ void __launch_bounds__(1024)
@@ -674,7 +688,7 @@ template <int TS, int PPT>
 __device__ __forceinline__ void blend_box(int2 rg, const int32_t *__restrict__ pair_gauss,
                                           const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
                                           const float4 *__restrict__ rec2, int W, int H, int tx, int ty, int wbox,
-                                          const uint32_t *__restrict__ pkeys, bool regions,
+                                          const uint32_t *__restrict__ pkeys, int rmode,
                                           float *__restrict__ image, float *__restrict__ T_final,
                                           int32_t *__restrict__ n_last, float4 (*s0)[32], float4 (*s1)[32],
                                           float4 (*s2)[32])
@@ -716,10 +730,11 @@ __device__ __forceinline__ void blend_box(int2 rg, const int32_t *__restrict__ p
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
     auto gauss = [&](int idx) { return idx < n ? pair_gauss[rg.x + idx] : 0; };
-    // the entry's key: its region mask above REGION_SHIFT (all ones without
+    // the entry's key: its region mask above the tile id (all ones without
     // masks), tested against the regions this box overlaps
-    auto keyat = [&](int idx) { return regions && idx < n ? pkeys[rg.x + idx] : 0xffffffffu; };
-    const unsigned bmask = box_regions<TS, PPT>(wbox);
+    auto keyat = [&](int idx) { return rmode && idx < n ? pkeys[rg.x + idx] : 0xffffffffu; };
+    const unsigned bmask = box_regions<TS, PPT>(wbox, region_cols(rmode));
+    const int rshift = region_shift(rmode);
     if (n > 0 && __any_sync(0xffffffffu, any_live)) {
         // indices and keys run two batches ahead of the walk and records one,
         // so no load's latency is waited for in the loop
@@ -745,7 +760,7 @@ __device__ __forceinline__ void blend_box(int2 rg, const int32_t *__restrict__ p
                 const float4 r1 = s1[b][lane];
                 const int ra = __float_as_int(r1.z), rc = __float_as_int(r1.w);
                 hit = (rc & 0xffff) >= bx0 && (ra & 0xffff) <= bx1 && (int)((unsigned)rc >> 16) >= by0 &&
-                      (int)((unsigned)ra >> 16) <= by1 && ((k_cur >> REGION_SHIFT) & bmask) != 0u;
+                      (int)((unsigned)ra >> 16) <= by1 && ((k_cur >> rshift) & bmask) != 0u;
             }
             unsigned hits = __ballot_sync(0xffffffffu, hit);
             // one Gaussian's contribution to pixel k (the front-to-back step),
@@ -828,13 +843,14 @@ constexpr uint32_t KEY_NO_TILE = 0xffffffffu;
 // from (tx0, ty0)); key = kbase + ty kstride + tx, value gval, or
 // KEY_NO_TILE where the Gaussian's ellipse cannot reach the tile (the rect
 // is the ellipse's bounding box: about a fifth of its tiles lie in the
-// corners the ellipse misses).  With regions (tile ids below 2^24), the key
-// carries above REGION_SHIFT the mask of the tile's regions the ellipse
-// reaches, which the blend tests instead of evaluating the ellipse per box;
-// the tile sort covers only the tile bits and moves the mask with the key.
+// corners the ellipse misses).  In region modes 1 and 2 the key carries
+// above the tile id the mask of the tile's regions the ellipse reaches
+// (tile_regions), which the blend tests instead of evaluating the ellipse
+// per box; the tile sort covers only the tile bits and moves the mask with
+// the key.
 // Every store is coalesced; slots at or beyond cap are not written.
 __device__ __forceinline__ void emit_pairs_warp(int n, long off, int gval, int tx0, int ty0, int w, int kbase,
-                                                int kstride, const TileReach &tr, int TS, bool regions, long cap,
+                                                int kstride, const TileReach &tr, int TS, int rmode, long cap,
                                                 uint32_t *__restrict__ keys, int32_t *__restrict__ vals)
 {
     const int lane = threadIdx.x & 31;
@@ -876,8 +892,9 @@ __device__ __forceinline__ void emit_pairs_warp(int n, long off, int gval, int t
             const int local = sl - o_excl;
             const int q = (int)__fdividef((float)local + 0.5f, (float)o_w);  // exact for local < 2^22
             const int tx = o_tx0 + (local - q * o_w), ty = o_ty0 + q;
-            const unsigned m = tile_regions(o_tr, tx, ty, TS);
-            keys[dst] = m ? (uint32_t)(o_base + ty * o_stride + tx) | (regions ? m << REGION_SHIFT : 0u) : KEY_NO_TILE;
+            const unsigned m = tile_regions(o_tr, tx, ty, TS, region_cols(rmode));
+            keys[dst] = m ? (uint32_t)(o_base + ty * o_stride + tx) | (rmode ? m << region_shift(rmode) : 0u)
+                          : KEY_NO_TILE;
             vals[dst] = o_g;
         }
     }
@@ -897,7 +914,7 @@ template <int TS, int PPT>
 __device__ __forceinline__ void blend_backward_box(int2 rg, const int32_t *__restrict__ pair_gauss,
                                                    const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
                                                    const float4 *__restrict__ rec2, int W, int H, int tx, int ty,
-                                                   int wbox, const uint32_t *__restrict__ pkeys, bool regions,
+                                                   int wbox, const uint32_t *__restrict__ pkeys, int rmode,
                                                    const float *__restrict__ T_final,
                                                    const int32_t *__restrict__ n_last,
                                                    const float *__restrict__ d_image, size_t cs,
@@ -948,8 +965,9 @@ __device__ __forceinline__ void blend_backward_box(int2 rg, const int32_t *__res
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
     auto gauss = [&](int idx) { return idx >= 0 ? pair_gauss[rg.x + idx] : 0; };
-    auto keyat = [&](int idx) { return regions && idx >= 0 ? pkeys[rg.x + idx] : 0xffffffffu; };
-    const unsigned bmask = box_regions<TS, PPT>(wbox);
+    auto keyat = [&](int idx) { return rmode && idx >= 0 ? pkeys[rg.x + idx] : 0xffffffffu; };
+    const unsigned bmask = box_regions<TS, PPT>(wbox, region_cols(rmode));
+    const int rshift = region_shift(rmode);
     if (n == 0) return;
     // indices and keys run two batches ahead of the walk and records one
     int g_next = gauss(n - 64 + lane);
@@ -974,7 +992,7 @@ __device__ __forceinline__ void blend_backward_box(int2 rg, const int32_t *__res
             const float4 q1 = s1[b][lane];
             const int ra = __float_as_int(q1.z), rc = __float_as_int(q1.w);
             hit = (rc & 0xffff) >= bx0 && (ra & 0xffff) <= bx1 && (int)((unsigned)rc >> 16) >= by0 &&
-                  (int)((unsigned)ra >> 16) <= by1 && ((k_cur >> REGION_SHIFT) & bmask) != 0u;
+                  (int)((unsigned)ra >> 16) <= by1 && ((k_cur >> rshift) & bmask) != 0u;
         }
         unsigned hits = __ballot_sync(0xffffffffu, hit);
         while (hits) {
