@@ -286,8 +286,9 @@ def choose_tiles(render, st, tile, flush, reps=10):
     or per workload the faster of 16 and 32 pixels (graph replays with the L2
     flushed before each, as the timed region runs them)."""
     import torch
-    if tile:
-        return tile, tile, None
+    edges = [int(x) for x in str(tile).split(",")]
+    if edges != [0]:
+        return edges[0], edges[-1], None
     trials = {}
     for t in (16, 32):
         r = render.Renderer(st, tile=t)
@@ -1051,7 +1052,9 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--tile", type=int, default=0, help="tile edge (8, 16, 32); 0 = the faster of 16 and 32")
+    ap.add_argument("--tile", default="0",
+                    help="tile edge (8, 16, 32) for both workloads, 'F,T' for the frame and the training step, "
+                         "or 0 = per workload the faster of 16 and 32")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the precision / relighting / batching forms")
     ap.add_argument("--forms", default="precision,relight,knn,paper_vis,batch,mlp,densify,stress",
