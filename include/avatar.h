@@ -95,7 +95,11 @@ enum avatar_tune_key {
                                       AVATAR_ERR_TIMEOUT to the status word and counts its offsets from the
                                       earlier keys itself, so the result is unchanged, only slower.  The
                                       tensor-core kernels' completion waits keep their own fixed limit. */
-    AVATAR_TUNE_COUNT = 5
+    AVATAR_TUNE_REGION_MASKS = 5,  /* 1 (default): pair keys carry the mask of the tile regions a
+                                      Gaussian's ellipse reaches and the blends test it; 0: rect test
+                                      alone (the form past 2^24 tiles).  Keep it fixed from a bin to
+                                      the blend and backward that use its lists. */
+    AVATAR_TUNE_COUNT = 6
 };
 int avatar_ctx_set_tuning(avatar_ctx *ctx, int key, int value);
 /* Current value of a knob, or -1 for an invalid key. */

@@ -27,6 +27,7 @@ TUNE_BLEND_BWD_PPT = 1
 TUNE_BATCH_TILE = 2
 TUNE_VIS_CLUSTER = 3
 TUNE_WAIT_LIMIT = 4
+TUNE_REGION_MASKS = 5
 VIS_FACE_CHUNK = 1024   # faces per raster chunk (AVATAR_VIS_FACE_CHUNK)
 PROBE_FFMA, PROBE_IADD3, PROBE_LOP3, PROBE_IMAD = 0, 1, 2, 3   # avatar_probe_kind
 

@@ -70,6 +70,7 @@ extern "C" int avatar_ctx_create(avatar_ctx **out, int device)
     c->tune[AVATAR_TUNE_BLEND_PPT] = 1;
     c->tune[AVATAR_TUNE_BLEND_BWD_PPT] = 1;
     c->tune[AVATAR_TUNE_BATCH_TILE] = 16;
+    c->tune[AVATAR_TUNE_REGION_MASKS] = 1;
     *out = c;
     return AVATAR_OK;
 }
@@ -111,6 +112,9 @@ extern "C" int avatar_ctx_set_tuning(avatar_ctx *ctx, int key, int value)
             break;
         case AVATAR_TUNE_WAIT_LIMIT:
             if (value < 0 || value > (1 << 30)) return AVATAR_ERR_INVALID_ARG;
+            break;
+        case AVATAR_TUNE_REGION_MASKS:
+            if (value != 0 && value != 1) return AVATAR_ERR_INVALID_ARG;
             break;
         default: break;
     }

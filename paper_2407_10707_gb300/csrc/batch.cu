@@ -574,6 +574,9 @@ int prep(avatar_ctx *ctx, const avatar_batch_desc *d, void *ws, size_t ws_bytes,
     return AVATAR_OK;
 }
 
+bool masks_on(const avatar_ctx *ctx) { return ctx->tune[AVATAR_TUNE_REGION_MASKS] != 0; }
+int masks_mode(const avatar_ctx *ctx, long T, int TS) { return region_mode(T, TS, masks_on(ctx)); }
+
 template <int TS, int PPT>
 int launch_blend_batch(const avatar_ctx *ctx, const avatar_batch_desc *d, const BatchWs &w, int T, cudaStream_t st)
 {
@@ -585,7 +588,7 @@ int launch_blend_batch(const avatar_ctx *ctx, const avatar_batch_desc *d, const 
     const long long wblocks = ((long long)std::max(T, 1) * NB + BWD_WARPS - 1) / BWD_WARPS;
     const int grid = (int)std::min<long long>((long long)ctx->sm_count * per_sm, wblocks);
     kern<<<grid, BWD_WARPS * 32, 0, st>>>(w.views, d->V, T, w.ranges, w.pval_a, w.rec0, w.rec1, w.rec2, w.pkey_a,
-                                         region_mode(T, TS), d->images, w.T_final, w.n_last, w.counter);
+                                         masks_mode(ctx, T, TS), d->images, w.T_final, w.n_last, w.counter);
     AV_CHECK_LAUNCH();
     return AVATAR_OK;
 }
@@ -602,7 +605,7 @@ int launch_blend_bwd_batch(const avatar_ctx *ctx, const avatar_batch_desc *d, co
     const long long wblocks = ((long long)std::max(T, 1) * NB + BWD_WARPS - 1) / BWD_WARPS;
     const int grid = (int)std::min<long long>((long long)ctx->sm_count * per_sm, wblocks);
     kern<<<grid, BWD_WARPS * 32, 0, st>>>(w.views, d->V, T, w.ranges, w.pval_a, w.rec0, w.rec1, w.rec2, w.pkey_a,
-                                         region_mode(T, TS), w.T_final, w.n_last, g->d_images, m.VG, w.d_mean2d,
+                                         masks_mode(ctx, T, TS), w.T_final, w.n_last, g->d_images, m.VG, w.d_mean2d,
                                          w.d_conic, w.d_opacity_v, w.d_color, w.counter);
     AV_CHECK_LAUNCH();
     return AVATAR_OK;
@@ -697,11 +700,12 @@ int render_batch(avatar_ctx *ctx, const avatar_batch_desc *d, void *ws, size_t w
     int32_t *v_other = (passes % 2 == 0) ? w.pval_b : w.pval_a;
     emit_batch_kernel<<<grid_cap(ctx, m.VG, 256, 8), 256, 0, st>>>(w.views, m.G, m.VG, TS, w.dval_a, w.offsets,
                                                                     w.npairs, w.rect, w.rec0, w.rec1,
-                                                                    region_mode(T, TS), (long)m.cap, k_emit, v_emit);
+                                                                    masks_mode(ctx, T, TS), (long)m.cap, k_emit,
+                                                                    v_emit);
     AV_CHECK_LAUNCH();
     AV_TRY(radix_sort(k_emit, v_emit, k_other, v_other, passes * 8, d->num_pairs, (int)m.cap, sw, d->status, st, sort_spin_limit(ctx)));
     tile_ranges_kernel<<<ctx->sm_count * 8, 256, 0, st>>>(w.pkey_a, d->num_pairs, (long)m.cap, (int)T,
-                                                          tile_key_mask(T, TS), w.ranges);
+                                                          tile_key_mask(T, TS, masks_on(ctx)), w.ranges);
     AV_CHECK_LAUNCH();
     // persistent blend over every view's tiles
     if (cudaMemsetAsync(w.counter, 0, sizeof(int32_t), st) != cudaSuccess) return AVATAR_ERR_CUDA;

@@ -40,6 +40,7 @@ struct SplatWs {
     float *d_conic;              // [3][G]
     int32_t *tile_order;         // [ntiles] tiles by descending list length (bucketed)
     int NB;
+    bool masks;                  // region masks in the pair keys (AVATAR_TUNE_REGION_MASKS)
 };
 
 // Fixed radix grid: two blocks per SM of a 152-SM GB300.
@@ -291,6 +292,7 @@ int prep(avatar_ctx *ctx, const avatar_splat_args *a, void *ws, size_t ws_bytes,
     AV_TRY(check_splat(a));
     if (!ws || (((uintptr_t)ws) & 255)) return AVATAR_ERR_WORKSPACE;
     if (splat_ws_layout(a, radix_blocks(ctx), ws, ws_bytes, w) > ws_bytes) return AVATAR_ERR_WORKSPACE;
+    w->masks = ctx->tune[AVATAR_TUNE_REGION_MASKS] != 0;
     return AVATAR_OK;
 }
 
@@ -362,7 +364,7 @@ extern "C" int avatar_splat_bin(avatar_ctx *ctx, const avatar_splat_args *a, voi
     const int ntx = (a->cam.width + ts - 1) / ts;
     int tbits = bits_for(ntiles);
     int passes = tbits <= 8 ? 1 : (tbits + 7) / 8;
-    const int rmode = region_mode(ntiles, ts);
+    const int rmode = region_mode(ntiles, ts, w.masks);
     uint32_t *k_emit = (passes % 2 == 0) ? w.pkey_a : w.pkey_b;
     int32_t *v_emit = (passes % 2 == 0) ? a->pair_gauss : w.pval_b;
     uint32_t *k_other = (passes % 2 == 0) ? w.pkey_b : w.pkey_a;
@@ -375,7 +377,7 @@ extern "C" int avatar_splat_bin(avatar_ctx *ctx, const avatar_splat_args *a, voi
                        SortWs{w.sort_hist, w.sort_desc}, a->status, st, sort_spin_limit(ctx)));
     // 5. tile ranges (sorted keys are in pkey_a)
     tile_ranges_kernel<<<ctx->sm_count * 8, 256, 0, st>>>(w.pkey_a, a->num_pairs, cap, ntiles,
-                                                          tile_key_mask(ntiles, ts), (int2 *)a->tile_range);
+                                                          tile_key_mask(ntiles, ts, w.masks), (int2 *)a->tile_range);
     // 6. the blend's tile order, longest lists first
     tile_order_kernel<<<1, 1024, 0, st>>>((const int2 *)a->tile_range, ntiles, w.tile_order);
     AV_CHECK_LAUNCH();
@@ -389,8 +391,8 @@ void launch_blend(const avatar_splat_args *a, const SplatWs &w, int ntiles, int 
     const int blocks = (int)(((long long)ntiles * NB + BWD_WARPS - 1) / BWD_WARPS);
     blend_kernel<TS, PPT><<<blocks, BWD_WARPS * 32, 0, st>>>((const int2 *)a->tile_range, a->pair_gauss, w.rec0,
                                                              w.rec1, w.rec2, a->cam.width, a->cam.height, ntx, ntiles,
-                                                             w.pkey_a, region_mode(ntiles, TS), a->image, a->T_final,
-                                                             a->n_last, w.tile_order);
+                                                             w.pkey_a, region_mode(ntiles, TS, w.masks), a->image,
+                                                             a->T_final, a->n_last, w.tile_order);
 }
 
 template <int TS>
@@ -440,8 +442,8 @@ void launch_blend_bwd(const avatar_splat_args *a, const avatar_splat_grads *g, c
     const int blocks = (int)(((long long)ntiles * NB + BWD_WARPS - 1) / BWD_WARPS);
     blend_backward_kernel<TS, PPT><<<blocks, BWD_WARPS * 32, 0, st>>>(
         (const int2 *)a->tile_range, a->pair_gauss, w.rec0, w.rec1, w.rec2, a->cam.width, a->cam.height, ntx, ntiles,
-        w.pkey_a, region_mode(ntiles, TS), a->T_final, a->n_last, g->d_image, G, w.d_mean2d, w.d_conic, g->d_opacity,
-        g->d_color, w.tile_order);
+        w.pkey_a, region_mode(ntiles, TS, w.masks), a->T_final, a->n_last, g->d_image, G, w.d_mean2d, w.d_conic,
+        g->d_opacity, g->d_color, w.tile_order);
 }
 
 template <int TS>

@@ -576,15 +576,16 @@ inline int bits_for(long ntiles)
 // 4 x 4 grid (mode 2) where the sort covers at most 16 bits, so that a blend
 // box is half a region; other tiles take the 2 x 4 grid (mode 1, exact boxes
 // at 16 pixels, and cheaper to emit) where it covers at most 24; else none.
-inline int region_mode(long ntiles, int TS)
+inline int region_mode(long ntiles, int TS, bool allowed = true)
 {
+    if (!allowed) return 0;
     const int tb = bits_for(ntiles);
     const int sorted = tb <= 8 ? 8 : (tb + 7) / 8 * 8;
     return TS == 32 && sorted <= 16 ? 2 : sorted <= 24 ? 1 : 0;
 }
-inline uint32_t tile_key_mask(long ntiles, int TS)
+inline uint32_t tile_key_mask(long ntiles, int TS, bool allowed = true)
 {
-    const int rm = region_mode(ntiles, TS);
+    const int rm = region_mode(ntiles, TS, allowed);
     return rm ? (1u << region_shift(rm)) - 1u : 0xffffffffu;
 }
 

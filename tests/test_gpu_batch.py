@@ -134,6 +134,25 @@ def test_batch_graph_replay_is_identical(gpu, batch):
         assert rel_err(N(br.grads[k]), N(v)) < 1e-5, k   # atomics may add in another order
 
 
+def test_batch_images_do_not_depend_on_region_masks(gpu, batch):
+    """The batch's pair keys with and without region masks give the same
+    images bit for bit (AVATAR_TUNE_REGION_MASKS, the form past 2^24 tiles)."""
+    api, render = gpu
+    from paper_2407_10707_gb300 import _lib as L
+    lib, ctx = L.load(), api.context()
+    imgs = []
+    try:
+        for masks in (1, 0):
+            assert lib.avatar_ctx_set_tuning(ctx, L.TUNE_REGION_MASKS, masks) == 0
+            br = render.BatchRenderer(batch, tile=32)
+            torch.cuda.synchronize()
+            br.check()
+            imgs.append(br.images.clone())
+    finally:
+        lib.avatar_ctx_set_tuning(ctx, L.TUNE_REGION_MASKS, 1)
+    assert torch.equal(imgs[0], imgs[1])
+
+
 def test_pair_overflow_is_reported(gpu, batch):
     api, render = gpu
     from paper_2407_10707_gb300 import _lib as L

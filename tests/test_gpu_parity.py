@@ -383,6 +383,37 @@ def test_image_is_tile_size_invariant_and_graph_replay_is_identical(gpu):
     assert np.array_equal(N(r.sb.image), eager)
 
 
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_region_masks_change_neither_image_nor_gradients(gpu, tile):
+    """Pair keys carry the mask of the tile regions a Gaussian's ellipse
+    reaches and the blends skip the boxes it misses; with the masks off
+    (AVATAR_TUNE_REGION_MASKS = 0, the form past 2^24 tiles) the blends use
+    the rect test alone.  Both must give the same image bit for bit (the
+    skipped hits add nothing) and the same gradients up to the order of the
+    atomic additions."""
+    api, render = gpu
+    from paper_2407_10707_gb300 import _lib as L
+    lib, ctx = L.load(), api.context()
+    st = render.scene_tensors(scene("c1_small"))
+    target = torch.as_tensor(np.full((3, 256, 256), 0.3, np.float32), device="cuda")
+    out = {}
+    try:
+        for masks in (1, 0):
+            assert lib.avatar_ctx_set_tuning(ctx, L.TUNE_REGION_MASKS, masks) == 0
+            ts = render.TrainStep(st, target, tile=tile)
+            torch.cuda.synchronize()
+            ts.check()
+            out[masks] = (N(ts.sb.image).copy(), {k: N(v).copy() for k, v in ts.grads().items()},
+                          int(N(ts.sb.num_pairs)[0]))
+    finally:
+        lib.avatar_ctx_set_tuning(ctx, L.TUNE_REGION_MASKS, 1)
+    assert lib.avatar_ctx_set_tuning(ctx, L.TUNE_REGION_MASKS, 2) != 0
+    assert out[1][2] == out[0][2]                       # the same pairs are emitted either way
+    assert np.array_equal(out[1][0], out[0][0])
+    for k in out[1][1]:
+        assert rel_err(out[1][1][k], out[0][1][k]) < 1e-5, k
+
+
 def test_pair_overflow_is_reported_not_faulted(gpu):
     api, render = gpu
     st = render.scene_tensors(scene("c3_fd"))
