@@ -542,8 +542,8 @@ skin_gaussians_backward_kernel(avatar_skin_args a, avatar_skin_grads gr, const V
 #pragma unroll
         for (int j = 0; j < K; ++j) sdot += dub[j] * s.ub[j];
         float dxg[3] = {dxb[0], dxb[1], dxb[2]};
-#pragma unroll
         const float ius = 1.f / s.usum;
+#pragma unroll
         for (int j = 0; j < K; ++j) {
             float du = (dub[j] - sdot) * ius;
             float d = s.dist[j];
