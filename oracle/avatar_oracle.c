@@ -823,7 +823,10 @@ void orc_project(int G, const double *xd, const double *cov, const double *opaci
 /*   order; T = 1; for each: if T(1-alpha) < 1e-4 stop; C += c alpha T;  */
 /*   T *= 1 - alpha.  Outputs C, T_final, the contributor count and an   */
 /*   ambiguity flag (some traversed alpha within 2e-5 (relative) of      */
-/*   1/255, or the stop test within 1e-7 of 1e-4).                        */
+/*   1/255, widened by the FP32 rounding bound of the exponent the       */
+/*   kernel evaluates, 6 u (|q|_abs / 2 + |ln o|) with u = 2^-24 and     */
+/*   |q|_abs = |a| dx^2 + 2 |b dx dy| + |c| dy^2: large for thin         */
+/*   ellipses, whose terms cancel; or the stop test within 1e-7 of 1e-4). */
 /* pix: list of npix pixel indices (j*W+i), or NULL for all W*H.         */
 /* ------------------------------------------------------------------ */
 typedef struct {
@@ -861,7 +864,10 @@ void orc_composite(int G, int W, int Hh, const double *mean2d, const double *con
                 double q = conic[3 * g] * dx * dx + 2.0 * conic[3 * g + 1] * dx * dy +
                            conic[3 * g + 2] * dy * dy;
                 double araw = opacity[g] * exp(-0.5 * q);
-                int near_t = fabs(araw * 255.0 - 1.0) < 2e-5;
+                double qabs = fabs(conic[3 * g]) * dx * dx + 2.0 * fabs(conic[3 * g + 1] * dx * dy) +
+                              fabs(conic[3 * g + 2]) * dy * dy;
+                double margin = 2e-5 + 6.0 * 0x1p-24 * (0.5 * qabs + fabs(log(opacity[g])));
+                int near_t = fabs(araw * 255.0 - 1.0) < margin;
                 double a = araw < 0.99 ? araw : 0.99;
                 if (a >= 1.0 / 255.0 || near_t) {
                     list[m].depth = depth[g];

@@ -341,8 +341,36 @@ def test_blend_matches_bruteforce_oracle(gpu, name, tile, ppt):
         assert lib.avatar_ctx_set_tuning(api.context(), L.TUNE_BLEND_PPT, 1) == 0
 
 
-def _blend_case(api, name, tile):
-    sc, ref, xd, cov, op, col, cull = _splat_inputs(name)
+def _elongated_cov(G, seed=5, scales=(0.12, 2e-4, 2e-4)):
+    """Covariances R diag(s^2) R^T of random rotations with one axis 600x
+    the others (projected: ellipses up to 180 pixels long, det / (a c) of
+    the conic down to 1e-3), in the [G][6] (xx, xy, xz, yy, yz, zz) layout."""
+    rng = np.random.default_rng(seed)
+    q = rng.normal(size=(G, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q.T
+    R = np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                  2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                  2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], 1).reshape(G, 3, 3)
+    s = np.asarray(scales)[None] * rng.uniform(0.5, 2.0, size=(G, 3))
+    S = np.einsum("gij,gj,gkj->gik", R, s * s, R)
+    return f32(np.stack([S[:, 0, 0], S[:, 0, 1], S[:, 0, 2], S[:, 1, 1], S[:, 1, 2], S[:, 2, 2]], 1))
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_blend_of_elongated_gaussians_matches_bruteforce_oracle(gpu, tile):
+    """Thin, long, rotated ellipses spanning up to six 32-pixel tiles: the
+    tile lists and region masks drop only pairs whose ellipse cannot reach a
+    pixel (the reach tests run on conics near their degenerate limit), so the
+    image meets brute-force compositing as everywhere else."""
+    api, render = gpu
+    sc = scene("c1_small")
+    _blend_case(api, "c1_small", tile, cov=_elongated_cov(sc.avatar.G))
+
+
+def _blend_case(api, name, tile, cov=None):
+    sc, ref, xd, cov0, op, col, cull = _splat_inputs(name)
+    cov = cov0 if cov is None else cov
     pr = O.project(xd.astype(np.float64), cov.astype(np.float64), op.astype(np.float64), cull, sc.camera)
     m32, c32, d32 = f32(pr["mean2d"]), f32(pr["conic"]), f32(pr["depth"])
     W, H = sc.camera.width, sc.camera.height
