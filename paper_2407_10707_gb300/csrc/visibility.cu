@@ -36,6 +36,7 @@ struct VisParams {
     int H, M, biasq;
     int rows_per_cta;
     int inv_rows;  // ceil(2^20 / rows_per_cta): row / rows_per_cta == (row * inv_rows) >> 20 for row < 2^11
+    int route;     // vertex words routed to the CTA owning their first vertex's depth row (inbox of NW ints)
 };
 
 // blockIdx.y = pose: xp holds gridDim.y poses ([3][B Nv]), qv [B Nv].
@@ -111,6 +112,7 @@ constexpr int VIS_TPT = VIS_CHUNK / VIS_THREADS; // triangles per thread per chu
 constexpr int VIS_VCAP = 1024;                   // cached projected vertices per chunk (10-bit offsets)
 static_assert(VIS_VCAP == 1024, "packed face offsets are 10 bits");
 constexpr int VIS_SLAB_BYTES = 32 * 1024;        // depth-map share of one CTA (R <= 256)
+constexpr size_t VIS_INBOX_MAX = 8 * 1024;       // routed vertex test: at most 2,048 words (65,536 vertices)
 
 __device__ __forceinline__ uint2 pack_proj(const Proj &q)
 {
@@ -351,8 +353,14 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
     // chunks (mostly back-facing) takes more and the cluster reaches its
     // barrier together; the depth map is a minimum, so the order is free.
     __shared__ int s_chunk_ctr, s_next;
+    __shared__ int s_in_count, s_in_next;  // this CTA's inbox of vertex words (routed test)
+    int *inbox = reinterpret_cast<int *>(vcache + VIS_VCAP);
     int chunk = rank;
     if (CL > 1 && rank == 0 && threadIdx.x == 0) s_chunk_ctr = CL;
+    if (threadIdx.x == 0) {
+        s_in_count = 0;
+        s_in_next = 0;
+    }
     if (chunk < nchunks) load_faces(chunk, cur);
     cluster.sync();
 
@@ -402,19 +410,34 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
         for (int t = 0; t < TPT; ++t) cur[t] = nxt[t];
         chunk = next;
     }
-    cluster.sync();
-
-    // ---- depth-test vertices: one warp -> 32-bit words of this direction,
-    // four words in flight per iteration
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = NT / 32;
     const int wstride = CL * nwarps;
-    for (int w0 = rank * nwarps + warp; w0 < p.NW; w0 += 4 * wstride) {
+    if (CL > 1 && p.route) {
+        // route every vertex word to the CTA owning the depth row of its
+        // first vertex: a word's 32 vertices lie close on the surface, so
+        // that CTA reads most of their depths from its own slab
+        for (int wb = (rank * nwarps + warp) * 32; wb < p.NW; wb += wstride * 32) {
+            const int w = wb + lane;
+            if (w < p.NW) {
+                int owner = rank;
+                const Proj pr = project_vertex(__ldg(qv + (size_t)w * 32), B, p);
+                if (pr.in) owner = ((pr.Y >> 4) * p.inv_rows) >> 20;
+                const int slot = atomicAdd(cluster.map_shared_rank(&s_in_count, owner), 1);
+                cluster.map_shared_rank(inbox, owner)[slot] = w;
+            }
+        }
+    }
+    cluster.sync();
+
+    // ---- depth-test vertices: one warp -> 32-bit words of this direction,
+    // four words in flight per iteration (a word index of -1: none)
+    auto test_words = [&](const int (&ws)[4]) {
         int4 qq[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            int v = (w0 + u * wstride) * 32 + lane;
-            qq[u] = (w0 + u * wstride < p.NW && v < p.Nv) ? __ldg(qv + v) : make_int4(0, 0, 0, 2);
+            int v = ws[u] * 32 + lane;
+            qq[u] = (ws[u] >= 0 && v < p.Nv) ? __ldg(qv + v) : make_int4(0, 0, 0, 2);
         }
         int dep[4];
         Proj pr[4];
@@ -431,10 +454,36 @@ vis_raster_test_kernel(VisParams p, const int4 *__restrict__ qv, const int32_t *
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int w = w0 + u * wstride;
             bool vis = !pr[u].in || dep[u] == EMPTY_DEPTH || pr[u].Z <= dep[u] + p.biasq;
             unsigned word = __ballot_sync(0xffffffffu, vis && qq[u].w != 2);
-            if (lane == 0 && w < p.NW) dirbits[((size_t)blockIdx.z * p.D + d) * p.NW + w] = word;
+            if (lane == 0 && ws[u] >= 0) dirbits[((size_t)blockIdx.z * p.D + d) * p.NW + ws[u]] = word;
+        }
+    };
+    if (CL > 1 && p.route) {
+        // this CTA's inbox first, then the others' (a CTA whose slab holds
+        // much of the body has more words than the rest): four words per grab
+        for (int k = 0; k < CL; ++k) {
+            const int owner = rank + k < CL ? rank + k : rank + k - CL;
+            int *nextp = cluster.map_shared_rank(&s_in_next, owner);
+            const int count = *cluster.map_shared_rank(&s_in_count, owner);
+            const int *box = cluster.map_shared_rank(inbox, owner);
+            for (;;) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(nextp, 4);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (base >= count) break;
+                int ws[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) ws[u] = base + u < count ? box[base + u] : -1;
+                test_words(ws);
+            }
+        }
+    } else {
+        for (int w0 = rank * nwarps + warp; w0 < p.NW; w0 += 4 * wstride) {
+            int ws[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) ws[u] = w0 + u * wstride < p.NW ? w0 + u * wstride : -1;
+            test_words(ws);
         }
     }
     cluster.sync();  // keep every slab alive until all remote reads are done
@@ -857,6 +906,11 @@ int vis_run(avatar_ctx *ctx, const avatar_vis_args *a, int B, void *ws, size_t w
     p.rows_per_cta = a->R / CL;
     p.inv_rows = ((1 << 20) + p.rows_per_cta - 1) / p.rows_per_cta;
     size_t smem = (size_t)p.rows_per_cta * a->R * sizeof(int) + (size_t)VIS_VCAP * sizeof(uint2);
+    // the routed vertex test keeps an inbox of word indices per CTA (a CTA
+    // may receive every word), where it fits beside four slabs per SM
+    const size_t inbox = ((size_t)p.NW * sizeof(int) + 15) & ~(size_t)15;
+    p.route = CL > 1 && inbox <= VIS_INBOX_MAX && smem + inbox <= (size_t)ctx->max_smem_optin;
+    if (p.route) smem += inbox;
 
     int qgrid = (int)((a->Nv + 255) / 256);
     if (qgrid > ctx->sm_count * 8) qgrid = ctx->sm_count * 8;
@@ -1000,6 +1054,7 @@ extern "C" int avatar_visibility_soft(avatar_ctx *ctx, const avatar_vis_soft_arg
         qc[i] = (int)q;
     }
     VisParams p;
+    p.route = 0;
     p.B = 1;
     p.Nv = b.Nv;
     p.F = b.F;
