@@ -224,20 +224,10 @@ __device__ __forceinline__ bool gauss_gather(const avatar_skin_args &a, const Ve
         }
         s.idx[j] = v;
     }
+    // one pass: each neighbour's record is read once, the sums taken with the
+    // unnormalised weights 1/d_j and scaled by 1/sum_j(1/d_j) at the end, so
+    // no neighbour's loads wait for another's distance
     s.usum = 0.f;
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-        float4 xr = __ldg(&rec[s.idx[j]].xr);
-        float ex = s.x[0] - xr.x, ey = s.x[1] - xr.y, ez = s.x[2] - xr.z;
-        float d = sqrtf(ex * ex + ey * ey + ez * ez);
-        s.dist[j] = d;
-        float u = 1.0f / fmaxf(d, 1e-8f);
-        s.ub[j] = u;
-        s.usum += u;
-    }
-    float inv = 1.0f / s.usum;
-#pragma unroll
-    for (int j = 0; j < K; ++j) s.ub[j] *= inv;
 #pragma unroll
     for (int i = 0; i < 12; ++i) s.A[i] = 0.f;
     s.a[0] = s.a[1] = s.a[2] = s.r = s.p = 0.f;
@@ -245,9 +235,14 @@ __device__ __forceinline__ bool gauss_gather(const avatar_skin_args &a, const Ve
 #pragma unroll
     for (int j = 0; j < K; ++j) {
         const VertexRec *vr = rec + s.idx[j];
-        float u = s.ub[j];
         float4 a0 = __ldg(&vr->a0), a1 = __ldg(&vr->a1), a2 = __ldg(&vr->a2);
         float4 xr = __ldg(&vr->xr), ap = __ldg(&vr->ap), n0 = __ldg(&vr->nd0), d12 = __ldg(&vr->d12);
+        float ex = s.x[0] - xr.x, ey = s.x[1] - xr.y, ez = s.x[2] - xr.z;
+        float d = sqrtf(ex * ex + ey * ey + ez * ez);
+        s.dist[j] = d;
+        float u = 1.0f / fmaxf(d, 1e-8f);
+        s.ub[j] = u;
+        s.usum += u;
         s.A[0] = fmaf(u, a0.x, s.A[0]);
         s.A[1] = fmaf(u, a0.y, s.A[1]);
         s.A[2] = fmaf(u, a0.z, s.A[2]);
@@ -272,11 +267,30 @@ __device__ __forceinline__ bool gauss_gather(const avatar_skin_args &a, const Ve
         s.dx[1] = fmaf(u, d12.x, s.dx[1]);
         s.dx[2] = fmaf(u, d12.y, s.dx[2]);
     }
+    const float inv = 1.0f / s.usum;
+#pragma unroll
+    for (int j = 0; j < K; ++j) s.ub[j] *= inv;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) s.A[i] *= inv;
+    s.a[0] *= inv;
+    s.a[1] *= inv;
+    s.a[2] *= inv;
+    s.r *= inv;
+    s.p *= inv;
+    s.n[0] *= inv;
+    s.n[1] *= inv;
+    s.n[2] *= inv;
+    s.dx[0] *= inv;
+    s.dx[1] *= inv;
+    s.dx[2] *= inv;
     return ok;
 }
 
+// Three blocks per SM (80 registers): the one-pass gather keeps the four
+// neighbours' 28 record loads in flight; unbounded it takes 87 registers and
+// two blocks.
 template <int K>
-__global__ void __launch_bounds__(SKIN_THREADS)
+__global__ void __launch_bounds__(SKIN_THREADS, 3)
 skin_gaussians_kernel(avatar_skin_args a, const VertexRec *__restrict__ rec)
 {
     // blockIdx.y = pose of a batch: xd, nd [3][B G], cov [6][B G], records
