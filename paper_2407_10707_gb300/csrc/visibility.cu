@@ -162,8 +162,11 @@ __device__ __forceinline__ void raster_triangle(uint2 pa, uint2 pb, uint2 pc, in
             area = -area;
         }
     }
-    int i0 = max(0, (min(ax, min(bx, cx)) + 7) >> 4), i1 = min(R - 1, (max(ax, max(bx, cx)) - 8) >> 4);
-    int j0 = max(0, (min(ay, min(by, cy)) + 7) >> 4), j1 = min(R - 1, (max(ay, max(by, cy)) - 8) >> 4);
+    // pixel centres 16i+8 inside the box; every vertex lies in [0, 16R), so
+    // i0 >= 0 and i1 <= R - 1 hold without clamps (i1 = -1 when all lie
+    // left of the first centre)
+    int i0 = (min(ax, min(bx, cx)) + 7) >> 4, i1 = (max(ax, max(bx, cx)) - 8) >> 4;
+    int j0 = (min(ay, min(by, cy)) + 7) >> 4, j1 = (max(ay, max(by, cy)) - 8) >> 4;
     if (i0 > i1 || j0 > j1) return;
     // depth = az + floor((wb (bz - az) + wc (cz - az)) / area) since wa + wb + wc = area;
     // 32-bit arithmetic when the products provably fit, else 64-bit
@@ -209,8 +212,11 @@ __device__ __forceinline__ bool triangle_appears(uint2 pa, uint2 pb, uint2 pc, c
     int bx = pb.x & 0xffff, by = pb.x >> 16, bz = (int)pb.y;
     int cx = pc.x & 0xffff, cy = pc.x >> 16, cz = (int)pc.y;
     const int R = p.R;
-    int i0 = max(0, (min(ax, min(bx, cx)) + 7) >> 4), i1 = min(R - 1, (max(ax, max(bx, cx)) - 8) >> 4);
-    int j0 = max(0, (min(ay, min(by, cy)) + 7) >> 4), j1 = min(R - 1, (max(ay, max(by, cy)) - 8) >> 4);
+    // pixel centres 16i+8 inside the box; every vertex lies in [0, 16R), so
+    // i0 >= 0 and i1 <= R - 1 hold without clamps (i1 = -1 when all lie
+    // left of the first centre)
+    int i0 = (min(ax, min(bx, cx)) + 7) >> 4, i1 = (max(ax, max(bx, cx)) - 8) >> 4;
+    int j0 = (min(ay, min(by, cy)) + 7) >> 4, j1 = (max(ay, max(by, cy)) - 8) >> 4;
     if (i0 > i1 || j0 > j1) return false;
     int area = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
     if (CULL_BACK) {
